@@ -1,0 +1,196 @@
+"""Seeded synthetic workloads for the free-mesh transform (FMT).
+
+This module only draws inputs: point clouds, sample values of the test
+functions and target points.  It holds none of the method's arithmetic
+(no quantisation, no basis, no fit), so both the CPU oracle and the CUDA
+path may take their inputs from here.
+
+Random numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+"Parallel random numbers: as easy as 1, 2, 3", SC'11), written out below
+from its published definition so that every machine draws identical bits.
+
+Workloads follow the paper's experiments (random grids in [0,1]^3 with
+3-D Franke values, Sec. 3 Eq. eqF1 and Sec. 4) at the sizes of the
+benchmark configurations:
+
+* ``small``  : 4096 uniform points, p=4, depth 3, min 64, tol 1e-4, 1e4 targets
+* ``scale``  : 1e6 points (half uniform, half in 8 Gaussian clusters,
+               sigma 0.05, centres U[0.2,0.8]^3, rejection into [0,1)^3),
+               p=8, depth 7, min 128, tol 1e-8, 1e7 targets
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 1511013530
+
+_M0 = np.uint64(0xD2511F53)
+_M1 = np.uint64(0xCD9E8D57)
+_W0 = np.uint64(0x9E3779B9)
+_W1 = np.uint64(0xBB67AE85)
+_MASK = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32 with 10 rounds.
+
+    ctr: four uint32 arrays (broadcastable), key: two uint32 scalars.
+    Returns four uint32 arrays.  Each round multiplies words 0 and 2 by
+    the Philox constants, swaps hi/lo halves and xors in the round key;
+    the key is bumped by the Weyl constants between rounds.
+    """
+    c0, c1, c2, c3 = (np.asarray(c, dtype=np.uint64) & _MASK for c in ctr)
+    k0 = np.uint64(int(key[0]) & 0xFFFFFFFF)
+    k1 = np.uint64(int(key[1]) & 0xFFFFFFFF)
+    for _ in range(10):
+        p0 = _M0 * c0
+        p1 = _M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+        k0 = (k0 + _W0) & _MASK
+        k1 = (k1 + _W1) & _MASK
+    return tuple(c.astype(np.uint32) for c in (c0, c1, c2, c3))
+
+
+def uniform(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """n doubles in [0,1) from counters (i, stream, 0, 0), i = offset/2 ...
+
+    Each counter yields two doubles with 53 random bits each
+    (27 high bits from one word, 26 from the next).  ``offset`` must be even.
+    """
+    if n <= 0:
+        return np.zeros(0, dtype=np.float64)
+    assert offset % 2 == 0
+    ncounter = (n + 1) // 2
+    i = np.arange(offset // 2, offset // 2 + ncounter, dtype=np.uint64)
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    z = np.zeros_like(i)
+    w0, w1, w2, w3 = philox4x32_10((i, np.full_like(i, stream), z, z), key)
+    a = np.empty(2 * ncounter, dtype=np.float64)
+    a[0::2] = ((w0 >> 5).astype(np.float64) * 67108864.0 + (w1 >> 6).astype(np.float64))
+    a[1::2] = ((w2 >> 5).astype(np.float64) * 67108864.0 + (w3 >> 6).astype(np.float64))
+    a *= 2.0 ** -53
+    return a[:n]
+
+
+def normal(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """n standard normals by Box-Muller on consecutive uniform pairs.
+
+    Normal 2s uses cos, 2s+1 uses sin of the pair (u[2s], u[2s+1]) drawn at
+    uniform offset ``offset + 2s``; 1-u keeps the logarithm finite.
+    """
+    if n <= 0:
+        return np.zeros(0, dtype=np.float64)
+    npair = (n + 1) // 2
+    u = uniform(seed, stream, 2 * npair, offset)
+    rad = np.sqrt(-2.0 * np.log1p(-u[0::2]))
+    ang = 2.0 * math.pi * u[1::2]
+    z = np.empty(2 * npair, dtype=np.float64)
+    z[0::2] = rad * np.cos(ang)
+    z[1::2] = rad * np.sin(ang)
+    return z[:n]
+
+
+def franke_bj(x, y, z):
+    """3-D Franke function as written in the benchmark configurations:
+    the second exponential has (9y+1)/10 and (9z+1)/10 unsquared."""
+    x, y, z = (np.asarray(a, dtype=np.float64) for a in (x, y, z))
+    return (0.75 * np.exp(-((9 * x - 2) ** 2 + (9 * y - 2) ** 2 + (9 * z - 2) ** 2) / 4)
+            + 0.75 * np.exp(-(9 * x + 1) ** 2 / 49 - (9 * y + 1) / 10 - (9 * z + 1) / 10)
+            + 0.5 * np.exp(-((9 * x - 7) ** 2 + (9 * y - 3) ** 2 + (9 * z - 5) ** 2) / 4)
+            - 0.2 * np.exp(-(9 * x - 4) ** 2 - (9 * y - 7) ** 2 - (9 * z - 5) ** 2))
+
+
+def franke_paper(x, y, z):
+    """3-D Franke function of Sec. 3, Eq. eqF1 (second term squares 9y+1, 9z+1)."""
+    x, y, z = (np.asarray(a, dtype=np.float64) for a in (x, y, z))
+    return (0.75 * (np.exp(-0.25 * ((9 * x - 2) ** 2 + (9 * y - 2) ** 2 + (9 * z - 2) ** 2))
+                    + np.exp(-(9 * x + 1) ** 2 / 49 - (9 * y + 1) ** 2 / 10 - (9 * z + 1) ** 2 / 10))
+            + 0.5 * np.exp(-0.25 * ((9 * x - 7) ** 2 + (9 * y - 3) ** 2 + (9 * z - 5) ** 2))
+            - 0.2 * np.exp(-(9 * x - 4) ** 2 - (9 * y - 7) ** 2 - (9 * z - 5) ** 2))
+
+
+def uniform_points(seed: int, stream: int, n: int):
+    a = uniform(seed, stream, 3 * n).reshape(n, 3) if n > 0 else np.zeros((0, 3))
+    return np.ascontiguousarray(a[:, 0]), np.ascontiguousarray(a[:, 1]), np.ascontiguousarray(a[:, 2])
+
+
+def clustered_points(seed: int, stream: int, n: int, centre, sigma: float):
+    """n points from an isotropic Gaussian around ``centre``; candidates that
+    fall outside [0,1)^3 are rejected and the next candidate is taken.
+    Candidate t uses normals 3t, 3t+1, 3t+2 of the stream, so the result
+    does not depend on how candidates are batched."""
+    out = np.zeros((0, 3))
+    t0 = 0                                   # first candidate of the batch (kept even)
+    batch = max(64, 2 * n + (n % 2))         # even, so normal 3*t0 starts a Box-Muller pair
+    c = np.asarray(centre, dtype=np.float64).reshape(1, 3)
+    while out.shape[0] < n:
+        z = normal(seed, stream, 3 * batch, offset=3 * t0)
+        cand = c + sigma * z.reshape(batch, 3)
+        ok = np.all((cand >= 0.0) & (cand < 1.0), axis=1)
+        out = np.concatenate([out, cand[ok]], axis=0)
+        t0 += batch
+    out = out[:n]
+    return np.ascontiguousarray(out[:, 0]), np.ascontiguousarray(out[:, 1]), np.ascontiguousarray(out[:, 2])
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    degree: int
+    max_depth: int
+    min_pts: int
+    tol_rel: float
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    f: np.ndarray
+    xq: np.ndarray
+    yq: np.ndarray
+    zq: np.ndarray
+
+    @property
+    def n(self):
+        return int(self.x.shape[0])
+
+    @property
+    def m(self):
+        return int(self.xq.shape[0])
+
+
+def small(n: int = 4096, n_targets: int = 10_000, seed: int = SEED_BASE + 0) -> Workload:
+    """Uniform cloud with 3-D Franke values, p=4, depth 3, min 64, tol 1e-4."""
+    x, y, z = uniform_points(seed, 1, n)
+    xq, yq, zq = uniform_points(seed, 7, n_targets)
+    return Workload("small_fp64_n%d_p4_d3" % n, 4, 3, 64, 1e-4, x, y, z, franke_bj(x, y, z), xq, yq, zq)
+
+
+def scale(n: int = 1_000_000, n_targets: int = 10_000_000, seed: int = SEED_BASE + 1,
+          degree: int = 8, max_depth: int = 7, min_pts: int = 128, tol_rel: float = 1e-8) -> Workload:
+    """Half uniform, half in 8 Gaussian clusters (sigma 0.05, centres U[0.2,0.8]^3)."""
+    n_uni = n // 2
+    n_clu = n - n_uni
+    xs, ys, zs = [], [], []
+    x, y, z = uniform_points(seed, 1, n_uni)
+    xs.append(x); ys.append(y); zs.append(z)
+    centres = 0.2 + 0.6 * uniform(seed, 2, 24).reshape(8, 3)
+    per = [n_clu // 8 + (1 if c < n_clu % 8 else 0) for c in range(8)]
+    for c in range(8):
+        x, y, z = clustered_points(seed, 100 + c, per[c], centres[c], 0.05)
+        xs.append(x); ys.append(y); zs.append(z)
+    x, y, z = np.concatenate(xs), np.concatenate(ys), np.concatenate(zs)
+    xq, yq, zq = uniform_points(seed, 7, n_targets)
+    return Workload("scale_fp64_n%d_p%d_d%d" % (n, degree, max_depth), degree, max_depth, min_pts, tol_rel,
+                    x, y, z, franke_bj(x, y, z), xq, yq, zq)
+
+
+def errors(pred, truth):
+    """E_rms and E_inf of Sec. 4 (RMS and max absolute deviation)."""
+    d = np.asarray(pred, dtype=np.float64) - np.asarray(truth, dtype=np.float64)
+    if d.size == 0:
+        return 0.0, 0.0
+    return float(np.sqrt(np.mean(d * d))), float(np.max(np.abs(d)))
