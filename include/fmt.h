@@ -1,0 +1,232 @@
+/*
+ * fmt.h -- C ABI of the GB300 free-mesh transform (FMT) library, libfmt.so.
+ *
+ * The free-mesh transform (Challacombe, "A N-Body Solver for Free Mesh
+ * Interpolation", arXiv 1511.01353) fits scattered samples f(x_i) with a
+ * tree of local polynomials: Alg. 1 recursively splits an octree, Alg. 2 fits
+ * each node's current residual by least squares over the geometric moments
+ * Lambda_lmn = u^l v^m w^n / (l! m! n!), l+m+n <= p, and hands the residual
+ * to the children whose RMS error is still above tau.  The interpolant at a
+ * target is the sum of the polynomials of the nodes on its octree path
+ * (Sec. 2, end: f(r) = Lambda(r) . F).
+ *
+ * Conventions shared by every call:
+ *  - All functions are extern "C", take plain pointers and sizes, and never
+ *    throw.  They return fmt_status; details of the last failure are in
+ *    fmt_last_error().
+ *  - "device" pointers are CUDA device (or managed) memory on the current
+ *    device; "host" pointers are ordinary host memory.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Work is enqueued on it asynchronously; calls marked
+ *    "synchronises" wait for the stream before returning.
+ *  - Caller-owned inputs must stay valid and unmodified until the stream has
+ *    reached the call.  The tree owns its sorted copies, scratch and
+ *    coefficients; fmt_tree_free releases them.
+ *  - Errors are sticky per tree: after a device-side error every later call
+ *    on that tree returns the same status.
+ *  - Precision: everything on the FP64 path is IEEE binary64.  The
+ *    quantisation and node-frame arithmetic use no fused multiply-add so the
+ *    tree structure is bit-reproducible.
+ */
+#ifndef FMT_H
+#define FMT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FMT_OK = 0,
+  FMT_EINVAL = 1,    /* bad argument, non-finite input, or call out of order */
+  FMT_ENOMEM = 2,    /* device or host allocation failed */
+  FMT_ECUDA = 3,     /* a CUDA runtime call failed */
+  FMT_ETIMEOUT = 4,  /* reserved for bounded device waits */
+  FMT_EINTERNAL = 5  /* a device-side consistency check failed */
+} fmt_status;
+
+#define FMT_FP64 0  /* FP64 path (the only one implemented) */
+#define FMT_MIXED 1 /* reserved: split-BF16/TF32 products with FP64 refinement */
+
+#define FMT_MAX_DEPTH 21  /* 21 bits per axis in the Morton code */
+#define FMT_MAX_DEGREE 14 /* nmono(14) = 680, the largest order in Sec. 3 */
+
+/* Node flags (fmt_tree_export node_flags[]). */
+#define FMT_FLAG_NEAR_TAU 1     /* created by a decision with |E - tau| <= 1e-9 tau */
+#define FMT_FLAG_RANK 2         /* back substitution dropped dependent columns */
+#define FMT_FLAG_DEG_CLAMPED 4  /* root with N < nmono: degree lowered */
+
+/*
+ * Parameters of Alg. 1 (L, nmono, tau and the root box P) plus the depth and
+ * point-count limits of the benchmark configurations.
+ *   degree     p, 0 <= p <= 14; nmono = (p+1)(p+2)(p+3)/6 (Sec. 3 prints 84,
+ *              286, 680 for p = 6, 10, 14).
+ *   max_depth  deepest octree level, 0 <= max_depth <= 21 (root = 0).
+ *   min_pts    an octant becomes a child only if it holds at least
+ *              max(nmono, min_pts) points (Alg. 1 requires n_o >= nmono).
+ *   precision  FMT_FP64.
+ *   tol_rel    tau = tol_rel * max_i |f_i| (>= 0); an octant is refined when
+ *              its RMS residual E_RMS > tau (strict, Alg. 1).
+ *   lo, side   root cube [lo, lo+side)^3, side > 0.  Points and targets
+ *              outside it are clamped into the boundary cells.
+ *   chunk_rows rows per QR work item for large nodes (multiple of 64);
+ *              0 picks a size from the number of active points.
+ */
+typedef struct {
+  int32_t degree;
+  int32_t max_depth;
+  int32_t min_pts;
+  int32_t precision;
+  double tol_rel;
+  double lo[3];
+  double side;
+  int64_t chunk_rows;
+} fmt_params;
+
+typedef struct fmt_tree fmt_tree; /* opaque, device resident */
+
+/* Number of monomials of total degree <= p in 3-D (the rank stride of Sec. 2
+ * evaluated at p+1); 0 for p < 0. */
+int32_t fmt_nmono(int32_t degree);
+
+/*
+ * oct_build -- stage the points and build the root of the octree.
+ * Covers the steps before the first Alg. 1 fit: tau = tol_rel * max|f|,
+ * residual r := f, the exact quantisation q = floor((x-lo)*2^21/side)
+ * clamped to [0, 2^21-1] per axis, 63-bit Morton codes (bit 3j: x bit j,
+ * 3j+1: y, 3j+2: z), a stable sort of the points by the top 3*max_depth code
+ * bits (every octree node becomes a contiguous range), and the root node.
+ *   params   host, read during the call.
+ *   n        number of points, n >= 1.
+ *   x,y,z,f  device, n doubles each, caller owned (copied into the tree).
+ *   out      host; receives the new tree (NULL on failure).
+ * Returns FMT_EINVAL for bad parameters or any non-finite input value.
+ * Synchronises (reads back max|f| and the input check).
+ */
+fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const double* y,
+                     const double* z, const double* f, void* stream, fmt_tree** out);
+
+/*
+ * fit_level -- Alg. 2 for every active node at `depth`, in parallel.
+ * Per node: local frame u = (x - c) * s (Alg. 1 first step), Householder QR
+ * of the augmented matrix [Lambda(u) | r] (row chunks reduced pairwise),
+ * F = R^{-1} Q^T r with the rank rule (columns with |R_jj| <= 64 nmono eps
+ * max|R_kk| are dropped and the rest re-triangularised), the residual update
+ * r <- r - Lambda F, and each octant's sum of squared residuals and count.
+ * Legal for depth 0 right after oct_build and for depth d+1 after refine(d)
+ * reported new nodes; otherwise FMT_EINVAL.  Asynchronous.
+ */
+fmt_status fit_level(fmt_tree* tree, int32_t depth, void* stream);
+
+/*
+ * refine -- the decision loop of Alg. 1 for every node at `depth`:
+ * E_RMS = sqrt(S_o / n_o) per octant; octant o becomes a node at depth+1 iff
+ * E_RMS > tau, n_o >= max(nmono, min_pts) and depth+1 <= max_depth.  New
+ * nodes are compacted in Morton order.  Legal right after fit_level(depth).
+ *   n_new_nodes  host, receives the number of nodes created at depth+1.
+ * Synchronises (one small device-to-host read).
+ */
+fmt_status refine(fmt_tree* tree, int32_t depth, int64_t* n_new_nodes, void* stream);
+
+/*
+ * evaluate -- the tree interpolant at m targets: for each target, the sum
+ * over depth d = 0, 1, ... of Lambda(u_d) . F_d for the node at depth d that
+ * contains it (same quantisation as oct_build), stopping at the first depth
+ * with no such node or past the last fitted level.
+ *   xq,yq,zq   device, m doubles each, caller owned.
+ *   out        device, m doubles, caller owned, written.
+ *   n_outside  host or NULL; if given, receives how many targets lie outside
+ *              the closed root cube (they are extrapolated from the clamped
+ *              path) and the call synchronises.
+ * m = 0 is legal.  Asynchronous unless n_outside is given.
+ */
+fmt_status evaluate(fmt_tree* tree, int64_t m, const double* xq, const double* yq, const double* zq,
+                    double* out, int64_t* n_outside, void* stream);
+
+/* Per-level counters.  Synchronises. */
+typedef struct {
+  int32_t degree, nmono, max_depth, n_levels; /* n_levels = levels with nodes */
+  int32_t n_fitted;                           /* levels whose fit is done */
+  int32_t pad_;
+  int64_t n_points;
+  double tau, maxabs_f;
+  int64_t nodes[FMT_MAX_DEPTH + 1];
+  int64_t points[FMT_MAX_DEPTH + 1];
+  int64_t items[FMT_MAX_DEPTH + 1];      /* QR work items (row chunks) */
+  int64_t chunk_rows[FMT_MAX_DEPTH + 1];
+  int64_t near_tau[FMT_MAX_DEPTH + 1];   /* nodes flagged FMT_FLAG_NEAR_TAU */
+  int64_t rank_flagged[FMT_MAX_DEPTH + 1];
+} fmt_stats;
+fmt_status fmt_tree_stats(fmt_tree* tree, fmt_stats* out);
+
+/*
+ * Serialised tree ("FMT1" blob, little endian, every array 8-byte aligned).
+ * Layout: fmt_export_header, then for the n_nodes nodes (level by level,
+ * Morton order inside a level):
+ *   uint64 prefix[n]     Morton prefix of the node (code >> 3*(21-depth))
+ *   int64  start[n]      first point (sorted order)
+ *   int64  count[n]      number of points
+ *   int32  depth[n], flags[n], deg_used[n], masks[n] (refine_mask | near_mask<<8)
+ *   double child_E[8n]   RMS residual of each octant after the node's fit
+ *   int64  child_n[8n]   points per octant
+ *   double coef[nmono*n] F in Alg. 2 order (l outer, m, n inner)
+ * and, when has_points = 1:
+ *   uint64 code[N]       full Morton codes, sorted order
+ *   int64  perm[N]       sorted position -> input index
+ *   double resid[N]      current residual, INPUT order
+ */
+typedef struct {
+  uint32_t magic;   /* 0x31544d46, "FMT1" */
+  uint32_t version; /* 1 */
+  int32_t degree, nmono, max_depth, min_pts;
+  int32_t n_levels, n_fitted, has_points, pad_;
+  double tol_rel, tau, maxabs_f, lo[3], side;
+  int64_t n_points, n_nodes;
+  int64_t level_nodes[FMT_MAX_DEPTH + 1];
+} fmt_export_header;
+
+/* Export the tree into host_buf.  With host_buf == NULL only *len is set to
+ * the required size.  FMT_EINVAL if *len is too small.  Synchronises. */
+fmt_status fmt_tree_export(fmt_tree* tree, void* host_buf, size_t* len);
+
+/* Rebuild an evaluation-only tree from a blob (has_points may be 0; every
+ * level in the blob is taken as fitted).  fit_level/refine on it return
+ * FMT_EINVAL.  Synchronises. */
+fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_tree** out);
+
+/*
+ * Kernel-level instrumentation (no counterpart in the paper; it serves the
+ * roofline measurements).  Process-wide counters per kernel class: number of
+ * kernel launches, and -- while enabled -- the device time between CUDA events
+ * recorded on the launching stream right before and after each launch, plus
+ * the work units the launch processed (rows for tile_qr/residual, node pairs
+ * for combine, nodes for back_solve/refine, targets x fitted levels for
+ * evaluate, points for the build kernels).
+ * fmt_profile_enable(1) resets the counters and starts event timing;
+ * fmt_profile_enable(0) stops it.  fmt_profile_read synchronises the device.
+ */
+#define FMT_PROFILE_CLASSES 16
+typedef struct {
+  int64_t launches[FMT_PROFILE_CLASSES];
+  double ms[FMT_PROFILE_CLASSES];
+  double units[FMT_PROFILE_CLASSES];
+  double flops[FMT_PROFILE_CLASSES]; /* algorithmic FP64 flops (FMA = 2) */
+} fmt_profile;
+fmt_status fmt_profile_enable(int32_t on);
+fmt_status fmt_profile_read(fmt_profile* out);
+/* Name of a kernel class ("tile_qr", ...), or NULL past the last class. */
+const char* fmt_profile_class_name(int32_t k);
+
+/* Release the tree (waits for its last stream).  NULL is ignored. */
+void fmt_tree_free(fmt_tree* tree);
+
+/* Message of the last failure on `tree`, or of the calling thread's last
+ * failure when tree == NULL (e.g. a failed oct_build).  Never NULL. */
+const char* fmt_last_error(const fmt_tree* tree);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMT_H */

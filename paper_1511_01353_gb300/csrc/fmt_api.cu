@@ -1,0 +1,808 @@
+// fmt_api.cu -- the C ABI of libfmt (declared in include/fmt.h): argument
+// checks, the tree's memory, the call-order state machine, and the sequence
+// of kernels behind oct_build / fit_level / refine / evaluate.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+
+#include "fmt_internal.cuh"
+
+namespace {
+
+thread_local char g_msg[256] = "no error";
+
+fmt_status set_err(fmt_tree* t, fmt_status st, const char* fmt, ...) {
+  char buf[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (t) {
+    memcpy(t->msg, buf, sizeof(buf));
+    if (st == FMT_ECUDA || st == FMT_EINTERNAL) t->sticky = st;
+  }
+  memcpy(g_msg, buf, sizeof(buf));
+  return st;
+}
+
+std::mutex g_mu;
+cudaMemPool_t g_pool[64];
+bool g_inited[64];
+
+fmt_status device_init(int dev) {
+  if (dev < 0 || dev >= 64) return set_err(nullptr, FMT_ECUDA, "device id %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_inited[dev]) return FMT_OK;
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaError_t e = cudaMemPoolCreate(&g_pool[dev], &props);
+  if (e != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "memory pool: %s", cudaGetErrorString(e));
+  uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool
+  cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+  g_inited[dev] = true;
+  return FMT_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+enum {
+  K_CHECK = 0, K_MORTON, K_SORT, K_GATHER, K_PLAN, K_TILE_QR, K_COMBINE, K_BACKSOLVE,
+  K_RESIDUAL, K_CHILD, K_REFINE, K_EVALUATE, K_HCOEF, K_NCLASS
+};
+const char* const kClassNames[K_NCLASS] = {"check_maxabs", "morton", "radix_sort", "gather", "plan_root",
+                                           "tile_qr", "combine", "back_solve", "residual", "child_stats",
+                                           "refine", "evaluate", "make_hcoef"};
+struct ProfRec {
+  int k;
+  cudaEvent_t a, b;
+};
+std::mutex g_pmu;
+bool g_prof_on = false;
+int64_t g_launch[FMT_PROFILE_CLASSES];
+double g_units[FMT_PROFILE_CLASSES];
+double g_flops[FMT_PROFILE_CLASSES];
+ProfRec* g_recs = nullptr;
+int64_t g_nrecs = 0, g_caprecs = 0;
+cudaEvent_t* g_evpool = nullptr;
+int64_t g_nev = 0;
+
+cudaEvent_t prof_event() {
+  if (g_nev > 0) return g_evpool[--g_nev];
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Counts the launches of one kernel class and, while profiling is on, brackets
+// them with events on the launching stream.
+struct ProfScope {
+  int k;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  bool on = false;
+  ProfScope(int k_, cudaStream_t s_, int nlaunch, double units, double flops) : k(k_), s(s_) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    g_launch[k] += nlaunch;
+    g_units[k] += units;
+    g_flops[k] += flops;
+    if (g_prof_on) {
+      a = prof_event();
+      if (a && cudaEventRecord(a, s) == cudaSuccess) on = true;
+    }
+  }
+  ~ProfScope() {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_pmu);
+    cudaEvent_t b = prof_event();
+    if (!b || cudaEventRecord(b, s) != cudaSuccess) return;
+    if (g_nrecs == g_caprecs) {
+      int64_t nc = g_caprecs ? 2 * g_caprecs : 1024;
+      ProfRec* nr = (ProfRec*)realloc(g_recs, sizeof(ProfRec) * (size_t)nc);
+      if (!nr) return;
+      g_recs = nr;
+      g_caprecs = nc;
+    }
+    g_recs[g_nrecs++] = ProfRec{k, a, b};
+  }
+};
+
+double horner_flops(int p) {
+  // nmono FMAs for the coefficients, one per (l, m) pair, one per l
+  return 2.0 * ((double)fmt_nmono(p) + (p + 1) * (p + 2) / 2.0 + (p + 1));
+}
+
+template <typename T>
+fmt_status talloc(fmt_tree* t, T** p, int64_t count, cudaStream_t s) {
+  size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* ptr = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&ptr, bytes, g_pool[t->device], s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(t, FMT_ENOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  if (t->n_allocs == t->cap_allocs) {
+    int nc = t->cap_allocs ? 2 * t->cap_allocs : 64;
+    void** na = (void**)realloc(t->allocs, sizeof(void*) * (size_t)nc);
+    if (!na) {
+      cudaFreeAsync(ptr, s);
+      return set_err(t, FMT_ENOMEM, "host allocation failed");
+    }
+    t->allocs = na;
+    t->cap_allocs = nc;
+  }
+  t->allocs[t->n_allocs++] = ptr;
+  *p = (T*)ptr;
+  return FMT_OK;
+}
+
+void tfree_one(fmt_tree* t, void* ptr, cudaStream_t s) {
+  for (int i = 0; i < t->n_allocs; ++i)
+    if (t->allocs[i] == ptr) {
+      cudaFreeAsync(ptr, s);
+      t->allocs[i] = t->allocs[--t->n_allocs];
+      return;
+    }
+}
+
+#define TRY(expr)                 \
+  do {                            \
+    fmt_status st_ = (expr);      \
+    if (st_ != FMT_OK) return st_; \
+  } while (0)
+
+#define CUDA_TRY(t, expr, what)                                                         \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) return set_err(t, FMT_ECUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+  } while (0)
+
+int64_t nmin_of(const fmt_tree* t) {
+  int64_t v = t->P.min_pts > t->nmono ? t->P.min_pts : t->nmono;
+  return v < 1 ? 1 : v;
+}
+
+int64_t min_chunk(const fmt_tree* t) {
+  return t->P.chunk_rows > 0 ? t->P.chunk_rows : t->chunk_floor;
+}
+
+fmt_status alloc_level(fmt_tree* t, int d, int64_t cap_nodes, int64_t cap_items, cudaStream_t s) {
+  fmt_level& L = t->lv[d];
+  L.cap_nodes = cap_nodes;
+  L.cap_items = cap_items;
+  const int64_t nm = t->nmono;
+  TRY(talloc(t, &L.prefix, cap_nodes, s));
+  TRY(talloc(t, &L.start, cap_nodes, s));
+  TRY(talloc(t, &L.count, cap_nodes, s));
+  TRY(talloc(t, &L.flags, cap_nodes, s));
+  TRY(talloc(t, &L.deg_used, cap_nodes, s));
+  TRY(talloc(t, &L.masks, cap_nodes, s));
+  TRY(talloc(t, &L.bounds, 9 * cap_nodes, s));
+  TRY(talloc(t, &L.child_S, 8 * cap_nodes, s));
+  TRY(talloc(t, &L.child_n, 8 * cap_nodes, s));
+  TRY(talloc(t, &L.child_E, 8 * cap_nodes, s));
+  TRY(talloc(t, &L.coef, nm * cap_nodes, s));
+  TRY(talloc(t, &L.hcoef, nm * cap_nodes, s));
+  TRY(talloc(t, &L.node_item0, cap_nodes, s));
+  TRY(talloc(t, &L.node_nitems, cap_nodes, s));
+  TRY(talloc(t, &L.item_node, cap_items, s));
+  TRY(talloc(t, &L.item_start, cap_items, s));
+  TRY(talloc(t, &L.item_end, cap_items, s));
+  TRY(talloc(t, &L.item_local, cap_items, s));
+  CUDA_TRY(t, cudaMemsetAsync(L.masks, 0, sizeof(int32_t) * (size_t)cap_nodes, s), "memset");
+  CUDA_TRY(t, cudaMemsetAsync(L.child_E, 0, sizeof(double) * 8 * (size_t)cap_nodes, s), "memset");
+  return FMT_OK;
+}
+
+fmt_status check_tree(fmt_tree* t) {
+  if (!t) return set_err(nullptr, FMT_EINVAL, "tree is NULL");
+  if (t->sticky != FMT_OK) return t->sticky;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != t->device)
+    return set_err(t, FMT_EINVAL, "current device %d differs from the tree's device %d", dev, t->device);
+  return FMT_OK;
+}
+
+// read back the plan block and the device error word
+fmt_status read_plan(fmt_tree* t, cudaStream_t s) {
+  CUDA_TRY(t, cudaMemcpyAsync(t->h_plan, t->d_plan, sizeof(fmt_plan_out), cudaMemcpyDeviceToHost, s), "plan copy");
+  int herr = 0;
+  CUDA_TRY(t, cudaMemcpyAsync(&t->h_plan->err, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "err copy");
+  CUDA_TRY(t, cudaStreamSynchronize(s), "synchronise");
+  herr = (int)(t->h_plan->err & 0xffffffff);
+  t->h_plan->err = herr;
+  return FMT_OK;
+}
+
+void destroy(fmt_tree* t) {
+  if (!t) return;
+  cudaDeviceSynchronize();
+  for (int i = 0; i < t->n_allocs; ++i) cudaFreeAsync(t->allocs[i], 0);
+  cudaStreamSynchronize(0);
+  free(t->allocs);
+  if (t->h_plan) cudaFreeHost(t->h_plan);
+  delete t;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t fmt_nmono(int32_t degree) {
+  if (degree < 0) return 0;
+  return (degree + 1) * (degree + 2) * (degree + 3) / 6;
+}
+
+const char* fmt_last_error(const fmt_tree* tree) { return tree ? tree->msg : g_msg; }
+
+fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const double* y, const double* z,
+                     const double* f, void* stream, fmt_tree** out) {
+  if (!out) return set_err(nullptr, FMT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!params) return set_err(nullptr, FMT_EINVAL, "params is NULL");
+  const fmt_params& P = *params;
+  if (P.degree < 0 || P.degree > FMT_MAX_DEGREE)
+    return set_err(nullptr, FMT_EINVAL, "degree %d outside [0, %d]", P.degree, FMT_MAX_DEGREE);
+  if (P.max_depth < 0 || P.max_depth > FMT_MAX_DEPTH)
+    return set_err(nullptr, FMT_EINVAL, "max_depth %d outside [0, %d]", P.max_depth, FMT_MAX_DEPTH);
+  if (P.min_pts < 0) return set_err(nullptr, FMT_EINVAL, "min_pts %d < 0", P.min_pts);
+  if (P.precision != FMT_FP64) return set_err(nullptr, FMT_EINVAL, "only FMT_FP64 is implemented");
+  if (!(P.tol_rel >= 0.0) || !isfinite(P.tol_rel)) return set_err(nullptr, FMT_EINVAL, "tol_rel must be finite, >= 0");
+  if (!(P.side > 0.0) || !isfinite(P.side)) return set_err(nullptr, FMT_EINVAL, "side must be finite, > 0");
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(P.lo[a])) return set_err(nullptr, FMT_EINVAL, "lo must be finite");
+  if (P.chunk_rows < 0) return set_err(nullptr, FMT_EINVAL, "chunk_rows < 0");
+  if (n < 1 || n > (int64_t)0xfffffffe) return set_err(nullptr, FMT_EINVAL, "n = %lld outside [1, 2^32-2]", (long long)n);
+  if (!x || !y || !z || !f) return set_err(nullptr, FMT_EINVAL, "NULL input pointer");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
+  TRY(device_init(dev));
+
+  cudaStream_t s = (cudaStream_t)stream;
+  fmt_tree* t = new (std::nothrow) fmt_tree();
+  if (!t) return set_err(nullptr, FMT_ENOMEM, "host allocation failed");
+  t->P = P;
+  if (t->P.chunk_rows > 0) t->P.chunk_rows = (t->P.chunk_rows + 63) / 64 * 64;
+  t->device = dev;
+  t->stream = s;
+  t->n = n;
+  t->nmono = fmt_nmono(P.degree);
+  t->S = 2097152.0 / P.side;
+  {
+    int64_t fl = 16 * (int64_t)(t->nmono + 1);
+    t->chunk_floor = fl < 64 ? 64 : (fl + 63) / 64 * 64;
+  }
+  const int sort_levels = P.max_depth + 1 < FMT_QBITS ? P.max_depth + 1 : FMT_QBITS;
+  t->sort_bits = 3 * sort_levels;
+  const bool key64 = t->sort_bits > 32;
+  const int sort_shift = 3 * (FMT_QBITS - sort_levels);
+
+  fmt_status st = FMT_OK;
+  auto fail = [&](fmt_status e) {
+    destroy(t);
+    return e;
+  };
+  void *keys = nullptr, *keys_alt = nullptr, *temp = nullptr;
+  uint32_t *vals = nullptr, *vals_alt = nullptr;
+  unsigned long long* d_maxbits = nullptr;
+  const size_t ksz = key64 ? 8 : 4;
+  if ((st = talloc(t, &t->x, n, s)) || (st = talloc(t, &t->y, n, s)) || (st = talloc(t, &t->z, n, s)) ||
+      (st = talloc(t, &t->r, n, s)) || (st = talloc(t, &t->code, n, s)) ||
+      (st = talloc(t, (char**)&keys, (int64_t)ksz * n, s)) || (st = talloc(t, (char**)&keys_alt, (int64_t)ksz * n, s)) ||
+      (st = talloc(t, &vals, n, s)) || (st = talloc(t, &vals_alt, n, s)) ||
+      (st = talloc(t, (char**)&temp, (int64_t)radix_sort_temp_bytes(n, key64), s)) ||
+      (st = talloc(t, &t->d_err, 1, s)) || (st = talloc(t, &d_maxbits, 1, s)) ||
+      (st = talloc(t, &t->d_plan, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)))
+    return fail(st);
+  if (cudaMallocHost((void**)&t->h_plan, sizeof(fmt_plan_out)) != cudaSuccess) {
+    cudaGetLastError();
+    set_err(nullptr, FMT_ENOMEM, "pinned host allocation failed");
+    return fail(FMT_ENOMEM);
+  }
+  // root level: one node, ceil(n / chunk) items at most
+  const int64_t cap_items0 = n / min_chunk(t) + 2;
+  if ((st = alloc_level(t, 0, 1, cap_items0, s))) return fail(st);
+  int32_t q = P.degree;
+  if (n < t->nmono) {
+    q = -1;
+    while (fmt_nmono(q + 1) <= n) ++q;
+  }
+  t->lv[0].q = q;
+
+  cudaError_t e = cudaSuccess;
+  void* kout = nullptr;
+  uint32_t* vout = nullptr;
+  do {
+    if ((e = cudaMemsetAsync(t->d_err, 0, sizeof(int), s)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(d_maxbits, 0, sizeof(unsigned long long), s)) != cudaSuccess) break;
+    {
+      ProfScope ps(K_CHECK, s, 1, (double)n, 0.0);
+      if ((e = launch_check_maxabs(n, x, y, z, f, d_maxbits, t->d_err, s)) != cudaSuccess) break;
+    }
+    {
+      ProfScope ps(K_MORTON, s, 1, (double)n, 0.0);
+      e = launch_morton(n, x, y, z, P.lo[0], P.lo[1], P.lo[2], t->S, sort_shift, key64, keys, vals, s);
+      if (e != cudaSuccess) break;
+    }
+    {
+      ProfScope ps(K_SORT, s, 4 * ((t->sort_bits + 7) / 8), (double)n, 0.0);
+      e = launch_radix_sort(n, t->sort_bits, key64, keys, vals, keys_alt, vals_alt, temp, &kout, &vout, s);
+      if (e != cudaSuccess) break;
+    }
+    t->perm = vout;
+    {
+      ProfScope ps(K_GATHER, s, 1, (double)n, 0.0);
+      e = launch_gather(n, t->perm, x, y, z, f, P.lo[0], P.lo[1], P.lo[2], t->S, t->x, t->y, t->z, t->r, t->code, s);
+      if (e != cudaSuccess) break;
+    }
+    {
+      ProfScope ps(K_PLAN, s, 1, 1.0, 0.0);
+      e = launch_plan_root(t, t->P.chunk_rows, t->chunk_floor, t->d_plan, s);
+    }
+  } while (0);
+  if (e != cudaSuccess) {
+    set_err(nullptr, FMT_ECUDA, "oct_build launch: %s", cudaGetErrorString(e));
+    return fail(FMT_ECUDA);
+  }
+  unsigned long long hbits = 0;
+  if ((e = cudaMemcpyAsync(&hbits, d_maxbits, sizeof(hbits), cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+    set_err(nullptr, FMT_ECUDA, "copy: %s", cudaGetErrorString(e));
+    return fail(FMT_ECUDA);
+  }
+  if (read_plan(t, s) != FMT_OK) {
+    set_err(nullptr, FMT_ECUDA, "%s", t->msg);
+    return fail(FMT_ECUDA);
+  }
+  const fmt_plan_out& pl = *t->h_plan;
+  if (pl.err & FMT_ERR_NONFINITE) {
+    set_err(nullptr, FMT_EINVAL, "non-finite coordinate or value in the input");
+    return fail(FMT_EINVAL);
+  }
+  if (pl.err) {
+    set_err(nullptr, FMT_EINTERNAL, "device check failed in oct_build (0x%llx)", (unsigned long long)pl.err);
+    return fail(FMT_EINTERNAL);
+  }
+  double mx;
+  memcpy(&mx, &hbits, sizeof(mx));
+  t->maxabs = mx;
+  t->tau = P.tol_rel * mx;
+  fmt_level& L0 = t->lv[0];
+  L0.n_nodes = 1;
+  L0.n_items = pl.n_items;
+  L0.max_chunks = pl.max_chunks;
+  L0.chunk_rows = pl.chunk_rows;
+  L0.n_points = n;
+  t->n_levels = 1;
+  t->next_fit = 0;
+  t->next_refine = -1;
+  // the sort buffers are not needed any more (the permutation stays)
+  tfree_one(t, keys, s);
+  tfree_one(t, keys_alt, s);
+  tfree_one(t, temp, s);
+  tfree_one(t, vout == vals ? (void*)vals_alt : (void*)vals, s);
+  tfree_one(t, d_maxbits, s);
+  *out = t;
+  return FMT_OK;
+}
+
+fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
+  TRY(check_tree(t));
+  cudaStream_t s = (cudaStream_t)stream;
+  t->stream = s;
+  if (t->imported) return set_err(t, FMT_EINVAL, "fit_level on an imported (evaluation-only) tree");
+  if (t->done || depth != t->next_fit)
+    return set_err(t, FMT_EINVAL, "fit_level(%d) out of order (expected %d)", depth, t->done ? -1 : t->next_fit);
+  fmt_level& L = t->lv[depth];
+  const int m = fmt_nmono(L.q) + 1;
+  const size_t need = (size_t)L.n_items * (size_t)m * (size_t)m;
+  if (need > t->Rbuf_cap) {
+    if (t->Rbuf) tfree_one(t, t->Rbuf, s);
+    t->Rbuf = nullptr;
+    t->Rbuf_cap = 0;
+    TRY(talloc(t, &t->Rbuf, (int64_t)need, s));
+    t->Rbuf_cap = need;
+  }
+  const double dm = (double)m, rows = (double)L.n_points;
+  {
+    // Householder on [Lambda | r]: 2 m^2 flops per row (m = nmono + 1)
+    ProfScope ps(K_TILE_QR, s, 1, rows, 2.0 * dm * dm * rows);
+    CUDA_TRY(t, launch_tile_qr(t, depth, t->Rbuf, s), "tile QR launch");
+  }
+  int levels = 0;
+  while ((int64_t(1) << levels) < L.max_chunks) ++levels;
+  for (int tl = 0; tl < levels; ++tl) {
+    // a merge of two triangles costs (2/3) m^3 flops; n_items - n_nodes merges in all
+    const double pairs = tl == 0 ? (double)(L.n_items - L.n_nodes) : 0.0;
+    ProfScope ps(K_COMBINE, s, 1, pairs, pairs * (2.0 / 3.0) * dm * dm * dm);
+    CUDA_TRY(t, launch_combine(t, depth, tl, t->Rbuf, s), "combine launch");
+  }
+  {
+    ProfScope ps(K_BACKSOLVE, s, 1, (double)L.n_nodes, (double)L.n_nodes * (dm - 1) * (dm - 1));
+    CUDA_TRY(t, launch_backsolve(t, depth, t->Rbuf, s), "back-solve launch");
+  }
+  {
+    ProfScope ps(K_RESIDUAL, s, 1, rows, rows * horner_flops(t->P.degree));
+    CUDA_TRY(t, launch_residual(t, depth, s), "residual launch");
+  }
+  {
+    ProfScope ps(K_CHILD, s, 2, rows, 2.0 * rows);
+    CUDA_TRY(t, launch_child_stats(t, depth, s), "child statistics launch");
+  }
+  L.fitted = true;
+  t->next_fit = -1;
+  t->next_refine = depth;
+  return FMT_OK;
+}
+
+fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream) {
+  TRY(check_tree(t));
+  cudaStream_t s = (cudaStream_t)stream;
+  t->stream = s;
+  if (!n_new_nodes) return set_err(t, FMT_EINVAL, "n_new_nodes is NULL");
+  *n_new_nodes = 0;
+  if (t->imported) return set_err(t, FMT_EINVAL, "refine on an imported (evaluation-only) tree");
+  if (depth != t->next_refine)
+    return set_err(t, FMT_EINVAL, "refine(%d) out of order (expected %d)", depth, t->next_refine);
+  const fmt_level& L = t->lv[depth];
+  const bool deep_ok = depth + 1 <= t->P.max_depth && depth + 1 <= FMT_MAX_DEPTH;
+  if (deep_ok) {
+    int64_t cap = t->n / nmin_of(t) + 1;
+    if (cap > 8 * L.n_nodes) cap = 8 * L.n_nodes;
+    if (cap < 1) cap = 1;
+    fmt_level& N = t->lv[depth + 1];
+    if (N.cap_nodes < cap) TRY(alloc_level(t, depth + 1, cap, cap + t->n / min_chunk(t) + 2, s));
+  }
+  {
+    ProfScope ps(K_REFINE, s, 1, (double)L.n_nodes, 0.0);
+    CUDA_TRY(t, launch_refine(t, depth, t->P.chunk_rows, t->chunk_floor, t->d_plan, s), "refine launch");
+  }
+  TRY(read_plan(t, s));
+  const fmt_plan_out& pl = *t->h_plan;
+  if (pl.err) return set_err(t, FMT_EINTERNAL, "device check failed in refine (0x%llx)", (unsigned long long)pl.err);
+  t->next_refine = -1;
+  if (!deep_ok || pl.n_new <= 0) {
+    t->done = 1;
+    return FMT_OK;
+  }
+  fmt_level& N = t->lv[depth + 1];
+  N.n_nodes = pl.n_new;
+  N.n_items = pl.n_items;
+  N.max_chunks = pl.max_chunks;
+  N.chunk_rows = pl.chunk_rows;
+  N.n_points = pl.n_points;
+  N.q = t->P.degree;
+  N.fitted = false;
+  t->n_levels = depth + 2;
+  t->next_fit = depth + 1;
+  *n_new_nodes = pl.n_new;
+  return FMT_OK;
+}
+
+fmt_status evaluate(fmt_tree* t, int64_t m, const double* xq, const double* yq, const double* zq, double* out,
+                    int64_t* n_outside, void* stream) {
+  TRY(check_tree(t));
+  cudaStream_t s = (cudaStream_t)stream;
+  t->stream = s;
+  if (m < 0) return set_err(t, FMT_EINVAL, "m < 0");
+  if (m > 0 && (!xq || !yq || !zq || !out)) return set_err(t, FMT_EINVAL, "NULL target or output pointer");
+  if (!t->lv[0].fitted) return set_err(t, FMT_EINVAL, "evaluate before the root was fitted");
+  if (n_outside) *n_outside = 0;
+  if (m == 0) return FMT_OK;
+  if (n_outside) CUDA_TRY(t, cudaMemsetAsync(t->d_counter, 0, sizeof(unsigned long long), s), "memset");
+  {
+    ProfScope ps(K_EVALUATE, s, 1, (double)m, 0.0);
+    CUDA_TRY(t, launch_evaluate(t, m, xq, yq, zq, out, n_outside ? t->d_counter : nullptr, s), "evaluate launch");
+  }
+  if (n_outside) {
+    unsigned long long h = 0;
+    CUDA_TRY(t, cudaMemcpyAsync(&h, t->d_counter, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
+    CUDA_TRY(t, cudaStreamSynchronize(s), "synchronise");
+    *n_outside = (int64_t)h;
+  }
+  return FMT_OK;
+}
+
+fmt_status fmt_tree_stats(fmt_tree* t, fmt_stats* o) {
+  TRY(check_tree(t));
+  if (!o) return set_err(t, FMT_EINVAL, "out is NULL");
+  memset(o, 0, sizeof(*o));
+  CUDA_TRY(t, cudaDeviceSynchronize(), "synchronise");
+  o->degree = t->P.degree;
+  o->nmono = t->nmono;
+  o->max_depth = t->P.max_depth;
+  o->n_levels = t->n_levels;
+  int nf = 0;
+  while (nf < t->n_levels && t->lv[nf].fitted) ++nf;
+  o->n_fitted = nf;
+  o->n_points = t->n;
+  o->tau = t->tau;
+  o->maxabs_f = t->maxabs;
+  for (int d = 0; d < t->n_levels; ++d) {
+    const fmt_level& L = t->lv[d];
+    o->nodes[d] = L.n_nodes;
+    o->points[d] = L.n_points;
+    o->items[d] = L.n_items;
+    o->chunk_rows[d] = L.chunk_rows;
+    if (L.n_nodes > 0) {
+      int32_t* hf = (int32_t*)malloc(sizeof(int32_t) * (size_t)L.n_nodes);
+      if (!hf) return set_err(t, FMT_ENOMEM, "host allocation failed");
+      cudaError_t e = cudaMemcpy(hf, L.flags, sizeof(int32_t) * (size_t)L.n_nodes, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        free(hf);
+        return set_err(t, FMT_ECUDA, "copy: %s", cudaGetErrorString(e));
+      }
+      for (int64_t i = 0; i < L.n_nodes; ++i) {
+        o->near_tau[d] += (hf[i] & FMT_FLAG_NEAR_TAU) ? 1 : 0;
+        o->rank_flagged[d] += (hf[i] & FMT_FLAG_RANK) ? 1 : 0;
+      }
+      free(hf);
+    }
+  }
+  return FMT_OK;
+}
+
+fmt_status fmt_tree_export(fmt_tree* t, void* host_buf, size_t* len) {
+  TRY(check_tree(t));
+  if (!len) return set_err(t, FMT_EINVAL, "len is NULL");
+  int64_t K = 0;
+  for (int d = 0; d < t->n_levels; ++d) K += t->lv[d].n_nodes;
+  const int64_t nm = t->nmono;
+  const int has_pts = (t->imported || !t->x) ? 0 : 1;
+  const int64_t N = has_pts ? t->n : 0;
+  const size_t need = sizeof(fmt_export_header) + (size_t)K * (8 + 8 + 8 + 4 * 4 + 8 * 8 + 8 * 8 + 8 * (size_t)nm) +
+                      (size_t)N * (8 + 8 + 8);
+  if (!host_buf) {
+    *len = need;
+    return FMT_OK;
+  }
+  if (*len < need) {
+    *len = need;
+    return set_err(t, FMT_EINVAL, "export buffer too small (%zu bytes needed)", need);
+  }
+  *len = need;
+  CUDA_TRY(t, cudaDeviceSynchronize(), "synchronise");
+  char* b = (char*)host_buf;
+  fmt_export_header* H = (fmt_export_header*)b;
+  memset(H, 0, sizeof(*H));
+  H->magic = 0x31544d46u;
+  H->version = 1;
+  H->degree = t->P.degree;
+  H->nmono = t->nmono;
+  H->max_depth = t->P.max_depth;
+  H->min_pts = t->P.min_pts;
+  H->n_levels = t->n_levels;
+  int nf = 0;
+  while (nf < t->n_levels && t->lv[nf].fitted) ++nf;
+  H->n_fitted = nf;
+  H->has_points = has_pts;
+  H->tol_rel = t->P.tol_rel;
+  H->tau = t->tau;
+  H->maxabs_f = t->maxabs;
+  for (int a = 0; a < 3; ++a) H->lo[a] = t->P.lo[a];
+  H->side = t->P.side;
+  H->n_points = t->n;
+  H->n_nodes = K;
+  for (int d = 0; d < t->n_levels; ++d) H->level_nodes[d] = t->lv[d].n_nodes;
+  char* p = b + sizeof(fmt_export_header);
+  uint64_t* prefix = (uint64_t*)p;
+  int64_t* start = (int64_t*)(prefix + K);
+  int64_t* count = start + K;
+  int32_t* depth = (int32_t*)(count + K);
+  int32_t* flags = depth + K;
+  int32_t* deg = flags + K;
+  int32_t* masks = deg + K;
+  double* cE = (double*)(masks + K);
+  int64_t* cn = (int64_t*)(cE + 8 * K);
+  double* coef = (double*)(cn + 8 * K);
+  char* pts = (char*)(coef + nm * K);
+  int64_t off = 0;
+  for (int d = 0; d < t->n_levels; ++d) {
+    const fmt_level& L = t->lv[d];
+    const size_t k = (size_t)L.n_nodes;
+    if (!k) continue;
+    CUDA_TRY(t, cudaMemcpy(prefix + off, L.prefix, 8 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(start + off, L.start, 8 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(count + off, L.count, 8 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(flags + off, L.flags, 4 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(deg + off, L.deg_used, 4 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(masks + off, L.masks, 4 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(cE + 8 * off, L.child_E, 64 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(cn + 8 * off, L.child_n, 64 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(coef + nm * off, L.coef, 8 * nm * k, cudaMemcpyDeviceToHost), "copy");
+    for (size_t i = 0; i < k; ++i) depth[off + i] = d;
+    if (!L.fitted) {  // nodes created by refine but not fitted yet carry no coefficients
+      memset(coef + nm * off, 0, 8 * nm * k);
+      memset(cE + 8 * off, 0, 64 * k);
+      memset(cn + 8 * off, 0, 64 * k);
+      for (size_t i = 0; i < k; ++i) deg[off + i] = -1;
+    }
+    off += (int64_t)k;
+  }
+  if (has_pts) {
+    uint64_t* code = (uint64_t*)pts;
+    int64_t* perm = (int64_t*)(code + N);
+    double* resid = (double*)(perm + N);
+    CUDA_TRY(t, cudaMemcpy(code, t->code, 8 * (size_t)N, cudaMemcpyDeviceToHost), "copy");
+    uint32_t* p32 = (uint32_t*)malloc(4 * (size_t)N);
+    double* rs = (double*)malloc(8 * (size_t)N);
+    if (!p32 || !rs) {
+      free(p32);
+      free(rs);
+      return set_err(t, FMT_ENOMEM, "host allocation failed");
+    }
+    cudaError_t e1 = cudaMemcpy(p32, t->perm, 4 * (size_t)N, cudaMemcpyDeviceToHost);
+    cudaError_t e2 = cudaMemcpy(rs, t->r, 8 * (size_t)N, cudaMemcpyDeviceToHost);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      free(p32);
+      free(rs);
+      return set_err(t, FMT_ECUDA, "copy failed");
+    }
+    for (int64_t i = 0; i < N; ++i) {
+      perm[i] = p32[i];
+      resid[p32[i]] = rs[i];
+    }
+    free(p32);
+    free(rs);
+  }
+  return FMT_OK;
+}
+
+fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_tree** out) {
+  if (!out) return set_err(nullptr, FMT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!host_buf || len < sizeof(fmt_export_header)) return set_err(nullptr, FMT_EINVAL, "blob too small");
+  const fmt_export_header* H = (const fmt_export_header*)host_buf;
+  if (H->magic != 0x31544d46u || H->version != 1) return set_err(nullptr, FMT_EINVAL, "not an FMT1 blob");
+  if (H->degree < 0 || H->degree > FMT_MAX_DEGREE || H->nmono != fmt_nmono(H->degree) || H->n_levels < 1 ||
+      H->n_levels > FMT_MAX_DEPTH + 1 || H->n_nodes < 1 || !(H->side > 0.0))
+    return set_err(nullptr, FMT_EINVAL, "inconsistent blob header");
+  const int64_t K = H->n_nodes, nm = H->nmono;
+  int64_t sumk = 0;
+  for (int d = 0; d < H->n_levels; ++d) {
+    if (H->level_nodes[d] < 1) return set_err(nullptr, FMT_EINVAL, "empty level %d in blob", d);
+    sumk += H->level_nodes[d];
+  }
+  if (sumk != K) return set_err(nullptr, FMT_EINVAL, "level sizes do not add up");
+  const size_t need = sizeof(fmt_export_header) + (size_t)K * (8 + 8 + 8 + 16 + 64 + 64 + 8 * (size_t)nm);
+  if (len < need) return set_err(nullptr, FMT_EINVAL, "blob truncated");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
+  TRY(device_init(dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  fmt_tree* t = new (std::nothrow) fmt_tree();
+  if (!t) return set_err(nullptr, FMT_ENOMEM, "host allocation failed");
+  t->imported = true;
+  t->device = dev;
+  t->stream = s;
+  t->P.degree = H->degree;
+  t->P.max_depth = H->max_depth;
+  t->P.min_pts = H->min_pts;
+  t->P.precision = FMT_FP64;
+  t->P.tol_rel = H->tol_rel;
+  for (int a = 0; a < 3; ++a) t->P.lo[a] = H->lo[a];
+  t->P.side = H->side;
+  t->nmono = (int32_t)nm;
+  t->n = H->n_points;
+  t->tau = H->tau;
+  t->maxabs = H->maxabs_f;
+  t->S = 2097152.0 / H->side;
+  const char* p = (const char*)host_buf + sizeof(fmt_export_header);
+  const uint64_t* prefix = (const uint64_t*)p;
+  const int64_t* start = (const int64_t*)(prefix + K);
+  const int64_t* count = start + K;
+  const int32_t* depth = (const int32_t*)(count + K);
+  const int32_t* flags = depth + K;
+  const int32_t* deg = flags + K;
+  const int32_t* masks = deg + K;
+  const double* cE = (const double*)(masks + K);
+  const int64_t* cn = (const int64_t*)(cE + 8 * K);
+  const double* coef = (const double*)(cn + 8 * K);
+  fmt_status st = FMT_OK;
+  if ((st = talloc(t, &t->d_err, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)) || (st = talloc(t, &t->d_plan, 1, s))) {
+    destroy(t);
+    return st;
+  }
+  int64_t off = 0;
+  for (int d = 0; d < H->n_levels; ++d) {
+    const int64_t k = H->level_nodes[d];
+    for (int64_t i = 1; i < k; ++i)
+      if (prefix[off + i] <= prefix[off + i - 1] || depth[off + i] != d) {
+        destroy(t);
+        return set_err(nullptr, FMT_EINVAL, "blob level %d is not sorted by Morton prefix", d);
+      }
+    if ((st = alloc_level(t, d, k, 1, s))) {
+      destroy(t);
+      return st;
+    }
+    fmt_level& L = t->lv[d];
+    L.n_nodes = k;
+    L.q = H->degree;
+    L.fitted = true;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMemcpyAsync(L.prefix, prefix + off, 8 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.start, start + off, 8 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.count, count + off, 8 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.flags, flags + off, 4 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.deg_used, deg + off, 4 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.masks, masks + off, 4 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.child_E, cE + 8 * off, 64 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.child_n, cn + 8 * off, 64 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.coef, coef + nm * off, 8 * nm * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = [&] {
+          ProfScope ps(K_HCOEF, s, 1, (double)k, 0.0);
+          return launch_make_hcoef(k, H->degree, (int)nm, L.coef, L.hcoef, s);
+        }()) != cudaSuccess) {
+      destroy(t);
+      return set_err(nullptr, FMT_ECUDA, "import upload: %s", cudaGetErrorString(e));
+    }
+    off += k;
+  }
+  t->n_levels = H->n_levels;
+  t->done = 1;
+  t->next_fit = -1;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    destroy(t);
+    return set_err(nullptr, FMT_ECUDA, "synchronise: %s", cudaGetErrorString(e));
+  }
+  *out = t;
+  return FMT_OK;
+}
+
+void fmt_tree_free(fmt_tree* t) { destroy(t); }
+
+fmt_status fmt_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_pmu);
+  if (on) {
+    for (int64_t i = 0; i < g_nrecs; ++i) {
+      cudaEventDestroy(g_recs[i].a);
+      cudaEventDestroy(g_recs[i].b);
+    }
+    g_nrecs = 0;
+    for (int k = 0; k < FMT_PROFILE_CLASSES; ++k) {
+      g_launch[k] = 0;
+      g_units[k] = 0.0;
+      g_flops[k] = 0.0;
+    }
+  }
+  g_prof_on = on != 0;
+  return FMT_OK;
+}
+
+fmt_status fmt_profile_read(fmt_profile* out) {
+  if (!out) return set_err(nullptr, FMT_EINVAL, "out is NULL");
+  memset(out, 0, sizeof(*out));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "synchronise: %s", cudaGetErrorString(e));
+  std::lock_guard<std::mutex> lk(g_pmu);
+  for (int k = 0; k < FMT_PROFILE_CLASSES; ++k) {
+    out->launches[k] = g_launch[k];
+    out->units[k] = g_units[k];
+    out->flops[k] = g_flops[k];
+  }
+  for (int64_t i = 0; i < g_nrecs; ++i) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, g_recs[i].a, g_recs[i].b) == cudaSuccess) out->ms[g_recs[i].k] += ms;
+    else cudaGetLastError();
+  }
+  return FMT_OK;
+}
+
+const char* fmt_profile_class_name(int32_t k) { return (k >= 0 && k < K_NCLASS) ? kClassNames[k] : nullptr; }
+
+}  // extern "C"

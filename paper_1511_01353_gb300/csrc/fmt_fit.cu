@@ -1,0 +1,619 @@
+// fmt_fit.cu -- fit_level kernels (Alg. 2 for all active nodes of a level).
+//
+// Per node, the least-squares fit of the residual over the geometric-moment
+// basis is a Householder QR of the augmented matrix [Lambda(u) | r]
+// (Alg. 2: DGEQRF, then F = R^{-1} Q^T f).  Q is never formed: the reflectors
+// act on the last column, which ends up holding Q^T r.
+//
+// GB300 mapping.  The FP64 pipe is the bottleneck (about 1/60 of the FP32
+// rate, and a masked lane still costs a full slot), so the kernels keep every
+// FP64 instruction full-warp and avoid cross-lane reductions on the long
+// loops:
+//  * k_tile_qr: one CTA per work item (a chunk of <= C rows of one node).  The
+//    item's triangle R (m x m, m = nmono+1) lives in global memory (L2); row
+//    blocks of 4*RPT rows of [Lambda | r] are generated into shared memory and
+//    absorbed by a structured Householder step per column j (the reflector
+//    touches R's row j and the block's rows).  Threads form quads: a quad owns
+//    a column k > j, each lane a quarter of the block's rows, so a column's
+//    dot product needs only two shuffle-adds.
+//  * k_combine: pairwise reduction of the triangles of a node (TSQR), same
+//    absorb step with the second triangle as the row block.
+//  * k_backsolve: one warp per node, column-oriented back substitution.
+//  * k_residual: r <- r - Lambda F in Horner form (nmono FMAs per point).
+//  * k_child_bounds / k_child_sums: octant ranges by binary search on the
+//    sorted Morton codes and deterministic sums of squared residuals.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fmt_internal.cuh"
+
+namespace {
+
+constexpr int kQRThreads = 128;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_maxd(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_sumi(int v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct QRArgs {
+  const int64_t* item_node;
+  const int64_t* item_start;
+  const int64_t* item_end;
+  const int32_t* item_local;
+  const int32_t* node_nitems;
+  const uint64_t* prefix;
+  const double* x;
+  const double* y;
+  const double* z;
+  const double* r;
+  double lo0, lo1, lo2, side;
+  int depth, q, m, ldB;
+  double* R;
+};
+
+// Structured Householder absorb of a row block B (NB x m in shared memory,
+// leading dimension ldB) into the upper triangle R (m x m, row-major, global).
+// For each column j >= j_begin: u = [alpha - beta; x] with alpha = R_jj,
+// x = B[:, j], beta = -sign(alpha) sqrt(alpha^2 + |x|^2) (sign(0) = +), and
+// H = I - gamma u u^T, gamma = 1 / (beta (beta - alpha)).  A column with
+// |x| = 0 is left alone (no reflection).
+template <int RPT>
+__device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, int j_begin, int m,
+                                             double* __restrict__ R, double* sc) {
+  constexpr int NB = 4 * RPT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, rg = tid & 3;
+  for (int j = j_begin; j < m; ++j) {
+    if (warp == 0) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = lane; i < NB; i += 32) {
+        double xv = B[i * ldB + j];
+        s = fma(xv, xv, s);
+      }
+      s = warp_sum(s);
+      if (lane == 0) {
+        double* rjj = R + (size_t)j * m + j;
+        double alpha = *rjj;
+        if (s == 0.0) {
+          sc[0] = 0.0;
+          sc[1] = 0.0;
+        } else {
+          double h = sqrt(fma(alpha, alpha, s));
+          double beta = alpha >= 0.0 ? -h : h;
+          sc[0] = 1.0 / (h * (h + fabs(alpha)));
+          sc[1] = alpha - beta;
+          *rjj = beta;
+        }
+      }
+    }
+    __syncthreads();
+    const double gamma = sc[0];
+    if (gamma != 0.0) {
+      const double amb = sc[1];
+      double xr[RPT];
+#pragma unroll
+      for (int t = 0; t < RPT; ++t) xr[t] = B[(rg + 4 * t) * ldB + j];
+      // warp w covers columns j+1+8w .. j+8+8w of each 32-column round
+      for (int k0 = j + 1 + 8 * warp; k0 < m; k0 += 32) {
+        const int k = k0 + (lane >> 2);
+        const bool act = k < m;
+        const int kk = act ? k : j;
+        double acc = 0.0;
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) acc = fma(xr[t], B[(rg + 4 * t) * ldB + kk], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (act) {
+          double* rjk = R + (size_t)j * m + k;
+          const double rv = *rjk;
+          const double d = gamma * fma(amb, rv, acc);
+#pragma unroll
+          for (int t = 0; t < RPT; ++t) {
+            double* bp = B + (rg + 4 * t) * ldB + k;
+            *bp = fma(-d, xr[t], *bp);
+          }
+          if (rg == 0) *rjk = fma(-d, amb, rv);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void node_frame(const QRArgs& a, uint64_t pf, double& c0, double& s0, double& c1,
+                                           double& s1, double& c2, double& s2) {
+  fmt_frame(a.lo0, a.side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(a.lo1, a.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(a.lo2, a.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
+  extern __shared__ double Bs[];
+  __shared__ double sc[2];
+  constexpr int NB = 4 * RPT;
+  const int item = blockIdx.x;
+  const int64_t node = a.item_node[item];
+  const int64_t rs = a.item_start[item], re = a.item_end[item];
+  const int m = a.m;
+  double* R = a.R + (size_t)item * m * m;
+  for (int e = threadIdx.x; e < m * m; e += kQRThreads) {
+    int j = e / m, k = e - j * m;
+    if (k >= j) R[e] = 0.0;
+  }
+  double c0, s0, c1, s1, c2, s2;
+  node_frame(a, a.prefix[node], c0, s0, c1, s1, c2, s2);
+  const int q = a.q;
+  __syncthreads();
+  for (int64_t b0 = rs; b0 < re; b0 += NB) {
+    const int nb = (int)((re - b0) < NB ? (re - b0) : NB);
+    if (threadIdx.x < NB) {
+      double* row = Bs + threadIdx.x * a.ldB;
+      if ((int)threadIdx.x < nb) {
+        const int64_t i = b0 + threadIdx.x;
+        const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+        double pu[FMT_MAX_DEGREE + 1], pv[FMT_MAX_DEGREE + 1], pw[FMT_MAX_DEGREE + 1];
+        double tu = 1.0, tv = 1.0, tw = 1.0;
+        for (int l = 0; l <= q; ++l) {
+          const double f = c_invfact[l];
+          pu[l] = tu * f;
+          pv[l] = tv * f;
+          pw[l] = tw * f;
+          tu *= u;
+          tv *= v;
+          tw *= w;
+        }
+        int k = 0;
+        for (int l = 0; l <= q; ++l)
+          for (int mm = 0; mm <= q - l; ++mm) {
+            const double plm = pu[l] * pv[mm];
+            for (int n = 0; n <= q - l - mm; ++n) row[k++] = plm * pw[n];
+          }
+        row[k] = a.r[i];
+      } else {
+        for (int k = 0; k < m; ++k) row[k] = 0.0;
+      }
+    }
+    __syncthreads();
+    absorb_block<RPT>(Bs, a.ldB, 0, m, R, sc);
+  }
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(kQRThreads) k_combine(QRArgs a, int level) {
+  extern __shared__ double Bs[];
+  __shared__ double sc[2];
+  constexpr int NB = 4 * RPT;
+  const int item = blockIdx.x;
+  const int s = a.item_local[item];
+  const int cnt = a.node_nitems[a.item_node[item]];
+  const int step = 1 << level;
+  if ((s & (2 * step - 1)) != 0 || s + step >= cnt) return;
+  const int m = a.m;
+  double* Ra = a.R + (size_t)item * m * m;
+  const double* Rb = a.R + (size_t)(item + step) * m * m;
+  for (int r0 = 0; r0 < m; r0 += NB) {
+    for (int e = threadIdx.x; e < NB * m; e += kQRThreads) {
+      const int i = e / m, k = e - i * m;
+      const int row = r0 + i;
+      Bs[i * a.ldB + k] = (row < m && k >= row) ? Rb[(size_t)row * m + k] : 0.0;
+    }
+    __syncthreads();
+    absorb_block<RPT>(Bs, a.ldB, r0, m, Ra, sc);
+  }
+}
+
+// ---------------------------------------------------------------- back solve
+struct BSArgs {
+  int64_t n_nodes;
+  const int64_t* node_item0;
+  double* R;
+  int m, q, p, nmono_p;
+  double* coef;
+  double* hcoef;
+  int32_t* flags;
+  int32_t* deg_used;
+};
+
+__device__ __forceinline__ int tri2(int k) { return (k + 1) * (k + 2) / 2; }
+
+// (l, m, n) of the idx-th monomial of degree <= p in Alg. 2 order
+__device__ void mono_lmn(int p, int idx, int& l, int& m, int& n) {
+  l = 0;
+  while (idx >= tri2(p - l)) {
+    idx -= tri2(p - l);
+    ++l;
+  }
+  m = 0;
+  while (idx >= p - l - m + 1) {
+    idx -= p - l - m + 1;
+    ++m;
+  }
+  n = idx;
+}
+__device__ int mono_index(int p, int l, int m, int n) {
+  int idx = 0;
+  for (int a = 0; a < l; ++a) idx += tri2(p - a);
+  for (int b = 0; b < m; ++b) idx += p - l - b + 1;
+  return idx + n;
+}
+
+__global__ void __launch_bounds__(128) k_backsolve(BSArgs a) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t node = (int64_t)blockIdx.x * 4 + wib;
+  if (node >= a.n_nodes) return;
+  const int m = a.m, L = m - 1;
+  double* y = sm + (size_t)wib * (3 * L + (L + 1) / 2 + 1);
+  double* inv = y + L;
+  double* F = inv + L;
+  int* keep = (int*)(F + L);
+  double* R = a.R + (size_t)a.node_item0[node] * m * m;
+
+  double rmax = 0.0;
+  for (int j = lane; j < L; j += 32) rmax = fmax(rmax, fabs(R[(size_t)j * m + j]));
+  rmax = warp_maxd(rmax);
+  const double thresh = 64.0 * (double)L * DBL_EPSILON * rmax;
+  int ndrop = 0;
+  for (int j = lane; j < L; j += 32) ndrop += fabs(R[(size_t)j * m + j]) <= thresh ? 1 : 0;
+  ndrop = warp_sumi(ndrop);
+  int Lk = L;
+  if (ndrop > 0) {
+    // Rank rule: drop dependent columns, re-triangularise [R_kept | Q^T r].
+    int c = 0;
+    for (int j0 = 0; j0 < L; j0 += 32) {
+      const int j = j0 + lane;
+      const bool kp = j < L && fabs(R[(size_t)j * m + j]) > thresh;
+      const unsigned b = __ballot_sync(0xffffffffu, kp);
+      if (kp) keep[c + __popc(b & ((1u << lane) - 1u))] = j;
+      c += __popc(b);
+    }
+    Lk = c;
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) {
+      for (int cc = 0; cc < Lk; ++cc) {
+        const int src = keep[cc];
+        R[(size_t)i * m + cc] = (i <= src) ? R[(size_t)i * m + src] : 0.0;
+      }
+      R[(size_t)i * m + Lk] = R[(size_t)i * m + L];
+    }
+    __syncwarp();
+    for (int cc = 0; cc <= Lk && cc < m; ++cc) {
+      const int rmx = (cc < Lk) ? keep[cc] : L;
+      const double alpha = R[(size_t)cc * m + cc];
+      double s = 0.0;
+      for (int i = cc + 1 + lane; i <= rmx; i += 32) {
+        const double t = R[(size_t)i * m + cc];
+        s = fma(t, t, s);
+      }
+      s = warp_sum(s);
+      if (s == 0.0) continue;
+      const double h = sqrt(fma(alpha, alpha, s));
+      const double beta = alpha >= 0.0 ? -h : h;
+      const double amb = alpha - beta;
+      const double gamma = 1.0 / (h * (h + fabs(alpha)));
+      for (int k = cc + 1 + lane; k <= Lk; k += 32) {
+        double w = amb * R[(size_t)cc * m + k];
+        for (int i = cc + 1; i <= rmx; ++i) w = fma(R[(size_t)i * m + cc], R[(size_t)i * m + k], w);
+        const double d = gamma * w;
+        R[(size_t)cc * m + k] = fma(-d, amb, R[(size_t)cc * m + k]);
+        for (int i = cc + 1; i <= rmx; ++i) R[(size_t)i * m + k] = fma(-d, R[(size_t)i * m + cc], R[(size_t)i * m + k]);
+      }
+      __syncwarp();
+      if (lane == 0) R[(size_t)cc * m + cc] = beta;
+      for (int i = cc + 1 + lane; i <= rmx; i += 32) R[(size_t)i * m + cc] = 0.0;
+      __syncwarp();
+    }
+  }
+  for (int j = lane; j < Lk; j += 32) {
+    const double dg = R[(size_t)j * m + j];
+    y[j] = R[(size_t)j * m + Lk];
+    inv[j] = fabs(dg) <= thresh ? 0.0 : 1.0 / dg;
+  }
+  __syncwarp();
+  for (int j = Lk - 1; j >= 0; --j) {
+    const double Fj = y[j] * inv[j];
+    if (lane == 0) F[j] = Fj;
+    for (int k = lane; k < j; k += 32) y[k] = fma(-R[(size_t)k * m + j], Fj, y[k]);
+    __syncwarp();
+  }
+  // write F (and F / (l! m! n!)) in the degree-p layout
+  double* cf = a.coef + (size_t)node * a.nmono_p;
+  double* hc = a.hcoef + (size_t)node * a.nmono_p;
+  if (a.q != a.p || ndrop > 0) {
+    for (int k = lane; k < a.nmono_p; k += 32) {
+      cf[k] = 0.0;
+      hc[k] = 0.0;
+    }
+    __syncwarp();
+  }
+  for (int c = lane; c < Lk; c += 32) {
+    const int jq = ndrop > 0 ? keep[c] : c;
+    int l, mm, n;
+    mono_lmn(a.q, jq, l, mm, n);
+    const int jp = (a.q == a.p) ? jq : mono_index(a.p, l, mm, n);
+    cf[jp] = F[c];
+    hc[jp] = F[c] * (c_invfact[l] * c_invfact[mm] * c_invfact[n]);
+  }
+  if (lane == 0) {
+    a.deg_used[node] = a.q;
+    if (ndrop > 0) a.flags[node] |= FMT_FLAG_RANK;
+  }
+}
+
+// ---------------------------------------------------------------- residual
+struct ResArgs {
+  const int64_t* item_node;
+  const int64_t* item_start;
+  const int64_t* item_end;
+  const uint64_t* prefix;
+  const double* x;
+  const double* y;
+  const double* z;
+  double* r;
+  const double* hcoef;
+  double lo0, lo1, lo2, side;
+  int depth, p, nmono;
+};
+
+__global__ void __launch_bounds__(256) k_residual(ResArgs a) {
+  const int item = blockIdx.x;
+  const int64_t node = a.item_node[item];
+  const int64_t rs = a.item_start[item], re = a.item_end[item];
+  const uint64_t pf = a.prefix[node];
+  double c0, s0, c1, s1, c2, s2;
+  fmt_frame(a.lo0, a.side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(a.lo1, a.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(a.lo2, a.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  const double* G = a.hcoef + (size_t)node * a.nmono;
+  for (int64_t i = rs + threadIdx.x; i < re; i += blockDim.x) {
+    const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+    a.r[i] -= fmt_horner(G, a.p, a.nmono, u, v, w);
+  }
+}
+
+// ---------------------------------------------------------------- child stats
+struct ChildArgs {
+  int64_t n_nodes;
+  const uint64_t* prefix;
+  const int64_t* start;
+  const int64_t* count;
+  const uint64_t* code;
+  const double* r;
+  int64_t* bounds;
+  double* child_S;
+  int64_t* child_n;
+  int shift;  // 3*(21-depth-1); < 0 when the node has no child level
+};
+
+__global__ void __launch_bounds__(256) k_child_bounds(ChildArgs a) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= a.n_nodes * 9) return;
+  const int64_t node = gid / 9;
+  const int o = (int)(gid - node * 9);
+  const int64_t s = a.start[node], e = s + a.count[node];
+  int64_t b;
+  if (a.shift < 0) {
+    b = s;  // no octants below the deepest code level
+  } else if (o == 0) {
+    b = s;
+  } else if (o == 8) {
+    b = e;
+  } else {
+    const uint64_t target = a.prefix[node] * 8ull + (uint64_t)o;
+    int64_t lo = s, hi = e;
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if ((a.code[mid] >> a.shift) < target) lo = mid + 1;
+      else hi = mid;
+    }
+    b = lo;
+  }
+  a.bounds[node * 9 + o] = b;
+}
+
+__global__ void __launch_bounds__(128) k_child_sums(ChildArgs a) {
+  __shared__ double red[4];
+  const int64_t node = blockIdx.x >> 3;
+  const int o = blockIdx.x & 7;
+  const int64_t b0 = a.bounds[node * 9 + o], b1 = a.bounds[node * 9 + o + 1];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t i = b0 + threadIdx.x;
+  for (; i + 3 * 128 < b1; i += 4 * 128) {
+    const double t0 = a.r[i], t1 = a.r[i + 128], t2 = a.r[i + 256], t3 = a.r[i + 384];
+    s0 = fma(t0, t0, s0);
+    s1 = fma(t1, t1, s1);
+    s2 = fma(t2, t2, s2);
+    s3 = fma(t3, t3, s3);
+  }
+  for (; i < b1; i += 128) {
+    const double t = a.r[i];
+    s0 = fma(t, t, s0);
+  }
+  double s = (s0 + s1) + (s2 + s3);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.child_S[node * 8 + o] = (red[0] + red[1]) + (red[2] + red[3]);
+    a.child_n[node * 8 + o] = b1 - b0;
+  }
+}
+
+template <int RPT>
+cudaError_t set_smem_attr(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_tile_qr<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_combine<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int ld_for(int m) {
+  int ld = m;
+  while ((ld & 31) != 8) ++ld;
+  return ld;
+}
+
+QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
+  const fmt_level& L = t->lv[depth];
+  QRArgs a;
+  a.item_node = L.item_node;
+  a.item_start = L.item_start;
+  a.item_end = L.item_end;
+  a.item_local = L.item_local;
+  a.node_nitems = L.node_nitems;
+  a.prefix = L.prefix;
+  a.x = t->x;
+  a.y = t->y;
+  a.z = t->z;
+  a.r = t->r;
+  a.lo0 = t->P.lo[0];
+  a.lo1 = t->P.lo[1];
+  a.lo2 = t->P.lo[2];
+  a.side = t->P.side;
+  a.depth = depth;
+  a.q = L.q;
+  a.m = fmt_nmono(L.q) + 1;
+  a.ldB = ld_for(a.m);
+  a.R = R;
+  return a;
+}
+
+}  // namespace
+
+int qr_rows_per_block(int m) {
+  const size_t ld = (size_t)ld_for(m);
+  if (64 * ld * sizeof(double) <= 110 * 1024) return 64;
+  if (32 * ld * sizeof(double) <= 200 * 1024) return 32;
+  return 16;
+}
+
+size_t qr_smem_bytes(int m, int rows) { return (size_t)rows * ld_for(m) * sizeof(double); }
+
+cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t s) {
+  QRArgs a = make_qr_args(t, depth, R);
+  const int64_t n_items = t->lv[depth].n_items;
+  if (n_items <= 0) return cudaSuccess;
+  const int rows = qr_rows_per_block(a.m);
+  const size_t smem = qr_smem_bytes(a.m, rows);
+  cudaError_t e;
+  switch (rows) {
+    case 64:
+      if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;
+      k_tile_qr<16><<<(unsigned)n_items, kQRThreads, smem, s>>>(a);
+      break;
+    case 32:
+      if ((e = set_smem_attr<8>(smem)) != cudaSuccess) return e;
+      k_tile_qr<8><<<(unsigned)n_items, kQRThreads, smem, s>>>(a);
+      break;
+    default:
+      if ((e = set_smem_attr<4>(smem)) != cudaSuccess) return e;
+      k_tile_qr<4><<<(unsigned)n_items, kQRThreads, smem, s>>>(a);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s) {
+  QRArgs a = make_qr_args(t, depth, R);
+  const int64_t n_items = t->lv[depth].n_items;
+  if (n_items <= 1) return cudaSuccess;
+  const int rows = qr_rows_per_block(a.m);
+  const size_t smem = qr_smem_bytes(a.m, rows);
+  cudaError_t e;
+  switch (rows) {
+    case 64:
+      if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;
+      k_combine<16><<<(unsigned)n_items, kQRThreads, smem, s>>>(a, tree_level);
+      break;
+    case 32:
+      if ((e = set_smem_attr<8>(smem)) != cudaSuccess) return e;
+      k_combine<8><<<(unsigned)n_items, kQRThreads, smem, s>>>(a, tree_level);
+      break;
+    default:
+      if ((e = set_smem_attr<4>(smem)) != cudaSuccess) return e;
+      k_combine<4><<<(unsigned)n_items, kQRThreads, smem, s>>>(a, tree_level);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  BSArgs a;
+  a.n_nodes = L.n_nodes;
+  a.node_item0 = L.node_item0;
+  a.R = R;
+  a.m = fmt_nmono(L.q) + 1;
+  a.q = L.q;
+  a.p = t->P.degree;
+  a.nmono_p = t->nmono;
+  a.coef = L.coef;
+  a.hcoef = L.hcoef;
+  a.flags = L.flags;
+  a.deg_used = L.deg_used;
+  const int Lq = a.m - 1;
+  const size_t per_warp = (size_t)(3 * Lq + (Lq + 1) / 2 + 1) * sizeof(double);
+  const size_t smem = 4 * per_warp;
+  cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((L.n_nodes + 3) / 4);
+  if (grid == 0) return cudaSuccess;
+  k_backsolve<<<grid, 128, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_items <= 0) return cudaSuccess;
+  ResArgs a;
+  a.item_node = L.item_node;
+  a.item_start = L.item_start;
+  a.item_end = L.item_end;
+  a.prefix = L.prefix;
+  a.x = t->x;
+  a.y = t->y;
+  a.z = t->z;
+  a.r = t->r;
+  a.hcoef = L.hcoef;
+  a.lo0 = t->P.lo[0];
+  a.lo1 = t->P.lo[1];
+  a.lo2 = t->P.lo[2];
+  a.side = t->P.side;
+  a.depth = depth;
+  a.p = t->P.degree;
+  a.nmono = t->nmono;
+  k_residual<<<(unsigned)L.n_items, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_child_stats(const fmt_tree* t, int depth, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_nodes <= 0) return cudaSuccess;
+  ChildArgs a;
+  a.n_nodes = L.n_nodes;
+  a.prefix = L.prefix;
+  a.start = L.start;
+  a.count = L.count;
+  a.code = t->code;
+  a.r = t->r;
+  a.bounds = L.bounds;
+  a.child_S = L.child_S;
+  a.child_n = L.child_n;
+  const int child_depth = depth + 1;
+  a.shift = (child_depth <= FMT_QBITS && child_depth <= t->sort_bits / 3) ? 3 * (FMT_QBITS - child_depth) : -1;
+  const int64_t nb = L.n_nodes * 9;
+  k_child_bounds<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(a);
+  k_child_sums<<<(unsigned)(L.n_nodes * 8), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}

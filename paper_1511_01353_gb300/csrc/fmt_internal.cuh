@@ -1,0 +1,194 @@
+// fmt_internal.cuh -- internal types and device helpers of libfmt (not part of
+// the C ABI).  Every kernel of the FP64 path is declared here through a host
+// launcher; fmt_api.cu sequences them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmt.h"
+
+#define FMT_QBITS 21
+#define FMT_QMAX 0x1fffffu
+
+// device error word bits
+#define FMT_ERR_NONFINITE 1
+#define FMT_ERR_INDEX 2
+#define FMT_ERR_CAPACITY 4
+
+// 1/l! for l = 0..14, each a correctly rounded binary64 quotient (l! is exact)
+static __constant__ double c_invfact[FMT_MAX_DEGREE + 1] = {
+    1.0,          1.0,          1.0 / 2.0,          1.0 / 6.0,           1.0 / 24.0,
+    1.0 / 120.0,  1.0 / 720.0,  1.0 / 5040.0,       1.0 / 40320.0,       1.0 / 362880.0,
+    1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0, 1.0 / 87178291200.0};
+
+// ---------------------------------------------------------------------------
+// Morton codes: 21 bits per axis; bit 3j <- x bit j, 3j+1 <- y, 3j+2 <- z.
+__host__ __device__ inline uint64_t fmt_spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+__host__ __device__ inline uint32_t fmt_compact3(uint64_t v) {
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+  v = (v ^ (v >> 32)) & 0x1fffffull;
+  return (uint32_t)v;
+}
+
+// Exact quantisation: floor((x - lo) * S), S = 2^21/side, clamped; the
+// subtraction and the product are separately rounded (no contraction).
+__device__ __forceinline__ uint32_t fmt_quant(double x, double lo, double S) {
+  double t = __dmul_rn(__dsub_rn(x, lo), S);
+  if (!(t >= 0.0)) return 0u;
+  if (t >= 2097152.0) return FMT_QMAX;
+  return (uint32_t)floor(t);
+}
+
+// Node frame of Alg. 1: h = side 2^-(d+1), c = lo + (2i+1) h, s = 1/h.
+__device__ __forceinline__ void fmt_frame(double lo, double side, int depth, uint32_t i, double& c,
+                                          double& s) {
+  double h = ldexp(side, -(depth + 1));
+  c = __dadd_rn(lo, __dmul_rn((double)(2u * i + 1u), h));
+  s = __ddiv_rn(1.0, h);
+}
+
+// u = (x - c) * s without contraction
+__device__ __forceinline__ double fmt_local(double x, double c, double s) {
+  return __dmul_rn(__dsub_rn(x, c), s);
+}
+
+// Polynomial of a node in Horner form.  G holds F_lmn / (l! m! n!) in Alg. 2
+// order (l outer, m, n inner, all ascending); reading it backwards visits
+// (l, m, n) in descending lexicographic order, which is exactly the nested
+// Horner order  sum_l u^l sum_m v^m sum_n w^n G_lmn.
+__device__ __forceinline__ double fmt_horner(const double* __restrict__ G, int p, int nmono, double u,
+                                             double v, double w) {
+  int idx = nmono - 1;
+  double P = 0.0;
+  for (int l = p; l >= 0; --l) {
+    double t = 0.0;
+    for (int m = p - l; m >= 0; --m) {
+      double s = 0.0;
+      for (int n = p - l - m; n >= 0; --n) s = fma(s, w, __ldg(G + idx--));
+      t = fma(t, v, s);
+    }
+    P = fma(P, u, t);
+  }
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// One octree level as stored on the device (structure of arrays).
+struct fmt_level {
+  // host-side copies of the sizes
+  int64_t n_nodes = 0, cap_nodes = 0;
+  int64_t n_items = 0, cap_items = 0, max_chunks = 0, chunk_rows = 0, n_points = 0;
+  int32_t q = 0;  // degree used by this level's fit (root may be clamped)
+  bool fitted = false;
+  // nodes
+  uint64_t* prefix = nullptr;  // Morton prefix (code >> 3(21-d))
+  int64_t* start = nullptr;
+  int64_t* count = nullptr;
+  int32_t* flags = nullptr;
+  int32_t* deg_used = nullptr;
+  int32_t* masks = nullptr;    // refine_mask | near_mask << 8
+  int64_t* bounds = nullptr;   // 9 per node: octant ranges in sorted order
+  double* child_S = nullptr;   // 8 per node: sum of squared residuals
+  int64_t* child_n = nullptr;  // 8 per node
+  double* child_E = nullptr;   // 8 per node: RMS
+  double* coef = nullptr;      // nmono per node: F (Alg. 2 order)
+  double* hcoef = nullptr;     // nmono per node: F / (l! m! n!) for Horner
+  int64_t* node_item0 = nullptr;
+  int32_t* node_nitems = nullptr;
+  // QR work items: (node, [start, end)) row chunks, node-major
+  int64_t* item_node = nullptr;
+  int64_t* item_start = nullptr;
+  int64_t* item_end = nullptr;
+  int32_t* item_local = nullptr;  // chunk index inside its node
+};
+
+// Small result block that refine reads back in one copy.
+struct fmt_plan_out {
+  int64_t n_new, n_items, max_chunks, chunk_rows, n_points, n_near, err;
+  int64_t pad_;
+};
+
+struct fmt_tree {
+  fmt_params P{};
+  int32_t nmono = 0;
+  int64_t n = 0;
+  bool imported = false;
+  int device = 0;
+  cudaStream_t stream = nullptr;  // last stream used (for the final free)
+  double tau = 0.0, maxabs = 0.0;
+  double S = 0.0;  // 2^21 / side
+  int sort_bits = 0;
+  // sorted point data
+  double *x = nullptr, *y = nullptr, *z = nullptr, *r = nullptr;
+  uint64_t* code = nullptr;
+  uint32_t* perm = nullptr;
+  // levels
+  fmt_level lv[FMT_MAX_DEPTH + 1];
+  int32_t n_levels = 0;     // levels that hold nodes
+  int32_t next_fit = 0;     // depth fit_level expects next
+  int32_t next_refine = -1; // depth refine expects next
+  int32_t done = 0;         // no further levels
+  // scratch
+  double* Rbuf = nullptr;
+  size_t Rbuf_cap = 0;  // doubles
+  int* d_err = nullptr;
+  fmt_plan_out* d_plan = nullptr;
+  fmt_plan_out* h_plan = nullptr;  // pinned
+  unsigned long long* d_counter = nullptr;
+  int64_t chunk_floor = 64;
+  fmt_status sticky = FMT_OK;
+  char msg[256] = {0};
+  // every device allocation, freed together
+  void** allocs = nullptr;
+  int n_allocs = 0, cap_allocs = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (return cudaGetLastError() of the launch).
+
+// build
+cudaError_t launch_check_maxabs(int64_t n, const double* x, const double* y, const double* z,
+                                const double* f, unsigned long long* d_maxbits, int* d_err,
+                                cudaStream_t s);
+cudaError_t launch_morton(int64_t n, const double* x, const double* y, const double* z, double lo0,
+                          double lo1, double lo2, double S, int sort_shift, bool key64, void* keys,
+                          uint32_t* vals, cudaStream_t s);
+size_t radix_sort_temp_bytes(int64_t n, bool key64);
+cudaError_t launch_radix_sort(int64_t n, int bits, bool key64, void* keys, uint32_t* vals, void* keys_alt,
+                              uint32_t* vals_alt, void* temp, void** keys_out, uint32_t** vals_out,
+                              cudaStream_t s);
+cudaError_t launch_gather(int64_t n, const uint32_t* perm, const double* x, const double* y,
+                          const double* z, const double* f, double lo0, double lo1, double lo2, double S,
+                          double* xs, double* ys, double* zs, double* rs, uint64_t* code, cudaStream_t s);
+cudaError_t launch_plan_root(const fmt_tree* t, int64_t chunk_rows_fixed, int64_t chunk_floor,
+                             fmt_plan_out* d_plan, cudaStream_t s);
+
+// fit
+int qr_rows_per_block(int m);
+size_t qr_smem_bytes(int m, int rows);
+cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t s);
+cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s);
+cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream_t s);
+cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s);
+cudaError_t launch_child_stats(const fmt_tree* t, int depth, cudaStream_t s);
+
+// refine / evaluate
+cudaError_t launch_refine(const fmt_tree* t, int depth, int64_t chunk_rows_fixed, int64_t chunk_floor,
+                          fmt_plan_out* d_plan, cudaStream_t s);
+cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const double* xq, const double* yq,
+                            const double* zq, double* out, unsigned long long* d_outside,
+                            cudaStream_t s);
+cudaError_t launch_make_hcoef(int64_t n, int p, int nmono, const double* coef, double* hcoef, cudaStream_t s);

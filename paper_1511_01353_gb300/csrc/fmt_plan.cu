@@ -1,0 +1,391 @@
+// fmt_plan.cu -- refinement decisions and level planning (Alg. 1's loop over
+// octants), the work-item plan of a level, and the evaluation kernel.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fmt_internal.cuh"
+
+namespace {
+
+constexpr int kPlanThreads = 1024;
+
+template <typename T>
+__device__ T block_exscan(T v, T* total) {
+  __shared__ T ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  T base = 0, tot = 0;
+  for (int w = 0; w < nw; ++w) {
+    T c = ws[w];
+    if (w < warp) base += c;
+    tot += c;
+  }
+  __syncthreads();
+  *total = tot;
+  return base + inc - v;
+}
+
+template <typename T>
+__device__ T block_max(T v) {
+  __shared__ T ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    T t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  T r = ws[0];
+  for (int w = 1; w < nw; ++w) r = ws[w] > r ? ws[w] : r;
+  __syncthreads();
+  return r;
+}
+
+struct PlanArgs {
+  int64_t n_nodes;      // nodes of the planned level
+  const int64_t* start;
+  const int64_t* count;
+  int64_t total_points;
+  int64_t chunk_fixed, chunk_floor, nsm;
+  int64_t cap_items;
+  int64_t* node_item0;
+  int32_t* node_nitems;
+  int64_t* item_node;
+  int64_t* item_start;
+  int64_t* item_end;
+  int32_t* item_local;
+};
+
+// Split every node into ceil(count / C) nearly equal row chunks.
+__device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
+  int64_t C = a.chunk_fixed;
+  if (C <= 0) {
+    int64_t per = (a.total_points + a.nsm - 1) / a.nsm;
+    per = (per + 63) / 64 * 64;
+    C = per > a.chunk_floor ? per : a.chunk_floor;
+  }
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  int64_t maxc = 0;
+  for (int64_t b = 0; b < a.n_nodes; b += blockDim.x) {
+    const int64_t node = b + threadIdx.x;
+    int64_t nch = 0, cnt = 0, st = 0;
+    if (node < a.n_nodes) {
+      cnt = a.count[node];
+      st = a.start[node];
+      nch = (cnt + C - 1) / C;
+      if (nch < 1) nch = 1;
+    }
+    int64_t tot;
+    const int64_t ex = block_exscan<int64_t>(nch, &tot);
+    if (node < a.n_nodes) {
+      const int64_t i0 = carry + ex;
+      a.node_item0[node] = i0;
+      a.node_nitems[node] = (int32_t)nch;
+      if (i0 + nch > a.cap_items) {
+        atomicOr(err, FMT_ERR_CAPACITY);
+      } else {
+        for (int64_t c = 0; c < nch; ++c) {
+          a.item_node[i0 + c] = node;
+          a.item_start[i0 + c] = st + (cnt * c) / nch;
+          a.item_end[i0 + c] = st + (cnt * (c + 1)) / nch;
+          a.item_local[i0 + c] = (int32_t)c;
+        }
+      }
+      maxc = nch > maxc ? nch : maxc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  maxc = block_max<int64_t>(maxc);
+  if (threadIdx.x == 0) {
+    out->n_items = carry;
+    out->max_chunks = maxc;
+    out->chunk_rows = C;
+    out->n_points = a.total_points;
+  }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan_root(PlanArgs a, uint64_t* prefix, int64_t* start,
+                                                            int64_t* count, int32_t* flags, int32_t root_flags,
+                                                            fmt_plan_out* out, int* err) {
+  if (threadIdx.x == 0) {
+    prefix[0] = 0;
+    start[0] = 0;
+    count[0] = a.total_points;
+    flags[0] = root_flags;
+    out->n_new = 1;
+    out->n_near = 0;
+  }
+  __syncthreads();
+  plan_items(a, out, err);
+}
+
+struct RefineArgs {
+  int64_t n_nodes;
+  double tau;
+  int64_t nmin;
+  int deep_ok;
+  const uint64_t* prefix;
+  const int64_t* bounds;
+  const double* child_S;
+  const int64_t* child_n;
+  double* child_E;
+  int32_t* masks;
+  int64_t cap_nodes;
+  uint64_t* nprefix;
+  int64_t* nstart;
+  int64_t* ncount;
+  int32_t* nflags;
+};
+
+// Alg. 1 loop body for all nodes: E_RMS = sqrt(S_o / n_o); refine iff
+// E_RMS > tau (strict), n_o >= max(nmono, min_pts) and depth+1 <= max_depth.
+// New nodes are written in Morton order (node-major, octant-minor).
+__global__ void __launch_bounds__(kPlanThreads) k_refine(RefineArgs r, PlanArgs a, fmt_plan_out* out, int* err) {
+  __shared__ int64_t carry, pts, nnear;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    pts = 0;
+    nnear = 0;
+  }
+  __syncthreads();
+  for (int64_t b = 0; b < r.n_nodes; b += blockDim.x) {
+    const int64_t node = b + threadIdx.x;
+    int64_t cnt = 0, npt = 0, nn = 0;
+    unsigned rmask = 0, nmask = 0;
+    if (node < r.n_nodes) {
+      for (int o = 0; o < 8; ++o) {
+        const int64_t no = r.child_n[node * 8 + o];
+        const double E = no > 0 ? sqrt(r.child_S[node * 8 + o] / (double)no) : 0.0;
+        r.child_E[node * 8 + o] = E;
+        const bool ok = r.deep_ok && no > 0 && no >= r.nmin;
+        if (ok && fabs(E - r.tau) <= 1e-9 * r.tau) nmask |= 1u << o;
+        if (ok && E > r.tau) {
+          rmask |= 1u << o;
+          ++cnt;
+          npt += no;
+        }
+      }
+      r.masks[node] = (int32_t)(rmask | (nmask << 8));
+      nn = __popc(rmask & nmask);
+    }
+    int64_t tot;
+    const int64_t ex = block_exscan<int64_t>(cnt, &tot);
+    int64_t ptot, ntot;
+    (void)block_exscan<int64_t>(npt, &ptot);
+    (void)block_exscan<int64_t>(nn, &ntot);
+    if (node < r.n_nodes && cnt > 0) {
+      int64_t idx = carry + ex;
+      const uint64_t pf = r.prefix[node];
+      for (int o = 0; o < 8; ++o) {
+        if (!(rmask & (1u << o))) continue;
+        if (idx >= r.cap_nodes) {
+          atomicOr(err, FMT_ERR_CAPACITY);
+          break;
+        }
+        r.nprefix[idx] = pf * 8ull + (uint64_t)o;
+        r.nstart[idx] = r.bounds[node * 9 + o];
+        r.ncount[idx] = r.child_n[node * 8 + o];
+        r.nflags[idx] = (nmask & (1u << o)) ? FMT_FLAG_NEAR_TAU : 0;
+        ++idx;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      carry += tot;
+      pts += ptot;
+      nnear += ntot;
+    }
+    __syncthreads();
+  }
+  const int64_t n_new = carry;
+  if (threadIdx.x == 0) {
+    out->n_new = n_new;
+    out->n_near = nnear;
+  }
+  if (n_new > r.cap_nodes || n_new == 0) {
+    if (threadIdx.x == 0) {
+      out->n_items = 0;
+      out->max_chunks = 0;
+      out->chunk_rows = 0;
+      out->n_points = pts;
+    }
+    return;
+  }
+  a.n_nodes = n_new;
+  a.total_points = pts;
+  plan_items(a, out, err);
+}
+
+// ---------------------------------------------------------------- evaluate
+struct EvalArgs {
+  int n_levels, p, nmono;
+  double lo0, lo1, lo2, side, S, hi0, hi1, hi2;
+  const uint64_t* prefix[FMT_MAX_DEPTH + 1];
+  const double* hcoef[FMT_MAX_DEPTH + 1];
+  int64_t n_nodes[FMT_MAX_DEPTH + 1];
+};
+
+__global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const double* __restrict__ xq,
+                                                  const double* __restrict__ yq, const double* __restrict__ zq,
+                                                  double* __restrict__ out, unsigned long long* outside) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t last = ((m + stride - 1) / stride) * stride;  // uniform trip count for the ballot
+  for (int64_t t = first; t < last; t += stride) {
+    const bool valid = t < m;
+    bool outs = false;
+    if (valid) {
+      const double x = xq[t], y = yq[t], z = zq[t];
+      outs = !(x >= a.lo0 && x <= a.hi0 && y >= a.lo1 && y <= a.hi1 && z >= a.lo2 && z <= a.hi2);
+      const uint64_t code = fmt_spread3(fmt_quant(x, a.lo0, a.S)) | (fmt_spread3(fmt_quant(y, a.lo1, a.S)) << 1) |
+                            (fmt_spread3(fmt_quant(z, a.lo2, a.S)) << 2);
+      double acc = 0.0;
+      for (int d = 0; d < a.n_levels; ++d) {
+        const uint64_t P = d == 0 ? 0ull : (code >> (3 * (FMT_QBITS - d)));
+        const uint64_t* pr = a.prefix[d];
+        int64_t lo = 0, hi = a.n_nodes[d];
+        while (lo < hi) {
+          const int64_t mid = lo + ((hi - lo) >> 1);
+          if (pr[mid] < P) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo >= a.n_nodes[d] || pr[lo] != P) break;
+        double c0, s0, c1, s1, c2, s2;
+        fmt_frame(a.lo0, a.side, d, fmt_compact3(P), c0, s0);
+        fmt_frame(a.lo1, a.side, d, fmt_compact3(P >> 1), c1, s1);
+        fmt_frame(a.lo2, a.side, d, fmt_compact3(P >> 2), c2, s2);
+        acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.nmono, a.p, a.nmono, fmt_local(x, c0, s0),
+                          fmt_local(y, c1, s1), fmt_local(z, c2, s2));
+      }
+      out[t] = acc;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, outs);
+    if (outside != nullptr && (threadIdx.x & 31) == 0 && b) atomicAdd(outside, (unsigned long long)__popc(b));
+  }
+}
+
+__global__ void k_make_hcoef(int64_t n, int p, int nmono, const double* __restrict__ coef,
+                             double* __restrict__ hcoef) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nmono) return;
+  int k = (int)(i % nmono);
+  int l = 0;
+  while (k >= (p - l + 1) * (p - l + 2) / 2) {
+    k -= (p - l + 1) * (p - l + 2) / 2;
+    ++l;
+  }
+  int mm = 0;
+  while (k >= p - l - mm + 1) {
+    k -= p - l - mm + 1;
+    ++mm;
+  }
+  hcoef[i] = coef[i] * (c_invfact[l] * c_invfact[mm] * c_invfact[k]);
+}
+
+PlanArgs plan_args_for(const fmt_tree* t, const fmt_level& L, int64_t chunk_fixed, int64_t chunk_floor) {
+  PlanArgs a;
+  a.n_nodes = L.n_nodes;
+  a.start = L.start;
+  a.count = L.count;
+  a.total_points = 0;
+  a.chunk_fixed = chunk_fixed;
+  a.chunk_floor = chunk_floor;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  a.nsm = nsm > 0 ? nsm : 152;
+  a.cap_items = L.cap_items;
+  a.node_item0 = L.node_item0;
+  a.node_nitems = L.node_nitems;
+  a.item_node = L.item_node;
+  a.item_start = L.item_start;
+  a.item_end = L.item_end;
+  a.item_local = L.item_local;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t launch_plan_root(const fmt_tree* t, int64_t chunk_rows_fixed, int64_t chunk_floor,
+                             fmt_plan_out* d_plan, cudaStream_t s) {
+  const fmt_level& L = t->lv[0];
+  PlanArgs a = plan_args_for(t, L, chunk_rows_fixed, chunk_floor);
+  a.n_nodes = 1;
+  a.total_points = t->n;
+  const int32_t rf = (L.q != t->P.degree) ? FMT_FLAG_DEG_CLAMPED : 0;
+  k_plan_root<<<1, kPlanThreads, 0, s>>>(a, L.prefix, L.start, L.count, L.flags, rf, d_plan, t->d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const fmt_tree* t, int depth, int64_t chunk_rows_fixed, int64_t chunk_floor,
+                          fmt_plan_out* d_plan, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  const fmt_level& N = t->lv[depth + 1 <= FMT_MAX_DEPTH ? depth + 1 : depth];
+  RefineArgs r;
+  r.n_nodes = L.n_nodes;
+  r.tau = t->tau;
+  int64_t nmin = t->P.min_pts > t->nmono ? t->P.min_pts : t->nmono;
+  r.nmin = nmin < 1 ? 1 : nmin;
+  r.deep_ok = (depth + 1 <= t->P.max_depth && depth + 1 <= FMT_MAX_DEPTH) ? 1 : 0;
+  r.prefix = L.prefix;
+  r.bounds = L.bounds;
+  r.child_S = L.child_S;
+  r.child_n = L.child_n;
+  r.child_E = L.child_E;
+  r.masks = L.masks;
+  r.cap_nodes = r.deep_ok ? N.cap_nodes : 0;
+  r.nprefix = N.prefix;
+  r.nstart = N.start;
+  r.ncount = N.count;
+  r.nflags = N.flags;
+  PlanArgs a = plan_args_for(t, N, chunk_rows_fixed, chunk_floor);
+  k_refine<<<1, kPlanThreads, 0, s>>>(r, a, d_plan, t->d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const double* xq, const double* yq,
+                            const double* zq, double* out, unsigned long long* d_outside,
+                            cudaStream_t s) {
+  EvalArgs a;
+  int nf = 0;
+  while (nf < t->n_levels && t->lv[nf].fitted) ++nf;
+  a.n_levels = nf;
+  a.p = t->P.degree;
+  a.nmono = t->nmono;
+  a.lo0 = t->P.lo[0];
+  a.lo1 = t->P.lo[1];
+  a.lo2 = t->P.lo[2];
+  a.side = t->P.side;
+  a.S = t->S;
+  a.hi0 = t->P.lo[0] + t->P.side;
+  a.hi1 = t->P.lo[1] + t->P.side;
+  a.hi2 = t->P.lo[2] + t->P.side;
+  for (int d = 0; d <= FMT_MAX_DEPTH; ++d) {
+    a.prefix[d] = d < nf ? t->lv[d].prefix : nullptr;
+    a.hcoef[d] = d < nf ? t->lv[d].hcoef : nullptr;
+    a.n_nodes[d] = d < nf ? t->lv[d].n_nodes : 0;
+  }
+  int64_t blocks = (m + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  k_evaluate<<<(unsigned)blocks, 256, 0, s>>>(a, m, xq, yq, zq, out, d_outside);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_make_hcoef(int64_t n, int p, int nmono, const double* coef, double* hcoef, cudaStream_t s) {
+  const int64_t tot = n * nmono;
+  if (tot <= 0) return cudaSuccess;
+  k_make_hcoef<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, p, nmono, coef, hcoef);
+  return cudaGetLastError();
+}

@@ -1,0 +1,357 @@
+"""Thin ctypes binding of libfmt (include/fmt.h).
+
+The functions keep the C names (oct_build, fit_level, refine, evaluate,
+fmt_tree_stats, fmt_tree_export, fmt_tree_import, fmt_tree_free,
+fmt_last_error, fmt_nmono) and only marshal arguments: device buffers are
+torch CUDA tensors (float64, contiguous), streams are torch.cuda.Stream or
+None (torch's current stream).  All arithmetic runs in the library's CUDA
+kernels; there is no CPU fallback: loading fails loudly when libfmt.so is
+missing or cannot be built.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmt.so")
+
+FMT_OK, FMT_EINVAL, FMT_ENOMEM, FMT_ECUDA, FMT_ETIMEOUT, FMT_EINTERNAL = range(6)
+FMT_FP64, FMT_MIXED = 0, 1
+FMT_FLAG_NEAR_TAU, FMT_FLAG_RANK, FMT_FLAG_DEG_CLAMPED = 1, 2, 4
+MAX_DEPTH = 21
+_STATUS = {0: "FMT_OK", 1: "FMT_EINVAL", 2: "FMT_ENOMEM", 3: "FMT_ECUDA", 4: "FMT_ETIMEOUT", 5: "FMT_EINTERNAL"}
+
+
+class FmtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class fmt_params(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("min_pts", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("tol_rel", ctypes.c_double), ("lo", ctypes.c_double * 3),
+                ("side", ctypes.c_double), ("chunk_rows", ctypes.c_int64)]
+
+
+_NL = MAX_DEPTH + 1
+
+
+class fmt_stats(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("nmono", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("n_fitted", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("n_points", ctypes.c_int64), ("tau", ctypes.c_double), ("maxabs_f", ctypes.c_double),
+                ("nodes", ctypes.c_int64 * _NL), ("points", ctypes.c_int64 * _NL),
+                ("items", ctypes.c_int64 * _NL), ("chunk_rows", ctypes.c_int64 * _NL),
+                ("near_tau", ctypes.c_int64 * _NL), ("rank_flagged", ctypes.c_int64 * _NL)]
+
+
+class fmt_export_header(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32), ("degree", ctypes.c_int32),
+                ("nmono", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("min_pts", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("n_fitted", ctypes.c_int32), ("has_points", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("tol_rel", ctypes.c_double), ("tau", ctypes.c_double),
+                ("maxabs_f", ctypes.c_double), ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
+                ("n_points", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("level_nodes", ctypes.c_int64 * _NL)]
+
+
+EXPORTED = ["fmt_nmono", "oct_build", "fit_level", "refine", "evaluate", "fmt_tree_stats", "fmt_tree_export",
+            "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
+            "fmt_profile_class_name"]
+PROFILE_CLASSES = 16
+
+
+class fmt_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * PROFILE_CLASSES), ("ms", ctypes.c_double * PROFILE_CLASSES),
+                ("units", ctypes.c_double * PROFILE_CLASSES), ("flops", ctypes.c_double * PROFILE_CLASSES)]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build: bool = True):
+    """Load libfmt.so (building it with nvcc first when it is stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build:
+            from . import build as _b
+            _b.build()
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libfmt.so not found at %s; run paper_1511_01353_gb300/build.py" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.fmt_nmono.argtypes = [i32]
+        L.fmt_nmono.restype = i32
+        L.oct_build.argtypes = [ctypes.POINTER(fmt_params), i64, P, P, P, P, P, ctypes.POINTER(P)]
+        L.oct_build.restype = ctypes.c_int
+        L.fit_level.argtypes = [P, i32, P]
+        L.fit_level.restype = ctypes.c_int
+        L.refine.argtypes = [P, i32, ctypes.POINTER(i64), P]
+        L.refine.restype = ctypes.c_int
+        L.evaluate.argtypes = [P, i64, P, P, P, P, ctypes.POINTER(i64), P]
+        L.evaluate.restype = ctypes.c_int
+        L.fmt_tree_stats.argtypes = [P, ctypes.POINTER(fmt_stats)]
+        L.fmt_tree_stats.restype = ctypes.c_int
+        L.fmt_tree_export.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
+        L.fmt_tree_export.restype = ctypes.c_int
+        L.fmt_tree_import.argtypes = [P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+        L.fmt_tree_import.restype = ctypes.c_int
+        L.fmt_tree_free.argtypes = [P]
+        L.fmt_tree_free.restype = None
+        L.fmt_last_error.argtypes = [P]
+        L.fmt_last_error.restype = ctypes.c_char_p
+        L.fmt_profile_enable.argtypes = [i32]
+        L.fmt_profile_enable.restype = ctypes.c_int
+        L.fmt_profile_read.argtypes = [ctypes.POINTER(fmt_profile)]
+        L.fmt_profile_read.restype = ctypes.c_int
+        L.fmt_profile_class_name.argtypes = [i32]
+        L.fmt_profile_class_name.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(st, tree=None):
+    if st != FMT_OK:
+        L = load(build=False)
+        msg = L.fmt_last_error(tree.handle if tree is not None else None)
+        raise FmtError(st, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float64 tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Tree:
+    """Owning handle of an fmt_tree (freed on close() or garbage collection)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            load(build=False).fmt_tree_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(degree, max_depth, min_pts, tol_rel, lo=(0.0, 0.0, 0.0), side=1.0, chunk_rows=0,
+                precision=FMT_FP64):
+    p = fmt_params()
+    p.degree, p.max_depth, p.min_pts, p.precision = degree, max_depth, min_pts, precision
+    p.tol_rel = tol_rel
+    for a in range(3):
+        p.lo[a] = lo[a]
+    p.side = side
+    p.chunk_rows = chunk_rows
+    return p
+
+
+def fmt_nmono(degree: int) -> int:
+    return int(load().fmt_nmono(degree))
+
+
+def oct_build(params: fmt_params, x, y, z, f, stream=None) -> Tree:
+    L = load()
+    h = ctypes.c_void_p()
+    n = int(x.numel())
+    st = L.oct_build(ctypes.byref(params), n, _dptr(x, "x"), _dptr(y, "y"), _dptr(z, "z"), _dptr(f, "f"),
+                     _stream_handle(stream), ctypes.byref(h))
+    _check(st)
+    return Tree(h)
+
+
+def fit_level(tree: Tree, depth: int, stream=None):
+    _check(load().fit_level(tree.handle, depth, _stream_handle(stream)), tree)
+
+
+def refine(tree: Tree, depth: int, stream=None) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().refine(tree.handle, depth, ctypes.byref(n), _stream_handle(stream)), tree)
+    return int(n.value)
+
+
+def evaluate(tree: Tree, xq, yq, zq, out, count_outside=False, stream=None):
+    m = int(xq.numel())
+    nout = ctypes.c_int64(0)
+    st = load().evaluate(tree.handle, m, _dptr(xq, "xq"), _dptr(yq, "yq"), _dptr(zq, "zq"), _dptr(out, "out"),
+                         ctypes.byref(nout) if count_outside else None, _stream_handle(stream))
+    _check(st, tree)
+    return int(nout.value) if count_outside else None
+
+
+def fmt_tree_stats(tree: Tree) -> fmt_stats:
+    s = fmt_stats()
+    _check(load().fmt_tree_stats(tree.handle, ctypes.byref(s)), tree)
+    return s
+
+
+def fmt_tree_export(tree: Tree) -> bytes:
+    L = load()
+    n = ctypes.c_size_t(0)
+    _check(L.fmt_tree_export(tree.handle, None, ctypes.byref(n)), tree)
+    buf = (ctypes.c_char * n.value)()
+    _check(L.fmt_tree_export(tree.handle, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(n)), tree)
+    return bytes(buf)
+
+
+def fmt_tree_import(blob: bytes, stream=None) -> Tree:
+    L = load()
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(L.fmt_tree_import(ctypes.cast(buf, ctypes.c_void_p), len(blob), _stream_handle(stream), ctypes.byref(h)))
+    return Tree(h)
+
+
+def fmt_profile_enable(on: bool):
+    _check(load().fmt_profile_enable(1 if on else 0))
+
+
+def fmt_profile_read() -> dict:
+    """{class name: dict(launches, ms, units, flops)} for the classes the library defines."""
+    L = load()
+    p = fmt_profile()
+    _check(L.fmt_profile_read(ctypes.byref(p)))
+    out = {}
+    for k in range(PROFILE_CLASSES):
+        name = L.fmt_profile_class_name(k)
+        if not name:
+            break
+        out[name.decode()] = dict(launches=int(p.launches[k]), ms=float(p.ms[k]), units=float(p.units[k]),
+                                  flops=float(p.flops[k]))
+    return out
+
+
+def fmt_profile_class_name(k: int):
+    n = load().fmt_profile_class_name(k)
+    return n.decode() if n else None
+
+
+def fmt_tree_free(tree: Tree):
+    tree.close()
+
+
+def fmt_last_error(tree: Tree | None = None) -> str:
+    msg = load().fmt_last_error(tree.handle if tree is not None else None)
+    return msg.decode() if msg else ""
+
+
+# ----------------------------------------------------------------- helpers
+def fit(params: fmt_params, x, y, z, f, stream=None) -> Tree:
+    """The driver loop of the four calls: oct_build; for depth 0, 1, ...:
+    fit_level, then refine until it creates no node."""
+    tree = oct_build(params, x, y, z, f, stream)
+    d = 0
+    while True:
+        fit_level(tree, d, stream)
+        if refine(tree, d, stream) == 0:
+            break
+        d += 1
+    return tree
+
+
+@dataclasses.dataclass
+class ExportedTree:
+    header: dict
+    prefix: np.ndarray
+    start: np.ndarray
+    count: np.ndarray
+    depth: np.ndarray
+    flags: np.ndarray
+    deg_used: np.ndarray
+    refine_mask: np.ndarray
+    near_mask: np.ndarray
+    child_E: np.ndarray
+    child_n: np.ndarray
+    coef: np.ndarray
+    code: np.ndarray | None
+    perm: np.ndarray | None
+    resid: np.ndarray | None
+
+
+def parse_export(blob: bytes) -> ExportedTree:
+    H = fmt_export_header.from_buffer_copy(blob[:ctypes.sizeof(fmt_export_header)])
+    hdr = {name: getattr(H, name) for name, _ in fmt_export_header._fields_}
+    hdr["lo"] = tuple(H.lo)
+    hdr["level_nodes"] = list(H.level_nodes)
+    K, nm, N = H.n_nodes, H.nmono, H.n_points if H.has_points else 0
+    off = ctypes.sizeof(fmt_export_header)
+
+    def take(dtype, count):
+        nonlocal off
+        a = np.frombuffer(blob, dtype=dtype, count=count, offset=off).copy()
+        off += a.nbytes
+        return a
+
+    prefix = take(np.uint64, K)
+    start = take(np.int64, K)
+    count = take(np.int64, K)
+    depth = take(np.int32, K)
+    flags = take(np.int32, K)
+    deg = take(np.int32, K)
+    masks = take(np.int32, K)
+    cE = take(np.float64, 8 * K).reshape(K, 8)
+    cn = take(np.int64, 8 * K).reshape(K, 8)
+    coef = take(np.float64, nm * K).reshape(K, nm)
+    code = perm = resid = None
+    if H.has_points:
+        code = take(np.uint64, N)
+        perm = take(np.int64, N)
+        resid = take(np.float64, N)
+    return ExportedTree(hdr, prefix, start, count, depth, flags, deg, masks & 0xFF, (masks >> 8) & 0xFF, cE, cn,
+                        coef, code, perm, resid)
+
+
+def build_export(header: dict, prefix, depth, flags, deg_used, child_E, child_n, coef, start=None, count=None,
+                 refine_mask=None, near_mask=None) -> bytes:
+    """Serialise node arrays into an FMT1 blob (no per-point arrays), e.g. to
+    upload a tree built elsewhere for evaluation through fmt_tree_import."""
+    K = int(prefix.shape[0])
+    H = fmt_export_header()
+    H.magic, H.version = 0x31544D46, 1
+    H.degree, H.nmono = header["degree"], header["nmono"]
+    H.max_depth, H.min_pts = header["max_depth"], header["min_pts"]
+    lv = np.bincount(np.asarray(depth, dtype=np.int64), minlength=1)
+    H.n_levels = H.n_fitted = int(lv.shape[0])
+    H.has_points = 0
+    H.tol_rel, H.tau, H.maxabs_f = header["tol_rel"], header["tau"], header["maxabs_f"]
+    for a in range(3):
+        H.lo[a] = header["lo"][a]
+    H.side = header["side"]
+    H.n_points = header.get("n_points", 0)
+    H.n_nodes = K
+    for d in range(lv.shape[0]):
+        H.level_nodes[d] = int(lv[d])
+    z64 = np.zeros(K, np.int64)
+    rm = np.zeros(K, np.int32) if refine_mask is None else np.asarray(refine_mask, np.int32)
+    nm_ = np.zeros(K, np.int32) if near_mask is None else np.asarray(near_mask, np.int32)
+    parts = [bytes(H), np.asarray(prefix, np.uint64).tobytes(),
+             (z64 if start is None else np.asarray(start, np.int64)).tobytes(),
+             (z64 if count is None else np.asarray(count, np.int64)).tobytes(),
+             np.asarray(depth, np.int32).tobytes(), np.asarray(flags, np.int32).tobytes(),
+             np.asarray(deg_used, np.int32).tobytes(), (rm | (nm_ << 8)).astype(np.int32).tobytes(),
+             np.asarray(child_E, np.float64).tobytes(), np.asarray(child_n, np.int64).tobytes(),
+             np.asarray(coef, np.float64).tobytes()]
+    return b"".join(parts)

@@ -1,0 +1,115 @@
+"""Host-side checks of the C ABI: libfmt.so builds for sm_103a, exports every
+function include/fmt.h declares, the ctypes structures match the C layout,
+and argument validation answers before any device work."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_1511_01353_gb300 import fmt as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fmt.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([A-Za-z_][A-Za-z0-9_]*)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_four_calls():
+    names = declared_functions()
+    for n in ("oct_build", "fit_level", "refine", "evaluate"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = F.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(F.EXPORTED) == declared_functions()
+
+
+def _c_layout():
+    code = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "fmt.h"
+int main(void){
+  printf("%zu %zu %zu %zu %zu\n", sizeof(fmt_params), offsetof(fmt_params, tol_rel), offsetof(fmt_params, side),
+         offsetof(fmt_params, chunk_rows), sizeof(fmt_stats));
+  printf("%zu %zu %zu\n", sizeof(fmt_export_header), offsetof(fmt_export_header, tol_rel),
+         offsetof(fmt_export_header, level_nodes));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write(code)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return [int(v) for v in out]
+
+
+def test_struct_layouts_match_c():
+    v = _c_layout()
+    assert v[0] == ctypes.sizeof(F.fmt_params)
+    assert v[1] == F.fmt_params.tol_rel.offset
+    assert v[2] == F.fmt_params.side.offset
+    assert v[3] == F.fmt_params.chunk_rows.offset
+    assert v[4] == ctypes.sizeof(F.fmt_stats)
+    assert v[5] == ctypes.sizeof(F.fmt_export_header)
+    assert v[6] == F.fmt_export_header.tol_rel.offset
+    assert v[7] == F.fmt_export_header.level_nodes.offset
+
+
+def test_nmono_matches_paper_values():
+    assert [F.fmt_nmono(p) for p in (6, 10, 14)] == [84, 286, 680]
+    assert F.fmt_nmono(-1) == 0
+
+
+@pytest.mark.parametrize("field,value", [("degree", 15), ("degree", -1), ("max_depth", 22), ("min_pts", -3),
+                                         ("tol_rel", -1.0), ("tol_rel", float("nan")), ("side", 0.0),
+                                         ("precision", 1), ("chunk_rows", -64)])
+def test_oct_build_rejects_bad_params_before_device_work(field, value):
+    lib = F.load()
+    p = F.make_params(4, 3, 64, 1e-4)
+    setattr(p, field, value)
+    h = ctypes.c_void_p()
+    st = lib.oct_build(ctypes.byref(p), 10, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8),
+                       ctypes.c_void_p(8), None, ctypes.byref(h))
+    assert st == F.FMT_EINVAL
+    assert not h.value
+    assert F.fmt_last_error()
+
+
+def test_oct_build_rejects_empty_and_null():
+    lib = F.load()
+    p = F.make_params(4, 3, 64, 1e-4)
+    h = ctypes.c_void_p()
+    assert lib.oct_build(ctypes.byref(p), 0, None, None, None, None, None, ctypes.byref(h)) == F.FMT_EINVAL
+    assert lib.oct_build(ctypes.byref(p), 5, None, None, None, None, None, ctypes.byref(h)) == F.FMT_EINVAL
+    assert lib.oct_build(None, 5, None, None, None, None, None, ctypes.byref(h)) == F.FMT_EINVAL
+
+
+def test_calls_on_null_tree_fail_cleanly():
+    lib = F.load()
+    n = ctypes.c_int64(7)
+    assert lib.fit_level(None, 0, None) == F.FMT_EINVAL
+    assert lib.refine(None, 0, ctypes.byref(n), None) == F.FMT_EINVAL
+    assert lib.evaluate(None, 0, None, None, None, None, None, None) == F.FMT_EINVAL
+    lib.fmt_tree_free(None)
+
+
+def test_import_rejects_garbage():
+    lib = F.load()
+    h = ctypes.c_void_p()
+    junk = ctypes.create_string_buffer(b"\0" * 512, 512)
+    assert lib.fmt_tree_import(junk, 512, None, ctypes.byref(h)) == F.FMT_EINVAL
+    assert lib.fmt_tree_import(junk, 8, None, ctypes.byref(h)) == F.FMT_EINVAL
