@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the FP64 free-mesh transform hot path on GB300.
+
+One step = one pass of the whole hot path on one synthetic problem whose
+inputs are already resident in HBM: oct_build (tau, Morton codes, sort,
+gather, root), fit_level / refine for every level, then evaluate at the
+targets.  Workload (default): 1e6 points (half uniform, half in 8 Gaussian
+clusters), 3-D Franke values, p = 8 (165 monomials), max depth 7, min 128
+points, tol 1e-8 relative, 1e7 uniform targets.
+
+Printed (rank 0, one JSON line): value = fitted points/s (the fit phase of
+the step, CUDA events on the launching stream), evals_per_s, the roofline of
+the dominant kernel (tile_qr, FP64 pipe), an end-to-end figure through host
+buffers, the CPU oracle baseline, clocks sampled during the timed region, and
+the kernel launch count.
+
+Multi-GPU: the path does not shard one problem; every rank fits its own
+replica (weak scaling) and value sums the ranks' points over the slowest
+rank's time.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fitted pts/s & evals/s, mixed vs FP64 at stated err; p50/p99 req latency"
+UNIT = "fitted pts/s"
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["fmt", "reference"], default="fmt")
+    ap.add_argument("--workload", choices=["scale", "small"], default="scale")
+    ap.add_argument("--points", type=int, default=0, help="override the number of points")
+    ap.add_argument("--targets", type=int, default=0, help="override the number of targets")
+    ap.add_argument("--cpu-points", type=int, default=200_000, help="oracle sample size for cpu_baseline")
+    ap.add_argument("--ref-points", type=int, default=40_000, help="oracle sample per step for --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="run warmup+steps, print nothing (for ncu)")
+    return ap.parse_args()
+
+
+def make_workload(args, rank=0):
+    from paper_1511_01353_gb300 import workloads as W
+    if args.workload == "small":
+        kw = {}
+        if args.points:
+            kw["n"] = args.points
+        if args.targets:
+            kw["n_targets"] = args.targets
+        return W.small(**kw)
+    kw = dict(seed=W.SEED_BASE + 1 + 1000 * rank)
+    if args.points:
+        kw["n"] = args.points
+    if args.targets:
+        kw["n_targets"] = args.targets
+    return W.scale(**kw)
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _morton_np(x, y, z, lo, side):
+    import numpy as np
+
+    def spread(v):
+        out = np.zeros_like(v)
+        for b in range(21):
+            out |= ((v >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b)
+        return out
+
+    qs = []
+    for a, arr in enumerate((x, y, z)):
+        t = (np.asarray(arr, np.float64) - lo[a]) * (2097152.0 / side)
+        q = np.where(t >= 2097152.0, 2097151.0, np.floor(np.where(t >= 0, t, 0.0)))
+        qs.append(spread(q.astype(np.uint64)))
+    return qs[0] | (qs[1] << np.uint64(1)) | (qs[2] << np.uint64(2))
+
+
+def levels_visited(ex, xq, yq, zq, lo, side):
+    """Sum over targets of the number of tree levels evaluate visits (for flops)."""
+    import numpy as np
+    code = _morton_np(xq, yq, zq, lo, side)
+    alive = np.ones(code.shape[0], bool)
+    total = 0
+    off = 0
+    for d, k in enumerate(ex.header["level_nodes"]):
+        if k == 0:
+            break
+        pref = np.sort(ex.prefix[off:off + k])
+        off += k
+        P = code >> np.uint64(3 * (21 - d)) if d > 0 else np.zeros_like(code)
+        idx = np.searchsorted(pref, P)
+        hit = (idx < k) & (pref[np.minimum(idx, k - 1)] == P)
+        alive &= hit
+        total += int(alive.sum())
+    return total
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as it stands, timed on this host's cores."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1511_01353_gb300 import workloads as W
+    n = args.ref_points
+    w = W.scale(n=n, n_targets=n) if args.workload == "scale" else W.small()
+    n = w.n
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        T = O.fit(w.x, w.y, w.z, w.f, w.degree, w.max_depth, w.min_pts, w.tol_rel, mode="omp")
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            times.append(t1 - t0)
+        del T
+    t = sum(times) / len(times)
+    value = n / t
+    cores = O.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample_points": n, "degree": w.degree, "max_depth": w.max_depth,
+                       "min_pts": w.min_pts, "tol_rel": w.tol_rel},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d points of the same recipe per step, fit only, OpenMP over sibling "
+                                       "subtrees" % n},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args):
+    from oracle import oracle as O
+    from paper_1511_01353_gb300 import workloads as W
+    n = args.cpu_points
+    w = W.scale(n=n, n_targets=n) if args.workload == "scale" else W.small()
+    t0 = time.perf_counter()
+    T = O.fit(w.x, w.y, w.z, w.f, w.degree, w.max_depth, w.min_pts, w.tol_rel, mode="omp")
+    t1 = time.perf_counter()
+    T.evaluate(w.xq, w.yq, w.zq)
+    t2 = time.perf_counter()
+    return {"value": w.n / (t1 - t0), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%s: %d points (same recipe, p, depth, min_pts, tol), fit %.2f s; OpenMP over sibling "
+                      "subtrees, each node serial" % (w.name, w.n, t1 - t0),
+            "evals_per_s": w.m / (t2 - t1)}
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return 0
+
+    import numpy as np
+    import torch
+    from paper_1511_01353_gb300 import fmt as F
+    from paper_1511_01353_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    F.load()
+    stream = torch.cuda.Stream()
+    w = make_workload(args, rank)
+    params = F.make_params(w.degree, w.max_depth, w.min_pts, w.tol_rel)
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+    x, y, z, f = dev(w.x), dev(w.y), dev(w.z), dev(w.f)
+    xq, yq, zq = dev(w.xq), dev(w.yq), dev(w.zq)
+    out = torch.empty(w.m, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    torch.cuda.synchronize()
+
+    def step(timed):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tree = F.fit(params, x, y, z, f, stream)
+            e1.record(stream)
+            F.evaluate(tree, xq, yq, zq, out, stream=stream)
+            e2.record(stream)
+        return tree, (e0, e1, e2)
+
+    for _ in range(args.warmup):
+        tree, _ = step(False)
+        stream.synchronize()
+        tree.close()
+
+    gpu_name = torch.cuda.get_device_properties(local_rank).name
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        uuid = str(local_rank)
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    F.fmt_profile_enable(True)
+    evs, trees = [], []
+    for _ in range(args.steps):
+        tree, ev = step(True)
+        evs.append(ev)
+        trees.append(tree)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = F.fmt_profile_read()
+    F.fmt_profile_enable(False)
+    clocks = sampler.stop()
+    fit_ms = [a.elapsed_time(b) for a, b, _ in evs]
+    eval_ms = [b.elapsed_time(c) for _, b, c in evs]
+    last = trees[-1]
+    ex = F.parse_export(F.fmt_tree_export(last))
+    stats = F.fmt_tree_stats(last)
+    for t in trees[:-1]:
+        t.close()
+
+    fit_s = sum(fit_ms) / len(fit_ms) / 1e3
+    eval_s = sum(eval_ms) / len(eval_ms) / 1e3
+    if dist:
+        tt = torch.tensor([fit_s, eval_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        fit_s, eval_s = float(tt[0]), float(tt[1])
+
+    # accuracy of the interpolant against the closed form (last timed step)
+    pred = out.cpu().numpy()
+    erms, einf = W.errors(pred, W.franke_bj(w.xq, w.yq, w.zq))
+
+    # roofline of the dominant kernel (tile_qr, FP64 pipe); flops = 2 m^2 per row
+    qr = prof.get("tile_qr", {})
+    qr_tflops = qr["flops"] / (qr["ms"] * 1e-3) / 1e12 if qr.get("ms") else None
+    dfma = F.fmt_probe_dfma(20000, stream)
+    probe_tflops = 2.0 * dfma / 1e12
+    fit_flops = sum(v["flops"] for k, v in prof.items() if k != "evaluate")
+    ev_levels = levels_visited(ex, w.xq, w.yq, w.zq, (0.0, 0.0, 0.0), 1.0)
+    hf = 2.0 * (F.fmt_nmono(w.degree) + (w.degree + 1) * (w.degree + 2) / 2 + (w.degree + 1))
+    ev = prof.get("evaluate", {})
+    ev_tflops = ev_levels * hf * args.steps / (ev["ms"] * 1e-3) / 1e12 if ev.get("ms") else None
+    total_ms = sum(v["ms"] for v in prof.values())
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                   "share": (v["ms"] / total_ms if total_ms else None)} for k, v in prof.items() if v["launches"]}
+    gpu_launches = sum(v["launches"] for v in prof.values())
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API: pinned host inputs -> device -> fit -> evaluate -> host
+        hx, hy, hz, hf_ = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (w.x, w.y, w.z, w.f))
+        hxq, hyq, hzq = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (w.xq, w.yq, w.zq))
+        hout = torch.empty(w.m, dtype=torch.float64).pin_memory()
+        dx, dy, dz, df = (torch.empty_like(x) for _ in range(4))
+        dxq, dyq, dzq = (torch.empty_like(xq) for _ in range(3))
+        e2e_fit, e2e_eval = [], []
+        for i in range(args.warmup + args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                c = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for d_, h_ in ((dx, hx), (dy, hy), (dz, hz), (df, hf_)):
+                    d_.copy_(h_, non_blocking=True)
+                tr = F.fit(params, dx, dy, dz, df, stream)
+                b.record(stream)
+                for d_, h_ in ((dxq, hxq), (dyq, hyq), (dzq, hzq)):
+                    d_.copy_(h_, non_blocking=True)
+                F.evaluate(tr, dxq, dyq, dzq, out, stream=stream)
+                hout.copy_(out, non_blocking=True)
+                c.record(stream)
+            stream.synchronize()
+            if i >= args.warmup:
+                e2e_fit.append(a.elapsed_time(b) / 1e3)
+                e2e_eval.append(b.elapsed_time(c) / 1e3)
+            tr.close()
+        tf = sum(e2e_fit) / len(e2e_fit)
+        te = sum(e2e_eval) / len(e2e_eval)
+        e2e = {"value": world * w.n / tf, "unit": UNIT, "evals_per_s": world * w.m / te,
+               "h2d_bytes_per_step": 32 * w.n + 24 * w.m, "d2h_bytes_per_step": 8 * w.m,
+               "ms_per_step": (tf + te) * 1e3}
+
+    if args.profile_only:
+        return 0
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    nodes = [int(stats.nodes[d]) for d in range(stats.n_levels)]
+    points = [int(stats.points[d]) for d in range(stats.n_levels)]
+    line = {
+        "metric": METRIC, "value": world * w.n / fit_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": (fit_s + eval_s) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "points": w.n, "targets": w.m, "degree": w.degree,
+                   "nmono": F.fmt_nmono(w.degree), "max_depth": w.max_depth, "min_pts": w.min_pts,
+                   "tol_rel": w.tol_rel, "values": "3-D Franke (benchmark form)",
+                   "l2": "flushed before every step (256 MB write)", "parallelism": "replicas",
+                   "gpu": gpu_name},
+        "evals_per_s": world * w.m / eval_s, "fit_ms": fit_s * 1e3, "eval_ms": eval_s * 1e3,
+        "roofline": {"bound": "alu", "kernel": "tile_qr", "achieved": qr_tflops, "peak": FP64_NOMINAL_TFLOPS,
+                     "unit": "TFLOP/s", "frac": (qr_tflops / FP64_NOMINAL_TFLOPS if qr_tflops else None),
+                     "traffic": None,
+                     "peak_source": "GB300 nominal FP64 (non-tensor) 1.25 TFLOP/s",
+                     "probe_fp64_tflops": probe_tflops,
+                     "frac_of_probe": (qr_tflops / probe_tflops if qr_tflops else None),
+                     "flops_per_row": "2 m^2, m = nmono + 1 (Householder on [Lambda | r])"},
+        "fit_roofline": {"bound": "alu", "achieved": fit_flops / args.steps / fit_s * 1e-12, "unit": "TFLOP/s",
+                         "peak": FP64_NOMINAL_TFLOPS,
+                         "frac": fit_flops / args.steps / fit_s * 1e-12 / FP64_NOMINAL_TFLOPS,
+                         "what": "algorithmic flops of the whole fit phase / fit wall time"},
+        "eval_roofline": {"bound": "alu", "achieved": ev_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                          "frac": (ev_tflops / FP64_NOMINAL_TFLOPS if ev_tflops else None),
+                          "flops_per_target_level": hf},
+        "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clocks,
+        "tree": {"nodes": nodes, "points": points, "near_tau": int(sum(stats.near_tau[d] for d in range(22))),
+                 "rank_flagged": int(sum(stats.rank_flagged[d] for d in range(22)))},
+        "accuracy": {"E_rms": erms, "E_inf": einf, "vs": "closed-form Franke at the targets"},
+        "e2e": e2e, "cpu_baseline": cpu,
+    }
+    last.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

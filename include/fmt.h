@@ -219,6 +219,15 @@ fmt_status fmt_profile_read(fmt_profile* out);
 /* Name of a kernel class ("tile_qr", ...), or NULL past the last class. */
 const char* fmt_profile_class_name(int32_t k);
 
+/*
+ * FP64 pipe throughput probe (no counterpart in the paper): runs a kernel of
+ * independent fused multiply-adds on every SM for about `iters` x 8 DFMA per
+ * thread and returns the measured rate in DFMA per second (FLOP/s = 2x).  It
+ * is the denominator of the FP64 roofline reported next to the fit kernels.
+ * Synchronises.
+ */
+fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream);
+
 /* Release the tree (waits for its last stream).  NULL is ignored. */
 void fmt_tree_free(fmt_tree* tree);
 

@@ -201,6 +201,7 @@ fmt_status alloc_level(fmt_tree* t, int d, int64_t cap_nodes, int64_t cap_items,
   TRY(talloc(t, &L.item_start, cap_items, s));
   TRY(talloc(t, &L.item_end, cap_items, s));
   TRY(talloc(t, &L.item_local, cap_items, s));
+  TRY(talloc(t, &L.sched, cap_items, s));
   CUDA_TRY(t, cudaMemsetAsync(L.masks, 0, sizeof(int32_t) * (size_t)cap_nodes, s), "memset");
   CUDA_TRY(t, cudaMemsetAsync(L.child_E, 0, sizeof(double) * 8 * (size_t)cap_nodes, s), "memset");
   return FMT_OK;
@@ -306,7 +307,8 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
       (st = talloc(t, &vals, n, s)) || (st = talloc(t, &vals_alt, n, s)) ||
       (st = talloc(t, (char**)&temp, (int64_t)radix_sort_temp_bytes(n, key64), s)) ||
       (st = talloc(t, &t->d_err, 1, s)) || (st = talloc(t, &d_maxbits, 1, s)) ||
-      (st = talloc(t, &t->d_plan, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)))
+      (st = talloc(t, &t->d_plan, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)) ||
+      (st = talloc(t, &t->d_work, 1, s)))
     return fail(st);
   if (cudaMallocHost((void**)&t->h_plan, sizeof(fmt_plan_out)) != cudaSuccess) {
     cudaGetLastError();
@@ -800,6 +802,41 @@ fmt_status fmt_profile_read(fmt_profile* out) {
     if (cudaEventElapsedTime(&ms, g_recs[i].a, g_recs[i].b) == cudaSuccess) out->ms[g_recs[i].k] += ms;
     else cudaGetLastError();
   }
+  return FMT_OK;
+}
+
+fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream) {
+  if (!dfma_per_s || iters < 1) return set_err(nullptr, FMT_EINVAL, "bad probe arguments");
+  *dfma_per_s = 0.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = (nsm > 0 ? nsm : 152) * 4;  // 32 warps per SM
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * (size_t)blocks * 256) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(nullptr, FMT_ENOMEM, "probe buffer allocation failed");
+  }
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaError_t e = launch_probe_dfma(iters / 8 + 1, blocks, buf, s);  // warm-up
+  float best = 0.0f;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(a, s);
+    e = launch_probe_dfma(iters, blocks, buf, s);
+    cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && (best == 0.0f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(buf);
+  if (e != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "probe: %s", cudaGetErrorString(e));
+  *dfma_per_s = 8.0 * (double)iters * blocks * 256.0 / (best * 1e-3);
   return FMT_OK;
 }
 

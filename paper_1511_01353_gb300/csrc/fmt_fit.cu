@@ -60,6 +60,9 @@ struct QRArgs {
   double lo0, lo1, lo2, side;
   int depth, q, m, ldB;
   double* R;
+  const int32_t* sched;
+  int* work;
+  int n_items;
 };
 
 // Structured Householder absorb of a row block B (NB x m in shared memory,
@@ -68,64 +71,116 @@ struct QRArgs {
 // x = B[:, j], beta = -sign(alpha) sqrt(alpha^2 + |x|^2) (sign(0) = +), and
 // H = I - gamma u u^T, gamma = 1 / (beta (beta - alpha)).  A column with
 // |x| = 0 is left alone (no reflection).
+//
+// Schedule per step j (one barrier per step):
+//  * row j of R sits in shared memory (Rs[j&1]); row j+1 was prefetched into
+//    registers during step j-1 and is stashed into Rs[(j+1)&1] here, while
+//    row j+2 is fetched from global memory for the next step;
+//  * quads update the columns k > j (round r covers 32 columns); updated R_jk
+//    are written through to global memory;
+//  * warp 0, right after its first round (which updates column j+1), computes
+//    the reflector of step j+1 (look-ahead), so no step waits on a serial
+//    norm / sqrt / divide phase of its own.
+constexpr int kPrefetch = 6;  // ceil((681 - 1) / 128): enough for degree 14
+
+__device__ __forceinline__ void reflector(const double* __restrict__ B, int ldB, int NB, int j, double* Rrow,
+                                          double* __restrict__ Rg, int m, double* sc) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < NB; i += 32) {
+    const double xv = B[i * ldB + j];
+    s = fma(xv, xv, s);
+  }
+  s = warp_sum(s);
+  if (lane == 0) {
+    const double alpha = Rrow[j];
+    if (s == 0.0) {
+      sc[0] = 0.0;
+      sc[1] = 0.0;
+    } else {
+      const double h = sqrt(fma(alpha, alpha, s));
+      const double beta = alpha >= 0.0 ? -h : h;
+      sc[0] = 1.0 / (h * (h + fabs(alpha)));
+      sc[1] = alpha - beta;
+      Rrow[j] = beta;
+      Rg[(size_t)j * m + j] = beta;
+    }
+  }
+}
+
 template <int RPT>
 __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, int j_begin, int m,
-                                             double* __restrict__ R, double* sc) {
+                                             double* __restrict__ R, double* __restrict__ Rs, double* sc) {
   constexpr int NB = 4 * RPT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, rg = tid & 3;
-  for (int j = j_begin; j < m; ++j) {
-    if (warp == 0) {
-      double s = 0.0;
+  if (j_begin >= m) return;
+  // prologue: row j_begin into shared memory, its reflector, prefetch of the next row
+  for (int k = j_begin + tid; k < m; k += kQRThreads) Rs[(j_begin & 1) * ldB + k] = R[(size_t)j_begin * m + k];
+  __syncthreads();
+  if (warp == 0) reflector(B, ldB, NB, j_begin, Rs + (j_begin & 1) * ldB, R, m, sc + (j_begin & 1) * 2);
+  double pf[kPrefetch];
 #pragma unroll
-      for (int i = lane; i < NB; i += 32) {
-        double xv = B[i * ldB + j];
-        s = fma(xv, xv, s);
-      }
-      s = warp_sum(s);
-      if (lane == 0) {
-        double* rjj = R + (size_t)j * m + j;
-        double alpha = *rjj;
-        if (s == 0.0) {
-          sc[0] = 0.0;
-          sc[1] = 0.0;
-        } else {
-          double h = sqrt(fma(alpha, alpha, s));
-          double beta = alpha >= 0.0 ? -h : h;
-          sc[0] = 1.0 / (h * (h + fabs(alpha)));
-          sc[1] = alpha - beta;
-          *rjj = beta;
-        }
-      }
+  for (int e = 0; e < kPrefetch; ++e) {
+    const int k = j_begin + 1 + tid + kQRThreads * e;
+    pf[e] = (k < m) ? R[(size_t)(j_begin + 1) * m + k] : 0.0;
+  }
+  __syncthreads();
+  for (int j = j_begin; j < m; ++j) {
+    const int cur = j & 1, nxt = cur ^ 1;
+    double* Rc = Rs + cur * ldB;
+    double* Rn = Rs + nxt * ldB;
+#pragma unroll
+    for (int e = 0; e < kPrefetch; ++e) {
+      const int k = j + 1 + tid + kQRThreads * e;
+      if (k < m) Rn[k] = pf[e];
     }
-    __syncthreads();
-    const double gamma = sc[0];
-    if (gamma != 0.0) {
-      const double amb = sc[1];
-      double xr[RPT];
+#pragma unroll
+    for (int e = 0; e < kPrefetch; ++e) {
+      const int k = j + 2 + tid + kQRThreads * e;
+      pf[e] = (k < m) ? R[(size_t)(j + 2) * m + k] : 0.0;
+    }
+    const double gamma = sc[cur * 2], amb = sc[cur * 2 + 1];
+    const bool upd = gamma != 0.0;
+    double xr[RPT];
+    if (upd) {
 #pragma unroll
       for (int t = 0; t < RPT; ++t) xr[t] = B[(rg + 4 * t) * ldB + j];
-      // warp w covers columns j+1+8w .. j+8+8w of each 32-column round
-      for (int k0 = j + 1 + 8 * warp; k0 < m; k0 += 32) {
+    }
+    int k0 = j + 1 + 8 * warp;  // warp w covers columns j+1+8w .. j+8+8w of each round
+    bool lookahead = (warp == 0) && (j + 1 < m);
+    for (;;) {
+      if (upd && k0 < m) {
         const int k = k0 + (lane >> 2);
         const bool act = k < m;
         const int kk = act ? k : j;
-        double acc = 0.0;
+        double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-        for (int t = 0; t < RPT; ++t) acc = fma(xr[t], B[(rg + 4 * t) * ldB + kk], acc);
+        for (int t = 0; t < RPT; t += 2) {
+          a0 = fma(xr[t], B[(rg + 4 * t) * ldB + kk], a0);
+          a1 = fma(xr[t + 1], B[(rg + 4 * t + 4) * ldB + kk], a1);
+        }
+        double acc = a0 + a1;
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (act) {
-          double* rjk = R + (size_t)j * m + k;
-          const double rv = *rjk;
+          const double rv = Rc[k];
           const double d = gamma * fma(amb, rv, acc);
 #pragma unroll
           for (int t = 0; t < RPT; ++t) {
             double* bp = B + (rg + 4 * t) * ldB + k;
             *bp = fma(-d, xr[t], *bp);
           }
-          if (rg == 0) *rjk = fma(-d, amb, rv);
+          if (rg == 0) R[(size_t)j * m + k] = fma(-d, amb, rv);
         }
+        k0 += 32;
       }
+      if (lookahead) {  // column j+1 is final for this step: reflector of step j+1
+        __syncwarp();
+        reflector(B, ldB, NB, j + 1, Rn, R, m, sc + nxt * 2);
+        lookahead = false;
+        continue;
+      }
+      if (!upd || k0 >= m) break;
     }
     __syncthreads();
   }
@@ -138,63 +193,77 @@ __device__ __forceinline__ void node_frame(const QRArgs& a, uint64_t pf, double&
   fmt_frame(a.lo2, a.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
 }
 
+// Persistent CTAs take work items from a queue in the order of `sched`
+// (largest items first), so the longest chunks start early.
 template <int RPT>
 __global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
-  extern __shared__ double Bs[];
-  __shared__ double sc[2];
+  extern __shared__ double smem[];
   constexpr int NB = 4 * RPT;
-  const int item = blockIdx.x;
-  const int64_t node = a.item_node[item];
-  const int64_t rs = a.item_start[item], re = a.item_end[item];
+  double* Bs = smem;
+  double* Rs = smem + NB * a.ldB;
+  double* sc = Rs + 2 * a.ldB;
+  __shared__ int s_item;
   const int m = a.m;
-  double* R = a.R + (size_t)item * m * m;
-  for (int e = threadIdx.x; e < m * m; e += kQRThreads) {
-    int j = e / m, k = e - j * m;
-    if (k >= j) R[e] = 0.0;
-  }
-  double c0, s0, c1, s1, c2, s2;
-  node_frame(a, a.prefix[node], c0, s0, c1, s1, c2, s2);
   const int q = a.q;
-  __syncthreads();
-  for (int64_t b0 = rs; b0 < re; b0 += NB) {
-    const int nb = (int)((re - b0) < NB ? (re - b0) : NB);
-    if (threadIdx.x < NB) {
-      double* row = Bs + threadIdx.x * a.ldB;
-      if ((int)threadIdx.x < nb) {
-        const int64_t i = b0 + threadIdx.x;
-        const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
-        double pu[FMT_MAX_DEGREE + 1], pv[FMT_MAX_DEGREE + 1], pw[FMT_MAX_DEGREE + 1];
-        double tu = 1.0, tv = 1.0, tw = 1.0;
-        for (int l = 0; l <= q; ++l) {
-          const double f = c_invfact[l];
-          pu[l] = tu * f;
-          pv[l] = tv * f;
-          pw[l] = tw * f;
-          tu *= u;
-          tv *= v;
-          tw *= w;
-        }
-        int k = 0;
-        for (int l = 0; l <= q; ++l)
-          for (int mm = 0; mm <= q - l; ++mm) {
-            const double plm = pu[l] * pv[mm];
-            for (int n = 0; n <= q - l - mm; ++n) row[k++] = plm * pw[n];
-          }
-        row[k] = a.r[i];
-      } else {
-        for (int k = 0; k < m; ++k) row[k] = 0.0;
-      }
-    }
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
     __syncthreads();
-    absorb_block<RPT>(Bs, a.ldB, 0, m, R, sc);
+    const int it = s_item;
+    __syncthreads();
+    if (it >= a.n_items) break;
+    const int item = a.sched[it];
+    const int64_t node = a.item_node[item];
+    const int64_t rs = a.item_start[item], re = a.item_end[item];
+    double* R = a.R + (size_t)item * m * m;
+    for (int e = threadIdx.x; e < m * m; e += kQRThreads) {
+      const int j = e / m, k = e - j * m;
+      if (k >= j) R[e] = 0.0;
+    }
+    double c0, s0, c1, s1, c2, s2;
+    node_frame(a, a.prefix[node], c0, s0, c1, s1, c2, s2);
+    __syncthreads();
+    for (int64_t b0 = rs; b0 < re; b0 += NB) {
+      const int nb = (int)((re - b0) < NB ? (re - b0) : NB);
+      if (threadIdx.x < NB) {
+        double* row = Bs + threadIdx.x * a.ldB;
+        if ((int)threadIdx.x < nb) {
+          const int64_t i = b0 + threadIdx.x;
+          const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+          double pu[FMT_MAX_DEGREE + 1], pv[FMT_MAX_DEGREE + 1], pw[FMT_MAX_DEGREE + 1];
+          double tu = 1.0, tv = 1.0, tw = 1.0;
+          for (int l = 0; l <= q; ++l) {
+            const double f = c_invfact[l];
+            pu[l] = tu * f;
+            pv[l] = tv * f;
+            pw[l] = tw * f;
+            tu *= u;
+            tv *= v;
+            tw *= w;
+          }
+          int k = 0;
+          for (int l = 0; l <= q; ++l)
+            for (int mm = 0; mm <= q - l; ++mm) {
+              const double plm = pu[l] * pv[mm];
+              for (int n = 0; n <= q - l - mm; ++n) row[k++] = plm * pw[n];
+            }
+          row[k] = a.r[i];
+        } else {
+          for (int k = 0; k < m; ++k) row[k] = 0.0;
+        }
+      }
+      __syncthreads();
+      absorb_block<RPT>(Bs, a.ldB, 0, m, R, Rs, sc);
+    }
   }
 }
 
 template <int RPT>
 __global__ void __launch_bounds__(kQRThreads) k_combine(QRArgs a, int level) {
-  extern __shared__ double Bs[];
-  __shared__ double sc[2];
+  extern __shared__ double smem[];
   constexpr int NB = 4 * RPT;
+  double* Bs = smem;
+  double* Rs = smem + NB * a.ldB;
+  double* sc = Rs + 2 * a.ldB;
   const int item = blockIdx.x;
   const int s = a.item_local[item];
   const int cnt = a.node_nitems[a.item_node[item]];
@@ -210,7 +279,7 @@ __global__ void __launch_bounds__(kQRThreads) k_combine(QRArgs a, int level) {
       Bs[i * a.ldB + k] = (row < m && k >= row) ? Rb[(size_t)row * m + k] : 0.0;
     }
     __syncthreads();
-    absorb_block<RPT>(Bs, a.ldB, r0, m, Ra, sc);
+    absorb_block<RPT>(Bs, a.ldB, r0, m, Ra, Rs, sc);
   }
 }
 
@@ -458,9 +527,12 @@ cudaError_t set_smem_attr(size_t smem) {
   return cudaFuncSetAttribute(k_combine<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// 64-bit shared accesses are served per half-warp (16 lanes = 4 columns x 4
+// row groups); with ldB = 4 (mod 16) doubles the four row groups fall into
+// distinct 32-byte bank segments, so the quads' accesses are conflict free.
 int ld_for(int m) {
   int ld = m;
-  while ((ld & 31) != 8) ++ld;
+  while ((ld & 15) != 4) ++ld;
   return ld;
 }
 
@@ -486,6 +558,9 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.m = fmt_nmono(L.q) + 1;
   a.ldB = ld_for(a.m);
   a.R = R;
+  a.sched = L.sched;
+  a.work = t->d_work;
+  a.n_items = (int)L.n_items;
   return a;
 }
 
@@ -493,12 +568,35 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
 
 int qr_rows_per_block(int m) {
   const size_t ld = (size_t)ld_for(m);
-  if (64 * ld * sizeof(double) <= 110 * 1024) return 64;
-  if (32 * ld * sizeof(double) <= 200 * 1024) return 32;
+  if (66 * ld * sizeof(double) + 32 <= 110 * 1024) return 64;
+  if (34 * ld * sizeof(double) + 32 <= 200 * 1024) return 32;
   return 16;
 }
 
-size_t qr_smem_bytes(int m, int rows) { return (size_t)rows * ld_for(m) * sizeof(double); }
+// row block + two rows of R + reflector scalars (2 steps x 2)
+size_t qr_smem_bytes(int m, int rows) { return ((size_t)(rows + 2) * ld_for(m) + 4) * sizeof(double); }
+
+template <int RPT>
+int resident_for(size_t smem) {
+  int per_sm = 0;
+  if (set_smem_attr<RPT>(smem) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_qr<RPT>, kQRThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return per_sm > 0 ? per_sm : 1;
+}
+
+int qr_resident_ctas(int m) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nsm <= 0) nsm = 1;
+  const int rows = qr_rows_per_block(m);
+  const size_t smem = qr_smem_bytes(m, rows);
+  const int per_sm = rows == 64 ? resident_for<16>(smem) : rows == 32 ? resident_for<8>(smem) : resident_for<4>(smem);
+  return nsm * per_sm;
+}
 
 cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t s) {
   QRArgs a = make_qr_args(t, depth, R);
@@ -506,19 +604,22 @@ cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t
   if (n_items <= 0) return cudaSuccess;
   const int rows = qr_rows_per_block(a.m);
   const size_t smem = qr_smem_bytes(a.m, rows);
-  cudaError_t e;
+  int64_t grid = qr_resident_ctas(a.m);
+  if (grid > n_items) grid = n_items;
+  cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   switch (rows) {
     case 64:
       if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;
-      k_tile_qr<16><<<(unsigned)n_items, kQRThreads, smem, s>>>(a);
+      k_tile_qr<16><<<(unsigned)grid, kQRThreads, smem, s>>>(a);
       break;
     case 32:
       if ((e = set_smem_attr<8>(smem)) != cudaSuccess) return e;
-      k_tile_qr<8><<<(unsigned)n_items, kQRThreads, smem, s>>>(a);
+      k_tile_qr<8><<<(unsigned)grid, kQRThreads, smem, s>>>(a);
       break;
     default:
       if ((e = set_smem_attr<4>(smem)) != cudaSuccess) return e;
-      k_tile_qr<4><<<(unsigned)n_items, kQRThreads, smem, s>>>(a);
+      k_tile_qr<4><<<(unsigned)grid, kQRThreads, smem, s>>>(a);
       break;
   }
   return cudaGetLastError();

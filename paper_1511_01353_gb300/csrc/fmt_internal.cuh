@@ -113,6 +113,7 @@ struct fmt_level {
   int64_t* item_start = nullptr;
   int64_t* item_end = nullptr;
   int32_t* item_local = nullptr;  // chunk index inside its node
+  int32_t* sched = nullptr;       // item order for the QR queue (largest first)
 };
 
 // Small result block that refine reads back in one copy.
@@ -148,6 +149,7 @@ struct fmt_tree {
   fmt_plan_out* d_plan = nullptr;
   fmt_plan_out* h_plan = nullptr;  // pinned
   unsigned long long* d_counter = nullptr;
+  int* d_work = nullptr;  // work-queue counter of the persistent QR kernel
   int64_t chunk_floor = 64;
   fmt_status sticky = FMT_OK;
   char msg[256] = {0};
@@ -178,6 +180,7 @@ cudaError_t launch_plan_root(const fmt_tree* t, int64_t chunk_rows_fixed, int64_
 
 // fit
 int qr_rows_per_block(int m);
+int qr_resident_ctas(int m);  // SMs x resident QR CTAs per SM
 size_t qr_smem_bytes(int m, int rows);
 cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t s);
 cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s);
@@ -191,4 +194,5 @@ cudaError_t launch_refine(const fmt_tree* t, int depth, int64_t chunk_rows_fixed
 cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const double* xq, const double* yq,
                             const double* zq, double* out, unsigned long long* d_outside,
                             cudaStream_t s);
+cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream_t s);
 cudaError_t launch_make_hcoef(int64_t n, int p, int nmono, const double* coef, double* hcoef, cudaStream_t s);

@@ -61,12 +61,14 @@ struct PlanArgs {
   int64_t* item_start;
   int64_t* item_end;
   int32_t* item_local;
+  int32_t* sched;
 };
 
 // Split every node into ceil(count / C) nearly equal row chunks.
 __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
   int64_t C = a.chunk_fixed;
   if (C <= 0) {
+    // nsm carries the number of resident QR CTAs (SMs x CTAs per SM)
     int64_t per = (a.total_points + a.nsm - 1) / a.nsm;
     per = (per + 63) / 64 * 64;
     C = per > a.chunk_floor ? per : a.chunk_floor;
@@ -107,6 +109,35 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
     __syncthreads();
   }
   maxc = block_max<int64_t>(maxc);
+  // Queue order for the QR kernel: items bucketed by floor(log2(rows)),
+  // largest bucket first (order inside a bucket does not matter: every item
+  // writes its own triangle).
+  __shared__ int bucket_cnt[64];
+  const int64_t n_items = carry;
+  if (threadIdx.x < 64) bucket_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  if (n_items <= a.cap_items) {
+    for (int64_t i = threadIdx.x; i < n_items; i += blockDim.x) {
+      const int64_t rows = a.item_end[i] - a.item_start[i];
+      const int b = 63 - __clzll(rows > 0 ? rows : 1);
+      atomicAdd(&bucket_cnt[b], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int b = 63; b >= 0; --b) {
+        const int c = bucket_cnt[b];
+        bucket_cnt[b] = acc;
+        acc += c;
+      }
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n_items; i += blockDim.x) {
+      const int64_t rows = a.item_end[i] - a.item_start[i];
+      const int b = 63 - __clzll(rows > 0 ? rows : 1);
+      a.sched[atomicAdd(&bucket_cnt[b], 1)] = (int32_t)i;
+    }
+  }
   if (threadIdx.x == 0) {
     out->n_items = carry;
     out->max_chunks = maxc;
@@ -293,6 +324,24 @@ __global__ void k_make_hcoef(int64_t n, int p, int nmono, const double* __restri
   hcoef[i] = coef[i] * (c_invfact[l] * c_invfact[mm] * c_invfact[k]);
 }
 
+// eight independent FMA chains per thread keep the FP64 pipe saturated
+__global__ void __launch_bounds__(256) k_probe_dfma(int64_t iters, double* out) {
+  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,
+         a7 = a0 + 7;
+  const double m = 0.999999, c = 1e-7;
+  for (int64_t i = 0; i < iters; ++i) {
+    a0 = fma(a0, m, c);
+    a1 = fma(a1, m, c);
+    a2 = fma(a2, m, c);
+    a3 = fma(a3, m, c);
+    a4 = fma(a4, m, c);
+    a5 = fma(a5, m, c);
+    a6 = fma(a6, m, c);
+    a7 = fma(a7, m, c);
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+}
+
 PlanArgs plan_args_for(const fmt_tree* t, const fmt_level& L, int64_t chunk_fixed, int64_t chunk_floor) {
   PlanArgs a;
   a.n_nodes = L.n_nodes;
@@ -301,10 +350,7 @@ PlanArgs plan_args_for(const fmt_tree* t, const fmt_level& L, int64_t chunk_fixe
   a.total_points = 0;
   a.chunk_fixed = chunk_fixed;
   a.chunk_floor = chunk_floor;
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  a.nsm = nsm > 0 ? nsm : 152;
+  a.nsm = qr_resident_ctas(fmt_nmono(L.q > 0 ? L.q : t->P.degree) + 1);
   a.cap_items = L.cap_items;
   a.node_item0 = L.node_item0;
   a.node_nitems = L.node_nitems;
@@ -312,6 +358,7 @@ PlanArgs plan_args_for(const fmt_tree* t, const fmt_level& L, int64_t chunk_fixe
   a.item_start = L.item_start;
   a.item_end = L.item_end;
   a.item_local = L.item_local;
+  a.sched = L.sched;
   return a;
 }
 
@@ -387,5 +434,10 @@ cudaError_t launch_make_hcoef(int64_t n, int p, int nmono, const double* coef, d
   const int64_t tot = n * nmono;
   if (tot <= 0) return cudaSuccess;
   k_make_hcoef<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, p, nmono, coef, hcoef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream_t s) {
+  k_probe_dfma<<<blocks, 256, 0, s>>>(iters, out);
   return cudaGetLastError();
 }

@@ -62,7 +62,7 @@ class fmt_export_header(ctypes.Structure):
 
 EXPORTED = ["fmt_nmono", "oct_build", "fit_level", "refine", "evaluate", "fmt_tree_stats", "fmt_tree_export",
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
-            "fmt_profile_class_name"]
+            "fmt_profile_class_name", "fmt_probe_dfma"]
 PROFILE_CLASSES = 16
 
 
@@ -113,6 +113,8 @@ def load(build: bool = True):
         L.fmt_profile_read.restype = ctypes.c_int
         L.fmt_profile_class_name.argtypes = [i32]
         L.fmt_profile_class_name.restype = ctypes.c_char_p
+        L.fmt_probe_dfma.argtypes = [i64, ctypes.POINTER(ctypes.c_double), P]
+        L.fmt_probe_dfma.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -242,6 +244,13 @@ def fmt_profile_read() -> dict:
         out[name.decode()] = dict(launches=int(p.launches[k]), ms=float(p.ms[k]), units=float(p.units[k]),
                                   flops=float(p.flops[k]))
     return out
+
+
+def fmt_probe_dfma(iters: int = 20000, stream=None) -> float:
+    """Measured FP64 FMA rate of the current GPU (DFMA per second)."""
+    v = ctypes.c_double(0.0)
+    _check(load().fmt_probe_dfma(iters, ctypes.byref(v), _stream_handle(stream)))
+    return float(v.value)
 
 
 def fmt_profile_class_name(k: int):
