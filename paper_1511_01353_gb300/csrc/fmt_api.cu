@@ -284,7 +284,11 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
   t->nmono = fmt_nmono(P.degree);
   t->S = 2097152.0 / P.side;
   {
-    int64_t fl = 16 * (int64_t)(t->nmono + 1);
+    // A chunk of C rows costs about 2 m^2 C flops and one merge about (2/3) m^3,
+    // so C >= 4m keeps merges under ~10% of the chunk work; above that floor
+    // the planner sizes chunks to the rows per resident QR CTA, so that the
+    // largest item is no longer than the average share of a CTA.
+    int64_t fl = 4 * (int64_t)(t->nmono + 1);
     t->chunk_floor = fl < 64 ? 64 : (fl + 63) / 64 * 64;
   }
   const int sort_levels = P.max_depth + 1 < FMT_QBITS ? P.max_depth + 1 : FMT_QBITS;

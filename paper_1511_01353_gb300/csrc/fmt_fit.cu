@@ -81,8 +81,6 @@ struct QRArgs {
 //  * warp 0, right after its first round (which updates column j+1), computes
 //    the reflector of step j+1 (look-ahead), so no step waits on a serial
 //    norm / sqrt / divide phase of its own.
-constexpr int kPrefetch = 6;  // ceil((681 - 1) / 128): enough for degree 14
-
 __device__ __forceinline__ void reflector(const double* __restrict__ B, int ldB, int NB, int j, double* Rrow,
                                           double* __restrict__ Rg, int m, double* sc) {
   const int lane = threadIdx.x & 31;
@@ -108,20 +106,26 @@ __device__ __forceinline__ void reflector(const double* __restrict__ B, int ldB,
   }
 }
 
-template <int RPT>
+// tri_row0 >= 0 marks a block whose row i is zero left of column tri_row0+i
+// (rows of another triangle): at step j only rows i <= j - tri_row0 can be
+// nonzero, so whole groups of four rows are skipped (warp-uniform bound).
+template <int RPT, int NW>
 __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, int j_begin, int m,
-                                             double* __restrict__ R, double* __restrict__ Rs, double* sc) {
+                                             double* __restrict__ R, double* __restrict__ Rs, double* sc,
+                                             int tri_row0) {
   constexpr int NB = 4 * RPT;
+  constexpr int NT = 32 * NW;
+  constexpr int kPF = (680 + NT - 1) / NT;  // enough prefetch registers for degree 14
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, rg = tid & 3;
   if (j_begin >= m) return;
   // prologue: row j_begin into shared memory, its reflector, prefetch of the next row
-  for (int k = j_begin + tid; k < m; k += kQRThreads) Rs[(j_begin & 1) * ldB + k] = R[(size_t)j_begin * m + k];
+  for (int k = j_begin + tid; k < m; k += NT) Rs[(j_begin & 1) * ldB + k] = R[(size_t)j_begin * m + k];
   __syncthreads();
   if (warp == 0) reflector(B, ldB, NB, j_begin, Rs + (j_begin & 1) * ldB, R, m, sc + (j_begin & 1) * 2);
-  double pf[kPrefetch];
+  double pf[kPF];
 #pragma unroll
-  for (int e = 0; e < kPrefetch; ++e) {
-    const int k = j_begin + 1 + tid + kQRThreads * e;
+  for (int e = 0; e < kPF; ++e) {
+    const int k = j_begin + 1 + tid + NT * e;
     pf[e] = (k < m) ? R[(size_t)(j_begin + 1) * m + k] : 0.0;
   }
   __syncthreads();
@@ -130,21 +134,23 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
     double* Rc = Rs + cur * ldB;
     double* Rn = Rs + nxt * ldB;
 #pragma unroll
-    for (int e = 0; e < kPrefetch; ++e) {
-      const int k = j + 1 + tid + kQRThreads * e;
+    for (int e = 0; e < kPF; ++e) {
+      const int k = j + 1 + tid + NT * e;
       if (k < m) Rn[k] = pf[e];
     }
 #pragma unroll
-    for (int e = 0; e < kPrefetch; ++e) {
-      const int k = j + 2 + tid + kQRThreads * e;
+    for (int e = 0; e < kPF; ++e) {
+      const int k = j + 2 + tid + NT * e;
       pf[e] = (k < m) ? R[(size_t)(j + 2) * m + k] : 0.0;
     }
+    // groups of four rows that can hold nonzeros at this step (warp uniform)
+    const int tmax = tri_row0 < 0 ? RPT : min(RPT, max(0, (j - tri_row0) / 4 + 1));
     const double gamma = sc[cur * 2], amb = sc[cur * 2 + 1];
     const bool upd = gamma != 0.0;
     double xr[RPT];
     if (upd) {
 #pragma unroll
-      for (int t = 0; t < RPT; ++t) xr[t] = B[(rg + 4 * t) * ldB + j];
+      for (int t = 0; t < RPT; ++t) xr[t] = (t < tmax) ? B[(rg + 4 * t) * ldB + j] : 0.0;
     }
     int k0 = j + 1 + 8 * warp;  // warp w covers columns j+1+8w .. j+8+8w of each round
     bool lookahead = (warp == 0) && (j + 1 < m);
@@ -156,8 +162,8 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
         double a0 = 0.0, a1 = 0.0;
 #pragma unroll
         for (int t = 0; t < RPT; t += 2) {
-          a0 = fma(xr[t], B[(rg + 4 * t) * ldB + kk], a0);
-          a1 = fma(xr[t + 1], B[(rg + 4 * t + 4) * ldB + kk], a1);
+          if (t < tmax) a0 = fma(xr[t], B[(rg + 4 * t) * ldB + kk], a0);
+          if (t + 1 < tmax) a1 = fma(xr[t + 1], B[(rg + 4 * t + 4) * ldB + kk], a1);
         }
         double acc = a0 + a1;
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -167,12 +173,14 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
           const double d = gamma * fma(amb, rv, acc);
 #pragma unroll
           for (int t = 0; t < RPT; ++t) {
-            double* bp = B + (rg + 4 * t) * ldB + k;
-            *bp = fma(-d, xr[t], *bp);
+            if (t < tmax) {
+              double* bp = B + (rg + 4 * t) * ldB + k;
+              *bp = fma(-d, xr[t], *bp);
+            }
           }
           if (rg == 0) R[(size_t)j * m + k] = fma(-d, amb, rv);
         }
-        k0 += 32;
+        k0 += 8 * NW;
       }
       if (lookahead) {  // column j+1 is final for this step: reflector of step j+1
         __syncwarp();
@@ -252,13 +260,17 @@ __global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
         }
       }
       __syncthreads();
-      absorb_block<RPT>(Bs, a.ldB, 0, m, R, Rs, sc);
+      absorb_block<RPT, kQRThreads / 32>(Bs, a.ldB, 0, m, R, Rs, sc, -1);
     }
   }
 }
 
+// Pairwise merge of two triangles of one node (a TSQR tree level): the second
+// triangle is absorbed into the first in blocks of NB rows.  Few pairs are
+// active at the top of the tree, so this kernel runs 16 warps per CTA.
+constexpr int kCombineWarps = 16;
 template <int RPT>
-__global__ void __launch_bounds__(kQRThreads) k_combine(QRArgs a, int level) {
+__global__ void __launch_bounds__(32 * kCombineWarps) k_combine(QRArgs a, int level) {
   extern __shared__ double smem[];
   constexpr int NB = 4 * RPT;
   double* Bs = smem;
@@ -273,13 +285,13 @@ __global__ void __launch_bounds__(kQRThreads) k_combine(QRArgs a, int level) {
   double* Ra = a.R + (size_t)item * m * m;
   const double* Rb = a.R + (size_t)(item + step) * m * m;
   for (int r0 = 0; r0 < m; r0 += NB) {
-    for (int e = threadIdx.x; e < NB * m; e += kQRThreads) {
+    for (int e = threadIdx.x; e < NB * m; e += 32 * kCombineWarps) {
       const int i = e / m, k = e - i * m;
       const int row = r0 + i;
       Bs[i * a.ldB + k] = (row < m && k >= row) ? Rb[(size_t)row * m + k] : 0.0;
     }
     __syncthreads();
-    absorb_block<RPT>(Bs, a.ldB, r0, m, Ra, Rs, sc);
+    absorb_block<RPT, kCombineWarps>(Bs, a.ldB, r0, m, Ra, Rs, sc, r0);
   }
 }
 
@@ -635,15 +647,15 @@ cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double*
   switch (rows) {
     case 64:
       if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;
-      k_combine<16><<<(unsigned)n_items, kQRThreads, smem, s>>>(a, tree_level);
+      k_combine<16><<<(unsigned)n_items, 32 * kCombineWarps, smem, s>>>(a, tree_level);
       break;
     case 32:
       if ((e = set_smem_attr<8>(smem)) != cudaSuccess) return e;
-      k_combine<8><<<(unsigned)n_items, kQRThreads, smem, s>>>(a, tree_level);
+      k_combine<8><<<(unsigned)n_items, 32 * kCombineWarps, smem, s>>>(a, tree_level);
       break;
     default:
       if ((e = set_smem_attr<4>(smem)) != cudaSuccess) return e;
-      k_combine<4><<<(unsigned)n_items, kQRThreads, smem, s>>>(a, tree_level);
+      k_combine<4><<<(unsigned)n_items, 32 * kCombineWarps, smem, s>>>(a, tree_level);
       break;
   }
   return cudaGetLastError();
