@@ -228,6 +228,42 @@ const char* fmt_profile_class_name(int32_t k);
  */
 fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream);
 
+/*
+ * fmt_fit_node_static -- allocation-free least-squares fit of ONE point set.
+ * The paper has no counterpart: this exists for callers that cannot let a
+ * library allocate device memory -- code whose device memory is owned by
+ * another allocator or a fixed budget, or that must not risk the implicit
+ * device synchronisation and run-time out-of-memory failures of cudaMalloc.
+ * It performs the per-node fit of the tree path (Householder QR of
+ * [Lambda(u) | r], back substitution with the rank rule, residual update) for
+ * a single node whose box is the root cube [lo, lo+side)^3, and allocates
+ * nothing: its scratch is one static device array of 166 x 166 doubles
+ * (220,448 bytes, FMT_STATIC_MAX_DEGREE = 8), which stays on every GPU that
+ * loads the library until the process exits.
+ *   degree   0 <= degree <= FMT_STATIC_MAX_DEGREE, else FMT_EINVAL with a
+ *            message naming the limit.  When n < nmono(degree) the degree is
+ *            lowered as at the root of a tree (flag FMT_FLAG_DEG_CLAMPED).
+ *   n        number of points, 1 <= n < 2^31.
+ *   x,y,z    device, n doubles each (global coordinates), caller owned.
+ *   r_in     device, n doubles: the values to fit, caller owned.
+ *   lo, side host: the box, read during the call.
+ *   coef     device, nmono(degree) doubles, written: F in Alg. 2 order.
+ *   r_out    device, n doubles, written: r_in - Lambda F (may equal r_in).
+ *   flags    device int32 or NULL, written: FMT_FLAG_RANK | FMT_FLAG_DEG_CLAMPED.
+ * One CTA does the whole fit, so it suits small point sets (it is slow for
+ * millions of points).  Every call on a device uses the same scratch array
+ * and leaves its contents behind (each call clears what it reads before
+ * use): calls that can overlap on the GPU (different streams, or threads
+ * without ordering) race and corrupt each other -- order them on one stream.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Asynchronous.
+ */
+#define FMT_STATIC_MAX_DEGREE 8
+fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const double* x, const double* y, const double* z,
+                               const double* r_in, const double* lo, double side, double* coef, double* r_out,
+                               int32_t* flags, void* stream);
+
 /* Release the tree (waits for its last stream).  NULL is ignored. */
 void fmt_tree_free(fmt_tree* tree);
 

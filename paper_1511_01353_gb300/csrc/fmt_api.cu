@@ -240,6 +240,9 @@ void destroy(fmt_tree* t) {
 
 }  // namespace
 
+// error reporting for entry points defined in other translation units
+fmt_status fmt_set_error(fmt_status st, const char* msg) { return set_err(nullptr, st, "%s", msg); }
+
 extern "C" {
 
 int32_t fmt_nmono(int32_t degree) {

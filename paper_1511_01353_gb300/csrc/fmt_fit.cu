@@ -26,6 +26,9 @@
 #include <float.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+
+#include <mutex>
 
 #include "fmt_internal.cuh"
 
@@ -330,17 +333,20 @@ __device__ int mono_index(int p, int l, int m, int n) {
   return idx + n;
 }
 
-__global__ void __launch_bounds__(128) k_backsolve(BSArgs a) {
-  extern __shared__ double sm[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t node = (int64_t)blockIdx.x * 4 + wib;
-  if (node >= a.n_nodes) return;
-  const int m = a.m, L = m - 1;
-  double* y = sm + (size_t)wib * (3 * L + (L + 1) / 2 + 1);
+// Back substitution of one node by one warp: F = R^{-1} (Q^T r) on the final
+// triangle [R | Q^T r] (m x m, row-major), with the rank rule (columns with
+// |R_jj| <= 64 L eps max|R_kk| dropped and the rest re-triangularised).
+// Writes F and F / (l! m! n!) in the degree-p layout (zeros for monomials of
+// degree > q and for dropped columns).  ws: 3L + (L+1)/2 + 1 doubles.
+// Returns the number of dropped columns.
+__device__ int backsolve_warp(double* __restrict__ R, int m, int q, int p, int nmono_p, double* ws,
+                              double* __restrict__ cf, double* __restrict__ hc) {
+  const int lane = threadIdx.x & 31;
+  const int L = m - 1;
+  double* y = ws;
   double* inv = y + L;
   double* F = inv + L;
   int* keep = (int*)(F + L);
-  double* R = a.R + (size_t)a.node_item0[node] * m * m;
 
   double rmax = 0.0;
   for (int j = lane; j < L; j += 32) rmax = fmax(rmax, fabs(R[(size_t)j * m + j]));
@@ -409,11 +415,8 @@ __global__ void __launch_bounds__(128) k_backsolve(BSArgs a) {
     for (int k = lane; k < j; k += 32) y[k] = fma(-R[(size_t)k * m + j], Fj, y[k]);
     __syncwarp();
   }
-  // write F (and F / (l! m! n!)) in the degree-p layout
-  double* cf = a.coef + (size_t)node * a.nmono_p;
-  double* hc = a.hcoef + (size_t)node * a.nmono_p;
-  if (a.q != a.p || ndrop > 0) {
-    for (int k = lane; k < a.nmono_p; k += 32) {
+  if (q != p || ndrop > 0) {
+    for (int k = lane; k < nmono_p; k += 32) {
       cf[k] = 0.0;
       hc[k] = 0.0;
     }
@@ -422,11 +425,27 @@ __global__ void __launch_bounds__(128) k_backsolve(BSArgs a) {
   for (int c = lane; c < Lk; c += 32) {
     const int jq = ndrop > 0 ? keep[c] : c;
     int l, mm, n;
-    mono_lmn(a.q, jq, l, mm, n);
-    const int jp = (a.q == a.p) ? jq : mono_index(a.p, l, mm, n);
+    mono_lmn(q, jq, l, mm, n);
+    const int jp = (q == p) ? jq : mono_index(p, l, mm, n);
     cf[jp] = F[c];
     hc[jp] = F[c] * (c_invfact[l] * c_invfact[mm] * c_invfact[n]);
   }
+  __syncwarp();
+  return ndrop;
+}
+
+__host__ __device__ inline int backsolve_ws_doubles(int L) { return 3 * L + (L + 1) / 2 + 1; }
+
+__global__ void __launch_bounds__(128) k_backsolve(BSArgs a) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t node = (int64_t)blockIdx.x * 4 + wib;
+  if (node >= a.n_nodes) return;
+  const int m = a.m;
+  double* ws = sm + (size_t)wib * backsolve_ws_doubles(m - 1);
+  double* R = a.R + (size_t)a.node_item0[node] * m * m;
+  const int ndrop = backsolve_warp(R, m, a.q, a.p, a.nmono_p, ws, a.coef + (size_t)node * a.nmono_p,
+                                   a.hcoef + (size_t)node * a.nmono_p);
   if (lane == 0) {
     a.deg_used[node] = a.q;
     if (ndrop > 0) a.flags[node] |= FMT_FLAG_RANK;
@@ -675,8 +694,7 @@ cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream
   a.hcoef = L.hcoef;
   a.flags = L.flags;
   a.deg_used = L.deg_used;
-  const int Lq = a.m - 1;
-  const size_t per_warp = (size_t)(3 * Lq + (Lq + 1) / 2 + 1) * sizeof(double);
+  const size_t per_warp = (size_t)backsolve_ws_doubles(a.m - 1) * sizeof(double);
   const size_t smem = 4 * per_warp;
   cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -729,4 +747,172 @@ cudaError_t launch_child_stats(const fmt_tree* t, int depth, cudaStream_t s) {
   k_child_bounds<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(a);
   k_child_sums<<<(unsigned)(L.n_nodes * 8), 128, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free single-node fit (fmt_fit_node_static in include/fmt.h).
+//
+// Its only scratch, the m x m triangle of the QR (m <= nmono(8) + 1 = 166), is
+// this file-scope device array: 166 * 166 doubles = 220,448 bytes, present on
+// every GPU that loads the library until the process exits.  All calls on a
+// device share it; each call clears the part it uses before the QR starts.
+// Host code must not pass the array's name to a kernel (in host code it is a
+// stand-in, not a device address): the address is looked up once per device
+// with cudaGetSymbolAddress and cached below.
+static __device__ __align__(256) double g_static_tri[FMT_STATIC_MAX_M * FMT_STATIC_MAX_M];
+
+namespace {
+
+struct StaticArgs {
+  int64_t n;
+  const double* x;
+  const double* y;
+  const double* z;
+  const double* r_in;
+  double* r_out;
+  double* coef;
+  int32_t* flags;
+  double lo0, lo1, lo2, side;
+  int p, q, m, ldB, nmono_p;
+  double* R;
+};
+
+// One CTA: structured Householder over all rows into the static triangle,
+// back substitution by warp 0, then the residual update by every thread.
+__global__ void __launch_bounds__(kQRThreads) k_fit_node_static(StaticArgs a) {
+  extern __shared__ double smem[];
+  constexpr int RPT = 16, NB = 4 * RPT;
+  double* Bs = smem;
+  double* Rs = smem + NB * a.ldB;
+  double* sc = Rs + 2 * a.ldB;
+  double* G = sc + 4;  // F / (l! m! n!), degree-p layout
+  const int m = a.m, q = a.q;
+  double* R = a.R;
+  for (int e = threadIdx.x; e < m * m; e += kQRThreads) {
+    const int j = e / m, k = e - j * m;
+    if (k >= j) R[e] = 0.0;
+  }
+  double c0, s0, c1, s1, c2, s2;
+  fmt_frame(a.lo0, a.side, 0, 0u, c0, s0);
+  fmt_frame(a.lo1, a.side, 0, 0u, c1, s1);
+  fmt_frame(a.lo2, a.side, 0, 0u, c2, s2);
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < a.n; b0 += NB) {
+    const int nb = (int)((a.n - b0) < NB ? (a.n - b0) : NB);
+    if (threadIdx.x < NB) {
+      double* row = Bs + threadIdx.x * a.ldB;
+      if ((int)threadIdx.x < nb) {
+        const int64_t i = b0 + threadIdx.x;
+        const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+        double pu[FMT_MAX_DEGREE + 1], pv[FMT_MAX_DEGREE + 1], pw[FMT_MAX_DEGREE + 1];
+        double tu = 1.0, tv = 1.0, tw = 1.0;
+        for (int l = 0; l <= q; ++l) {
+          const double f = c_invfact[l];
+          pu[l] = tu * f;
+          pv[l] = tv * f;
+          pw[l] = tw * f;
+          tu *= u;
+          tv *= v;
+          tw *= w;
+        }
+        int k = 0;
+        for (int l = 0; l <= q; ++l)
+          for (int mm = 0; mm <= q - l; ++mm) {
+            const double plm = pu[l] * pv[mm];
+            for (int n = 0; n <= q - l - mm; ++n) row[k++] = plm * pw[n];
+          }
+        row[k] = a.r_in[i];
+      } else {
+        for (int k = 0; k < m; ++k) row[k] = 0.0;
+      }
+    }
+    __syncthreads();
+    absorb_block<RPT, kQRThreads / 32>(Bs, a.ldB, 0, m, R, Rs, sc, -1);
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    const int ndrop = backsolve_warp(R, m, q, a.p, a.nmono_p, Bs, a.coef, G);
+    if (threadIdx.x == 0 && a.flags)
+      *a.flags = (ndrop > 0 ? FMT_FLAG_RANK : 0) | (q != a.p ? FMT_FLAG_DEG_CLAMPED : 0);
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < a.n; i += kQRThreads) {
+    const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+    a.r_out[i] = a.r_in[i] - fmt_horner_t<false>(G, a.p, a.nmono_p, u, v, w);  // G is in shared memory
+  }
+}
+
+std::mutex g_static_mu;
+double* g_static_addr[64];
+bool g_static_ready[64];
+
+}  // namespace
+
+extern "C" fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const double* x, const double* y,
+                                          const double* z, const double* r_in, const double* lo, double side,
+                                          double* coef, double* r_out, int32_t* flags, void* stream) {
+  char msg[200];
+  if (degree < 0 || degree > FMT_STATIC_MAX_DEGREE) {
+    snprintf(msg, sizeof(msg),
+             "fmt_fit_node_static: degree %d outside [0, %d] (its static triangle holds %d x %d doubles)",
+             degree, FMT_STATIC_MAX_DEGREE, FMT_STATIC_MAX_M, FMT_STATIC_MAX_M);
+    return fmt_set_error(FMT_EINVAL, msg);
+  }
+  if (n < 1 || n > (int64_t)0x7fffffff) return fmt_set_error(FMT_EINVAL, "fmt_fit_node_static: n outside [1, 2^31-1]");
+  if (!x || !y || !z || !r_in || !lo || !coef || !r_out)
+    return fmt_set_error(FMT_EINVAL, "fmt_fit_node_static: NULL pointer argument");
+  if (!(side > 0.0) || !isfinite(side) || !isfinite(lo[0]) || !isfinite(lo[1]) || !isfinite(lo[2]))
+    return fmt_set_error(FMT_EINVAL, "fmt_fit_node_static: the box needs finite lo and side > 0");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) return fmt_set_error(FMT_ECUDA, "fmt_fit_node_static: no current device");
+  double* R = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ready[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_static_tri);
+      if (e != cudaSuccess) {
+        snprintf(msg, sizeof(msg), "fmt_fit_node_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return fmt_set_error(FMT_ECUDA, msg);
+      }
+      g_static_addr[dev] = (double*)ptr;
+      g_static_ready[dev] = true;
+    }
+    R = g_static_addr[dev];
+  }
+  int q = degree;
+  if (n < fmt_nmono(degree)) {
+    q = -1;
+    while (fmt_nmono(q + 1) <= n) ++q;
+  }
+  StaticArgs a;
+  a.n = n;
+  a.x = x;
+  a.y = y;
+  a.z = z;
+  a.r_in = r_in;
+  a.r_out = r_out;
+  a.coef = coef;
+  a.flags = flags;
+  a.lo0 = lo[0];
+  a.lo1 = lo[1];
+  a.lo2 = lo[2];
+  a.side = side;
+  a.p = degree;
+  a.q = q;
+  a.m = fmt_nmono(q) + 1;
+  a.ldB = ld_for(a.m);
+  a.nmono_p = fmt_nmono(degree);
+  a.R = R;
+  const size_t smem = ((size_t)66 * a.ldB + 4 + a.nmono_p) * sizeof(double);
+  e = cudaFuncSetAttribute(k_fit_node_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    k_fit_node_static<<<1, kQRThreads, smem, (cudaStream_t)stream>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    snprintf(msg, sizeof(msg), "fmt_fit_node_static: launch failed: %s", cudaGetErrorString(e));
+    return fmt_set_error(FMT_ECUDA, msg);
+  }
+  return FMT_OK;
 }

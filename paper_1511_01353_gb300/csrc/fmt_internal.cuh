@@ -9,6 +9,7 @@
 #include "fmt.h"
 
 #define FMT_QBITS 21
+#define FMT_STATIC_MAX_M 166  // nmono(FMT_STATIC_MAX_DEGREE) + 1
 #define FMT_QMAX 0x1fffffu
 
 // device error word bits
@@ -69,20 +70,27 @@ __device__ __forceinline__ double fmt_local(double x, double c, double s) {
 // order (l outer, m, n inner, all ascending); reading it backwards visits
 // (l, m, n) in descending lexicographic order, which is exactly the nested
 // Horner order  sum_l u^l sum_m v^m sum_n w^n G_lmn.
-__device__ __forceinline__ double fmt_horner(const double* __restrict__ G, int p, int nmono, double u,
-                                             double v, double w) {
+// kGlobal: G is in global memory and read through the read-only path
+// (ld.global.nc, global addresses only); otherwise plain generic loads.
+template <bool kGlobal>
+__device__ __forceinline__ double fmt_horner_t(const double* __restrict__ G, int p, int nmono, double u,
+                                               double v, double w) {
   int idx = nmono - 1;
   double P = 0.0;
   for (int l = p; l >= 0; --l) {
     double t = 0.0;
     for (int m = p - l; m >= 0; --m) {
       double s = 0.0;
-      for (int n = p - l - m; n >= 0; --n) s = fma(s, w, __ldg(G + idx--));
+      for (int n = p - l - m; n >= 0; --n) s = fma(s, w, kGlobal ? __ldg(G + idx--) : G[idx--]);
       t = fma(t, v, s);
     }
     P = fma(P, u, t);
   }
   return P;
+}
+__device__ __forceinline__ double fmt_horner(const double* __restrict__ G, int p, int nmono, double u, double v,
+                                             double w) {
+  return fmt_horner_t<true>(G, p, nmono, u, v, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,6 +165,9 @@ struct fmt_tree {
   void** allocs = nullptr;
   int n_allocs = 0, cap_allocs = 0;
 };
+
+// Records msg as the calling thread's last error (fmt_last_error(NULL)).
+fmt_status fmt_set_error(fmt_status st, const char* msg);
 
 // ---------------------------------------------------------------------------
 // Launchers (return cudaGetLastError() of the launch).

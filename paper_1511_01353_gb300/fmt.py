@@ -62,7 +62,8 @@ class fmt_export_header(ctypes.Structure):
 
 EXPORTED = ["fmt_nmono", "oct_build", "fit_level", "refine", "evaluate", "fmt_tree_stats", "fmt_tree_export",
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
-            "fmt_profile_class_name", "fmt_probe_dfma"]
+            "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static"]
+STATIC_MAX_DEGREE = 8
 PROFILE_CLASSES = 16
 
 
@@ -115,6 +116,8 @@ def load(build: bool = True):
         L.fmt_profile_class_name.restype = ctypes.c_char_p
         L.fmt_probe_dfma.argtypes = [i64, ctypes.POINTER(ctypes.c_double), P]
         L.fmt_probe_dfma.restype = ctypes.c_int
+        L.fmt_fit_node_static.argtypes = [i32, i64, P, P, P, P, P, ctypes.c_double, P, P, P, P]
+        L.fmt_fit_node_static.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -251,6 +254,26 @@ def fmt_probe_dfma(iters: int = 20000, stream=None) -> float:
     v = ctypes.c_double(0.0)
     _check(load().fmt_probe_dfma(iters, ctypes.byref(v), _stream_handle(stream)))
     return float(v.value)
+
+
+def fmt_fit_node_static(degree: int, x, y, z, r_in, coef, r_out, flags=None, lo=(0.0, 0.0, 0.0), side=1.0,
+                        stream=None):
+    """Allocation-free fit of one point set in the root frame of [lo, lo+side)^3.
+
+    All buffers are caller-owned CUDA tensors: coef (nmono(degree) float64)
+    and r_out (n float64) are written; flags, if given, is a 1-element int32
+    CUDA tensor.  The library allocates nothing for this call."""
+    import torch
+    lo_a = (ctypes.c_double * 3)(*lo)
+    fp = None
+    if flags is not None:
+        if not (isinstance(flags, torch.Tensor) and flags.is_cuda and flags.dtype == torch.int32):
+            raise TypeError("flags must be an int32 CUDA tensor")
+        fp = ctypes.c_void_p(flags.data_ptr())
+    st = load().fmt_fit_node_static(degree, int(x.numel()), _dptr(x, "x"), _dptr(y, "y"), _dptr(z, "z"),
+                                    _dptr(r_in, "r_in"), ctypes.cast(lo_a, ctypes.c_void_p), side,
+                                    _dptr(coef, "coef"), _dptr(r_out, "r_out"), fp, _stream_handle(stream))
+    _check(st)
 
 
 def fmt_profile_class_name(k: int):
