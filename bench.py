@@ -246,6 +246,24 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     torch.cuda.synchronize()
 
+    level_events = []
+
+    def fit_with_level_events(lv):
+        # the driver loop of F.fit, with events around every fit_level
+        tree = F.oct_build(params, x, y, z, f, stream)
+        d = 0
+        while True:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            F.fit_level(tree, d, stream)
+            b.record(stream)
+            lv.append((d, a, b))
+            if F.refine(tree, d, stream) == 0:
+                break
+            d += 1
+        return tree
+
     def step(timed):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
@@ -253,7 +271,7 @@ def main():
             e1 = torch.cuda.Event(enable_timing=True)
             e2 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            tree = F.fit(params, x, y, z, f, stream)
+            tree = fit_with_level_events(level_events if timed else [])
             e1.record(stream)
             F.evaluate(tree, xq, yq, zq, out, stream=stream)
             e2.record(stream)
@@ -296,6 +314,10 @@ def main():
     for t in trees[:-1]:
         t.close()
 
+    lvl_ms = {}
+    for d, a, b in level_events:
+        lvl_ms.setdefault(d, []).append(a.elapsed_time(b))
+    level_fit_ms = [sum(lvl_ms[d]) / len(lvl_ms[d]) for d in sorted(lvl_ms)]
     fit_s = sum(fit_ms) / len(fit_ms) / 1e3
     eval_s = sum(eval_ms) / len(eval_ms) / 1e3
     if dist:
@@ -391,7 +413,9 @@ def main():
                           "frac": (ev_tflops / FP64_NOMINAL_TFLOPS if ev_tflops else None),
                           "flops_per_target_level": hf},
         "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clocks,
-        "tree": {"nodes": nodes, "points": points, "near_tau": int(sum(stats.near_tau[d] for d in range(22))),
+        "tree": {"nodes": nodes, "points": points, "level_fit_ms": level_fit_ms,
+                 "level_items": [int(stats.items[d]) for d in range(stats.n_levels)],
+                 "level_chunk_rows": [int(stats.chunk_rows[d]) for d in range(stats.n_levels)], "near_tau": int(sum(stats.near_tau[d] for d in range(22))),
                  "rank_flagged": int(sum(stats.rank_flagged[d] for d in range(22)))},
         "accuracy": {"E_rms": erms, "E_inf": einf, "vs": "closed-form Franke at the targets"},
         "e2e": e2e, "cpu_baseline": cpu,

@@ -35,6 +35,7 @@
 namespace {
 
 constexpr int kQRThreads = 128;
+int ld_for(int m);
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -125,26 +126,39 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
   for (int k = j_begin + tid; k < m; k += NT) Rs[(j_begin & 1) * ldB + k] = R[(size_t)j_begin * m + k];
   __syncthreads();
   if (warp == 0) reflector(B, ldB, NB, j_begin, Rs + (j_begin & 1) * ldB, R, m, sc + (j_begin & 1) * 2);
+  static_assert((NW & (NW - 1)) == 0, "warp count must be a power of two");
+  // The look-ahead warp of step j is lw(j) = (j + blockIdx.x) mod NW.  Row j+1
+  // is prefetched and stashed with the thread index rotated so that lane 0 of
+  // lw(j) holds its first element R_{j+1,j+1}: the look-ahead then reads it
+  // after a __syncwarp, without a block barrier.
+  auto rot = [&](int jj) { return (tid - 32 * ((jj + (int)blockIdx.x) & (NW - 1))) & (NT - 1); };
   double pf[kPF];
+  {
+    const int rt = rot(j_begin);
 #pragma unroll
-  for (int e = 0; e < kPF; ++e) {
-    const int k = j_begin + 1 + tid + NT * e;
-    pf[e] = (k < m) ? R[(size_t)(j_begin + 1) * m + k] : 0.0;
+    for (int e = 0; e < kPF; ++e) {
+      const int k = j_begin + 1 + rt + NT * e;
+      pf[e] = (k < m) ? R[(size_t)(j_begin + 1) * m + k] : 0.0;
+    }
   }
   __syncthreads();
   for (int j = j_begin; j < m; ++j) {
     const int cur = j & 1, nxt = cur ^ 1;
     double* Rc = Rs + cur * ldB;
     double* Rn = Rs + nxt * ldB;
+    {
+      const int rs = rot(j);  // row j+1 was fetched with this mapping
 #pragma unroll
-    for (int e = 0; e < kPF; ++e) {
-      const int k = j + 1 + tid + NT * e;
-      if (k < m) Rn[k] = pf[e];
-    }
+      for (int e = 0; e < kPF; ++e) {
+        const int k = j + 1 + rs + NT * e;
+        if (k < m) Rn[k] = pf[e];
+      }
+      const int rp = rot(j + 1);  // row j+2 is stashed at step j+1
 #pragma unroll
-    for (int e = 0; e < kPF; ++e) {
-      const int k = j + 2 + tid + NT * e;
-      pf[e] = (k < m) ? R[(size_t)(j + 2) * m + k] : 0.0;
+      for (int e = 0; e < kPF; ++e) {
+        const int k = j + 2 + rp + NT * e;
+        pf[e] = (k < m) ? R[(size_t)(j + 2) * m + k] : 0.0;
+      }
     }
     // groups of four rows that can hold nonzeros at this step (warp uniform)
     const int tmax = tri_row0 < 0 ? RPT : min(RPT, max(0, (j - tri_row0) / 4 + 1));
@@ -155,20 +169,35 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
 #pragma unroll
       for (int t = 0; t < RPT; ++t) xr[t] = (t < tmax) ? B[(rg + 4 * t) * ldB + j] : 0.0;
     }
-    int k0 = j + 1 + 8 * warp;  // warp w covers columns j+1+8w .. j+8+8w of each round
-    bool lookahead = (warp == 0) && (j + 1 < m);
+    // The warp roles rotate with the step (and differ between CTAs): the warp
+    // with slot 0 takes columns j+1..j+8 of each round and the look-ahead, so
+    // the extra work does not always land on the same SM sub-partition.
+    const int slot = (warp - j - (int)blockIdx.x) & (NW - 1);
+    int k0 = j + 1 + 8 * slot;  // columns j+1+8*slot .. j+8+8*slot of each round
+    bool lookahead = (slot == 0) && (j + 1 < m);
     for (;;) {
       if (upd && k0 < m) {
         const int k = k0 + (lane >> 2);
         const bool act = k < m;
         const int kk = act ? k : j;
-        double a0 = 0.0, a1 = 0.0;
+        double acc;
+        if (NW <= 4) {
+          // pipe-bound (several rounds per step): one chain, since the DFMA
+          // latency is below the FP64 issue interval and the join add is saved
+          acc = 0.0;
 #pragma unroll
-        for (int t = 0; t < RPT; t += 2) {
-          if (t < tmax) a0 = fma(xr[t], B[(rg + 4 * t) * ldB + kk], a0);
-          if (t + 1 < tmax) a1 = fma(xr[t + 1], B[(rg + 4 * t + 4) * ldB + kk], a1);
+          for (int t = 0; t < RPT; ++t)
+            if (t < tmax) acc = fma(xr[t], B[(rg + 4 * t) * ldB + kk], acc);
+        } else {
+          // latency-bound (about one round per step): two chains
+          double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+          for (int t = 0; t < RPT; t += 2) {
+            if (t < tmax) a0 = fma(xr[t], B[(rg + 4 * t) * ldB + kk], a0);
+            if (t + 1 < tmax) a1 = fma(xr[t + 1], B[(rg + 4 * t + 4) * ldB + kk], a1);
+          }
+          acc = a0 + a1;
         }
-        double acc = a0 + a1;
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (act) {
@@ -296,6 +325,140 @@ __global__ void __launch_bounds__(32 * kCombineWarps) k_combine(QRArgs a, int le
     __syncthreads();
     absorb_block<RPT, kCombineWarps>(Bs, a.ldB, r0, m, Ra, Rs, sc, r0);
   }
+}
+
+// Pairwise merge with the whole second triangle in shared memory (packed upper
+// triangle, m(m+1)/2 doubles): one pass of m Householder steps.  Step j
+// reflects row j of R_a with rows 0..j of R_b (rows below j are still zero in
+// column j); columns k > j are updated by quads whose four lanes split the
+// rows 0..j.  R_a's rows are streamed through shared memory with a one-step
+// prefetch, and the warp holding column j+1 computes the next reflector
+// (look-ahead), as in absorb_block.  Used when the packed triangle fits.
+constexpr int kMergeWarps = 8;
+constexpr int kMergeThreads = 32 * kMergeWarps;
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
+  extern __shared__ double smem[];
+  const int m = a.m;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, rg = tid & 3;
+  const int item = blockIdx.x;
+  const int sidx = a.item_local[item];
+  const int cnt = a.node_nitems[a.item_node[item]];
+  const int step = 1 << level;
+  if ((sidx & (2 * step - 1)) != 0 || sidx + step >= cnt) return;
+  double* Ra = a.R + (size_t)item * m * m;
+  const double* Rb = a.R + (size_t)(item + step) * m * m;
+  const int ldR = a.ldB;
+  double* Bp = smem;                                   // packed R_b
+  double* Rs = Bp + ((m * (m + 1) / 2 + 1) & ~1);      // two rows of R_a
+  double* sc = Rs + 2 * ldR;                           // reflector scalars of two steps
+  int* offr = (int*)(sc + 4);                          // row i of R_b starts at Bp[offr[i] + i]
+  for (int i = tid; i < m; i += kMergeThreads) offr[i] = i * m - i * (i - 1) / 2 - i;
+  __syncthreads();
+  for (int i = warp; i < m; i += kMergeWarps)
+    for (int k = i + lane; k < m; k += 32) Bp[offr[i] + k] = Rb[(size_t)i * m + k];
+  for (int k = tid; k < m; k += kMergeThreads) Rs[k] = Ra[k];  // row 0 of R_a
+  __syncthreads();
+
+  auto reflect = [&](int j, double* Rrow, double* scj) {  // one warp
+    double sq = 0.0;
+    for (int i = lane; i <= j; i += 32) {
+      const double v = Bp[offr[i] + j];
+      sq = fma(v, v, sq);
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) {
+      const double alpha = Rrow[j];
+      if (sq == 0.0) {
+        scj[0] = 0.0;
+        scj[1] = 0.0;
+      } else {
+        const double h = sqrt(fma(alpha, alpha, sq));
+        const double beta = alpha >= 0.0 ? -h : h;
+        scj[0] = 1.0 / (h * (h + fabs(alpha)));
+        scj[1] = alpha - beta;
+        Rrow[j] = beta;
+        Ra[(size_t)j * m + j] = beta;
+      }
+    }
+  };
+  auto rot = [&](int jj) { return (tid - 32 * ((jj + (int)blockIdx.x) & (kMergeWarps - 1))) & (kMergeThreads - 1); };
+  constexpr int kPF = (680 + kMergeThreads - 1) / kMergeThreads;
+  if (warp == 0) reflect(0, Rs, sc);
+  double pf[kPF];
+  {
+    const int rt = rot(0);
+#pragma unroll
+    for (int e = 0; e < kPF; ++e) {
+      const int k = 1 + rt + kMergeThreads * e;
+      pf[e] = (k < m) ? Ra[(size_t)1 * m + k] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    const int cur = j & 1, nxt = cur ^ 1;
+    double* Rc = Rs + cur * ldR;
+    double* Rn = Rs + nxt * ldR;
+    {
+      const int rs = rot(j);
+#pragma unroll
+      for (int e = 0; e < kPF; ++e) {
+        const int k = j + 1 + rs + kMergeThreads * e;
+        if (k < m) Rn[k] = pf[e];
+      }
+      const int rp = rot(j + 1);
+#pragma unroll
+      for (int e = 0; e < kPF; ++e) {
+        const int k = j + 2 + rp + kMergeThreads * e;
+        pf[e] = (k < m) ? Ra[(size_t)(j + 2) * m + k] : 0.0;
+      }
+    }
+    const double gamma = sc[cur * 2], amb = sc[cur * 2 + 1];
+    const bool upd = gamma != 0.0;
+    const int slot = (warp - j - (int)blockIdx.x) & (kMergeWarps - 1);
+    int k0 = j + 1 + 8 * slot;
+    bool lookahead = (slot == 0) && (j + 1 < m);
+    for (;;) {
+      if (upd && k0 < m) {
+        const int k = k0 + (lane >> 2);
+        const bool act = k < m;
+        const int kk = act ? k : j;
+        double a0 = 0.0, a1 = 0.0;
+        int i = rg;
+        for (; i + 4 <= j; i += 8) {
+          a0 = fma(Bp[offr[i] + j], Bp[offr[i] + kk], a0);
+          a1 = fma(Bp[offr[i + 4] + j], Bp[offr[i + 4] + kk], a1);
+        }
+        if (i <= j) a0 = fma(Bp[offr[i] + j], Bp[offr[i] + kk], a0);
+        double acc = a0 + a1;
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (act) {
+          const double rv = Rc[k];
+          const double d = gamma * fma(amb, rv, acc);
+          for (int i2 = rg; i2 <= j; i2 += 4) {
+            double* bp = Bp + offr[i2] + k;
+            *bp = fma(-d, Bp[offr[i2] + j], *bp);
+          }
+          if (rg == 0) Ra[(size_t)j * m + k] = fma(-d, amb, rv);
+        }
+        k0 += 8 * kMergeWarps;
+      }
+      if (lookahead) {
+        __syncwarp();
+        reflect(j + 1, Rn, sc + nxt * 2);
+        lookahead = false;
+        continue;
+      }
+      if (!upd || k0 >= m) break;
+    }
+    __syncthreads();
+  }
+}
+
+size_t merge_smem_bytes(int m) {
+  return ((size_t)((m * (m + 1) / 2 + 1) & ~1) + 2 * (size_t)ld_for(m) + 4) * sizeof(double) +
+         (size_t)m * sizeof(int);
 }
 
 // ---------------------------------------------------------------- back solve
@@ -660,9 +823,17 @@ cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double*
   QRArgs a = make_qr_args(t, depth, R);
   const int64_t n_items = t->lv[depth].n_items;
   if (n_items <= 1) return cudaSuccess;
+  cudaError_t e;
+  const size_t msm = merge_smem_bytes(a.m);
+  if (msm <= 200 * 1024) {
+    if ((e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm)) != cudaSuccess)
+      return e;
+    k_merge<<<(unsigned)n_items, kMergeThreads, msm, s>>>(a, tree_level);
+    return cudaGetLastError();
+  }
+  // large degrees: the packed triangle does not fit; merge in row blocks
   const int rows = qr_rows_per_block(a.m);
   const size_t smem = qr_smem_bytes(a.m, rows);
-  cudaError_t e;
   switch (rows) {
     case 64:
       if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;

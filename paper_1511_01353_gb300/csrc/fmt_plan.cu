@@ -68,10 +68,45 @@ struct PlanArgs {
 __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
   int64_t C = a.chunk_fixed;
   if (C <= 0) {
-    // nsm carries the number of resident QR CTAs (SMs x CTAs per SM)
-    int64_t per = (a.total_points + a.nsm - 1) / a.nsm;
-    per = (per + 63) / 64 * 64;
-    C = per > a.chunk_floor ? per : a.chunk_floor;
+    // nsm carries the number of resident QR CTAs.  Candidates C_k = rows /
+    // (k * slots) (multiple of 64, at least chunk_floor); the estimated time of
+    // a candidate is (waves of items) x C_k plus its merges (a merge of two
+    // triangles costs about m/3 rows of QR work, m ~ chunk_floor / 4), spread
+    // over the slots.  Equal items that fill one wave (a single big node) keep
+    // k = 1; many unequal nodes move to smaller chunks and several waves.
+    __shared__ int64_t cand_items[8];
+    const int ks[6] = {1, 2, 3, 4, 6, 8};
+    int64_t Cs[6];
+    for (int c = 0; c < 6; ++c) {
+      int64_t per = (a.total_points + (int64_t)ks[c] * a.nsm - 1) / ((int64_t)ks[c] * a.nsm);
+      per = (per + 63) / 64 * 64;
+      Cs[c] = per > a.chunk_floor ? per : a.chunk_floor;
+    }
+    if (threadIdx.x < 8) cand_items[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t loc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t node = threadIdx.x; node < a.n_nodes; node += blockDim.x) {
+      const int64_t cnt = a.count[node];
+      for (int c = 0; c < 6; ++c) {
+        const int64_t nch = (cnt + Cs[c] - 1) / Cs[c];
+        loc[c] += nch < 1 ? 1 : nch;
+      }
+    }
+    for (int c = 0; c < 6; ++c) atomicAdd((unsigned long long*)&cand_items[c], (unsigned long long)loc[c]);
+    __syncthreads();
+    double best = 0.0;
+    C = Cs[0];
+    for (int c = 0; c < 6; ++c) {
+      const int64_t ni = cand_items[c];
+      const double waves = (double)((ni + a.nsm - 1) / a.nsm);
+      const double merges = (double)(ni - a.n_nodes) * ((double)a.chunk_floor / 12.0) / (double)a.nsm;
+      const double cost = waves * (double)Cs[c] + merges;
+      if (c == 0 || cost < best) {
+        best = cost;
+        C = Cs[c];
+      }
+    }
+    __syncthreads();
   }
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
