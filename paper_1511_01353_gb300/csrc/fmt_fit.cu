@@ -327,14 +327,17 @@ __global__ void __launch_bounds__(32 * kCombineWarps) k_combine(QRArgs a, int le
   }
 }
 
-// Pairwise merge with the whole second triangle in shared memory (packed upper
-// triangle, m(m+1)/2 doubles): one pass of m Householder steps.  Step j
-// reflects row j of R_a with rows 0..j of R_b (rows below j are still zero in
-// column j); columns k > j are updated by quads whose four lanes split the
-// rows 0..j.  R_a's rows are streamed through shared memory with a one-step
-// prefetch, and the warp holding column j+1 computes the next reflector
-// (look-ahead), as in absorb_block.  Used when the packed triangle fits.
-constexpr int kMergeWarps = 8;
+// Pairwise merge with the whole second triangle in shared memory, stored
+// column by column (column k of the upper triangle, rows 0..k, starts at
+// k(k+1)/2), so that the rows of a column are contiguous: one pass of m
+// Householder steps.  Step j reflects row j of R_a with rows 0..j of R_b
+// (rows below j are still zero in column j); columns k > j are updated by
+// quads whose four lanes split the rows 0..j.  R_a's rows are streamed
+// through shared memory with a one-step prefetch, and the warp holding column
+// j+1 computes the next reflector (look-ahead), as in absorb_block.  Used
+// when the packed triangle fits in shared memory (m <= 166 with two CTAs per
+// SM); the merge is latency-bound, so it runs 16 warps.
+constexpr int kMergeWarps = 16;
 constexpr int kMergeThreads = 32 * kMergeWarps;
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
@@ -349,23 +352,20 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
   double* Ra = a.R + (size_t)item * m * m;
   const double* Rb = a.R + (size_t)(item + step) * m * m;
   const int ldR = a.ldB;
-  double* Bp = smem;                                   // packed R_b
+  double* Bp = smem;                                   // R_b, packed by columns
   double* Rs = Bp + ((m * (m + 1) / 2 + 1) & ~1);      // two rows of R_a
   double* sc = Rs + 2 * ldR;                           // reflector scalars of two steps
-  int* offr = (int*)(sc + 4);                          // row i of R_b starts at Bp[offr[i] + i]
-  for (int i = tid; i < m; i += kMergeThreads) offr[i] = i * m - i * (i - 1) / 2 - i;
-  __syncthreads();
-  for (int i = warp; i < m; i += kMergeWarps)
-    for (int k = i + lane; k < m; k += 32) Bp[offr[i] + k] = Rb[(size_t)i * m + k];
+  for (int k = warp; k < m; k += kMergeWarps) {
+    const int cb = k * (k + 1) / 2;
+    for (int i = lane; i <= k; i += 32) Bp[cb + i] = Rb[(size_t)i * m + k];
+  }
   for (int k = tid; k < m; k += kMergeThreads) Rs[k] = Ra[k];  // row 0 of R_a
   __syncthreads();
 
   auto reflect = [&](int j, double* Rrow, double* scj) {  // one warp
+    const double* col = Bp + j * (j + 1) / 2;
     double sq = 0.0;
-    for (int i = lane; i <= j; i += 32) {
-      const double v = Bp[offr[i] + j];
-      sq = fma(v, v, sq);
-    }
+    for (int i = lane; i <= j; i += 32) sq = fma(col[i], col[i], sq);
     sq = warp_sum(sq);
     if (lane == 0) {
       const double alpha = Rrow[j];
@@ -415,6 +415,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
     }
     const double gamma = sc[cur * 2], amb = sc[cur * 2 + 1];
     const bool upd = gamma != 0.0;
+    const double* xj = Bp + j * (j + 1) / 2;  // column j, rows 0..j
     const int slot = (warp - j - (int)blockIdx.x) & (kMergeWarps - 1);
     int k0 = j + 1 + 8 * slot;
     bool lookahead = (slot == 0) && (j + 1 < m);
@@ -422,24 +423,34 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
       if (upd && k0 < m) {
         const int k = k0 + (lane >> 2);
         const bool act = k < m;
-        const int kk = act ? k : j;
-        double a0 = 0.0, a1 = 0.0;
+        double* ck = Bp + (act ? k * (k + 1) / 2 : j * (j + 1) / 2);  // column k (column j when idle)
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         int i = rg;
-        for (; i + 4 <= j; i += 8) {
-          a0 = fma(Bp[offr[i] + j], Bp[offr[i] + kk], a0);
-          a1 = fma(Bp[offr[i + 4] + j], Bp[offr[i + 4] + kk], a1);
+        for (; i + 12 <= j; i += 16) {
+          a0 = fma(xj[i], ck[i], a0);
+          a1 = fma(xj[i + 4], ck[i + 4], a1);
+          a2 = fma(xj[i + 8], ck[i + 8], a2);
+          a3 = fma(xj[i + 12], ck[i + 12], a3);
         }
-        if (i <= j) a0 = fma(Bp[offr[i] + j], Bp[offr[i] + kk], a0);
-        double acc = a0 + a1;
+        for (; i <= j; i += 4) a0 = fma(xj[i], ck[i], a0);
+        double acc = (a0 + a1) + (a2 + a3);
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (act) {
           const double rv = Rc[k];
           const double d = gamma * fma(amb, rv, acc);
-          for (int i2 = rg; i2 <= j; i2 += 4) {
-            double* bp = Bp + offr[i2] + k;
-            *bp = fma(-d, Bp[offr[i2] + j], *bp);
+          int i2 = rg;
+          for (; i2 + 12 <= j; i2 += 16) {
+            const double b0 = fma(-d, xj[i2], ck[i2]);
+            const double b1 = fma(-d, xj[i2 + 4], ck[i2 + 4]);
+            const double b2 = fma(-d, xj[i2 + 8], ck[i2 + 8]);
+            const double b3 = fma(-d, xj[i2 + 12], ck[i2 + 12]);
+            ck[i2] = b0;
+            ck[i2 + 4] = b1;
+            ck[i2 + 8] = b2;
+            ck[i2 + 12] = b3;
           }
+          for (; i2 <= j; i2 += 4) ck[i2] = fma(-d, xj[i2], ck[i2]);
           if (rg == 0) Ra[(size_t)j * m + k] = fma(-d, amb, rv);
         }
         k0 += 8 * kMergeWarps;
@@ -457,8 +468,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
 }
 
 size_t merge_smem_bytes(int m) {
-  return ((size_t)((m * (m + 1) / 2 + 1) & ~1) + 2 * (size_t)ld_for(m) + 4) * sizeof(double) +
-         (size_t)m * sizeof(int);
+  return ((size_t)((m * (m + 1) / 2 + 1) & ~1) + 2 * (size_t)ld_for(m) + 4) * sizeof(double);
 }
 
 // ---------------------------------------------------------------- back solve
