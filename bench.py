@@ -35,6 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "fitted pts/s & evals/s, mixed vs FP64 at stated err; p50/p99 req latency"
 UNIT = "fitted pts/s"
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
+# DRAM bytes (read + write) per row of k_tile_qr, from one ncu capture of the
+# current kernel on the 3e5-point recipe (profiles/tile_qr_3e5pts_p8.md):
+# 14.85 MB read + 80.61 MB written for 3e5 rows.  Scaled to a full launch by
+# its rows; set to None whenever the kernel changes until it is re-captured.
+TILE_QR_DRAM_BYTES_PER_ROW = (14.853376e6 + 80.612096e6) / 3.0e5
 
 
 def parse_args():
@@ -400,7 +405,11 @@ def main():
         "evals_per_s": world * w.m / eval_s, "fit_ms": fit_s * 1e3, "eval_ms": eval_s * 1e3,
         "roofline": {"bound": "alu", "kernel": "tile_qr", "achieved": qr_tflops, "peak": FP64_NOMINAL_TFLOPS,
                      "unit": "TFLOP/s", "frac": (qr_tflops / FP64_NOMINAL_TFLOPS if qr_tflops else None),
-                     "traffic": None,
+                     "traffic": (TILE_QR_DRAM_BYTES_PER_ROW * qr["units"] / qr["launches"]
+                                 if TILE_QR_DRAM_BYTES_PER_ROW and qr.get("launches") else None),
+                     "traffic_unit": "bytes per launch (ncu dram read+write, scaled per row from a "
+                                     "3e5-point capture)",
+                     "algorithmic_bytes": 32.0 * qr["units"] / qr["launches"] if qr.get("launches") else None,
                      "peak_source": "GB300 nominal FP64 (non-tensor) 1.25 TFLOP/s",
                      "probe_fp64_tflops": probe_tflops,
                      "frac_of_probe": (qr_tflops / probe_tflops if qr_tflops else None),
