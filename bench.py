@@ -170,6 +170,22 @@ def levels_visited(ex, xq, yq, zq, lo, side):
     return total
 
 
+def reduce_max(values, dist=None, device="cpu"):
+    """Max over ranks of a list of floats (the slowest rank's times); the
+    identity when torch.distributed is not initialised or has one rank."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_throughput(world, units_per_rank, seconds_max):
+    """Whole-job rate: every rank processed units_per_rank in at most seconds_max."""
+    return world * units_per_rank / seconds_max
+
+
 def run_reference(args, rank, world):
     """The FP64 CPU oracle as it stands, timed on this host's cores."""
     if rank != 0:
@@ -325,10 +341,7 @@ def main():
     level_fit_ms = [sum(lvl_ms[d]) / len(lvl_ms[d]) for d in sorted(lvl_ms)]
     fit_s = sum(fit_ms) / len(fit_ms) / 1e3
     eval_s = sum(eval_ms) / len(eval_ms) / 1e3
-    if dist:
-        tt = torch.tensor([fit_s, eval_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        fit_s, eval_s = float(tt[0]), float(tt[1])
+    fit_s, eval_s = reduce_max([fit_s, eval_s], dist, device="cuda")
 
     # accuracy of the interpolant against the closed form (last timed step)
     pred = out.cpu().numpy()
@@ -394,7 +407,7 @@ def main():
     nodes = [int(stats.nodes[d]) for d in range(stats.n_levels)]
     points = [int(stats.points[d]) for d in range(stats.n_levels)]
     line = {
-        "metric": METRIC, "value": world * w.n / fit_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": job_throughput(world, w.n, fit_s), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (fit_s + eval_s) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "points": w.n, "targets": w.m, "degree": w.degree,
@@ -402,7 +415,7 @@ def main():
                    "tol_rel": w.tol_rel, "values": "3-D Franke (benchmark form)",
                    "l2": "flushed before every step (256 MB write)", "parallelism": "replicas",
                    "gpu": gpu_name},
-        "evals_per_s": world * w.m / eval_s, "fit_ms": fit_s * 1e3, "eval_ms": eval_s * 1e3,
+        "evals_per_s": job_throughput(world, w.m, eval_s), "fit_ms": fit_s * 1e3, "eval_ms": eval_s * 1e3,
         "roofline": {"bound": "alu", "kernel": "tile_qr", "achieved": qr_tflops, "peak": FP64_NOMINAL_TFLOPS,
                      "unit": "TFLOP/s", "frac": (qr_tflops / FP64_NOMINAL_TFLOPS if qr_tflops else None),
                      "traffic": (TILE_QR_DRAM_BYTES_PER_ROW * qr["units"] / qr["launches"]
