@@ -131,6 +131,27 @@ fmt_status fit_level(fmt_tree* tree, int32_t depth, void* stream);
 fmt_status refine(fmt_tree* tree, int32_t depth, int64_t* n_new_nodes, void* stream);
 
 /*
+ * oct_build_batch -- oct_build for a forest of independent problems, fitted
+ * together level by level (every fit_level / refine covers all problems).
+ *   params       host: max_depth, min_pts, tol_rel, precision, chunk_rows
+ *                are shared; degree and the box are the defaults.
+ *   n_problems   >= 1.
+ *   offsets      host, n_problems+1 values, offsets[0] = 0, strictly
+ *                increasing: problem i owns inputs offsets[i] .. offsets[i+1]-1.
+ *   degrees      host, n_problems values (0..14), or NULL for params->degree.
+ *   boxes        host, 4 values per problem (lo x, lo y, lo z, side), or NULL
+ *                for params->lo / params->side.
+ *   x,y,z,f      device, offsets[n_problems] doubles each, caller owned.
+ * tau is per problem: tol_rel * max |f| over that problem's points.  The
+ * problem index sits above the Morton bits of the sort key and of the node
+ * keys, so ceil(log2(n_problems)) + 3 * (max_depth + 1) must not exceed 64
+ * (FMT_EINVAL otherwise).  Synchronises.
+ */
+fmt_status oct_build_batch(const fmt_params* params, int64_t n_problems, const int64_t* offsets,
+                           const int32_t* degrees, const double* boxes, const double* x, const double* y,
+                           const double* z, const double* f, void* stream, fmt_tree** out);
+
+/*
  * evaluate -- the tree interpolant at m targets: for each target, the sum
  * over depth d = 0, 1, ... of Lambda(u_d) . F_d for the node at depth d that
  * contains it (same quantisation as oct_build), stopping at the first depth
@@ -145,11 +166,20 @@ fmt_status refine(fmt_tree* tree, int32_t depth, int64_t* n_new_nodes, void* str
 fmt_status evaluate(fmt_tree* tree, int64_t m, const double* xq, const double* yq, const double* zq,
                     double* out, int64_t* n_outside, void* stream);
 
+/*
+ * evaluate_batch -- evaluate for a forest: target i is evaluated in the tree
+ * of problem target_problem[i] (device, m int32 values in [0, n_problems);
+ * may be NULL for a single-problem tree).  An index out of range is reported
+ * as FMT_EINVAL when n_outside is given (the call then synchronises).
+ */
+fmt_status evaluate_batch(fmt_tree* tree, int64_t m, const int32_t* target_problem, const double* xq,
+                          const double* yq, const double* zq, double* out, int64_t* n_outside, void* stream);
+
 /* Per-level counters.  Synchronises. */
 typedef struct {
   int32_t degree, nmono, max_depth, n_levels; /* n_levels = levels with nodes */
   int32_t n_fitted;                           /* levels whose fit is done */
-  int32_t pad_;
+  int32_t n_problems;
   int64_t n_points;
   double tau, maxabs_f;
   int64_t nodes[FMT_MAX_DEPTH + 1];
@@ -162,26 +192,33 @@ typedef struct {
 fmt_status fmt_tree_stats(fmt_tree* tree, fmt_stats* out);
 
 /*
- * Serialised tree ("FMT1" blob, little endian, every array 8-byte aligned).
- * Layout: fmt_export_header, then for the n_nodes nodes (level by level,
- * Morton order inside a level):
- *   uint64 prefix[n]     Morton prefix of the node (code >> 3*(21-depth))
+ * Serialised tree ("FMT2" blob, little endian, every array 8-byte aligned).
+ * Layout: fmt_export_header, then for the n_nodes nodes (level by level, in
+ * node-key order inside a level; a node key is problem << 3*depth | Morton
+ * prefix, the prefix being code >> 3*(21-depth)):
+ *   uint64 key[n]
  *   int64  start[n]      first point (sorted order)
  *   int64  count[n]      number of points
- *   int32  depth[n], flags[n], deg_used[n], masks[n] (refine_mask | near_mask<<8)
+ *   int32  depth[n], flags[n], deg_used[n], masks[n] (refine_mask | near_mask<<8),
+ *          problem[n], pad[n]
  *   double child_E[8n]   RMS residual of each octant after the node's fit
  *   int64  child_n[8n]   points per octant
- *   double coef[nmono*n] F in Alg. 2 order (l outer, m, n inner)
+ *   double coef[nmono*n] F in Alg. 2 order (l outer, m, n inner); nmono of the
+ *                        largest degree, zeros past a node's own degree
+ * then the problem table (P = n_problems entries):
+ *   int32 degree[P], q_root[P] (root degree after the clamp);
+ *   double tau[P], maxabs_f[P], lo[3P], side[P]; int64 start[P], count[P]
  * and, when has_points = 1:
  *   uint64 code[N]       full Morton codes, sorted order
  *   int64  perm[N]       sorted position -> input index
  *   double resid[N]      current residual, INPUT order
+ * The header's tau, maxabs_f, lo and side are those of problem 0.
  */
 typedef struct {
-  uint32_t magic;   /* 0x31544d46, "FMT1" */
-  uint32_t version; /* 1 */
-  int32_t degree, nmono, max_depth, min_pts;
-  int32_t n_levels, n_fitted, has_points, pad_;
+  uint32_t magic;   /* 0x32544d46, "FMT2" */
+  uint32_t version; /* 2 */
+  int32_t degree, nmono, max_depth, min_pts; /* degree/nmono: the largest */
+  int32_t n_levels, n_fitted, has_points, n_problems;
   double tol_rel, tau, maxabs_f, lo[3], side;
   int64_t n_points, n_nodes;
   int64_t level_nodes[FMT_MAX_DEPTH + 1];

@@ -118,11 +118,6 @@ struct ProfScope {
   }
 };
 
-double horner_flops(int p) {
-  // nmono FMAs for the coefficients, one per (l, m) pair, one per l
-  return 2.0 * ((double)fmt_nmono(p) + (p + 1) * (p + 2) / 2.0 + (p + 1));
-}
-
 template <typename T>
 fmt_status talloc(fmt_tree* t, T** p, int64_t count, cudaStream_t s) {
   size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
@@ -170,7 +165,12 @@ void tfree_one(fmt_tree* t, void* ptr, cudaStream_t s) {
   } while (0)
 
 int64_t nmin_of(const fmt_tree* t) {
-  int64_t v = t->P.min_pts > t->nmono ? t->P.min_pts : t->nmono;
+  // the smallest child any problem of the forest can create
+  int64_t v = t->P.min_pts > fmt_nmono(0) ? t->P.min_pts : 1;
+  int32_t dmin = t->max_degree;
+  for (int64_t i = 0; i < t->n_problems; ++i)
+    if (t->h_prob[i].degree < dmin) dmin = t->h_prob[i].degree;
+  if (fmt_nmono(dmin) > v) v = fmt_nmono(dmin);
   return v < 1 ? 1 : v;
 }
 
@@ -184,6 +184,7 @@ fmt_status alloc_level(fmt_tree* t, int d, int64_t cap_nodes, int64_t cap_items,
   L.cap_items = cap_items;
   const int64_t nm = t->nmono;
   TRY(talloc(t, &L.prefix, cap_nodes, s));
+  TRY(talloc(t, &L.prob, cap_nodes, s));
   TRY(talloc(t, &L.start, cap_nodes, s));
   TRY(talloc(t, &L.count, cap_nodes, s));
   TRY(talloc(t, &L.flags, cap_nodes, s));
@@ -202,6 +203,7 @@ fmt_status alloc_level(fmt_tree* t, int d, int64_t cap_nodes, int64_t cap_items,
   TRY(talloc(t, &L.item_end, cap_items, s));
   TRY(talloc(t, &L.item_local, cap_items, s));
   TRY(talloc(t, &L.sched, cap_items, s));
+  TRY(talloc(t, &L.item_roff, cap_items, s));
   CUDA_TRY(t, cudaMemsetAsync(L.masks, 0, sizeof(int32_t) * (size_t)cap_nodes, s), "memset");
   CUDA_TRY(t, cudaMemsetAsync(L.child_E, 0, sizeof(double) * 8 * (size_t)cap_nodes, s), "memset");
   return FMT_OK;
@@ -220,11 +222,9 @@ fmt_status check_tree(fmt_tree* t) {
 // read back the plan block and the device error word
 fmt_status read_plan(fmt_tree* t, cudaStream_t s) {
   CUDA_TRY(t, cudaMemcpyAsync(t->h_plan, t->d_plan, sizeof(fmt_plan_out), cudaMemcpyDeviceToHost, s), "plan copy");
-  int herr = 0;
-  CUDA_TRY(t, cudaMemcpyAsync(&t->h_plan->err, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "err copy");
+  CUDA_TRY(t, cudaMemcpyAsync(t->h_err, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "err copy");
   CUDA_TRY(t, cudaStreamSynchronize(s), "synchronise");
-  herr = (int)(t->h_plan->err & 0xffffffff);
-  t->h_plan->err = herr;
+  t->h_plan->err = *t->h_err;
   return FMT_OK;
 }
 
@@ -235,7 +235,257 @@ void destroy(fmt_tree* t) {
   cudaStreamSynchronize(0);
   free(t->allocs);
   if (t->h_plan) cudaFreeHost(t->h_plan);
+  if (t->h_err) cudaFreeHost(t->h_err);
+  free(t->h_prob);
   delete t;
+}
+
+int bits_for(int64_t v) {  // bits to hold the values 0 .. v-1
+  int b = 0;
+  while (b < 62 && (int64_t(1) << b) < v) ++b;
+  return b;
+}
+
+fmt_status validate_shared(const fmt_params& P) {
+  if (P.max_depth < 0 || P.max_depth > FMT_MAX_DEPTH)
+    return set_err(nullptr, FMT_EINVAL, "max_depth %d outside [0, %d]", P.max_depth, FMT_MAX_DEPTH);
+  if (P.min_pts < 0) return set_err(nullptr, FMT_EINVAL, "min_pts %d < 0", P.min_pts);
+  if (P.precision != FMT_FP64) return set_err(nullptr, FMT_EINVAL, "only FMT_FP64 is implemented");
+  if (!(P.tol_rel >= 0.0) || !isfinite(P.tol_rel)) return set_err(nullptr, FMT_EINVAL, "tol_rel must be finite, >= 0");
+  if (P.chunk_rows < 0) return set_err(nullptr, FMT_EINVAL, "chunk_rows < 0");
+  return FMT_OK;
+}
+
+fmt_status validate_box(double lo0, double lo1, double lo2, double side) {
+  if (!(side > 0.0) || !isfinite(side)) return set_err(nullptr, FMT_EINVAL, "side must be finite, > 0");
+  if (!isfinite(lo0) || !isfinite(lo1) || !isfinite(lo2)) return set_err(nullptr, FMT_EINVAL, "lo must be finite");
+  return FMT_OK;
+}
+
+// Stage a forest of n_problems independent problems (offsets[p] .. offsets[p+1]
+// of the inputs) and build its roots.
+fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offsets, const int32_t* degrees,
+                        const double* boxes, const double* x, const double* y, const double* z, const double* f,
+                        cudaStream_t s, fmt_tree** out) {
+  if (!out) return set_err(nullptr, FMT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!params) return set_err(nullptr, FMT_EINVAL, "params is NULL");
+  const fmt_params& PP = *params;
+  TRY(validate_shared(PP));
+  if (P < 1) return set_err(nullptr, FMT_EINVAL, "n_problems = %lld < 1", (long long)P);
+  if (!offsets || offsets[0] != 0) return set_err(nullptr, FMT_EINVAL, "offsets must start at 0");
+  for (int64_t i = 0; i < P; ++i)
+    if (offsets[i + 1] <= offsets[i])
+      return set_err(nullptr, FMT_EINVAL, "problem %lld has no point (offsets must increase)", (long long)i);
+  const int64_t n = offsets[P];
+  if (n > (int64_t)0xfffffffe) return set_err(nullptr, FMT_EINVAL, "n = %lld above 2^32-2 points", (long long)n);
+  if (!x || !y || !z || !f) return set_err(nullptr, FMT_EINVAL, "NULL input pointer");
+  int32_t maxdeg = -1;
+  for (int64_t i = 0; i < P; ++i) {
+    const int32_t p = degrees ? degrees[i] : PP.degree;
+    if (p < 0 || p > FMT_MAX_DEGREE)
+      return set_err(nullptr, FMT_EINVAL, "degree %d outside [0, %d]", p, FMT_MAX_DEGREE);
+    if (p > maxdeg) maxdeg = p;
+    const double* b = boxes ? boxes + 4 * i : nullptr;
+    TRY(validate_box(b ? b[0] : PP.lo[0], b ? b[1] : PP.lo[1], b ? b[2] : PP.lo[2], b ? b[3] : PP.side));
+  }
+  const int sort_levels = PP.max_depth + 1 < FMT_QBITS ? PP.max_depth + 1 : FMT_QBITS;
+  const int sort_bits = 3 * sort_levels;
+  const int pid_bits = P > 1 ? bits_for(P) : 0;
+  if (pid_bits + sort_bits > 64 || pid_bits + 3 * PP.max_depth > 63)
+    return set_err(nullptr, FMT_EINVAL, "%lld problems need %d key bits: lower max_depth (at most %d here)",
+                   (long long)P, pid_bits, (63 - pid_bits) / 3 - 1);
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
+  TRY(device_init(dev));
+
+  fmt_tree* t = new (std::nothrow) fmt_tree();
+  if (!t) return set_err(nullptr, FMT_ENOMEM, "host allocation failed");
+  auto fail = [&](fmt_status e) {
+    destroy(t);
+    return e;
+  };
+  t->P = PP;
+  if (t->P.chunk_rows > 0) t->P.chunk_rows = (t->P.chunk_rows + 63) / 64 * 64;
+  t->device = dev;
+  t->stream = s;
+  t->n = n;
+  t->n_problems = P;
+  t->max_degree = maxdeg;
+  t->nmono = fmt_nmono(maxdeg);
+  t->sort_bits = sort_bits;
+  t->pid_bits = pid_bits;
+  {
+    // A chunk of C rows costs about 2 m^2 C flops and one merge about (2/3) m^3,
+    // so C >= 4m keeps merges under ~10% of the chunk work; above that floor
+    // the planner sizes chunks to the rows per resident QR CTA, so that the
+    // largest item is no longer than the average share of a CTA.
+    int64_t fl = 4 * (int64_t)(t->nmono + 1);
+    t->chunk_floor = fl < 64 ? 64 : (fl + 63) / 64 * 64;
+  }
+  t->h_prob = (fmt_problem*)calloc((size_t)P, sizeof(fmt_problem));
+  if (!t->h_prob) {
+    set_err(nullptr, FMT_ENOMEM, "host allocation failed");
+    return fail(FMT_ENOMEM);
+  }
+  for (int64_t i = 0; i < P; ++i) {
+    fmt_problem& pr = t->h_prob[i];
+    const double* b = boxes ? boxes + 4 * i : nullptr;
+    pr.lo[0] = b ? b[0] : PP.lo[0];
+    pr.lo[1] = b ? b[1] : PP.lo[1];
+    pr.lo[2] = b ? b[2] : PP.lo[2];
+    pr.side = b ? b[3] : PP.side;
+    pr.S = 2097152.0 / pr.side;
+    pr.degree = degrees ? degrees[i] : PP.degree;
+    pr.start = offsets[i];
+    pr.count = offsets[i + 1] - offsets[i];
+    int32_t q = pr.degree;
+    if (pr.count < fmt_nmono(q)) {
+      q = -1;
+      while (fmt_nmono(q + 1) <= pr.count) ++q;
+    }
+    pr.q_root = q;
+  }
+  if (P == 1) {  // the single-problem parameters mirror problem 0
+    t->P.degree = t->h_prob[0].degree;
+    t->P.lo[0] = t->h_prob[0].lo[0];
+    t->P.lo[1] = t->h_prob[0].lo[1];
+    t->P.lo[2] = t->h_prob[0].lo[2];
+    t->P.side = t->h_prob[0].side;
+  }
+  const bool key64 = pid_bits + sort_bits > 32;
+  const int sort_shift = 3 * (FMT_QBITS - sort_levels);
+
+  fmt_status st = FMT_OK;
+  void *keys = nullptr, *keys_alt = nullptr, *temp = nullptr;
+  uint32_t *vals = nullptr, *vals_alt = nullptr;
+  unsigned long long* d_maxbits = nullptr;
+  const size_t ksz = key64 ? 8 : 4;
+  if ((st = talloc(t, &t->x, n, s)) || (st = talloc(t, &t->y, n, s)) || (st = talloc(t, &t->z, n, s)) ||
+      (st = talloc(t, &t->r, n, s)) || (st = talloc(t, &t->code, n, s)) ||
+      (st = talloc(t, (char**)&keys, (int64_t)ksz * n, s)) || (st = talloc(t, (char**)&keys_alt, (int64_t)ksz * n, s)) ||
+      (st = talloc(t, &vals, n, s)) || (st = talloc(t, &vals_alt, n, s)) ||
+      (st = talloc(t, (char**)&temp, (int64_t)radix_sort_temp_bytes(n, key64), s)) ||
+      (st = talloc(t, &t->d_err, 1, s)) || (st = talloc(t, &d_maxbits, P, s)) ||
+      (st = talloc(t, &t->d_plan, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)) ||
+      (st = talloc(t, &t->d_work, 1, s)) || (st = talloc(t, &t->d_prob, P, s)))
+    return fail(st);
+  if (cudaMallocHost((void**)&t->h_plan, sizeof(fmt_plan_out)) != cudaSuccess ||
+      cudaMallocHost((void**)&t->h_err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    set_err(nullptr, FMT_ENOMEM, "pinned host allocation failed");
+    return fail(FMT_ENOMEM);
+  }
+  // roots: one node per problem
+  const int64_t cap_items0 = n / min_chunk(t) + P + 2;
+  if ((st = alloc_level(t, 0, P, cap_items0, s))) return fail(st);
+
+  cudaError_t e = cudaSuccess;
+  void* kout = nullptr;
+  uint32_t* vout = nullptr;
+  do {
+    if ((e = cudaMemcpyAsync(t->d_prob, t->h_prob, sizeof(fmt_problem) * (size_t)P, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaMemsetAsync(t->d_err, 0, sizeof(int), s)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(d_maxbits, 0, sizeof(unsigned long long) * (size_t)P, s)) != cudaSuccess) break;
+    {
+      ProfScope ps(K_CHECK, s, 1, (double)n, 0.0);
+      if ((e = launch_check_maxabs(n, x, y, z, f, t->d_prob, (int)P, d_maxbits, t->d_err, s)) != cudaSuccess) break;
+    }
+    {
+      ProfScope ps(K_MORTON, s, 1, (double)n, 0.0);
+      e = launch_morton(n, x, y, z, t->d_prob, (int)P, sort_shift, sort_bits, key64, keys, vals, s);
+      if (e != cudaSuccess) break;
+    }
+    {
+      const int bits = pid_bits + sort_bits;
+      ProfScope ps(K_SORT, s, 4 * ((bits + 7) / 8), (double)n, 0.0);
+      e = launch_radix_sort(n, bits, key64, keys, vals, keys_alt, vals_alt, temp, &kout, &vout, s);
+      if (e != cudaSuccess) break;
+    }
+    t->perm = vout;
+    {
+      ProfScope ps(K_GATHER, s, 1, (double)n, 0.0);
+      e = launch_gather(n, t->perm, x, y, z, f, t->d_prob, (int)P, t->x, t->y, t->z, t->r, t->code, s);
+    }
+  } while (0);
+  if (e != cudaSuccess) {
+    set_err(nullptr, FMT_ECUDA, "oct_build launch: %s", cudaGetErrorString(e));
+    return fail(FMT_ECUDA);
+  }
+  // per-problem tau = tol_rel * max |f| (host), then the roots
+  unsigned long long* hbits = (unsigned long long*)malloc(sizeof(unsigned long long) * (size_t)P);
+  if (!hbits) {
+    set_err(nullptr, FMT_ENOMEM, "host allocation failed");
+    return fail(FMT_ENOMEM);
+  }
+  if ((e = cudaMemcpyAsync(hbits, d_maxbits, sizeof(unsigned long long) * (size_t)P, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(t->h_err, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    free(hbits);
+    set_err(nullptr, FMT_ECUDA, "copy: %s", cudaGetErrorString(e));
+    return fail(FMT_ECUDA);
+  }
+  if (*t->h_err & FMT_ERR_NONFINITE) {
+    free(hbits);
+    set_err(nullptr, FMT_EINVAL, "non-finite coordinate or value in the input");
+    return fail(FMT_EINVAL);
+  }
+  for (int64_t i = 0; i < P; ++i) {
+    double mx;
+    memcpy(&mx, &hbits[i], sizeof(mx));
+    t->h_prob[i].maxabs = mx;
+    t->h_prob[i].tau = PP.tol_rel * mx;
+  }
+  free(hbits);
+  t->maxabs = t->h_prob[0].maxabs;
+  t->tau = t->h_prob[0].tau;
+  if ((e = cudaMemcpyAsync(t->d_prob, t->h_prob, sizeof(fmt_problem) * (size_t)P, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess) {
+    set_err(nullptr, FMT_ECUDA, "copy: %s", cudaGetErrorString(e));
+    return fail(FMT_ECUDA);
+  }
+  {
+    ProfScope ps(K_PLAN, s, 1, (double)P, 0.0);
+    e = launch_plan_root(t, t->P.chunk_rows, t->chunk_floor, t->d_plan, s);
+  }
+  if (e != cudaSuccess) {
+    set_err(nullptr, FMT_ECUDA, "oct_build launch: %s", cudaGetErrorString(e));
+    return fail(FMT_ECUDA);
+  }
+  if (read_plan(t, s) != FMT_OK) {
+    set_err(nullptr, FMT_ECUDA, "%s", t->msg);
+    return fail(FMT_ECUDA);
+  }
+  const fmt_plan_out& pl = *t->h_plan;
+  if (pl.err) {
+    set_err(nullptr, FMT_EINTERNAL, "device check failed in oct_build (0x%llx)", (unsigned long long)pl.err);
+    return fail(FMT_EINTERNAL);
+  }
+  fmt_level& L0 = t->lv[0];
+  L0.n_nodes = P;
+  L0.n_items = pl.n_items;
+  L0.max_chunks = pl.max_chunks;
+  L0.chunk_rows = pl.chunk_rows;
+  L0.n_points = n;
+  L0.max_m = (int32_t)pl.max_m;
+  L0.r_total = pl.r_total;
+  L0.qr_flops = pl.qr_flops;
+  L0.horner_flops = pl.horner_flops;
+  t->n_levels = 1;
+  t->next_fit = 0;
+  t->next_refine = -1;
+  // the sort buffers are not needed any more (the permutation stays)
+  tfree_one(t, keys, s);
+  tfree_one(t, keys_alt, s);
+  tfree_one(t, temp, s);
+  tfree_one(t, vout == vals ? (void*)vals_alt : (void*)vals, s);
+  tfree_one(t, d_maxbits, s);
+  *out = t;
+  return FMT_OK;
 }
 
 }  // namespace
@@ -254,158 +504,18 @@ const char* fmt_last_error(const fmt_tree* tree) { return tree ? tree->msg : g_m
 
 fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const double* y, const double* z,
                      const double* f, void* stream, fmt_tree** out) {
-  if (!out) return set_err(nullptr, FMT_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!params) return set_err(nullptr, FMT_EINVAL, "params is NULL");
-  const fmt_params& P = *params;
-  if (P.degree < 0 || P.degree > FMT_MAX_DEGREE)
-    return set_err(nullptr, FMT_EINVAL, "degree %d outside [0, %d]", P.degree, FMT_MAX_DEGREE);
-  if (P.max_depth < 0 || P.max_depth > FMT_MAX_DEPTH)
-    return set_err(nullptr, FMT_EINVAL, "max_depth %d outside [0, %d]", P.max_depth, FMT_MAX_DEPTH);
-  if (P.min_pts < 0) return set_err(nullptr, FMT_EINVAL, "min_pts %d < 0", P.min_pts);
-  if (P.precision != FMT_FP64) return set_err(nullptr, FMT_EINVAL, "only FMT_FP64 is implemented");
-  if (!(P.tol_rel >= 0.0) || !isfinite(P.tol_rel)) return set_err(nullptr, FMT_EINVAL, "tol_rel must be finite, >= 0");
-  if (!(P.side > 0.0) || !isfinite(P.side)) return set_err(nullptr, FMT_EINVAL, "side must be finite, > 0");
-  for (int a = 0; a < 3; ++a)
-    if (!isfinite(P.lo[a])) return set_err(nullptr, FMT_EINVAL, "lo must be finite");
-  if (P.chunk_rows < 0) return set_err(nullptr, FMT_EINVAL, "chunk_rows < 0");
+  if (out) *out = nullptr;
+  if (params && (params->degree < 0 || params->degree > FMT_MAX_DEGREE))
+    return set_err(nullptr, FMT_EINVAL, "degree %d outside [0, %d]", params->degree, FMT_MAX_DEGREE);
   if (n < 1 || n > (int64_t)0xfffffffe) return set_err(nullptr, FMT_EINVAL, "n = %lld outside [1, 2^32-2]", (long long)n);
-  if (!x || !y || !z || !f) return set_err(nullptr, FMT_EINVAL, "NULL input pointer");
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
-  TRY(device_init(dev));
+  const int64_t offsets[2] = {0, n};
+  return build_forest(params, 1, offsets, nullptr, nullptr, x, y, z, f, (cudaStream_t)stream, out);
+}
 
-  cudaStream_t s = (cudaStream_t)stream;
-  fmt_tree* t = new (std::nothrow) fmt_tree();
-  if (!t) return set_err(nullptr, FMT_ENOMEM, "host allocation failed");
-  t->P = P;
-  if (t->P.chunk_rows > 0) t->P.chunk_rows = (t->P.chunk_rows + 63) / 64 * 64;
-  t->device = dev;
-  t->stream = s;
-  t->n = n;
-  t->nmono = fmt_nmono(P.degree);
-  t->S = 2097152.0 / P.side;
-  {
-    // A chunk of C rows costs about 2 m^2 C flops and one merge about (2/3) m^3,
-    // so C >= 4m keeps merges under ~10% of the chunk work; above that floor
-    // the planner sizes chunks to the rows per resident QR CTA, so that the
-    // largest item is no longer than the average share of a CTA.
-    int64_t fl = 4 * (int64_t)(t->nmono + 1);
-    t->chunk_floor = fl < 64 ? 64 : (fl + 63) / 64 * 64;
-  }
-  const int sort_levels = P.max_depth + 1 < FMT_QBITS ? P.max_depth + 1 : FMT_QBITS;
-  t->sort_bits = 3 * sort_levels;
-  const bool key64 = t->sort_bits > 32;
-  const int sort_shift = 3 * (FMT_QBITS - sort_levels);
-
-  fmt_status st = FMT_OK;
-  auto fail = [&](fmt_status e) {
-    destroy(t);
-    return e;
-  };
-  void *keys = nullptr, *keys_alt = nullptr, *temp = nullptr;
-  uint32_t *vals = nullptr, *vals_alt = nullptr;
-  unsigned long long* d_maxbits = nullptr;
-  const size_t ksz = key64 ? 8 : 4;
-  if ((st = talloc(t, &t->x, n, s)) || (st = talloc(t, &t->y, n, s)) || (st = talloc(t, &t->z, n, s)) ||
-      (st = talloc(t, &t->r, n, s)) || (st = talloc(t, &t->code, n, s)) ||
-      (st = talloc(t, (char**)&keys, (int64_t)ksz * n, s)) || (st = talloc(t, (char**)&keys_alt, (int64_t)ksz * n, s)) ||
-      (st = talloc(t, &vals, n, s)) || (st = talloc(t, &vals_alt, n, s)) ||
-      (st = talloc(t, (char**)&temp, (int64_t)radix_sort_temp_bytes(n, key64), s)) ||
-      (st = talloc(t, &t->d_err, 1, s)) || (st = talloc(t, &d_maxbits, 1, s)) ||
-      (st = talloc(t, &t->d_plan, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)) ||
-      (st = talloc(t, &t->d_work, 1, s)))
-    return fail(st);
-  if (cudaMallocHost((void**)&t->h_plan, sizeof(fmt_plan_out)) != cudaSuccess) {
-    cudaGetLastError();
-    set_err(nullptr, FMT_ENOMEM, "pinned host allocation failed");
-    return fail(FMT_ENOMEM);
-  }
-  // root level: one node, ceil(n / chunk) items at most
-  const int64_t cap_items0 = n / min_chunk(t) + 2;
-  if ((st = alloc_level(t, 0, 1, cap_items0, s))) return fail(st);
-  int32_t q = P.degree;
-  if (n < t->nmono) {
-    q = -1;
-    while (fmt_nmono(q + 1) <= n) ++q;
-  }
-  t->lv[0].q = q;
-
-  cudaError_t e = cudaSuccess;
-  void* kout = nullptr;
-  uint32_t* vout = nullptr;
-  do {
-    if ((e = cudaMemsetAsync(t->d_err, 0, sizeof(int), s)) != cudaSuccess) break;
-    if ((e = cudaMemsetAsync(d_maxbits, 0, sizeof(unsigned long long), s)) != cudaSuccess) break;
-    {
-      ProfScope ps(K_CHECK, s, 1, (double)n, 0.0);
-      if ((e = launch_check_maxabs(n, x, y, z, f, d_maxbits, t->d_err, s)) != cudaSuccess) break;
-    }
-    {
-      ProfScope ps(K_MORTON, s, 1, (double)n, 0.0);
-      e = launch_morton(n, x, y, z, P.lo[0], P.lo[1], P.lo[2], t->S, sort_shift, key64, keys, vals, s);
-      if (e != cudaSuccess) break;
-    }
-    {
-      ProfScope ps(K_SORT, s, 4 * ((t->sort_bits + 7) / 8), (double)n, 0.0);
-      e = launch_radix_sort(n, t->sort_bits, key64, keys, vals, keys_alt, vals_alt, temp, &kout, &vout, s);
-      if (e != cudaSuccess) break;
-    }
-    t->perm = vout;
-    {
-      ProfScope ps(K_GATHER, s, 1, (double)n, 0.0);
-      e = launch_gather(n, t->perm, x, y, z, f, P.lo[0], P.lo[1], P.lo[2], t->S, t->x, t->y, t->z, t->r, t->code, s);
-      if (e != cudaSuccess) break;
-    }
-    {
-      ProfScope ps(K_PLAN, s, 1, 1.0, 0.0);
-      e = launch_plan_root(t, t->P.chunk_rows, t->chunk_floor, t->d_plan, s);
-    }
-  } while (0);
-  if (e != cudaSuccess) {
-    set_err(nullptr, FMT_ECUDA, "oct_build launch: %s", cudaGetErrorString(e));
-    return fail(FMT_ECUDA);
-  }
-  unsigned long long hbits = 0;
-  if ((e = cudaMemcpyAsync(&hbits, d_maxbits, sizeof(hbits), cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
-    set_err(nullptr, FMT_ECUDA, "copy: %s", cudaGetErrorString(e));
-    return fail(FMT_ECUDA);
-  }
-  if (read_plan(t, s) != FMT_OK) {
-    set_err(nullptr, FMT_ECUDA, "%s", t->msg);
-    return fail(FMT_ECUDA);
-  }
-  const fmt_plan_out& pl = *t->h_plan;
-  if (pl.err & FMT_ERR_NONFINITE) {
-    set_err(nullptr, FMT_EINVAL, "non-finite coordinate or value in the input");
-    return fail(FMT_EINVAL);
-  }
-  if (pl.err) {
-    set_err(nullptr, FMT_EINTERNAL, "device check failed in oct_build (0x%llx)", (unsigned long long)pl.err);
-    return fail(FMT_EINTERNAL);
-  }
-  double mx;
-  memcpy(&mx, &hbits, sizeof(mx));
-  t->maxabs = mx;
-  t->tau = P.tol_rel * mx;
-  fmt_level& L0 = t->lv[0];
-  L0.n_nodes = 1;
-  L0.n_items = pl.n_items;
-  L0.max_chunks = pl.max_chunks;
-  L0.chunk_rows = pl.chunk_rows;
-  L0.n_points = n;
-  t->n_levels = 1;
-  t->next_fit = 0;
-  t->next_refine = -1;
-  // the sort buffers are not needed any more (the permutation stays)
-  tfree_one(t, keys, s);
-  tfree_one(t, keys_alt, s);
-  tfree_one(t, temp, s);
-  tfree_one(t, vout == vals ? (void*)vals_alt : (void*)vals, s);
-  tfree_one(t, d_maxbits, s);
-  *out = t;
-  return FMT_OK;
+fmt_status oct_build_batch(const fmt_params* params, int64_t n_problems, const int64_t* offsets,
+                           const int32_t* degrees, const double* boxes, const double* x, const double* y,
+                           const double* z, const double* f, void* stream, fmt_tree** out) {
+  return build_forest(params, n_problems, offsets, degrees, boxes, x, y, z, f, (cudaStream_t)stream, out);
 }
 
 fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
@@ -416,8 +526,8 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
   if (t->done || depth != t->next_fit)
     return set_err(t, FMT_EINVAL, "fit_level(%d) out of order (expected %d)", depth, t->done ? -1 : t->next_fit);
   fmt_level& L = t->lv[depth];
-  const int m = fmt_nmono(L.q) + 1;
-  const size_t need = (size_t)L.n_items * (size_t)m * (size_t)m;
+  const int m = L.max_m;
+  const size_t need = (size_t)L.r_total;
   if (need > t->Rbuf_cap) {
     if (t->Rbuf) tfree_one(t, t->Rbuf, s);
     t->Rbuf = nullptr;
@@ -427,8 +537,8 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
   }
   const double dm = (double)m, rows = (double)L.n_points;
   {
-    // Householder on [Lambda | r]: 2 m^2 flops per row (m = nmono + 1)
-    ProfScope ps(K_TILE_QR, s, 1, rows, 2.0 * dm * dm * rows);
+    // Householder on [Lambda | r]: 2 m^2 flops per row (m = nmono + 1 of the row's node)
+    ProfScope ps(K_TILE_QR, s, 1, rows, L.qr_flops);
     CUDA_TRY(t, launch_tile_qr(t, depth, t->Rbuf, s), "tile QR launch");
   }
   int levels = 0;
@@ -444,7 +554,7 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
     CUDA_TRY(t, launch_backsolve(t, depth, t->Rbuf, s), "back-solve launch");
   }
   {
-    ProfScope ps(K_RESIDUAL, s, 1, rows, rows * horner_flops(t->P.degree));
+    ProfScope ps(K_RESIDUAL, s, 1, rows, L.horner_flops);
     CUDA_TRY(t, launch_residual(t, depth, s), "residual launch");
   }
   {
@@ -493,7 +603,10 @@ fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream
   N.max_chunks = pl.max_chunks;
   N.chunk_rows = pl.chunk_rows;
   N.n_points = pl.n_points;
-  N.q = t->P.degree;
+  N.max_m = (int32_t)pl.max_m;
+  N.r_total = pl.r_total;
+  N.qr_flops = pl.qr_flops;
+  N.horner_flops = pl.horner_flops;
   N.fitted = false;
   t->n_levels = depth + 2;
   t->next_fit = depth + 1;
@@ -501,28 +614,38 @@ fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream
   return FMT_OK;
 }
 
-fmt_status evaluate(fmt_tree* t, int64_t m, const double* xq, const double* yq, const double* zq, double* out,
-                    int64_t* n_outside, void* stream) {
+fmt_status evaluate_batch(fmt_tree* t, int64_t m, const int32_t* target_problem, const double* xq,
+                          const double* yq, const double* zq, double* out, int64_t* n_outside, void* stream) {
   TRY(check_tree(t));
   cudaStream_t s = (cudaStream_t)stream;
   t->stream = s;
   if (m < 0) return set_err(t, FMT_EINVAL, "m < 0");
   if (m > 0 && (!xq || !yq || !zq || !out)) return set_err(t, FMT_EINVAL, "NULL target or output pointer");
-  if (!t->lv[0].fitted) return set_err(t, FMT_EINVAL, "evaluate before the root was fitted");
+  if (t->n_problems > 1 && m > 0 && !target_problem)
+    return set_err(t, FMT_EINVAL, "a forest needs the problem of every target");
+  if (!t->lv[0].fitted) return set_err(t, FMT_EINVAL, "evaluate before the roots were fitted");
   if (n_outside) *n_outside = 0;
   if (m == 0) return FMT_OK;
   if (n_outside) CUDA_TRY(t, cudaMemsetAsync(t->d_counter, 0, sizeof(unsigned long long), s), "memset");
   {
     ProfScope ps(K_EVALUATE, s, 1, (double)m, 0.0);
-    CUDA_TRY(t, launch_evaluate(t, m, xq, yq, zq, out, n_outside ? t->d_counter : nullptr, s), "evaluate launch");
+    CUDA_TRY(t, launch_evaluate(t, m, target_problem, xq, yq, zq, out, n_outside ? t->d_counter : nullptr, s),
+             "evaluate launch");
   }
   if (n_outside) {
     unsigned long long h = 0;
     CUDA_TRY(t, cudaMemcpyAsync(&h, t->d_counter, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
+    CUDA_TRY(t, cudaMemcpyAsync(t->h_err, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
     CUDA_TRY(t, cudaStreamSynchronize(s), "synchronise");
+    if (*t->h_err & FMT_ERR_INDEX) return set_err(t, FMT_EINVAL, "target problem index out of range");
     *n_outside = (int64_t)h;
   }
   return FMT_OK;
+}
+
+fmt_status evaluate(fmt_tree* t, int64_t m, const double* xq, const double* yq, const double* zq, double* out,
+                    int64_t* n_outside, void* stream) {
+  return evaluate_batch(t, m, nullptr, xq, yq, zq, out, n_outside, stream);
 }
 
 fmt_status fmt_tree_stats(fmt_tree* t, fmt_stats* o) {
@@ -530,13 +653,14 @@ fmt_status fmt_tree_stats(fmt_tree* t, fmt_stats* o) {
   if (!o) return set_err(t, FMT_EINVAL, "out is NULL");
   memset(o, 0, sizeof(*o));
   CUDA_TRY(t, cudaDeviceSynchronize(), "synchronise");
-  o->degree = t->P.degree;
+  o->degree = t->max_degree;
   o->nmono = t->nmono;
   o->max_depth = t->P.max_depth;
   o->n_levels = t->n_levels;
   int nf = 0;
   while (nf < t->n_levels && t->lv[nf].fitted) ++nf;
   o->n_fitted = nf;
+  o->n_problems = (int32_t)t->n_problems;
   o->n_points = t->n;
   o->tau = t->tau;
   o->maxabs_f = t->maxabs;
@@ -564,16 +688,22 @@ fmt_status fmt_tree_stats(fmt_tree* t, fmt_stats* o) {
   return FMT_OK;
 }
 
+// bytes of the node and problem sections of an FMT2 blob
+static size_t blob_node_bytes(int64_t K, int64_t nm) {
+  return (size_t)K * (8 + 8 + 8 + 4 * 6 + 8 * 8 + 8 * 8 + 8 * (size_t)nm);
+}
+static size_t blob_problem_bytes(int64_t P) { return (size_t)P * (4 + 4 + 8 * 6 + 8 + 8); }
+
 fmt_status fmt_tree_export(fmt_tree* t, void* host_buf, size_t* len) {
   TRY(check_tree(t));
   if (!len) return set_err(t, FMT_EINVAL, "len is NULL");
   int64_t K = 0;
   for (int d = 0; d < t->n_levels; ++d) K += t->lv[d].n_nodes;
-  const int64_t nm = t->nmono;
+  const int64_t nm = t->nmono, P = t->n_problems;
   const int has_pts = (t->imported || !t->x) ? 0 : 1;
   const int64_t N = has_pts ? t->n : 0;
-  const size_t need = sizeof(fmt_export_header) + (size_t)K * (8 + 8 + 8 + 4 * 4 + 8 * 8 + 8 * 8 + 8 * (size_t)nm) +
-                      (size_t)N * (8 + 8 + 8);
+  const size_t need =
+      sizeof(fmt_export_header) + blob_node_bytes(K, nm) + blob_problem_bytes(P) + (size_t)N * (8 + 8 + 8);
   if (!host_buf) {
     *len = need;
     return FMT_OK;
@@ -587,9 +717,9 @@ fmt_status fmt_tree_export(fmt_tree* t, void* host_buf, size_t* len) {
   char* b = (char*)host_buf;
   fmt_export_header* H = (fmt_export_header*)b;
   memset(H, 0, sizeof(*H));
-  H->magic = 0x31544d46u;
-  H->version = 1;
-  H->degree = t->P.degree;
+  H->magic = 0x32544d46u;
+  H->version = 2;
+  H->degree = t->max_degree;
   H->nmono = t->nmono;
   H->max_depth = t->P.max_depth;
   H->min_pts = t->P.min_pts;
@@ -598,11 +728,12 @@ fmt_status fmt_tree_export(fmt_tree* t, void* host_buf, size_t* len) {
   while (nf < t->n_levels && t->lv[nf].fitted) ++nf;
   H->n_fitted = nf;
   H->has_points = has_pts;
+  H->n_problems = (int32_t)P;
   H->tol_rel = t->P.tol_rel;
   H->tau = t->tau;
   H->maxabs_f = t->maxabs;
-  for (int a = 0; a < 3; ++a) H->lo[a] = t->P.lo[a];
-  H->side = t->P.side;
+  for (int a = 0; a < 3; ++a) H->lo[a] = t->h_prob[0].lo[a];
+  H->side = t->h_prob[0].side;
   H->n_points = t->n;
   H->n_nodes = K;
   for (int d = 0; d < t->n_levels; ++d) H->level_nodes[d] = t->lv[d].n_nodes;
@@ -614,10 +745,12 @@ fmt_status fmt_tree_export(fmt_tree* t, void* host_buf, size_t* len) {
   int32_t* flags = depth + K;
   int32_t* deg = flags + K;
   int32_t* masks = deg + K;
-  double* cE = (double*)(masks + K);
+  int32_t* nprob = masks + K;
+  int32_t* npad = nprob + K;
+  double* cE = (double*)(npad + K);
   int64_t* cn = (int64_t*)(cE + 8 * K);
   double* coef = (double*)(cn + 8 * K);
-  char* pts = (char*)(coef + nm * K);
+  char* pp = (char*)(coef + nm * K);
   int64_t off = 0;
   for (int d = 0; d < t->n_levels; ++d) {
     const fmt_level& L = t->lv[d];
@@ -629,10 +762,14 @@ fmt_status fmt_tree_export(fmt_tree* t, void* host_buf, size_t* len) {
     CUDA_TRY(t, cudaMemcpy(flags + off, L.flags, 4 * k, cudaMemcpyDeviceToHost), "copy");
     CUDA_TRY(t, cudaMemcpy(deg + off, L.deg_used, 4 * k, cudaMemcpyDeviceToHost), "copy");
     CUDA_TRY(t, cudaMemcpy(masks + off, L.masks, 4 * k, cudaMemcpyDeviceToHost), "copy");
+    CUDA_TRY(t, cudaMemcpy(nprob + off, L.prob, 4 * k, cudaMemcpyDeviceToHost), "copy");
     CUDA_TRY(t, cudaMemcpy(cE + 8 * off, L.child_E, 64 * k, cudaMemcpyDeviceToHost), "copy");
     CUDA_TRY(t, cudaMemcpy(cn + 8 * off, L.child_n, 64 * k, cudaMemcpyDeviceToHost), "copy");
     CUDA_TRY(t, cudaMemcpy(coef + nm * off, L.coef, 8 * nm * k, cudaMemcpyDeviceToHost), "copy");
-    for (size_t i = 0; i < k; ++i) depth[off + i] = d;
+    for (size_t i = 0; i < k; ++i) {
+      depth[off + i] = d;
+      npad[off + i] = 0;
+    }
     if (!L.fitted) {  // nodes created by refine but not fitted yet carry no coefficients
       memset(coef + nm * off, 0, 8 * nm * k);
       memset(cE + 8 * off, 0, 64 * k);
@@ -641,6 +778,27 @@ fmt_status fmt_tree_export(fmt_tree* t, void* host_buf, size_t* len) {
     }
     off += (int64_t)k;
   }
+  // problem table: degree, q_root, tau, maxabs, lo[3], side, start, count
+  int32_t* pdeg = (int32_t*)pp;
+  int32_t* pq = pdeg + P;
+  double* ptau = (double*)(pq + P);
+  double* pmax = ptau + P;
+  double* plo = pmax + P;
+  double* pside = plo + 3 * P;
+  int64_t* pstart = (int64_t*)(pside + P);
+  int64_t* pcount = pstart + P;
+  for (int64_t i = 0; i < P; ++i) {
+    const fmt_problem& pr = t->h_prob[i];
+    pdeg[i] = pr.degree;
+    pq[i] = pr.q_root;
+    ptau[i] = pr.tau;
+    pmax[i] = pr.maxabs;
+    for (int a = 0; a < 3; ++a) plo[3 * i + a] = pr.lo[a];
+    pside[i] = pr.side;
+    pstart[i] = pr.start;
+    pcount[i] = pr.count;
+  }
+  char* pts = (char*)(pcount + P);
   if (has_pts) {
     uint64_t* code = (uint64_t*)pts;
     int64_t* perm = (int64_t*)(code + N);
@@ -675,24 +833,53 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
   *out = nullptr;
   if (!host_buf || len < sizeof(fmt_export_header)) return set_err(nullptr, FMT_EINVAL, "blob too small");
   const fmt_export_header* H = (const fmt_export_header*)host_buf;
-  if (H->magic != 0x31544d46u || H->version != 1) return set_err(nullptr, FMT_EINVAL, "not an FMT1 blob");
+  if (H->magic != 0x32544d46u || H->version != 2) return set_err(nullptr, FMT_EINVAL, "not an FMT2 blob");
   if (H->degree < 0 || H->degree > FMT_MAX_DEGREE || H->nmono != fmt_nmono(H->degree) || H->n_levels < 1 ||
-      H->n_levels > FMT_MAX_DEPTH + 1 || H->n_nodes < 1 || !(H->side > 0.0))
+      H->n_levels > FMT_MAX_DEPTH + 1 || H->n_nodes < 1 || H->n_problems < 1)
     return set_err(nullptr, FMT_EINVAL, "inconsistent blob header");
-  const int64_t K = H->n_nodes, nm = H->nmono;
+  const int64_t K = H->n_nodes, nm = H->nmono, P = H->n_problems;
   int64_t sumk = 0;
   for (int d = 0; d < H->n_levels; ++d) {
     if (H->level_nodes[d] < 1) return set_err(nullptr, FMT_EINVAL, "empty level %d in blob", d);
     sumk += H->level_nodes[d];
   }
   if (sumk != K) return set_err(nullptr, FMT_EINVAL, "level sizes do not add up");
-  const size_t need = sizeof(fmt_export_header) + (size_t)K * (8 + 8 + 8 + 16 + 64 + 64 + 8 * (size_t)nm);
+  const size_t need = sizeof(fmt_export_header) + blob_node_bytes(K, nm) + blob_problem_bytes(P);
   if (len < need) return set_err(nullptr, FMT_EINVAL, "blob truncated");
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
   TRY(device_init(dev));
   cudaStream_t s = (cudaStream_t)stream;
+  const char* p = (const char*)host_buf + sizeof(fmt_export_header);
+  const uint64_t* prefix = (const uint64_t*)p;
+  const int64_t* start = (const int64_t*)(prefix + K);
+  const int64_t* count = start + K;
+  const int32_t* depth = (const int32_t*)(count + K);
+  const int32_t* flags = depth + K;
+  const int32_t* deg = flags + K;
+  const int32_t* masks = deg + K;
+  const int32_t* nprob = masks + K;
+  const int32_t* npad = nprob + K;
+  const double* cE = (const double*)(npad + K);
+  const int64_t* cn = (const int64_t*)(cE + 8 * K);
+  const double* coef = (const double*)(cn + 8 * K);
+  const char* pp = (const char*)(coef + nm * K);
+  const int32_t* pdeg = (const int32_t*)pp;
+  const int32_t* pq = pdeg + P;
+  const double* ptau = (const double*)(pq + P);
+  const double* pmax = ptau + P;
+  const double* plo = pmax + P;
+  const double* pside = plo + 3 * P;
+  const int64_t* pstart = (const int64_t*)(pside + P);
+  const int64_t* pcount = pstart + P;
+  for (int64_t i = 0; i < P; ++i) {
+    if (pdeg[i] < 0 || pdeg[i] > H->degree) return set_err(nullptr, FMT_EINVAL, "problem degree out of range");
+    TRY(validate_box(plo[3 * i], plo[3 * i + 1], plo[3 * i + 2], pside[i]));
+  }
+  for (int64_t i = 0; i < K; ++i)
+    if (nprob[i] < 0 || nprob[i] >= P) return set_err(nullptr, FMT_EINVAL, "node problem out of range");
+
   fmt_tree* t = new (std::nothrow) fmt_tree();
   if (!t) return set_err(nullptr, FMT_ENOMEM, "host allocation failed");
   t->imported = true;
@@ -706,25 +893,44 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
   for (int a = 0; a < 3; ++a) t->P.lo[a] = H->lo[a];
   t->P.side = H->side;
   t->nmono = (int32_t)nm;
+  t->max_degree = H->degree;
   t->n = H->n_points;
+  t->n_problems = P;
   t->tau = H->tau;
   t->maxabs = H->maxabs_f;
-  t->S = 2097152.0 / H->side;
-  const char* p = (const char*)host_buf + sizeof(fmt_export_header);
-  const uint64_t* prefix = (const uint64_t*)p;
-  const int64_t* start = (const int64_t*)(prefix + K);
-  const int64_t* count = start + K;
-  const int32_t* depth = (const int32_t*)(count + K);
-  const int32_t* flags = depth + K;
-  const int32_t* deg = flags + K;
-  const int32_t* masks = deg + K;
-  const double* cE = (const double*)(masks + K);
-  const int64_t* cn = (const int64_t*)(cE + 8 * K);
-  const double* coef = (const double*)(cn + 8 * K);
+  t->h_prob = (fmt_problem*)calloc((size_t)P, sizeof(fmt_problem));
+  if (!t->h_prob) {
+    destroy(t);
+    return set_err(nullptr, FMT_ENOMEM, "host allocation failed");
+  }
+  for (int64_t i = 0; i < P; ++i) {
+    fmt_problem& pr = t->h_prob[i];
+    pr.degree = pdeg[i];
+    pr.q_root = pq[i];
+    pr.tau = ptau[i];
+    pr.maxabs = pmax[i];
+    for (int a = 0; a < 3; ++a) pr.lo[a] = plo[3 * i + a];
+    pr.side = pside[i];
+    pr.S = 2097152.0 / pr.side;
+    pr.start = pstart[i];
+    pr.count = pcount[i];
+  }
   fmt_status st = FMT_OK;
-  if ((st = talloc(t, &t->d_err, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)) || (st = talloc(t, &t->d_plan, 1, s))) {
+  if ((st = talloc(t, &t->d_err, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)) ||
+      (st = talloc(t, &t->d_plan, 1, s)) || (st = talloc(t, &t->d_prob, P, s))) {
     destroy(t);
     return st;
+  }
+  if (cudaMallocHost((void**)&t->h_err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(t);
+    return set_err(nullptr, FMT_ENOMEM, "pinned host allocation failed");
+  }
+  cudaError_t e0 = cudaMemcpyAsync(t->d_prob, t->h_prob, sizeof(fmt_problem) * (size_t)P, cudaMemcpyHostToDevice, s);
+  if (e0 == cudaSuccess) e0 = cudaMemsetAsync(t->d_err, 0, sizeof(int), s);
+  if (e0 != cudaSuccess) {
+    destroy(t);
+    return set_err(nullptr, FMT_ECUDA, "import upload: %s", cudaGetErrorString(e0));
   }
   int64_t off = 0;
   for (int d = 0; d < H->n_levels; ++d) {
@@ -732,7 +938,7 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
     for (int64_t i = 1; i < k; ++i)
       if (prefix[off + i] <= prefix[off + i - 1] || depth[off + i] != d) {
         destroy(t);
-        return set_err(nullptr, FMT_EINVAL, "blob level %d is not sorted by Morton prefix", d);
+        return set_err(nullptr, FMT_EINVAL, "blob level %d is not sorted by node key", d);
       }
     if ((st = alloc_level(t, d, k, 1, s))) {
       destroy(t);
@@ -740,10 +946,10 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
     }
     fmt_level& L = t->lv[d];
     L.n_nodes = k;
-    L.q = H->degree;
     L.fitted = true;
     cudaError_t e = cudaSuccess;
     if ((e = cudaMemcpyAsync(L.prefix, prefix + off, 8 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(L.prob, nprob + off, 4 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(L.start, start + off, 8 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(L.count, count + off, 8 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(L.flags, flags + off, 4 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
@@ -751,11 +957,15 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
         (e = cudaMemcpyAsync(L.masks, masks + off, 4 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(L.child_E, cE + 8 * off, 64 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(L.child_n, cn + 8 * off, 64 * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(L.coef, coef + nm * off, 8 * nm * k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = [&] {
-          ProfScope ps(K_HCOEF, s, 1, (double)k, 0.0);
-          return launch_make_hcoef(k, H->degree, (int)nm, L.coef, L.hcoef, s);
-        }()) != cudaSuccess) {
+        (e = cudaMemcpyAsync(L.coef, coef + nm * off, 8 * nm * k, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+      destroy(t);
+      return set_err(nullptr, FMT_ECUDA, "import upload: %s", cudaGetErrorString(e));
+    }
+    {
+      ProfScope ps(K_HCOEF, s, 1, (double)k, 0.0);
+      e = launch_make_hcoef(t, d, s);
+    }
+    if (e != cudaSuccess) {
       destroy(t);
       return set_err(nullptr, FMT_ECUDA, "import upload: %s", cudaGetErrorString(e));
     }

@@ -22,42 +22,76 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// max |f| and a finiteness check of every coordinate and value
+// problem of point i (problems are contiguous ranges of the input)
+__device__ __forceinline__ int problem_of_point(const fmt_problem* __restrict__ prob, int P, int64_t i) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prob[mid].start <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per-problem max |f| and a finiteness check of every coordinate and value.
+// A block whose points all belong to one problem reduces in shared memory and
+// issues one atomic; otherwise every thread updates its problem directly.
 __global__ void __launch_bounds__(256) k_check_maxabs(int64_t n, const double* __restrict__ x,
                                                       const double* __restrict__ y,
                                                       const double* __restrict__ z,
                                                       const double* __restrict__ f,
+                                                      const fmt_problem* __restrict__ prob, int P,
                                                       unsigned long long* maxbits, int* err) {
   __shared__ double red[8];
-  double m = 0.0;
-  bool bad = false;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double a = x[i], b = y[i], c = z[i], v = f[i];
-    bad |= !isfinite(a) || !isfinite(b) || !isfinite(c) || !isfinite(v);
-    m = fmax(m, fabs(v));
-  }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, FMT_ERR_NONFINITE);
-  m = warp_max(m);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    v = warp_max(v);
-    // non-negative doubles order like their bit patterns
-    if (threadIdx.x == 0 && isfinite(v)) atomicMax(maxbits, (unsigned long long)__double_as_longlong(v));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rounds = (n + stride - 1) / stride;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t base = r * stride + (int64_t)blockIdx.x * blockDim.x;
+    const int64_t i = first + r * stride;
+    const int64_t last = (base + blockDim.x < n ? base + blockDim.x : n) - 1;
+    const int p0 = base < n ? problem_of_point(prob, P, base) : 0;
+    const int p1 = base < n ? problem_of_point(prob, P, last) : 0;
+    double m = 0.0;
+    bool bad = false;
+    if (i < n) {
+      const double a = x[i], b = y[i], c = z[i], v = f[i];
+      bad = !isfinite(a) || !isfinite(b) || !isfinite(c) || !isfinite(v);
+      m = fabs(v);
+      if (p0 != p1 && isfinite(m) && m > 0.0)
+        atomicMax(&maxbits[problem_of_point(prob, P, i)], (unsigned long long)__double_as_longlong(m));
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, FMT_ERR_NONFINITE);
+    if (p0 == p1) {  // block-uniform
+      m = warp_max(m);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        v = warp_max(v);
+        // non-negative doubles order like their bit patterns
+        if (threadIdx.x == 0 && isfinite(v) && v > 0.0)
+          atomicMax(&maxbits[p0], (unsigned long long)__double_as_longlong(v));
+      }
+      __syncthreads();
+    }
   }
 }
 
+// Sort key: problem id above the top sort_bits bits of the Morton code.
 template <typename K>
 __global__ void __launch_bounds__(256) k_morton(int64_t n, const double* __restrict__ x,
                                                 const double* __restrict__ y,
-                                                const double* __restrict__ z, double lo0, double lo1,
-                                                double lo2, double S, int sort_shift, K* __restrict__ keys,
-                                                uint32_t* __restrict__ vals) {
+                                                const double* __restrict__ z,
+                                                const fmt_problem* __restrict__ prob, int P, int sort_shift,
+                                                int sort_bits, K* __restrict__ keys, uint32_t* __restrict__ vals) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t code = fmt_spread3(fmt_quant(x[i], lo0, S)) | (fmt_spread3(fmt_quant(y[i], lo1, S)) << 1) |
-                    (fmt_spread3(fmt_quant(z[i], lo2, S)) << 2);
-    keys[i] = (K)(code >> sort_shift);
+    const int p = P > 1 ? problem_of_point(prob, P, i) : 0;
+    const fmt_problem& pr = prob[p];
+    const uint64_t code = fmt_spread3(fmt_quant(x[i], pr.lo[0], pr.S)) |
+                          (fmt_spread3(fmt_quant(y[i], pr.lo[1], pr.S)) << 1) |
+                          (fmt_spread3(fmt_quant(z[i], pr.lo[2], pr.S)) << 2);
+    keys[i] = (K)(((uint64_t)p << sort_bits) | (code >> sort_shift));
     vals[i] = (uint32_t)i;
   }
 }
@@ -169,19 +203,20 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
 __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* __restrict__ perm,
                                                 const double* __restrict__ x, const double* __restrict__ y,
                                                 const double* __restrict__ z, const double* __restrict__ f,
-                                                double lo0, double lo1, double lo2, double S,
+                                                const fmt_problem* __restrict__ prob, int P,
                                                 double* __restrict__ xs, double* __restrict__ ys,
                                                 double* __restrict__ zs, double* __restrict__ rs,
                                                 uint64_t* __restrict__ code) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t j = perm[i];
-    double a = x[j], b = y[j], c = z[j];
+    const uint32_t j = perm[i];
+    const double a = x[j], b = y[j], c = z[j];
+    const fmt_problem& pr = prob[P > 1 ? problem_of_point(prob, P, i) : 0];
     xs[i] = a;
     ys[i] = b;
     zs[i] = c;
     rs[i] = f[j];
-    code[i] = fmt_spread3(fmt_quant(a, lo0, S)) | (fmt_spread3(fmt_quant(b, lo1, S)) << 1) |
-              (fmt_spread3(fmt_quant(c, lo2, S)) << 2);
+    code[i] = fmt_spread3(fmt_quant(a, pr.lo[0], pr.S)) | (fmt_spread3(fmt_quant(b, pr.lo[1], pr.S)) << 1) |
+              (fmt_spread3(fmt_quant(c, pr.lo[2], pr.S)) << 2);
   }
 }
 
@@ -196,20 +231,20 @@ int grid_for(int64_t n, int threads) {
 }  // namespace
 
 cudaError_t launch_check_maxabs(int64_t n, const double* x, const double* y, const double* z,
-                                const double* f, unsigned long long* d_maxbits, int* d_err,
-                                cudaStream_t s) {
-  k_check_maxabs<<<grid_for(n, 256), 256, 0, s>>>(n, x, y, z, f, d_maxbits, d_err);
+                                const double* f, const fmt_problem* prob, int P, unsigned long long* d_maxbits,
+                                int* d_err, cudaStream_t s) {
+  k_check_maxabs<<<grid_for(n, 256), 256, 0, s>>>(n, x, y, z, f, prob, P, d_maxbits, d_err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_morton(int64_t n, const double* x, const double* y, const double* z, double lo0,
-                          double lo1, double lo2, double S, int sort_shift, bool key64, void* keys,
-                          uint32_t* vals, cudaStream_t s) {
+cudaError_t launch_morton(int64_t n, const double* x, const double* y, const double* z, const fmt_problem* prob,
+                          int P, int sort_shift, int sort_bits, bool key64, void* keys, uint32_t* vals,
+                          cudaStream_t s) {
   if (key64)
-    k_morton<uint64_t><<<grid_for(n, 256), 256, 0, s>>>(n, x, y, z, lo0, lo1, lo2, S, sort_shift,
+    k_morton<uint64_t><<<grid_for(n, 256), 256, 0, s>>>(n, x, y, z, prob, P, sort_shift, sort_bits,
                                                         (uint64_t*)keys, vals);
   else
-    k_morton<uint32_t><<<grid_for(n, 256), 256, 0, s>>>(n, x, y, z, lo0, lo1, lo2, S, sort_shift,
+    k_morton<uint32_t><<<grid_for(n, 256), 256, 0, s>>>(n, x, y, z, prob, P, sort_shift, sort_bits,
                                                         (uint32_t*)keys, vals);
   return cudaGetLastError();
 }
@@ -268,8 +303,8 @@ cudaError_t launch_radix_sort(int64_t n, int bits, bool key64, void* keys, uint3
 }
 
 cudaError_t launch_gather(int64_t n, const uint32_t* perm, const double* x, const double* y,
-                          const double* z, const double* f, double lo0, double lo1, double lo2, double S,
-                          double* xs, double* ys, double* zs, double* rs, uint64_t* code, cudaStream_t s) {
-  k_gather<<<grid_for(n, 256), 256, 0, s>>>(n, perm, x, y, z, f, lo0, lo1, lo2, S, xs, ys, zs, rs, code);
+                          const double* z, const double* f, const fmt_problem* prob, int P, double* xs, double* ys,
+                          double* zs, double* rs, uint64_t* code, cudaStream_t s) {
+  k_gather<<<grid_for(n, 256), 256, 0, s>>>(n, perm, x, y, z, f, prob, P, xs, ys, zs, rs, code);
   return cudaGetLastError();
 }

@@ -57,17 +57,38 @@ struct QRArgs {
   const int32_t* item_local;
   const int32_t* node_nitems;
   const uint64_t* prefix;
+  const int32_t* node_prob;
+  const fmt_problem* prob;
   const double* x;
   const double* y;
   const double* z;
   const double* r;
-  double lo0, lo1, lo2, side;
-  int depth, q, m, ldB;
+  int depth;
+  int ld_max;       // shared-memory pitch for the level's largest m
+  const int64_t* item_roff;  // offset of each item's triangle in R
   double* R;
   const int32_t* sched;
   int* work;
   int n_items;
 };
+
+// degree, column count and frame of a node of the level
+struct NodeGeom {
+  int q, m, ldB;
+  double c0, s0, c1, s1, c2, s2;
+};
+__device__ __forceinline__ NodeGeom node_geom(const QRArgs& a, int64_t node) {
+  NodeGeom g;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  g.q = a.depth == 0 ? pr.q_root : pr.degree;
+  g.m = fmt_nmono_d(g.q) + 1;
+  g.ldB = fmt_ld_for(g.m);
+  const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
+  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), g.c0, g.s0);
+  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), g.c1, g.s1);
+  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), g.c2, g.s2);
+  return g;
+}
 
 // Structured Householder absorb of a row block B (NB x m in shared memory,
 // leading dimension ldB) into the upper triangle R (m x m, row-major, global).
@@ -226,13 +247,6 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
   }
 }
 
-__device__ __forceinline__ void node_frame(const QRArgs& a, uint64_t pf, double& c0, double& s0, double& c1,
-                                           double& s1, double& c2, double& s2) {
-  fmt_frame(a.lo0, a.side, a.depth, fmt_compact3(pf), c0, s0);
-  fmt_frame(a.lo1, a.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
-  fmt_frame(a.lo2, a.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
-}
-
 // Persistent CTAs take work items from a queue in the order of `sched`
 // (largest items first), so the longest chunks start early.
 template <int RPT>
@@ -240,11 +254,9 @@ __global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
   extern __shared__ double smem[];
   constexpr int NB = 4 * RPT;
   double* Bs = smem;
-  double* Rs = smem + NB * a.ldB;
-  double* sc = Rs + 2 * a.ldB;
+  double* Rs = smem + NB * a.ld_max;
+  double* sc = Rs + 2 * a.ld_max;
   __shared__ int s_item;
-  const int m = a.m;
-  const int q = a.q;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
     __syncthreads();
@@ -254,21 +266,22 @@ __global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
     const int item = a.sched[it];
     const int64_t node = a.item_node[item];
     const int64_t rs = a.item_start[item], re = a.item_end[item];
-    double* R = a.R + (size_t)item * m * m;
+    const NodeGeom g = node_geom(a, node);
+    const int m = g.m, q = g.q, ldB = g.ldB;
+    double* R = a.R + a.item_roff[item];
     for (int e = threadIdx.x; e < m * m; e += kQRThreads) {
       const int j = e / m, k = e - j * m;
       if (k >= j) R[e] = 0.0;
     }
-    double c0, s0, c1, s1, c2, s2;
-    node_frame(a, a.prefix[node], c0, s0, c1, s1, c2, s2);
     __syncthreads();
     for (int64_t b0 = rs; b0 < re; b0 += NB) {
       const int nb = (int)((re - b0) < NB ? (re - b0) : NB);
       if (threadIdx.x < NB) {
-        double* row = Bs + threadIdx.x * a.ldB;
+        double* row = Bs + threadIdx.x * ldB;
         if ((int)threadIdx.x < nb) {
           const int64_t i = b0 + threadIdx.x;
-          const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+          const double u = fmt_local(a.x[i], g.c0, g.s0), v = fmt_local(a.y[i], g.c1, g.s1),
+                       w = fmt_local(a.z[i], g.c2, g.s2);
           double pu[FMT_MAX_DEGREE + 1], pv[FMT_MAX_DEGREE + 1], pw[FMT_MAX_DEGREE + 1];
           double tu = 1.0, tv = 1.0, tw = 1.0;
           for (int l = 0; l <= q; ++l) {
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
         }
       }
       __syncthreads();
-      absorb_block<RPT, kQRThreads / 32>(Bs, a.ldB, 0, m, R, Rs, sc, -1);
+      absorb_block<RPT, kQRThreads / 32>(Bs, ldB, 0, m, R, Rs, sc, -1);
     }
   }
 }
@@ -306,24 +319,26 @@ __global__ void __launch_bounds__(32 * kCombineWarps) k_combine(QRArgs a, int le
   extern __shared__ double smem[];
   constexpr int NB = 4 * RPT;
   double* Bs = smem;
-  double* Rs = smem + NB * a.ldB;
-  double* sc = Rs + 2 * a.ldB;
+  double* Rs = smem + NB * a.ld_max;
+  double* sc = Rs + 2 * a.ld_max;
   const int item = blockIdx.x;
   const int s = a.item_local[item];
-  const int cnt = a.node_nitems[a.item_node[item]];
+  const int64_t node = a.item_node[item];
+  const int cnt = a.node_nitems[node];
   const int step = 1 << level;
   if ((s & (2 * step - 1)) != 0 || s + step >= cnt) return;
-  const int m = a.m;
-  double* Ra = a.R + (size_t)item * m * m;
-  const double* Rb = a.R + (size_t)(item + step) * m * m;
+  const NodeGeom g = node_geom(a, node);
+  const int m = g.m;
+  double* Ra = a.R + a.item_roff[item];
+  const double* Rb = a.R + a.item_roff[item + step];
   for (int r0 = 0; r0 < m; r0 += NB) {
     for (int e = threadIdx.x; e < NB * m; e += 32 * kCombineWarps) {
       const int i = e / m, k = e - i * m;
       const int row = r0 + i;
-      Bs[i * a.ldB + k] = (row < m && k >= row) ? Rb[(size_t)row * m + k] : 0.0;
+      Bs[i * g.ldB + k] = (row < m && k >= row) ? Rb[(size_t)row * m + k] : 0.0;
     }
     __syncthreads();
-    absorb_block<RPT, kCombineWarps>(Bs, a.ldB, r0, m, Ra, Rs, sc, r0);
+    absorb_block<RPT, kCombineWarps>(Bs, g.ldB, r0, m, Ra, Rs, sc, r0);
   }
 }
 
@@ -342,16 +357,17 @@ constexpr int kMergeThreads = 32 * kMergeWarps;
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
   extern __shared__ double smem[];
-  const int m = a.m;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, rg = tid & 3;
   const int item = blockIdx.x;
   const int sidx = a.item_local[item];
   const int cnt = a.node_nitems[a.item_node[item]];
   const int step = 1 << level;
   if ((sidx & (2 * step - 1)) != 0 || sidx + step >= cnt) return;
-  double* Ra = a.R + (size_t)item * m * m;
-  const double* Rb = a.R + (size_t)(item + step) * m * m;
-  const int ldR = a.ldB;
+  const NodeGeom g = node_geom(a, a.item_node[item]);
+  const int m = g.m;
+  double* Ra = a.R + a.item_roff[item];
+  const double* Rb = a.R + a.item_roff[item + step];
+  const int ldR = g.ldB;
   double* Bp = smem;                                   // R_b, packed by columns
   double* Rs = Bp + ((m * (m + 1) / 2 + 1) & ~1);      // two rows of R_a
   double* sc = Rs + 2 * ldR;                           // reflector scalars of two steps
@@ -475,8 +491,13 @@ size_t merge_smem_bytes(int m) {
 struct BSArgs {
   int64_t n_nodes;
   const int64_t* node_item0;
+  const int64_t* item_roff;
   double* R;
-  int m, q, p, nmono_p;
+  int depth;
+  const int32_t* node_prob;
+  const fmt_problem* prob;
+  int stride;  // coefficients per node (nmono of the largest degree)
+  int ws;      // back-solve workspace per warp (doubles)
   double* coef;
   double* hcoef;
   int32_t* flags;
@@ -614,13 +635,22 @@ __global__ void __launch_bounds__(128) k_backsolve(BSArgs a) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t node = (int64_t)blockIdx.x * 4 + wib;
   if (node >= a.n_nodes) return;
-  const int m = a.m;
-  double* ws = sm + (size_t)wib * backsolve_ws_doubles(m - 1);
-  double* R = a.R + (size_t)a.node_item0[node] * m * m;
-  const int ndrop = backsolve_warp(R, m, a.q, a.p, a.nmono_p, ws, a.coef + (size_t)node * a.nmono_p,
-                                   a.hcoef + (size_t)node * a.nmono_p);
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const int p = pr.degree;
+  const int q = a.depth == 0 ? pr.q_root : p;
+  const int m = fmt_nmono_d(q) + 1;
+  const int nmono_p = fmt_nmono_d(p);
+  double* ws = sm + (size_t)wib * a.ws;
+  double* R = a.R + a.item_roff[a.node_item0[node]];
+  double* cf = a.coef + (size_t)node * a.stride;
+  double* hc = a.hcoef + (size_t)node * a.stride;
+  const int ndrop = backsolve_warp(R, m, q, p, nmono_p, ws, cf, hc);
+  for (int k = nmono_p + lane; k < a.stride; k += 32) {  // lower-degree problems in a forest
+    cf[k] = 0.0;
+    hc[k] = 0.0;
+  }
   if (lane == 0) {
-    a.deg_used[node] = a.q;
+    a.deg_used[node] = q;
     if (ndrop > 0) a.flags[node] |= FMT_FLAG_RANK;
   }
 }
@@ -631,28 +661,31 @@ struct ResArgs {
   const int64_t* item_start;
   const int64_t* item_end;
   const uint64_t* prefix;
+  const int32_t* node_prob;
+  const fmt_problem* prob;
   const double* x;
   const double* y;
   const double* z;
   double* r;
   const double* hcoef;
-  double lo0, lo1, lo2, side;
-  int depth, p, nmono;
+  int depth, stride;
 };
 
 __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   const int item = blockIdx.x;
   const int64_t node = a.item_node[item];
   const int64_t rs = a.item_start[item], re = a.item_end[item];
-  const uint64_t pf = a.prefix[node];
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
-  fmt_frame(a.lo0, a.side, a.depth, fmt_compact3(pf), c0, s0);
-  fmt_frame(a.lo1, a.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
-  fmt_frame(a.lo2, a.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
-  const double* G = a.hcoef + (size_t)node * a.nmono;
+  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  const int p = pr.degree, nm = fmt_nmono_d(p);
+  const double* G = a.hcoef + (size_t)node * a.stride;
   for (int64_t i = rs + threadIdx.x; i < re; i += blockDim.x) {
     const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
-    a.r[i] -= fmt_horner(G, a.p, a.nmono, u, v, w);
+    a.r[i] -= fmt_horner(G, p, nm, u, v, w);
   }
 }
 
@@ -668,6 +701,7 @@ struct ChildArgs {
   double* child_S;
   int64_t* child_n;
   int shift;  // 3*(21-depth-1); < 0 when the node has no child level
+  int depth;
 };
 
 __global__ void __launch_bounds__(256) k_child_bounds(ChildArgs a) {
@@ -684,7 +718,7 @@ __global__ void __launch_bounds__(256) k_child_bounds(ChildArgs a) {
   } else if (o == 8) {
     b = e;
   } else {
-    const uint64_t target = a.prefix[node] * 8ull + (uint64_t)o;
+    const uint64_t target = fmt_morton_part(a.prefix[node], a.depth) * 8ull + (uint64_t)o;
     int64_t lo = s, hi = e;
     while (lo < hi) {
       const int64_t mid = lo + ((hi - lo) >> 1);
@@ -734,11 +768,7 @@ cudaError_t set_smem_attr(size_t smem) {
 // 64-bit shared accesses are served per half-warp (16 lanes = 4 columns x 4
 // row groups); with ldB = 4 (mod 16) doubles the four row groups fall into
 // distinct 32-byte bank segments, so the quads' accesses are conflict free.
-int ld_for(int m) {
-  int ld = m;
-  while ((ld & 15) != 4) ++ld;
-  return ld;
-}
+int ld_for(int m) { return fmt_ld_for(m); }
 
 QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   const fmt_level& L = t->lv[depth];
@@ -749,18 +779,15 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.item_local = L.item_local;
   a.node_nitems = L.node_nitems;
   a.prefix = L.prefix;
+  a.node_prob = L.prob;
+  a.prob = t->d_prob;
   a.x = t->x;
   a.y = t->y;
   a.z = t->z;
   a.r = t->r;
-  a.lo0 = t->P.lo[0];
-  a.lo1 = t->P.lo[1];
-  a.lo2 = t->P.lo[2];
-  a.side = t->P.side;
   a.depth = depth;
-  a.q = L.q;
-  a.m = fmt_nmono(L.q) + 1;
-  a.ldB = ld_for(a.m);
+  a.ld_max = ld_for(L.max_m);
+  a.item_roff = L.item_roff;
   a.R = R;
   a.sched = L.sched;
   a.work = t->d_work;
@@ -806,9 +833,10 @@ cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t
   QRArgs a = make_qr_args(t, depth, R);
   const int64_t n_items = t->lv[depth].n_items;
   if (n_items <= 0) return cudaSuccess;
-  const int rows = qr_rows_per_block(a.m);
-  const size_t smem = qr_smem_bytes(a.m, rows);
-  int64_t grid = qr_resident_ctas(a.m);
+  const int mx = t->lv[depth].max_m;
+  const int rows = qr_rows_per_block(mx);
+  const size_t smem = qr_smem_bytes(mx, rows);
+  int64_t grid = qr_resident_ctas(mx);
   if (grid > n_items) grid = n_items;
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -834,7 +862,8 @@ cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double*
   const int64_t n_items = t->lv[depth].n_items;
   if (n_items <= 1) return cudaSuccess;
   cudaError_t e;
-  const size_t msm = merge_smem_bytes(a.m);
+  const int mx = t->lv[depth].max_m;
+  const size_t msm = merge_smem_bytes(mx);
   if (msm <= 200 * 1024) {
     if ((e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm)) != cudaSuccess)
       return e;
@@ -842,8 +871,8 @@ cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double*
     return cudaGetLastError();
   }
   // large degrees: the packed triangle does not fit; merge in row blocks
-  const int rows = qr_rows_per_block(a.m);
-  const size_t smem = qr_smem_bytes(a.m, rows);
+  const int rows = qr_rows_per_block(mx);
+  const size_t smem = qr_smem_bytes(mx, rows);
   switch (rows) {
     case 64:
       if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;
@@ -867,16 +896,17 @@ cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream
   a.n_nodes = L.n_nodes;
   a.node_item0 = L.node_item0;
   a.R = R;
-  a.m = fmt_nmono(L.q) + 1;
-  a.q = L.q;
-  a.p = t->P.degree;
-  a.nmono_p = t->nmono;
+  a.item_roff = L.item_roff;
+  a.depth = depth;
+  a.node_prob = L.prob;
+  a.prob = t->d_prob;
+  a.stride = t->nmono;
+  a.ws = backsolve_ws_doubles(L.max_m - 1);
   a.coef = L.coef;
   a.hcoef = L.hcoef;
   a.flags = L.flags;
   a.deg_used = L.deg_used;
-  const size_t per_warp = (size_t)backsolve_ws_doubles(a.m - 1) * sizeof(double);
-  const size_t smem = 4 * per_warp;
+  const size_t smem = 4 * (size_t)a.ws * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((L.n_nodes + 3) / 4);
@@ -893,18 +923,15 @@ cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s) {
   a.item_start = L.item_start;
   a.item_end = L.item_end;
   a.prefix = L.prefix;
+  a.node_prob = L.prob;
+  a.prob = t->d_prob;
   a.x = t->x;
   a.y = t->y;
   a.z = t->z;
   a.r = t->r;
   a.hcoef = L.hcoef;
-  a.lo0 = t->P.lo[0];
-  a.lo1 = t->P.lo[1];
-  a.lo2 = t->P.lo[2];
-  a.side = t->P.side;
   a.depth = depth;
-  a.p = t->P.degree;
-  a.nmono = t->nmono;
+  a.stride = t->nmono;
   k_residual<<<(unsigned)L.n_items, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -922,6 +949,7 @@ cudaError_t launch_child_stats(const fmt_tree* t, int depth, cudaStream_t s) {
   a.bounds = L.bounds;
   a.child_S = L.child_S;
   a.child_n = L.child_n;
+  a.depth = depth;
   const int child_depth = depth + 1;
   a.shift = (child_depth <= FMT_QBITS && child_depth <= t->sort_bits / 3) ? 3 * (FMT_QBITS - child_depth) : -1;
   const int64_t nb = L.n_nodes * 9;

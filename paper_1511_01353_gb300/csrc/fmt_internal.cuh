@@ -93,16 +93,52 @@ __device__ __forceinline__ double fmt_horner(const double* __restrict__ G, int p
   return fmt_horner_t<true>(G, p, nmono, u, v, w);
 }
 
+// nmono(p) on the device
+__host__ __device__ __forceinline__ int fmt_nmono_d(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// Shared-memory row pitch of the QR kernels for m columns: the smallest
+// ld >= m with ld = 4 (mod 16) doubles (64-bit accesses are served per
+// half-warp: 4 columns x 4 row groups; this puts the row groups of a quad
+// pattern in distinct 32-byte bank segments).
+__host__ __device__ __forceinline__ int fmt_ld_for(int m) { return m + ((4 - m) & 15); }
+
+// ---------------------------------------------------------------------------
+// A forest holds independent problems; every problem has its own root box,
+// degree and threshold.  Point ranges are in sorted order (problems keep the
+// input order, so these are also the input ranges).
+struct fmt_problem {
+  double lo[3];
+  double side;
+  double S;       // 2^21 / side
+  double tau;     // tol_rel * max |f| over the problem's points
+  double maxabs;
+  int32_t degree; // p
+  int32_t q_root; // root degree after the N < nmono clamp
+  int64_t start, count;
+  int64_t pad_;
+};
+
+// Node keys of a forest: the problem id sits above the 3d Morton bits of a
+// node at depth d, so one sorted array per level covers every problem.
+__host__ __device__ __forceinline__ uint64_t fmt_morton_part(uint64_t key, int depth) {
+  return depth == 0 ? 0ull : (key & ((1ull << (3 * depth)) - 1ull));
+}
+__host__ __device__ __forceinline__ int fmt_problem_of(uint64_t key, int depth) {
+  return (int)(key >> (3 * depth));
+}
+
 // ---------------------------------------------------------------------------
 // One octree level as stored on the device (structure of arrays).
 struct fmt_level {
   // host-side copies of the sizes
   int64_t n_nodes = 0, cap_nodes = 0;
   int64_t n_items = 0, cap_items = 0, max_chunks = 0, chunk_rows = 0, n_points = 0;
-  int32_t q = 0;  // degree used by this level's fit (root may be clamped)
+  int32_t max_m = 0;  // largest nmono + 1 among this level's nodes
+  double qr_flops = 0.0, horner_flops = 0.0;  // algorithmic flops of the level's fit
   bool fitted = false;
   // nodes
-  uint64_t* prefix = nullptr;  // Morton prefix (code >> 3(21-d))
+  uint64_t* prefix = nullptr;  // (problem << 3d) | Morton prefix (code >> 3(21-d))
+  int32_t* prob = nullptr;     // problem of the node
   int64_t* start = nullptr;
   int64_t* count = nullptr;
   int32_t* flags = nullptr;
@@ -122,24 +158,34 @@ struct fmt_level {
   int64_t* item_end = nullptr;
   int32_t* item_local = nullptr;  // chunk index inside its node
   int32_t* sched = nullptr;       // item order for the QR queue (largest first)
+  int64_t* item_roff = nullptr;   // offset of the item's m x m triangle in the QR scratch
+  int64_t r_total = 0;            // doubles of QR scratch the level needs
 };
 
 // Small result block that refine reads back in one copy.
 struct fmt_plan_out {
   int64_t n_new, n_items, max_chunks, chunk_rows, n_points, n_near, err;
+  int64_t max_m;       // largest nmono + 1 among the planned nodes
+  double qr_flops;     // sum over nodes of rows x 2 m^2 (Householder on [Lambda | r])
+  double horner_flops; // sum over nodes of rows x Horner flops of the node degree
+  int64_t r_total;     // doubles of QR scratch: sum over items of m^2
   int64_t pad_;
 };
 
 struct fmt_tree {
-  fmt_params P{};
-  int32_t nmono = 0;
+  fmt_params P{};   // shared parameters (degree and box of problem 0 when P == 1)
+  int32_t nmono = 0;       // coefficient stride: nmono of the largest degree
+  int32_t max_degree = 0;
   int64_t n = 0;
+  int64_t n_problems = 1;
   bool imported = false;
   int device = 0;
   cudaStream_t stream = nullptr;  // last stream used (for the final free)
-  double tau = 0.0, maxabs = 0.0;
-  double S = 0.0;  // 2^21 / side
-  int sort_bits = 0;
+  double tau = 0.0, maxabs = 0.0; // problem 0 (single-problem trees)
+  int sort_bits = 0;       // Morton bits in the sort key (3 per sorted level)
+  int pid_bits = 0;        // problem-id bits above them
+  fmt_problem* d_prob = nullptr;  // device table
+  fmt_problem* h_prob = nullptr;  // host copy
   // sorted point data
   double *x = nullptr, *y = nullptr, *z = nullptr, *r = nullptr;
   uint64_t* code = nullptr;
@@ -156,6 +202,7 @@ struct fmt_tree {
   int* d_err = nullptr;
   fmt_plan_out* d_plan = nullptr;
   fmt_plan_out* h_plan = nullptr;  // pinned
+  int* h_err = nullptr;            // pinned
   unsigned long long* d_counter = nullptr;
   int* d_work = nullptr;  // work-queue counter of the persistent QR kernel
   int64_t chunk_floor = 64;
@@ -174,18 +221,18 @@ fmt_status fmt_set_error(fmt_status st, const char* msg);
 
 // build
 cudaError_t launch_check_maxabs(int64_t n, const double* x, const double* y, const double* z,
-                                const double* f, unsigned long long* d_maxbits, int* d_err,
-                                cudaStream_t s);
-cudaError_t launch_morton(int64_t n, const double* x, const double* y, const double* z, double lo0,
-                          double lo1, double lo2, double S, int sort_shift, bool key64, void* keys,
-                          uint32_t* vals, cudaStream_t s);
+                                const double* f, const fmt_problem* prob, int P, unsigned long long* d_maxbits,
+                                int* d_err, cudaStream_t s);
+cudaError_t launch_morton(int64_t n, const double* x, const double* y, const double* z, const fmt_problem* prob,
+                          int P, int sort_shift, int sort_bits, bool key64, void* keys, uint32_t* vals,
+                          cudaStream_t s);
 size_t radix_sort_temp_bytes(int64_t n, bool key64);
 cudaError_t launch_radix_sort(int64_t n, int bits, bool key64, void* keys, uint32_t* vals, void* keys_alt,
                               uint32_t* vals_alt, void* temp, void** keys_out, uint32_t** vals_out,
                               cudaStream_t s);
 cudaError_t launch_gather(int64_t n, const uint32_t* perm, const double* x, const double* y,
-                          const double* z, const double* f, double lo0, double lo1, double lo2, double S,
-                          double* xs, double* ys, double* zs, double* rs, uint64_t* code, cudaStream_t s);
+                          const double* z, const double* f, const fmt_problem* prob, int P, double* xs, double* ys,
+                          double* zs, double* rs, uint64_t* code, cudaStream_t s);
 cudaError_t launch_plan_root(const fmt_tree* t, int64_t chunk_rows_fixed, int64_t chunk_floor,
                              fmt_plan_out* d_plan, cudaStream_t s);
 
@@ -202,8 +249,8 @@ cudaError_t launch_child_stats(const fmt_tree* t, int depth, cudaStream_t s);
 // refine / evaluate
 cudaError_t launch_refine(const fmt_tree* t, int depth, int64_t chunk_rows_fixed, int64_t chunk_floor,
                           fmt_plan_out* d_plan, cudaStream_t s);
-cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const double* xq, const double* yq,
-                            const double* zq, double* out, unsigned long long* d_outside,
+cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, const double* xq,
+                            const double* yq, const double* zq, double* out, unsigned long long* d_outside,
                             cudaStream_t s);
 cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream_t s);
-cudaError_t launch_make_hcoef(int64_t n, int p, int nmono, const double* coef, double* hcoef, cudaStream_t s);
+cudaError_t launch_make_hcoef(const fmt_tree* t, int depth, cudaStream_t s);

@@ -62,7 +62,28 @@ struct PlanArgs {
   int64_t* item_end;
   int32_t* item_local;
   int32_t* sched;
+  int64_t* item_roff;
+  const int32_t* node_prob;
+  const fmt_problem* prob;
+  int depth;
 };
+
+__device__ __forceinline__ double horner_flops_d(int p) {
+  return 2.0 * ((double)fmt_nmono_d(p) + (p + 1) * (p + 2) / 2.0 + (p + 1));
+}
+
+template <typename T>
+__device__ T block_sum(T v) {
+  __shared__ T ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  T r = ws[0];
+  for (int w = 1; w < nw; ++w) r += ws[w];
+  __syncthreads();
+  return r;
+}
 
 // Split every node into ceil(count / C) nearly equal row chunks.
 __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
@@ -111,18 +132,29 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  int64_t maxc = 0;
+  int64_t maxc = 0, maxm = 0;
+  double qrf = 0.0, hf = 0.0;
+  __shared__ int64_t rcarry;
+  if (threadIdx.x == 0) rcarry = 0;
+  __syncthreads();
   for (int64_t b = 0; b < a.n_nodes; b += blockDim.x) {
     const int64_t node = b + threadIdx.x;
-    int64_t nch = 0, cnt = 0, st = 0;
+    int64_t nch = 0, cnt = 0, st = 0, m = 0;
     if (node < a.n_nodes) {
       cnt = a.count[node];
       st = a.start[node];
       nch = (cnt + C - 1) / C;
       if (nch < 1) nch = 1;
+      const fmt_problem& pr = a.prob[a.node_prob[node]];
+      const int q = a.depth == 0 ? pr.q_root : pr.degree;
+      m = fmt_nmono_d(q) + 1;
+      maxm = m > maxm ? m : maxm;
+      qrf += 2.0 * (double)m * (double)m * (double)cnt;
+      hf += horner_flops_d(pr.degree) * (double)cnt;
     }
-    int64_t tot;
+    int64_t tot, rtot;
     const int64_t ex = block_exscan<int64_t>(nch, &tot);
+    const int64_t rex = block_exscan<int64_t>(nch * m * m, &rtot);
     if (node < a.n_nodes) {
       const int64_t i0 = carry + ex;
       a.node_item0[node] = i0;
@@ -135,15 +167,22 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
           a.item_start[i0 + c] = st + (cnt * c) / nch;
           a.item_end[i0 + c] = st + (cnt * (c + 1)) / nch;
           a.item_local[i0 + c] = (int32_t)c;
+          a.item_roff[i0 + c] = rcarry + rex + c * m * m;
         }
       }
       maxc = nch > maxc ? nch : maxc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
+    if (threadIdx.x == 0) {
+      carry += tot;
+      rcarry += rtot;
+    }
     __syncthreads();
   }
   maxc = block_max<int64_t>(maxc);
+  maxm = block_max<int64_t>(maxm);
+  qrf = block_sum<double>(qrf);
+  hf = block_sum<double>(hf);
   // Queue order for the QR kernel: items bucketed by floor(log2(rows)),
   // largest bucket first (order inside a bucket does not matter: every item
   // writes its own triangle).
@@ -175,21 +214,30 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
   }
   if (threadIdx.x == 0) {
     out->n_items = carry;
+    out->r_total = rcarry;
     out->max_chunks = maxc;
+    out->max_m = maxm;
+    out->qr_flops = qrf;
+    out->horner_flops = hf;
     out->chunk_rows = C;
     out->n_points = a.total_points;
   }
 }
 
-__global__ void __launch_bounds__(kPlanThreads) k_plan_root(PlanArgs a, uint64_t* prefix, int64_t* start,
-                                                            int64_t* count, int32_t* flags, int32_t root_flags,
-                                                            fmt_plan_out* out, int* err) {
+// One root per problem: node i covers problem i's points.
+__global__ void __launch_bounds__(kPlanThreads) k_plan_root(PlanArgs a, const fmt_problem* __restrict__ prob,
+                                                            uint64_t* prefix, int64_t* start, int64_t* count,
+                                                            int32_t* flags, int32_t* node_prob, fmt_plan_out* out,
+                                                            int* err) {
+  for (int64_t i = threadIdx.x; i < a.n_nodes; i += blockDim.x) {
+    prefix[i] = (uint64_t)i;
+    start[i] = prob[i].start;
+    count[i] = prob[i].count;
+    flags[i] = prob[i].q_root != prob[i].degree ? FMT_FLAG_DEG_CLAMPED : 0;
+    node_prob[i] = (int32_t)i;
+  }
   if (threadIdx.x == 0) {
-    prefix[0] = 0;
-    start[0] = 0;
-    count[0] = a.total_points;
-    flags[0] = root_flags;
-    out->n_new = 1;
+    out->n_new = a.n_nodes;
     out->n_near = 0;
   }
   __syncthreads();
@@ -198,8 +246,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_root(PlanArgs a, uint64_t
 
 struct RefineArgs {
   int64_t n_nodes;
-  double tau;
-  int64_t nmin;
+  const fmt_problem* prob;
+  const int32_t* node_prob;
+  int32_t* nprob;
+  int min_pts;
   int deep_ok;
   const uint64_t* prefix;
   const int64_t* bounds;
@@ -229,14 +279,21 @@ __global__ void __launch_bounds__(kPlanThreads) k_refine(RefineArgs r, PlanArgs 
     const int64_t node = b + threadIdx.x;
     int64_t cnt = 0, npt = 0, nn = 0;
     unsigned rmask = 0, nmask = 0;
+    int pid = 0;
     if (node < r.n_nodes) {
+      pid = r.node_prob[node];
+      const fmt_problem& pr = r.prob[pid];
+      const double tau = pr.tau;
+      int64_t nmin = fmt_nmono_d(pr.degree);
+      if (r.min_pts > nmin) nmin = r.min_pts;
+      if (nmin < 1) nmin = 1;
       for (int o = 0; o < 8; ++o) {
         const int64_t no = r.child_n[node * 8 + o];
         const double E = no > 0 ? sqrt(r.child_S[node * 8 + o] / (double)no) : 0.0;
         r.child_E[node * 8 + o] = E;
-        const bool ok = r.deep_ok && no > 0 && no >= r.nmin;
-        if (ok && fabs(E - r.tau) <= 1e-9 * r.tau) nmask |= 1u << o;
-        if (ok && E > r.tau) {
+        const bool ok = r.deep_ok && no > 0 && no >= nmin;
+        if (ok && fabs(E - tau) <= 1e-9 * tau) nmask |= 1u << o;
+        if (ok && E > tau) {
           rmask |= 1u << o;
           ++cnt;
           npt += no;
@@ -263,6 +320,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_refine(RefineArgs r, PlanArgs 
         r.nstart[idx] = r.bounds[node * 9 + o];
         r.ncount[idx] = r.child_n[node * 8 + o];
         r.nflags[idx] = (nmask & (1u << o)) ? FMT_FLAG_NEAR_TAU : 0;
+        r.nprob[idx] = pid;
         ++idx;
       }
     }
@@ -285,6 +343,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_refine(RefineArgs r, PlanArgs 
       out->max_chunks = 0;
       out->chunk_rows = 0;
       out->n_points = pts;
+      out->max_m = 0;
+      out->qr_flops = 0.0;
+      out->horner_flops = 0.0;
+      out->r_total = 0;
     }
     return;
   }
@@ -295,8 +357,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_refine(RefineArgs r, PlanArgs 
 
 // ---------------------------------------------------------------- evaluate
 struct EvalArgs {
-  int n_levels, p, nmono;
-  double lo0, lo1, lo2, side, S, hi0, hi1, hi2;
+  int n_levels, stride;
+  int n_problems;
+  const fmt_problem* prob;
+  const int32_t* tprob;  // problem of each target, or NULL (problem 0)
   const uint64_t* prefix[FMT_MAX_DEPTH + 1];
   const double* hcoef[FMT_MAX_DEPTH + 1];
   int64_t n_nodes[FMT_MAX_DEPTH + 1];
@@ -304,7 +368,8 @@ struct EvalArgs {
 
 __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const double* __restrict__ xq,
                                                   const double* __restrict__ yq, const double* __restrict__ zq,
-                                                  double* __restrict__ out, unsigned long long* outside) {
+                                                  double* __restrict__ out, unsigned long long* outside,
+                                                  int* err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t last = ((m + stride - 1) / stride) * stride;  // uniform trip count for the ballot
@@ -312,27 +377,37 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
     const bool valid = t < m;
     bool outs = false;
     if (valid) {
+      int pid = a.tprob ? a.tprob[t] : 0;
+      if (pid < 0 || pid >= a.n_problems) {
+        atomicOr(err, FMT_ERR_INDEX);
+        pid = 0;
+      }
+      const fmt_problem& pr = a.prob[pid];
       const double x = xq[t], y = yq[t], z = zq[t];
-      outs = !(x >= a.lo0 && x <= a.hi0 && y >= a.lo1 && y <= a.hi1 && z >= a.lo2 && z <= a.hi2);
-      const uint64_t code = fmt_spread3(fmt_quant(x, a.lo0, a.S)) | (fmt_spread3(fmt_quant(y, a.lo1, a.S)) << 1) |
-                            (fmt_spread3(fmt_quant(z, a.lo2, a.S)) << 2);
+      const double hi0 = pr.lo[0] + pr.side, hi1 = pr.lo[1] + pr.side, hi2 = pr.lo[2] + pr.side;
+      outs = !(x >= pr.lo[0] && x <= hi0 && y >= pr.lo[1] && y <= hi1 && z >= pr.lo[2] && z <= hi2);
+      const uint64_t code = fmt_spread3(fmt_quant(x, pr.lo[0], pr.S)) |
+                            (fmt_spread3(fmt_quant(y, pr.lo[1], pr.S)) << 1) |
+                            (fmt_spread3(fmt_quant(z, pr.lo[2], pr.S)) << 2);
+      const int p = pr.degree, nm = fmt_nmono_d(p);
       double acc = 0.0;
       for (int d = 0; d < a.n_levels; ++d) {
-        const uint64_t P = d == 0 ? 0ull : (code >> (3 * (FMT_QBITS - d)));
-        const uint64_t* pr = a.prefix[d];
+        const uint64_t mp = d == 0 ? 0ull : (code >> (3 * (FMT_QBITS - d)));
+        const uint64_t P = ((uint64_t)pid << (3 * d)) | mp;
+        const uint64_t* pr_ = a.prefix[d];
         int64_t lo = 0, hi = a.n_nodes[d];
         while (lo < hi) {
           const int64_t mid = lo + ((hi - lo) >> 1);
-          if (pr[mid] < P) lo = mid + 1;
+          if (pr_[mid] < P) lo = mid + 1;
           else hi = mid;
         }
-        if (lo >= a.n_nodes[d] || pr[lo] != P) break;
+        if (lo >= a.n_nodes[d] || pr_[lo] != P) break;
         double c0, s0, c1, s1, c2, s2;
-        fmt_frame(a.lo0, a.side, d, fmt_compact3(P), c0, s0);
-        fmt_frame(a.lo1, a.side, d, fmt_compact3(P >> 1), c1, s1);
-        fmt_frame(a.lo2, a.side, d, fmt_compact3(P >> 2), c2, s2);
-        acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.nmono, a.p, a.nmono, fmt_local(x, c0, s0),
-                          fmt_local(y, c1, s1), fmt_local(z, c2, s2));
+        fmt_frame(pr.lo[0], pr.side, d, fmt_compact3(mp), c0, s0);
+        fmt_frame(pr.lo[1], pr.side, d, fmt_compact3(mp >> 1), c1, s1);
+        fmt_frame(pr.lo[2], pr.side, d, fmt_compact3(mp >> 2), c2, s2);
+        acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.stride, p, nm, fmt_local(x, c0, s0), fmt_local(y, c1, s1),
+                          fmt_local(z, c2, s2));
       }
       out[t] = acc;
     }
@@ -341,11 +416,20 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
   }
 }
 
-__global__ void k_make_hcoef(int64_t n, int p, int nmono, const double* __restrict__ coef,
+// F / (l! m! n!) for imported trees (node degree from its problem; entries
+// past the problem's nmono are zero)
+__global__ void k_make_hcoef(int64_t n, int stride, const int32_t* __restrict__ node_prob,
+                             const fmt_problem* __restrict__ prob, const double* __restrict__ coef,
                              double* __restrict__ hcoef) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * nmono) return;
-  int k = (int)(i % nmono);
+  if (i >= n * stride) return;
+  const int64_t node = i / stride;
+  const int p = prob[node_prob[node]].degree;
+  int k = (int)(i - node * stride);
+  if (k >= fmt_nmono_d(p)) {
+    hcoef[i] = 0.0;
+    return;
+  }
   int l = 0;
   while (k >= (p - l + 1) * (p - l + 2) / 2) {
     k -= (p - l + 1) * (p - l + 2) / 2;
@@ -385,7 +469,7 @@ PlanArgs plan_args_for(const fmt_tree* t, const fmt_level& L, int64_t chunk_fixe
   a.total_points = 0;
   a.chunk_fixed = chunk_fixed;
   a.chunk_floor = chunk_floor;
-  a.nsm = qr_resident_ctas(fmt_nmono(L.q > 0 ? L.q : t->P.degree) + 1);
+  a.nsm = qr_resident_ctas(L.max_m > 0 ? L.max_m : fmt_nmono(t->max_degree) + 1);
   a.cap_items = L.cap_items;
   a.node_item0 = L.node_item0;
   a.node_nitems = L.node_nitems;
@@ -394,6 +478,10 @@ PlanArgs plan_args_for(const fmt_tree* t, const fmt_level& L, int64_t chunk_fixe
   a.item_end = L.item_end;
   a.item_local = L.item_local;
   a.sched = L.sched;
+  a.item_roff = L.item_roff;
+  a.node_prob = L.prob;
+  a.prob = t->d_prob;
+  a.depth = 0;
   return a;
 }
 
@@ -403,10 +491,10 @@ cudaError_t launch_plan_root(const fmt_tree* t, int64_t chunk_rows_fixed, int64_
                              fmt_plan_out* d_plan, cudaStream_t s) {
   const fmt_level& L = t->lv[0];
   PlanArgs a = plan_args_for(t, L, chunk_rows_fixed, chunk_floor);
-  a.n_nodes = 1;
+  a.n_nodes = t->n_problems;
   a.total_points = t->n;
-  const int32_t rf = (L.q != t->P.degree) ? FMT_FLAG_DEG_CLAMPED : 0;
-  k_plan_root<<<1, kPlanThreads, 0, s>>>(a, L.prefix, L.start, L.count, L.flags, rf, d_plan, t->d_err);
+  k_plan_root<<<1, kPlanThreads, 0, s>>>(a, t->d_prob, L.prefix, L.start, L.count, L.flags, L.prob, d_plan,
+                                         t->d_err);
   return cudaGetLastError();
 }
 
@@ -416,9 +504,10 @@ cudaError_t launch_refine(const fmt_tree* t, int depth, int64_t chunk_rows_fixed
   const fmt_level& N = t->lv[depth + 1 <= FMT_MAX_DEPTH ? depth + 1 : depth];
   RefineArgs r;
   r.n_nodes = L.n_nodes;
-  r.tau = t->tau;
-  int64_t nmin = t->P.min_pts > t->nmono ? t->P.min_pts : t->nmono;
-  r.nmin = nmin < 1 ? 1 : nmin;
+  r.prob = t->d_prob;
+  r.node_prob = L.prob;
+  r.nprob = N.prob;
+  r.min_pts = t->P.min_pts;
   r.deep_ok = (depth + 1 <= t->P.max_depth && depth + 1 <= FMT_MAX_DEPTH) ? 1 : 0;
   r.prefix = L.prefix;
   r.bounds = L.bounds;
@@ -432,27 +521,22 @@ cudaError_t launch_refine(const fmt_tree* t, int depth, int64_t chunk_rows_fixed
   r.ncount = N.count;
   r.nflags = N.flags;
   PlanArgs a = plan_args_for(t, N, chunk_rows_fixed, chunk_floor);
+  a.depth = depth + 1;
   k_refine<<<1, kPlanThreads, 0, s>>>(r, a, d_plan, t->d_err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const double* xq, const double* yq,
-                            const double* zq, double* out, unsigned long long* d_outside,
+cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, const double* xq,
+                            const double* yq, const double* zq, double* out, unsigned long long* d_outside,
                             cudaStream_t s) {
   EvalArgs a;
   int nf = 0;
   while (nf < t->n_levels && t->lv[nf].fitted) ++nf;
   a.n_levels = nf;
-  a.p = t->P.degree;
-  a.nmono = t->nmono;
-  a.lo0 = t->P.lo[0];
-  a.lo1 = t->P.lo[1];
-  a.lo2 = t->P.lo[2];
-  a.side = t->P.side;
-  a.S = t->S;
-  a.hi0 = t->P.lo[0] + t->P.side;
-  a.hi1 = t->P.lo[1] + t->P.side;
-  a.hi2 = t->P.lo[2] + t->P.side;
+  a.stride = t->nmono;
+  a.n_problems = (int)t->n_problems;
+  a.prob = t->d_prob;
+  a.tprob = tprob;
   for (int d = 0; d <= FMT_MAX_DEPTH; ++d) {
     a.prefix[d] = d < nf ? t->lv[d].prefix : nullptr;
     a.hcoef[d] = d < nf ? t->lv[d].hcoef : nullptr;
@@ -461,14 +545,16 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const double* xq, cons
   int64_t blocks = (m + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
-  k_evaluate<<<(unsigned)blocks, 256, 0, s>>>(a, m, xq, yq, zq, out, d_outside);
+  k_evaluate<<<(unsigned)blocks, 256, 0, s>>>(a, m, xq, yq, zq, out, d_outside, t->d_err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_make_hcoef(int64_t n, int p, int nmono, const double* coef, double* hcoef, cudaStream_t s) {
-  const int64_t tot = n * nmono;
+cudaError_t launch_make_hcoef(const fmt_tree* t, int depth, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  const int64_t tot = L.n_nodes * t->nmono;
   if (tot <= 0) return cudaSuccess;
-  k_make_hcoef<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, p, nmono, coef, hcoef);
+  k_make_hcoef<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.n_nodes, t->nmono, L.prob, t->d_prob, L.coef,
+                                                             L.hcoef);
   return cudaGetLastError();
 }
 

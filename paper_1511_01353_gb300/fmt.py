@@ -44,7 +44,7 @@ _NL = MAX_DEPTH + 1
 
 class fmt_stats(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int32), ("nmono", ctypes.c_int32), ("max_depth", ctypes.c_int32),
-                ("n_levels", ctypes.c_int32), ("n_fitted", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("n_fitted", ctypes.c_int32), ("n_problems", ctypes.c_int32),
                 ("n_points", ctypes.c_int64), ("tau", ctypes.c_double), ("maxabs_f", ctypes.c_double),
                 ("nodes", ctypes.c_int64 * _NL), ("points", ctypes.c_int64 * _NL),
                 ("items", ctypes.c_int64 * _NL), ("chunk_rows", ctypes.c_int64 * _NL),
@@ -55,12 +55,13 @@ class fmt_export_header(ctypes.Structure):
     _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32), ("degree", ctypes.c_int32),
                 ("nmono", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("min_pts", ctypes.c_int32),
                 ("n_levels", ctypes.c_int32), ("n_fitted", ctypes.c_int32), ("has_points", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("tol_rel", ctypes.c_double), ("tau", ctypes.c_double),
+                ("n_problems", ctypes.c_int32), ("tol_rel", ctypes.c_double), ("tau", ctypes.c_double),
                 ("maxabs_f", ctypes.c_double), ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("n_points", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("level_nodes", ctypes.c_int64 * _NL)]
 
 
-EXPORTED = ["fmt_nmono", "oct_build", "fit_level", "refine", "evaluate", "fmt_tree_stats", "fmt_tree_export",
+EXPORTED = ["fmt_nmono", "oct_build", "oct_build_batch", "fit_level", "refine", "evaluate", "evaluate_batch",
+            "fmt_tree_stats", "fmt_tree_export",
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
             "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static"]
 STATIC_MAX_DEGREE = 8
@@ -98,6 +99,10 @@ def load(build: bool = True):
         L.refine.restype = ctypes.c_int
         L.evaluate.argtypes = [P, i64, P, P, P, P, ctypes.POINTER(i64), P]
         L.evaluate.restype = ctypes.c_int
+        L.oct_build_batch.argtypes = [ctypes.POINTER(fmt_params), i64, P, P, P, P, P, P, P, P, ctypes.POINTER(P)]
+        L.oct_build_batch.restype = ctypes.c_int
+        L.evaluate_batch.argtypes = [P, i64, P, P, P, P, P, ctypes.POINTER(i64), P]
+        L.evaluate_batch.restype = ctypes.c_int
         L.fmt_tree_stats.argtypes = [P, ctypes.POINTER(fmt_stats)]
         L.fmt_tree_stats.restype = ctypes.c_int
         L.fmt_tree_export.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
@@ -188,6 +193,23 @@ def oct_build(params: fmt_params, x, y, z, f, stream=None) -> Tree:
     return Tree(h)
 
 
+def oct_build_batch(params: fmt_params, offsets, x, y, z, f, degrees=None, boxes=None, stream=None) -> Tree:
+    """Forest of independent problems: offsets (n_problems+1, host), per-problem
+    degrees (host int32) and boxes (host, 4 per problem: lo x, lo y, lo z, side)."""
+    L = load()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    deg = None if degrees is None else np.ascontiguousarray(degrees, dtype=np.int32)
+    box = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1)
+    h = ctypes.c_void_p()
+    st = L.oct_build_batch(ctypes.byref(params), int(off.shape[0] - 1), off.ctypes.data_as(ctypes.c_void_p),
+                           None if deg is None else deg.ctypes.data_as(ctypes.c_void_p),
+                           None if box is None else box.ctypes.data_as(ctypes.c_void_p),
+                           _dptr(x, "x"), _dptr(y, "y"), _dptr(z, "z"), _dptr(f, "f"), _stream_handle(stream),
+                           ctypes.byref(h))
+    _check(st)
+    return Tree(h)
+
+
 def fit_level(tree: Tree, depth: int, stream=None):
     _check(load().fit_level(tree.handle, depth, _stream_handle(stream)), tree)
 
@@ -203,6 +225,21 @@ def evaluate(tree: Tree, xq, yq, zq, out, count_outside=False, stream=None):
     nout = ctypes.c_int64(0)
     st = load().evaluate(tree.handle, m, _dptr(xq, "xq"), _dptr(yq, "yq"), _dptr(zq, "zq"), _dptr(out, "out"),
                          ctypes.byref(nout) if count_outside else None, _stream_handle(stream))
+    _check(st, tree)
+    return int(nout.value) if count_outside else None
+
+
+def evaluate_batch(tree: Tree, target_problem, xq, yq, zq, out, count_outside=False, stream=None):
+    """target_problem: int32 CUDA tensor with the problem index of every target."""
+    import torch
+    if not (isinstance(target_problem, torch.Tensor) and target_problem.is_cuda and
+            target_problem.dtype == torch.int32 and target_problem.is_contiguous()):
+        raise TypeError("target_problem must be a contiguous int32 CUDA tensor")
+    m = int(xq.numel())
+    nout = ctypes.c_int64(0)
+    st = load().evaluate_batch(tree.handle, m, ctypes.c_void_p(target_problem.data_ptr()), _dptr(xq, "xq"),
+                               _dptr(yq, "yq"), _dptr(zq, "zq"), _dptr(out, "out"),
+                               ctypes.byref(nout) if count_outside else None, _stream_handle(stream))
     _check(st, tree)
     return int(nout.value) if count_outside else None
 
@@ -291,10 +328,9 @@ def fmt_last_error(tree: Tree | None = None) -> str:
 
 
 # ----------------------------------------------------------------- helpers
-def fit(params: fmt_params, x, y, z, f, stream=None) -> Tree:
-    """The driver loop of the four calls: oct_build; for depth 0, 1, ...:
-    fit_level, then refine until it creates no node."""
-    tree = oct_build(params, x, y, z, f, stream)
+def fit_all(tree: Tree, stream=None) -> Tree:
+    """The driver loop after oct_build: for depth 0, 1, ...: fit_level, then
+    refine until it creates no node."""
     d = 0
     while True:
         fit_level(tree, d, stream)
@@ -304,10 +340,15 @@ def fit(params: fmt_params, x, y, z, f, stream=None) -> Tree:
     return tree
 
 
+def fit(params: fmt_params, x, y, z, f, stream=None) -> Tree:
+    """oct_build followed by the driver loop of fit_level / refine."""
+    return fit_all(oct_build(params, x, y, z, f, stream), stream)
+
+
 @dataclasses.dataclass
 class ExportedTree:
     header: dict
-    prefix: np.ndarray
+    prefix: np.ndarray      # node keys: problem << 3*depth | Morton prefix
     start: np.ndarray
     count: np.ndarray
     depth: np.ndarray
@@ -315,20 +356,30 @@ class ExportedTree:
     deg_used: np.ndarray
     refine_mask: np.ndarray
     near_mask: np.ndarray
+    problem: np.ndarray
     child_E: np.ndarray
     child_n: np.ndarray
     coef: np.ndarray
+    problems: dict          # degree, q_root, tau, maxabs, lo [P,3], side, start, count
     code: np.ndarray | None
     perm: np.ndarray | None
     resid: np.ndarray | None
 
+    def morton_prefix(self):
+        """Node keys with the problem bits removed."""
+        d = self.depth.astype(np.uint64)
+        mask = np.where(d > 0, (np.uint64(1) << (np.uint64(3) * d)) - np.uint64(1), np.uint64(0))
+        return self.prefix & mask
+
 
 def parse_export(blob: bytes) -> ExportedTree:
     H = fmt_export_header.from_buffer_copy(blob[:ctypes.sizeof(fmt_export_header)])
+    if H.magic != 0x32544D46 or H.version != 2:
+        raise ValueError("not an FMT2 blob")
     hdr = {name: getattr(H, name) for name, _ in fmt_export_header._fields_}
     hdr["lo"] = tuple(H.lo)
     hdr["level_nodes"] = list(H.level_nodes)
-    K, nm, N = H.n_nodes, H.nmono, H.n_points if H.has_points else 0
+    K, nm, N, P = H.n_nodes, H.nmono, H.n_points if H.has_points else 0, H.n_problems
     off = ctypes.sizeof(fmt_export_header)
 
     def take(dtype, count):
@@ -344,30 +395,37 @@ def parse_export(blob: bytes) -> ExportedTree:
     flags = take(np.int32, K)
     deg = take(np.int32, K)
     masks = take(np.int32, K)
+    prob = take(np.int32, K)
+    take(np.int32, K)
     cE = take(np.float64, 8 * K).reshape(K, 8)
     cn = take(np.int64, 8 * K).reshape(K, 8)
     coef = take(np.float64, nm * K).reshape(K, nm)
+    problems = dict(degree=take(np.int32, P), q_root=take(np.int32, P), tau=take(np.float64, P),
+                    maxabs=take(np.float64, P), lo=take(np.float64, 3 * P).reshape(P, 3), side=take(np.float64, P),
+                    start=take(np.int64, P), count=take(np.int64, P))
     code = perm = resid = None
     if H.has_points:
         code = take(np.uint64, N)
         perm = take(np.int64, N)
         resid = take(np.float64, N)
-    return ExportedTree(hdr, prefix, start, count, depth, flags, deg, masks & 0xFF, (masks >> 8) & 0xFF, cE, cn,
-                        coef, code, perm, resid)
+    return ExportedTree(hdr, prefix, start, count, depth, flags, deg, masks & 0xFF, (masks >> 8) & 0xFF, prob, cE,
+                        cn, coef, problems, code, perm, resid)
 
 
 def build_export(header: dict, prefix, depth, flags, deg_used, child_E, child_n, coef, start=None, count=None,
                  refine_mask=None, near_mask=None) -> bytes:
-    """Serialise node arrays into an FMT1 blob (no per-point arrays), e.g. to
-    upload a tree built elsewhere for evaluation through fmt_tree_import."""
+    """Serialise the node arrays of a single-problem tree into an FMT2 blob (no
+    per-point arrays), e.g. to upload a tree built elsewhere for evaluation
+    through fmt_tree_import.  prefix holds Morton prefixes (problem 0)."""
     K = int(prefix.shape[0])
     H = fmt_export_header()
-    H.magic, H.version = 0x31544D46, 1
+    H.magic, H.version = 0x32544D46, 2
     H.degree, H.nmono = header["degree"], header["nmono"]
     H.max_depth, H.min_pts = header["max_depth"], header["min_pts"]
     lv = np.bincount(np.asarray(depth, dtype=np.int64), minlength=1)
     H.n_levels = H.n_fitted = int(lv.shape[0])
     H.has_points = 0
+    H.n_problems = 1
     H.tol_rel, H.tau, H.maxabs_f = header["tol_rel"], header["tau"], header["maxabs_f"]
     for a in range(3):
         H.lo[a] = header["lo"][a]
@@ -377,13 +435,20 @@ def build_export(header: dict, prefix, depth, flags, deg_used, child_E, child_n,
     for d in range(lv.shape[0]):
         H.level_nodes[d] = int(lv[d])
     z64 = np.zeros(K, np.int64)
-    rm = np.zeros(K, np.int32) if refine_mask is None else np.asarray(refine_mask, np.int32)
-    nm_ = np.zeros(K, np.int32) if near_mask is None else np.asarray(near_mask, np.int32)
+    z32 = np.zeros(K, np.int32)
+    rm = z32 if refine_mask is None else np.asarray(refine_mask, np.int32)
+    nm_ = z32 if near_mask is None else np.asarray(near_mask, np.int32)
+    n_pts = int(header.get("n_points", 0))
     parts = [bytes(H), np.asarray(prefix, np.uint64).tobytes(),
              (z64 if start is None else np.asarray(start, np.int64)).tobytes(),
              (z64 if count is None else np.asarray(count, np.int64)).tobytes(),
              np.asarray(depth, np.int32).tobytes(), np.asarray(flags, np.int32).tobytes(),
              np.asarray(deg_used, np.int32).tobytes(), (rm | (nm_ << 8)).astype(np.int32).tobytes(),
+             z32.tobytes(), z32.tobytes(),
              np.asarray(child_E, np.float64).tobytes(), np.asarray(child_n, np.int64).tobytes(),
-             np.asarray(coef, np.float64).tobytes()]
+             np.asarray(coef, np.float64).tobytes(),
+             np.array([header["degree"]], np.int32).tobytes(), np.array([header["degree"]], np.int32).tobytes(),
+             np.array([header["tau"]], np.float64).tobytes(), np.array([header["maxabs_f"]], np.float64).tobytes(),
+             np.asarray(header["lo"], np.float64).tobytes(), np.array([header["side"]], np.float64).tobytes(),
+             np.array([0], np.int64).tobytes(), np.array([n_pts], np.int64).tobytes()]
     return b"".join(parts)

@@ -194,3 +194,99 @@ def errors(pred, truth):
     if d.size == 0:
         return 0.0, 0.0
     return float(np.sqrt(np.mean(d * d))), float(np.max(np.abs(d)))
+
+
+@dataclasses.dataclass
+class Batch:
+    """Many independent problems, concatenated (problem i owns offsets[i] ..
+    offsets[i+1]-1 of the point arrays and toff[i] .. toff[i+1]-1 of the
+    targets)."""
+    name: str
+    max_depth: int
+    min_pts: int
+    tol_rel: float
+    offsets: np.ndarray
+    degrees: np.ndarray
+    boxes: np.ndarray        # [P, 4]: lo x, lo y, lo z, side
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    f: np.ndarray
+    toff: np.ndarray
+    xq: np.ndarray
+    yq: np.ndarray
+    zq: np.ndarray
+    tprob: np.ndarray        # problem of every target (int32)
+    fkind: list              # per problem: ("franke", shift, scale) or ("gauss", centres, exps, weights)
+
+    @property
+    def n_problems(self):
+        return int(self.offsets.shape[0] - 1)
+
+    def truth(self, i, x, y, z):
+        """The generating function of problem i at (x, y, z)."""
+        return _batch_value(self.fkind[i], x, y, z)
+
+
+def _batch_value(kind, x, y, z):
+    if kind[0] == "franke":
+        _, shift, scale = kind
+        return franke_bj(0.5 + scale * (x - 0.5) + shift[0], 0.5 + scale * (y - 0.5) + shift[1],
+                         0.5 + scale * (z - 0.5) + shift[2])
+    _, cen, ex, wt = kind
+    v = np.zeros_like(np.asarray(x, dtype=np.float64))
+    for c, a, wk in zip(cen, ex, wt):
+        v = v + wk * np.exp(-a * ((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2))
+    return v
+
+
+def batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536, deg_min: int = 4, deg_max: int = 10,
+          targets_per_problem: int = 1000, tol_rel: float = 1e-6, max_depth: int = 8, min_pts: int = 0,
+          seed: int = SEED_BASE + 3) -> Batch:
+    """Independent problems shaped like the batched configuration: point counts
+    log-uniform in [n_min, n_max]; uniform clouds or 1-8 Gaussian clusters
+    (sigma U[0.02, 0.2], centres U[0.2, 0.8]^3, rejected into [0,1)^3);
+    degree uniform in [deg_min, deg_max]; values a shifted/scaled Franke
+    function (shift U[-0.2,0.2]^3, scale U[0.5,2]) or a sum of 1-16 Gaussians
+    (centres U[0,1]^3, exponent U[1,50], weight N(0,1)); uniform targets."""
+    P = n_problems
+    u = uniform(seed, 1, 16 * P).reshape(P, 16)
+    nrm = normal(seed, 2, 16 * P).reshape(P, 16)
+    counts = np.floor(np.exp(np.log(n_min) + u[:, 0] * (np.log(n_max) - np.log(n_min)))).astype(np.int64)
+    counts = np.clip(counts, n_min, n_max)
+    degrees = (deg_min + np.floor(u[:, 1] * (deg_max - deg_min + 1))).astype(np.int32)
+    degrees = np.minimum(degrees, deg_max)
+    xs, ys, zs, fs, kinds = [], [], [], [], []
+    for i in range(P):
+        n = int(counts[i])
+        if u[i, 2] < 0.5:
+            x, y, z = uniform_points(seed, 1000 + i, n)
+        else:
+            k = 1 + int(u[i, 3] * 8) if u[i, 3] < 1.0 else 8
+            sig = 0.02 + 0.18 * u[i, 4]
+            cen = 0.2 + 0.6 * uniform(seed, 200000 + i, 3 * k).reshape(k, 3)
+            per = [n // k + (1 if c < n % k else 0) for c in range(k)]
+            parts = [clustered_points(seed, 400000 + 8 * i + c, per[c], cen[c], sig) for c in range(k) if per[c] > 0]
+            x = np.concatenate([p[0] for p in parts])
+            y = np.concatenate([p[1] for p in parts])
+            z = np.concatenate([p[2] for p in parts])
+        if u[i, 5] < 0.5:
+            shift = -0.2 + 0.4 * u[i, 6:9]
+            scale = 0.5 + 1.5 * u[i, 9]
+            kind = ("franke", shift, scale)
+        else:
+            ng = 1 + int(u[i, 10] * 16) if u[i, 10] < 1.0 else 16
+            gu = uniform(seed, 600000 + i, 4 * ng).reshape(ng, 4)
+            kind = ("gauss", gu[:, :3], 1.0 + 49.0 * gu[:, 3], normal(seed, 800000 + i, ng))
+        xs.append(x); ys.append(y); zs.append(z)
+        fs.append(_batch_value(kind, x, y, z))
+        kinds.append(kind)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    nt = targets_per_problem
+    tq = uniform(seed, 3, 3 * nt * P).reshape(P * nt, 3)
+    tprob = np.repeat(np.arange(P, dtype=np.int32), nt)
+    boxes = np.tile(np.array([0.0, 0.0, 0.0, 1.0]), (P, 1))
+    return Batch("batch_fp64_%dproblems_p%d-%d" % (P, deg_min, deg_max), max_depth, min_pts, tol_rel, offsets,
+                 degrees, boxes, np.concatenate(xs), np.concatenate(ys), np.concatenate(zs), np.concatenate(fs),
+                 np.arange(P + 1, dtype=np.int64) * nt, np.ascontiguousarray(tq[:, 0]),
+                 np.ascontiguousarray(tq[:, 1]), np.ascontiguousarray(tq[:, 2]), tprob, kinds)

@@ -40,11 +40,14 @@ def morton_np(x, y, z, lo=(0.0, 0.0, 0.0), side=1.0):
         (spread3(quantise_np(z, lo[2], side)) << np.uint64(2))
 
 
-def gpu_keys(ex):
-    """{(depth, ix, iy, iz): index} of an exported tree."""
+def gpu_keys(ex, problem=0):
+    """{(depth, ix, iy, iz): index} of one problem of an exported tree."""
     keys = {}
+    mp = ex.morton_prefix()
     for i in range(ex.prefix.shape[0]):
-        p = np.uint64(ex.prefix[i])
+        if int(ex.problem[i]) != problem:
+            continue
+        p = np.uint64(mp[i])
         keys[(int(ex.depth[i]), int(compact3(p)), int(compact3(p >> np.uint64(1))), int(compact3(p >> np.uint64(2))))] = i
     return keys
 
@@ -69,7 +72,7 @@ def node_poly(coef, p, key, lo, side, pts):
     return val
 
 
-def excluded_subtrees(T, ex):
+def excluded_subtrees(T, ex, problem=0):
     """Keys below a decision flagged near tau on either side (excluded from the
     node-set comparison), plus the flagged nodes themselves."""
     bad = set()
@@ -78,7 +81,7 @@ def excluded_subtrees(T, ex):
         for o in range(8):
             if T.near_mask[i] & (1 << o):
                 bad.add((k[0] + 1, 2 * k[1] + (o & 1), 2 * k[2] + ((o >> 1) & 1), 2 * k[3] + ((o >> 2) & 1)))
-    gk = gpu_keys(ex)
+    gk = gpu_keys(ex, problem)
     for k, i in gk.items():
         for o in range(8):
             if ex.near_mask[i] & (1 << o):
@@ -94,14 +97,14 @@ def excluded_subtrees(T, ex):
     return under
 
 
-def compare_trees(T, ex, tol, n_poly_pts=6, seed=0):
+def compare_trees(T, ex, tol, n_poly_pts=6, seed=0, problem=0):
     """Assert that the exported CUDA tree matches the oracle tree T.
 
     Structure (node set, point counts, octant counts, degrees) must be
     bit-exact outside subtrees below near-tau decisions; residuals and node
     polynomials must agree within tol (absolute)."""
-    under = excluded_subtrees(T, ex)
-    ok, gk = oracle_keys(T), gpu_keys(ex)
+    under = excluded_subtrees(T, ex, problem)
+    ok, gk = oracle_keys(T), gpu_keys(ex, problem)
     so = {k for k in ok if not under(k)}
     sg = {k for k in gk if not under(k)}
     assert so == sg, "node sets differ: only oracle %s, only gpu %s" % (sorted(so - sg)[:5], sorted(sg - so)[:5])
