@@ -97,12 +97,16 @@ def excluded_subtrees(T, ex, problem=0):
     return under
 
 
-def compare_trees(T, ex, tol, n_poly_pts=6, seed=0, problem=0):
+def compare_trees(T, ex, tol, n_poly_pts=6, seed=0, problem=0, data_xyz=None):
     """Assert that the exported CUDA tree matches the oracle tree T.
 
     Structure (node set, point counts, octant counts, degrees) must be
-    bit-exact outside subtrees below near-tau decisions; residuals and node
-    polynomials must agree within tol (absolute)."""
+    bit-exact outside subtrees below near-tau decisions; node polynomials
+    must agree within tol (absolute).  With data_xyz = (x, y, z) (the whole
+    input, input order) the polynomials are compared at up to n_poly_pts of
+    each node's own points -- where a least-squares fit is determined even
+    when the node basis is ill conditioned; otherwise at random points of
+    the node box."""
     under = excluded_subtrees(T, ex, problem)
     ok, gk = oracle_keys(T), gpu_keys(ex, problem)
     so = {k for k in ok if not under(k)}
@@ -120,8 +124,12 @@ def compare_trees(T, ex, tol, n_poly_pts=6, seed=0, problem=0):
         assert np.max(np.abs(T.child_E[i] - ex.child_E[j])) <= tol, k
         d = k[0]
         h = T.side / 2 ** d
-        lo = np.array([T.lo[0] + k[1] * h, T.lo[1] + k[2] * h, T.lo[2] + k[3] * h])
-        pts = lo + h * rng.uniform(0, 1, (n_poly_pts, 3))
+        if data_xyz is not None:
+            sel = ex.perm[ex.start[j] + rng.choice(int(ex.count[j]), min(n_poly_pts, int(ex.count[j])), replace=False)]
+            pts = np.stack([data_xyz[0][sel], data_xyz[1][sel], data_xyz[2][sel]], axis=1)
+        else:
+            lo = np.array([T.lo[0] + k[1] * h, T.lo[1] + k[2] * h, T.lo[2] + k[3] * h])
+            pts = lo + h * rng.uniform(0, 1, (n_poly_pts, 3))
         a = node_poly(T.coef[i], p, k, T.lo, T.side, pts)
         b = node_poly(ex.coef[j], p, k, T.lo, T.side, pts)
         worst = max(worst, float(np.max(np.abs(a - b))))
