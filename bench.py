@@ -48,7 +48,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["fmt", "reference"], default="fmt")
-    ap.add_argument("--workload", choices=["scale", "small"], default="scale")
+    ap.add_argument("--workload", choices=["scale", "small", "batch"], default="scale")
+    ap.add_argument("--problems", type=int, default=4096, help="problems of the batch workload")
     ap.add_argument("--points", type=int, default=0, help="override the number of points")
     ap.add_argument("--targets", type=int, default=0, help="override the number of targets")
     ap.add_argument("--cpu-points", type=int, default=200_000, help="oracle sample size for cpu_baseline")
@@ -61,6 +62,8 @@ def parse_args():
 
 def make_workload(args, rank=0):
     from paper_1511_01353_gb300 import workloads as W
+    if args.workload == "batch":
+        return W.batch(n_problems=args.problems, seed=W.SEED_BASE + 3 + 1000 * rank)
     if args.workload == "small":
         kw = {}
         if args.points:
@@ -218,6 +221,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def cpu_baseline_batch(args, w):
+    """The oracle on the first problems of the batch, one after another (each
+    with OpenMP over its sibling subtrees), until ~10 s of work."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    pts = 0
+    k = 0
+    while k < w.n_problems and time.perf_counter() - t0 < 10.0:
+        a, b = int(w.offsets[k]), int(w.offsets[k + 1])
+        O.fit(w.x[a:b], w.y[a:b], w.z[a:b], w.f[a:b], int(w.degrees[k]), w.max_depth, w.min_pts, w.tol_rel,
+              mode="omp")
+        pts += b - a
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": pts / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "first %d problems of the batch (%d points), fitted one after another, %.1f s" % (k, pts, dt)}
+
+
 def cpu_baseline(args):
     from oracle import oracle as O
     from paper_1511_01353_gb300 import workloads as W
@@ -256,14 +277,33 @@ def main():
     F.load()
     stream = torch.cuda.Stream()
     w = make_workload(args, rank)
-    params = F.make_params(w.degree, w.max_depth, w.min_pts, w.tol_rel)
+    params = None if args.workload == "batch" else F.make_params(w.degree, w.max_depth, w.min_pts, w.tol_rel)
 
     def dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
 
+    is_batch = args.workload == "batch"
+    if is_batch:
+        params = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel)
+        w.n = int(w.offsets[-1])
+        w.m = int(w.xq.shape[0])
+        w.name = w.name
+        tprob = torch.from_numpy(w.tprob).to("cuda")
     x, y, z, f = dev(w.x), dev(w.y), dev(w.z), dev(w.f)
     xq, yq, zq = dev(w.xq), dev(w.yq), dev(w.zq)
     out = torch.empty(w.m, dtype=torch.float64, device="cuda")
+
+    def build(xx, yy, zz, ff):
+        if is_batch:
+            return F.oct_build_batch(params, w.offsets, xx, yy, zz, ff, degrees=w.degrees, boxes=w.boxes,
+                                     stream=stream)
+        return F.oct_build(params, xx, yy, zz, ff, stream)
+
+    def evaluate(tree, qx, qy, qz):
+        if is_batch:
+            F.evaluate_batch(tree, tprob, qx, qy, qz, out, stream=stream)
+        else:
+            F.evaluate(tree, qx, qy, qz, out, stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     torch.cuda.synchronize()
 
@@ -271,7 +311,7 @@ def main():
 
     def fit_with_level_events(lv):
         # the driver loop of F.fit, with events around every fit_level
-        tree = F.oct_build(params, x, y, z, f, stream)
+        tree = build(x, y, z, f)
         d = 0
         while True:
             a = torch.cuda.Event(enable_timing=True)
@@ -294,7 +334,7 @@ def main():
             e0.record(stream)
             tree = fit_with_level_events(level_events if timed else [])
             e1.record(stream)
-            F.evaluate(tree, xq, yq, zq, out, stream=stream)
+            evaluate(tree, xq, yq, zq)
             e2.record(stream)
         return tree, (e0, e1, e2)
 
@@ -345,7 +385,12 @@ def main():
 
     # accuracy of the interpolant against the closed form (last timed step)
     pred = out.cpu().numpy()
-    erms, einf = W.errors(pred, W.franke_bj(w.xq, w.yq, w.zq))
+    if is_batch:
+        truth = np.concatenate([w.truth(i, w.xq[w.toff[i]:w.toff[i + 1]], w.yq[w.toff[i]:w.toff[i + 1]],
+                                        w.zq[w.toff[i]:w.toff[i + 1]]) for i in range(w.n_problems)])
+        erms, einf = W.errors(pred, truth)
+    else:
+        erms, einf = W.errors(pred, W.franke_bj(w.xq, w.yq, w.zq))
 
     # roofline of the dominant kernel (tile_qr, FP64 pipe); flops = 2 m^2 per row
     qr = prof.get("tile_qr", {})
@@ -353,8 +398,9 @@ def main():
     dfma = F.fmt_probe_dfma(20000, stream)
     probe_tflops = 2.0 * dfma / 1e12
     fit_flops = sum(v["flops"] for k, v in prof.items() if k != "evaluate")
-    ev_levels = levels_visited(ex, w.xq, w.yq, w.zq, (0.0, 0.0, 0.0), 1.0)
-    hf = 2.0 * (F.fmt_nmono(w.degree) + (w.degree + 1) * (w.degree + 2) / 2 + (w.degree + 1))
+    deg = int(w.degrees.max()) if is_batch else w.degree
+    ev_levels = 0 if is_batch else levels_visited(ex, w.xq, w.yq, w.zq, (0.0, 0.0, 0.0), 1.0)
+    hf = 2.0 * (F.fmt_nmono(deg) + (deg + 1) * (deg + 2) / 2 + (deg + 1))
     ev = prof.get("evaluate", {})
     ev_tflops = ev_levels * hf * args.steps / (ev["ms"] * 1e-3) / 1e12 if ev.get("ms") else None
     total_ms = sum(v["ms"] for v in prof.values())
@@ -380,11 +426,11 @@ def main():
                 a.record(stream)
                 for d_, h_ in ((dx, hx), (dy, hy), (dz, hz), (df, hf_)):
                     d_.copy_(h_, non_blocking=True)
-                tr = F.fit(params, dx, dy, dz, df, stream)
+                tr = F.fit_all(build(dx, dy, dz, df), stream)
                 b.record(stream)
                 for d_, h_ in ((dxq, hxq), (dyq, hyq), (dzq, hzq)):
                     d_.copy_(h_, non_blocking=True)
-                F.evaluate(tr, dxq, dyq, dzq, out, stream=stream)
+                evaluate(tr, dxq, dyq, dzq)
                 hout.copy_(out, non_blocking=True)
                 c.record(stream)
             stream.synchronize()
@@ -402,7 +448,7 @@ def main():
         return 0
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args)
+        cpu = cpu_baseline_batch(args, w) if is_batch else cpu_baseline(args)
 
     nodes = [int(stats.nodes[d]) for d in range(stats.n_levels)]
     points = [int(stats.points[d]) for d in range(stats.n_levels)]
@@ -410,9 +456,13 @@ def main():
         "metric": METRIC, "value": job_throughput(world, w.n, fit_s), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (fit_s + eval_s) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "points": w.n, "targets": w.m, "degree": w.degree,
-                   "nmono": F.fmt_nmono(w.degree), "max_depth": w.max_depth, "min_pts": w.min_pts,
-                   "tol_rel": w.tol_rel, "values": "3-D Franke (benchmark form)",
+        "config": {"workload": w.name, "points": w.n, "targets": w.m,
+                   "degree": ("%d..%d per problem" % (w.degrees.min(), w.degrees.max())) if is_batch else w.degree,
+                   "problems": w.n_problems if is_batch else 1,
+                   "nmono": F.fmt_nmono(deg), "max_depth": w.max_depth, "min_pts": w.min_pts,
+                   "tol_rel": w.tol_rel,
+                   "values": ("shifted/scaled Franke or Gaussian sums per problem" if is_batch
+                              else "3-D Franke (benchmark form)"),
                    "l2": "flushed before every step (256 MB write)", "parallelism": "replicas",
                    "gpu": gpu_name},
         "evals_per_s": job_throughput(world, w.m, eval_s), "fit_ms": fit_s * 1e3, "eval_ms": eval_s * 1e3,
