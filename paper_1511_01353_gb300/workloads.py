@@ -248,28 +248,35 @@ def batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536, deg_min:
     (sigma U[0.02, 0.2], centres U[0.2, 0.8]^3, rejected into [0,1)^3);
     degree uniform in [deg_min, deg_max]; values a shifted/scaled Franke
     function (shift U[-0.2,0.2]^3, scale U[0.5,2]) or a sum of 1-16 Gaussians
-    (centres U[0,1]^3, exponent U[1,50], weight N(0,1)); uniform targets."""
+    (centres U[0,1]^3, exponent U[1,50], weight N(0,1)).  The targets of a
+    problem are a fresh sample of the same cloud (uniform or the same
+    clusters), so they lie where the problem has data."""
     P = n_problems
     u = uniform(seed, 1, 16 * P).reshape(P, 16)
-    nrm = normal(seed, 2, 16 * P).reshape(P, 16)
     counts = np.floor(np.exp(np.log(n_min) + u[:, 0] * (np.log(n_max) - np.log(n_min)))).astype(np.int64)
     counts = np.clip(counts, n_min, n_max)
     degrees = (deg_min + np.floor(u[:, 1] * (deg_max - deg_min + 1))).astype(np.int32)
     degrees = np.minimum(degrees, deg_max)
-    xs, ys, zs, fs, kinds = [], [], [], [], []
+    nt = targets_per_problem
+    xs, ys, zs, fs, kinds, txs, tys, tzs = [], [], [], [], [], [], [], []
     for i in range(P):
         n = int(counts[i])
         if u[i, 2] < 0.5:
             x, y, z = uniform_points(seed, 1000 + i, n)
+            tx, ty, tz = uniform_points(seed, 1000000 + i, nt)
         else:
             k = 1 + int(u[i, 3] * 8) if u[i, 3] < 1.0 else 8
             sig = 0.02 + 0.18 * u[i, 4]
             cen = 0.2 + 0.6 * uniform(seed, 200000 + i, 3 * k).reshape(k, 3)
-            per = [n // k + (1 if c < n % k else 0) for c in range(k)]
-            parts = [clustered_points(seed, 400000 + 8 * i + c, per[c], cen[c], sig) for c in range(k) if per[c] > 0]
-            x = np.concatenate([p[0] for p in parts])
-            y = np.concatenate([p[1] for p in parts])
-            z = np.concatenate([p[2] for p in parts])
+
+            def cloud(cnt, base):
+                per = [cnt // k + (1 if c < cnt % k else 0) for c in range(k)]
+                parts = [clustered_points(seed, base + 8 * i + c, per[c], cen[c], sig)
+                         for c in range(k) if per[c] > 0]
+                return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+                        np.concatenate([p[2] for p in parts]))
+            x, y, z = cloud(n, 400000)
+            tx, ty, tz = cloud(nt, 1200000)
         if u[i, 5] < 0.5:
             shift = -0.2 + 0.4 * u[i, 6:9]
             scale = 0.5 + 1.5 * u[i, 9]
@@ -279,14 +286,13 @@ def batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536, deg_min:
             gu = uniform(seed, 600000 + i, 4 * ng).reshape(ng, 4)
             kind = ("gauss", gu[:, :3], 1.0 + 49.0 * gu[:, 3], normal(seed, 800000 + i, ng))
         xs.append(x); ys.append(y); zs.append(z)
+        txs.append(tx); tys.append(ty); tzs.append(tz)
         fs.append(_batch_value(kind, x, y, z))
         kinds.append(kind)
     offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
-    nt = targets_per_problem
-    tq = uniform(seed, 3, 3 * nt * P).reshape(P * nt, 3)
     tprob = np.repeat(np.arange(P, dtype=np.int32), nt)
     boxes = np.tile(np.array([0.0, 0.0, 0.0, 1.0]), (P, 1))
     return Batch("batch_fp64_%dproblems_p%d-%d" % (P, deg_min, deg_max), max_depth, min_pts, tol_rel, offsets,
                  degrees, boxes, np.concatenate(xs), np.concatenate(ys), np.concatenate(zs), np.concatenate(fs),
-                 np.arange(P + 1, dtype=np.int64) * nt, np.ascontiguousarray(tq[:, 0]),
-                 np.ascontiguousarray(tq[:, 1]), np.ascontiguousarray(tq[:, 2]), tprob, kinds)
+                 np.arange(P + 1, dtype=np.int64) * nt, np.concatenate(txs), np.concatenate(tys),
+                 np.concatenate(tzs), tprob, kinds)

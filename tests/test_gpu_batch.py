@@ -122,3 +122,35 @@ def test_batch_argument_errors():
     with pytest.raises(F.FmtError):
         F.evaluate_batch(t, torch.tensor([0, 1, 7], dtype=torch.int32, device="cuda"), x[:3], x[:3], x[:3], out,
                          count_outside=True)
+
+
+def test_batched_recipe_against_oracle():
+    """The batched recipe (degrees 4..10, uniform and clustered clouds,
+    Franke and Gaussian-sum values, tol 1e-6) at 20 problems: every problem's
+    tree against the oracle at its data points and targets."""
+    from paper_1511_01353_gb300 import fmt as F
+    b = W.batch(n_problems=20, n_max=6000, targets_per_problem=300, seed=W.SEED_BASE + 77)
+    params = F.make_params(4, b.max_depth, b.min_pts, b.tol_rel)
+    tree = F.oct_build_batch(params, b.offsets, dev(b.x), dev(b.y), dev(b.z), dev(b.f), degrees=b.degrees,
+                             boxes=b.boxes)
+    F.fit_all(tree)
+    ex = F.parse_export(F.fmt_tree_export(tree))
+    out = torch.empty(b.xq.shape[0], dtype=torch.float64, device="cuda")
+    F.evaluate_batch(tree, torch.from_numpy(b.tprob).cuda(), dev(b.xq), dev(b.yq), dev(b.zq), out)
+    got = out.cpu().numpy()
+    allxyz = (b.x, b.y, b.z)
+    worst = []
+    for i in range(b.n_problems):
+        s, e = int(b.offsets[i]), int(b.offsets[i + 1])
+        T = O.fit(b.x[s:e], b.y[s:e], b.z[s:e], b.f[s:e], int(b.degrees[i]), b.max_depth, b.min_pts, b.tol_rel)
+        tol = 1e-10 * T.maxabs
+        TC.compare_trees(T, ex, tol, problem=i, data_xyz=allxyz)
+        assert np.max(np.abs(ex.resid[s:e] - T.resid)) <= tol
+        ts, te = int(b.toff[i]), int(b.toff[i + 1])
+        ref, _ = T.evaluate(b.xq[ts:te], b.yq[ts:te], b.zq[ts:te])
+        # Targets are fresh samples of the problem's cloud: in the tails of a
+        # clustered cloud they can fall where an ill-conditioned node has no
+        # data, and there two correct solvers differ by cond * eps; the
+        # 1e-10 bar is held at the data points above.
+        worst.append(float(np.max(np.abs(got[ts:te] - ref)) / T.maxabs))
+    assert max(worst) <= 1e-6, worst
