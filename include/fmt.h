@@ -26,7 +26,9 @@
  *    on that tree returns the same status.
  *  - Precision: everything on the FP64 path is IEEE binary64.  The
  *    quantisation and node-frame arithmetic use no fused multiply-add so the
- *    tree structure is bit-reproducible.
+ *    tree structure is bit-reproducible.  The mixed path (FMT_MIXED) forms
+ *    the least-squares projections with BF16 tensor-core products and wins
+ *    the accuracy back in FP64; see fit_level.
  */
 #ifndef FMT_H
 #define FMT_H
@@ -43,12 +45,14 @@ typedef enum {
   FMT_EINVAL = 1,    /* bad argument, non-finite input, or call out of order */
   FMT_ENOMEM = 2,    /* device or host allocation failed */
   FMT_ECUDA = 3,     /* a CUDA runtime call failed */
-  FMT_ETIMEOUT = 4,  /* reserved for bounded device waits */
+  FMT_ETIMEOUT = 4,  /* a bounded device wait ran out (mixed path) */
   FMT_EINTERNAL = 5  /* a device-side consistency check failed */
 } fmt_status;
 
-#define FMT_FP64 0  /* FP64 path (the only one implemented) */
-#define FMT_MIXED 1 /* reserved: split-BF16/TF32 products with FP64 refinement */
+#define FMT_FP64 0  /* FP64 path: Householder QR of every node in binary64 */
+#define FMT_MIXED 1 /* split-BF16 tensor-core Gram + FP64 factorisation and refinement */
+#define FMT_MIXED_MAX_DEGREE 9 /* nodes of higher degree take the FP64 path */
+#define FMT_MIXED_MAX_SWEEPS 3
 
 #define FMT_MAX_DEPTH 21  /* 21 bits per axis in the Morton code */
 #define FMT_MAX_DEGREE 14 /* nmono(14) = 680, the largest order in Sec. 3 */
@@ -57,6 +61,7 @@ typedef enum {
 #define FMT_FLAG_NEAR_TAU 1     /* created by a decision with |E - tau| <= 1e-9 tau */
 #define FMT_FLAG_RANK 2         /* back substitution dropped dependent columns */
 #define FMT_FLAG_DEG_CLAMPED 4  /* root with N < nmono: degree lowered */
+#define FMT_FLAG_MIXED 8        /* fitted by the mixed-precision path */
 
 /*
  * Parameters of Alg. 1 (L, nmono, tau and the root box P) plus the depth and
@@ -66,13 +71,17 @@ typedef enum {
  *   max_depth  deepest octree level, 0 <= max_depth <= 21 (root = 0).
  *   min_pts    an octant becomes a child only if it holds at least
  *              max(nmono, min_pts) points (Alg. 1 requires n_o >= nmono).
- *   precision  FMT_FP64.
+ *   precision  FMT_FP64 or FMT_MIXED (fit_level describes both).
  *   tol_rel    tau = tol_rel * max_i |f_i| (>= 0); an octant is refined when
  *              its RMS residual E_RMS > tau (strict, Alg. 1).
  *   lo, side   root cube [lo, lo+side)^3, side > 0.  Points and targets
  *              outside it are clamped into the boundary cells.
  *   chunk_rows rows per QR work item for large nodes (multiple of 64);
  *              0 picks a size from the number of active points.
+ *   sweeps     FMT_MIXED only: FP64 refinement sweeps after the first solve:
+ *              1..3 (FMT_MIXED_MAX_SWEEPS), 0 selects 3, -1 none (then no
+ *              convergence test either).  Ignored for FP64.
+ *   reserved   must be 0.
  */
 typedef struct {
   int32_t degree;
@@ -83,6 +92,8 @@ typedef struct {
   double lo[3];
   double side;
   int64_t chunk_rows;
+  int32_t sweeps;
+  int32_t reserved;
 } fmt_params;
 
 typedef struct fmt_tree fmt_tree; /* opaque, device resident */
@@ -117,6 +128,32 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  * r <- r - Lambda F, and each octant's sum of squared residuals and count.
  * Legal for depth 0 right after oct_build and for depth d+1 after refine(d)
  * reported new nodes; otherwise FMT_EINVAL.  Asynchronous.
+ *
+ * With precision FMT_MIXED the same least-squares fit is computed another
+ * way for nodes of degree <= FMT_MIXED_MAX_DEGREE (the paper has only the
+ * FP64 Householder form):
+ *  - basis: Legendre products P_a(t_x) P_b(t_y) P_c(t_z), a+b+c <= p, with
+ *    t = 2^e u per axis, e >= 0 the largest power of two that keeps the
+ *    node's points in |t| <= 1.  It spans the same polynomial space as the
+ *    moments of Alg. 2, so the least-squares fit is the same function.
+ *  - the Gram matrix [B | r]^T [B | r] of the node (r scaled by a power of
+ *    two) is formed on the tensor cores from 3-term BF16 splits of FP32
+ *    values, FP32 accumulation, promoted to FP64 every 256 rows;
+ *  - its FP64 Cholesky factor is the R-hat = [[R, Q^T r], [0, rho]] of the
+ *    FP64 path (same matrix, up to row signs); F = R^{-1} Q^T r;
+ *  - `sweeps` refinement steps: s = r - Lambda F in FP64, g = B^T s on the
+ *    tensor cores as above, F += (R^T R)^{-1} g;
+ *  - F is converted exactly to Alg. 2's moment basis in the node frame (the
+ *    stored coefficients have the FP64 path's layout), and r <- r - Lambda F
+ *    runs in FP64 as on the FP64 path.
+ * A node whose Cholesky pivot falls below 1e-6 of its diagonal entry, whose
+ * last sweep still changed the fit by more than 1e-7 of its norm, whose
+ * degree exceeds FMT_MIXED_MAX_DEGREE, or whose root degree was clamped, is
+ * refitted by the FP64 path; nodes fitted the mixed way carry FMT_FLAG_MIXED.
+ * The mixed path targets an interpolant within 1e-6 max|f| of the FP64
+ * path (not the 1e-10 of FP64), and its tree may differ where a refinement
+ * decision is that close to tau.  FMT_ETIMEOUT if a tensor-core completion
+ * wait exceeds 2 s (the tree is then unusable).
  */
 fmt_status fit_level(fmt_tree* tree, int32_t depth, void* stream);
 
@@ -188,6 +225,8 @@ typedef struct {
   int64_t chunk_rows[FMT_MAX_DEPTH + 1];
   int64_t near_tau[FMT_MAX_DEPTH + 1];   /* nodes flagged FMT_FLAG_NEAR_TAU */
   int64_t rank_flagged[FMT_MAX_DEPTH + 1];
+  int64_t mixed[FMT_MAX_DEPTH + 1];         /* nodes fitted by the mixed path */
+  int64_t mixed_points[FMT_MAX_DEPTH + 1];  /* their points */
 } fmt_stats;
 fmt_status fmt_tree_stats(fmt_tree* tree, fmt_stats* out);
 
@@ -244,7 +283,7 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
  * fmt_profile_enable(1) resets the counters and starts event timing;
  * fmt_profile_enable(0) stops it.  fmt_profile_read synchronises the device.
  */
-#define FMT_PROFILE_CLASSES 16
+#define FMT_PROFILE_CLASSES 24
 typedef struct {
   int64_t launches[FMT_PROFILE_CLASSES];
   double ms[FMT_PROFILE_CLASSES];

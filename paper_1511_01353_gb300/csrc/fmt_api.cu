@@ -56,11 +56,13 @@ fmt_status device_init(int dev) {
 // ---------------------------------------------------------------- profiling
 enum {
   K_CHECK = 0, K_MORTON, K_SORT, K_GATHER, K_PLAN, K_TILE_QR, K_COMBINE, K_BACKSOLVE,
-  K_RESIDUAL, K_CHILD, K_REFINE, K_EVALUATE, K_HCOEF, K_NCLASS
+  K_RESIDUAL, K_CHILD, K_REFINE, K_EVALUATE, K_HCOEF, K_MBOX, K_MGRAM, K_MFACTOR, K_MSRESID, K_MPROJ,
+  K_MUPDATE, K_NCLASS
 };
 const char* const kClassNames[K_NCLASS] = {"check_maxabs", "morton", "radix_sort", "gather", "plan_root",
                                            "tile_qr", "combine", "back_solve", "residual", "child_stats",
-                                           "refine", "evaluate", "make_hcoef"};
+                                           "refine", "evaluate", "make_hcoef", "mixed_box", "mixed_gram",
+                                           "mixed_factor", "mixed_sresid", "mixed_proj", "mixed_update"};
 struct ProfRec {
   int k;
   cudaEvent_t a, b;
@@ -250,7 +252,11 @@ fmt_status validate_shared(const fmt_params& P) {
   if (P.max_depth < 0 || P.max_depth > FMT_MAX_DEPTH)
     return set_err(nullptr, FMT_EINVAL, "max_depth %d outside [0, %d]", P.max_depth, FMT_MAX_DEPTH);
   if (P.min_pts < 0) return set_err(nullptr, FMT_EINVAL, "min_pts %d < 0", P.min_pts);
-  if (P.precision != FMT_FP64) return set_err(nullptr, FMT_EINVAL, "only FMT_FP64 is implemented");
+  if (P.precision != FMT_FP64 && P.precision != FMT_MIXED)
+    return set_err(nullptr, FMT_EINVAL, "precision must be FMT_FP64 or FMT_MIXED");
+  if (P.sweeps < -1 || P.sweeps > FMT_MIXED_MAX_SWEEPS)
+    return set_err(nullptr, FMT_EINVAL, "sweeps %d outside [-1, %d]", P.sweeps, FMT_MIXED_MAX_SWEEPS);
+  if (P.reserved != 0) return set_err(nullptr, FMT_EINVAL, "reserved must be 0");
   if (!(P.tol_rel >= 0.0) || !isfinite(P.tol_rel)) return set_err(nullptr, FMT_EINVAL, "tol_rel must be finite, >= 0");
   if (P.chunk_rows < 0) return set_err(nullptr, FMT_EINVAL, "chunk_rows < 0");
   return FMT_OK;
@@ -488,6 +494,77 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
   return FMT_OK;
 }
 
+// Grows the mixed path's scratch to the level's needs.
+fmt_status ensure_mixed(fmt_tree* t, int depth, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  fmt_mixed_bufs& b = t->mx;
+  if (!b.s) TRY(talloc(t, &b.s, t->n, s));
+  if (b.cap_nodes < L.n_nodes) {
+    if (b.mstat) tfree_one(t, b.mstat, s);
+    if (b.lcoef) tfree_one(t, b.lcoef, s);
+    b.mstat = nullptr;
+    b.lcoef = nullptr;
+    b.cap_nodes = 0;
+    TRY(talloc(t, &b.mstat, 4 * L.n_nodes, s));
+    TRY(talloc(t, &b.lcoef, (int64_t)t->nmono * L.n_nodes, s));
+    b.cap_nodes = L.n_nodes;
+  }
+  if (b.cap_items < L.n_items) {
+    if (b.gacc) tfree_one(t, b.gacc, s);
+    b.gacc = nullptr;
+    b.cap_items = 0;
+    TRY(talloc(t, &b.gacc, 256 * L.n_items, s));
+    b.cap_items = L.n_items;
+  }
+  b.acc_stride = (int64_t)mixed_acc_stride(L.max_m);
+  const int64_t need = b.acc_stride * L.n_items;
+  if (b.cap_acc < need) {
+    if (b.acc) tfree_one(t, b.acc, s);
+    b.acc = nullptr;
+    b.cap_acc = 0;
+    TRY(talloc(t, &b.acc, need, s));
+    b.cap_acc = need;
+  }
+  return FMT_OK;
+}
+
+// The mixed-precision fit of one level (fmt_mixed.cu): nodes it fits carry
+// FMT_FLAG_MIXED afterwards and are skipped by the FP64 kernels.
+fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
+  TRY(ensure_mixed(t, depth, s));
+  const fmt_level& L = t->lv[depth];
+  const fmt_mixed_bufs& b = t->mx;
+  const double rows = (double)L.n_points, nodes = (double)L.n_nodes;
+  {
+    ProfScope ps(K_MBOX, s, 2, rows, 0.0);
+    CUDA_TRY(t, launch_mixed_box(t, depth, b, s), "mixed box launch");
+  }
+  {
+    ProfScope ps(K_MGRAM, s, 1, rows, 0.0);
+    CUDA_TRY(t, launch_mixed_gram(t, depth, b, false, s), "mixed Gram launch");
+  }
+  {
+    ProfScope ps(K_MFACTOR, s, 1, nodes, 0.0);
+    CUDA_TRY(t, launch_mixed_factor(t, depth, b, s), "mixed factor launch");
+  }
+  const int sweeps = t->P.sweeps == 0 ? FMT_MIXED_MAX_SWEEPS : (t->P.sweeps < 0 ? 0 : t->P.sweeps);
+  for (int k = 0; k < sweeps; ++k) {
+    {
+      ProfScope ps(K_MSRESID, s, 1, rows, L.horner_flops);
+      CUDA_TRY(t, launch_mixed_sresid(t, depth, b, s), "mixed sweep residual launch");
+    }
+    {
+      ProfScope ps(K_MPROJ, s, 1, rows, 0.0);
+      CUDA_TRY(t, launch_mixed_gram(t, depth, b, true, s), "mixed projection launch");
+    }
+    {
+      ProfScope ps(K_MUPDATE, s, 1, nodes, 0.0);
+      CUDA_TRY(t, launch_mixed_update(t, depth, b, k == sweeps - 1, s), "mixed update launch");
+    }
+  }
+  return FMT_OK;
+}
+
 }  // namespace
 
 // error reporting for entry points defined in other translation units
@@ -536,9 +613,11 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
     t->Rbuf_cap = need;
   }
   const double dm = (double)m, rows = (double)L.n_points;
+  if (t->P.precision == FMT_MIXED) TRY(fit_level_mixed(t, depth, s));
   {
-    // Householder on [Lambda | r]: 2 m^2 flops per row (m = nmono + 1 of the row's node)
-    ProfScope ps(K_TILE_QR, s, 1, rows, L.qr_flops);
+    // Householder on [Lambda | r]: 2 m^2 flops per row (m = nmono + 1 of the row's node);
+    // on the mixed path only the nodes it left to FP64 are factorised here
+    ProfScope ps(K_TILE_QR, s, 1, rows, t->P.precision == FMT_MIXED ? 0.0 : L.qr_flops);
     CUDA_TRY(t, launch_tile_qr(t, depth, t->Rbuf, s), "tile QR launch");
   }
   int levels = 0;
@@ -591,6 +670,8 @@ fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream
   }
   TRY(read_plan(t, s));
   const fmt_plan_out& pl = *t->h_plan;
+  if (pl.err & FMT_ERR_TIMEOUT)
+    return set_err(t, FMT_ETIMEOUT, "a tensor-core completion wait of the mixed fit timed out");
   if (pl.err) return set_err(t, FMT_EINTERNAL, "device check failed in refine (0x%llx)", (unsigned long long)pl.err);
   t->next_refine = -1;
   if (!deep_ok || pl.n_new <= 0) {
@@ -678,11 +759,27 @@ fmt_status fmt_tree_stats(fmt_tree* t, fmt_stats* o) {
         free(hf);
         return set_err(t, FMT_ECUDA, "copy: %s", cudaGetErrorString(e));
       }
+      int64_t* hc = (int64_t*)malloc(sizeof(int64_t) * (size_t)L.n_nodes);
+      if (!hc) {
+        free(hf);
+        return set_err(t, FMT_ENOMEM, "host allocation failed");
+      }
+      e = cudaMemcpy(hc, L.count, sizeof(int64_t) * (size_t)L.n_nodes, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        free(hf);
+        free(hc);
+        return set_err(t, FMT_ECUDA, "copy: %s", cudaGetErrorString(e));
+      }
       for (int64_t i = 0; i < L.n_nodes; ++i) {
         o->near_tau[d] += (hf[i] & FMT_FLAG_NEAR_TAU) ? 1 : 0;
         o->rank_flagged[d] += (hf[i] & FMT_FLAG_RANK) ? 1 : 0;
+        if (hf[i] & FMT_FLAG_MIXED) {
+          o->mixed[d] += 1;
+          o->mixed_points[d] += hc[i];
+        }
       }
       free(hf);
+      free(hc);
     }
   }
   return FMT_OK;

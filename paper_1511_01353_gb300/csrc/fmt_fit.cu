@@ -70,7 +70,12 @@ struct QRArgs {
   const int32_t* sched;
   int* work;
   int n_items;
+  const int32_t* flags;  // nodes with FMT_FLAG_MIXED are already fitted (mixed path)
 };
+
+__device__ __forceinline__ bool node_done(const QRArgs& a, int64_t node) {
+  return (a.flags[node] & FMT_FLAG_MIXED) != 0;
+}
 
 // degree, column count and frame of a node of the level
 struct NodeGeom {
@@ -265,6 +270,7 @@ __global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
     if (it >= a.n_items) break;
     const int item = a.sched[it];
     const int64_t node = a.item_node[item];
+    if (node_done(a, node)) continue;
     const int64_t rs = a.item_start[item], re = a.item_end[item];
     const NodeGeom g = node_geom(a, node);
     const int m = g.m, q = g.q, ldB = g.ldB;
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(32 * kCombineWarps) k_combine(QRArgs a, int le
   const int64_t node = a.item_node[item];
   const int cnt = a.node_nitems[node];
   const int step = 1 << level;
-  if ((s & (2 * step - 1)) != 0 || s + step >= cnt) return;
+  if ((s & (2 * step - 1)) != 0 || s + step >= cnt || node_done(a, node)) return;
   const NodeGeom g = node_geom(a, node);
   const int m = g.m;
   double* Ra = a.R + a.item_roff[item];
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
   const int sidx = a.item_local[item];
   const int cnt = a.node_nitems[a.item_node[item]];
   const int step = 1 << level;
-  if ((sidx & (2 * step - 1)) != 0 || sidx + step >= cnt) return;
+  if ((sidx & (2 * step - 1)) != 0 || sidx + step >= cnt || node_done(a, a.item_node[item])) return;
   const NodeGeom g = node_geom(a, a.item_node[item]);
   const int m = g.m;
   double* Ra = a.R + a.item_roff[item];
@@ -635,6 +641,7 @@ __global__ void __launch_bounds__(128) k_backsolve(BSArgs a) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t node = (int64_t)blockIdx.x * 4 + wib;
   if (node >= a.n_nodes) return;
+  if (a.flags[node] & FMT_FLAG_MIXED) return;  // fitted by the mixed path
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const int p = pr.degree;
   const int q = a.depth == 0 ? pr.q_root : p;
@@ -792,6 +799,7 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.sched = L.sched;
   a.work = t->d_work;
   a.n_items = (int)L.n_items;
+  a.flags = L.flags;
   return a;
 }
 

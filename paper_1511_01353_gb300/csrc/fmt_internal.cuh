@@ -16,6 +16,7 @@
 #define FMT_ERR_NONFINITE 1
 #define FMT_ERR_INDEX 2
 #define FMT_ERR_CAPACITY 4
+#define FMT_ERR_TIMEOUT 8
 
 // 1/l! for l = 0..14, each a correctly rounded binary64 quotient (l! is exact)
 static __constant__ double c_invfact[FMT_MAX_DEGREE + 1] = {
@@ -172,6 +173,17 @@ struct fmt_plan_out {
   int64_t pad_;
 };
 
+// Scratch of the mixed-precision fit (fmt_mixed.cu), grown per tree.
+struct fmt_mixed_bufs {
+  double* s = nullptr;                  // n: sweep residual
+  unsigned long long* mstat = nullptr;  // 4 per node
+  double* acc = nullptr;                // acc_stride per item
+  int64_t acc_stride = 0;
+  double* gacc = nullptr;               // 256 per item
+  double* lcoef = nullptr;              // nmono per node
+  int64_t cap_nodes = 0, cap_items = 0, cap_acc = 0;
+};
+
 struct fmt_tree {
   fmt_params P{};   // shared parameters (degree and box of problem 0 when P == 1)
   int32_t nmono = 0;       // coefficient stride: nmono of the largest degree
@@ -206,6 +218,7 @@ struct fmt_tree {
   unsigned long long* d_counter = nullptr;
   int* d_work = nullptr;  // work-queue counter of the persistent QR kernel
   int64_t chunk_floor = 64;
+  fmt_mixed_bufs mx;
   fmt_status sticky = FMT_OK;
   char msg[256] = {0};
   // every device allocation, freed together
@@ -252,5 +265,15 @@ cudaError_t launch_refine(const fmt_tree* t, int depth, int64_t chunk_rows_fixed
 cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, const double* xq,
                             const double* yq, const double* zq, double* out, unsigned long long* d_outside,
                             cudaStream_t s);
+// mixed precision (fmt_mixed.cu)
+int mixed_m_cap(int max_m);            // largest m a mixed node of the level can have
+size_t mixed_acc_stride(int max_m);    // doubles of Gram accumulator per work item
+cudaError_t launch_mixed_box(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
+cudaError_t launch_mixed_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool projection,
+                              cudaStream_t s);
+cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
+cudaError_t launch_mixed_sresid(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
+cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool last,
+                                cudaStream_t s);
 cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream_t s);
 cudaError_t launch_make_hcoef(const fmt_tree* t, int depth, cudaStream_t s);

@@ -1,0 +1,925 @@
+// fmt_mixed.cu -- the mixed-precision fit of one level (FMT_MIXED).
+//
+// Alg. 2 asks, per node, for the least-squares fit of the residual r by the
+// polynomials of total degree <= p.  The FP64 path factorises [Lambda | r] by
+// Householder QR, which costs 2 m^2 FP64 flops per row (m = nmono + 1).  Here
+// the same fit is computed with the O(n m^2) part on the tensor cores:
+//
+//  1. k_mbox: per node, max |u| per axis and max |r| over its points.  The
+//     basis is B = P_a(t_x) P_b(t_y) P_c(t_z) (Legendre, a+b+c <= p) with
+//     t = 2^e u, e the largest power of two that keeps |t| <= 1; r is scaled
+//     by a power of two to O(1).  Same polynomial space as Alg. 2's moments,
+//     so the same least-squares function; far better conditioned.
+//  2. k_mgram: per work item, the Gram matrix [B | r]^T [B | r] on the tensor
+//     cores (tcgen05.mma kind::f16): every FP32 value is split into three
+//     BF16 terms h + m + l, the six products hh, hm, mh, mm, hl, lh are
+//     accumulated in FP32 in tensor memory, and every 256 rows the FP32
+//     accumulator is added into an FP64 copy in global memory.
+//  3. k_mfactor: per node, the item Grams are summed in FP64 and factorised by
+//     Cholesky; the factor is R-hat = [[R, Q^T r], [0, rho]] of the FP64 path
+//     (the same matrix's R factor, up to row signs).  F = R^{-1} Q^T r.
+//  4. sweeps: s = r - Lambda F in FP64 (k_msresid), g = B^T s on the tensor
+//     cores (k_mgram projection mode), F += R^{-1} R^{-T} g (k_mupdate).
+//  5. F is converted to the moment basis of Alg. 2 in the node frame (exact
+//     in the scaling, Legendre coefficients are dyadic rationals), so the
+//     residual update, the evaluation and the export are those of the FP64
+//     path.
+// Nodes whose Cholesky pivot is below kPivotFloor of its diagonal entry, or
+// whose last sweep still moved the fit by more than kConvergedRel, lose
+// FMT_FLAG_MIXED and are refitted by the FP64 kernels of fmt_fit.cu.
+
+#include <cuda_bf16.h>
+
+#include "fmt_internal.cuh"
+
+namespace {
+
+constexpr int kMThreads = 128;   // one warpgroup: thread i reads TMEM lane i
+constexpr int kAtom = 64;        // rows per operand tile: one 128-byte swizzle row of BF16
+constexpr int kDrainAtoms = 4;   // FP32 -> FP64 promotion every 256 rows
+constexpr int kFThreads = 256;   // factor / update kernels
+constexpr double kPivotFloor = 1e-6;
+constexpr double kConvergedRel = 1e-7;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
+
+// ------------------------------------------------------------------ shapes
+__host__ __device__ __forceinline__ int mpad16(int m) { return (m + 15) & ~15; }
+// operand-tile rows: an M = 128 MMA reads rows [0, 128) even for small m
+__host__ __device__ __forceinline__ int mrows_for(int m) {
+  const int l = mpad16(m);
+  return l < 128 ? 128 : l;
+}
+// TMEM columns of the Gram: band 0 = rows [0,128) x cols [0, Lp); band 1 =
+// rows [Lp-128, Lp) x cols [128, Lp) when Lp > 128
+__host__ __device__ __forceinline__ int gram_cols(int m) {
+  const int l = mpad16(m);
+  return l <= 128 ? l : l + (l - 128);
+}
+__host__ __device__ __forceinline__ bool mixed_ok_degree(int p) { return p >= 0 && p <= FMT_MIXED_MAX_DEGREE; }
+__device__ __forceinline__ bool mixed_eligible(const fmt_problem& pr, int depth) {
+  return mixed_ok_degree(pr.degree) && !(depth == 0 && pr.q_root < pr.degree);
+}
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of `parity` to complete; false after kWaitNs.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// whole warp
+__device__ __forceinline__ void tc_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// D[tmem] (+)= A * B^T, both operands K-major BF16 in shared memory
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// the mbarrier completes one phase when every MMA issued so far by this thread is done
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  // the registers are valid only after wait::ld; tie them to it
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
+               :
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle (8-row
+// atoms of 128-byte rows, 16-byte chunks XOR-ed with the row index), atoms
+// 1024 bytes apart.  Fields: start >> 4 (bits 0-13), leading offset >> 4
+// (16-29, unused for this layout), stride offset >> 4 (32-45), descriptor
+// version 1 (46), swizzle mode 2 = 128 B (61-63).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// byte offset of element (row j, k) in a K-major 128-byte-swizzled tile of 64 BF16 per row
+__device__ __forceinline__ uint32_t sw_off(int j, int k) {
+  return (uint32_t)((j >> 3) * 1024 + (j & 7) * 128 + ((((k >> 3) ^ j) & 7) << 4) + ((k & 7) << 1));
+}
+
+// v = h + m + l, each a BF16 (the remainders are exact in FP32)
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  const float r1 = __fsub_rn(v, __bfloat162float(h));
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m)));
+}
+__device__ __forceinline__ void put3(uint8_t* t0, uint32_t tile_bytes, int j, int k, float v) {
+  __nv_bfloat16 h, m, l;
+  split3(v, h, m, l);
+  const uint32_t o = sw_off(j, k);
+  *reinterpret_cast<__nv_bfloat16*>(t0 + o) = h;
+  *reinterpret_cast<__nv_bfloat16*>(t0 + tile_bytes + o) = m;
+  *reinterpret_cast<__nv_bfloat16*>(t0 + 2 * tile_bytes + o) = l;
+}
+
+// Legendre polynomials P_0..P_P at t in FP32 (Bonnet's recurrence)
+template <int P>
+__device__ __forceinline__ void legendre_f(float t, float (&q)[P + 1]) {
+  q[0] = 1.0f;
+  if (P >= 1) q[1] = t;
+#pragma unroll
+  for (int k = 1; k < P; ++k) {
+    const float a = (float)(2 * k + 1) / (float)(k + 1), b = (float)k / (float)(k + 1);
+    q[k + 1] = a * t * q[k] - b * q[k - 1];
+  }
+}
+
+// ------------------------------------------------------------------ node frame
+struct MFrame {
+  double c[3], s[3], ex[3];  // u = (x - c) s ; t = u ex (ex = 2^e)
+  int e[3];
+  double sig;                // r scale: sig max|r| in [0.5, 1)
+};
+__device__ __forceinline__ MFrame mframe(const fmt_problem& pr, uint64_t key, int depth,
+                                         const unsigned long long* ms) {
+  MFrame F;
+  const uint64_t pf = fmt_morton_part(key, depth);
+  fmt_frame(pr.lo[0], pr.side, depth, fmt_compact3(pf), F.c[0], F.s[0]);
+  fmt_frame(pr.lo[1], pr.side, depth, fmt_compact3(pf >> 1), F.c[1], F.s[1]);
+  fmt_frame(pr.lo[2], pr.side, depth, fmt_compact3(pf >> 2), F.c[2], F.s[2]);
+  for (int a = 0; a < 3; ++a) {
+    const double mu = __longlong_as_double((long long)ms[a]);
+    int e = 0;
+    while (e < 20 && ldexp(mu, e + 1) <= 1.0) ++e;
+    F.e[a] = e;
+    F.ex[a] = ldexp(1.0, e);
+  }
+  const double mr = __longlong_as_double((long long)ms[3]);
+  int er = 0;
+  if (mr > 0.0) frexp(mr, &er);
+  F.sig = ldexp(1.0, -er);
+  return F;
+}
+
+__device__ __forceinline__ double block_max_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < nw; ++i) r = fmax(r, red[i]);
+  return r;
+}
+
+// ------------------------------------------------------------------ args
+struct MArgs {
+  const int64_t* item_node;
+  const int64_t* item_start;
+  const int64_t* item_end;
+  const int32_t* sched;
+  const int64_t* node_item0;
+  const int32_t* node_nitems;
+  int n_items;
+  int64_t n_nodes;
+  int* work;
+  const uint64_t* prefix;
+  const int32_t* node_prob;
+  const fmt_problem* prob;
+  int32_t* flags;
+  int32_t* deg_used;
+  const double* x;
+  const double* y;
+  const double* z;
+  const double* r;
+  double* s;                    // sweep residual, sorted order
+  unsigned long long* mstat;    // 4 per node: max |u|,|v|,|w| and max |r| (bit patterns)
+  double* acc;                  // per item: Gram accumulator (acc_stride doubles) / R-hat of the node
+  int64_t acc_stride;
+  double* gacc;                 // per item: projection accumulator, 256 doubles
+  double* lcoef;                // per node: F in the Legendre basis (stride doubles)
+  double* coef;
+  double* hcoef;
+  int stride;                   // coefficient stride (nmono of the largest degree)
+  int depth;
+  int MR;                       // operand-tile rows of the level
+  int tmem_cols;
+  int last_sweep;
+  int* err;
+};
+
+// ------------------------------------------------------------------ k_mbox
+__global__ void __launch_bounds__(256) k_mbox(MArgs a) {
+  __shared__ double red[8];
+  const int item = blockIdx.x;
+  const int64_t node = a.item_node[item];
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  if (!mixed_eligible(pr, a.depth)) return;
+  const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
+  double c0, s0, c1, s1, c2, s2;
+  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  double mu = 0.0, mv = 0.0, mw = 0.0, mr = 0.0;
+  for (int64_t i = a.item_start[item] + threadIdx.x; i < a.item_end[item]; i += blockDim.x) {
+    mu = fmax(mu, fabs(fmt_local(a.x[i], c0, s0)));
+    mv = fmax(mv, fabs(fmt_local(a.y[i], c1, s1)));
+    mw = fmax(mw, fabs(fmt_local(a.z[i], c2, s2)));
+    mr = fmax(mr, fabs(a.r[i]));
+  }
+  mu = block_max_d(mu, red);
+  mv = block_max_d(mv, red);
+  mw = block_max_d(mw, red);
+  mr = block_max_d(mr, red);
+  if (threadIdx.x == 0) {
+    // non-negative doubles order like their bit patterns
+    unsigned long long* d = a.mstat + 4 * node;
+    atomicMax(d + 0, (unsigned long long)__double_as_longlong(mu));
+    atomicMax(d + 1, (unsigned long long)__double_as_longlong(mv));
+    atomicMax(d + 2, (unsigned long long)__double_as_longlong(mw));
+    atomicMax(d + 3, (unsigned long long)__double_as_longlong(mr));
+  }
+}
+
+// ------------------------------------------------------------------ k_mgram
+// One 64-row atom of the operand tiles.  Thread (k, half): point k, and half
+// of the basis rows (the split point is a compile-time constant, so each
+// instantiation stores only its own rows).
+template <int P, bool kProj, int HALF>
+__device__ __forceinline__ void gen_rows(uint8_t* t0, uint32_t tile_bytes, uint8_t* stile, int k, bool valid,
+                                         double u, double v, double w, double val, const MFrame& F) {
+  constexpr int L = (P + 1) * (P + 2) * (P + 3) / 6;
+  constexpr int NW = kProj ? L : L + 1;  // rows written: basis (+ r in Gram mode)
+  constexpr int J1 = (NW + 1) / 2;
+  constexpr int jlo = HALF == 0 ? 0 : J1, jhi = HALF == 0 ? J1 : NW;
+  float qx[P + 1], qy[P + 1], qz[P + 1];
+  legendre_f<P>((float)(u * F.ex[0]), qx);
+  legendre_f<P>((float)(v * F.ex[1]), qy);
+  legendre_f<P>((float)(w * F.ex[2]), qz);
+  int j = 0;
+#pragma unroll
+  for (int l = 0; l <= P; ++l)
+#pragma unroll
+    for (int mm = 0; mm <= P - l; ++mm) {
+      const float plm = qx[l] * qy[mm];
+#pragma unroll
+      for (int n = 0; n <= P - l - mm; ++n, ++j)
+        if (j >= jlo && j < jhi) put3(t0, tile_bytes, j, k, valid ? plm * qz[n] : 0.0f);
+    }
+  const float sv = valid ? (float)(val * F.sig) : 0.0f;
+  if (!kProj) {
+    if (L >= jlo && L < jhi) put3(t0, tile_bytes, L, k, sv);
+  } else if (HALF == 0) {
+    __nv_bfloat16 h, m, l;
+    split3(sv, h, m, l);
+    *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(0, k)) = h;
+    *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(1, k)) = m;
+    *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(2, k)) = l;
+  }
+}
+
+template <bool kProj>
+__device__ __forceinline__ void gen_dispatch(int p, int half, uint8_t* t0, uint32_t tb, uint8_t* stile, int k,
+                                             bool valid, double u, double v, double w, double val,
+                                             const MFrame& F) {
+#define FMT_GEN_CASE(PP)                                                     \
+  case PP:                                                                   \
+    if (half == 0)                                                           \
+      gen_rows<PP, kProj, 0>(t0, tb, stile, k, valid, u, v, w, val, F);      \
+    else                                                                     \
+      gen_rows<PP, kProj, 1>(t0, tb, stile, k, valid, u, v, w, val, F);      \
+    break;
+  switch (p) {
+    FMT_GEN_CASE(0)
+    FMT_GEN_CASE(1)
+    FMT_GEN_CASE(2)
+    FMT_GEN_CASE(3)
+    FMT_GEN_CASE(4)
+    FMT_GEN_CASE(5)
+    FMT_GEN_CASE(6)
+    FMT_GEN_CASE(7)
+    FMT_GEN_CASE(8)
+    FMT_GEN_CASE(9)
+    default:
+      break;
+  }
+#undef FMT_GEN_CASE
+}
+
+// Persistent over the level's work items (largest first).  Gram mode
+// (kProj = false): acc[item] += [B | sig r]^T [B | sig r], column-major by
+// TMEM column, 128 lanes each.  Projection mode: gacc[item] += B^T (sig s),
+// band 0 rows in [0,128), band 1 rows in [128,256).
+template <bool kProj>
+__global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
+  extern __shared__ uint8_t dsm_raw[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_item;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint8_t* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
+  const uint32_t tile_bytes = (uint32_t)a.MR * 128u;
+  const uint32_t stage_bytes = 3u * tile_bytes + (kProj ? 2048u : 0u);
+  const uint32_t total = 2u * stage_bytes;
+  for (uint32_t o = 16u * tid; o < total; o += 16u * kMThreads) *reinterpret_cast<uint4*>(dsm + o) = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tc_alloc(&tmem_slot, (uint32_t)a.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t sbase = smem_u32(dsm);
+  uint32_t ncommit[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  int hi[2] = {0, 0};  // rows of each stage that may hold non-zero values
+  int stage = 0;
+  bool ok = true;
+  const int k = tid & 63, half = tid >> 6;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.work, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= a.n_items) break;
+    const int item = a.sched[it];
+    const int64_t node = a.item_node[item];
+    const fmt_problem& pr = a.prob[a.node_prob[node]];
+    if (kProj ? !(a.flags[node] & FMT_FLAG_MIXED) : !mixed_eligible(pr, a.depth)) continue;
+    const int p = pr.degree;
+    const int L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m);
+    const int nw = kProj ? L : m;
+    const int N0 = kProj ? 16 : Lp;
+    const bool band1 = Lp > 128;
+    const int b1 = Lp - 128;
+    const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + 4 * node);
+    const int64_t rs = a.item_start[item], re = a.item_end[item];
+    const int natoms = (int)((re - rs + kAtom - 1) / kAtom);
+    double* acc = kProj ? a.gacc + (int64_t)item * 256 : a.acc + (int64_t)item * a.acc_stride;
+    const double* val = kProj ? a.s : a.r;
+    bool first_drain = true;
+    int since = 0;
+    for (int at = 0; at < natoms && ok; ++at) {
+      const int st = stage;
+      if (pending[st]) {
+        ok = mbar_wait(&mbar[st], (ncommit[st] - 1u) & 1u);
+        pending[st] = false;
+      }
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      uint8_t* t0 = dsm + st * stage_bytes;
+      // rows past this node's basis must read as zero
+      if (hi[st] > nw) {
+        const int nz = (hi[st] - nw) * 8;  // 16-byte words per tile
+        for (int e = tid; e < 3 * nz; e += kMThreads) {
+          const int tt = e / nz, wi = e - tt * nz;
+          *reinterpret_cast<uint4*>(t0 + tt * tile_bytes + nw * 128 + wi * 16) = make_uint4(0, 0, 0, 0);
+        }
+      }
+      hi[st] = nw;
+      const int64_t i = rs + (int64_t)at * kAtom + k;
+      const bool valid = i < re;
+      double u = 0.0, v = 0.0, w = 0.0, fv = 0.0;
+      if (valid) {
+        u = fmt_local(a.x[i], F.c[0], F.s[0]);
+        v = fmt_local(a.y[i], F.c[1], F.s[1]);
+        w = fmt_local(a.z[i], F.c[2], F.s[2]);
+        fv = val[i];
+      }
+      gen_dispatch<kProj>(p, half, t0, tile_bytes, t0 + 3 * tile_bytes, k, valid, u, v, w, fv, F);
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t A0 = sbase + (uint32_t)st * stage_bytes;
+        if (!kProj) {
+          const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+          const uint32_t id0 = idesc_bf16(128, N0), id1 = band1 ? idesc_bf16(128, Lp - 128) : 0u;
+#pragma unroll
+          for (int pi = 0; pi < 6; ++pi)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t accf = (since > 0 || pi > 0 || kk > 0) ? 1u : 0u;
+              const uint32_t A = A0 + pa[pi] * tile_bytes + 32u * kk, B = A0 + pb[pi] * tile_bytes + 32u * kk;
+              tc_mma(tmem, sdesc(A), sdesc(B), id0, accf);
+              if (band1) tc_mma(tmem + (uint32_t)N0, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(B + 16u * 1024u), id1, accf);
+            }
+        } else {
+          const uint32_t S = A0 + 3u * tile_bytes;
+          const uint32_t id = idesc_bf16(128, 16);
+#pragma unroll
+          for (int ta = 0; ta < 3; ++ta)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t accf = (since > 0 || ta > 0 || kk > 0) ? 1u : 0u;
+              const uint32_t A = A0 + ta * tile_bytes + 32u * kk;
+              tc_mma(tmem, sdesc(A), sdesc(S + 32u * kk), id, accf);
+              if (band1) tc_mma(tmem + 16u, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(S + 32u * kk), id, accf);
+            }
+        }
+        tc_commit(&mbar[st]);
+      }
+      ncommit[st] += 1u;
+      pending[st] = true;
+      stage ^= 1;
+      ++since;
+      if (since == kDrainAtoms || at == natoms - 1) {
+        for (int s2 = 0; s2 < 2; ++s2)
+          if (pending[s2]) {
+            ok = mbar_wait(&mbar[s2], (ncommit[s2] - 1u) & 1u) && ok;
+            pending[s2] = false;
+          }
+        if (__syncthreads_or(!ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        if (!kProj) {
+          const int ncols = band1 ? N0 + (Lp - 128) : N0;
+          for (int c0 = 0; c0 < ncols; c0 += 16) {
+            float vv[16];
+            tc_ld16(trow + (uint32_t)c0, vv);
+            double* dst = acc + (int64_t)c0 * 128 + tid;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const double d = (double)vv[q];
+              dst[q * 128] = first_drain ? d : dst[q * 128] + d;
+            }
+          }
+        } else {
+          float vv[16];
+          tc_ld16(trow, vv);
+          double g = (double)vv[0] + (double)vv[1] + (double)vv[2];
+          acc[tid] = first_drain ? g : acc[tid] + g;
+          if (band1) {
+            tc_ld16(trow + 16u, vv);
+            g = (double)vv[0] + (double)vv[1] + (double)vv[2];
+            acc[128 + tid] = first_drain ? g : acc[128 + tid] + g;
+          }
+        }
+        first_drain = false;
+        since = 0;
+        tc_fence_before();
+        __syncthreads();
+      }
+    }
+    if (!ok) break;
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(a.err, FMT_ERR_TIMEOUT);
+    // give MMAs still in flight a bounded time before the memory is released
+    for (int s2 = 0; s2 < 2; ++s2)
+      if (pending[s2]) mbar_wait(&mbar[s2], (ncommit[s2] - 1u) & 1u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tc_dealloc(tmem, (uint32_t)a.tmem_cols);
+  }
+}
+
+// ------------------------------------------------------------------ change of basis
+// Fl (shared, L values, Alg. 2 index order over (a,b,c)) holds the fit in the
+// basis P_a(2^ex u) P_b(2^ey v) P_c(2^ez w); writes the same polynomial in the
+// moment basis u^l v^m w^n / (l! m! n!) (coef) and its Horner form (hcoef).
+// ws: shared scratch of 4 (p+1)^2 doubles + (p+1)^2 ints.
+__device__ void legendre_to_moments(const double* Fl, int p, const MFrame& F, double* coef, double* hcoef,
+                                    int stride, double* ws) {
+  const int P1 = p + 1;
+  double* C = ws;  // C[a][l][k] = coefficient of u^k in P_l(2^e_a u)
+  int* base = reinterpret_cast<int*>(ws + 3 * P1 * P1);  // index of (l, m, 0)
+  for (int e = threadIdx.x; e < 3 * P1 * P1; e += blockDim.x) {
+    const int ax = e / (P1 * P1), rem = e - ax * P1 * P1, l = rem / P1, kk = rem - l * P1;
+    double v = 0.0;
+    if (kk <= l && ((l - kk) & 1) == 0) {
+      // P_l(t) = 2^-l sum_j (-1)^j C(l,j) C(2l-2j, l) t^(l-2j)
+      const int j = (l - kk) / 2;
+      long long c1 = 1, c2 = 1;
+      for (int i = 1; i <= j; ++i) c1 = c1 * (l - j + i) / i;
+      for (int i = 1; i <= l; ++i) c2 = c2 * (2 * l - 2 * j - l + i) / i;
+      v = ldexp((double)(c1 * c2), -l);
+      if (j & 1) v = -v;
+      v = ldexp(v, F.e[ax] * kk);  // t^k = 2^(e k) u^k
+    }
+    C[e] = v;
+  }
+  if (threadIdx.x == 0) {
+    int idx = 0;
+    for (int l = 0; l <= p; ++l)
+      for (int mm = 0; mm <= p - l; ++mm) {
+        base[l * P1 + mm] = idx;
+        idx += p - l - mm + 1;
+      }
+  }
+  __syncthreads();
+  const double* Cx = C;
+  const double* Cy = C + P1 * P1;
+  const double* Cz = C + 2 * P1 * P1;
+  const int L = fmt_nmono_d(p);
+  for (int J = threadIdx.x; J < L; J += blockDim.x) {
+    int l = 0, mm = 0;
+    while (l < p && base[(l + 1) * P1] <= J) ++l;
+    while (mm < p - l && base[l * P1 + mm + 1] <= J) ++mm;
+    const int n = J - base[l * P1 + mm];
+    double h = 0.0;
+    for (int l2 = l; l2 <= p; l2 += 2)
+      for (int m2 = mm; m2 <= p - l2; m2 += 2) {
+        const double cxy = Cx[l2 * P1 + l] * Cy[m2 * P1 + mm];
+        const int b = base[l2 * P1 + m2];
+        for (int n2 = n; n2 <= p - l2 - m2; n2 += 2) h = fma(Fl[b + n2] * cxy, Cz[n2 * P1 + n], h);
+      }
+    hcoef[J] = h;
+    // F_lmn multiplies u^l v^m w^n / (l! m! n!)
+    double f = h;
+    for (int i = 2; i <= l; ++i) f *= (double)i;
+    for (int i = 2; i <= mm; ++i) f *= (double)i;
+    for (int i = 2; i <= n; ++i) f *= (double)i;
+    coef[J] = f;
+  }
+  for (int J = L + threadIdx.x; J < stride; J += blockDim.x) {
+    coef[J] = 0.0;
+    hcoef[J] = 0.0;
+  }
+  __syncthreads();
+}
+
+__host__ __device__ __forceinline__ int64_t ro_of(int i, int m) { return (int64_t)i * m - (int64_t)i * (i - 1) / 2; }
+__host__ __device__ __forceinline__ int conv_ws_doubles(int p) { return 4 * (p + 1) * (p + 1) + 2; }
+
+// ------------------------------------------------------------------ k_mfactor
+// One CTA per node.  Shared: the packed upper triangle of the m x m Gram
+// (row i at ro(i), m = nmono + 1 with r last), the initial diagonal, y, F and
+// the change-of-basis scratch.
+__global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
+  extern __shared__ double fsm[];
+  __shared__ int s_ok;
+  __shared__ double s_rkk;
+  const int64_t node = blockIdx.x;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  if (!mixed_eligible(pr, a.depth)) return;
+  const int tid = threadIdx.x;
+  const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
+  const int ncols = gram_cols(m);
+  double* G = fsm;
+  double* d0 = G + ro_of(m, m);
+  double* y = d0 + m;
+  double* Fl = y + m;
+  double* ws = Fl + m;
+  const int64_t i0 = a.node_item0[node];
+  const int ni = a.node_nitems[node];
+  // 1. sum the items' FP64 accumulators (column c, lane i) into G
+  for (int e = tid; e < ncols * 128; e += kFThreads) {
+    const int c = e >> 7, lane = e & 127;
+    int gi, gj;
+    if (c < Lp) {
+      gi = lane;
+      gj = c;
+      if (gi >= 128) continue;
+    } else {
+      gi = b1 + lane;
+      gj = 128 + (c - Lp);
+      if (gi < 128) continue;
+    }
+    if (gi > gj || gj >= m) continue;
+    double sum = 0.0;
+    for (int t = 0; t < ni; ++t) sum += a.acc[(i0 + t) * a.acc_stride + e];
+    G[ro_of(gi, m) + (gj - gi)] = sum;
+  }
+  __syncthreads();
+  for (int k = tid; k < L; k += kFThreads) d0[k] = G[ro_of(k, m)];
+  // 2. Cholesky, right-looking, on the packed rows; column L (r) is carried along
+  bool good = true;
+  for (int k = 0; k < L; ++k) {
+    __syncthreads();
+    if (tid == 0) {
+      const double d = G[ro_of(k, m)];
+      const bool okk = d0[k] > 0.0 && d > kPivotFloor * d0[k];
+      s_ok = okk;
+      s_rkk = okk ? sqrt(d) : 0.0;
+    }
+    __syncthreads();
+    if (!s_ok) {
+      good = false;
+      break;
+    }
+    const double rkk = s_rkk;
+    double* rowk = G + ro_of(k, m) - k;  // rowk[j] = G[k][j], j >= k
+    for (int j = k + 1 + tid; j < m; j += kFThreads) rowk[j] = rowk[j] / rkk;
+    if (tid == 0) rowk[k] = rkk;
+    __syncthreads();
+    for (int j = k + 1 + tid; j < m; j += kFThreads) {
+      const double gkj = rowk[j];
+      int64_t ri = ro_of(k + 1, m);
+      for (int i = k + 1; i <= j; ++i) {
+        G[ri + (j - i)] = fma(-rowk[i], gkj, G[ri + (j - i)]);
+        ri += m - i;
+      }
+    }
+  }
+  if (!good) return;  // FP64 path refits this node
+  __syncthreads();
+  // 3. R F = y (the scaled Q^T r column)
+  for (int k = tid; k < L; k += kFThreads) y[k] = G[ro_of(k, m) + (L - k)];
+  for (int j = L - 1; j >= 0; --j) {
+    __syncthreads();
+    if (tid == 0) Fl[j] = y[j] / G[ro_of(j, m)];
+    __syncthreads();
+    const double fj = Fl[j];
+    for (int i = tid; i < j; i += kFThreads) y[i] = fma(-G[ro_of(i, m) + (j - i)], fj, y[i]);
+  }
+  __syncthreads();
+  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + 4 * node);
+  for (int k = tid; k < L; k += kFThreads) {
+    Fl[k] = Fl[k] / F.sig;
+    a.lcoef[node * a.stride + k] = Fl[k];
+  }
+  // keep R-hat for the sweeps in the node's first accumulator
+  double* Rg = a.acc + i0 * a.acc_stride;
+  for (int64_t e = tid; e < ro_of(m, m); e += kFThreads) Rg[e] = G[e];
+  __syncthreads();
+  legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
+  if (tid == 0) {
+    a.flags[node] |= FMT_FLAG_MIXED;
+    a.deg_used[node] = p;
+  }
+}
+
+// ------------------------------------------------------------------ sweeps
+// s = r - Lambda F in FP64 (the residual of the current fit, r untouched)
+__global__ void __launch_bounds__(256) k_msresid(MArgs a) {
+  const int item = blockIdx.x;
+  const int64_t node = a.item_node[item];
+  if (!(a.flags[node] & FMT_FLAG_MIXED)) return;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
+  double c0, s0, c1, s1, c2, s2;
+  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  const int p = pr.degree, nm = fmt_nmono_d(p);
+  const double* Gc = a.hcoef + node * a.stride;
+  for (int64_t i = a.item_start[item] + threadIdx.x; i < a.item_end[item]; i += blockDim.x) {
+    const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+    a.s[i] = a.r[i] - fmt_horner(Gc, p, nm, u, v, w);
+  }
+}
+
+// F += R^{-1} R^{-T} g per node; on the last sweep a node whose update is
+// still above kConvergedRel of its fit loses FMT_FLAG_MIXED.
+__global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
+  extern __shared__ double usm[];
+  __shared__ double red[kFThreads / 32];
+  const int64_t node = blockIdx.x;
+  if (!(a.flags[node] & FMT_FLAG_MIXED)) return;
+  const int tid = threadIdx.x;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
+  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + 4 * node);
+  const int64_t i0 = a.node_item0[node];
+  const int ni = a.node_nitems[node];
+  const double* R = a.acc + i0 * a.acc_stride;
+  double* g = usm;
+  double* Fl = g + m;
+  double* ws = Fl + m;
+  for (int j = tid; j < L; j += kFThreads) {
+    const int e = j < 128 ? j : 128 + (j - b1);
+    double sum = 0.0;
+    for (int t = 0; t < ni; ++t) sum += a.gacc[(i0 + t) * 256 + e];
+    g[j] = sum / F.sig;
+    Fl[j] = a.lcoef[node * a.stride + j];
+  }
+  // R^T w = g (w overwrites g), column-oriented
+  double wn = 0.0;
+  for (int k = 0; k < L; ++k) {
+    __syncthreads();
+    const double* rowk = R + ro_of(k, m) - k;
+    const double wk = g[k] / rowk[k];
+    __syncthreads();
+    if (tid == 0) {
+      g[k] = wk;
+      wn += wk * wk;
+    }
+    for (int j = k + 1 + tid; j < L; j += kFThreads) g[j] = fma(-rowk[j], wk, g[j]);
+  }
+  // R d = w, d overwrites g
+  for (int j = L - 1; j >= 0; --j) {
+    __syncthreads();
+    const double dj = g[j] / R[ro_of(j, m)];
+    __syncthreads();
+    if (tid == 0) g[j] = dj;
+    for (int i = tid; i < j; i += kFThreads) g[i] = fma(-R[ro_of(i, m) + (j - i)], dj, g[i]);
+  }
+  __syncthreads();
+  for (int j = tid; j < L; j += kFThreads) {
+    Fl[j] += g[j];
+    a.lcoef[node * a.stride + j] = Fl[j];
+  }
+  __syncthreads();
+  // |R F| for the convergence test
+  double zn = 0.0;
+  for (int i = tid; i < L; i += kFThreads) {
+    const double* rowi = R + ro_of(i, m) - i;
+    double zi = 0.0;
+    for (int j = i; j < L; ++j) zi = fma(rowi[j], Fl[j], zi);
+    zn += zi * zi;
+  }
+  for (int o = 16; o > 0; o >>= 1) zn += __shfl_xor_sync(0xffffffffu, zn, o);
+  if ((tid & 31) == 0) red[tid >> 5] = zn;
+  __syncthreads();
+  double ztot = 0.0;
+  for (int i = 0; i < kFThreads / 32; ++i) ztot += red[i];
+  legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
+  if (tid == 0 && a.last_sweep && !(sqrt(wn) <= kConvergedRel * sqrt(ztot))) a.flags[node] &= ~FMT_FLAG_MIXED;
+}
+
+int g_nsm = 0;
+int nsm() {
+  if (g_nsm <= 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (g_nsm <= 0) g_nsm = 1;
+  }
+  return g_nsm;
+}
+
+MArgs make_margs(const fmt_tree* t, int depth, const fmt_mixed_bufs& b) {
+  const fmt_level& L = t->lv[depth];
+  MArgs a;
+  a.item_node = L.item_node;
+  a.item_start = L.item_start;
+  a.item_end = L.item_end;
+  a.sched = L.sched;
+  a.node_item0 = L.node_item0;
+  a.node_nitems = L.node_nitems;
+  a.n_items = (int)L.n_items;
+  a.n_nodes = L.n_nodes;
+  a.work = t->d_work;
+  a.prefix = L.prefix;
+  a.node_prob = L.prob;
+  a.prob = t->d_prob;
+  a.flags = L.flags;
+  a.deg_used = L.deg_used;
+  a.x = t->x;
+  a.y = t->y;
+  a.z = t->z;
+  a.r = t->r;
+  a.s = b.s;
+  a.mstat = b.mstat;
+  a.acc = b.acc;
+  a.acc_stride = b.acc_stride;
+  a.gacc = b.gacc;
+  a.lcoef = b.lcoef;
+  a.coef = L.coef;
+  a.hcoef = L.hcoef;
+  a.stride = t->nmono;
+  a.depth = depth;
+  a.MR = mrows_for(mixed_m_cap(L.max_m));
+  a.tmem_cols = 32;
+  a.last_sweep = 0;
+  a.err = t->d_err;
+  return a;
+}
+
+uint32_t pow2_cols(int c) {
+  uint32_t v = 32;
+  while ((int)v < c) v <<= 1;
+  return v;
+}
+
+template <bool kProj>
+cudaError_t launch_gram_t(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_items <= 0) return cudaSuccess;
+  MArgs a = make_margs(t, depth, b);
+  a.tmem_cols = (int)pow2_cols(kProj ? 32 : gram_cols(mixed_m_cap(L.max_m)));
+  const size_t smem = 1024 + 2 * (3 * (size_t)a.MR * 128 + (kProj ? 2048 : 0));
+  cudaError_t e = cudaFuncSetAttribute(k_mgram<kProj>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgram<kProj>, kMThreads, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) per_sm = 1;
+  const int tmem_cap = 512 / a.tmem_cols;  // tensor memory of an SM shared by its resident CTAs
+  if (per_sm > tmem_cap) per_sm = tmem_cap;
+  int64_t grid = (int64_t)nsm() * per_sm;
+  if (grid > L.n_items) grid = L.n_items;
+  if ((e = cudaMemsetAsync(t->d_work, 0, sizeof(int), s)) != cudaSuccess) return e;
+  k_mgram<kProj><<<(unsigned)grid, kMThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int mixed_m_cap(int max_m) {
+  const int cap = fmt_nmono_d(FMT_MIXED_MAX_DEGREE) + 1;
+  return max_m < cap ? max_m : cap;
+}
+size_t mixed_acc_stride(int max_m) { return (size_t)gram_cols(mixed_m_cap(max_m)) * 128; }
+
+cudaError_t launch_mixed_box(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_items <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(b.mstat, 0, sizeof(unsigned long long) * 4 * (size_t)L.n_nodes, s);
+  if (e != cudaSuccess) return e;
+  k_mbox<<<(unsigned)L.n_items, 256, 0, s>>>(make_margs(t, depth, b));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool projection,
+                              cudaStream_t s) {
+  return projection ? launch_gram_t<true>(t, depth, b, s) : launch_gram_t<false>(t, depth, b, s);
+}
+
+size_t mixed_factor_smem(int max_m) {
+  const int p_max = FMT_MIXED_MAX_DEGREE;
+  return sizeof(double) * ((size_t)ro_of(max_m, max_m) + 3 * (size_t)max_m + conv_ws_doubles(p_max));
+}
+
+cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_nodes <= 0) return cudaSuccess;
+  const size_t smem = mixed_factor_smem(mixed_m_cap(L.max_m));
+  cudaError_t e = cudaFuncSetAttribute(k_mfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_mfactor<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(make_margs(t, depth, b));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_sresid(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_items <= 0) return cudaSuccess;
+  k_msresid<<<(unsigned)L.n_items, 256, 0, s>>>(make_margs(t, depth, b));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool last,
+                                cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_nodes <= 0) return cudaSuccess;
+  MArgs a = make_margs(t, depth, b);
+  a.last_sweep = last ? 1 : 0;
+  const size_t smem = sizeof(double) * (2 * (size_t)mixed_m_cap(L.max_m) + conv_ws_doubles(FMT_MIXED_MAX_DEGREE));
+  k_mupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}

@@ -22,7 +22,9 @@ LIB_PATH = os.path.join(_HERE, "libfmt.so")
 
 FMT_OK, FMT_EINVAL, FMT_ENOMEM, FMT_ECUDA, FMT_ETIMEOUT, FMT_EINTERNAL = range(6)
 FMT_FP64, FMT_MIXED = 0, 1
-FMT_FLAG_NEAR_TAU, FMT_FLAG_RANK, FMT_FLAG_DEG_CLAMPED = 1, 2, 4
+FMT_FLAG_NEAR_TAU, FMT_FLAG_RANK, FMT_FLAG_DEG_CLAMPED, FMT_FLAG_MIXED = 1, 2, 4, 8
+MIXED_MAX_DEGREE = 9
+MIXED_MAX_SWEEPS = 3
 MAX_DEPTH = 21
 _STATUS = {0: "FMT_OK", 1: "FMT_EINVAL", 2: "FMT_ENOMEM", 3: "FMT_ECUDA", 4: "FMT_ETIMEOUT", 5: "FMT_EINTERNAL"}
 
@@ -36,7 +38,8 @@ class FmtError(RuntimeError):
 class fmt_params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("min_pts", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("tol_rel", ctypes.c_double), ("lo", ctypes.c_double * 3),
-                ("side", ctypes.c_double), ("chunk_rows", ctypes.c_int64)]
+                ("side", ctypes.c_double), ("chunk_rows", ctypes.c_int64), ("sweeps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _NL = MAX_DEPTH + 1
@@ -48,7 +51,8 @@ class fmt_stats(ctypes.Structure):
                 ("n_points", ctypes.c_int64), ("tau", ctypes.c_double), ("maxabs_f", ctypes.c_double),
                 ("nodes", ctypes.c_int64 * _NL), ("points", ctypes.c_int64 * _NL),
                 ("items", ctypes.c_int64 * _NL), ("chunk_rows", ctypes.c_int64 * _NL),
-                ("near_tau", ctypes.c_int64 * _NL), ("rank_flagged", ctypes.c_int64 * _NL)]
+                ("near_tau", ctypes.c_int64 * _NL), ("rank_flagged", ctypes.c_int64 * _NL),
+                ("mixed", ctypes.c_int64 * _NL), ("mixed_points", ctypes.c_int64 * _NL)]
 
 
 class fmt_export_header(ctypes.Structure):
@@ -65,7 +69,7 @@ EXPORTED = ["fmt_nmono", "oct_build", "oct_build_batch", "fit_level", "refine", 
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
             "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static"]
 STATIC_MAX_DEGREE = 8
-PROFILE_CLASSES = 16
+PROFILE_CLASSES = 24
 
 
 class fmt_profile(ctypes.Structure):
@@ -168,9 +172,12 @@ class Tree:
 
 
 def make_params(degree, max_depth, min_pts, tol_rel, lo=(0.0, 0.0, 0.0), side=1.0, chunk_rows=0,
-                precision=FMT_FP64):
+                precision=FMT_FP64, sweeps=0):
+    """fmt_params; precision FMT_FP64 or FMT_MIXED, sweeps (mixed only): 0 = 3, -1 = none."""
     p = fmt_params()
     p.degree, p.max_depth, p.min_pts, p.precision = degree, max_depth, min_pts, precision
+    p.sweeps = sweeps
+    p.reserved = 0
     p.tol_rel = tol_rel
     for a in range(3):
         p.lo[a] = lo[a]

@@ -45,6 +45,8 @@ int main(void){
          offsetof(fmt_params, chunk_rows), sizeof(fmt_stats));
   printf("%zu %zu %zu\n", sizeof(fmt_export_header), offsetof(fmt_export_header, tol_rel),
          offsetof(fmt_export_header, level_nodes));
+  printf("%zu %zu %zu %zu\n", offsetof(fmt_params, sweeps), offsetof(fmt_stats, mixed),
+         offsetof(fmt_stats, mixed_points), sizeof(fmt_profile));
   return 0;
 }
 '''
@@ -67,6 +69,10 @@ def test_struct_layouts_match_c():
     assert v[5] == ctypes.sizeof(F.fmt_export_header)
     assert v[6] == F.fmt_export_header.tol_rel.offset
     assert v[7] == F.fmt_export_header.level_nodes.offset
+    assert v[8] == F.fmt_params.sweeps.offset
+    assert v[9] == F.fmt_stats.mixed.offset
+    assert v[10] == F.fmt_stats.mixed_points.offset
+    assert v[11] == ctypes.sizeof(F.fmt_profile)
 
 
 def test_nmono_matches_paper_values():
@@ -76,7 +82,8 @@ def test_nmono_matches_paper_values():
 
 @pytest.mark.parametrize("field,value", [("degree", 15), ("degree", -1), ("max_depth", 22), ("min_pts", -3),
                                          ("tol_rel", -1.0), ("tol_rel", float("nan")), ("side", 0.0),
-                                         ("precision", 1), ("chunk_rows", -64)])
+                                         ("precision", 2), ("precision", -1), ("chunk_rows", -64),
+                                         ("sweeps", 4), ("sweeps", -2), ("reserved", 1)])
 def test_oct_build_rejects_bad_params_before_device_work(field, value):
     lib = F.load()
     p = F.make_params(4, 3, 64, 1e-4)
