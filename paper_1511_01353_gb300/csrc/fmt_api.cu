@@ -505,7 +505,7 @@ fmt_status ensure_mixed(fmt_tree* t, int depth, cudaStream_t s) {
     b.mstat = nullptr;
     b.lcoef = nullptr;
     b.cap_nodes = 0;
-    TRY(talloc(t, &b.mstat, 4 * L.n_nodes, s));
+    TRY(talloc(t, &b.mstat, 8 * L.n_nodes, s));
     TRY(talloc(t, &b.lcoef, (int64_t)t->nmono * L.n_nodes, s));
     b.cap_nodes = L.n_nodes;
   }

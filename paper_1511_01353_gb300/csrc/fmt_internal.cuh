@@ -176,7 +176,7 @@ struct fmt_plan_out {
 // Scratch of the mixed-precision fit (fmt_mixed.cu), grown per tree.
 struct fmt_mixed_bufs {
   double* s = nullptr;                  // n: sweep residual
-  unsigned long long* mstat = nullptr;  // 4 per node
+  unsigned long long* mstat = nullptr;  // 8 per node
   double* acc = nullptr;                // acc_stride per item
   int64_t acc_stride = 0;
   double* gacc = nullptr;               // 256 per item

@@ -41,6 +41,7 @@ constexpr int kFThreads = 256;   // factor / update kernels
 constexpr double kPivotFloor = 1e-6;
 constexpr double kConvergedRel = 1e-7;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
+constexpr int kMStat = 8;        // per-node words of mstat
 
 // ------------------------------------------------------------------ shapes
 __host__ __device__ __forceinline__ int mpad16(int m) { return (m + 15) & ~15; }
@@ -245,7 +246,7 @@ struct MArgs {
   const double* z;
   const double* r;
   double* s;                    // sweep residual, sorted order
-  unsigned long long* mstat;    // 4 per node: max |u|,|v|,|w| and max |r| (bit patterns)
+  unsigned long long* mstat;    // kMStat per node: max |u|,|v|,|w|, max |r| (bit patterns), last update norm
   double* acc;                  // per item: Gram accumulator (acc_stride doubles) / R-hat of the node
   int64_t acc_stride;
   double* gacc;                 // per item: projection accumulator, 256 doubles
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
   mr = block_max_d(mr, red);
   if (threadIdx.x == 0) {
     // non-negative doubles order like their bit patterns
-    unsigned long long* d = a.mstat + 4 * node;
+    unsigned long long* d = a.mstat + kMStat * node;
     atomicMax(d + 0, (unsigned long long)__double_as_longlong(mu));
     atomicMax(d + 1, (unsigned long long)__double_as_longlong(mv));
     atomicMax(d + 2, (unsigned long long)__double_as_longlong(mw));
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
     const int N0 = kProj ? 16 : Lp;
     const bool band1 = Lp > 128;
     const int b1 = Lp - 128;
-    const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + 4 * node);
+    const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
     const int64_t rs = a.item_start[item], re = a.item_end[item];
     const int natoms = (int)((re - rs + kAtom - 1) / kAtom);
     double* acc = kProj ? a.gacc + (int64_t)item * 256 : a.acc + (int64_t)item * a.acc_stride;
@@ -688,7 +689,7 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
     for (int i = tid; i < j; i += kFThreads) y[i] = fma(-G[ro_of(i, m) + (j - i)], fj, y[i]);
   }
   __syncthreads();
-  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + 4 * node);
+  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
   for (int k = tid; k < L; k += kFThreads) {
     Fl[k] = Fl[k] / F.sig;
     a.lcoef[node * a.stride + k] = Fl[k];
@@ -734,7 +735,7 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   const int tid = threadIdx.x;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
-  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + 4 * node);
+  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
   const int64_t i0 = a.node_item0[node];
   const int ni = a.node_nitems[node];
   const double* R = a.acc + i0 * a.acc_stride;
@@ -789,7 +790,21 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   double ztot = 0.0;
   for (int i = 0; i < kFThreads / 32; ++i) ztot += red[i];
   legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
-  if (tid == 0 && a.last_sweep && !(sqrt(wn) <= kConvergedRel * sqrt(ztot))) a.flags[node] &= ~FMT_FLAG_MIXED;
+  if (tid == 0) {
+    // |R d| = |Lambda d| is the change of the fit; with the previous change it
+    // gives the contraction rho and the remaining error ~ |R d| rho / (1 - rho)
+    unsigned long long* slot = a.mstat + kMStat * node + 4;
+    const double upd = sqrt(wn), zn = sqrt(ztot), prev = __longlong_as_double((long long)*slot);
+    *slot = (unsigned long long)__double_as_longlong(upd);
+    if (a.last_sweep) {
+      bool conv = upd <= kConvergedRel * zn;
+      if (!conv && prev > 0.0 && upd < prev) {
+        const double rho = upd / prev;
+        conv = upd * rho / (1.0 - rho) <= kConvergedRel * zn;
+      }
+      if (!conv) a.flags[node] &= ~FMT_FLAG_MIXED;
+    }
+  }
 }
 
 int g_nsm = 0;
@@ -880,7 +895,7 @@ size_t mixed_acc_stride(int max_m) { return (size_t)gram_cols(mixed_m_cap(max_m)
 cudaError_t launch_mixed_box(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
   const fmt_level& L = t->lv[depth];
   if (L.n_items <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(b.mstat, 0, sizeof(unsigned long long) * 4 * (size_t)L.n_nodes, s);
+  cudaError_t e = cudaMemsetAsync(b.mstat, 0, sizeof(unsigned long long) * kMStat * (size_t)L.n_nodes, s);
   if (e != cudaSuccess) return e;
   k_mbox<<<(unsigned)L.n_items, 256, 0, s>>>(make_margs(t, depth, b));
   return cudaGetLastError();

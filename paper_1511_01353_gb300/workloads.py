@@ -218,6 +218,7 @@ class Batch:
     zq: np.ndarray
     tprob: np.ndarray        # problem of every target (int32)
     fkind: list              # per problem: ("franke", shift, scale) or ("gauss", centres, exps, weights)
+    cloud: list = dataclasses.field(default_factory=list)  # per problem: "uniform" or "clusters" 
 
     @property
     def n_problems(self):
@@ -258,12 +259,13 @@ def batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536, deg_min:
     degrees = (deg_min + np.floor(u[:, 1] * (deg_max - deg_min + 1))).astype(np.int32)
     degrees = np.minimum(degrees, deg_max)
     nt = targets_per_problem
-    xs, ys, zs, fs, kinds, txs, tys, tzs = [], [], [], [], [], [], [], []
+    xs, ys, zs, fs, kinds, txs, tys, tzs, clouds = [], [], [], [], [], [], [], [], []
     for i in range(P):
         n = int(counts[i])
         if u[i, 2] < 0.5:
             x, y, z = uniform_points(seed, 1000 + i, n)
             tx, ty, tz = uniform_points(seed, 1000000 + i, nt)
+            clouds.append("uniform")
         else:
             k = 1 + int(u[i, 3] * 8) if u[i, 3] < 1.0 else 8
             sig = 0.02 + 0.18 * u[i, 4]
@@ -277,6 +279,7 @@ def batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536, deg_min:
                         np.concatenate([p[2] for p in parts]))
             x, y, z = cloud(n, 400000)
             tx, ty, tz = cloud(nt, 1200000)
+            clouds.append("clusters")
         if u[i, 5] < 0.5:
             shift = -0.2 + 0.4 * u[i, 6:9]
             scale = 0.5 + 1.5 * u[i, 9]
@@ -295,4 +298,4 @@ def batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536, deg_min:
     return Batch("batch_fp64_%dproblems_p%d-%d" % (P, deg_min, deg_max), max_depth, min_pts, tol_rel, offsets,
                  degrees, boxes, np.concatenate(xs), np.concatenate(ys), np.concatenate(zs), np.concatenate(fs),
                  np.arange(P + 1, dtype=np.int64) * nt, np.concatenate(txs), np.concatenate(tys),
-                 np.concatenate(tzs), tprob, kinds)
+                 np.concatenate(tzs), tprob, kinds, clouds)
