@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="run warmup+steps, print nothing (for ncu)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="path of the headline value; the other path is reported in the 'mixed' / 'fp64' block")
+    ap.add_argument("--no-second-path", action="store_true", help="skip the block of the other precision")
     return ap.parse_args()
 
 
@@ -211,7 +214,9 @@ def run_reference(args, rank, world):
     cores = O.num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+bf16x3 (tensor-core Gram, FP64 factor/refine)",
+        "data": "synthetic",
             "config": {"workload": w.name, "sample_points": n, "degree": w.degree, "max_depth": w.max_depth,
                        "min_pts": w.min_pts, "tol_rel": w.tol_rel},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -277,14 +282,16 @@ def main():
     F.load()
     stream = torch.cuda.Stream()
     w = make_workload(args, rank)
-    params = None if args.workload == "batch" else F.make_params(w.degree, w.max_depth, w.min_pts, w.tol_rel)
+    prec_of = {"fp64": F.FMT_FP64, "mixed": F.FMT_MIXED}
+    params = None if args.workload == "batch" else F.make_params(w.degree, w.max_depth, w.min_pts, w.tol_rel,
+                                                                 precision=prec_of[args.precision])
 
     def dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
 
     is_batch = args.workload == "batch"
     if is_batch:
-        params = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel)
+        params = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel, precision=prec_of[args.precision])
         w.n = int(w.offsets[-1])
         w.m = int(w.xq.shape[0])
         w.name = w.name
@@ -293,11 +300,12 @@ def main():
     xq, yq, zq = dev(w.xq), dev(w.yq), dev(w.zq)
     out = torch.empty(w.m, dtype=torch.float64, device="cuda")
 
-    def build(xx, yy, zz, ff):
+    def build(xx, yy, zz, ff, prm=None):
+        prm = params if prm is None else prm
         if is_batch:
-            return F.oct_build_batch(params, w.offsets, xx, yy, zz, ff, degrees=w.degrees, boxes=w.boxes,
+            return F.oct_build_batch(prm, w.offsets, xx, yy, zz, ff, degrees=w.degrees, boxes=w.boxes,
                                      stream=stream)
-        return F.oct_build(params, xx, yy, zz, ff, stream)
+        return F.oct_build(prm, xx, yy, zz, ff, stream)
 
     def evaluate(tree, qx, qy, qz):
         if is_batch:
@@ -309,9 +317,9 @@ def main():
 
     level_events = []
 
-    def fit_with_level_events(lv):
+    def fit_with_level_events(lv, prm=None):
         # the driver loop of F.fit, with events around every fit_level
-        tree = build(x, y, z, f)
+        tree = build(x, y, z, f, prm)
         d = 0
         while True:
             a = torch.cuda.Event(enable_timing=True)
@@ -325,14 +333,14 @@ def main():
             d += 1
         return tree
 
-    def step(timed):
+    def step(timed, prm=None):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e2 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            tree = fit_with_level_events(level_events if timed else [])
+            tree = fit_with_level_events(level_events if timed else [], prm)
             e1.record(stream)
             evaluate(tree, xq, yq, zq)
             e2.record(stream)
@@ -421,6 +429,48 @@ def main():
                    "share": (v["ms"] / total_ms if total_ms else None)} for k, v in prof.items() if v["launches"]}
     gpu_launches = sum(v["launches"] for v in prof.values())
 
+    # the other precision on the same inputs: throughput and its error against the headline path
+    other = None
+    if not args.no_second_path and not args.profile_only:
+        oprec = "mixed" if args.precision == "fp64" else "fp64"
+        oparams = F.make_params(params.degree, params.max_depth, params.min_pts, params.tol_rel,
+                                precision=prec_of[oprec])
+        for _ in range(max(1, min(args.warmup, 2))):
+            tr, _ = step(False, oparams)
+            stream.synchronize()
+            tr.close()
+        F.fmt_profile_enable(True)
+        oev, otrees = [], []
+        for _ in range(args.steps):
+            tr, ev = step(False, oparams)
+            oev.append(ev)
+            otrees.append(tr)
+        stream.synchronize()
+        oprof = F.fmt_profile_read()
+        F.fmt_profile_enable(False)
+        ofit = reduce_max([sum(a.elapsed_time(b) for a, b, _ in oev) / len(oev) / 1e3,
+                           sum(b.elapsed_time(c) for _, b, c in oev) / len(oev) / 1e3], dist, device="cuda")
+        opred = out.cpu().numpy()
+        ost = F.fmt_tree_stats(otrees[-1])
+        for tr in otrees:
+            tr.close()
+        fscale = max(float(np.max(np.abs(w.f))), 1e-300)
+        mst = ost if oprec == "mixed" else stats
+        mixed_pts = sum(int(mst.mixed_points[d]) for d in range(mst.n_levels))
+        all_pts = sum(int(mst.points[d]) for d in range(mst.n_levels))
+        gram = oprof.get("mixed_gram", {}) if oprec == "mixed" else prof.get("mixed_gram", {})
+        other = {"precision": oprec, "value": job_throughput(world, w.n, ofit[0]), "unit": UNIT,
+                 "evals_per_s": job_throughput(world, w.m, ofit[1]), "fit_ms": ofit[0] * 1e3,
+                 "eval_ms": ofit[1] * 1e3,
+                 "fit_speedup_mixed_over_fp64": (fit_s / ofit[0]) if oprec == "mixed" else (ofit[0] / fit_s),
+                 "max_abs_diff_vs_headline_over_max_f": float(np.max(np.abs(opred - pred))) / fscale,
+                 "mixed_share_of_fitted_points": mixed_pts / max(all_pts, 1),
+                 "mixed_nodes": int(sum(mst.mixed[d] for d in range(mst.n_levels))),
+                 "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps}
+                             for k, v in oprof.items() if v["launches"]},
+                 "note": "error vs the FP64 GPU path, which matches the FP64 oracle to 1e-10 max|f|; "
+                         "target for the mixed path: 1e-6 max|f|"}
+
     e2e = None
     if not args.no_e2e:
         # end to end through the public API: pinned host inputs -> device -> fit -> evaluate -> host
@@ -468,7 +518,9 @@ def main():
     line = {
         "metric": METRIC, "value": job_throughput(world, w.n, fit_s), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (fit_s + eval_s) * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+bf16x3 (tensor-core Gram, FP64 factor/refine)",
+        "data": "synthetic",
         "config": {"workload": w.name, "points": w.n, "targets": w.m,
                    "degree": ("%d..%d per problem" % (w.degrees.min(), w.degrees.max())) if is_batch else w.degree,
                    "problems": w.n_problems if is_batch else 1,
@@ -506,6 +558,7 @@ def main():
                           "vs": ("generating function of each problem at its targets" if is_batch
                                  else "closed-form Franke at the targets")}, **acc_extra),
         "e2e": e2e, "cpu_baseline": cpu,
+        "precision": args.precision, ("mixed" if args.precision == "fp64" else "fp64"): other,
     }
     last.close()
     if rank == 0:

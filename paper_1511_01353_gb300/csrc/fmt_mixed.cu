@@ -257,6 +257,7 @@ struct MArgs {
   int depth;
   int MR;                       // operand-tile rows of the level
   int tmem_cols;
+  int nstages;                  // operand-tile stages (1 or 2) of k_mgram
   int last_sweep;
   int* err;
 };
@@ -295,14 +296,82 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
 }
 
 // ------------------------------------------------------------------ k_mgram
+// Gram mode: the basis in FP32, every value split into three BF16 terms
+// (floating point; the six leading products are accumulated).
+// Projection mode: the basis in double-float (pairs of FP32, about 48 bits)
+// and s in FP64, both cut into four signed 8-bit digits of a fixed-point
+// number (|P_l(t)| <= 1 for |t| <= 1, and |s| is scaled below 1 per node):
+//   v = (d0 2^23 + d1 2^15 + d2 2^7 + d3) 2^-30,   |d| <= 128,
+// so every digit is an exact BF16 integer and each digit pair's sum over 256
+// rows stays below 2^22: the FP32 tensor-core accumulation is exact, each
+// pair has its own accumulator, and the pairs are combined in FP64.
+
+// double-float arithmetic (Dekker / Knuth error-free transformations)
+struct dfl {
+  float h, l;
+};
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_sub(dfl x, dfl y) {
+  const float s = __fsub_rn(x.h, y.h);
+  const float bb = __fsub_rn(s, x.h);
+  const float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(-y.h, bb));
+  return fast_two_sum(s, __fadd_rn(e, __fsub_rn(x.l, y.l)));
+}
+__device__ __forceinline__ dfl df_of(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+template <int P>
+__device__ __forceinline__ void legendre_df(double t, dfl (&q)[P + 1]) {
+  q[0] = {1.0f, 0.0f};
+  if (P >= 1) q[1] = df_of(t);
+#pragma unroll
+  for (int k = 1; k < P; ++k) {
+    const double ad = (double)(2 * k + 1) / (double)(k + 1), bd = (double)k / (double)(k + 1);
+    const dfl a = {(float)ad, (float)(ad - (double)(float)ad)}, b = {(float)bd, (float)(bd - (double)(float)bd)};
+    q[k + 1] = df_sub(df_mul(a, df_mul(q[1], q[k])), df_mul(b, q[k - 1]));
+  }
+}
+// four signed digits of round(v 2^30), |v| <= 1
+__device__ __forceinline__ void digits4(int X, int (&d)[4]) {
+  d[0] = (X + (1 << 22)) >> 23;
+  X -= d[0] << 23;
+  d[1] = (X + (1 << 14)) >> 15;
+  X -= d[1] << 15;
+  d[2] = (X + (1 << 6)) >> 7;
+  d[3] = X - (d[2] << 7);
+}
+__device__ __forceinline__ void put_digits(uint8_t* t0, uint32_t tile_bytes, int j, int k, int X) {
+  int d[4];
+  digits4(X, d);
+  const uint32_t o = sw_off(j, k);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<__nv_bfloat16*>(t0 + q * tile_bytes + o) = __float2bfloat16_rn((float)d[q]);
+}
+__device__ __forceinline__ int fixed30(dfl v) {
+  return __float2int_rn(__fmul_rn(v.h, 1073741824.0f)) + __float2int_rn(__fmul_rn(v.l, 1073741824.0f));
+}
+__host__ __device__ constexpr int digit_exp(int q) { return q == 0 ? -7 : q == 1 ? -15 : q == 2 ? -23 : -30; }
+
 // One 64-row atom of the operand tiles.  Thread (k, half): point k, and half
 // of the basis rows (the split point is a compile-time constant, so each
 // instantiation stores only its own rows).
-template <int P, bool kProj, int HALF>
-__device__ __forceinline__ void gen_rows(uint8_t* t0, uint32_t tile_bytes, uint8_t* stile, int k, bool valid,
-                                         double u, double v, double w, double val, const MFrame& F) {
+template <int P, int HALF>
+__device__ __forceinline__ void gen_rows_gram(uint8_t* t0, uint32_t tile_bytes, int k, bool valid, double u,
+                                              double v, double w, double val, const MFrame& F) {
   constexpr int L = (P + 1) * (P + 2) * (P + 3) / 6;
-  constexpr int NW = kProj ? L : L + 1;  // rows written: basis (+ r in Gram mode)
+  constexpr int NW = L + 1;  // basis rows and r
   constexpr int J1 = (NW + 1) / 2;
   constexpr int jlo = HALF == 0 ? 0 : J1, jhi = HALF == 0 ? J1 : NW;
   float qx[P + 1], qy[P + 1], qz[P + 1];
@@ -319,49 +388,59 @@ __device__ __forceinline__ void gen_rows(uint8_t* t0, uint32_t tile_bytes, uint8
       for (int n = 0; n <= P - l - mm; ++n, ++j)
         if (j >= jlo && j < jhi) put3(t0, tile_bytes, j, k, valid ? plm * qz[n] : 0.0f);
     }
-  const float sv = valid ? (float)(val * F.sig) : 0.0f;
-  if (!kProj) {
-    if (L >= jlo && L < jhi) put3(t0, tile_bytes, L, k, sv);
-  } else if (HALF == 0) {
-    __nv_bfloat16 h, m, l;
-    split3(sv, h, m, l);
-    *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(0, k)) = h;
-    *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(1, k)) = m;
-    *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(2, k)) = l;
+  if (L >= jlo && L < jhi) put3(t0, tile_bytes, L, k, valid ? (float)(val * F.sig) : 0.0f);
+}
+
+template <int P, int HALF>
+__device__ __forceinline__ void gen_rows_proj(uint8_t* t0, uint32_t tile_bytes, uint8_t* stile, int k, bool valid,
+                                              double u, double v, double w, double sval, double sscale,
+                                              const MFrame& F) {
+  constexpr int L = (P + 1) * (P + 2) * (P + 3) / 6;
+  constexpr int J1 = (L + 1) / 2;
+  constexpr int jlo = HALF == 0 ? 0 : J1, jhi = HALF == 0 ? J1 : L;
+  dfl qx[P + 1], qy[P + 1], qz[P + 1];
+  legendre_df<P>(u * F.ex[0], qx);
+  legendre_df<P>(v * F.ex[1], qy);
+  legendre_df<P>(w * F.ex[2], qz);
+  int j = 0;
+#pragma unroll
+  for (int l = 0; l <= P; ++l)
+#pragma unroll
+    for (int mm = 0; mm <= P - l; ++mm) {
+      const dfl plm = df_mul(qx[l], qy[mm]);
+#pragma unroll
+      for (int n = 0; n <= P - l - mm; ++n, ++j)
+        if (j >= jlo && j < jhi) put_digits(t0, tile_bytes, j, k, valid ? fixed30(df_mul(plm, qz[n])) : 0);
+    }
+  if (HALF == 0) {
+    // |s sscale| < 1; round(s sscale 2^30) exactly from FP64
+    const int X = valid ? __double2int_rn(sval * sscale * 1073741824.0) : 0;
+    int d[4];
+    digits4(X, d);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(q, k)) = __float2bfloat16_rn((float)d[q]);
   }
 }
 
-template <bool kProj>
-__device__ __forceinline__ void gen_dispatch(int p, int half, uint8_t* t0, uint32_t tb, uint8_t* stile, int k,
-                                             bool valid, double u, double v, double w, double val,
-                                             const MFrame& F) {
-#define FMT_GEN_CASE(PP)                                                     \
-  case PP:                                                                   \
-    if (half == 0)                                                           \
-      gen_rows<PP, kProj, 0>(t0, tb, stile, k, valid, u, v, w, val, F);      \
-    else                                                                     \
-      gen_rows<PP, kProj, 1>(t0, tb, stile, k, valid, u, v, w, val, F);      \
-    break;
-  switch (p) {
-    FMT_GEN_CASE(0)
-    FMT_GEN_CASE(1)
-    FMT_GEN_CASE(2)
-    FMT_GEN_CASE(3)
-    FMT_GEN_CASE(4)
-    FMT_GEN_CASE(5)
-    FMT_GEN_CASE(6)
-    FMT_GEN_CASE(7)
-    FMT_GEN_CASE(8)
-    FMT_GEN_CASE(9)
-    default:
-      break;
+#define FMT_DEG_SWITCH(p, CALL) \
+  switch (p) {                  \
+    case 0: CALL(0); break;     \
+    case 1: CALL(1); break;     \
+    case 2: CALL(2); break;     \
+    case 3: CALL(3); break;     \
+    case 4: CALL(4); break;     \
+    case 5: CALL(5); break;     \
+    case 6: CALL(6); break;     \
+    case 7: CALL(7); break;     \
+    case 8: CALL(8); break;     \
+    case 9: CALL(9); break;     \
+    default: break;             \
   }
-#undef FMT_GEN_CASE
-}
 
 // Persistent over the level's work items (largest first).  Gram mode
 // (kProj = false): acc[item] += [B | sig r]^T [B | sig r], column-major by
-// TMEM column, 128 lanes each.  Projection mode: gacc[item] += B^T (sig s),
+// TMEM column, 128 lanes each.  Projection mode: gacc[item] += B^T s,
 // band 0 rows in [0,128), band 1 rows in [128,256).
 template <bool kProj>
 __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
@@ -369,11 +448,13 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_item;
+  constexpr int kTiles = kProj ? 4 : 3;
   const int tid = threadIdx.x, warp = tid >> 5;
   uint8_t* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
   const uint32_t tile_bytes = (uint32_t)a.MR * 128u;
-  const uint32_t stage_bytes = 3u * tile_bytes + (kProj ? 2048u : 0u);
-  const uint32_t total = 2u * stage_bytes;
+  const uint32_t stage_bytes = kTiles * tile_bytes + (kProj ? 2048u : 0u);
+  const int nst = a.nstages;
+  const uint32_t total = (uint32_t)nst * stage_bytes;
   for (uint32_t o = 16u * tid; o < total; o += 16u * kMThreads) *reinterpret_cast<uint4*>(dsm + o) = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
@@ -410,11 +491,19 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
     const bool band1 = Lp > 128;
     const int b1 = Lp - 128;
     const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
+    // projection: |s| scaled below 1 by a power of two (max |s| of the node, this sweep)
+    int se = 0;
+    if (kProj) {
+      const double ms = __longlong_as_double((long long)a.mstat[kMStat * node + 5]);
+      if (ms > 0.0) frexp(ms, &se);
+    }
+    const double sscale = ldexp(1.0, -se);
     const int64_t rs = a.item_start[item], re = a.item_end[item];
     const int natoms = (int)((re - rs + kAtom - 1) / kAtom);
     double* acc = kProj ? a.gacc + (int64_t)item * 256 : a.acc + (int64_t)item * a.acc_stride;
     const double* val = kProj ? a.s : a.r;
     bool first_drain = true;
+    double g0 = 0.0, g1 = 0.0;  // projection: this lane's FP64 sums of band 0 and band 1
     int since = 0;
     for (int at = 0; at < natoms && ok; ++at) {
       const int st = stage;
@@ -430,7 +519,7 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
       // rows past this node's basis must read as zero
       if (hi[st] > nw) {
         const int nz = (hi[st] - nw) * 8;  // 16-byte words per tile
-        for (int e = tid; e < 3 * nz; e += kMThreads) {
+        for (int e = tid; e < kTiles * nz; e += kMThreads) {
           const int tt = e / nz, wi = e - tt * nz;
           *reinterpret_cast<uint4*>(t0 + tt * tile_bytes + nw * 128 + wi * 16) = make_uint4(0, 0, 0, 0);
         }
@@ -445,7 +534,23 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
         w = fmt_local(a.z[i], F.c[2], F.s[2]);
         fv = val[i];
       }
-      gen_dispatch<kProj>(p, half, t0, tile_bytes, t0 + 3 * tile_bytes, k, valid, u, v, w, fv, F);
+      if (kProj) {
+#define FMT_PROJ_CALL(PP)                                                                                   \
+  if (half == 0)                                                                                             \
+    gen_rows_proj<PP, 0>(t0, tile_bytes, t0 + 4 * tile_bytes, k, valid, u, v, w, fv, sscale, F);             \
+  else                                                                                                       \
+    gen_rows_proj<PP, 1>(t0, tile_bytes, t0 + 4 * tile_bytes, k, valid, u, v, w, fv, sscale, F);
+        FMT_DEG_SWITCH(p, FMT_PROJ_CALL)
+#undef FMT_PROJ_CALL
+      } else {
+#define FMT_GRAM_CALL(PP)                                                  \
+  if (half == 0)                                                            \
+    gen_rows_gram<PP, 0>(t0, tile_bytes, k, valid, u, v, w, fv, F);         \
+  else                                                                      \
+    gen_rows_gram<PP, 1>(t0, tile_bytes, k, valid, u, v, w, fv, F);
+        FMT_DEG_SWITCH(p, FMT_GRAM_CALL)
+#undef FMT_GRAM_CALL
+      }
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
@@ -464,23 +569,24 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
               if (band1) tc_mma(tmem + (uint32_t)N0, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(B + 16u * 1024u), id1, accf);
             }
         } else {
-          const uint32_t S = A0 + 3u * tile_bytes;
+          // digit q of the basis -> its own accumulators: columns [32 q, 32 q + 16) band 0, +16 band 1
+          const uint32_t S = A0 + 4u * tile_bytes;
           const uint32_t id = idesc_bf16(128, 16);
 #pragma unroll
-          for (int ta = 0; ta < 3; ++ta)
+          for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t accf = (since > 0 || ta > 0 || kk > 0) ? 1u : 0u;
-              const uint32_t A = A0 + ta * tile_bytes + 32u * kk;
-              tc_mma(tmem, sdesc(A), sdesc(S + 32u * kk), id, accf);
-              if (band1) tc_mma(tmem + 16u, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(S + 32u * kk), id, accf);
+              const uint32_t accf = (since > 0 || kk > 0) ? 1u : 0u;
+              const uint32_t A = A0 + q * tile_bytes + 32u * kk;
+              tc_mma(tmem + 32u * q, sdesc(A), sdesc(S + 32u * kk), id, accf);
+              if (band1) tc_mma(tmem + 32u * q + 16u, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(S + 32u * kk), id, accf);
             }
         }
         tc_commit(&mbar[st]);
       }
       ncommit[st] += 1u;
       pending[st] = true;
-      stage ^= 1;
+      stage = (stage + 1) % nst;
       ++since;
       if (since == kDrainAtoms || at == natoms - 1) {
         for (int s2 = 0; s2 < 2; ++s2)
@@ -507,14 +613,18 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
             }
           }
         } else {
-          float vv[16];
-          tc_ld16(trow, vv);
-          double g = (double)vv[0] + (double)vv[1] + (double)vv[2];
-          acc[tid] = first_drain ? g : acc[tid] + g;
-          if (band1) {
-            tc_ld16(trow + 16u, vv);
-            g = (double)vv[0] + (double)vv[1] + (double)vv[2];
-            acc[128 + tid] = first_drain ? g : acc[128 + tid] + g;
+          // exact integer sums per digit pair (q basis, c of s), weighted in FP64
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float vv[16];
+            tc_ld16(trow + 32u * q, vv);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) g0 += ldexp((double)vv[c], digit_exp(q) + digit_exp(c));
+            if (band1) {
+              tc_ld16(trow + 32u * q + 16u, vv);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) g1 += ldexp((double)vv[c], digit_exp(q) + digit_exp(c));
+            }
           }
         }
         first_drain = false;
@@ -524,6 +634,11 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
       }
     }
     if (!ok) break;
+    if (kProj) {
+      // B^T s of this item: undo the scale of s
+      acc[tid] = ldexp(g0, se);
+      if (band1) acc[128 + tid] = ldexp(g1, se);
+    }
   }
   if (!ok) {
     if (tid == 0) atomicOr(a.err, FMT_ERR_TIMEOUT);
@@ -719,10 +834,17 @@ __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
   fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
   const int p = pr.degree, nm = fmt_nmono_d(p);
   const double* Gc = a.hcoef + node * a.stride;
+  double ms = 0.0;
   for (int64_t i = a.item_start[item] + threadIdx.x; i < a.item_end[item]; i += blockDim.x) {
     const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
-    a.s[i] = a.r[i] - fmt_horner(Gc, p, nm, u, v, w);
+    const double si = a.r[i] - fmt_horner(Gc, p, nm, u, v, w);
+    a.s[i] = si;
+    ms = fmax(ms, fabs(si));
   }
+  __shared__ double red[8];
+  ms = block_max_d(ms, red);
+  if (threadIdx.x == 0)
+    atomicMax(a.mstat + kMStat * node + 5, (unsigned long long)__double_as_longlong(ms));
 }
 
 // F += R^{-1} R^{-T} g per node; on the last sweep a node whose update is
@@ -796,6 +918,7 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
     unsigned long long* slot = a.mstat + kMStat * node + 4;
     const double upd = sqrt(wn), zn = sqrt(ztot), prev = __longlong_as_double((long long)*slot);
     *slot = (unsigned long long)__double_as_longlong(upd);
+    a.mstat[kMStat * node + 5] = 0ull;  // max |s| of the next sweep
     if (a.last_sweep) {
       bool conv = upd <= kConvergedRel * zn;
       if (!conv && prev > 0.0 && upd < prev) {
@@ -851,6 +974,7 @@ MArgs make_margs(const fmt_tree* t, int depth, const fmt_mixed_bufs& b) {
   a.depth = depth;
   a.MR = mrows_for(mixed_m_cap(L.max_m));
   a.tmem_cols = 32;
+  a.nstages = 2;
   a.last_sweep = 0;
   a.err = t->d_err;
   return a;
@@ -867,8 +991,11 @@ cudaError_t launch_gram_t(const fmt_tree* t, int depth, const fmt_mixed_bufs& b,
   const fmt_level& L = t->lv[depth];
   if (L.n_items <= 0) return cudaSuccess;
   MArgs a = make_margs(t, depth, b);
-  a.tmem_cols = (int)pow2_cols(kProj ? 32 : gram_cols(mixed_m_cap(L.max_m)));
-  const size_t smem = 1024 + 2 * (3 * (size_t)a.MR * 128 + (kProj ? 2048 : 0));
+  // projection: 4 digits x 2 bands x 16 columns; Gram: the two bands of the matrix
+  a.tmem_cols = (int)pow2_cols(kProj ? 128 : gram_cols(mixed_m_cap(L.max_m)));
+  const size_t stage = (kProj ? 4 : 3) * (size_t)a.MR * 128 + (kProj ? 2048 : 0);
+  a.nstages = 1024 + 2 * stage <= 227 * 1024 ? 2 : 1;
+  const size_t smem = 1024 + a.nstages * stage;
   cudaError_t e = cudaFuncSetAttribute(k_mgram<kProj>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
