@@ -214,9 +214,7 @@ def run_reference(args, rank, world):
     cores = O.num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+bf16x3 (tensor-core Gram, FP64 factor/refine)",
-        "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "sample_points": n, "degree": w.degree, "max_depth": w.max_depth,
                        "min_pts": w.min_pts, "tol_rel": w.tol_rel},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
