@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
     const int e = j < 128 ? j : 128 + (j - b1);
     double sum = 0.0;
     for (int t = 0; t < ni; ++t) sum += a.gacc[(i0 + t) * 256 + e];
-    g[j] = sum / F.sig;
+    g[j] = sum;  // the projection kernel has undone the scale of s
     Fl[j] = a.lcoef[node * a.stride + j];
   }
   // R^T w = g (w overwrites g), column-oriented
