@@ -344,12 +344,12 @@ __device__ __forceinline__ void legendre_df(double t, dfl (&q)[P + 1]) {
 }
 // four signed digits of round(v 2^30), |v| <= 1
 __device__ __forceinline__ void digits4(int X, int (&d)[4]) {
-  d[0] = (X + (1 << 22)) >> 23;
-  X -= d[0] << 23;
+  d[0] = (X + (1 << 22)) >> 23;  // arithmetic shifts: floor division
+  X -= d[0] * (1 << 23);
   d[1] = (X + (1 << 14)) >> 15;
-  X -= d[1] << 15;
+  X -= d[1] * (1 << 15);
   d[2] = (X + (1 << 6)) >> 7;
-  d[3] = X - (d[2] << 7);
+  d[3] = X - d[2] * (1 << 7);
 }
 __device__ __forceinline__ void put_digits(uint8_t* t0, uint32_t tile_bytes, int j, int k, int X) {
   int d[4];
