@@ -34,7 +34,6 @@
 
 namespace {
 
-constexpr int kMThreads = 128;   // one warpgroup: thread i reads TMEM lane i
 constexpr int kAtom = 64;        // rows per operand tile: one 128-byte swizzle row of BF16
 constexpr int kDrainAtoms = 4;   // FP32 -> FP64 promotion every 256 rows
 constexpr int kFThreads = 256;   // factor / update kernels
@@ -331,17 +330,6 @@ __device__ __forceinline__ dfl df_of(double v) {
   const float h = __double2float_rn(v);
   return {h, __double2float_rn(v - (double)h)};
 }
-template <int P>
-__device__ __forceinline__ void legendre_df(double t, dfl (&q)[P + 1]) {
-  q[0] = {1.0f, 0.0f};
-  if (P >= 1) q[1] = df_of(t);
-#pragma unroll
-  for (int k = 1; k < P; ++k) {
-    const double ad = (double)(2 * k + 1) / (double)(k + 1), bd = (double)k / (double)(k + 1);
-    const dfl a = {(float)ad, (float)(ad - (double)(float)ad)}, b = {(float)bd, (float)(bd - (double)(float)bd)};
-    q[k + 1] = df_sub(df_mul(a, df_mul(q[1], q[k])), df_mul(b, q[k - 1]));
-  }
-}
 // four signed digits of round(v 2^30), |v| <= 1
 __device__ __forceinline__ void digits4(int X, int (&d)[4]) {
   d[0] = (X + (1 << 22)) >> 23;  // arithmetic shifts: floor division
@@ -364,102 +352,39 @@ __device__ __forceinline__ int fixed30(dfl v) {
 }
 __host__ __device__ constexpr int digit_exp(int q) { return q == 0 ? -7 : q == 1 ? -15 : q == 2 ? -23 : -30; }
 
-// One 64-row atom of the operand tiles.  Thread (k, half): point k, and half
-// of the basis rows (the split point is a compile-time constant, so each
-// instantiation stores only its own rows).
-template <int P, int HALF>
-__device__ __forceinline__ void gen_rows_gram(uint8_t* t0, uint32_t tile_bytes, int k, bool valid, double u,
-                                              double v, double w, double val, const MFrame& F) {
-  constexpr int L = (P + 1) * (P + 2) * (P + 3) / 6;
-  constexpr int NW = L + 1;  // basis rows and r
-  constexpr int J1 = (NW + 1) / 2;
-  constexpr int jlo = HALF == 0 ? 0 : J1, jhi = HALF == 0 ? J1 : NW;
-  float qx[P + 1], qy[P + 1], qz[P + 1];
-  legendre_f<P>((float)(u * F.ex[0]), qx);
-  legendre_f<P>((float)(v * F.ex[1]), qy);
-  legendre_f<P>((float)(w * F.ex[2]), qz);
-  int j = 0;
-#pragma unroll
-  for (int l = 0; l <= P; ++l)
-#pragma unroll
-    for (int mm = 0; mm <= P - l; ++mm) {
-      const float plm = qx[l] * qy[mm];
-#pragma unroll
-      for (int n = 0; n <= P - l - mm; ++n, ++j)
-        if (j >= jlo && j < jhi) put3(t0, tile_bytes, j, k, valid ? plm * qz[n] : 0.0f);
-    }
-  if (L >= jlo && L < jhi) put3(t0, tile_bytes, L, k, valid ? (float)(val * F.sig) : 0.0f);
-}
+// One 64-row atom of the operand tiles is generated in two phases: 192
+// threads evaluate the 1-D Legendre values P_0..P_p of the atom's rows (one
+// axis each) into shared memory; then every thread takes one row and every
+// eighth column j, forms P_l(t_x) P_m(t_y) P_n(t_z) for the (l, m, n) of j and
+// stores its BF16 terms / digits.
+constexpr int kGThreads = 512;            // k_mgram: 16 warps
+constexpr int kGParts = kGThreads / kAtom;
+constexpr int kLegBytes = 3 * (FMT_MIXED_MAX_DEGREE + 1) * kAtom * 8;
 
-template <int P, int HALF>
-__device__ __forceinline__ void gen_rows_proj(uint8_t* t0, uint32_t tile_bytes, uint8_t* stile, int k, bool valid,
-                                              double u, double v, double w, double sval, double sscale,
-                                              const MFrame& F) {
-  constexpr int L = (P + 1) * (P + 2) * (P + 3) / 6;
-  constexpr int J1 = (L + 1) / 2;
-  constexpr int jlo = HALF == 0 ? 0 : J1, jhi = HALF == 0 ? J1 : L;
-  dfl qx[P + 1], qy[P + 1], qz[P + 1];
-  legendre_df<P>(u * F.ex[0], qx);
-  legendre_df<P>(v * F.ex[1], qy);
-  legendre_df<P>(w * F.ex[2], qz);
-  int j = 0;
-#pragma unroll
-  for (int l = 0; l <= P; ++l)
-#pragma unroll
-    for (int mm = 0; mm <= P - l; ++mm) {
-      const dfl plm = df_mul(qx[l], qy[mm]);
-#pragma unroll
-      for (int n = 0; n <= P - l - mm; ++n, ++j)
-        if (j >= jlo && j < jhi) put_digits(t0, tile_bytes, j, k, valid ? fixed30(df_mul(plm, qz[n])) : 0);
-    }
-  if (HALF == 0) {
-    // |s sscale| < 1; round(s sscale 2^30) exactly from FP64
-    const int X = valid ? __double2int_rn(sval * sscale * 1073741824.0) : 0;
-    int d[4];
-    digits4(X, d);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(q, k)) = __float2bfloat16_rn((float)d[q]);
-  }
-}
-
-#define FMT_DEG_SWITCH(p, CALL) \
-  switch (p) {                  \
-    case 0: CALL(0); break;     \
-    case 1: CALL(1); break;     \
-    case 2: CALL(2); break;     \
-    case 3: CALL(3); break;     \
-    case 4: CALL(4); break;     \
-    case 5: CALL(5); break;     \
-    case 6: CALL(6); break;     \
-    case 7: CALL(7); break;     \
-    case 8: CALL(8); break;     \
-    case 9: CALL(9); break;     \
-    default: break;             \
-  }
-
-// Persistent over the level's work items (largest first).  Gram mode
-// (kProj = false): acc[item] += [B | sig r]^T [B | sig r], column-major by
-// TMEM column, 128 lanes each.  Projection mode: gacc[item] += B^T s,
-// band 0 rows in [0,128), band 1 rows in [128,256).
 template <bool kProj>
-__global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
+__global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
   extern __shared__ uint8_t dsm_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_item;
+  __shared__ int s_item, s_deg;
+  __shared__ uint16_t s_lmn[(FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6];
+  __shared__ double s_val[kAtom];
+  __shared__ double s_red[kProj ? 2 * 4 * 128 : 1];
   constexpr int kTiles = kProj ? 4 : 3;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
   const uint32_t tile_bytes = (uint32_t)a.MR * 128u;
   const uint32_t stage_bytes = kTiles * tile_bytes + (kProj ? 2048u : 0u);
   const int nst = a.nstages;
   const uint32_t total = (uint32_t)nst * stage_bytes;
-  for (uint32_t o = 16u * tid; o < total; o += 16u * kMThreads) *reinterpret_cast<uint4*>(dsm + o) = make_uint4(0, 0, 0, 0);
+  float* legf = reinterpret_cast<float*>(dsm + total);  // Gram: [3][p+1][64] floats
+  dfl* legd = reinterpret_cast<dfl*>(dsm + total);      // projection: the same, double-float
+  for (uint32_t o = 16u * tid; o < total; o += 16u * kGThreads) *reinterpret_cast<uint4*>(dsm + o) = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
     fence_mbar_init();
+    s_deg = -1;
   }
   if (warp == 0) tc_alloc(&tmem_slot, (uint32_t)a.tmem_cols);
   tc_fence_before();
@@ -472,7 +397,9 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
   int hi[2] = {0, 0};  // rows of each stage that may hold non-zero values
   int stage = 0;
   bool ok = true;
-  const int k = tid & 63, half = tid >> 6;
+  const int k = tid & (kAtom - 1), part = tid / kAtom;
+  const int lg = warp & 3;                 // TMEM lane group of this warp
+  const int trow_lane = 32 * lg + lane;    // TMEM lane (matrix row) this thread drains
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(a.work, 1);
@@ -490,6 +417,23 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
     const int N0 = kProj ? 16 : Lp;
     const bool band1 = Lp > 128;
     const int b1 = Lp - 128;
+    if (p != s_deg) {  // (l, m, n) of every column, Alg. 2 order
+      for (int j = tid; j < L; j += kGThreads) {
+        int r = j, l = 0;
+        while (r >= (p - l + 1) * (p - l + 2) / 2) {
+          r -= (p - l + 1) * (p - l + 2) / 2;
+          ++l;
+        }
+        int mm = 0;
+        while (r >= p - l - mm + 1) {
+          r -= p - l - mm + 1;
+          ++mm;
+        }
+        s_lmn[j] = (uint16_t)(l | (mm << 4) | (r << 8));
+      }
+      __syncthreads();
+      if (tid == 0) s_deg = p;
+    }
     const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
     // projection: |s| scaled below 1 by a power of two (max |s| of the node, this sweep)
     int se = 0;
@@ -497,13 +441,13 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
       const double ms = __longlong_as_double((long long)a.mstat[kMStat * node + 5]);
       if (ms > 0.0) frexp(ms, &se);
     }
-    const double sscale = ldexp(1.0, -se);
+    const double vscale = kProj ? ldexp(1.0, -se) : F.sig;
     const int64_t rs = a.item_start[item], re = a.item_end[item];
     const int natoms = (int)((re - rs + kAtom - 1) / kAtom);
     double* acc = kProj ? a.gacc + (int64_t)item * 256 : a.acc + (int64_t)item * a.acc_stride;
     const double* val = kProj ? a.s : a.r;
     bool first_drain = true;
-    double g0 = 0.0, g1 = 0.0;  // projection: this lane's FP64 sums of band 0 and band 1
+    double g0 = 0.0, g1 = 0.0;  // projection, threads < 128: FP64 sums of band 0 / band 1 at lane tid
     int since = 0;
     for (int at = 0; at < natoms && ok; ++at) {
       const int st = stage;
@@ -519,37 +463,83 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
       // rows past this node's basis must read as zero
       if (hi[st] > nw) {
         const int nz = (hi[st] - nw) * 8;  // 16-byte words per tile
-        for (int e = tid; e < kTiles * nz; e += kMThreads) {
+        for (int e = tid; e < kTiles * nz; e += kGThreads) {
           const int tt = e / nz, wi = e - tt * nz;
           *reinterpret_cast<uint4*>(t0 + tt * tile_bytes + nw * 128 + wi * 16) = make_uint4(0, 0, 0, 0);
         }
       }
       hi[st] = nw;
-      const int64_t i = rs + (int64_t)at * kAtom + k;
-      const bool valid = i < re;
-      double u = 0.0, v = 0.0, w = 0.0, fv = 0.0;
-      if (valid) {
-        u = fmt_local(a.x[i], F.c[0], F.s[0]);
-        v = fmt_local(a.y[i], F.c[1], F.s[1]);
-        w = fmt_local(a.z[i], F.c[2], F.s[2]);
-        fv = val[i];
+      // phase A: 1-D Legendre values (threads 0..191) and the value column (192..255)
+      const int64_t i0 = rs + (int64_t)at * kAtom;
+      if (tid < 3 * kAtom) {
+        const int ax = tid / kAtom;
+        const int64_t i = i0 + k;
+        const double* X = ax == 0 ? a.x : ax == 1 ? a.y : a.z;
+        const double t = i < re ? fmt_local(X[i], F.c[ax], F.s[ax]) * F.ex[ax] : 0.0;
+        if (kProj) {
+          dfl* q = legd + ax * (p + 1) * kAtom + k;
+          const dfl td = df_of(t);
+          dfl qm = {1.0f, 0.0f}, q0 = td;
+          q[0] = qm;
+          if (p >= 1) q[kAtom] = q0;
+          for (int kk = 1; kk < p; ++kk) {
+            const double ad = (double)(2 * kk + 1) / (double)(kk + 1), bd = (double)kk / (double)(kk + 1);
+            const dfl ca = {(float)ad, (float)(ad - (double)(float)ad)}, cb = {(float)bd, (float)(bd - (double)(float)bd)};
+            const dfl qn = df_sub(df_mul(ca, df_mul(td, q0)), df_mul(cb, qm));
+            q[(kk + 1) * kAtom] = qn;
+            qm = q0;
+            q0 = qn;
+          }
+        } else {
+          float* q = legf + ax * (p + 1) * kAtom + k;
+          const float tf = (float)t;
+          float qm = 1.0f, q0 = tf;
+          q[0] = qm;
+          if (p >= 1) q[kAtom] = q0;
+          for (int kk = 1; kk < p; ++kk) {
+            const float ca = (float)(2 * kk + 1) / (float)(kk + 1), cb = (float)kk / (float)(kk + 1);
+            const float qn = ca * tf * q0 - cb * qm;
+            q[(kk + 1) * kAtom] = qn;
+            qm = q0;
+            q0 = qn;
+          }
+        }
+      } else if (tid < 4 * kAtom) {
+        const int64_t i = i0 + k;
+        s_val[k] = i < re ? val[i] * vscale : 0.0;
       }
+      __syncthreads();
+      // phase B: products, every kGParts-th column
+      const bool valid = i0 + k < re;
+      const int P1 = p + 1;
       if (kProj) {
-#define FMT_PROJ_CALL(PP)                                                                                   \
-  if (half == 0)                                                                                             \
-    gen_rows_proj<PP, 0>(t0, tile_bytes, t0 + 4 * tile_bytes, k, valid, u, v, w, fv, sscale, F);             \
-  else                                                                                                       \
-    gen_rows_proj<PP, 1>(t0, tile_bytes, t0 + 4 * tile_bytes, k, valid, u, v, w, fv, sscale, F);
-        FMT_DEG_SWITCH(p, FMT_PROJ_CALL)
-#undef FMT_PROJ_CALL
+        const dfl* qx = legd + k;
+        const dfl* qy = legd + P1 * kAtom + k;
+        const dfl* qz = legd + 2 * P1 * kAtom + k;
+        for (int j = part; j < L; j += kGParts) {
+          const int c = s_lmn[j];
+          const dfl v = df_mul(df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]), qz[(c >> 8) * kAtom]);
+          put_digits(t0, tile_bytes, j, k, valid ? fixed30(v) : 0);
+        }
+        if (part == kGParts - 1) {
+          // |s vscale| < 1: round(s vscale 2^30) exactly from FP64
+          int d[4];
+          digits4(__double2int_rn(s_val[k] * 1073741824.0), d);
+          uint8_t* stile = t0 + 4 * tile_bytes;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(q, k)) = __float2bfloat16_rn((float)d[q]);
+        }
       } else {
-#define FMT_GRAM_CALL(PP)                                                  \
-  if (half == 0)                                                            \
-    gen_rows_gram<PP, 0>(t0, tile_bytes, k, valid, u, v, w, fv, F);         \
-  else                                                                      \
-    gen_rows_gram<PP, 1>(t0, tile_bytes, k, valid, u, v, w, fv, F);
-        FMT_DEG_SWITCH(p, FMT_GRAM_CALL)
-#undef FMT_GRAM_CALL
+        const float* qx = legf + k;
+        const float* qy = legf + P1 * kAtom + k;
+        const float* qz = legf + 2 * P1 * kAtom + k;
+        for (int j = part; j < L; j += kGParts) {
+          const int c = s_lmn[j];
+          const float v = qx[(c & 15) * kAtom] * qy[((c >> 4) & 15) * kAtom] * qz[(c >> 8) * kAtom];
+          put3(t0, tile_bytes, j, k, valid ? v : 0.0f);
+        }
+        if (part == kGParts - 1) put3(t0, tile_bytes, L, k, (float)s_val[k]);
       }
       fence_async_smem();
       __syncthreads();
@@ -599,13 +589,14 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
           break;
         }
         tc_fence_after();
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16);
         if (!kProj) {
+          // the four warps of a lane group take every fourth 16-column chunk
           const int ncols = band1 ? N0 + (Lp - 128) : N0;
-          for (int c0 = 0; c0 < ncols; c0 += 16) {
+          for (int c0 = 16 * (warp >> 2); c0 < ncols; c0 += 64) {
             float vv[16];
             tc_ld16(trow + (uint32_t)c0, vv);
-            double* dst = acc + (int64_t)c0 * 128 + tid;
+            double* dst = acc + (int64_t)c0 * 128 + trow_lane;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
               const double d = (double)vv[q];
@@ -613,18 +604,24 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
             }
           }
         } else {
-          // exact integer sums per digit pair (q basis, c of s), weighted in FP64
+          // warp (digit q, lane group): exact integer sums per digit pair (q, c), weighted in FP64
+          const int q = warp >> 2;
+          float vv[16];
+          tc_ld16(trow + 32u * q, vv);
+          double part0 = 0.0, part1 = 0.0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            float vv[16];
-            tc_ld16(trow + 32u * q, vv);
+          for (int c = 0; c < 4; ++c) part0 += ldexp((double)vv[c], digit_exp(q) + digit_exp(c));
+          if (band1) {
+            tc_ld16(trow + 32u * q + 16u, vv);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) g0 += ldexp((double)vv[c], digit_exp(q) + digit_exp(c));
-            if (band1) {
-              tc_ld16(trow + 32u * q + 16u, vv);
-#pragma unroll
-              for (int c = 0; c < 4; ++c) g1 += ldexp((double)vv[c], digit_exp(q) + digit_exp(c));
-            }
+            for (int c = 0; c < 4; ++c) part1 += ldexp((double)vv[c], digit_exp(q) + digit_exp(c));
+          }
+          s_red[q * 128 + trow_lane] = part0;
+          s_red[512 + q * 128 + trow_lane] = part1;
+          __syncthreads();
+          if (tid < 128) {
+            g0 += (s_red[tid] + s_red[128 + tid]) + (s_red[256 + tid] + s_red[384 + tid]);
+            g1 += (s_red[512 + tid] + s_red[640 + tid]) + (s_red[768 + tid] + s_red[896 + tid]);
           }
         }
         first_drain = false;
@@ -634,7 +631,7 @@ __global__ void __launch_bounds__(kMThreads, 1) k_mgram(MArgs a) {
       }
     }
     if (!ok) break;
-    if (kProj) {
+    if (kProj && tid < 128) {
       // B^T s of this item: undo the scale of s
       acc[tid] = ldexp(g0, se);
       if (band1) acc[128 + tid] = ldexp(g1, se);
@@ -994,12 +991,13 @@ cudaError_t launch_gram_t(const fmt_tree* t, int depth, const fmt_mixed_bufs& b,
   // projection: 4 digits x 2 bands x 16 columns; Gram: the two bands of the matrix
   a.tmem_cols = (int)pow2_cols(kProj ? 128 : gram_cols(mixed_m_cap(L.max_m)));
   const size_t stage = (kProj ? 4 : 3) * (size_t)a.MR * 128 + (kProj ? 2048 : 0);
-  a.nstages = 1024 + 2 * stage <= 227 * 1024 ? 2 : 1;
-  const size_t smem = 1024 + a.nstages * stage;
+  const size_t fixed = 1024 + kLegBytes + 12 * 1024;  // alignment, Legendre table, static shared
+  a.nstages = fixed + 2 * stage <= 227 * 1024 ? 2 : 1;
+  const size_t smem = 1024 + kLegBytes + a.nstages * stage;
   cudaError_t e = cudaFuncSetAttribute(k_mgram<kProj>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgram<kProj>, kMThreads, smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgram<kProj>, kGThreads, smem)) != cudaSuccess)
     return e;
   if (per_sm < 1) per_sm = 1;
   const int tmem_cap = 512 / a.tmem_cols;  // tensor memory of an SM shared by its resident CTAs
@@ -1007,7 +1005,7 @@ cudaError_t launch_gram_t(const fmt_tree* t, int depth, const fmt_mixed_bufs& b,
   int64_t grid = (int64_t)nsm() * per_sm;
   if (grid > L.n_items) grid = L.n_items;
   if ((e = cudaMemsetAsync(t->d_work, 0, sizeof(int), s)) != cudaSuccess) return e;
-  k_mgram<kProj><<<(unsigned)grid, kMThreads, smem, s>>>(a);
+  k_mgram<kProj><<<(unsigned)grid, kGThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
