@@ -60,6 +60,7 @@ def parse_args():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="path of the headline value; the other path is reported in the 'mixed' / 'fp64' block")
     ap.add_argument("--no-second-path", action="store_true", help="skip the block of the other precision")
+    ap.add_argument("--sweeps", type=int, default=0, help="mixed path: FP64 refinement sweeps (0 = library default)")
     return ap.parse_args()
 
 
@@ -282,14 +283,16 @@ def main():
     w = make_workload(args, rank)
     prec_of = {"fp64": F.FMT_FP64, "mixed": F.FMT_MIXED}
     params = None if args.workload == "batch" else F.make_params(w.degree, w.max_depth, w.min_pts, w.tol_rel,
-                                                                 precision=prec_of[args.precision])
+                                                                 precision=prec_of[args.precision],
+                                                                 sweeps=args.sweeps)
 
     def dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
 
     is_batch = args.workload == "batch"
     if is_batch:
-        params = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel, precision=prec_of[args.precision])
+        params = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel, precision=prec_of[args.precision],
+                               sweeps=args.sweeps)
         w.n = int(w.offsets[-1])
         w.m = int(w.xq.shape[0])
         w.name = w.name
@@ -432,7 +435,7 @@ def main():
     if not args.no_second_path and not args.profile_only:
         oprec = "mixed" if args.precision == "fp64" else "fp64"
         oparams = F.make_params(params.degree, params.max_depth, params.min_pts, params.tol_rel,
-                                precision=prec_of[oprec])
+                                precision=prec_of[oprec], sweeps=args.sweeps)
         for _ in range(max(1, min(args.warmup, 2))):
             tr, _ = step(False, oparams)
             stream.synchronize()

@@ -719,6 +719,30 @@ __device__ void legendre_to_moments(const double* Fl, int p, const MFrame& F, do
 __host__ __device__ __forceinline__ int64_t ro_of(int i, int m) { return (int64_t)i * m - (int64_t)i * (i - 1) / 2; }
 __host__ __device__ __forceinline__ int conv_ws_doubles(int p) { return 4 * (p + 1) * (p + 1) + 2; }
 
+// ------------------------------------------------------------------ k_mreduce
+// Sums the FP64 Gram accumulators of a node's work items into its first
+// item's accumulator (fixed item order: deterministic).  Grid: nodes x chunks
+// of kRedChunk accumulator words, so a root split into hundreds of items is
+// reduced by many SMs.
+constexpr int kRedChunk = 4096;
+__global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
+  const int64_t node = blockIdx.x / chunks;
+  const int ch = blockIdx.x - (int)(node * chunks);
+  const int ni = a.node_nitems[node];
+  if (ni <= 1) return;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  if (!mixed_eligible(pr, a.depth)) return;
+  const int64_t words = (int64_t)gram_cols(fmt_nmono_d(pr.degree) + 1) * 128;
+  const int64_t i0 = a.node_item0[node];
+  double* dst = a.acc + i0 * a.acc_stride;
+  for (int64_t e = (int64_t)ch * kRedChunk + threadIdx.x; e < words && e < (int64_t)(ch + 1) * kRedChunk;
+       e += blockDim.x) {
+    double sum = dst[e];
+    for (int t = 1; t < ni; ++t) sum += a.acc[(i0 + t) * a.acc_stride + e];
+    dst[e] = sum;
+  }
+}
+
 // ------------------------------------------------------------------ k_mfactor
 // One CTA per node.  Shared: the packed upper triangle of the m x m Gram
 // (row i at ro(i), m = nmono + 1 with r last), the initial diagonal, y, F and
@@ -739,8 +763,7 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   double* Fl = y + m;
   double* ws = Fl + m;
   const int64_t i0 = a.node_item0[node];
-  const int ni = a.node_nitems[node];
-  // 1. sum the items' FP64 accumulators (column c, lane i) into G
+  // 1. the node's FP64 Gram (column c, lane i), summed over items by k_mreduce
   for (int e = tid; e < ncols * 128; e += kFThreads) {
     const int c = e >> 7, lane = e & 127;
     int gi, gj;
@@ -754,9 +777,7 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
       if (gi < 128) continue;
     }
     if (gi > gj || gj >= m) continue;
-    double sum = 0.0;
-    for (int t = 0; t < ni; ++t) sum += a.acc[(i0 + t) * a.acc_stride + e];
-    G[ro_of(gi, m) + (gj - gi)] = sum;
+    G[ro_of(gi, m) + (gj - gi)] = a.acc[i0 * a.acc_stride + e];
   }
   __syncthreads();
   for (int k = tid; k < L; k += kFThreads) d0[k] = G[ro_of(k, m)];
@@ -857,10 +878,14 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
   const int64_t i0 = a.node_item0[node];
   const int ni = a.node_nitems[node];
-  const double* R = a.acc + i0 * a.acc_stride;
-  double* g = usm;
+  double* R = usm;  // R-hat rows 0..L-1, packed (row i at ro(i)), copied from the node's first accumulator
+  double* g = R + ro_of(m, m);
   double* Fl = g + m;
   double* ws = Fl + m;
+  {
+    const double* Rg = a.acc + i0 * a.acc_stride;
+    for (int64_t e = tid; e < ro_of(m, m); e += kFThreads) R[e] = Rg[e];
+  }
   for (int j = tid; j < L; j += kFThreads) {
     const int e = j < 128 ? j : 128 + (j - b1);
     double sum = 0.0;
@@ -1039,6 +1064,12 @@ size_t mixed_factor_smem(int max_m) {
 cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
   const fmt_level& L = t->lv[depth];
   if (L.n_nodes <= 0) return cudaSuccess;
+  if (L.max_chunks > 1) {
+    const int chunks = (int)((mixed_acc_stride(L.max_m) + kRedChunk - 1) / kRedChunk);
+    k_mreduce<<<(unsigned)(L.n_nodes * chunks), 256, 0, s>>>(make_margs(t, depth, b), chunks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = mixed_factor_smem(mixed_m_cap(L.max_m));
   cudaError_t e = cudaFuncSetAttribute(k_mfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1059,7 +1090,10 @@ cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bu
   if (L.n_nodes <= 0) return cudaSuccess;
   MArgs a = make_margs(t, depth, b);
   a.last_sweep = last ? 1 : 0;
-  const size_t smem = sizeof(double) * (2 * (size_t)mixed_m_cap(L.max_m) + conv_ws_doubles(FMT_MIXED_MAX_DEGREE));
+  const int mc = mixed_m_cap(L.max_m);
+  const size_t smem = sizeof(double) * ((size_t)ro_of(mc, mc) + 2 * (size_t)mc + conv_ws_doubles(FMT_MIXED_MAX_DEGREE));
+  cudaError_t e = cudaFuncSetAttribute(k_mupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   k_mupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
