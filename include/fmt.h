@@ -62,6 +62,8 @@ typedef enum {
 #define FMT_FLAG_RANK 2         /* back substitution dropped dependent columns */
 #define FMT_FLAG_DEG_CLAMPED 4  /* root with N < nmono: degree lowered */
 #define FMT_FLAG_MIXED 8        /* fitted by the mixed-precision path */
+#define FMT_FLAG_MIXED_SLOW 16  /* mixed path: refinement not converged, refitted in FP64 */
+#define FMT_FLAG_MIXED_PIVOT 32 /* mixed path: Cholesky pivot too small, refitted in FP64 */
 
 /*
  * Parameters of Alg. 1 (L, nmono, tau and the root box P) plus the depth and

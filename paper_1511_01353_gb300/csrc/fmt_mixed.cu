@@ -747,10 +747,39 @@ __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
 // One CTA per node.  Shared: the packed upper triangle of the m x m Gram
 // (row i at ro(i), m = nmono + 1 with r last), the initial diagonal, y, F and
 // the change-of-basis scratch.
+// G[i][j] -= rk[i] rk[j] for k < i <= j < m (packed rows): threads form a
+// 16 x 16 grid over the upper tiles of the trailing matrix.
+__device__ __forceinline__ void trailing_update(double* __restrict__ G, const double* __restrict__ rk, int k,
+                                                int m) {
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  const int n = m - k - 1;
+  for (int ib = 0; ib < n; ib += 16) {
+    const int i = k + 1 + ib + ti;
+    if (i >= m) break;
+    const double ri = rk[i];
+    double* Gi = G + ro_of(i, m) - i;  // Gi[j] = G[i][j]
+    for (int jb = ib; jb < n; jb += 16) {
+      const int j = k + 1 + jb + tj;
+      if (j >= i && j < m) Gi[j] = fma(-ri, rk[j], Gi[j]);
+    }
+  }
+}
+
+// One warp: R x = y (x overwrites y).
+__device__ void warp_back_solve(const double* __restrict__ R, int m, int L, const double* __restrict__ invd,
+                                double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  for (int j = L - 1; j >= 0; --j) {
+    const double xj = y[j] * invd[j];
+    __syncwarp();
+    if (lane == 0) y[j] = xj;
+    for (int i = lane; i < j; i += 32) y[i] = fma(-R[ro_of(i, m) + (j - i)], xj, y[i]);
+    __syncwarp();
+  }
+}
+
 __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   extern __shared__ double fsm[];
-  __shared__ int s_ok;
-  __shared__ double s_rkk;
   const int64_t node = blockIdx.x;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   if (!mixed_eligible(pr, a.depth)) return;
@@ -758,9 +787,10 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
   const int ncols = gram_cols(m);
   double* G = fsm;
-  double* d0 = G + ro_of(m, m);
-  double* y = d0 + m;
-  double* Fl = y + m;
+  double* rk = G + ro_of(m, m);
+  double* d0 = rk + m;
+  double* invd = d0 + m;
+  double* Fl = invd + m;
   double* ws = Fl + m;
   const int64_t i0 = a.node_item0[node];
   // 1. the node's FP64 Gram (column c, lane i), summed over items by k_mreduce
@@ -782,45 +812,30 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   __syncthreads();
   for (int k = tid; k < L; k += kFThreads) d0[k] = G[ro_of(k, m)];
   // 2. Cholesky, right-looking, on the packed rows; column L (r) is carried along
-  bool good = true;
   for (int k = 0; k < L; ++k) {
     __syncthreads();
-    if (tid == 0) {
-      const double d = G[ro_of(k, m)];
-      const bool okk = d0[k] > 0.0 && d > kPivotFloor * d0[k];
-      s_ok = okk;
-      s_rkk = okk ? sqrt(d) : 0.0;
+    const double d = G[ro_of(k, m)];
+    if (!(d0[k] > 0.0 && d > kPivotFloor * d0[k])) {  // the same decision in every thread
+      if (tid == 0) a.flags[node] |= FMT_FLAG_MIXED_PIVOT;
+      return;  // the FP64 path refits this node
     }
-    __syncthreads();
-    if (!s_ok) {
-      good = false;
-      break;
-    }
-    const double rkk = s_rkk;
-    double* rowk = G + ro_of(k, m) - k;  // rowk[j] = G[k][j], j >= k
-    for (int j = k + 1 + tid; j < m; j += kFThreads) rowk[j] = rowk[j] / rkk;
-    if (tid == 0) rowk[k] = rkk;
-    __syncthreads();
+    const double rkk = sqrt(d);
+    double* Gk = G + ro_of(k, m) - k;
     for (int j = k + 1 + tid; j < m; j += kFThreads) {
-      const double gkj = rowk[j];
-      int64_t ri = ro_of(k + 1, m);
-      for (int i = k + 1; i <= j; ++i) {
-        G[ri + (j - i)] = fma(-rowk[i], gkj, G[ri + (j - i)]);
-        ri += m - i;
-      }
+      const double v = Gk[j] / rkk;
+      rk[j] = v;
+      Gk[j] = v;
     }
+    if (tid == 0) invd[k] = 1.0 / rkk;
+    __syncthreads();
+    if (tid == 0) Gk[k] = rkk;  // every thread has read the pivot by now
+    trailing_update(G, rk, k, m);
   }
-  if (!good) return;  // FP64 path refits this node
   __syncthreads();
-  // 3. R F = y (the scaled Q^T r column)
-  for (int k = tid; k < L; k += kFThreads) y[k] = G[ro_of(k, m) + (L - k)];
-  for (int j = L - 1; j >= 0; --j) {
-    __syncthreads();
-    if (tid == 0) Fl[j] = y[j] / G[ro_of(j, m)];
-    __syncthreads();
-    const double fj = Fl[j];
-    for (int i = tid; i < j; i += kFThreads) y[i] = fma(-G[ro_of(i, m) + (j - i)], fj, y[i]);
-  }
+  // 3. R F = y, y = the scaled Q^T r column
+  for (int k = tid; k < L; k += kFThreads) Fl[k] = G[ro_of(k, m) + (L - k)];
+  __syncthreads();
+  if (tid < 32) warp_back_solve(G, m, L, invd, Fl);
   __syncthreads();
   const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
   for (int k = tid; k < L; k += kFThreads) {
@@ -881,7 +896,8 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   double* R = usm;  // R-hat rows 0..L-1, packed (row i at ro(i)), copied from the node's first accumulator
   double* g = R + ro_of(m, m);
   double* Fl = g + m;
-  double* ws = Fl + m;
+  double* invd = Fl + m;
+  double* ws = invd + m;
   {
     const double* Rg = a.acc + i0 * a.acc_stride;
     for (int64_t e = tid; e < ro_of(m, m); e += kFThreads) R[e] = Rg[e];
@@ -893,26 +909,24 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
     g[j] = sum;  // the projection kernel has undone the scale of s
     Fl[j] = a.lcoef[node * a.stride + j];
   }
-  // R^T w = g (w overwrites g), column-oriented
+  for (int k = tid; k < L; k += kFThreads) invd[k] = 1.0 / R[ro_of(k, m)];
+  __syncthreads();
   double wn = 0.0;
-  for (int k = 0; k < L; ++k) {
-    __syncthreads();
-    const double* rowk = R + ro_of(k, m) - k;
-    const double wk = g[k] / rowk[k];
-    __syncthreads();
-    if (tid == 0) {
-      g[k] = wk;
-      wn += wk * wk;
+  if (tid < 32) {
+    // |R d|^2 = |R^{-T} g|^2 is taken between the two triangular solves
+    const int lane = tid;
+    for (int k = 0; k < L; ++k) {
+      const double wk = g[k] * invd[k];
+      __syncwarp();
+      if (lane == 0) {
+        g[k] = wk;
+        wn += wk * wk;
+      }
+      const double* rowk = R + ro_of(k, m) - k;
+      for (int j = k + 1 + lane; j < L; j += 32) g[j] = fma(-rowk[j], wk, g[j]);
+      __syncwarp();
     }
-    for (int j = k + 1 + tid; j < L; j += kFThreads) g[j] = fma(-rowk[j], wk, g[j]);
-  }
-  // R d = w, d overwrites g
-  for (int j = L - 1; j >= 0; --j) {
-    __syncthreads();
-    const double dj = g[j] / R[ro_of(j, m)];
-    __syncthreads();
-    if (tid == 0) g[j] = dj;
-    for (int i = tid; i < j; i += kFThreads) g[i] = fma(-R[ro_of(i, m) + (j - i)], dj, g[i]);
+    warp_back_solve(R, m, L, invd, g);
   }
   __syncthreads();
   for (int j = tid; j < L; j += kFThreads) {
@@ -947,7 +961,7 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
         const double rho = upd / prev;
         conv = upd * rho / (1.0 - rho) <= kConvergedRel * zn;
       }
-      if (!conv) a.flags[node] &= ~FMT_FLAG_MIXED;
+      if (!conv) a.flags[node] = (a.flags[node] & ~FMT_FLAG_MIXED) | FMT_FLAG_MIXED_SLOW;
     }
   }
 }
@@ -1058,7 +1072,7 @@ cudaError_t launch_mixed_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs
 
 size_t mixed_factor_smem(int max_m) {
   const int p_max = FMT_MIXED_MAX_DEGREE;
-  return sizeof(double) * ((size_t)ro_of(max_m, max_m) + 3 * (size_t)max_m + conv_ws_doubles(p_max));
+  return sizeof(double) * ((size_t)ro_of(max_m, max_m) + 4 * (size_t)max_m + conv_ws_doubles(p_max));
 }
 
 cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
@@ -1091,7 +1105,7 @@ cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bu
   MArgs a = make_margs(t, depth, b);
   a.last_sweep = last ? 1 : 0;
   const int mc = mixed_m_cap(L.max_m);
-  const size_t smem = sizeof(double) * ((size_t)ro_of(mc, mc) + 2 * (size_t)mc + conv_ws_doubles(FMT_MIXED_MAX_DEGREE));
+  const size_t smem = sizeof(double) * ((size_t)ro_of(mc, mc) + 3 * (size_t)mc + conv_ws_doubles(FMT_MIXED_MAX_DEGREE));
   cudaError_t e = cudaFuncSetAttribute(k_mupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_mupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
