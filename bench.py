@@ -453,10 +453,16 @@ def main():
                            sum(b.elapsed_time(c) for _, b, c in oev) / len(oev) / 1e3], dist, device="cuda")
         opred = out.cpu().numpy()
         ost = F.fmt_tree_stats(otrees[-1])
+        oex = F.parse_export(F.fmt_tree_export(otrees[-1]))
         for tr in otrees:
             tr.close()
         fscale = max(float(np.max(np.abs(w.f))), 1e-300)
         mst = ost if oprec == "mixed" else stats
+        mex = oex if oprec == "mixed" else ex
+        fallback = {"not_converged_nodes": int(np.sum((mex.flags & F.FMT_FLAG_MIXED_SLOW) != 0)),
+                    "not_converged_points": int(np.sum(mex.count[(mex.flags & F.FMT_FLAG_MIXED_SLOW) != 0])),
+                    "small_pivot_nodes": int(np.sum((mex.flags & F.FMT_FLAG_MIXED_PIVOT) != 0)),
+                    "small_pivot_points": int(np.sum(mex.count[(mex.flags & F.FMT_FLAG_MIXED_PIVOT) != 0]))}
         mixed_pts = sum(int(mst.mixed_points[d]) for d in range(mst.n_levels))
         all_pts = sum(int(mst.points[d]) for d in range(mst.n_levels))
         gram = oprof.get("mixed_gram", {}) if oprec == "mixed" else prof.get("mixed_gram", {})
@@ -467,6 +473,7 @@ def main():
                  "max_abs_diff_vs_headline_over_max_f": float(np.max(np.abs(opred - pred))) / fscale,
                  "mixed_share_of_fitted_points": mixed_pts / max(all_pts, 1),
                  "mixed_nodes": int(sum(mst.mixed[d] for d in range(mst.n_levels))),
+                 "fp64_fallback": fallback,
                  "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps}
                              for k, v in oprof.items() if v["launches"]},
                  "note": "error vs the FP64 GPU path, which matches the FP64 oracle to 1e-10 max|f|; "
