@@ -909,6 +909,7 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
     g[j] = sum;  // the projection kernel has undone the scale of s
     Fl[j] = a.lcoef[node * a.stride + j];
   }
+  __syncthreads();  // R, g and F complete
   for (int k = tid; k < L; k += kFThreads) invd[k] = 1.0 / R[ro_of(k, m)];
   __syncthreads();
   double wn = 0.0;
