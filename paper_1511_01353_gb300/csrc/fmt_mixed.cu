@@ -724,7 +724,7 @@ __host__ __device__ __forceinline__ int conv_ws_doubles(int p) { return 4 * (p +
 // item's accumulator (fixed item order: deterministic).  Grid: nodes x chunks
 // of kRedChunk accumulator words, so a root split into hundreds of items is
 // reduced by many SMs.
-constexpr int kRedChunk = 4096;
+constexpr int kRedChunk = 256;
 __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
   const int64_t node = blockIdx.x / chunks;
   const int ch = blockIdx.x - (int)(node * chunks);
