@@ -48,7 +48,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["fmt", "reference"], default="fmt")
-    ap.add_argument("--workload", choices=["scale", "small", "batch"], default="scale")
+    ap.add_argument("--workload", choices=["scale", "small", "batch", "serve"], default="scale")
+    ap.add_argument("--requests", type=int, default=48, help="serve: requests in the arrival stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=2, help="serve: worker slots (streams)")
     ap.add_argument("--problems", type=int, default=4096, help="problems of the batch workload")
     ap.add_argument("--points", type=int, default=0, help="override the number of points")
     ap.add_argument("--targets", type=int, default=0, help="override the number of targets")
@@ -259,6 +262,83 @@ def cpu_baseline(args):
             "evals_per_s": w.m / (t2 - t1)}
 
 
+def run_serve(args, rank, world):
+    """Serving: a Poisson stream of fit+evaluate requests through the
+    library's serving engine (continuous batching over worker streams);
+    latency = completion minus submission on the engine's clock, with the
+    host->device copy of the request's arrays and the device->host copy of
+    its results inside it."""
+    import threading
+
+    import numpy as np
+    import torch
+    from paper_1511_01353_gb300 import fmt as F
+    from paper_1511_01353_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    F.load()
+    reqs = W.serve_stream(n_requests=args.requests, rate=args.rate, seed=W.SEED_BASE + 4 + 1000 * rank)
+    prec = {"fp64": F.FMT_FP64, "mixed": F.FMT_MIXED}
+
+    def params(r):
+        return F.make_params(r.degree, 8, 0, 1e-6, precision=prec[r.precision], sweeps=args.sweeps)
+
+    sv = F.Server(slots=args.slots, budget_bytes=150e9, max_batch_points=4_000_000)
+    for r in reqs[:max(args.warmup, 1)]:  # warm-up: contexts, pools, kernels
+        sv.wait(sv.submit(params(r), r.x[:2000], r.y[:2000], r.z[:2000], r.f[:2000], r.xq[:100], r.yq[:100],
+                          r.zq[:100]))
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(0).uuid))
+    sampler.start()
+    tickets = [None] * len(reqs)
+    t0 = F.Server.clock()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            dt = t0 + r.arrival - F.Server.clock()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = sv.submit(params(r), r.x, r.y, r.z, r.f, r.xq, r.yq, r.zq)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    infos = [sv.wait(t)[1] for t in tickets]
+    clocks = sampler.stop()
+    sv.close()
+    lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
+    ok = all(i["status"] == F.FMT_OK for i in infos)
+    pts = np.array([r.x.shape[0] for r in reqs], dtype=np.float64)
+    tg = np.array([r.xq.shape[0] for r in reqs], dtype=np.float64)
+    span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    by = {}
+    for name in ("fp64", "mixed"):
+        sel = np.array([r.precision == name for r in reqs])
+        if sel.any():
+            by[name] = {"requests": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50) * 1e3),
+                        "p99_ms": float(np.percentile(lat[sel], 99) * 1e3), "points": int(pts[sel].sum())}
+    offered = pts.sum() / max(reqs[-1].arrival, 1e-9)
+    line = {"metric": "fitted pts/s and p50/p99 request latency (serving)", "value": float(pts.sum() / span),
+            "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": max(args.warmup, 1),
+            "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 and f64+bf16x3 per request", "data": "synthetic",
+            "config": {"workload": "serve: %d requests, Poisson %.0f/s, points log-uniform [1e3, 2e6], targets "
+                                   "log-uniform [1, 1e6], p 4..10, FP64 or mixed per request" % (len(reqs), args.rate),
+                       "slots": args.slots, "budget_bytes": 150e9, "max_batch_points": 4_000_000,
+                       "max_depth": 8, "tol_rel": 1e-6},
+            "evals_per_s": float(tg.sum() / span), "all_ok": ok,
+            "latency": by, "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "offered_points_per_s": float(offered), "completed_points_per_s": float(pts.sum() / span),
+            "saturated": bool(offered > pts.sum() / span),
+            "batches": len(set(i["batch_id"] for i in infos)),
+            "mean_batch_requests": float(np.mean([i["batch_requests"] for i in infos])),
+            "clocks": clocks,
+            "e2e": {"value": float(pts.sum() / span), "unit": UNIT,
+                    "h2d_bytes_per_step": int(32 * pts.sum() + 24 * tg.sum()), "d2h_bytes_per_step": int(8 * tg.sum())}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -267,6 +347,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return 0
+    if args.workload == "serve":
+        return run_serve(args, rank, world)
 
     import numpy as np
     import torch

@@ -351,6 +351,56 @@ void fmt_tree_free(fmt_tree* tree);
  * failure when tree == NULL (e.g. a failed oct_build).  Never NULL. */
 const char* fmt_last_error(const fmt_tree* tree);
 
+/*
+ * Serving (no counterpart in the paper; every numerical step is the calls
+ * above).  Fit+evaluate requests are queued and run by `slots` worker
+ * threads, each with its own CUDA stream.  A slot that frees up forms its
+ * next batch from the oldest queued request and every queued request with
+ * the same batch key (params.precision, max_depth, min_pts, tol_rel, sweeps,
+ * chunk_rows), as long as the batch stays within max_batch_points (the first
+ * request always goes) and the sum of the admitted requests' device-memory
+ * estimates stays within budget_bytes; the batch runs as one forest
+ * (oct_build_batch with each request's degree and box, the fit_level/refine
+ * loop, evaluate_batch).  So requests that arrive while other batches are on
+ * the GPU join the next batch, and batches of different slots overlap on the
+ * device.  A request whose estimate alone exceeds the budget completes with
+ * FMT_ENOMEM.  Each request's tree is independent of the others in its
+ * batch; its result equals the result of running it alone up to the
+ * rounding of a different row-chunk plan (FP64: within 1e-10 max|f|).
+ *
+ *   fmt_request   params: the request's fmt_params (degree, lo, side are per
+ *                 request; the rest is the batch key).  x,y,z,f: host, n
+ *                 each; xq,yq,zq: host, m each; out: host, m.  All must stay
+ *                 valid and unmodified until fmt_server_wait returns it.
+ *   fmt_request_result  status of the request; t_submit / t_start / t_done
+ *                 on fmt_server_clock(); the batch it ran in.
+ * fmt_server_create: slots 1..64, budget_bytes > 0, max_batch_points >= 1;
+ *   uses the current device.  fmt_server_submit copies the request struct
+ *   (not the arrays) and returns a ticket; FMT_EINVAL for bad fields.
+ * fmt_server_wait: blocks until the request is done (timeout_s < 0: no
+ *   limit; FMT_ETIMEOUT otherwise) and releases the ticket.
+ * fmt_server_destroy: runs what is queued, joins the slots, frees.
+ */
+typedef struct fmt_server fmt_server;
+typedef struct {
+  fmt_params params;
+  int64_t n, m;
+  const double *x, *y, *z, *f;
+  const double *xq, *yq, *zq;
+  double* out;
+} fmt_request;
+typedef struct {
+  fmt_status status;
+  int32_t batch_requests;
+  int64_t batch_id, batch_points;
+  double t_submit, t_start, t_done;
+} fmt_request_result;
+fmt_status fmt_server_create(int32_t slots, double budget_bytes, int64_t max_batch_points, fmt_server** out);
+fmt_status fmt_server_submit(fmt_server* server, const fmt_request* request, int64_t* ticket);
+fmt_status fmt_server_wait(fmt_server* server, int64_t ticket, double timeout_s, fmt_request_result* result);
+fmt_status fmt_server_destroy(fmt_server* server);
+double fmt_server_clock(void); /* seconds, steady clock of the server */
+
 #ifdef __cplusplus
 }
 #endif

@@ -967,15 +967,14 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   }
 }
 
-int g_nsm = 0;
 int nsm() {
-  if (g_nsm <= 0) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (g_nsm <= 0) g_nsm = 1;
-  }
-  return g_nsm;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  return n;
 }
 
 MArgs make_margs(const fmt_tree* t, int depth, const fmt_mixed_bufs& b) {

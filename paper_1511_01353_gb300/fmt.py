@@ -56,6 +56,18 @@ class fmt_stats(ctypes.Structure):
                 ("mixed", ctypes.c_int64 * _NL), ("mixed_points", ctypes.c_int64 * _NL)]
 
 
+class fmt_request(ctypes.Structure):
+    _fields_ = [("params", fmt_params), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("f", ctypes.c_void_p),
+                ("xq", ctypes.c_void_p), ("yq", ctypes.c_void_p), ("zq", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class fmt_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_requests", ctypes.c_int32), ("batch_id", ctypes.c_int64),
+                ("batch_points", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 class fmt_export_header(ctypes.Structure):
     _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32), ("degree", ctypes.c_int32),
                 ("nmono", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("min_pts", ctypes.c_int32),
@@ -68,7 +80,8 @@ class fmt_export_header(ctypes.Structure):
 EXPORTED = ["fmt_nmono", "oct_build", "oct_build_batch", "fit_level", "refine", "evaluate", "evaluate_batch",
             "fmt_tree_stats", "fmt_tree_export",
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
-            "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static"]
+            "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static", "fmt_server_create",
+            "fmt_server_submit", "fmt_server_wait", "fmt_server_destroy", "fmt_server_clock"]
 STATIC_MAX_DEGREE = 8
 PROFILE_CLASSES = 24
 
@@ -126,6 +139,16 @@ def load(build: bool = True):
         L.fmt_profile_class_name.restype = ctypes.c_char_p
         L.fmt_probe_dfma.argtypes = [i64, ctypes.POINTER(ctypes.c_double), P]
         L.fmt_probe_dfma.restype = ctypes.c_int
+        L.fmt_server_create.argtypes = [i32, ctypes.c_double, i64, ctypes.POINTER(P)]
+        L.fmt_server_create.restype = ctypes.c_int
+        L.fmt_server_submit.argtypes = [P, ctypes.POINTER(fmt_request), ctypes.POINTER(i64)]
+        L.fmt_server_submit.restype = ctypes.c_int
+        L.fmt_server_wait.argtypes = [P, i64, ctypes.c_double, ctypes.POINTER(fmt_request_result)]
+        L.fmt_server_wait.restype = ctypes.c_int
+        L.fmt_server_destroy.argtypes = [P]
+        L.fmt_server_destroy.restype = ctypes.c_int
+        L.fmt_server_clock.argtypes = []
+        L.fmt_server_clock.restype = ctypes.c_double
         L.fmt_fit_node_static.argtypes = [i32, i64, P, P, P, P, P, ctypes.c_double, P, P, P, P]
         L.fmt_fit_node_static.restype = ctypes.c_int
         _lib = L
@@ -460,3 +483,55 @@ def build_export(header: dict, prefix, depth, flags, deg_used, child_E, child_n,
              np.asarray(header["lo"], np.float64).tobytes(), np.array([header["side"]], np.float64).tobytes(),
              np.array([0], np.int64).tobytes(), np.array([n_pts], np.int64).tobytes()]
     return b"".join(parts)
+
+
+class Server:
+    """The serving engine (fmt_server_*): submit fit+evaluate requests with
+    host arrays, wait for their results.  Arrays are kept referenced here
+    until the request is returned by wait()."""
+
+    def __init__(self, slots=2, budget_bytes=150e9, max_batch_points=4_000_000):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.fmt_server_create(slots, float(budget_bytes), int(max_batch_points), ctypes.byref(h)))
+        self.handle = h
+        self._live = {}
+
+    @staticmethod
+    def clock():
+        return float(load().fmt_server_clock())
+
+    def submit(self, params: fmt_params, x, y, z, f, xq=None, yq=None, zq=None) -> int:
+        arr = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, f)]
+        q = [np.ascontiguousarray(a, dtype=np.float64) for a in (xq, yq, zq)] if xq is not None else \
+            [np.zeros(0) for _ in range(3)]
+        out = np.empty(q[0].shape[0], dtype=np.float64)
+        r = fmt_request()
+        r.params = params
+        r.n, r.m = arr[0].shape[0], q[0].shape[0]
+        r.x, r.y, r.z, r.f = (a.ctypes.data for a in arr)
+        r.xq, r.yq, r.zq = (a.ctypes.data if a.shape[0] else None for a in q)
+        r.out = out.ctypes.data if out.shape[0] else None
+        t = ctypes.c_int64()
+        _check(load().fmt_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        self._live[t.value] = (arr, q, out)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """(values at the targets, result dict) of a submitted request."""
+        res = fmt_request_result()
+        _check(load().fmt_server_wait(self.handle, ticket, float(timeout), ctypes.byref(res)))
+        arr, q, out = self._live.pop(ticket)
+        info = {name: getattr(res, name) for name, _ in fmt_request_result._fields_}
+        return out, info
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load().fmt_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -299,3 +299,65 @@ def batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536, deg_min:
                  degrees, boxes, np.concatenate(xs), np.concatenate(ys), np.concatenate(zs), np.concatenate(fs),
                  np.arange(P + 1, dtype=np.int64) * nt, np.concatenate(txs), np.concatenate(tys),
                  np.concatenate(tzs), tprob, kinds, clouds)
+
+
+@dataclasses.dataclass
+class ServeRequest:
+    arrival: float           # seconds after the start of the stream
+    precision: str           # "fp64" or "mixed"
+    degree: int
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    f: np.ndarray
+    xq: np.ndarray
+    yq: np.ndarray
+    zq: np.ndarray
+
+
+def serve_stream(n_requests: int = 48, rate: float = 200.0, n_min: int = 1000, n_max: int = 2_000_000,
+                 t_min: int = 1, t_max: int = 1_000_000, deg_min: int = 4, deg_max: int = 10,
+                 seed: int = SEED_BASE + 4) -> list:
+    """Fit+evaluate requests shaped like the serving configuration: Poisson
+    arrivals at `rate` per second; point counts log-uniform in [n_min,
+    n_max], target counts log-uniform in [t_min, t_max]; degree uniform in
+    [deg_min, deg_max]; clouds and values from the batched recipe's
+    generators (uniform or 1-8 Gaussian clusters; shifted/scaled Franke or
+    Gaussian sums), the targets a fresh sample of the same cloud; each
+    request FP64 or mixed precision with probability 1/2."""
+    R = n_requests
+    u = uniform(seed, 1, 16 * R).reshape(R, 16)
+    arrivals = np.cumsum(-np.log(1.0 - u[:, 0]) / rate)
+    counts = np.floor(np.exp(np.log(n_min) + u[:, 1] * (np.log(n_max) - np.log(n_min)))).astype(np.int64)
+    counts = np.clip(counts, n_min, n_max)
+    tcounts = np.floor(np.exp(np.log(t_min) + u[:, 2] * (np.log(t_max) - np.log(t_min)))).astype(np.int64)
+    tcounts = np.clip(tcounts, t_min, t_max)
+    degrees = np.minimum(deg_min + np.floor(u[:, 3] * (deg_max - deg_min + 1)), deg_max).astype(np.int32)
+    out = []
+    for i in range(R):
+        n, nt = int(counts[i]), int(tcounts[i])
+        if u[i, 4] < 0.5:
+            x, y, z = uniform_points(seed, 1000 + i, n)
+            tx, ty, tz = uniform_points(seed, 1000000 + i, nt)
+        else:
+            k = 1 + int(u[i, 5] * 8) if u[i, 5] < 1.0 else 8
+            sig = 0.02 + 0.18 * u[i, 6]
+            cen = 0.2 + 0.6 * uniform(seed, 200000 + i, 3 * k).reshape(k, 3)
+
+            def cloud(cnt, base):
+                per = [cnt // k + (1 if c < cnt % k else 0) for c in range(k)]
+                parts = [clustered_points(seed, base + 8 * i + c, per[c], cen[c], sig)
+                         for c in range(k) if per[c] > 0]
+                return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+                        np.concatenate([p[2] for p in parts]))
+            x, y, z = cloud(n, 400000)
+            tx, ty, tz = cloud(nt, 1200000)
+        if u[i, 7] < 0.5:
+            kind = ("franke", -0.2 + 0.4 * u[i, 8:11], 0.5 + 1.5 * u[i, 11])
+        else:
+            ng = 1 + int(u[i, 12] * 16) if u[i, 12] < 1.0 else 16
+            gu = uniform(seed, 600000 + i, 4 * ng).reshape(ng, 4)
+            kind = ("gauss", gu[:, :3], 1.0 + 49.0 * gu[:, 3], normal(seed, 800000 + i, ng))
+        out.append(ServeRequest(float(arrivals[i]), "mixed" if u[i, 13] < 0.5 else "fp64", int(degrees[i]),
+                                x, y, z, _batch_value(kind, x, y, z), tx, ty, tz))
+    return out
