@@ -516,6 +516,15 @@ fmt_status ensure_mixed(fmt_tree* t, int depth, cudaStream_t s) {
     TRY(talloc(t, &b.gacc, 256 * L.n_items, s));
     b.cap_items = L.n_items;
   }
+  // basis cache of the sweeps, unless it would exceed kCacheCap (then each sweep regenerates)
+  const size_t cache = mixed_cache_bytes(t, depth);
+  constexpr size_t kCacheCap = (size_t)16 << 30;
+  if (cache <= kCacheCap && b.cap_cache < cache) {
+    if (b.cache) tfree_one(t, b.cache, s);
+    b.cache = nullptr;
+    b.cap_cache = 0;
+    if (talloc(t, &b.cache, (int64_t)cache, s) == FMT_OK) b.cap_cache = cache;
+  }
   b.acc_stride = (int64_t)mixed_acc_stride(L.max_m);
   const int64_t need = b.acc_stride * L.n_items;
   if (b.cap_acc < need) {
@@ -533,7 +542,8 @@ fmt_status ensure_mixed(fmt_tree* t, int depth, cudaStream_t s) {
 fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
   TRY(ensure_mixed(t, depth, s));
   const fmt_level& L = t->lv[depth];
-  const fmt_mixed_bufs& b = t->mx;
+  fmt_mixed_bufs b = t->mx;
+  if (b.cap_cache < mixed_cache_bytes(t, depth)) b.cache = nullptr;  // too large: regenerate per sweep
   const double rows = (double)L.n_points, nodes = (double)L.n_nodes;
   {
     ProfScope ps(K_MBOX, s, 2, rows, 0.0);
@@ -541,7 +551,7 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
   }
   {
     ProfScope ps(K_MGRAM, s, 1, rows, 0.0);
-    CUDA_TRY(t, launch_mixed_gram(t, depth, b, false, s), "mixed Gram launch");
+    CUDA_TRY(t, launch_mixed_gram(t, depth, b, false, 0, s), "mixed Gram launch");
   }
   {
     ProfScope ps(K_MFACTOR, s, 1, nodes, 0.0);
@@ -555,7 +565,7 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
     }
     {
       ProfScope ps(K_MPROJ, s, 1, rows, 0.0);
-      CUDA_TRY(t, launch_mixed_gram(t, depth, b, true, s), "mixed projection launch");
+      CUDA_TRY(t, launch_mixed_gram(t, depth, b, true, k == 0 ? 1 : 2, s), "mixed projection launch");
     }
     {
       ProfScope ps(K_MUPDATE, s, 1, nodes, 0.0);

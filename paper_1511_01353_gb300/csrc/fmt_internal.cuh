@@ -181,6 +181,8 @@ struct fmt_mixed_bufs {
   int64_t acc_stride = 0;
   double* gacc = nullptr;               // 256 per item
   double* lcoef = nullptr;              // nmono per node
+  uint8_t* cache = nullptr;             // digit tiles of the projection basis, or NULL
+  size_t cap_cache = 0;
   int64_t cap_nodes = 0, cap_items = 0, cap_acc = 0;
 };
 
@@ -269,8 +271,10 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, 
 int mixed_m_cap(int max_m);            // largest m a mixed node of the level can have
 size_t mixed_acc_stride(int max_m);    // doubles of Gram accumulator per work item
 cudaError_t launch_mixed_box(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
+// cache_mode (projection only): 0 generate the basis, 1 generate and store it, 2 load it
 cudaError_t launch_mixed_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool projection,
-                              cudaStream_t s);
+                              int cache_mode, cudaStream_t s);
+size_t mixed_cache_bytes(const fmt_tree* t, int depth);  // device bytes of the basis cache of a level
 cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
 cudaError_t launch_mixed_sresid(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
 cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool last,

@@ -139,6 +139,29 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Bulk (TMA) copies between shared and global memory.  Addresses 16-byte
+// aligned, sizes multiples of 16.
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the shared-memory sources of every committed store have been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed store is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// load `bytes` into shared memory; the mbarrier's phase completes when they have landed
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle (8-row
 // atoms of 128-byte rows, 16-byte chunks XOR-ed with the row index), atoms
 // 1024 bytes apart.  Fields: start >> 4 (bits 0-13), leading offset >> 4
@@ -257,6 +280,9 @@ struct MArgs {
   int MR;                       // operand-tile rows of the level
   int tmem_cols;
   int nstages;                  // operand-tile stages (1 or 2) of k_mgram
+  uint8_t* cache;               // projection: digit tiles of every atom (4 tiles, cache_atom_bytes)
+  int cache_mode;               // 0 generate, 1 generate and store, 2 load
+  uint32_t cache_atom_bytes;
   int last_sweep;
   int* err;
 };
@@ -365,6 +391,7 @@ template <bool kProj>
 __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
   extern __shared__ uint8_t dsm_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t lbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_item, s_deg;
   __shared__ uint16_t s_lmn[(FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6];
@@ -383,9 +410,13 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
+    mbar_init(&lbar[0], 1);
+    mbar_init(&lbar[1], 1);
     fence_mbar_init();
     s_deg = -1;
   }
+  const int cmode = kProj ? a.cache_mode : 0;
+  uint32_t nload[2] = {0u, 0u};
   if (warp == 0) tc_alloc(&tmem_slot, (uint32_t)a.tmem_cols);
   tc_fence_before();
   __syncthreads();
@@ -455,13 +486,20 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
         ok = mbar_wait(&mbar[st], (ncommit[st] - 1u) & 1u);
         pending[st] = false;
       }
+      if (cmode == 1 && tid == 0) bulk_wait_read();  // the stage's previous store has read it
       if (__syncthreads_or(!ok)) {
         ok = false;
         break;
       }
       uint8_t* t0 = dsm + st * stage_bytes;
+      const int64_t atom_idx = (int64_t)item + (rs >> 6) + at;  // items are disjoint, ascending row ranges
+      if (cmode == 2) {
+        // the basis digits come from the cache; only s is generated
+        if (tid == 0) bulk_load(t0, a.cache + atom_idx * a.cache_atom_bytes, a.cache_atom_bytes, &lbar[st]);
+        nload[st] += 1u;
+      }
       // rows past this node's basis must read as zero
-      if (hi[st] > nw) {
+      if (cmode != 2 && hi[st] > nw) {
         const int nz = (hi[st] - nw) * 8;  // 16-byte words per tile
         for (int e = tid; e < kTiles * nz; e += kGThreads) {
           const int tt = e / nz, wi = e - tt * nz;
@@ -471,7 +509,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       hi[st] = nw;
       // phase A: 1-D Legendre values (threads 0..191) and the value column (192..255)
       const int64_t i0 = rs + (int64_t)at * kAtom;
-      if (tid < 3 * kAtom) {
+      if (tid < 3 * kAtom && cmode != 2) {
         const int ax = tid / kAtom;
         const int64_t i = i0 + k;
         const double* X = ax == 0 ? a.x : ax == 1 ? a.y : a.z;
@@ -504,7 +542,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
             q0 = qn;
           }
         }
-      } else if (tid < 4 * kAtom) {
+      } else if (tid >= 3 * kAtom && tid < 4 * kAtom) {
         const int64_t i = i0 + k;
         s_val[k] = i < re ? val[i] * vscale : 0.0;
       }
@@ -516,11 +554,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
         const dfl* qx = legd + k;
         const dfl* qy = legd + P1 * kAtom + k;
         const dfl* qz = legd + 2 * P1 * kAtom + k;
-        for (int j = part; j < L; j += kGParts) {
-          const int c = s_lmn[j];
-          const dfl v = df_mul(df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]), qz[(c >> 8) * kAtom]);
-          put_digits(t0, tile_bytes, j, k, valid ? fixed30(v) : 0);
-        }
+        if (cmode != 2)
+          for (int j = part; j < L; j += kGParts) {
+            const int c = s_lmn[j];
+            const dfl v = df_mul(df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]), qz[(c >> 8) * kAtom]);
+            put_digits(t0, tile_bytes, j, k, valid ? fixed30(v) : 0);
+          }
         if (part == kGParts - 1) {
           // |s vscale| < 1: round(s vscale 2^30) exactly from FP64
           int d[4];
@@ -544,6 +583,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
+        if (cmode == 2 && !mbar_wait(&lbar[st], (nload[st] - 1u) & 1u)) ok = false;
         tc_fence_after();
         const uint32_t A0 = sbase + (uint32_t)st * stage_bytes;
         if (!kProj) {
@@ -573,6 +613,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
             }
         }
         tc_commit(&mbar[st]);
+        if (cmode == 1) bulk_store(a.cache + atom_idx * a.cache_atom_bytes, t0, a.cache_atom_bytes);
       }
       ncommit[st] += 1u;
       pending[st] = true;
@@ -643,6 +684,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
     for (int s2 = 0; s2 < 2; ++s2)
       if (pending[s2]) mbar_wait(&mbar[s2], (ncommit[s2] - 1u) & 1u);
   }
+  if (cmode == 1 && tid == 0) bulk_wait_all();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -1011,6 +1053,9 @@ MArgs make_margs(const fmt_tree* t, int depth, const fmt_mixed_bufs& b) {
   a.MR = mrows_for(mixed_m_cap(L.max_m));
   a.tmem_cols = 32;
   a.nstages = 2;
+  a.cache = b.cache;
+  a.cache_mode = 0;
+  a.cache_atom_bytes = 0;
   a.last_sweep = 0;
   a.err = t->d_err;
   return a;
@@ -1023,10 +1068,12 @@ uint32_t pow2_cols(int c) {
 }
 
 template <bool kProj>
-cudaError_t launch_gram_t(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
+cudaError_t launch_gram_t(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, int cache_mode, cudaStream_t s) {
   const fmt_level& L = t->lv[depth];
   if (L.n_items <= 0) return cudaSuccess;
   MArgs a = make_margs(t, depth, b);
+  a.cache_mode = kProj && b.cache ? cache_mode : 0;
+  a.cache_atom_bytes = 4u * (uint32_t)a.MR * 128u;
   // projection: 4 digits x 2 bands x 16 columns; Gram: the two bands of the matrix
   a.tmem_cols = (int)pow2_cols(kProj ? 128 : gram_cols(mixed_m_cap(L.max_m)));
   const size_t stage = (kProj ? 4 : 3) * (size_t)a.MR * 128 + (kProj ? 2048 : 0);
@@ -1066,8 +1113,14 @@ cudaError_t launch_mixed_box(const fmt_tree* t, int depth, const fmt_mixed_bufs&
 }
 
 cudaError_t launch_mixed_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool projection,
-                              cudaStream_t s) {
-  return projection ? launch_gram_t<true>(t, depth, b, s) : launch_gram_t<false>(t, depth, b, s);
+                              int cache_mode, cudaStream_t s) {
+  return projection ? launch_gram_t<true>(t, depth, b, cache_mode, s) : launch_gram_t<false>(t, depth, b, 0, s);
+}
+
+size_t mixed_cache_bytes(const fmt_tree* t, int depth) {
+  const fmt_level& L = t->lv[depth];
+  // atom index item + row/64 + atom < n_items + n/64 + 2
+  return (size_t)(L.n_items + t->n / kAtom + 2) * 4 * (size_t)mrows_for(mixed_m_cap(L.max_m)) * 128;
 }
 
 size_t mixed_factor_smem(int max_m) {
