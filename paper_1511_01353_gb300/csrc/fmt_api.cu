@@ -198,6 +198,7 @@ fmt_status alloc_level(fmt_tree* t, int d, int64_t cap_nodes, int64_t cap_items,
   TRY(talloc(t, &L.child_E, 8 * cap_nodes, s));
   TRY(talloc(t, &L.coef, nm * cap_nodes, s));
   TRY(talloc(t, &L.hcoef, nm * cap_nodes, s));
+  if (t->P.precision == FMT_MIXED) TRY(talloc(t, &L.hcoef_df, nm * cap_nodes, s));
   TRY(talloc(t, &L.node_item0, cap_nodes, s));
   TRY(talloc(t, &L.node_nitems, cap_nodes, s));
   TRY(talloc(t, &L.item_node, cap_items, s));
@@ -649,6 +650,10 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
   {
     ProfScope ps(K_CHILD, s, 2, rows, 2.0 * rows);
     CUDA_TRY(t, launch_child_stats(t, depth, s), "child statistics launch");
+  }
+  if (L.hcoef_df) {
+    ProfScope ps(K_HCOEF, s, 1, (double)L.n_nodes, 0.0);
+    CUDA_TRY(t, launch_make_hcoef_df(t, depth, s), "double-float coefficients launch");
   }
   L.fitted = true;
   t->next_fit = -1;

@@ -94,6 +94,60 @@ __device__ __forceinline__ double fmt_horner(const double* __restrict__ G, int p
   return fmt_horner_t<true>(G, p, nmono, u, v, w);
 }
 
+// double-float arithmetic (Dekker / Knuth error-free transformations)
+struct dfl {  // value h + l, |l| <= ulp(h) / 2
+  float h, l;
+};
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_sub(dfl x, dfl y) {
+  const float s = __fsub_rn(x.h, y.h);
+  const float bb = __fsub_rn(s, x.h);
+  const float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(-y.h, bb));
+  return fast_two_sum(s, __fadd_rn(e, __fsub_rn(x.l, y.l)));
+}
+__device__ __forceinline__ dfl df_of(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  const float s = __fadd_rn(x.h, y.h);
+  const float bb = __fsub_rn(s, x.h);
+  const float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(y.h, bb));
+  return fast_two_sum(s, __fadd_rn(e, __fadd_rn(x.l, y.l)));
+}
+// x * w + c in double-float
+__device__ __forceinline__ dfl df_fma(dfl x, dfl w, dfl c) { return df_add(df_mul(x, w), c); }
+
+// The node polynomial of fmt_horner_t in double-float: the same nested Horner
+// order, coefficients G as (hi, lo) pairs.
+__device__ __forceinline__ dfl fmt_horner_df(const float2* __restrict__ G, int p, int nmono, dfl u, dfl v, dfl w) {
+  int idx = nmono - 1;
+  dfl P = {0.0f, 0.0f};
+  for (int l = p; l >= 0; --l) {
+    dfl t = {0.0f, 0.0f};
+    for (int m = p - l; m >= 0; --m) {
+      dfl s = {0.0f, 0.0f};
+      for (int n = p - l - m; n >= 0; --n) {
+        const float2 g = __ldg(G + idx--);
+        s = df_fma(s, w, dfl{g.x, g.y});
+      }
+      t = df_fma(t, v, s);
+    }
+    P = df_fma(P, u, t);
+  }
+  return P;
+}
+
 // nmono(p) on the device
 __host__ __device__ __forceinline__ int fmt_nmono_d(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
 
@@ -151,6 +205,7 @@ struct fmt_level {
   double* child_E = nullptr;   // 8 per node: RMS
   double* coef = nullptr;      // nmono per node: F (Alg. 2 order)
   double* hcoef = nullptr;     // nmono per node: F / (l! m! n!) for Horner
+  float2* hcoef_df = nullptr;  // mixed trees: hcoef as double-float (hi, lo) for evaluation
   int64_t* node_item0 = nullptr;
   int32_t* node_nitems = nullptr;
   // QR work items: (node, [start, end)) row chunks, node-major
@@ -281,3 +336,4 @@ cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bu
                                 cudaStream_t s);
 cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream_t s);
 cudaError_t launch_make_hcoef(const fmt_tree* t, int depth, cudaStream_t s);
+cudaError_t launch_make_hcoef_df(const fmt_tree* t, int depth, cudaStream_t s);

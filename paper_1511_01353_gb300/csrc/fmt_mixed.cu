@@ -331,31 +331,6 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
 // rows stays below 2^22: the FP32 tensor-core accumulation is exact, each
 // pair has its own accumulator, and the pairs are combined in FP64.
 
-// double-float arithmetic (Dekker / Knuth error-free transformations)
-struct dfl {
-  float h, l;
-};
-__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
-  const float p = __fmul_rn(x.h, y.h);
-  float e = __fmaf_rn(x.h, y.h, -p);
-  e = __fmaf_rn(x.h, y.l, e);
-  e = __fmaf_rn(x.l, y.h, e);
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ dfl df_sub(dfl x, dfl y) {
-  const float s = __fsub_rn(x.h, y.h);
-  const float bb = __fsub_rn(s, x.h);
-  const float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(-y.h, bb));
-  return fast_two_sum(s, __fadd_rn(e, __fsub_rn(x.l, y.l)));
-}
-__device__ __forceinline__ dfl df_of(double v) {
-  const float h = __double2float_rn(v);
-  return {h, __double2float_rn(v - (double)h)};
-}
 // four signed digits of round(v 2^30), |v| <= 1
 __device__ __forceinline__ void digits4(int X, int (&d)[4]) {
   d[0] = (X + (1 << 22)) >> 23;  // arithmetic shifts: floor division

@@ -363,9 +363,14 @@ struct EvalArgs {
   const int32_t* tprob;  // problem of each target, or NULL (problem 0)
   const uint64_t* prefix[FMT_MAX_DEPTH + 1];
   const double* hcoef[FMT_MAX_DEPTH + 1];
+  const float2* hcoef_df[FMT_MAX_DEPTH + 1];
   int64_t n_nodes[FMT_MAX_DEPTH + 1];
 };
 
+// Sec. 2 (end): the interpolant at a target is the sum over its octree path
+// of the node polynomials.  kDF: the node polynomials in double-float on the
+// FP32 pipe (mixed-precision trees), the frames and the sum over levels in FP64.
+template <bool kDF>
 __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const double* __restrict__ xq,
                                                   const double* __restrict__ yq, const double* __restrict__ zq,
                                                   double* __restrict__ out, unsigned long long* outside,
@@ -406,14 +411,29 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
         fmt_frame(pr.lo[0], pr.side, d, fmt_compact3(mp), c0, s0);
         fmt_frame(pr.lo[1], pr.side, d, fmt_compact3(mp >> 1), c1, s1);
         fmt_frame(pr.lo[2], pr.side, d, fmt_compact3(mp >> 2), c2, s2);
-        acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.stride, p, nm, fmt_local(x, c0, s0), fmt_local(y, c1, s1),
-                          fmt_local(z, c2, s2));
+        if (kDF) {
+          const dfl v = fmt_horner_df(a.hcoef_df[d] + (size_t)lo * a.stride, p, nm, df_of(fmt_local(x, c0, s0)),
+                                      df_of(fmt_local(y, c1, s1)), df_of(fmt_local(z, c2, s2)));
+          acc += (double)v.h + (double)v.l;
+        } else {
+          acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.stride, p, nm, fmt_local(x, c0, s0), fmt_local(y, c1, s1),
+                            fmt_local(z, c2, s2));
+        }
       }
       out[t] = acc;
     }
     const unsigned b = __ballot_sync(0xffffffffu, outs);
     if (outside != nullptr && (threadIdx.x & 31) == 0 && b) atomicAdd(outside, (unsigned long long)__popc(b));
   }
+}
+
+// hcoef as (hi, lo) FP32 pairs: hi = fl32(v), lo = fl32(v - hi)
+__global__ void k_make_hcoef_df(int64_t n, const double* __restrict__ hcoef, float2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = hcoef[i];
+  const float h = __double2float_rn(v);
+  out[i] = make_float2(h, __double2float_rn(v - (double)h));
 }
 
 // F / (l! m! n!) for imported trees (node degree from its problem; entries
@@ -540,12 +560,26 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, 
   for (int d = 0; d <= FMT_MAX_DEPTH; ++d) {
     a.prefix[d] = d < nf ? t->lv[d].prefix : nullptr;
     a.hcoef[d] = d < nf ? t->lv[d].hcoef : nullptr;
+    a.hcoef_df[d] = d < nf ? t->lv[d].hcoef_df : nullptr;
     a.n_nodes[d] = d < nf ? t->lv[d].n_nodes : 0;
   }
+  bool df = t->P.precision == FMT_MIXED && nf > 0;
+  for (int d = 0; d < nf; ++d) df = df && t->lv[d].hcoef_df != nullptr;
   int64_t blocks = (m + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
-  k_evaluate<<<(unsigned)blocks, 256, 0, s>>>(a, m, xq, yq, zq, out, d_outside, t->d_err);
+  if (df)
+    k_evaluate<true><<<(unsigned)blocks, 256, 0, s>>>(a, m, xq, yq, zq, out, d_outside, t->d_err);
+  else
+    k_evaluate<false><<<(unsigned)blocks, 256, 0, s>>>(a, m, xq, yq, zq, out, d_outside, t->d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_make_hcoef_df(const fmt_tree* t, int depth, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  const int64_t tot = L.n_nodes * t->nmono;
+  if (tot <= 0 || !L.hcoef_df) return cudaSuccess;
+  k_make_hcoef_df<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(tot, L.hcoef, L.hcoef_df);
   return cudaGetLastError();
 }
 
