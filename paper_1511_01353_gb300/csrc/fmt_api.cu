@@ -198,7 +198,8 @@ fmt_status alloc_level(fmt_tree* t, int d, int64_t cap_nodes, int64_t cap_items,
   TRY(talloc(t, &L.child_E, 8 * cap_nodes, s));
   TRY(talloc(t, &L.coef, nm * cap_nodes, s));
   TRY(talloc(t, &L.hcoef, nm * cap_nodes, s));
-  if (t->P.precision == FMT_MIXED) TRY(talloc(t, &L.hcoef_df, nm * cap_nodes, s));
+  TRY(talloc(t, &L.ccoef, nm * cap_nodes, s));
+  if (t->P.precision == FMT_MIXED) TRY(talloc(t, &L.ccoef_df, nm * cap_nodes, s));
   TRY(talloc(t, &L.node_item0, cap_nodes, s));
   TRY(talloc(t, &L.node_nitems, cap_nodes, s));
   TRY(talloc(t, &L.item_node, cap_items, s));
@@ -651,9 +652,9 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
     ProfScope ps(K_CHILD, s, 2, rows, 2.0 * rows);
     CUDA_TRY(t, launch_child_stats(t, depth, s), "child statistics launch");
   }
-  if (L.hcoef_df) {
+  {
     ProfScope ps(K_HCOEF, s, 1, (double)L.n_nodes, 0.0);
-    CUDA_TRY(t, launch_make_hcoef_df(t, depth, s), "double-float coefficients launch");
+    CUDA_TRY(t, launch_make_cum(t, depth, s), "cumulative polynomials launch");
   }
   L.fitted = true;
   t->next_fit = -1;
@@ -1074,8 +1075,9 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
       return set_err(nullptr, FMT_ECUDA, "import upload: %s", cudaGetErrorString(e));
     }
     {
-      ProfScope ps(K_HCOEF, s, 1, (double)k, 0.0);
+      ProfScope ps(K_HCOEF, s, 2, (double)k, 0.0);
       e = launch_make_hcoef(t, d, s);
+      if (e == cudaSuccess) e = launch_make_cum(t, d, s);
     }
     if (e != cudaSuccess) {
       destroy(t);

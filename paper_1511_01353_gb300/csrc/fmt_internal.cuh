@@ -205,7 +205,9 @@ struct fmt_level {
   double* child_E = nullptr;   // 8 per node: RMS
   double* coef = nullptr;      // nmono per node: F (Alg. 2 order)
   double* hcoef = nullptr;     // nmono per node: F / (l! m! n!) for Horner
-  float2* hcoef_df = nullptr;  // mixed trees: hcoef as double-float (hi, lo) for evaluation
+  double* ccoef = nullptr;     // nmono per node: the node's and all its ancestors' polynomials summed,
+                               // as one polynomial in the node's frame (Horner form, like hcoef)
+  float2* ccoef_df = nullptr;  // mixed trees: ccoef as double-float (hi, lo) for evaluation
   int64_t* node_item0 = nullptr;
   int32_t* node_nitems = nullptr;
   // QR work items: (node, [start, end)) row chunks, node-major
@@ -336,4 +338,5 @@ cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bu
                                 cudaStream_t s);
 cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream_t s);
 cudaError_t launch_make_hcoef(const fmt_tree* t, int depth, cudaStream_t s);
-cudaError_t launch_make_hcoef_df(const fmt_tree* t, int depth, cudaStream_t s);
+// ccoef (and ccoef_df) of a level from its hcoef and the parent level's ccoef
+cudaError_t launch_make_cum(const fmt_tree* t, int depth, cudaStream_t s);

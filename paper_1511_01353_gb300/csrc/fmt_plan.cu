@@ -363,13 +363,19 @@ struct EvalArgs {
   const int32_t* tprob;  // problem of each target, or NULL (problem 0)
   const uint64_t* prefix[FMT_MAX_DEPTH + 1];
   const double* hcoef[FMT_MAX_DEPTH + 1];
-  const float2* hcoef_df[FMT_MAX_DEPTH + 1];
+  const double* ccoef[FMT_MAX_DEPTH + 1];
+  const float2* ccoef_df[FMT_MAX_DEPTH + 1];
   int64_t n_nodes[FMT_MAX_DEPTH + 1];
 };
 
 // Sec. 2 (end): the interpolant at a target is the sum over its octree path
-// of the node polynomials.  kDF: the node polynomials in double-float on the
-// FP32 pipe (mixed-precision trees), the frames and the sum over levels in FP64.
+// of the node polynomials.  A target inside its problem's root cube takes the
+// deepest node on its path and evaluates that node's cumulative polynomial
+// (ccoef: the path's polynomials re-expanded in the node's frame, Sec. 5's
+// downward translation), one polynomial instead of one per level; a target
+// outside the cube, whose leaf-frame coordinates may be large, sums the
+// per-level polynomials as in Sec. 2.  kDF: the polynomial in double-float
+// on the FP32 pipe (mixed-precision trees); frames in FP64.
 template <bool kDF>
 __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const double* __restrict__ xq,
                                                   const double* __restrict__ yq, const double* __restrict__ zq,
@@ -396,6 +402,9 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
                             (fmt_spread3(fmt_quant(z, pr.lo[2], pr.S)) << 2);
       const int p = pr.degree, nm = fmt_nmono_d(p);
       double acc = 0.0;
+      int deep = -1;
+      int64_t deep_idx = 0;
+      uint64_t deep_mp = 0;
       for (int d = 0; d < a.n_levels; ++d) {
         const uint64_t mp = d == 0 ? 0ull : (code >> (3 * (FMT_QBITS - d)));
         const uint64_t P = ((uint64_t)pid << (3 * d)) | mp;
@@ -407,17 +416,32 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
           else hi = mid;
         }
         if (lo >= a.n_nodes[d] || pr_[lo] != P) break;
+        if (!outs) {
+          deep = d;
+          deep_idx = lo;
+          deep_mp = mp;
+          continue;
+        }
         double c0, s0, c1, s1, c2, s2;
         fmt_frame(pr.lo[0], pr.side, d, fmt_compact3(mp), c0, s0);
         fmt_frame(pr.lo[1], pr.side, d, fmt_compact3(mp >> 1), c1, s1);
         fmt_frame(pr.lo[2], pr.side, d, fmt_compact3(mp >> 2), c2, s2);
+        acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.stride, p, nm, fmt_local(x, c0, s0), fmt_local(y, c1, s1),
+                          fmt_local(z, c2, s2));
+      }
+      if (deep >= 0) {
+        double c0, s0, c1, s1, c2, s2;
+        fmt_frame(pr.lo[0], pr.side, deep, fmt_compact3(deep_mp), c0, s0);
+        fmt_frame(pr.lo[1], pr.side, deep, fmt_compact3(deep_mp >> 1), c1, s1);
+        fmt_frame(pr.lo[2], pr.side, deep, fmt_compact3(deep_mp >> 2), c2, s2);
         if (kDF) {
-          const dfl v = fmt_horner_df(a.hcoef_df[d] + (size_t)lo * a.stride, p, nm, df_of(fmt_local(x, c0, s0)),
-                                      df_of(fmt_local(y, c1, s1)), df_of(fmt_local(z, c2, s2)));
-          acc += (double)v.h + (double)v.l;
+          const dfl v = fmt_horner_df(a.ccoef_df[deep] + (size_t)deep_idx * a.stride, p, nm,
+                                      df_of(fmt_local(x, c0, s0)), df_of(fmt_local(y, c1, s1)),
+                                      df_of(fmt_local(z, c2, s2)));
+          acc = (double)v.h + (double)v.l;
         } else {
-          acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.stride, p, nm, fmt_local(x, c0, s0), fmt_local(y, c1, s1),
-                            fmt_local(z, c2, s2));
+          acc = fmt_horner(a.ccoef[deep] + (size_t)deep_idx * a.stride, p, nm, fmt_local(x, c0, s0),
+                           fmt_local(y, c1, s1), fmt_local(z, c2, s2));
         }
       }
       out[t] = acc;
@@ -427,13 +451,115 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
   }
 }
 
-// hcoef as (hi, lo) FP32 pairs: hi = fl32(v), lo = fl32(v - hi)
-__global__ void k_make_hcoef_df(int64_t n, const double* __restrict__ hcoef, float2* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double v = hcoef[i];
-  const float h = __double2float_rn(v);
-  out[i] = make_float2(h, __double2float_rn(v - (double)h));
+// The cumulative polynomial of a node: its parent's cumulative polynomial
+// (parent frame) re-expanded in the node's frame, plus its own.  With h the
+// node's half-width, the parent's coordinate is u_p = (u + sigma) / 2 per axis
+// (sigma = +1 for the upper octant, -1 for the lower), so
+//   u_p^L = 2^-L sum_l C(L, l) sigma^(L-l) u^l,
+// a separable transform applied along x, y and z to the dense coefficient
+// cube (zeros above total degree p); every factor is a dyadic rational.
+struct CumArgs {
+  int depth, stride;
+  const int32_t* node_prob;
+  const fmt_problem* prob;
+  const uint64_t* prefix;
+  const double* hcoef;
+  double* ccoef;
+  float2* ccoef_df;
+  const uint64_t* pprefix;  // parent level
+  int64_t pn;
+  const double* pccoef;
+  int* err;
+};
+
+__global__ void __launch_bounds__(128) k_make_cum(CumArgs a) {
+  extern __shared__ double cube[];  // (p+1)^3, index (l * P1 + m) * P1 + n
+  __shared__ double binom[(FMT_MAX_DEGREE + 1) * (FMT_MAX_DEGREE + 1)];
+  __shared__ int64_t s_parent;
+  const int64_t node = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int p = a.prob[a.node_prob[node]].degree, P1 = p + 1, nm = fmt_nmono_d(p);
+  const double* own = a.hcoef + node * a.stride;
+  double* out = a.ccoef + node * a.stride;
+  if (a.depth > 0) {
+    for (int e = tid; e < P1 * P1; e += blockDim.x) {
+      const int L = e / P1, l = e - L * P1;
+      double c = 0.0;
+      if (l <= L) {
+        c = 1.0;
+        for (int i = 1; i <= l; ++i) c = c * (double)(L - l + i) / (double)i;  // exact integers
+      }
+      binom[e] = c;
+    }
+    for (int e = tid; e < P1 * P1 * P1; e += blockDim.x) cube[e] = 0.0;
+    if (tid == 0) {
+      const uint64_t pk = a.prefix[node] >> 3;
+      int64_t lo = 0, hi = a.pn;
+      while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (a.pprefix[mid] < pk) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= a.pn || a.pprefix[lo] != pk) {
+        atomicOr(a.err, FMT_ERR_INDEX);
+        lo = 0;
+      }
+      s_parent = lo;
+    }
+    __syncthreads();
+    const double* G = a.pccoef + s_parent * a.stride;
+    for (int l = 0, J = 0; l <= p; ++l)
+      for (int m = 0; m <= p - l; ++m)
+        for (int n = 0; n <= p - l - m; ++n, ++J)
+          if ((J & (blockDim.x - 1)) == tid) cube[(l * P1 + m) * P1 + n] = G[J];
+    __syncthreads();
+    const unsigned oct = (unsigned)(a.prefix[node] & 7ull);
+    for (int ax = 0; ax < 3; ++ax) {
+      const double sg = ((oct >> ax) & 1u) ? 1.0 : -1.0;
+      // lines along axis ax: the other two indices (i, j) with i + j <= p
+      for (int e = tid; e < P1 * P1; e += blockDim.x) {
+        const int i = e / P1, j = e - i * P1;
+        if (i + j > p) continue;
+        const int top = p - i - j;
+        int stride_ax, base;
+        if (ax == 0) {
+          stride_ax = P1 * P1;
+          base = i * P1 + j;
+        } else if (ax == 1) {
+          stride_ax = P1;
+          base = i * P1 * P1 + j;
+        } else {
+          stride_ax = 1;
+          base = (i * P1 + j) * P1;
+        }
+        // new[l] = sum_{L >= l} old[L] 2^-L C(L, l) sg^(L - l), in place in ascending l
+        for (int l = 0; l <= top; ++l) {
+          double v = 0.0;
+          for (int L = l; L <= top; ++L) {
+            const double t = ldexp(binom[L * P1 + l], -L);
+            v = fma(((L - l) & 1) ? sg * t : t, cube[base + L * stride_ax], v);
+          }
+          cube[base + l * stride_ax] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int l = 0, J = 0; l <= p; ++l)
+    for (int m = 0; m <= p - l; ++m)
+      for (int n = 0; n <= p - l - m; ++n, ++J)
+        if ((J & (blockDim.x - 1)) == tid) {
+          const double v = own[J] + (a.depth > 0 ? cube[(l * P1 + m) * P1 + n] : 0.0);
+          out[J] = v;
+          if (a.ccoef_df) {
+            const float h = __double2float_rn(v);
+            a.ccoef_df[node * a.stride + J] = make_float2(h, __double2float_rn(v - (double)h));
+          }
+        }
+  for (int J = nm + tid; J < a.stride; J += blockDim.x) {
+    out[J] = 0.0;
+    if (a.ccoef_df) a.ccoef_df[node * a.stride + J] = make_float2(0.0f, 0.0f);
+  }
 }
 
 // F / (l! m! n!) for imported trees (node degree from its problem; entries
@@ -560,11 +686,12 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, 
   for (int d = 0; d <= FMT_MAX_DEPTH; ++d) {
     a.prefix[d] = d < nf ? t->lv[d].prefix : nullptr;
     a.hcoef[d] = d < nf ? t->lv[d].hcoef : nullptr;
-    a.hcoef_df[d] = d < nf ? t->lv[d].hcoef_df : nullptr;
+    a.ccoef[d] = d < nf ? t->lv[d].ccoef : nullptr;
+    a.ccoef_df[d] = d < nf ? t->lv[d].ccoef_df : nullptr;
     a.n_nodes[d] = d < nf ? t->lv[d].n_nodes : 0;
   }
   bool df = t->P.precision == FMT_MIXED && nf > 0;
-  for (int d = 0; d < nf; ++d) df = df && t->lv[d].hcoef_df != nullptr;
+  for (int d = 0; d < nf; ++d) df = df && t->lv[d].ccoef_df != nullptr;
   int64_t blocks = (m + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
@@ -575,11 +702,24 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_make_hcoef_df(const fmt_tree* t, int depth, cudaStream_t s) {
+cudaError_t launch_make_cum(const fmt_tree* t, int depth, cudaStream_t s) {
   const fmt_level& L = t->lv[depth];
-  const int64_t tot = L.n_nodes * t->nmono;
-  if (tot <= 0 || !L.hcoef_df) return cudaSuccess;
-  k_make_hcoef_df<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(tot, L.hcoef, L.hcoef_df);
+  if (L.n_nodes <= 0) return cudaSuccess;
+  CumArgs a;
+  a.depth = depth;
+  a.stride = t->nmono;
+  a.node_prob = L.prob;
+  a.prob = t->d_prob;
+  a.prefix = L.prefix;
+  a.hcoef = L.hcoef;
+  a.ccoef = L.ccoef;
+  a.ccoef_df = L.ccoef_df;
+  a.pprefix = depth > 0 ? t->lv[depth - 1].prefix : nullptr;
+  a.pn = depth > 0 ? t->lv[depth - 1].n_nodes : 0;
+  a.pccoef = depth > 0 ? t->lv[depth - 1].ccoef : nullptr;
+  a.err = t->d_err;
+  const int P1 = t->max_degree + 1;
+  k_make_cum<<<(unsigned)L.n_nodes, 128, sizeof(double) * (size_t)(P1 * P1 * P1), s>>>(a);
   return cudaGetLastError();
 }
 
