@@ -506,7 +506,8 @@ def main():
     ev_levels = 0 if is_batch else levels_visited(ex, w.xq, w.yq, w.zq, (0.0, 0.0, 0.0), 1.0)
     hf = 2.0 * (F.fmt_nmono(deg) + (deg + 1) * (deg + 2) / 2 + (deg + 1))
     ev = prof.get("evaluate", {})
-    ev_tflops = ev_levels * hf * args.steps / (ev["ms"] * 1e-3) / 1e12 if ev.get("ms") else None
+    # a target inside its root cube evaluates one cumulative polynomial (its deepest node's)
+    ev_tflops = w.m * hf * args.steps / (ev["ms"] * 1e-3) / 1e12 if ev.get("ms") else None
     total_ms = sum(v["ms"] for v in prof.values())
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                    "share": (v["ms"] / total_ms if total_ms else None)} for k, v in prof.items() if v["launches"]}
@@ -638,7 +639,8 @@ def main():
                          "what": "algorithmic flops of the whole fit phase / fit wall time"},
         "eval_roofline": {"bound": "alu", "achieved": ev_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                           "frac": (ev_tflops / FP64_NOMINAL_TFLOPS if ev_tflops else None),
-                          "flops_per_target_level": hf},
+                          "flops_per_target": hf, "levels_on_target_paths": ev_levels,
+                          "what": "one Horner evaluation of the deepest node's cumulative polynomial per target"},
         "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clocks,
         "tree": {"nodes": nodes, "points": points, "level_fit_ms": level_fit_ms,
                  "level_items": [int(stats.items[d]) for d in range(stats.n_levels)],
