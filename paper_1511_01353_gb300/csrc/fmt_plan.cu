@@ -371,8 +371,8 @@ struct EvalArgs {
 // Sec. 2 (end): the interpolant at a target is the sum over its octree path
 // of the node polynomials.  A target inside its problem's root cube takes the
 // deepest node on its path and evaluates that node's cumulative polynomial
-// (ccoef: the path's polynomials re-expanded in the node's frame, Sec. 5's
-// downward translation), one polynomial instead of one per level; a target
+// (ccoef: the path's polynomials re-expanded in the node's frame -- the
+// downward propagation the Conclusions mention), one polynomial instead of one per level; a target
 // outside the cube, whose leaf-frame coordinates may be large, sums the
 // per-level polynomials as in Sec. 2.  kDF: the polynomial in double-float
 // on the FP32 pipe (mixed-precision trees); frames in FP64.
