@@ -553,7 +553,7 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
   }
   {
     ProfScope ps(K_MGRAM, s, 1, rows, 0.0);
-    CUDA_TRY(t, launch_mixed_gram(t, depth, b, false, 0, s), "mixed Gram launch");
+    CUDA_TRY(t, launch_mixed_gram(t, depth, b, false, 1, s), "mixed Gram launch");
   }
   {
     ProfScope ps(K_MFACTOR, s, 1, nodes, 0.0);
@@ -567,7 +567,7 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
     }
     {
       ProfScope ps(K_MPROJ, s, 1, rows, 0.0);
-      CUDA_TRY(t, launch_mixed_gram(t, depth, b, true, k == 0 ? 1 : 2, s), "mixed projection launch");
+      CUDA_TRY(t, launch_mixed_gram(t, depth, b, true, 2, s), "mixed projection launch");
     }
     {
       ProfScope ps(K_MUPDATE, s, 1, nodes, 0.0);

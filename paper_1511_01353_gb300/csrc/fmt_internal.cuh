@@ -328,7 +328,8 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, 
 int mixed_m_cap(int max_m);            // largest m a mixed node of the level can have
 size_t mixed_acc_stride(int max_m);    // doubles of Gram accumulator per work item
 cudaError_t launch_mixed_box(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
-// cache_mode (projection only): 0 generate the basis, 1 generate and store it, 2 load it
+// cache_mode: 0 generate the basis digits, 1 generate and store them (Gram), 2 load them (projection);
+// without a cache buffer every launch generates
 cudaError_t launch_mixed_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool projection,
                               int cache_mode, cudaStream_t s);
 size_t mixed_cache_bytes(const fmt_tree* t, int depth);  // device bytes of the basis cache of a level

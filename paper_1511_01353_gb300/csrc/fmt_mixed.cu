@@ -11,15 +11,18 @@
 //     by a power of two to O(1).  Same polynomial space as Alg. 2's moments,
 //     so the same least-squares function; far better conditioned.
 //  2. k_mgram: per work item, the Gram matrix [B | r]^T [B | r] on the tensor
-//     cores (tcgen05.mma kind::f16): every FP32 value is split into three
-//     BF16 terms h + m + l, the six products hh, hm, mh, mm, hl, lh are
-//     accumulated in FP32 in tensor memory, and every 256 rows the FP32
-//     accumulator is added into an FP64 copy in global memory.
+//     cores (tcgen05.mma kind::f16): the basis (in double-float) and r are
+//     cut into four fixed-point digits stored as BF16 tiles; the six leading
+//     digit-tile products are accumulated in FP32 in tensor memory, and every
+//     256 rows the accumulator is added into an FP64 copy in global memory.
+//     The digit tiles are also stored in HBM (TMA bulk stores) for the sweeps.
 //  3. k_mfactor: per node, the item Grams are summed in FP64 and factorised by
 //     Cholesky; the factor is R-hat = [[R, Q^T r], [0, rho]] of the FP64 path
 //     (the same matrix's R factor, up to row signs).  F = R^{-1} Q^T r.
 //  4. sweeps: s = r - Lambda F in FP64 (k_msresid), g = B^T s on the tensor
-//     cores (k_mgram projection mode), F += R^{-1} R^{-T} g (k_mupdate).
+//     cores from the stored digit tiles (TMA bulk loads) and the integer
+//     digits of s, exactly (k_mgram projection mode), F += R^{-1} R^{-T} g
+//     (k_mupdate).
 //  5. F is converted to the moment basis of Alg. 2 in the node frame (exact
 //     in the scaling, Legendre coefficients are dyadic rationals), so the
 //     residual update, the evaluation and the export are those of the FP64
@@ -181,34 +184,6 @@ __device__ __forceinline__ uint32_t sw_off(int j, int k) {
   return (uint32_t)((j >> 3) * 1024 + (j & 7) * 128 + ((((k >> 3) ^ j) & 7) << 4) + ((k & 7) << 1));
 }
 
-// v = h + m + l, each a BF16 (the remainders are exact in FP32)
-__device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
-  h = __float2bfloat16_rn(v);
-  const float r1 = __fsub_rn(v, __bfloat162float(h));
-  m = __float2bfloat16_rn(r1);
-  l = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m)));
-}
-__device__ __forceinline__ void put3(uint8_t* t0, uint32_t tile_bytes, int j, int k, float v) {
-  __nv_bfloat16 h, m, l;
-  split3(v, h, m, l);
-  const uint32_t o = sw_off(j, k);
-  *reinterpret_cast<__nv_bfloat16*>(t0 + o) = h;
-  *reinterpret_cast<__nv_bfloat16*>(t0 + tile_bytes + o) = m;
-  *reinterpret_cast<__nv_bfloat16*>(t0 + 2 * tile_bytes + o) = l;
-}
-
-// Legendre polynomials P_0..P_P at t in FP32 (Bonnet's recurrence)
-template <int P>
-__device__ __forceinline__ void legendre_f(float t, float (&q)[P + 1]) {
-  q[0] = 1.0f;
-  if (P >= 1) q[1] = t;
-#pragma unroll
-  for (int k = 1; k < P; ++k) {
-    const float a = (float)(2 * k + 1) / (float)(k + 1), b = (float)k / (float)(k + 1);
-    q[k + 1] = a * t * q[k] - b * q[k - 1];
-  }
-}
-
 // ------------------------------------------------------------------ node frame
 struct MFrame {
   double c[3], s[3], ex[3];  // u = (x - c) s ; t = u ex (ex = 2^e)
@@ -340,19 +315,25 @@ __device__ __forceinline__ void digits4(int X, int (&d)[4]) {
   d[2] = (X + (1 << 6)) >> 7;
   d[3] = X - d[2] * (1 << 7);
 }
+__host__ __device__ constexpr int digit_exp(int q) { return q == 0 ? -7 : q == 1 ? -15 : q == 2 ? -23 : -30; }
+__host__ __device__ constexpr float digit_scale(int q) {
+  return q == 0 ? 0x1p-7f : q == 1 ? 0x1p-15f : q == 2 ? 0x1p-23f : 0x1p-30f;
+}
+// The four digits of X = round(v 2^30) stored pre-scaled, d_q 2^e_q (exact
+// in BF16), one per tile: the tiles sum to v (to 2^-31), so products of
+// tiles carry their weights, and a tile times the integer digits of s sums
+// exactly in FP32 over 256 rows (|d| <= 128).
 __device__ __forceinline__ void put_digits(uint8_t* t0, uint32_t tile_bytes, int j, int k, int X) {
   int d[4];
   digits4(X, d);
   const uint32_t o = sw_off(j, k);
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    *reinterpret_cast<__nv_bfloat16*>(t0 + q * tile_bytes + o) = __float2bfloat16_rn((float)d[q]);
+    *reinterpret_cast<__nv_bfloat16*>(t0 + q * tile_bytes + o) = __float2bfloat16_rn((float)d[q] * digit_scale(q));
 }
 __device__ __forceinline__ int fixed30(dfl v) {
   return __float2int_rn(__fmul_rn(v.h, 1073741824.0f)) + __float2int_rn(__fmul_rn(v.l, 1073741824.0f));
 }
-__host__ __device__ constexpr int digit_exp(int q) { return q == 0 ? -7 : q == 1 ? -15 : q == 2 ? -23 : -30; }
-
 // One 64-row atom of the operand tiles is generated in two phases: 192
 // threads evaluate the 1-D Legendre values P_0..P_p of the atom's rows (one
 // axis each) into shared memory; then every thread takes one row and every
@@ -372,15 +353,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
   __shared__ uint16_t s_lmn[(FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6];
   __shared__ double s_val[kAtom];
   __shared__ double s_red[kProj ? 2 * 4 * 128 : 1];
-  constexpr int kTiles = kProj ? 4 : 3;
+  constexpr int kTiles = 4;  // the four digit tiles of the basis (Gram: plus the r row)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
   const uint32_t tile_bytes = (uint32_t)a.MR * 128u;
   const uint32_t stage_bytes = kTiles * tile_bytes + (kProj ? 2048u : 0u);
   const int nst = a.nstages;
   const uint32_t total = (uint32_t)nst * stage_bytes;
-  float* legf = reinterpret_cast<float*>(dsm + total);  // Gram: [3][p+1][64] floats
-  dfl* legd = reinterpret_cast<dfl*>(dsm + total);      // projection: the same, double-float
+  dfl* legd = reinterpret_cast<dfl*>(dsm + total);  // [3][p+1][64] double-float Legendre values
   for (uint32_t o = 16u * tid; o < total; o += 16u * kGThreads) *reinterpret_cast<uint4*>(dsm + o) = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
@@ -390,7 +370,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
     fence_mbar_init();
     s_deg = -1;
   }
-  const int cmode = kProj ? a.cache_mode : 0;
+  const int cmode = a.cache_mode;  // Gram: 0 or 1 (store the tiles); projection: 0 or 2 (load them)
   uint32_t nload[2] = {0u, 0u};
   if (warp == 0) tc_alloc(&tmem_slot, (uint32_t)a.tmem_cols);
   tc_fence_before();
@@ -489,71 +469,50 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
         const int64_t i = i0 + k;
         const double* X = ax == 0 ? a.x : ax == 1 ? a.y : a.z;
         const double t = i < re ? fmt_local(X[i], F.c[ax], F.s[ax]) * F.ex[ax] : 0.0;
-        if (kProj) {
-          dfl* q = legd + ax * (p + 1) * kAtom + k;
-          const dfl td = df_of(t);
-          dfl qm = {1.0f, 0.0f}, q0 = td;
-          q[0] = qm;
-          if (p >= 1) q[kAtom] = q0;
-          for (int kk = 1; kk < p; ++kk) {
-            const double ad = (double)(2 * kk + 1) / (double)(kk + 1), bd = (double)kk / (double)(kk + 1);
-            const dfl ca = {(float)ad, (float)(ad - (double)(float)ad)}, cb = {(float)bd, (float)(bd - (double)(float)bd)};
-            const dfl qn = df_sub(df_mul(ca, df_mul(td, q0)), df_mul(cb, qm));
-            q[(kk + 1) * kAtom] = qn;
-            qm = q0;
-            q0 = qn;
-          }
-        } else {
-          float* q = legf + ax * (p + 1) * kAtom + k;
-          const float tf = (float)t;
-          float qm = 1.0f, q0 = tf;
-          q[0] = qm;
-          if (p >= 1) q[kAtom] = q0;
-          for (int kk = 1; kk < p; ++kk) {
-            const float ca = (float)(2 * kk + 1) / (float)(kk + 1), cb = (float)kk / (float)(kk + 1);
-            const float qn = ca * tf * q0 - cb * qm;
-            q[(kk + 1) * kAtom] = qn;
-            qm = q0;
-            q0 = qn;
-          }
+        dfl* q = legd + ax * (p + 1) * kAtom + k;
+        const dfl td = df_of(t);
+        dfl qm = {1.0f, 0.0f}, q0 = td;
+        q[0] = qm;
+        if (p >= 1) q[kAtom] = q0;
+        for (int kk = 1; kk < p; ++kk) {
+          const double ad = (double)(2 * kk + 1) / (double)(kk + 1), bd = (double)kk / (double)(kk + 1);
+          const dfl ca = {(float)ad, (float)(ad - (double)(float)ad)}, cb = {(float)bd, (float)(bd - (double)(float)bd)};
+          const dfl qn = df_sub(df_mul(ca, df_mul(td, q0)), df_mul(cb, qm));
+          q[(kk + 1) * kAtom] = qn;
+          qm = q0;
+          q0 = qn;
         }
       } else if (tid >= 3 * kAtom && tid < 4 * kAtom) {
         const int64_t i = i0 + k;
         s_val[k] = i < re ? val[i] * vscale : 0.0;
       }
       __syncthreads();
-      // phase B: products, every kGParts-th column
+      // phase B: products, every kGParts-th column, as pre-scaled digits
       const bool valid = i0 + k < re;
       const int P1 = p + 1;
-      if (kProj) {
+      if (cmode != 2) {
         const dfl* qx = legd + k;
         const dfl* qy = legd + P1 * kAtom + k;
         const dfl* qz = legd + 2 * P1 * kAtom + k;
-        if (cmode != 2)
-          for (int j = part; j < L; j += kGParts) {
-            const int c = s_lmn[j];
-            const dfl v = df_mul(df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]), qz[(c >> 8) * kAtom]);
-            put_digits(t0, tile_bytes, j, k, valid ? fixed30(v) : 0);
-          }
-        if (part == kGParts - 1) {
-          // |s vscale| < 1: round(s vscale 2^30) exactly from FP64
-          int d[4];
-          digits4(__double2int_rn(s_val[k] * 1073741824.0), d);
+        for (int j = part; j < L; j += kGParts) {
+          const int c = s_lmn[j];
+          const dfl v = df_mul(df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]), qz[(c >> 8) * kAtom]);
+          put_digits(t0, tile_bytes, j, k, valid ? fixed30(v) : 0);
+        }
+      }
+      if (part == kGParts - 1) {
+        // |value * vscale| < 1: round(. 2^30) exactly from FP64
+        const int X = __double2int_rn(s_val[k] * 1073741824.0);
+        if (!kProj) {
+          put_digits(t0, tile_bytes, L, k, X);  // r: row L of the tiles
+        } else {
+          int d[4];  // s: integer digits, rows 0..3 of the s tile
+          digits4(X, d);
           uint8_t* stile = t0 + 4 * tile_bytes;
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(q, k)) = __float2bfloat16_rn((float)d[q]);
         }
-      } else {
-        const float* qx = legf + k;
-        const float* qy = legf + P1 * kAtom + k;
-        const float* qz = legf + 2 * P1 * kAtom + k;
-        for (int j = part; j < L; j += kGParts) {
-          const int c = s_lmn[j];
-          const float v = qx[(c & 15) * kAtom] * qy[((c >> 4) & 15) * kAtom] * qz[(c >> 8) * kAtom];
-          put3(t0, tile_bytes, j, k, valid ? v : 0.0f);
-        }
-        if (part == kGParts - 1) put3(t0, tile_bytes, L, k, (float)s_val[k]);
       }
       fence_async_smem();
       __syncthreads();
@@ -626,11 +585,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           tc_ld16(trow + 32u * q, vv);
           double part0 = 0.0, part1 = 0.0;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) part0 += ldexp((double)vv[c], digit_exp(q) + digit_exp(c));
+          for (int c = 0; c < 4; ++c) part0 += ldexp((double)vv[c], digit_exp(c));
           if (band1) {
             tc_ld16(trow + 32u * q + 16u, vv);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) part1 += ldexp((double)vv[c], digit_exp(q) + digit_exp(c));
+            for (int c = 0; c < 4; ++c) part1 += ldexp((double)vv[c], digit_exp(c));
           }
           s_red[q * 128 + trow_lane] = part0;
           s_red[512 + q * 128 + trow_lane] = part1;
@@ -1047,11 +1006,11 @@ cudaError_t launch_gram_t(const fmt_tree* t, int depth, const fmt_mixed_bufs& b,
   const fmt_level& L = t->lv[depth];
   if (L.n_items <= 0) return cudaSuccess;
   MArgs a = make_margs(t, depth, b);
-  a.cache_mode = kProj && b.cache ? cache_mode : 0;
+  a.cache_mode = b.cache ? cache_mode : 0;
   a.cache_atom_bytes = 4u * (uint32_t)a.MR * 128u;
   // projection: 4 digits x 2 bands x 16 columns; Gram: the two bands of the matrix
   a.tmem_cols = (int)pow2_cols(kProj ? 128 : gram_cols(mixed_m_cap(L.max_m)));
-  const size_t stage = (kProj ? 4 : 3) * (size_t)a.MR * 128 + (kProj ? 2048 : 0);
+  const size_t stage = 4 * (size_t)a.MR * 128 + (kProj ? 2048 : 0);
   const size_t fixed = 1024 + kLegBytes + 12 * 1024;  // alignment, Legendre table, static shared
   a.nstages = fixed + 2 * stage <= 227 * 1024 ? 2 : 1;
   const size_t smem = 1024 + kLegBytes + a.nstages * stage;
@@ -1089,7 +1048,8 @@ cudaError_t launch_mixed_box(const fmt_tree* t, int depth, const fmt_mixed_bufs&
 
 cudaError_t launch_mixed_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool projection,
                               int cache_mode, cudaStream_t s) {
-  return projection ? launch_gram_t<true>(t, depth, b, cache_mode, s) : launch_gram_t<false>(t, depth, b, 0, s);
+  return projection ? launch_gram_t<true>(t, depth, b, cache_mode, s)
+                    : launch_gram_t<false>(t, depth, b, cache_mode, s);
 }
 
 size_t mixed_cache_bytes(const fmt_tree* t, int depth) {
