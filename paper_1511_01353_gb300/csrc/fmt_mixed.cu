@@ -331,9 +331,25 @@ __device__ __forceinline__ void put_digits(uint8_t* t0, uint32_t tile_bytes, int
   for (int q = 0; q < 4; ++q)
     *reinterpret_cast<__nv_bfloat16*>(t0 + q * tile_bytes + o) = __float2bfloat16_rn((float)d[q] * digit_scale(q));
 }
-__device__ __forceinline__ int fixed30(dfl v) {
-  return __float2int_rn(__fmul_rn(v.h, 1073741824.0f)) + __float2int_rn(__fmul_rn(v.l, 1073741824.0f));
+// The same four digits, pre-scaled, from a double-float |v| <= 1 without
+// integer conversions: adding and subtracting 1.5 * 2^(23+e) rounds an FP32
+// value to a multiple of 2^e (round to nearest even), and every remainder is
+// exact; v.l enters below 2^-8, rounding at 2^-32.  d[q] = d_q 2^e_q.
+__device__ __forceinline__ void digits_of(dfl v, float (&d)[4]) {
+  d[0] = __fsub_rn(__fadd_rn(v.h, 0x1.8p16f), 0x1.8p16f);     // multiple of 2^-7
+  float r = __fadd_rn(__fsub_rn(v.h, d[0]), v.l);
+  d[1] = __fsub_rn(__fadd_rn(r, 0x1.8p8f), 0x1.8p8f);         // 2^-15
+  r = __fsub_rn(r, d[1]);
+  d[2] = __fsub_rn(__fadd_rn(r, 0x1.8p0f), 0x1.8p0f);         // 2^-23
+  r = __fsub_rn(r, d[2]);
+  d[3] = __fsub_rn(__fadd_rn(r, 0x1.8p-7f), 0x1.8p-7f);       // 2^-30
 }
+__device__ __forceinline__ void put_digits_f(uint8_t* t0, uint32_t tile_bytes, int j, int k, const float (&d)[4]) {
+  const uint32_t o = sw_off(j, k);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) *reinterpret_cast<__nv_bfloat16*>(t0 + q * tile_bytes + o) = __float2bfloat16_rn(d[q]);
+}
+
 // One 64-row atom of the operand tiles is generated in two phases: 192
 // threads evaluate the 1-D Legendre values P_0..P_p of the atom's rows (one
 // axis each) into shared memory; then every thread takes one row and every
@@ -491,13 +507,23 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       const bool valid = i0 + k < re;
       const int P1 = p + 1;
       if (cmode != 2) {
+        // a contiguous range of columns per part: P_l P_m is formed once per (l, m)
         const dfl* qx = legd + k;
         const dfl* qy = legd + P1 * kAtom + k;
         const dfl* qz = legd + 2 * P1 * kAtom + k;
-        for (int j = part; j < L; j += kGParts) {
+        const int per = (L + kGParts - 1) / kGParts;
+        const int jb = part * per, je = jb + per < L ? jb + per : L;
+        int plm_key = -1;
+        dfl plm = {0.0f, 0.0f};
+        for (int j = jb; j < je; ++j) {
           const int c = s_lmn[j];
-          const dfl v = df_mul(df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]), qz[(c >> 8) * kAtom]);
-          put_digits(t0, tile_bytes, j, k, valid ? fixed30(v) : 0);
+          if ((c & 255) != plm_key) {
+            plm_key = c & 255;
+            plm = df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]);
+          }
+          float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          if (valid) digits_of(df_mul(plm, qz[(c >> 8) * kAtom]), d);
+          put_digits_f(t0, tile_bytes, j, k, d);
         }
       }
       if (part == kGParts - 1) {
