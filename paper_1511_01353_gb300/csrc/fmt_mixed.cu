@@ -355,20 +355,100 @@ __device__ __forceinline__ void put_digits_f(uint8_t* t0, uint32_t tile_bytes, i
 // axis each) into shared memory; then every thread takes one row and every
 // eighth column j, forms P_l(t_x) P_m(t_y) P_n(t_z) for the (l, m, n) of j and
 // stores its BF16 terms / digits.
-constexpr int kGThreads = 512;            // k_mgram: 16 warps
-constexpr int kGParts = kGThreads / kAtom;
+constexpr int kGThreads = 512;                // 16 warps: 15 generate and drain, the last issues the MMAs
+constexpr int kGenThreads = kGThreads - 32;   // generator threads
+constexpr int kGParts = kGenThreads / kAtom;  // column groups of the products (threads 0..447)
 constexpr int kLegBytes = 3 * (FMT_MIXED_MAX_DEGREE + 1) * kAtom * 8;
 
+// One atom's tensor-core work, handed from the generators to the MMA warp.
+struct MmaJob {
+  uint32_t A0;  // shared address of the stage
+  int N0, Lp, band1, b1;
+  int acc;      // 0: the atom opens a drain window (its first MMA overwrites the accumulator)
+  int stop;
+};
+
+// barrier 1 among the generator warps only
+__device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kGenThreads) : "memory"); }
+__device__ __forceinline__ bool gen_bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kGenThreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The MMA warp: one job per atom, in order, until a stop job.
+template <bool kProj>
+__device__ void mma_loop(uint64_t* fbar, uint64_t* mbar, volatile MmaJob* job, int nst, uint32_t tmem,
+                         uint32_t tile_bytes, int* err) {
+  uint32_t nfull[2] = {0u, 0u};
+  int st = 0;
+  for (;;) {
+    if (!mbar_wait(&fbar[st], nfull[st] & 1u)) {
+      atomicOr(err, FMT_ERR_TIMEOUT);
+      return;
+    }
+    nfull[st] += 1u;
+    const uint32_t A0 = job[st].A0;
+    const int N0 = job[st].N0, Lp = job[st].Lp, b1 = job[st].b1, acc = job[st].acc;
+    const bool band1 = job[st].band1 != 0;
+    if (job[st].stop) return;
+    tc_fence_after();
+    if (!kProj) {
+      const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+      const uint32_t id0 = idesc_bf16(128, N0), id1 = band1 ? idesc_bf16(128, Lp - 128) : 0u;
+#pragma unroll
+      for (int pi = 0; pi < 6; ++pi)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t accf = (acc || pi > 0 || kk > 0) ? 1u : 0u;
+          const uint32_t A = A0 + pa[pi] * tile_bytes + 32u * kk, B = A0 + pb[pi] * tile_bytes + 32u * kk;
+          tc_mma(tmem, sdesc(A), sdesc(B), id0, accf);
+          if (band1) tc_mma(tmem + (uint32_t)N0, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(B + 16u * 1024u), id1, accf);
+        }
+    } else {
+      // digit tile q of the basis -> its own accumulators: columns [32 q, 32 q + 16) band 0, +16 band 1
+      const uint32_t S = A0 + 4u * tile_bytes;
+      const uint32_t id = idesc_bf16(128, 16);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t accf = (acc || kk > 0) ? 1u : 0u;
+          const uint32_t A = A0 + q * tile_bytes + 32u * kk;
+          tc_mma(tmem + 32u * q, sdesc(A), sdesc(S + 32u * kk), id, accf);
+          if (band1) tc_mma(tmem + 32u * q + 16u, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(S + 32u * kk), id, accf);
+        }
+    }
+    tc_commit(&mbar[st]);
+    st = (st + 1) % nst;
+  }
+}
+
+// Persistent over the level's work items (largest first).  Gram mode
+// (kProj = false): acc[item] += [B | sig r]^T [B | sig r], column-major by
+// TMEM column, 128 lanes each.  Projection mode: gacc[item] += B^T s,
+// band 0 rows in [0,128), band 1 rows in [128,256).  Warps 0..14 generate the
+// operand tiles of an atom into a free stage and hand it to warp 15, which
+// issues its MMAs and commits them to the stage's mbarrier; the generators
+// go on with the next atom meanwhile.
 template <bool kProj>
 __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
   extern __shared__ uint8_t dsm_raw[];
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ __align__(8) uint64_t lbar[2];
+  __shared__ __align__(8) uint64_t mbar[2];  // the MMAs of a stage are complete
+  __shared__ __align__(8) uint64_t fbar[2];  // a stage's job is ready for the MMA warp
+  __shared__ __align__(8) uint64_t lbar[2];  // a stage's cached tiles have landed
+  __shared__ MmaJob job[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_item, s_deg;
   __shared__ uint16_t s_lmn[(FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6];
   __shared__ double s_val[kAtom];
-  __shared__ double s_red[kProj ? 2 * 4 * 128 : 1];
   constexpr int kTiles = 4;  // the four digit tiles of the basis (Gram: plus the r row)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
@@ -379,272 +459,262 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
   dfl* legd = reinterpret_cast<dfl*>(dsm + total);  // [3][p+1][64] double-float Legendre values
   for (uint32_t o = 16u * tid; o < total; o += 16u * kGThreads) *reinterpret_cast<uint4*>(dsm + o) = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    mbar_init(&lbar[0], 1);
-    mbar_init(&lbar[1], 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&mbar[i], 1);
+      mbar_init(&fbar[i], 1);
+      mbar_init(&lbar[i], 1);
+    }
     fence_mbar_init();
     s_deg = -1;
   }
   const int cmode = a.cache_mode;  // Gram: 0 or 1 (store the tiles); projection: 0 or 2 (load them)
-  uint32_t nload[2] = {0u, 0u};
   if (warp == 0) tc_alloc(&tmem_slot, (uint32_t)a.tmem_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t sbase = smem_u32(dsm);
-  uint32_t ncommit[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  int hi[2] = {0, 0};  // rows of each stage that may hold non-zero values
-  int stage = 0;
-  bool ok = true;
-  const int k = tid & (kAtom - 1), part = tid / kAtom;
-  const int lg = warp & 3;                 // TMEM lane group of this warp
-  const int trow_lane = 32 * lg + lane;    // TMEM lane (matrix row) this thread drains
 
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(a.work, 1);
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
-    if (it >= a.n_items) break;
-    const int item = a.sched[it];
-    const int64_t node = a.item_node[item];
-    const fmt_problem& pr = a.prob[a.node_prob[node]];
-    if (kProj ? !(a.flags[node] & FMT_FLAG_MIXED) : !mixed_eligible(pr, a.depth)) continue;
-    const int p = pr.degree;
-    const int L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m);
-    const int nw = kProj ? L : m;
-    const int N0 = kProj ? 16 : Lp;
-    const bool band1 = Lp > 128;
-    const int b1 = Lp - 128;
-    if (p != s_deg) {  // (l, m, n) of every column, Alg. 2 order
-      for (int j = tid; j < L; j += kGThreads) {
-        int r = j, l = 0;
-        while (r >= (p - l + 1) * (p - l + 2) / 2) {
-          r -= (p - l + 1) * (p - l + 2) / 2;
-          ++l;
-        }
-        int mm = 0;
-        while (r >= p - l - mm + 1) {
-          r -= p - l - mm + 1;
-          ++mm;
-        }
-        s_lmn[j] = (uint16_t)(l | (mm << 4) | (r << 8));
-      }
-      __syncthreads();
-      if (tid == 0) s_deg = p;
-    }
-    const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
-    // projection: |s| scaled below 1 by a power of two (max |s| of the node, this sweep)
-    int se = 0;
-    if (kProj) {
-      const double ms = __longlong_as_double((long long)a.mstat[kMStat * node + 5]);
-      if (ms > 0.0) frexp(ms, &se);
-    }
-    const double vscale = kProj ? ldexp(1.0, -se) : F.sig;
-    const int64_t rs = a.item_start[item], re = a.item_end[item];
-    const int natoms = (int)((re - rs + kAtom - 1) / kAtom);
-    double* acc = kProj ? a.gacc + (int64_t)item * 256 : a.acc + (int64_t)item * a.acc_stride;
-    const double* val = kProj ? a.s : a.r;
-    bool first_drain = true;
-    double g0 = 0.0, g1 = 0.0;  // projection, threads < 128: FP64 sums of band 0 / band 1 at lane tid
-    int since = 0;
-    for (int at = 0; at < natoms && ok; ++at) {
-      const int st = stage;
-      if (pending[st]) {
-        ok = mbar_wait(&mbar[st], (ncommit[st] - 1u) & 1u);
-        pending[st] = false;
-      }
-      if (cmode == 1 && tid == 0) bulk_wait_read();  // the stage's previous store has read it
-      if (__syncthreads_or(!ok)) {
-        ok = false;
-        break;
-      }
-      uint8_t* t0 = dsm + st * stage_bytes;
-      const int64_t atom_idx = (int64_t)item + (rs >> 6) + at;  // items are disjoint, ascending row ranges
-      if (cmode == 2) {
-        // the basis digits come from the cache; only s is generated
-        if (tid == 0) bulk_load(t0, a.cache + atom_idx * a.cache_atom_bytes, a.cache_atom_bytes, &lbar[st]);
-        nload[st] += 1u;
-      }
-      // rows past this node's basis must read as zero
-      if (cmode != 2 && hi[st] > nw) {
-        const int nz = (hi[st] - nw) * 8;  // 16-byte words per tile
-        for (int e = tid; e < kTiles * nz; e += kGThreads) {
-          const int tt = e / nz, wi = e - tt * nz;
-          *reinterpret_cast<uint4*>(t0 + tt * tile_bytes + nw * 128 + wi * 16) = make_uint4(0, 0, 0, 0);
-        }
-      }
-      hi[st] = nw;
-      // phase A: 1-D Legendre values (threads 0..191) and the value column (192..255)
-      const int64_t i0 = rs + (int64_t)at * kAtom;
-      if (tid < 3 * kAtom && cmode != 2) {
-        const int ax = tid / kAtom;
-        const int64_t i = i0 + k;
-        const double* X = ax == 0 ? a.x : ax == 1 ? a.y : a.z;
-        const double t = i < re ? fmt_local(X[i], F.c[ax], F.s[ax]) * F.ex[ax] : 0.0;
-        dfl* q = legd + ax * (p + 1) * kAtom + k;
-        const dfl td = df_of(t);
-        dfl qm = {1.0f, 0.0f}, q0 = td;
-        q[0] = qm;
-        if (p >= 1) q[kAtom] = q0;
-        for (int kk = 1; kk < p; ++kk) {
-          const double ad = (double)(2 * kk + 1) / (double)(kk + 1), bd = (double)kk / (double)(kk + 1);
-          const dfl ca = {(float)ad, (float)(ad - (double)(float)ad)}, cb = {(float)bd, (float)(bd - (double)(float)bd)};
-          const dfl qn = df_sub(df_mul(ca, df_mul(td, q0)), df_mul(cb, qm));
-          q[(kk + 1) * kAtom] = qn;
-          qm = q0;
-          q0 = qn;
-        }
-      } else if (tid >= 3 * kAtom && tid < 4 * kAtom) {
-        const int64_t i = i0 + k;
-        s_val[k] = i < re ? val[i] * vscale : 0.0;
-      }
-      __syncthreads();
-      // phase B: products, every kGParts-th column, as pre-scaled digits
-      const bool valid = i0 + k < re;
-      const int P1 = p + 1;
-      if (cmode != 2) {
-        // a contiguous range of columns per part: P_l P_m is formed once per (l, m)
-        const dfl* qx = legd + k;
-        const dfl* qy = legd + P1 * kAtom + k;
-        const dfl* qz = legd + 2 * P1 * kAtom + k;
-        const int per = (L + kGParts - 1) / kGParts;
-        const int jb = part * per, je = jb + per < L ? jb + per : L;
-        int plm_key = -1;
-        dfl plm = {0.0f, 0.0f};
-        for (int j = jb; j < je; ++j) {
-          const int c = s_lmn[j];
-          if ((c & 255) != plm_key) {
-            plm_key = c & 255;
-            plm = df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]);
+  if (warp == kGThreads / 32 - 1) {
+    if (lane == 0) mma_loop<kProj>(fbar, mbar, job, nst, tmem, tile_bytes, a.err);
+    __syncwarp();
+  } else {
+    uint32_t ncommit[2] = {0u, 0u}, nload[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    int hi[2] = {0, 0};  // rows of each stage that may hold non-zero values
+    int stage = 0;
+    bool ok = true;
+    const int k = tid & (kAtom - 1), part = tid / kAtom;
+    const int lg = warp & 3;               // TMEM lane group of this warp
+    const int trow_lane = 32 * lg + lane;  // TMEM lane (matrix row) this thread drains
+
+    for (;;) {
+      if (tid == 0) s_item = atomicAdd(a.work, 1);
+      gen_bar();
+      const int it = s_item;
+      gen_bar();
+      if (it >= a.n_items) break;
+      const int item = a.sched[it];
+      const int64_t node = a.item_node[item];
+      const fmt_problem& pr = a.prob[a.node_prob[node]];
+      if (kProj ? !(a.flags[node] & FMT_FLAG_MIXED) : !mixed_eligible(pr, a.depth)) continue;
+      const int p = pr.degree;
+      const int L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m);
+      const int nw = kProj ? L : m;
+      const int N0 = kProj ? 16 : Lp;
+      const bool band1 = Lp > 128;
+      const int b1 = Lp - 128;
+      if (p != s_deg) {  // (l, m, n) of every column, Alg. 2 order
+        for (int j = tid; j < L; j += kGenThreads) {
+          int r = j, l = 0;
+          while (r >= (p - l + 1) * (p - l + 2) / 2) {
+            r -= (p - l + 1) * (p - l + 2) / 2;
+            ++l;
           }
-          float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          if (valid) digits_of(df_mul(plm, qz[(c >> 8) * kAtom]), d);
-          put_digits_f(t0, tile_bytes, j, k, d);
-        }
-      }
-      if (part == kGParts - 1) {
-        // |value * vscale| < 1: round(. 2^30) exactly from FP64
-        const int X = __double2int_rn(s_val[k] * 1073741824.0);
-        if (!kProj) {
-          put_digits(t0, tile_bytes, L, k, X);  // r: row L of the tiles
-        } else {
-          int d[4];  // s: integer digits, rows 0..3 of the s tile
-          digits4(X, d);
-          uint8_t* stile = t0 + 4 * tile_bytes;
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(q, k)) = __float2bfloat16_rn((float)d[q]);
-        }
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        if (cmode == 2 && !mbar_wait(&lbar[st], (nload[st] - 1u) & 1u)) ok = false;
-        tc_fence_after();
-        const uint32_t A0 = sbase + (uint32_t)st * stage_bytes;
-        if (!kProj) {
-          const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
-          const uint32_t id0 = idesc_bf16(128, N0), id1 = band1 ? idesc_bf16(128, Lp - 128) : 0u;
-#pragma unroll
-          for (int pi = 0; pi < 6; ++pi)
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t accf = (since > 0 || pi > 0 || kk > 0) ? 1u : 0u;
-              const uint32_t A = A0 + pa[pi] * tile_bytes + 32u * kk, B = A0 + pb[pi] * tile_bytes + 32u * kk;
-              tc_mma(tmem, sdesc(A), sdesc(B), id0, accf);
-              if (band1) tc_mma(tmem + (uint32_t)N0, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(B + 16u * 1024u), id1, accf);
-            }
-        } else {
-          // digit q of the basis -> its own accumulators: columns [32 q, 32 q + 16) band 0, +16 band 1
-          const uint32_t S = A0 + 4u * tile_bytes;
-          const uint32_t id = idesc_bf16(128, 16);
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t accf = (since > 0 || kk > 0) ? 1u : 0u;
-              const uint32_t A = A0 + q * tile_bytes + 32u * kk;
-              tc_mma(tmem + 32u * q, sdesc(A), sdesc(S + 32u * kk), id, accf);
-              if (band1) tc_mma(tmem + 32u * q + 16u, sdesc(A + (uint32_t)(b1 >> 3) * 1024u), sdesc(S + 32u * kk), id, accf);
-            }
-        }
-        tc_commit(&mbar[st]);
-        if (cmode == 1) bulk_store(a.cache + atom_idx * a.cache_atom_bytes, t0, a.cache_atom_bytes);
-      }
-      ncommit[st] += 1u;
-      pending[st] = true;
-      stage = (stage + 1) % nst;
-      ++since;
-      if (since == kDrainAtoms || at == natoms - 1) {
-        for (int s2 = 0; s2 < 2; ++s2)
-          if (pending[s2]) {
-            ok = mbar_wait(&mbar[s2], (ncommit[s2] - 1u) & 1u) && ok;
-            pending[s2] = false;
+          int mm = 0;
+          while (r >= p - l - mm + 1) {
+            r -= p - l - mm + 1;
+            ++mm;
           }
-        if (__syncthreads_or(!ok)) {
+          s_lmn[j] = (uint16_t)(l | (mm << 4) | (r << 8));
+        }
+        gen_bar();
+        if (tid == 0) s_deg = p;
+      }
+      const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
+      // projection: |s| scaled below 1 by a power of two (max |s| of the node, this sweep)
+      int se = 0;
+      if (kProj) {
+        const double ms = __longlong_as_double((long long)a.mstat[kMStat * node + 5]);
+        if (ms > 0.0) frexp(ms, &se);
+      }
+      const double vscale = kProj ? ldexp(1.0, -se) : F.sig;
+      const int64_t rs = a.item_start[item], re = a.item_end[item];
+      const int natoms = (int)((re - rs + kAtom - 1) / kAtom);
+      double* acc = kProj ? a.gacc + (int64_t)item * 256 : a.acc + (int64_t)item * a.acc_stride;
+      const double* val = kProj ? a.s : a.r;
+      bool first_drain = true;
+      double g0 = 0.0, g1 = 0.0;  // projection, threads < 128: FP64 sums of band 0 / band 1 at lane tid
+      int since = 0;
+      for (int at = 0; at < natoms && ok; ++at) {
+        const int st = stage;
+        if (pending[st]) {
+          ok = mbar_wait(&mbar[st], (ncommit[st] - 1u) & 1u);
+          pending[st] = false;
+        }
+        if (cmode == 1 && tid == 0) bulk_wait_read();  // the stage's previous store has read it
+        if (gen_bar_or(!ok)) {
           ok = false;
           break;
         }
-        tc_fence_after();
-        const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16);
-        if (!kProj) {
-          // the four warps of a lane group take every fourth 16-column chunk
-          const int ncols = band1 ? N0 + (Lp - 128) : N0;
-          for (int c0 = 16 * (warp >> 2); c0 < ncols; c0 += 64) {
-            float vv[16];
-            tc_ld16(trow + (uint32_t)c0, vv);
-            double* dst = acc + (int64_t)c0 * 128 + trow_lane;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const double d = (double)vv[q];
-              dst[q * 128] = first_drain ? d : dst[q * 128] + d;
-            }
-          }
-        } else {
-          // warp (digit q, lane group): exact integer sums per digit pair (q, c), weighted in FP64
-          const int q = warp >> 2;
-          float vv[16];
-          tc_ld16(trow + 32u * q, vv);
-          double part0 = 0.0, part1 = 0.0;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) part0 += ldexp((double)vv[c], digit_exp(c));
-          if (band1) {
-            tc_ld16(trow + 32u * q + 16u, vv);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) part1 += ldexp((double)vv[c], digit_exp(c));
-          }
-          s_red[q * 128 + trow_lane] = part0;
-          s_red[512 + q * 128 + trow_lane] = part1;
-          __syncthreads();
-          if (tid < 128) {
-            g0 += (s_red[tid] + s_red[128 + tid]) + (s_red[256 + tid] + s_red[384 + tid]);
-            g1 += (s_red[512 + tid] + s_red[640 + tid]) + (s_red[768 + tid] + s_red[896 + tid]);
+        uint8_t* t0 = dsm + st * stage_bytes;
+        const int64_t atom_idx = (int64_t)item + (rs >> 6) + at;  // items are disjoint, ascending row ranges
+        if (cmode == 2) {
+          // the basis digits come from the cache; only s is generated
+          if (tid == 0) bulk_load(t0, a.cache + atom_idx * a.cache_atom_bytes, a.cache_atom_bytes, &lbar[st]);
+          nload[st] += 1u;
+        }
+        // rows past this node's basis must read as zero
+        if (cmode != 2 && hi[st] > nw) {
+          const int nz = (hi[st] - nw) * 8;  // 16-byte words per tile
+          for (int e = tid; e < kTiles * nz; e += kGenThreads) {
+            const int tt = e / nz, wi = e - tt * nz;
+            *reinterpret_cast<uint4*>(t0 + tt * tile_bytes + nw * 128 + wi * 16) = make_uint4(0, 0, 0, 0);
           }
         }
-        first_drain = false;
-        since = 0;
-        tc_fence_before();
-        __syncthreads();
+        hi[st] = nw;
+        // phase A: 1-D Legendre values (threads 0..191) and the value column (192..255)
+        const int64_t i0 = rs + (int64_t)at * kAtom;
+        if (tid < 3 * kAtom && cmode != 2) {
+          const int ax = tid / kAtom;
+          const int64_t i = i0 + k;
+          const double* X = ax == 0 ? a.x : ax == 1 ? a.y : a.z;
+          const double t = i < re ? fmt_local(X[i], F.c[ax], F.s[ax]) * F.ex[ax] : 0.0;
+          dfl* q = legd + ax * (p + 1) * kAtom + k;
+          const dfl td = df_of(t);
+          dfl qm = {1.0f, 0.0f}, q0 = td;
+          q[0] = qm;
+          if (p >= 1) q[kAtom] = q0;
+          for (int kk = 1; kk < p; ++kk) {
+            const double ad = (double)(2 * kk + 1) / (double)(kk + 1), bd = (double)kk / (double)(kk + 1);
+            const dfl ca = {(float)ad, (float)(ad - (double)(float)ad)}, cb = {(float)bd, (float)(bd - (double)(float)bd)};
+            const dfl qn = df_sub(df_mul(ca, df_mul(td, q0)), df_mul(cb, qm));
+            q[(kk + 1) * kAtom] = qn;
+            qm = q0;
+            q0 = qn;
+          }
+        } else if (tid >= 3 * kAtom && tid < 4 * kAtom) {
+          const int64_t i = i0 + k;
+          s_val[k] = i < re ? val[i] * vscale : 0.0;
+        }
+        gen_bar();
+        // phase B: products as pre-scaled digits, a contiguous range of columns per part
+        const bool valid = i0 + k < re;
+        const int P1 = p + 1;
+        if (cmode != 2 && part < kGParts) {
+          const dfl* qx = legd + k;
+          const dfl* qy = legd + P1 * kAtom + k;
+          const dfl* qz = legd + 2 * P1 * kAtom + k;
+          const int per = (L + kGParts - 1) / kGParts;
+          const int jb = part * per, je = jb + per < L ? jb + per : L;
+          int plm_key = -1;
+          dfl plm = {0.0f, 0.0f};
+          for (int j = jb; j < je; ++j) {
+            const int c = s_lmn[j];
+            if ((c & 255) != plm_key) {
+              plm_key = c & 255;
+              plm = df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]);
+            }
+            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (valid) digits_of(df_mul(plm, qz[(c >> 8) * kAtom]), d);
+            put_digits_f(t0, tile_bytes, j, k, d);
+          }
+        }
+        if (part == kGParts - 1) {
+          // |value * vscale| < 1: round(. 2^30) exactly from FP64
+          const int X = __double2int_rn(s_val[k] * 1073741824.0);
+          if (!kProj) {
+            put_digits(t0, tile_bytes, L, k, X);  // r: row L of the tiles
+          } else {
+            int d[4];  // s: integer digits, rows 0..3 of the s tile
+            digits4(X, d);
+            uint8_t* stile = t0 + 4 * tile_bytes;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(q, k)) = __float2bfloat16_rn((float)d[q]);
+          }
+        }
+        fence_async_smem();
+        if (cmode == 2 && tid == 0 && !mbar_wait(&lbar[st], (nload[st] - 1u) & 1u)) ok = false;
+        gen_bar();
+        if (tid == 0) {
+          job[st].A0 = sbase + (uint32_t)st * stage_bytes;
+          job[st].N0 = N0;
+          job[st].Lp = Lp;
+          job[st].band1 = band1 ? 1 : 0;
+          job[st].b1 = b1;
+          job[st].acc = since > 0 ? 1 : 0;
+          job[st].stop = 0;
+          mbar_arrive(&fbar[st]);
+          if (cmode == 1) bulk_store(a.cache + atom_idx * a.cache_atom_bytes, t0, a.cache_atom_bytes);
+        }
+        ncommit[st] += 1u;
+        pending[st] = true;
+        stage = (stage + 1) % nst;
+        ++since;
+        if (since == kDrainAtoms || at == natoms - 1) {
+          for (int s2 = 0; s2 < 2; ++s2)
+            if (pending[s2]) {
+              ok = mbar_wait(&mbar[s2], (ncommit[s2] - 1u) & 1u) && ok;
+              pending[s2] = false;
+            }
+          if (gen_bar_or(!ok)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16);
+          if (!kProj) {
+            // warps 0..11: three per lane group, every third 16-column chunk
+            if (warp < 12) {
+              const int ncols = band1 ? N0 + (Lp - 128) : N0;
+              for (int c0 = 16 * (warp >> 2); c0 < ncols; c0 += 48) {
+                float vv[16];
+                tc_ld16(trow + (uint32_t)c0, vv);
+                double* dst = acc + (int64_t)c0 * 128 + trow_lane;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                  const double d = (double)vv[q];
+                  dst[q * 128] = first_drain ? d : dst[q * 128] + d;
+                }
+              }
+            }
+          } else if (warp < 4) {
+            // exact integer sums per (basis tile, s digit), weighted in FP64
+            double part0 = 0.0, part1 = 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              float vv[16];
+              tc_ld16(trow + 32u * q, vv);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) part0 += ldexp((double)vv[c], digit_exp(c));
+              if (band1) {
+                tc_ld16(trow + 32u * q + 16u, vv);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) part1 += ldexp((double)vv[c], digit_exp(c));
+              }
+            }
+            g0 += part0;  // warp w < 4 drains lanes 32w.., i.e. thread tid = trow_lane
+            g1 += part1;
+          }
+          first_drain = false;
+          since = 0;
+          tc_fence_before();
+          gen_bar();
+        }
+      }
+      if (!ok) break;
+      if (kProj && tid < 128) {
+        // B^T s of this item: undo the scale of s
+        acc[tid] = ldexp(g0, se);
+        if (band1) acc[128 + tid] = ldexp(g1, se);
       }
     }
-    if (!ok) break;
-    if (kProj && tid < 128) {
-      // B^T s of this item: undo the scale of s
-      acc[tid] = ldexp(g0, se);
-      if (band1) acc[128 + tid] = ldexp(g1, se);
+    // stop the MMA warp (after the job last handed over on that stage is done)
+    const int st = stage;
+    if (pending[st]) mbar_wait(&mbar[st], (ncommit[st] - 1u) & 1u);
+    for (int s2 = 0; s2 < 2; ++s2)
+      if (pending[s2]) {
+        ok = mbar_wait(&mbar[s2], (ncommit[s2] - 1u) & 1u) && ok;
+        pending[s2] = false;
+      }
+    if (tid == 0) {
+      if (!ok) atomicOr(a.err, FMT_ERR_TIMEOUT);
+      job[st].stop = 1;
+      mbar_arrive(&fbar[st]);
+      if (cmode == 1) bulk_wait_all();
     }
   }
-  if (!ok) {
-    if (tid == 0) atomicOr(a.err, FMT_ERR_TIMEOUT);
-    // give MMAs still in flight a bounded time before the memory is released
-    for (int s2 = 0; s2 < 2; ++s2)
-      if (pending[s2]) mbar_wait(&mbar[s2], (ncommit[s2] - 1u) & 1u);
-  }
-  if (cmode == 1 && tid == 0) bulk_wait_all();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
