@@ -319,19 +319,11 @@ __host__ __device__ constexpr int digit_exp(int q) { return q == 0 ? -7 : q == 1
 __host__ __device__ constexpr float digit_scale(int q) {
   return q == 0 ? 0x1p-7f : q == 1 ? 0x1p-15f : q == 2 ? 0x1p-23f : 0x1p-30f;
 }
-// The four digits of X = round(v 2^30) stored pre-scaled, d_q 2^e_q (exact
-// in BF16), one per tile: the tiles sum to v (to 2^-31), so products of
-// tiles carry their weights, and a tile times the integer digits of s sums
-// exactly in FP32 over 256 rows (|d| <= 128).
-__device__ __forceinline__ void put_digits(uint8_t* t0, uint32_t tile_bytes, int j, int k, int X) {
-  int d[4];
-  digits4(X, d);
-  const uint32_t o = sw_off(j, k);
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    *reinterpret_cast<__nv_bfloat16*>(t0 + q * tile_bytes + o) = __float2bfloat16_rn((float)d[q] * digit_scale(q));
-}
-// The same four digits, pre-scaled, from a double-float |v| <= 1 without
+// The basis tiles hold the four digits of round(v 2^30) pre-scaled, d_q 2^e_q
+// (exact in BF16), one per tile: the tiles sum to v (to 2^-31), so products
+// of tiles carry their weights, and a tile times the integer digits of s
+// sums exactly in FP32 over 256 rows (|d| <= 128).
+// digits_of: those four digits, pre-scaled, from a double-float |v| <= 1 without
 // integer conversions: adding and subtracting 1.5 * 2^(23+e) rounds an FP32
 // value to a multiple of 2^e (round to nearest even), and every remainder is
 // exact; v.l enters below 2^-8, rounding at 2^-32.  d[q] = d_q 2^e_q.
@@ -344,10 +336,13 @@ __device__ __forceinline__ void digits_of(dfl v, float (&d)[4]) {
   r = __fsub_rn(r, d[2]);
   d[3] = __fsub_rn(__fadd_rn(r, 0x1.8p-7f), 0x1.8p-7f);       // 2^-30
 }
-__device__ __forceinline__ void put_digits_f(uint8_t* t0, uint32_t tile_bytes, int j, int k, const float (&d)[4]) {
+// digits of the points k (even) and k+1 of row j: one 32-bit store per tile
+__device__ __forceinline__ void put_digits_f2(uint8_t* t0, uint32_t tile_bytes, int j, int k, const float (&da)[4],
+                                              const float (&db)[4]) {
   const uint32_t o = sw_off(j, k);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) *reinterpret_cast<__nv_bfloat16*>(t0 + q * tile_bytes + o) = __float2bfloat16_rn(d[q]);
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<__nv_bfloat162*>(t0 + q * tile_bytes + o) = __floats2bfloat162_rn(da[q], db[q]);
 }
 
 // One 64-row atom of the operand tiles is generated in two phases: 192
@@ -357,7 +352,6 @@ __device__ __forceinline__ void put_digits_f(uint8_t* t0, uint32_t tile_bytes, i
 // stores its BF16 terms / digits.
 constexpr int kGThreads = 512;                // 16 warps: 15 generate and drain, the last issues the MMAs
 constexpr int kGenThreads = kGThreads - 32;   // generator threads
-constexpr int kGParts = kGenThreads / kAtom;  // column groups of the products (threads 0..447)
 constexpr int kLegBytes = 3 * (FMT_MIXED_MAX_DEGREE + 1) * kAtom * 8;
 
 // One atom's tensor-core work, handed from the generators to the MMA warp.
@@ -484,7 +478,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
     int hi[2] = {0, 0};  // rows of each stage that may hold non-zero values
     int stage = 0;
     bool ok = true;
-    const int k = tid & (kAtom - 1), part = tid / kAtom;
+    const int k = tid & (kAtom - 1);
     const int lg = warp & 3;               // TMEM lane group of this warp
     const int trow_lane = 32 * lg + lane;  // TMEM lane (matrix row) this thread drains
 
@@ -588,40 +582,60 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           s_val[k] = i < re ? val[i] * vscale : 0.0;
         }
         gen_bar();
-        // phase B: products as pre-scaled digits, a contiguous range of columns per part
-        const bool valid = i0 + k < re;
+        // phase B: products as pre-scaled digits; generator warp w takes a
+        // contiguous range of columns, lane l the points 2l and 2l+1
         const int P1 = p + 1;
-        if (cmode != 2 && part < kGParts) {
-          const dfl* qx = legd + k;
-          const dfl* qy = legd + P1 * kAtom + k;
-          const dfl* qz = legd + 2 * P1 * kAtom + k;
-          const int per = (L + kGParts - 1) / kGParts;
-          const int jb = part * per, je = jb + per < L ? jb + per : L;
+        const int kp = 2 * lane;
+        const bool va = i0 + kp < re, vb = i0 + kp + 1 < re;
+        if (cmode != 2) {
+          const float4* qx = reinterpret_cast<const float4*>(legd + kp);
+          const float4* qy = reinterpret_cast<const float4*>(legd + P1 * kAtom + kp);
+          const float4* qz = reinterpret_cast<const float4*>(legd + 2 * P1 * kAtom + kp);
+          constexpr int kWarps = kGenThreads / 32;
+          const int per = (L + kWarps - 1) / kWarps;
+          const int jb = warp * per, je = jb + per < L ? jb + per : L;
           int plm_key = -1;
-          dfl plm = {0.0f, 0.0f};
+          dfl pa = {0.0f, 0.0f}, pb = {0.0f, 0.0f};
           for (int j = jb; j < je; ++j) {
             const int c = s_lmn[j];
             if ((c & 255) != plm_key) {
               plm_key = c & 255;
-              plm = df_mul(qx[(c & 15) * kAtom], qy[((c >> 4) & 15) * kAtom]);
+              const float4 x = qx[(c & 15) * (kAtom / 2)], y = qy[((c >> 4) & 15) * (kAtom / 2)];
+              pa = df_mul(dfl{x.x, x.y}, dfl{y.x, y.y});
+              pb = df_mul(dfl{x.z, x.w}, dfl{y.z, y.w});
             }
-            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            if (valid) digits_of(df_mul(plm, qz[(c >> 8) * kAtom]), d);
-            put_digits_f(t0, tile_bytes, j, k, d);
+            const float4 z = qz[(c >> 8) * (kAtom / 2)];
+            float da[4] = {0.0f, 0.0f, 0.0f, 0.0f}, db[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (va) digits_of(df_mul(pa, dfl{z.x, z.y}), da);
+            if (vb) digits_of(df_mul(pb, dfl{z.z, z.w}), db);
+            put_digits_f2(t0, tile_bytes, j, kp, da, db);
           }
         }
-        if (part == kGParts - 1) {
+        if (warp == kGenThreads / 32 - 1 || (cmode == 2 && warp == 0)) {
           // |value * vscale| < 1: round(. 2^30) exactly from FP64
-          const int X = __double2int_rn(s_val[k] * 1073741824.0);
+          const int Xa = __double2int_rn(s_val[kp] * 1073741824.0), Xb = __double2int_rn(s_val[kp + 1] * 1073741824.0);
           if (!kProj) {
-            put_digits(t0, tile_bytes, L, k, X);  // r: row L of the tiles
-          } else {
-            int d[4];  // s: integer digits, rows 0..3 of the s tile
-            digits4(X, d);
+            if (warp == kGenThreads / 32 - 1) {  // r: row L of the tiles
+              int ia[4], ib[4];
+              digits4(Xa, ia);
+              digits4(Xb, ib);
+              float da[4], db[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                da[q] = (float)ia[q] * digit_scale(q);
+                db[q] = (float)ib[q] * digit_scale(q);
+              }
+              put_digits_f2(t0, tile_bytes, L, kp, da, db);
+            }
+          } else if (cmode == 2 ? warp == 0 : warp == kGenThreads / 32 - 1) {
+            int ia[4], ib[4];  // s: integer digits, rows 0..3 of the s tile
+            digits4(Xa, ia);
+            digits4(Xb, ib);
             uint8_t* stile = t0 + 4 * tile_bytes;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<__nv_bfloat16*>(stile + sw_off(q, k)) = __float2bfloat16_rn((float)d[q]);
+              *reinterpret_cast<__nv_bfloat162*>(stile + sw_off(q, kp)) =
+                  __floats2bfloat162_rn((float)ia[q], (float)ib[q]);
           }
         }
         fence_async_smem();
