@@ -14,7 +14,8 @@
 //     cores (tcgen05.mma kind::f16): the basis (in double-float) and r are
 //     cut into four fixed-point digits stored as BF16 tiles; the six leading
 //     digit-tile products are accumulated in FP32 in tensor memory, and every
-//     256 rows the accumulator is added into an FP64 copy in global memory.
+//     256 rows the accumulator is added into a double-float (FP32 pair) copy
+//     in global memory; k_mreduce sums a node's items in FP64.
 //     The digit tiles are also stored in HBM (TMA bulk stores) for the sweeps.
 //  3. k_mfactor: per node, the item Grams are summed in FP64 and factorised by
 //     Cholesky; the factor is R-hat = [[R, Q^T r], [0, rho]] of the FP64 path
@@ -315,7 +316,6 @@ __device__ __forceinline__ void digits4(int X, int (&d)[4]) {
   d[2] = (X + (1 << 6)) >> 7;
   d[3] = X - d[2] * (1 << 7);
 }
-__host__ __device__ constexpr int digit_exp(int q) { return q == 0 ? -7 : q == 1 ? -15 : q == 2 ? -23 : -30; }
 __host__ __device__ constexpr float digit_scale(int q) {
   return q == 0 ? 0x1p-7f : q == 1 ? 0x1p-15f : q == 2 ? 0x1p-23f : 0x1p-30f;
 }
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       double* acc = kProj ? a.gacc + (int64_t)item * 256 : a.acc + (int64_t)item * a.acc_stride;
       const double* val = kProj ? a.s : a.r;
       bool first_drain = true;
-      double g0 = 0.0, g1 = 0.0;  // projection, threads < 128: FP64 sums of band 0 / band 1 at lane tid
+      dfl g0 = {0.0f, 0.0f}, g1 = {0.0f, 0.0f};  // projection, threads < 128: sums of band 0 / 1 at lane tid
       int since = 0;
       for (int at = 0; at < natoms && ok; ++at) {
         const int st = stage;
@@ -671,35 +671,41 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           if (!kProj) {
             // warps 0..11: three per lane group, every third 16-column chunk
             if (warp < 12) {
+              // double-float running sums on the FP32 pipe (k_mreduce turns them into FP64)
               const int ncols = band1 ? N0 + (Lp - 128) : N0;
+              float2* acc2 = reinterpret_cast<float2*>(acc);
               for (int c0 = 16 * (warp >> 2); c0 < ncols; c0 += 48) {
                 float vv[16];
                 tc_ld16(trow + (uint32_t)c0, vv);
-                double* dst = acc + (int64_t)c0 * 128 + trow_lane;
+                float2* dst = acc2 + (int64_t)c0 * 128 + trow_lane;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                  const double d = (double)vv[q];
-                  dst[q * 128] = first_drain ? d : dst[q * 128] + d;
+                  if (first_drain) {
+                    dst[q * 128] = make_float2(vv[q], 0.0f);
+                  } else {
+                    const float2 o = dst[q * 128];
+                    const dfl r = df_add(dfl{o.x, o.y}, dfl{vv[q], 0.0f});
+                    dst[q * 128] = make_float2(r.h, r.l);
+                  }
                 }
               }
             }
           } else if (warp < 4) {
             // exact integer sums per (basis tile, s digit), weighted in FP64
-            double part0 = 0.0, part1 = 0.0;
+            // each term (an FP32 integer sum times 2^e_c) is exact in FP32; the
+            // running sums are double-float (warp w < 4 drains lanes 32w.., thread tid = lane)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               float vv[16];
               tc_ld16(trow + 32u * q, vv);
 #pragma unroll
-              for (int c = 0; c < 4; ++c) part0 += ldexp((double)vv[c], digit_exp(c));
+              for (int c = 0; c < 4; ++c) g0 = df_add(g0, dfl{vv[c] * digit_scale(c), 0.0f});
               if (band1) {
                 tc_ld16(trow + 32u * q + 16u, vv);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) part1 += ldexp((double)vv[c], digit_exp(c));
+                for (int c = 0; c < 4; ++c) g1 = df_add(g1, dfl{vv[c] * digit_scale(c), 0.0f});
               }
             }
-            g0 += part0;  // warp w < 4 drains lanes 32w.., i.e. thread tid = trow_lane
-            g1 += part1;
           }
           first_drain = false;
           since = 0;
@@ -710,8 +716,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       if (!ok) break;
       if (kProj && tid < 128) {
         // B^T s of this item: undo the scale of s
-        acc[tid] = ldexp(g0, se);
-        if (band1) acc[128 + tid] = ldexp(g1, se);
+        acc[tid] = ldexp((double)g0.h + (double)g0.l, se);
+        if (band1) acc[128 + tid] = ldexp((double)g1.h + (double)g1.l, se);
       }
     }
     // stop the MMA warp (after the job last handed over on that stage is done)
@@ -806,26 +812,28 @@ __host__ __device__ __forceinline__ int64_t ro_of(int i, int m) { return (int64_
 __host__ __device__ __forceinline__ int conv_ws_doubles(int p) { return 4 * (p + 1) * (p + 1) + 2; }
 
 // ------------------------------------------------------------------ k_mreduce
-// Sums the FP64 Gram accumulators of a node's work items into its first
-// item's accumulator (fixed item order: deterministic).  Grid: nodes x chunks
-// of kRedChunk accumulator words, so a root split into hundreds of items is
-// reduced by many SMs.
+// Sums the Gram accumulators of a node's work items ((hi, lo) FP32 pairs)
+// in FP64 into its first item's accumulator (fixed item order:
+// deterministic).  Grid: nodes x chunks of kRedChunk accumulator words, so a
+// root split into hundreds of items is reduced by many SMs.
 constexpr int kRedChunk = 256;
 __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
   const int64_t node = blockIdx.x / chunks;
   const int ch = blockIdx.x - (int)(node * chunks);
   const int ni = a.node_nitems[node];
-  if (ni <= 1) return;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   if (!mixed_eligible(pr, a.depth)) return;
   const int64_t words = (int64_t)gram_cols(fmt_nmono_d(pr.degree) + 1) * 128;
   const int64_t i0 = a.node_item0[node];
-  double* dst = a.acc + i0 * a.acc_stride;
+  // the Gram kernel leaves (hi, lo) FP32 pairs; the node's sum goes to its first item as FP64
   for (int64_t e = (int64_t)ch * kRedChunk + threadIdx.x; e < words && e < (int64_t)(ch + 1) * kRedChunk;
        e += blockDim.x) {
-    double sum = dst[e];
-    for (int t = 1; t < ni; ++t) sum += a.acc[(i0 + t) * a.acc_stride + e];
-    dst[e] = sum;
+    double sum = 0.0;
+    for (int t = 0; t < ni; ++t) {
+      const float2 v = reinterpret_cast<const float2*>(a.acc + (i0 + t) * a.acc_stride)[e];
+      sum += (double)v.x + (double)v.y;
+    }
+    a.acc[i0 * a.acc_stride + e] = sum;
   }
 }
 
@@ -1176,7 +1184,7 @@ size_t mixed_factor_smem(int max_m) {
 cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
   const fmt_level& L = t->lv[depth];
   if (L.n_nodes <= 0) return cudaSuccess;
-  if (L.max_chunks > 1) {
+  {
     const int chunks = (int)((mixed_acc_stride(L.max_m) + kRedChunk - 1) / kRedChunk);
     k_mreduce<<<(unsigned)(L.n_nodes * chunks), 256, 0, s>>>(make_margs(t, depth, b), chunks);
     cudaError_t e = cudaGetLastError();
