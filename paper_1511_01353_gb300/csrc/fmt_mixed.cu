@@ -185,6 +185,20 @@ __device__ __forceinline__ uint32_t sw_off(int j, int k) {
   return (uint32_t)((j >> 3) * 1024 + (j & 7) * 128 + ((((k >> 3) ^ j) & 7) << 4) + ((k & 7) << 1));
 }
 
+// Bonnet's recurrence P_{k+1} = a_k t P_k - b_k P_{k-1}, a_k = (2k+1)/(k+1),
+// b_k = k/(k+1): the constants as double-float pairs (hi, lo), k = 1..13.
+#define FMT_LA(k) ((double)(2 * (k) + 1) / (double)((k) + 1))
+#define FMT_LB(k) ((double)(k) / (double)((k) + 1))
+#define FMT_DF(v) {(float)(v), (float)((v) - (double)(float)(v))}
+#define FMT_LEG(k) {FMT_DF(FMT_LA(k)), FMT_DF(FMT_LB(k))}
+static __constant__ float c_leg_ab[FMT_MAX_DEGREE][2][2] = {
+    {{0.0f, 0.0f}, {0.0f, 0.0f}}, FMT_LEG(1), FMT_LEG(2),  FMT_LEG(3),  FMT_LEG(4),  FMT_LEG(5),  FMT_LEG(6),
+    FMT_LEG(7),                  FMT_LEG(8), FMT_LEG(9),  FMT_LEG(10), FMT_LEG(11), FMT_LEG(12), FMT_LEG(13)};
+#undef FMT_LEG
+#undef FMT_DF
+#undef FMT_LB
+#undef FMT_LA
+
 // ------------------------------------------------------------------ node frame
 struct MFrame {
   double c[3], s[3], ex[3];  // u = (x - c) s ; t = u ex (ex = 2^e)
@@ -570,8 +584,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           q[0] = qm;
           if (p >= 1) q[kAtom] = q0;
           for (int kk = 1; kk < p; ++kk) {
-            const double ad = (double)(2 * kk + 1) / (double)(kk + 1), bd = (double)kk / (double)(kk + 1);
-            const dfl ca = {(float)ad, (float)(ad - (double)(float)ad)}, cb = {(float)bd, (float)(bd - (double)(float)bd)};
+            const dfl ca = {c_leg_ab[kk][0][0], c_leg_ab[kk][0][1]}, cb = {c_leg_ab[kk][1][0], c_leg_ab[kk][1][1]};
             const dfl qn = df_sub(df_mul(ca, df_mul(td, q0)), df_mul(cb, qm));
             q[(kk + 1) * kAtom] = qn;
             qm = q0;
