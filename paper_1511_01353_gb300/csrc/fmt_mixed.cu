@@ -40,7 +40,7 @@ namespace {
 
 constexpr int kAtom = 64;        // rows per operand tile: one 128-byte swizzle row of BF16
 constexpr int kDrainAtoms = 4;   // FP32 -> FP64 promotion every 256 rows
-constexpr int kFThreads = 256;   // factor / update kernels
+constexpr int kFThreads = 512;   // factor / update kernels
 constexpr double kPivotFloor = 1e-6;
 constexpr double kConvergedRel = 1e-7;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
@@ -854,18 +854,20 @@ __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
 // One CTA per node.  Shared: the packed upper triangle of the m x m Gram
 // (row i at ro(i), m = nmono + 1 with r last), the initial diagonal, y, F and
 // the change-of-basis scratch.
-// G[i][j] -= rk[i] rk[j] for k < i <= j < m (packed rows): threads form a
-// 16 x 16 grid over the upper tiles of the trailing matrix.
+// G[i][j] -= rk[i] rk[j] for k < i <= j < m (packed rows): the block's
+// threads form a (kFThreads/32) x 32 grid over the trailing matrix, a warp
+// updating 32 consecutive columns of one row.
 __device__ __forceinline__ void trailing_update(double* __restrict__ G, const double* __restrict__ rk, int k,
                                                 int m) {
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  constexpr int TR = kFThreads / 32;
+  const int ti = threadIdx.x >> 5, tj = threadIdx.x & 31;
   const int n = m - k - 1;
-  for (int ib = 0; ib < n; ib += 16) {
+  for (int ib = 0; ib < n; ib += TR) {
     const int i = k + 1 + ib + ti;
     if (i >= m) break;
     const double ri = rk[i];
     double* Gi = G + ro_of(i, m) - i;  // Gi[j] = G[i][j]
-    for (int jb = ib; jb < n; jb += 16) {
+    for (int jb = ib - (ib & 31); jb < n; jb += 32) {
       const int j = k + 1 + jb + tj;
       if (j >= i && j < m) Gi[j] = fma(-ri, rk[j], Gi[j]);
     }
