@@ -40,7 +40,7 @@ namespace {
 
 constexpr int kAtom = 64;        // rows per operand tile: one 128-byte swizzle row of BF16
 constexpr int kDrainAtoms = 4;   // FP32 -> FP64 promotion every 256 rows
-constexpr int kFThreads = 512;   // factor / update kernels
+constexpr int kFThreads = 256;   // factor / update kernels
 constexpr double kPivotFloor = 1e-6;
 constexpr double kConvergedRel = 1e-7;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
@@ -854,20 +854,18 @@ __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
 // One CTA per node.  Shared: the packed upper triangle of the m x m Gram
 // (row i at ro(i), m = nmono + 1 with r last), the initial diagonal, y, F and
 // the change-of-basis scratch.
-// G[i][j] -= rk[i] rk[j] for k < i <= j < m (packed rows): the block's
-// threads form a (kFThreads/32) x 32 grid over the trailing matrix, a warp
-// updating 32 consecutive columns of one row.
+// G[i][j] -= rk[i] rk[j] for k < i <= j < m (packed rows): threads form a
+// 16 x 16 grid over the upper tiles of the trailing matrix.
 __device__ __forceinline__ void trailing_update(double* __restrict__ G, const double* __restrict__ rk, int k,
                                                 int m) {
-  constexpr int TR = kFThreads / 32;
-  const int ti = threadIdx.x >> 5, tj = threadIdx.x & 31;
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
   const int n = m - k - 1;
-  for (int ib = 0; ib < n; ib += TR) {
+  for (int ib = 0; ib < n; ib += 16) {
     const int i = k + 1 + ib + ti;
     if (i >= m) break;
     const double ri = rk[i];
     double* Gi = G + ro_of(i, m) - i;  // Gi[j] = G[i][j]
-    for (int jb = ib - (ib & 31); jb < n; jb += 32) {
+    for (int jb = ib; jb < n; jb += 16) {
       const int j = k + 1 + jb + tj;
       if (j >= i && j < m) Gi[j] = fma(-ri, rk[j], Gi[j]);
     }
@@ -928,14 +926,14 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
       if (tid == 0) a.flags[node] |= FMT_FLAG_MIXED_PIVOT;
       return;  // the FP64 path refits this node
     }
-    const double rkk = sqrt(d);
+    const double rkk = sqrt(d), irk = 1.0 / rkk;
     double* Gk = G + ro_of(k, m) - k;
     for (int j = k + 1 + tid; j < m; j += kFThreads) {
-      const double v = Gk[j] / rkk;
+      const double v = Gk[j] * irk;
       rk[j] = v;
       Gk[j] = v;
     }
-    if (tid == 0) invd[k] = 1.0 / rkk;
+    if (tid == 0) invd[k] = irk;
     __syncthreads();
     if (tid == 0) Gk[k] = rkk;  // every thread has read the pivot by now
     trailing_update(G, rk, k, m);
