@@ -39,7 +39,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
 # current kernel on the 3e5-point recipe (profiles/tile_qr_3e5pts_p8.md):
 # 14.85 MB read + 80.61 MB written for 3e5 rows.  Scaled to a full launch by
 # its rows; set to None whenever the kernel changes until it is re-captured.
-TILE_QR_DRAM_BYTES_PER_ROW = (14.853376e6 + 80.612096e6) / 3.0e5
+TILE_QR_DRAM_BYTES_PER_ROW = (14.921472e6 + 50.5216e6) / 3.0e5
 
 
 def parse_args():
