@@ -151,7 +151,9 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  * A node whose Cholesky pivot falls below 1e-6 of its diagonal entry, whose
  * fit after the last sweep is not within 1e-7 of converged (the last change
  * |Lambda d|, or its extrapolation by the ratio of the last two changes,
- * above 1e-7 |Lambda F|), whose
+ * above 1e-7 |Lambda F|), or whose polynomial may still change by more than
+ * 1e-8 max|f| somewhere in the node box (the same extrapolation of a bound
+ * of the last change over the box), whose
  * degree exceeds FMT_MIXED_MAX_DEGREE, or whose root degree was clamped, is
  * refitted by the FP64 path; nodes fitted the mixed way carry FMT_FLAG_MIXED.
  * The mixed path targets an interpolant within 1e-6 max|f| of the FP64

@@ -29,8 +29,11 @@
 //     residual update, the evaluation and the export are those of the FP64
 //     path.
 // Nodes whose Cholesky pivot is below kPivotFloor of its diagonal entry, or
-// whose last sweep still moved the fit by more than kConvergedRel, lose
-// FMT_FLAG_MIXED and are refitted by the FP64 kernels of fmt_fit.cu.
+// whose last sweep (extrapolated by the contraction of the last two) still
+// moves the fit at the data by more than kConvergedRel of its norm, or the
+// polynomial anywhere in the node box by more than kBoxChangeRel of the
+// problem's max |f|, lose FMT_FLAG_MIXED and are refitted by the FP64 kernels
+// of fmt_fit.cu.
 
 #include <cuda_bf16.h>
 
@@ -43,6 +46,7 @@ constexpr int kDrainAtoms = 4;   // FP32 -> FP64 promotion every 256 rows
 constexpr int kFThreads = 256;   // factor / update kernels
 constexpr double kPivotFloor = 1e-6;
 constexpr double kConvergedRel = 1e-7;
+constexpr double kBoxChangeRel = 1e-8;  // remaining change over the node box, relative to max |f| of the problem
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
 constexpr int kMStat = 8;        // per-node words of mstat
 
@@ -1042,26 +1046,69 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
     a.lcoef[node * a.stride + j] = Fl[j];
   }
   __syncthreads();
-  // |R F| for the convergence test
-  double zn = 0.0;
+  // |R F| (the fit at the data) and, over the node box, a bound of the change
+  // of the polynomial: |P_a(t_x) P_b(t_y) P_c(t_z)| <= P_a(T_x) P_b(T_y) P_c(T_z)
+  // with T = 2^e >= 1 (|u| <= 1 maps to |t| <= T), so the change anywhere in
+  // the box is at most sum_j |d_j| P(T)_j
+  __shared__ double s_pt[3][FMT_MIXED_MAX_DEGREE + 1];
+  if (tid < 3) {
+    const double T = F.ex[tid];
+    double q0 = 1.0, q1 = T;
+    s_pt[tid][0] = 1.0;
+    if (p >= 1) s_pt[tid][1] = T;
+    for (int kk = 1; kk < p; ++kk) {
+      const double q2 = ((double)(2 * kk + 1) * T * q1 - (double)kk * q0) / (double)(kk + 1);
+      s_pt[tid][kk + 1] = q2;
+      q0 = q1;
+      q1 = q2;
+    }
+  }
+  __syncthreads();
+  double zn = 0.0, cw = 0.0;
   for (int i = tid; i < L; i += kFThreads) {
     const double* rowi = R + ro_of(i, m) - i;
     double zi = 0.0;
     for (int j = i; j < L; ++j) zi = fma(rowi[j], Fl[j], zi);
     zn += zi * zi;
+    // (a, b, c) of column i in Alg. 2 order
+    int r = i, la = 0;
+    while (r >= (p - la + 1) * (p - la + 2) / 2) {
+      r -= (p - la + 1) * (p - la + 2) / 2;
+      ++la;
+    }
+    int lb = 0;
+    while (r >= p - la - lb + 1) {
+      r -= p - la - lb + 1;
+      ++lb;
+    }
+    cw += fabs(g[i]) * s_pt[0][la] * s_pt[1][lb] * s_pt[2][r];
   }
-  for (int o = 16; o > 0; o >>= 1) zn += __shfl_xor_sync(0xffffffffu, zn, o);
-  if ((tid & 31) == 0) red[tid >> 5] = zn;
+  for (int o = 16; o > 0; o >>= 1) {
+    zn += __shfl_xor_sync(0xffffffffu, zn, o);
+    cw += __shfl_xor_sync(0xffffffffu, cw, o);
+  }
+  __shared__ double red2[kFThreads / 32];
+  if ((tid & 31) == 0) {
+    red[tid >> 5] = zn;
+    red2[tid >> 5] = cw;
+  }
   __syncthreads();
-  double ztot = 0.0;
-  for (int i = 0; i < kFThreads / 32; ++i) ztot += red[i];
+  double ztot = 0.0, ctot = 0.0;
+  for (int i = 0; i < kFThreads / 32; ++i) {
+    ztot += red[i];
+    ctot += red2[i];
+  }
   legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
   if (tid == 0) {
-    // |R d| = |Lambda d| is the change of the fit; with the previous change it
-    // gives the contraction rho and the remaining error ~ |R d| rho / (1 - rho)
+    // |R d| = |Lambda d| is the change of the fit at the data, ctot its bound
+    // over the node box; with the previous sweep's values they give the
+    // contraction rho and the remaining error ~ change * rho / (1 - rho)
     unsigned long long* slot = a.mstat + kMStat * node + 4;
+    unsigned long long* cslot = a.mstat + kMStat * node + 6;
     const double upd = sqrt(wn), zn = sqrt(ztot), prev = __longlong_as_double((long long)*slot);
+    const double cprev = __longlong_as_double((long long)*cslot);
     *slot = (unsigned long long)__double_as_longlong(upd);
+    *cslot = (unsigned long long)__double_as_longlong(ctot);
     a.mstat[kMStat * node + 5] = 0ull;  // max |s| of the next sweep
     if (a.last_sweep) {
       bool conv = upd <= kConvergedRel * zn;
@@ -1069,7 +1116,13 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
         const double rho = upd / prev;
         conv = upd * rho / (1.0 - rho) <= kConvergedRel * zn;
       }
-      if (!conv) a.flags[node] = (a.flags[node] & ~FMT_FLAG_MIXED) | FMT_FLAG_MIXED_SLOW;
+      const double cthr = kBoxChangeRel * pr.maxabs;
+      bool cconv = ctot <= cthr;
+      if (!cconv && cprev > 0.0 && ctot < cprev) {
+        const double rho = ctot / cprev;
+        cconv = ctot * rho / (1.0 - rho) <= cthr;
+      }
+      if (!(conv && cconv)) a.flags[node] = (a.flags[node] & ~FMT_FLAG_MIXED) | FMT_FLAG_MIXED_SLOW;
     }
   }
 }
