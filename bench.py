@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["fmt", "reference"], default="fmt")
-    ap.add_argument("--workload", choices=["scale", "small", "batch", "serve"], default="scale")
+    ap.add_argument("--workload", choices=["scale", "small", "batch", "serve", "fig1", "sweep"], default="scale")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests in the arrival stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=2, help="serve: worker slots (streams)")
@@ -262,6 +262,67 @@ def cpu_baseline(args):
             "evals_per_s": w.m / (t2 - t1)}
 
 
+def run_experiments(args, rank, world):
+    """The paper's experiments on the GPU path (FP64).  fig1: the unscoped fit
+    (a single node, max_depth 0) of 8^6 random points at p = 6, 10, 14 (Fig. 1,
+    Sec. 3).  sweep: tau x N x p (Figs. 2-4, Sec. 4), error against the Franke
+    function (Eq. eqF1) at 1e5 random targets and the number of octree nodes.
+    The paper prints no numbers for these figures; this is a report."""
+    import numpy as np
+    import torch
+    from paper_1511_01353_gb300 import fmt as F
+    from paper_1511_01353_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    F.load()
+    seed = W.SEED_BASE + 5
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    xq, yq, zq = W.uniform_points(seed, 9, 100_000)
+    fq = W.franke_paper(xq, yq, zq)
+    dq = [dev(a) for a in (xq, yq, zq)]
+    out = torch.empty(xq.shape[0], dtype=torch.float64, device="cuda")
+
+    def run(n, p, D, tol):
+        x, y, z = W.uniform_points(seed, 1 + n, n)
+        f = W.franke_paper(x, y, z)
+        dx = [dev(a) for a in (x, y, z, f)]
+        prm = F.make_params(p, D, 0, tol)
+        F.fit(prm, *dx).close()  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tree = F.fit(prm, *dx)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        F.evaluate(tree, *dq, out)
+        torch.cuda.synchronize()
+        st = F.fmt_tree_stats(tree)
+        nodes = int(sum(st.nodes[d] for d in range(st.n_levels)))
+        tree.close()
+        erms, einf = W.errors(out.cpu().numpy(), fq)
+        return {"N": n, "p": p, "nmono": F.fmt_nmono(p), "max_depth": D, "tol_rel": tol, "nodes": nodes,
+                "E_rms": erms, "E_inf": einf, "fit_ms": t * 1e3, "fitted_pts_per_s": n / t}
+
+    rows = []
+    if args.workload == "fig1":
+        for p in (6, 10, 14):
+            rows.append(run(8 ** 6, p, 0, 0.0))
+        metric = "unscoped fit (Fig. 1): E_rms, E_inf vs p"
+    else:
+        for n in (8 ** 4, 8 ** 5, 8 ** 6):
+            for p in (4, 8, 12):
+                for tol in (1e-6, 1e-8, 1e-10, 1e-12):
+                    rows.append(run(n, p, 10, tol))
+        metric = "tau x N x p sweep (Figs. 2-4): E_rms, E_inf, nodes"
+    line = {"metric": metric, "unit": "see rows", "n_gpus": world, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "points": "uniform [0,1)^3", "values": "Franke (Eq. eqF1)",
+                       "targets": 100_000, "min_pts": 0}, "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args, rank, world):
     """Serving: a Poisson stream of fit+evaluate requests through the
     library's serving engine (continuous batching over worker streams);
@@ -349,6 +410,8 @@ def main():
         return 0
     if args.workload == "serve":
         return run_serve(args, rank, world)
+    if args.workload in ("fig1", "sweep"):
+        return run_experiments(args, rank, world)
 
     import numpy as np
     import torch

@@ -211,3 +211,20 @@ def test_stats_and_determinism():
     assert s.n_levels == s.n_fitted == len([d for d in range(22) if s.nodes[d] > 0])
     assert s.nodes[0] == 1 and s.points[0] == w.n
     assert sum(s.nodes[d] for d in range(22)) == e1.prefix.shape[0]
+
+
+@pytest.mark.parametrize("p,n,D", [(10, 3000, 1), (12, 5000, 1), (14, 7000, 1)])
+def test_high_degrees(p, n, D):
+    # the degrees of the paper's unscoped runs (nmono 286, 455, 680); the
+    # triangles no longer fit in shared memory, so the merges take the
+    # general path.  Monomials of degree 14 on [-1,1]^3 scaled by 1/(l!m!n!)
+    # make kappa ~ 1e13, so node polynomials are compared at the node's own
+    # data points, where the least-squares fit is determined.
+    rng = np.random.default_rng(100 + p)
+    x, y, z = (rng.uniform(0, 1, n) for _ in range(3))
+    f = W.franke_paper(x, y, z)
+    T = O.fit(x, y, z, f, p, D, 1, 1e-12)
+    tree, ex = gpu_fit(x, y, z, f, p, D, 1, 1e-12, chunk_rows=1024)
+    tol = REL_TOL * T.maxabs
+    TC.compare_trees(T, ex, tol, data_xyz=(x, y, z))
+    assert np.max(np.abs(ex.resid - T.resid)) <= tol
