@@ -97,10 +97,13 @@ __device__ __forceinline__ NodeGeom node_geom(const QRArgs& a, int64_t node) {
 
 // Structured Householder absorb of a row block B (NB x m in shared memory,
 // leading dimension ldB) into the upper triangle R (m x m, row-major, global).
-// For each column j >= j_begin: u = [alpha - beta; x] with alpha = R_jj,
-// x = B[:, j], beta = -sign(alpha) sqrt(alpha^2 + |x|^2) (sign(0) = +), and
-// H = I - gamma u u^T, gamma = 1 / (beta (beta - alpha)).  A column with
-// |x| = 0 is left alone (no reflection).
+// For each column j >= j_begin: alpha = R_jj, x = B[:, j],
+// beta = -sign(alpha) sqrt(alpha^2 + |x|^2) (sign(0) = +), and
+// H = I - tau [1; v][1; v]^T with v = x / (alpha - beta) and
+// tau = (beta - alpha) / beta = 1 + |alpha| / |beta| (LAPACK's normalisation:
+// tau lies in [1, 2] and |v| <= 1, so nothing over- or underflows however
+// small |x| is, e.g. the rounding residue left in a block's columns beyond
+// its rank).  A column with |x| = 0 is left alone (tau = 0).
 //
 // Schedule per step j (one barrier per step):
 //  * row j of R sits in shared memory (Rs[j&1]); row j+1 was prefetched into
@@ -111,7 +114,8 @@ __device__ __forceinline__ NodeGeom node_geom(const QRArgs& a, int64_t node) {
 //  * warp 0, right after its first round (which updates column j+1), computes
 //    the reflector of step j+1 (look-ahead), so no step waits on a serial
 //    norm / sqrt / divide phase of its own.
-__device__ __forceinline__ void reflector(const double* __restrict__ B, int ldB, int NB, int j, double* Rrow,
+// One warp: tau of column j into sc[0], beta into R_jj, and v over x in B.
+__device__ __forceinline__ void reflector(double* __restrict__ B, int ldB, int NB, int j, double* Rrow,
                                           double* __restrict__ Rg, int m, double* sc) {
   const int lane = threadIdx.x & 31;
   double s = 0.0;
@@ -120,20 +124,23 @@ __device__ __forceinline__ void reflector(const double* __restrict__ B, int ldB,
     s = fma(xv, xv, s);
   }
   s = warp_sum(s);
+  double inv = 0.0;
   if (lane == 0) {
     const double alpha = Rrow[j];
     if (s == 0.0) {
       sc[0] = 0.0;
-      sc[1] = 0.0;
     } else {
       const double h = sqrt(fma(alpha, alpha, s));
       const double beta = alpha >= 0.0 ? -h : h;
-      sc[0] = 1.0 / (h * (h + fabs(alpha)));
-      sc[1] = alpha - beta;
+      sc[0] = (h + fabs(alpha)) / h;
+      inv = 1.0 / (alpha - beta);
       Rrow[j] = beta;
       Rg[(size_t)j * m + j] = beta;
     }
   }
+  inv = __shfl_sync(0xffffffffu, inv, 0);
+  if (inv != 0.0)
+    for (int i = lane; i < NB; i += 32) B[i * ldB + j] *= inv;
 }
 
 // tri_row0 >= 0 marks a block whose row i is zero left of column tri_row0+i
@@ -188,9 +195,9 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
     }
     // groups of four rows that can hold nonzeros at this step (warp uniform)
     const int tmax = tri_row0 < 0 ? RPT : min(RPT, max(0, (j - tri_row0) / 4 + 1));
-    const double gamma = sc[cur * 2], amb = sc[cur * 2 + 1];
-    const bool upd = gamma != 0.0;
-    double xr[RPT];
+    const double tau = sc[cur * 2];
+    const bool upd = tau != 0.0;
+    double xr[RPT];  // v of step j
     if (upd) {
 #pragma unroll
       for (int t = 0; t < RPT; ++t) xr[t] = (t < tmax) ? B[(rg + 4 * t) * ldB + j] : 0.0;
@@ -228,7 +235,7 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (act) {
           const double rv = Rc[k];
-          const double d = gamma * fma(amb, rv, acc);
+          const double d = tau * (rv + acc);
 #pragma unroll
           for (int t = 0; t < RPT; ++t) {
             if (t < tmax) {
@@ -236,7 +243,7 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
               *bp = fma(-d, xr[t], *bp);
             }
           }
-          if (rg == 0) R[(size_t)j * m + k] = fma(-d, amb, rv);
+          if (rg == 0) R[(size_t)j * m + k] = rv - d;
         }
         k0 += 8 * NW;
       }
@@ -384,25 +391,28 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
   for (int k = tid; k < m; k += kMergeThreads) Rs[k] = Ra[k];  // row 0 of R_a
   __syncthreads();
 
-  auto reflect = [&](int j, double* Rrow, double* scj) {  // one warp
-    const double* col = Bp + j * (j + 1) / 2;
+  auto reflect = [&](int j, double* Rrow, double* scj) {  // one warp; tau and v as in reflector()
+    double* col = Bp + j * (j + 1) / 2;
     double sq = 0.0;
     for (int i = lane; i <= j; i += 32) sq = fma(col[i], col[i], sq);
     sq = warp_sum(sq);
+    double inv = 0.0;
     if (lane == 0) {
       const double alpha = Rrow[j];
       if (sq == 0.0) {
         scj[0] = 0.0;
-        scj[1] = 0.0;
       } else {
         const double h = sqrt(fma(alpha, alpha, sq));
         const double beta = alpha >= 0.0 ? -h : h;
-        scj[0] = 1.0 / (h * (h + fabs(alpha)));
-        scj[1] = alpha - beta;
+        scj[0] = (h + fabs(alpha)) / h;
+        inv = 1.0 / (alpha - beta);
         Rrow[j] = beta;
         Ra[(size_t)j * m + j] = beta;
       }
     }
+    inv = __shfl_sync(0xffffffffu, inv, 0);
+    if (inv != 0.0)
+      for (int i = lane; i <= j; i += 32) col[i] *= inv;
   };
   auto rot = [&](int jj) { return (tid - 32 * ((jj + (int)blockIdx.x) & (kMergeWarps - 1))) & (kMergeThreads - 1); };
   constexpr int kPF = (680 + kMergeThreads - 1) / kMergeThreads;
@@ -435,9 +445,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
         pf[e] = (k < m) ? Ra[(size_t)(j + 2) * m + k] : 0.0;
       }
     }
-    const double gamma = sc[cur * 2], amb = sc[cur * 2 + 1];
-    const bool upd = gamma != 0.0;
-    const double* xj = Bp + j * (j + 1) / 2;  // column j, rows 0..j
+    const double tau = sc[cur * 2];
+    const bool upd = tau != 0.0;
+    const double* xj = Bp + j * (j + 1) / 2;  // v of step j, rows 0..j
     const int slot = (warp - j - (int)blockIdx.x) & (kMergeWarps - 1);
     int k0 = j + 1 + 8 * slot;
     bool lookahead = (slot == 0) && (j + 1 < m);
@@ -460,7 +470,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (act) {
           const double rv = Rc[k];
-          const double d = gamma * fma(amb, rv, acc);
+          const double d = tau * (rv + acc);
           int i2 = rg;
           for (; i2 + 12 <= j; i2 += 16) {
             const double b0 = fma(-d, xj[i2], ck[i2]);
@@ -473,7 +483,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
             ck[i2 + 12] = b3;
           }
           for (; i2 <= j; i2 += 4) ck[i2] = fma(-d, xj[i2], ck[i2]);
-          if (rg == 0) Ra[(size_t)j * m + k] = fma(-d, amb, rv);
+          if (rg == 0) Ra[(size_t)j * m + k] = rv - d;
         }
         k0 += 8 * kMergeWarps;
       }
@@ -586,15 +596,18 @@ __device__ int backsolve_warp(double* __restrict__ R, int m, int q, int p, int n
       }
       s = warp_sum(s);
       if (s == 0.0) continue;
+      // reflector in the normalised form of reflector(): v over the column
       const double h = sqrt(fma(alpha, alpha, s));
       const double beta = alpha >= 0.0 ? -h : h;
-      const double amb = alpha - beta;
-      const double gamma = 1.0 / (h * (h + fabs(alpha)));
+      const double tau = (h + fabs(alpha)) / h;
+      const double inv = 1.0 / (alpha - beta);
+      for (int i = cc + 1 + lane; i <= rmx; i += 32) R[(size_t)i * m + cc] *= inv;
+      __syncwarp();
       for (int k = cc + 1 + lane; k <= Lk; k += 32) {
-        double w = amb * R[(size_t)cc * m + k];
+        double w = R[(size_t)cc * m + k];
         for (int i = cc + 1; i <= rmx; ++i) w = fma(R[(size_t)i * m + cc], R[(size_t)i * m + k], w);
-        const double d = gamma * w;
-        R[(size_t)cc * m + k] = fma(-d, amb, R[(size_t)cc * m + k]);
+        const double d = tau * w;
+        R[(size_t)cc * m + k] -= d;
         for (int i = cc + 1; i <= rmx; ++i) R[(size_t)i * m + k] = fma(-d, R[(size_t)i * m + cc], R[(size_t)i * m + k]);
       }
       __syncwarp();
