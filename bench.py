@@ -64,6 +64,11 @@ def parse_args():
                     help="path of the headline value; the other path is reported in the 'mixed' / 'fp64' block")
     ap.add_argument("--no-second-path", action="store_true", help="skip the block of the other precision")
     ap.add_argument("--sweeps", type=int, default=0, help="mixed path: FP64 refinement sweeps (0 = library default)")
+    ap.add_argument("--graph", action="store_true", help="capture each fit_level in a CUDA graph (FMT_OPT_GRAPH)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time QR launch configurations (fmt_autotune) for the workload's degrees before the run")
+    ap.add_argument("--sweep-max-exp", type=int, default=7,
+                    help="sweep: largest N = 8^E (E <= 9; degree 12 runs up to 8^7)")
     return ap.parse_args()
 
 
@@ -265,9 +270,10 @@ def cpu_baseline(args):
 def run_experiments(args, rank, world):
     """The paper's experiments on the GPU path (FP64).  fig1: the unscoped fit
     (a single node, max_depth 0) of 8^6 random points at p = 6, 10, 14 (Fig. 1,
-    Sec. 3).  sweep: tau x N x p (Figs. 2-4, Sec. 4), error against the Franke
-    function (Eq. eqF1) at 1e5 random targets and the number of octree nodes.
-    The paper prints no numbers for these figures; this is a report."""
+    Sec. 3).  sweep: tau x N x p (Figs. 2-4, Sec. 4): N_p = N_q = 8^4 .. 8^E
+    random points and targets, error against the Franke function (Eq. eqF1)
+    at the targets and the number of octree nodes.  The paper prints no
+    numbers for these figures; this is a report."""
     import numpy as np
     import torch
     from paper_1511_01353_gb300 import fmt as F
@@ -279,45 +285,59 @@ def run_experiments(args, rank, world):
 
     def dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    xq, yq, zq = W.uniform_points(seed, 9, 100_000)
-    fq = W.franke_paper(xq, yq, zq)
-    dq = [dev(a) for a in (xq, yq, zq)]
-    out = torch.empty(xq.shape[0], dtype=torch.float64, device="cuda")
 
-    def run(n, p, D, tol):
-        x, y, z = W.uniform_points(seed, 1 + n, n)
-        f = W.franke_paper(x, y, z)
-        dx = [dev(a) for a in (x, y, z, f)]
+    def cloud(n, stream):
+        x, y, z = W.uniform_points(seed, stream, n)
+        return [dev(a) for a in (x, y, z, W.franke_paper(x, y, z))]
+
+    def run(pts, tgt, p, D, tol, warm):
+        n = pts[0].shape[0]
         prm = F.make_params(p, D, 0, tol)
-        F.fit(prm, *dx).close()  # warm-up
+        if warm:
+            F.fit(prm, *pts[:4]).close()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tree = F.fit(prm, *dx)
+        tree = F.fit(prm, *pts[:4])
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
-        F.evaluate(tree, *dq, out)
+        out = torch.empty(tgt[0].shape[0], dtype=torch.float64, device="cuda")
+        F.evaluate(tree, *tgt[:3], out)
         torch.cuda.synchronize()
         st = F.fmt_tree_stats(tree)
         nodes = int(sum(st.nodes[d] for d in range(st.n_levels)))
+        depth = st.n_levels - 1
         tree.close()
-        erms, einf = W.errors(out.cpu().numpy(), fq)
-        return {"N": n, "p": p, "nmono": F.fmt_nmono(p), "max_depth": D, "tol_rel": tol, "nodes": nodes,
-                "E_rms": erms, "E_inf": einf, "fit_ms": t * 1e3, "fitted_pts_per_s": n / t}
+        erms, einf = W.errors(out.cpu().numpy(), tgt[3].cpu().numpy())
+        return {"N": n, "N_q": int(tgt[0].shape[0]), "p": p, "nmono": F.fmt_nmono(p), "max_depth": D,
+                "tol_rel": tol, "nodes": nodes, "depth": depth, "E_rms": erms, "E_inf": einf,
+                "fit_ms": t * 1e3, "fitted_pts_per_s": n / t}
 
     rows = []
     if args.workload == "fig1":
+        pts = cloud(8 ** 6, 1 + 8 ** 6)
+        tgt = cloud(100_000, 9)
         for p in (6, 10, 14):
-            rows.append(run(8 ** 6, p, 0, 0.0))
+            rows.append(run(pts, tgt, p, 0, 0.0, True))
         metric = "unscoped fit (Fig. 1): E_rms, E_inf vs p"
+        targets = 100_000
     else:
-        for n in (8 ** 4, 8 ** 5, 8 ** 6):
+        emax = max(4, min(9, args.sweep_max_exp))
+        for e in range(4, emax + 1):
+            n = 8 ** e
+            pts = cloud(n, 1 + n)
+            tgt = cloud(n, 9)
             for p in (4, 8, 12):
-                for tol in (1e-6, 1e-8, 1e-10, 1e-12):
-                    rows.append(run(n, p, 10, tol))
+                if p == 12 and e > 7:
+                    continue  # about 100 s per fit at 8^8 on the FP64 path
+                for k, tol in enumerate((1e-6, 1e-8, 1e-10, 1e-12)):
+                    rows.append(run(pts, tgt, p, 10, tol, k == 0))
+            del pts, tgt
+            torch.cuda.empty_cache()
         metric = "tau x N x p sweep (Figs. 2-4): E_rms, E_inf, nodes"
+        targets = "N_q = N_p"
     line = {"metric": metric, "unit": "see rows", "n_gpus": world, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "points": "uniform [0,1)^3", "values": "Franke (Eq. eqF1)",
-                       "targets": 100_000, "min_pts": 0}, "rows": rows}
+                       "targets": targets, "min_pts": 0}, "rows": rows}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -429,7 +449,7 @@ def main():
     prec_of = {"fp64": F.FMT_FP64, "mixed": F.FMT_MIXED}
     params = None if args.workload == "batch" else F.make_params(w.degree, w.max_depth, w.min_pts, w.tol_rel,
                                                                  precision=prec_of[args.precision],
-                                                                 sweeps=args.sweeps)
+                                                                 sweeps=args.sweeps, graph=args.graph)
 
     def dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
@@ -437,7 +457,7 @@ def main():
     is_batch = args.workload == "batch"
     if is_batch:
         params = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel, precision=prec_of[args.precision],
-                               sweeps=args.sweeps)
+                               sweeps=args.sweeps, graph=args.graph)
         w.n = int(w.offsets[-1])
         w.m = int(w.xq.shape[0])
         w.name = w.name
@@ -445,6 +465,13 @@ def main():
     x, y, z, f = dev(w.x), dev(w.y), dev(w.z), dev(w.f)
     xq, yq, zq = dev(w.xq), dev(w.yq), dev(w.zq)
     out = torch.empty(w.m, dtype=torch.float64, device="cuda")
+    tuning = "built-in rule"
+    if args.autotune:  # before any timed work; a level uses the entry of its largest degree
+        tuning = {}
+        for d in (sorted(set(int(v) for v in w.degrees)) if is_batch else [w.degree]):
+            e = F.fmt_autotune(d, stream=stream)
+            tuning[str(d)] = {k: e[k] for k in ("rows", "warps", "chunk_factor", "merge", "sample_points", "ms",
+                                                "ms_builtin")}
 
     def build(xx, yy, zz, ff, prm=None):
         prm = params if prm is None else prm
@@ -574,14 +601,15 @@ def main():
     total_ms = sum(v["ms"] for v in prof.values())
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                    "share": (v["ms"] / total_ms if total_ms else None)} for k, v in prof.items() if v["launches"]}
-    gpu_launches = sum(v["launches"] for v in prof.values())
+    # kernel and memset launches (a graph launch replays launches counted here)
+    gpu_launches = sum(v["launches"] for k, v in prof.items() if k != "graph_launch")
 
     # the other precision on the same inputs: throughput and its error against the headline path
     other = None
     if not args.no_second_path and not args.profile_only:
         oprec = "mixed" if args.precision == "fp64" else "fp64"
         oparams = F.make_params(params.degree, params.max_depth, params.min_pts, params.tol_rel,
-                                precision=prec_of[oprec], sweeps=args.sweeps)
+                                precision=prec_of[oprec], sweeps=args.sweeps, graph=args.graph)
         for _ in range(max(1, min(args.warmup, 2))):
             tr, _ = step(False, oparams)
             stream.synchronize()
@@ -683,7 +711,7 @@ def main():
                    "values": ("shifted/scaled Franke or Gaussian sums per problem" if is_batch
                               else "3-D Franke (benchmark form)"),
                    "l2": "flushed before every step (256 MB write)", "parallelism": "replicas",
-                   "gpu": gpu_name},
+                   "gpu": gpu_name, "graph": bool(args.graph), "qr_launch_config": tuning},
         "evals_per_s": job_throughput(world, w.m, eval_s), "fit_ms": fit_s * 1e3, "eval_ms": eval_s * 1e3,
         "roofline": {"bound": "alu", "kernel": "tile_qr", "achieved": qr_tflops, "peak": FP64_NOMINAL_TFLOPS,
                      "unit": "TFLOP/s", "frac": (qr_tflops / FP64_NOMINAL_TFLOPS if qr_tflops else None),

@@ -83,7 +83,9 @@ typedef enum {
  *   sweeps     FMT_MIXED only: FP64 refinement sweeps after the first solve:
  *              1..3 (FMT_MIXED_MAX_SWEEPS), 0 selects 3, -1 none (then no
  *              convergence test either).  Ignored for FP64.
- *   reserved   must be 0.
+ *   options    bit set: FMT_OPT_GRAPH captures the launches of each
+ *              fit_level in a CUDA graph (one graph per level step) and
+ *              launches that; other bits must be 0.
  */
 typedef struct {
   int32_t degree;
@@ -95,8 +97,17 @@ typedef struct {
   double side;
   int64_t chunk_rows;
   int32_t sweeps;
-  int32_t reserved;
+  int32_t options;
 } fmt_params;
+
+/* fmt_params.options bits.  FMT_OPT_GRAPH: fit_level captures its kernel and
+ * memset launches on an internal stream into a CUDA graph and launches the
+ * graph on the caller's stream.  The executable graph of each depth is kept
+ * per host thread and updated in place (cudaGraphExecUpdate) when the next
+ * level step has the same launch structure, so repeated fits of similar
+ * trees replay a graph instead of issuing launch by launch.  Results are
+ * bitwise the same as without the option. */
+#define FMT_OPT_GRAPH 1
 
 typedef struct fmt_tree fmt_tree; /* opaque, device resident */
 
@@ -309,6 +320,63 @@ const char* fmt_profile_class_name(int32_t k);
  * Synchronises.
  */
 fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream);
+
+/*
+ * Autotuner of the FP64 Householder fit (no counterpart in the paper, which
+ * fixes no GPU schedule).  For each degree p the library keeps one launch
+ * configuration of the QR of fit_level (Alg. 2 per node, chunks reduced
+ * pairwise):
+ *   rows          rows of [Lambda | r] absorbed per shared-memory block:
+ *                 16, 32 or 64, and (rows + 2) * ld * 8 + 32 bytes must fit
+ *                 in 227 KB, ld = the padded row pitch of nmono(p) + 1 columns;
+ *   warps         warps per tile-QR CTA: 4 or 8;
+ *   chunk_factor  smallest row chunk (one work item of the persistent queue)
+ *                 = chunk_factor * (nmono + 1) rows rounded up to 64:
+ *                 1, 2, 4, 8 or 16 (fmt_params.chunk_rows > 0 overrides it);
+ *   merge         pairwise reduction of a node's chunk triangles: 0 packs the
+ *                 second triangle into shared memory where it fits (nmono+1
+ *                 <= 166), 1 always streams it in row blocks.
+ * A degree without a tuned or installed entry uses the built-in rule
+ * (source 0): the largest of 64/32/16 rows that fits two (64) or one CTA per
+ * SM, 4 warps, chunk_factor 4, merge 0.  The configuration changes the order
+ * of floating-point operations, not the method: every configuration meets
+ * the same accuracy, and runs with one table are bitwise reproducible.  A
+ * level of a forest uses the entry of its largest node's degree.  The table
+ * is per process (all devices of this pool are alike); change it only while
+ * no fit is running.
+ *
+ * fmt_autotune times candidate configurations for `degree` on a synthetic
+ * forest of `sample_points` uniform random points (0 selects a size that
+ * keeps one trial near 50 ms): half in one problem, half in equal problems of
+ * at least 8 (nmono + 1) points each, tau = 0, depth 0, so that both one big
+ * node spread over every SM and many small nodes are in the timed work.  It
+ * times fit_level(0) with CUDA events (best of two after a warm-up) and
+ * searches coordinate-wise: rows x warps, then chunk_factor, then merge.
+ * The winner is installed (source 1) and returned in *out with its time and
+ * the time of the built-in rule on the same sample.  Synchronises; allocates
+ * and frees its own device memory.  FMT_EINVAL for a degree outside 0..14.
+ *
+ * fmt_tune_get returns the entry in force for `degree` (host only, no GPU
+ * needed).  fmt_tune_set installs an entry (e.g. one saved from an earlier
+ * autotune) after checking the values above, or with source = 0 restores the
+ * built-in rule for that degree; FMT_EINVAL on a bad value.
+ */
+typedef struct {
+  int32_t degree;
+  int32_t rows;
+  int32_t warps;
+  int32_t chunk_factor;
+  int32_t merge;
+  int32_t source;        /* 0 built-in rule, 1 autotuned, 2 installed by fmt_tune_set */
+  int64_t sample_points; /* autotune: points timed per trial */
+  double ms;             /* autotune: fit_level(0) time of this configuration */
+  double ms_builtin;     /* autotune: fit_level(0) time of the built-in rule */
+  int32_t trials;        /* autotune: configurations timed */
+  int32_t pad;
+} fmt_tune_entry;
+fmt_status fmt_autotune(int32_t degree, int64_t sample_points, void* stream, fmt_tune_entry* out);
+fmt_status fmt_tune_get(int32_t degree, fmt_tune_entry* out);
+fmt_status fmt_tune_set(const fmt_tune_entry* entry);
 
 /*
  * fmt_fit_node_static -- allocation-free least-squares fit of ONE point set.

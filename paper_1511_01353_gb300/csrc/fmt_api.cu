@@ -57,12 +57,13 @@ fmt_status device_init(int dev) {
 enum {
   K_CHECK = 0, K_MORTON, K_SORT, K_GATHER, K_PLAN, K_TILE_QR, K_COMBINE, K_BACKSOLVE,
   K_RESIDUAL, K_CHILD, K_REFINE, K_EVALUATE, K_HCOEF, K_MBOX, K_MGRAM, K_MFACTOR, K_MSRESID, K_MPROJ,
-  K_MUPDATE, K_NCLASS
+  K_MUPDATE, K_GRAPH, K_NCLASS
 };
 const char* const kClassNames[K_NCLASS] = {"check_maxabs", "morton", "radix_sort", "gather", "plan_root",
                                            "tile_qr", "combine", "back_solve", "residual", "child_stats",
                                            "refine", "evaluate", "make_hcoef", "mixed_box", "mixed_gram",
-                                           "mixed_factor", "mixed_sresid", "mixed_proj", "mixed_update"};
+                                           "mixed_factor", "mixed_sresid", "mixed_proj", "mixed_update",
+                                           "graph_launch"};
 struct ProfRec {
   int k;
   cudaEvent_t a, b;
@@ -101,14 +102,22 @@ struct ProfScope {
     g_flops[k] += flops;
     if (g_prof_on) {
       a = prof_event();
-      if (a && cudaEventRecord(a, s) == cudaSuccess) on = true;
+      if (a && record(a) == cudaSuccess) on = true;
     }
+  }
+  // Inside a stream capture the events become event-record nodes of the
+  // graph (recorded at every replay), so timing works in both modes.
+  cudaError_t record(cudaEvent_t ev) const {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    return cudaEventRecord(ev, s);
   }
   ~ProfScope() {
     if (!on) return;
     std::lock_guard<std::mutex> lk(g_pmu);
     cudaEvent_t b = prof_event();
-    if (!b || cudaEventRecord(b, s) != cudaSuccess) return;
+    if (!b || record(b) != cudaSuccess) return;
     if (g_nrecs == g_caprecs) {
       int64_t nc = g_caprecs ? 2 * g_caprecs : 1024;
       ProfRec* nr = (ProfRec*)realloc(g_recs, sizeof(ProfRec) * (size_t)nc);
@@ -258,7 +267,7 @@ fmt_status validate_shared(const fmt_params& P) {
     return set_err(nullptr, FMT_EINVAL, "precision must be FMT_FP64 or FMT_MIXED");
   if (P.sweeps < -1 || P.sweeps > FMT_MIXED_MAX_SWEEPS)
     return set_err(nullptr, FMT_EINVAL, "sweeps %d outside [-1, %d]", P.sweeps, FMT_MIXED_MAX_SWEEPS);
-  if (P.reserved != 0) return set_err(nullptr, FMT_EINVAL, "reserved must be 0");
+  if ((P.options & ~FMT_OPT_GRAPH) != 0) return set_err(nullptr, FMT_EINVAL, "options has unknown bits (0x%x)", P.options);
   if (!(P.tol_rel >= 0.0) || !isfinite(P.tol_rel)) return set_err(nullptr, FMT_EINVAL, "tol_rel must be finite, >= 0");
   if (P.chunk_rows < 0) return set_err(nullptr, FMT_EINVAL, "chunk_rows < 0");
   return FMT_OK;
@@ -326,10 +335,11 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
   t->pid_bits = pid_bits;
   {
     // A chunk of C rows costs about 2 m^2 C flops and one merge about (2/3) m^3,
-    // so C >= 4m keeps merges under ~10% of the chunk work; above that floor
-    // the planner sizes chunks to the rows per resident QR CTA, so that the
-    // largest item is no longer than the average share of a CTA.
-    int64_t fl = 4 * (int64_t)(t->nmono + 1);
+    // so C >= 4m keeps merges under ~10% of the chunk work (the built-in
+    // factor 4; the autotuner may pick another); above that floor the planner
+    // sizes chunks to the rows per resident QR CTA, so that the largest item
+    // is no longer than the average share of a CTA.
+    int64_t fl = (int64_t)qr_config(t->nmono + 1).chunk_factor * (int64_t)(t->nmono + 1);
     t->chunk_floor = fl < 64 ? 64 : (fl + 63) / 64 * 64;
   }
   t->h_prob = (fmt_problem*)calloc((size_t)P, sizeof(fmt_problem));
@@ -542,7 +552,6 @@ fmt_status ensure_mixed(fmt_tree* t, int depth, cudaStream_t s) {
 // The mixed-precision fit of one level (fmt_mixed.cu): nodes it fits carry
 // FMT_FLAG_MIXED afterwards and are skipped by the FP64 kernels.
 fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
-  TRY(ensure_mixed(t, depth, s));
   const fmt_level& L = t->lv[depth];
   fmt_mixed_bufs b = t->mx;
   if (b.cap_cache < mixed_cache_bytes(t, depth)) b.cache = nullptr;  // too large: regenerate per sweep
@@ -573,6 +582,104 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
       ProfScope ps(K_MUPDATE, s, 1, nodes, 0.0);
       CUDA_TRY(t, launch_mixed_update(t, depth, b, k == sweeps - 1, s), "mixed update launch");
     }
+  }
+  return FMT_OK;
+}
+
+// The launches of one level step (Alg. 2 for every node of the level, then
+// the octant statistics and the cumulative polynomials), all on stream s.
+fmt_status fit_level_launches(fmt_tree* t, int depth, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  const double dm = (double)L.max_m, rows = (double)L.n_points;
+  if (t->P.precision == FMT_MIXED) TRY(fit_level_mixed(t, depth, s));
+  {
+    // Householder on [Lambda | r]: 2 m^2 flops per row (m = nmono + 1 of the row's node);
+    // on the mixed path only the nodes it left to FP64 are factorised here
+    ProfScope ps(K_TILE_QR, s, 1, rows, t->P.precision == FMT_MIXED ? 0.0 : L.qr_flops);
+    CUDA_TRY(t, launch_tile_qr(t, depth, t->Rbuf, s), "tile QR launch");
+  }
+  int levels = 0;
+  while ((int64_t(1) << levels) < L.max_chunks) ++levels;
+  for (int tl = 0; tl < levels; ++tl) {
+    // a merge of two triangles costs (2/3) m^3 flops; n_items - n_nodes merges in all
+    const double pairs = tl == 0 ? (double)(L.n_items - L.n_nodes) : 0.0;
+    ProfScope ps(K_COMBINE, s, 1, pairs, pairs * (2.0 / 3.0) * dm * dm * dm);
+    CUDA_TRY(t, launch_combine(t, depth, tl, t->Rbuf, s), "combine launch");
+  }
+  {
+    ProfScope ps(K_BACKSOLVE, s, 1, (double)L.n_nodes, (double)L.n_nodes * (dm - 1) * (dm - 1));
+    CUDA_TRY(t, launch_backsolve(t, depth, t->Rbuf, s), "back-solve launch");
+  }
+  {
+    ProfScope ps(K_RESIDUAL, s, 1, rows, L.horner_flops);
+    CUDA_TRY(t, launch_residual(t, depth, s), "residual launch");
+  }
+  {
+    ProfScope ps(K_CHILD, s, 2, rows, 2.0 * rows);
+    CUDA_TRY(t, launch_child_stats(t, depth, s), "child statistics launch");
+  }
+  {
+    ProfScope ps(K_HCOEF, s, 1, (double)L.n_nodes, 0.0);
+    CUDA_TRY(t, launch_make_cum(t, depth, s), "cumulative polynomials launch");
+  }
+  return FMT_OK;
+}
+
+// Graph form of a level step: the launches are captured on a private stream
+// of this host thread and replayed on s.  The executable graph of each
+// (device, depth) is kept per thread and updated in place when the captured
+// structure matches (same kernels, same node count), else re-instantiated.
+struct GraphSlots {
+  cudaStream_t stream[64] = {};
+  cudaGraphExec_t exec[64][FMT_MAX_DEPTH + 1] = {};
+  ~GraphSlots() {
+    for (int d = 0; d < 64; ++d) {
+      for (int l = 0; l <= FMT_MAX_DEPTH; ++l)
+        if (exec[d][l]) cudaGraphExecDestroy(exec[d][l]);
+      if (stream[d]) cudaStreamDestroy(stream[d]);
+    }
+  }
+};
+thread_local GraphSlots g_graphs;
+
+fmt_status fit_level_graph(fmt_tree* t, int depth, cudaStream_t s) {
+  const int dev = t->device;
+  cudaStream_t& cs = g_graphs.stream[dev];
+  if (!cs) CUDA_TRY(t, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+  CUDA_TRY(t, cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed), "begin capture");
+  const fmt_status st = fit_level_launches(t, depth, cs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+  if (st != FMT_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+  if (ce != cudaSuccess || !g) return set_err(t, FMT_ECUDA, "end capture: %s", cudaGetErrorString(ce));
+  cudaGraphExec_t& ex = g_graphs.exec[dev][depth];
+  bool reused = false;
+  if (ex) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ex, g, &info) == cudaSuccess) {
+      reused = true;
+    } else {
+      cudaGetLastError();
+      cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+  }
+  if (!ex) {
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    if (ie != cudaSuccess) {
+      ex = nullptr;
+      cudaGraphDestroy(g);
+      return set_err(t, FMT_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+    }
+  }
+  cudaGraphDestroy(g);
+  {
+    ProfScope ps(K_GRAPH, s, 1, reused ? 1.0 : 0.0, 0.0);
+    CUDA_TRY(t, cudaGraphLaunch(ex, s), "graph launch");
   }
   return FMT_OK;
 }
@@ -615,7 +722,6 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
   if (t->done || depth != t->next_fit)
     return set_err(t, FMT_EINVAL, "fit_level(%d) out of order (expected %d)", depth, t->done ? -1 : t->next_fit);
   fmt_level& L = t->lv[depth];
-  const int m = L.max_m;
   const size_t need = (size_t)L.r_total;
   if (need > t->Rbuf_cap) {
     if (t->Rbuf) tfree_one(t, t->Rbuf, s);
@@ -624,38 +730,11 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
     TRY(talloc(t, &t->Rbuf, (int64_t)need, s));
     t->Rbuf_cap = need;
   }
-  const double dm = (double)m, rows = (double)L.n_points;
-  if (t->P.precision == FMT_MIXED) TRY(fit_level_mixed(t, depth, s));
-  {
-    // Householder on [Lambda | r]: 2 m^2 flops per row (m = nmono + 1 of the row's node);
-    // on the mixed path only the nodes it left to FP64 are factorised here
-    ProfScope ps(K_TILE_QR, s, 1, rows, t->P.precision == FMT_MIXED ? 0.0 : L.qr_flops);
-    CUDA_TRY(t, launch_tile_qr(t, depth, t->Rbuf, s), "tile QR launch");
-  }
-  int levels = 0;
-  while ((int64_t(1) << levels) < L.max_chunks) ++levels;
-  for (int tl = 0; tl < levels; ++tl) {
-    // a merge of two triangles costs (2/3) m^3 flops; n_items - n_nodes merges in all
-    const double pairs = tl == 0 ? (double)(L.n_items - L.n_nodes) : 0.0;
-    ProfScope ps(K_COMBINE, s, 1, pairs, pairs * (2.0 / 3.0) * dm * dm * dm);
-    CUDA_TRY(t, launch_combine(t, depth, tl, t->Rbuf, s), "combine launch");
-  }
-  {
-    ProfScope ps(K_BACKSOLVE, s, 1, (double)L.n_nodes, (double)L.n_nodes * (dm - 1) * (dm - 1));
-    CUDA_TRY(t, launch_backsolve(t, depth, t->Rbuf, s), "back-solve launch");
-  }
-  {
-    ProfScope ps(K_RESIDUAL, s, 1, rows, L.horner_flops);
-    CUDA_TRY(t, launch_residual(t, depth, s), "residual launch");
-  }
-  {
-    ProfScope ps(K_CHILD, s, 2, rows, 2.0 * rows);
-    CUDA_TRY(t, launch_child_stats(t, depth, s), "child statistics launch");
-  }
-  {
-    ProfScope ps(K_HCOEF, s, 1, (double)L.n_nodes, 0.0);
-    CUDA_TRY(t, launch_make_cum(t, depth, s), "cumulative polynomials launch");
-  }
+  if (t->P.precision == FMT_MIXED) TRY(ensure_mixed(t, depth, s));  // allocations precede any capture
+  if (t->P.options & FMT_OPT_GRAPH)
+    TRY(fit_level_graph(t, depth, s));
+  else
+    TRY(fit_level_launches(t, depth, s));
   L.fitted = true;
   t->next_fit = -1;
   t->next_refine = depth;

@@ -260,11 +260,13 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
 }
 
 // Persistent CTAs take work items from a queue in the order of `sched`
-// (largest items first), so the longest chunks start early.
-template <int RPT>
-__global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
+// (largest items first), so the longest chunks start early.  NW warps per
+// CTA (the autotuner picks 4 or 8).
+template <int RPT, int NW>
+__global__ void __launch_bounds__(32 * NW) k_tile_qr(QRArgs a) {
   extern __shared__ double smem[];
-  constexpr int NB = 4 * RPT;
+  constexpr int NB = 4 * RPT, NT = 32 * NW;
+  static_assert(NB <= NT, "one thread generates each row of a block");
   double* Bs = smem;
   double* Rs = smem + NB * a.ld_max;
   double* sc = Rs + 2 * a.ld_max;
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
     const NodeGeom g = node_geom(a, node);
     const int m = g.m, q = g.q, ldB = g.ldB;
     double* R = a.R + a.item_roff[item];
-    for (int e = threadIdx.x; e < m * m; e += kQRThreads) {
+    for (int e = threadIdx.x; e < m * m; e += NT) {
       const int j = e / m, k = e - j * m;
       if (k >= j) R[e] = 0.0;
     }
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(kQRThreads) k_tile_qr(QRArgs a) {
         }
       }
       __syncthreads();
-      absorb_block<RPT, kQRThreads / 32>(Bs, ldB, 0, m, R, Rs, sc, -1);
+      absorb_block<RPT, NW>(Bs, ldB, 0, m, R, Rs, sc, -1);
     }
   }
 }
@@ -778,16 +780,13 @@ __global__ void __launch_bounds__(128) k_child_sums(ChildArgs a) {
   }
 }
 
-template <int RPT>
+template <int RPT, int NW>
 cudaError_t set_smem_attr(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_tile_qr<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_tile_qr<RPT, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_combine<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// 64-bit shared accesses are served per half-warp (16 lanes = 4 columns x 4
-// row groups); with ldB = 4 (mod 16) doubles the four row groups fall into
-// distinct 32-byte bank segments, so the quads' accesses are conflict free.
 int ld_for(int m) { return fmt_ld_for(m); }
 
 QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
@@ -825,29 +824,122 @@ int qr_rows_per_block(int m) {
   return 16;
 }
 
-// row block + two rows of R + reflector scalars (2 steps x 2)
 size_t qr_smem_bytes(int m, int rows) { return ((size_t)(rows + 2) * ld_for(m) + 4) * sizeof(double); }
 
-template <int RPT>
+// ------------------------------------------------------------ launch table
+// One QR launch configuration per degree: the built-in rule, or an entry
+// from the autotuner / fmt_tune_set.
+namespace {
+std::mutex g_tune_mu;
+fmt_tune_entry g_tune[FMT_MAX_DEGREE + 1];  // zero: source 0 (built-in rule)
+
+int degree_of_m(int m) {
+  for (int p = 0; p <= FMT_MAX_DEGREE; ++p)
+    if (fmt_nmono_d(p) + 1 == m) return p;
+  return -1;
+}
+
+fmt_tune_entry builtin_entry(int p) {
+  fmt_tune_entry e{};
+  e.degree = p;
+  e.rows = qr_rows_per_block(fmt_nmono_d(p) + 1);
+  e.warps = 4;
+  e.chunk_factor = 4;
+  e.merge = 0;
+  e.source = 0;
+  return e;
+}
+
+bool entry_ok(const fmt_tune_entry& e) {
+  if (e.degree < 0 || e.degree > FMT_MAX_DEGREE) return false;
+  if (e.source == 0) return true;
+  if (e.rows != 16 && e.rows != 32 && e.rows != 64) return false;
+  if (e.warps != 4 && e.warps != 8) return false;
+  if (e.chunk_factor != 1 && e.chunk_factor != 2 && e.chunk_factor != 4 && e.chunk_factor != 8 &&
+      e.chunk_factor != 16)
+    return false;
+  if (e.merge != 0 && e.merge != 1) return false;
+  return qr_smem_bytes(fmt_nmono_d(e.degree) + 1, e.rows) <= kQRSmemMax;
+}
+}  // namespace
+
+QRConfig qr_config(int m) {
+  const int p = degree_of_m(m);
+  fmt_tune_entry e;
+  if (p < 0) {
+    e = builtin_entry(0);
+    e.rows = qr_rows_per_block(m);
+  } else {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    e = g_tune[p].source != 0 ? g_tune[p] : builtin_entry(p);
+  }
+  return QRConfig{e.rows, e.warps, e.chunk_factor, e.merge};
+}
+
+fmt_status tune_install(const fmt_tune_entry& in) {
+  if (!entry_ok(in)) return FMT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[in.degree] = in;
+  if (in.source == 0) g_tune[in.degree] = fmt_tune_entry{};
+  return FMT_OK;
+}
+
+fmt_tune_entry tune_current(int p) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune[p].source != 0 ? g_tune[p] : builtin_entry(p);
+}
+
+namespace {
+template <int RPT, int NW>
 int resident_for(size_t smem) {
   int per_sm = 0;
-  if (set_smem_attr<RPT>(smem) != cudaSuccess) return 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_qr<RPT>, kQRThreads, smem) != cudaSuccess) {
+  if (set_smem_attr<RPT, NW>(smem) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_qr<RPT, NW>, 32 * NW, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
   return per_sm > 0 ? per_sm : 1;
 }
 
+template <int RPT, int NW>
+cudaError_t tile_launch(const QRArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = set_smem_attr<RPT, NW>(smem);
+  if (e != cudaSuccess) return e;
+  k_tile_qr<RPT, NW><<<grid, 32 * NW, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int RPT, int NW>
+cudaError_t combine_launch(const QRArgs& a, unsigned grid, size_t smem, cudaStream_t s, int level) {
+  cudaError_t e = set_smem_attr<RPT, NW>(smem);
+  if (e != cudaSuccess) return e;
+  k_combine<RPT><<<grid, 32 * kCombineWarps, smem, s>>>(a, level);
+  return cudaGetLastError();
+}
+
+// the kernels of one (rows, warps) configuration
+struct QROps {
+  int (*resident)(size_t);
+  cudaError_t (*tile)(const QRArgs&, unsigned, size_t, cudaStream_t);
+  cudaError_t (*combine)(const QRArgs&, unsigned, size_t, cudaStream_t, int);
+};
+template <int RPT, int NW>
+QROps ops_for() {
+  return QROps{&resident_for<RPT, NW>, &tile_launch<RPT, NW>, &combine_launch<RPT, NW>};
+}
+QROps qr_ops(const QRConfig& c) {
+  if (c.warps == 8) return c.rows == 64 ? ops_for<16, 8>() : c.rows == 32 ? ops_for<8, 8>() : ops_for<4, 8>();
+  return c.rows == 64 ? ops_for<16, 4>() : c.rows == 32 ? ops_for<8, 4>() : ops_for<4, 4>();
+}
+}  // namespace
+
 int qr_resident_ctas(int m) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm <= 0) nsm = 1;
-  const int rows = qr_rows_per_block(m);
-  const size_t smem = qr_smem_bytes(m, rows);
-  const int per_sm = rows == 64 ? resident_for<16>(smem) : rows == 32 ? resident_for<8>(smem) : resident_for<4>(smem);
-  return nsm * per_sm;
+  const QRConfig c = qr_config(m);
+  return nsm * qr_ops(c).resident(qr_smem_bytes(m, c.rows));
 }
 
 cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t s) {
@@ -855,27 +947,13 @@ cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t
   const int64_t n_items = t->lv[depth].n_items;
   if (n_items <= 0) return cudaSuccess;
   const int mx = t->lv[depth].max_m;
-  const int rows = qr_rows_per_block(mx);
-  const size_t smem = qr_smem_bytes(mx, rows);
+  const QRConfig c = qr_config(mx);
+  const size_t smem = qr_smem_bytes(mx, c.rows);
   int64_t grid = qr_resident_ctas(mx);
   if (grid > n_items) grid = n_items;
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  switch (rows) {
-    case 64:
-      if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;
-      k_tile_qr<16><<<(unsigned)grid, kQRThreads, smem, s>>>(a);
-      break;
-    case 32:
-      if ((e = set_smem_attr<8>(smem)) != cudaSuccess) return e;
-      k_tile_qr<8><<<(unsigned)grid, kQRThreads, smem, s>>>(a);
-      break;
-    default:
-      if ((e = set_smem_attr<4>(smem)) != cudaSuccess) return e;
-      k_tile_qr<4><<<(unsigned)grid, kQRThreads, smem, s>>>(a);
-      break;
-  }
-  return cudaGetLastError();
+  return qr_ops(c).tile(a, (unsigned)grid, smem, s);
 }
 
 cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s) {
@@ -884,31 +962,18 @@ cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double*
   if (n_items <= 1) return cudaSuccess;
   cudaError_t e;
   const int mx = t->lv[depth].max_m;
+  const QRConfig cfg = qr_config(mx);
   const size_t msm = merge_smem_bytes(mx);
-  if (msm <= 200 * 1024) {
+  if (cfg.merge == 0 && msm <= 200 * 1024) {
     if ((e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm)) != cudaSuccess)
       return e;
     k_merge<<<(unsigned)n_items, kMergeThreads, msm, s>>>(a, tree_level);
     return cudaGetLastError();
   }
-  // large degrees: the packed triangle does not fit; merge in row blocks
-  const int rows = qr_rows_per_block(mx);
-  const size_t smem = qr_smem_bytes(mx, rows);
-  switch (rows) {
-    case 64:
-      if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;
-      k_combine<16><<<(unsigned)n_items, 32 * kCombineWarps, smem, s>>>(a, tree_level);
-      break;
-    case 32:
-      if ((e = set_smem_attr<8>(smem)) != cudaSuccess) return e;
-      k_combine<8><<<(unsigned)n_items, 32 * kCombineWarps, smem, s>>>(a, tree_level);
-      break;
-    default:
-      if ((e = set_smem_attr<4>(smem)) != cudaSuccess) return e;
-      k_combine<4><<<(unsigned)n_items, 32 * kCombineWarps, smem, s>>>(a, tree_level);
-      break;
-  }
-  return cudaGetLastError();
+  // the packed triangle does not fit (large degrees) or the configuration
+  // asks for row blocks
+  const size_t smem = qr_smem_bytes(mx, cfg.rows);
+  return qr_ops(cfg).combine(a, (unsigned)n_items, smem, s, tree_level);
 }
 
 cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream_t s) {
@@ -1144,5 +1209,21 @@ extern "C" fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const doubl
     snprintf(msg, sizeof(msg), "fmt_fit_node_static: launch failed: %s", cudaGetErrorString(e));
     return fmt_set_error(FMT_ECUDA, msg);
   }
+  return FMT_OK;
+}
+
+extern "C" fmt_status fmt_tune_get(int32_t degree, fmt_tune_entry* out) {
+  if (!out || degree < 0 || degree > FMT_MAX_DEGREE)
+    return fmt_set_error(FMT_EINVAL, "fmt_tune_get: degree outside [0, 14] or NULL output");
+  *out = tune_current(degree);
+  return FMT_OK;
+}
+
+extern "C" fmt_status fmt_tune_set(const fmt_tune_entry* entry) {
+  if (!entry) return fmt_set_error(FMT_EINVAL, "fmt_tune_set: NULL entry");
+  if (tune_install(*entry) != FMT_OK)
+    return fmt_set_error(FMT_EINVAL,
+                         "fmt_tune_set: bad entry (degree 0..14, rows 16/32/64 within 227 KB of shared memory, "
+                         "warps 4/8, chunk_factor 1/2/4/8/16, merge 0/1)");
   return FMT_OK;
 }

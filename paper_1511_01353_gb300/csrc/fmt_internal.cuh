@@ -309,7 +309,16 @@ cudaError_t launch_plan_root(const fmt_tree* t, int64_t chunk_rows_fixed, int64_
                              fmt_plan_out* d_plan, cudaStream_t s);
 
 // fit
-int qr_rows_per_block(int m);
+int qr_rows_per_block(int m);  // the built-in rule for rows per QR block
+// QR launch configuration of a level whose largest node has m columns (the
+// autotuner's entry for that degree, else the built-in rule)
+struct QRConfig {
+  int rows, warps, chunk_factor, merge;
+};
+QRConfig qr_config(int m);
+constexpr size_t kQRSmemMax = 227 * 1024 - 64;  // dynamic shared memory of one QR CTA
+fmt_status tune_install(const fmt_tune_entry& e);  // FMT_EINVAL on a bad entry
+fmt_tune_entry tune_current(int degree);
 int qr_resident_ctas(int m);  // SMs x resident QR CTAs per SM
 size_t qr_smem_bytes(int m, int rows);
 cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t s);

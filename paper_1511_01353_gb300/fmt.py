@@ -26,6 +26,7 @@ FMT_FLAG_NEAR_TAU, FMT_FLAG_RANK, FMT_FLAG_DEG_CLAMPED, FMT_FLAG_MIXED = 1, 2, 4
 FMT_FLAG_MIXED_SLOW, FMT_FLAG_MIXED_PIVOT = 16, 32
 MIXED_MAX_DEGREE = 9
 MIXED_MAX_SWEEPS = 3
+FMT_OPT_GRAPH = 1
 MAX_DEPTH = 21
 _STATUS = {0: "FMT_OK", 1: "FMT_EINVAL", 2: "FMT_ENOMEM", 3: "FMT_ECUDA", 4: "FMT_ETIMEOUT", 5: "FMT_EINTERNAL"}
 
@@ -40,7 +41,7 @@ class fmt_params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("min_pts", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("tol_rel", ctypes.c_double), ("lo", ctypes.c_double * 3),
                 ("side", ctypes.c_double), ("chunk_rows", ctypes.c_int64), ("sweeps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("options", ctypes.c_int32)]
 
 
 _NL = MAX_DEPTH + 1
@@ -81,9 +82,21 @@ EXPORTED = ["fmt_nmono", "oct_build", "oct_build_batch", "fit_level", "refine", 
             "fmt_tree_stats", "fmt_tree_export",
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
             "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static", "fmt_server_create",
-            "fmt_server_submit", "fmt_server_wait", "fmt_server_destroy", "fmt_server_clock"]
+            "fmt_server_submit", "fmt_server_wait", "fmt_server_destroy", "fmt_server_clock", "fmt_autotune",
+            "fmt_tune_get", "fmt_tune_set"]
 STATIC_MAX_DEGREE = 8
 PROFILE_CLASSES = 24
+
+
+class fmt_tune_entry(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("rows", ctypes.c_int32), ("warps", ctypes.c_int32),
+                ("chunk_factor", ctypes.c_int32), ("merge", ctypes.c_int32), ("source", ctypes.c_int32),
+                ("sample_points", ctypes.c_int64), ("ms", ctypes.c_double), ("ms_builtin", ctypes.c_double),
+                ("trials", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+TUNE_FIELDS = ("degree", "rows", "warps", "chunk_factor", "merge", "source", "sample_points", "ms", "ms_builtin",
+               "trials")
 
 
 class fmt_profile(ctypes.Structure):
@@ -151,6 +164,12 @@ def load(build: bool = True):
         L.fmt_server_clock.restype = ctypes.c_double
         L.fmt_fit_node_static.argtypes = [i32, i64, P, P, P, P, P, ctypes.c_double, P, P, P, P]
         L.fmt_fit_node_static.restype = ctypes.c_int
+        L.fmt_autotune.argtypes = [i32, i64, P, ctypes.POINTER(fmt_tune_entry)]
+        L.fmt_autotune.restype = ctypes.c_int
+        L.fmt_tune_get.argtypes = [i32, ctypes.POINTER(fmt_tune_entry)]
+        L.fmt_tune_get.restype = ctypes.c_int
+        L.fmt_tune_set.argtypes = [ctypes.POINTER(fmt_tune_entry)]
+        L.fmt_tune_set.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -196,12 +215,13 @@ class Tree:
 
 
 def make_params(degree, max_depth, min_pts, tol_rel, lo=(0.0, 0.0, 0.0), side=1.0, chunk_rows=0,
-                precision=FMT_FP64, sweeps=0):
-    """fmt_params; precision FMT_FP64 or FMT_MIXED, sweeps (mixed only): 0 = 3, -1 = none."""
+                precision=FMT_FP64, sweeps=0, graph=False):
+    """fmt_params; precision FMT_FP64 or FMT_MIXED, sweeps (mixed only): 0 = 3, -1 = none;
+    graph: capture each fit_level in a CUDA graph (FMT_OPT_GRAPH)."""
     p = fmt_params()
     p.degree, p.max_depth, p.min_pts, p.precision = degree, max_depth, min_pts, precision
     p.sweeps = sweeps
-    p.reserved = 0
+    p.options = FMT_OPT_GRAPH if graph else 0
     p.tol_rel = tol_rel
     for a in range(3):
         p.lo[a] = lo[a]
@@ -322,6 +342,35 @@ def fmt_probe_dfma(iters: int = 20000, stream=None) -> float:
     v = ctypes.c_double(0.0)
     _check(load().fmt_probe_dfma(iters, ctypes.byref(v), _stream_handle(stream)))
     return float(v.value)
+
+
+def _entry_dict(e: fmt_tune_entry) -> dict:
+    return {k: getattr(e, k) for k in TUNE_FIELDS}
+
+
+def fmt_autotune(degree: int, sample_points: int = 0, stream=None) -> dict:
+    """Time QR launch configurations for `degree` and install the fastest (synchronises)."""
+    e = fmt_tune_entry()
+    _check(load().fmt_autotune(degree, sample_points, _stream_handle(stream), ctypes.byref(e)))
+    return _entry_dict(e)
+
+
+def fmt_tune_get(degree: int) -> dict:
+    """The QR launch configuration in force for `degree` (host only)."""
+    e = fmt_tune_entry()
+    _check(load().fmt_tune_get(degree, ctypes.byref(e)))
+    return _entry_dict(e)
+
+
+def fmt_tune_set(entry: dict):
+    """Install a configuration (e.g. saved from fmt_autotune); source 0 restores the built-in rule."""
+    e = fmt_tune_entry()
+    for k in TUNE_FIELDS:
+        if k in entry:
+            setattr(e, k, entry[k])
+    if "source" not in entry:
+        e.source = 2
+    _check(load().fmt_tune_set(ctypes.byref(e)))
 
 
 def fmt_fit_node_static(degree: int, x, y, z, r_in, coef, r_out, flags=None, lo=(0.0, 0.0, 0.0), side=1.0,

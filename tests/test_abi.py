@@ -47,6 +47,9 @@ int main(void){
          offsetof(fmt_export_header, level_nodes));
   printf("%zu %zu %zu %zu\n", offsetof(fmt_params, sweeps), offsetof(fmt_stats, mixed),
          offsetof(fmt_stats, mixed_points), sizeof(fmt_profile));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(fmt_params, options), sizeof(fmt_tune_entry),
+         offsetof(fmt_tune_entry, sample_points), offsetof(fmt_tune_entry, ms_builtin),
+         offsetof(fmt_tune_entry, trials));
   return 0;
 }
 '''
@@ -73,6 +76,35 @@ def test_struct_layouts_match_c():
     assert v[9] == F.fmt_stats.mixed.offset
     assert v[10] == F.fmt_stats.mixed_points.offset
     assert v[11] == ctypes.sizeof(F.fmt_profile)
+    assert v[12] == F.fmt_params.options.offset
+    assert v[13] == ctypes.sizeof(F.fmt_tune_entry)
+    assert v[14] == F.fmt_tune_entry.sample_points.offset
+    assert v[15] == F.fmt_tune_entry.ms_builtin.offset
+    assert v[16] == F.fmt_tune_entry.trials.offset
+
+
+def test_tune_table_is_host_only_and_checks_entries():
+    # built-in rule: 64-row blocks while two CTAs fit (ld(166) = 180), 32 rows
+    # for degree 14 (ld(681) = 692), 4 warps, chunks of 4 m rows, packed merge
+    e = F.fmt_tune_get(8)
+    assert (e["source"], e["rows"], e["warps"], e["chunk_factor"], e["merge"]) == (0, 64, 4, 4, 0)
+    assert F.fmt_tune_get(14)["rows"] == 32
+    F.fmt_tune_set(dict(degree=8, rows=16, warps=8, chunk_factor=2, merge=1))
+    try:
+        g = F.fmt_tune_get(8)
+        assert (g["source"], g["rows"], g["warps"], g["chunk_factor"], g["merge"]) == (2, 16, 8, 2, 1)
+        assert F.fmt_tune_get(7)["source"] == 0  # other degrees untouched
+        good = dict(degree=8, rows=32, warps=4, chunk_factor=4, merge=0)
+        for k, v in (("rows", 48), ("warps", 6), ("chunk_factor", 3), ("merge", 2), ("degree", 15),
+                     ("degree", -1)):
+            with pytest.raises(F.FmtError):
+                F.fmt_tune_set(dict(good, **{k: v}))
+        with pytest.raises(F.FmtError):  # 66 rows x 692 doubles exceed 227 KB
+            F.fmt_tune_set(dict(degree=14, rows=64, warps=4, chunk_factor=4, merge=0))
+        assert F.fmt_tune_get(8)["rows"] == 16  # a rejected entry changes nothing
+    finally:
+        F.fmt_tune_set(dict(degree=8, source=0))
+    assert F.fmt_tune_get(8)["source"] == 0
 
 
 def test_nmono_matches_paper_values():
@@ -83,7 +115,8 @@ def test_nmono_matches_paper_values():
 @pytest.mark.parametrize("field,value", [("degree", 15), ("degree", -1), ("max_depth", 22), ("min_pts", -3),
                                          ("tol_rel", -1.0), ("tol_rel", float("nan")), ("side", 0.0),
                                          ("precision", 2), ("precision", -1), ("chunk_rows", -64),
-                                         ("sweeps", 4), ("sweeps", -2), ("reserved", 1)])
+                                         ("sweeps", 4), ("sweeps", -2), ("options", 2),
+                                         ("options", -1)])
 def test_oct_build_rejects_bad_params_before_device_work(field, value):
     lib = F.load()
     p = F.make_params(4, 3, 64, 1e-4)
