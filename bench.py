@@ -633,10 +633,18 @@ def main():
         fscale = max(float(np.max(np.abs(w.f))), 1e-300)
         mst = ost if oprec == "mixed" else stats
         mex = oex if oprec == "mixed" else ex
-        fallback = {"not_converged_nodes": int(np.sum((mex.flags & F.FMT_FLAG_MIXED_SLOW) != 0)),
-                    "not_converged_points": int(np.sum(mex.count[(mex.flags & F.FMT_FLAG_MIXED_SLOW) != 0])),
-                    "small_pivot_nodes": int(np.sum((mex.flags & F.FMT_FLAG_MIXED_PIVOT) != 0)),
-                    "small_pivot_points": int(np.sum(mex.count[(mex.flags & F.FMT_FLAG_MIXED_PIVOT) != 0]))}
+        def nodes_pts(sel):
+            return int(np.sum(sel)), int(np.sum(mex.count[sel]))
+        fl = mex.flags
+        tc = (fl & F.FMT_FLAG_MIXED) != 0
+        t2 = (fl & F.FMT_FLAG_MIXED_FP64) != 0
+        # tensor-core tier: fitted there; its failures (small pivot / not converged / degree > 9) go to the
+        # FP64 normal-equations tier, and what that tier cannot fit to the FP64 Householder path
+        fallback = {"tensor_tier_nodes": nodes_pts(tc & ~t2)[0], "tensor_tier_points": nodes_pts(tc & ~t2)[1],
+                    "fp64_tier_nodes": nodes_pts(t2)[0], "fp64_tier_points": nodes_pts(t2)[1],
+                    "householder_nodes": nodes_pts(~tc)[0], "householder_points": nodes_pts(~tc)[1],
+                    "tensor_tier_small_pivot_nodes": nodes_pts((fl & F.FMT_FLAG_MIXED_PIVOT) != 0)[0],
+                    "tensor_tier_not_converged_nodes": nodes_pts((fl & F.FMT_FLAG_MIXED_SLOW) != 0)[0]}
         mixed_pts = sum(int(mst.mixed_points[d]) for d in range(mst.n_levels))
         all_pts = sum(int(mst.points[d]) for d in range(mst.n_levels))
         gram = oprof.get("mixed_gram", {}) if oprec == "mixed" else prof.get("mixed_gram", {})
@@ -647,7 +655,7 @@ def main():
                  "max_abs_diff_vs_headline_over_max_f": float(np.max(np.abs(opred - pred))) / fscale,
                  "mixed_share_of_fitted_points": mixed_pts / max(all_pts, 1),
                  "mixed_nodes": int(sum(mst.mixed[d] for d in range(mst.n_levels))),
-                 "fp64_fallback": fallback,
+                 "tiers": fallback,
                  "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps}
                              for k, v in oprof.items() if v["launches"]},
                  "note": "error vs the FP64 GPU path, which matches the FP64 oracle to 1e-10 max|f|; "

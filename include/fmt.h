@@ -62,8 +62,9 @@ typedef enum {
 #define FMT_FLAG_RANK 2         /* back substitution dropped dependent columns */
 #define FMT_FLAG_DEG_CLAMPED 4  /* root with N < nmono: degree lowered */
 #define FMT_FLAG_MIXED 8        /* fitted by the mixed-precision path */
-#define FMT_FLAG_MIXED_SLOW 16  /* mixed path: refinement not converged, refitted in FP64 */
-#define FMT_FLAG_MIXED_PIVOT 32 /* mixed path: Cholesky pivot too small, refitted in FP64 */
+#define FMT_FLAG_MIXED_SLOW 16  /* mixed path: refinement not converged (tensor-core tier, or both tiers) */
+#define FMT_FLAG_MIXED_PIVOT 32 /* mixed path: a Cholesky pivot too small (tensor-core tier, or both tiers) */
+#define FMT_FLAG_MIXED_FP64 64  /* mixed path: fitted by its FP64 normal-equations tier (with FMT_FLAG_MIXED) */
 
 /*
  * Parameters of Alg. 1 (L, nmono, tau and the root box P) plus the depth and
@@ -159,14 +160,23 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  *  - F is converted exactly to Alg. 2's moment basis in the node frame (the
  *    stored coefficients have the FP64 path's layout), and r <- r - Lambda F
  *    runs in FP64 as on the FP64 path.
- * A node whose Cholesky pivot falls below 1e-6 of its diagonal entry, whose
- * fit after the last sweep is not within 1e-7 of converged (the last change
- * |Lambda d|, or its extrapolation by the ratio of the last two changes,
- * above 1e-7 |Lambda F|), or whose polynomial may still change by more than
- * 1e-8 max|f| somewhere in the node box (the same extrapolation of a bound
- * of the last change over the box), whose
- * degree exceeds FMT_MIXED_MAX_DEGREE, or whose root degree was clamped, is
- * refitted by the FP64 path; nodes fitted the mixed way carry FMT_FLAG_MIXED.
+ * A node whose Cholesky pivot falls below 1e-6 of its diagonal entry
+ * (FMT_FLAG_MIXED_PIVOT), or whose root degree was clamped, is refitted by
+ * the FP64 Householder path.  A node whose fit after the last sweep is not
+ * within 1e-7 of converged (the last change |Lambda d|, or its extrapolation
+ * by the ratio of the last two changes, above 1e-7 |Lambda F|), or whose
+ * polynomial may still change by more than 1e-8 max|f| somewhere in the node
+ * box (the same extrapolation of a bound of the last change over the box)
+ * (FMT_FLAG_MIXED_SLOW), and every node of degree above FMT_MIXED_MAX_DEGREE,
+ * goes to the mixed path's FP64 tier: the same basis, its Gram [B|r]^T[B|r]
+ * formed in FP64 on the CUDA cores (n m^2 flops, half of Householder's), an
+ * FP64 Cholesky (pivot floor 1e-12 of the diagonal), and `sweeps` corrected
+ * semi-normal steps with FP64 residuals and FP64 projections under the same
+ * convergence tests, plus one more: the change of the polynomial over the
+ * box caused by the FP64 rounding of the residual (a perturbation of that
+ * size solved through R^T R) must stay within 1e-9 max|f|.  Nodes this tier
+ * fits carry FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64; the rest are refitted by
+ * Householder.  Nodes fitted the mixed way carry FMT_FLAG_MIXED.
  * The mixed path targets an interpolant within 1e-6 max|f| of the FP64
  * path (not the 1e-10 of FP64), and its tree may differ where a refinement
  * decision is that close to tau.  FMT_ETIMEOUT if a tensor-core completion

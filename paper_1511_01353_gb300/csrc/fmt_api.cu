@@ -57,13 +57,15 @@ fmt_status device_init(int dev) {
 enum {
   K_CHECK = 0, K_MORTON, K_SORT, K_GATHER, K_PLAN, K_TILE_QR, K_COMBINE, K_BACKSOLVE,
   K_RESIDUAL, K_CHILD, K_REFINE, K_EVALUATE, K_HCOEF, K_MBOX, K_MGRAM, K_MFACTOR, K_MSRESID, K_MPROJ,
-  K_MUPDATE, K_GRAPH, K_NCLASS
+  K_MUPDATE, K_GRAPH, K_DGRAM, K_DFACTOR, K_DPROJ, K_DUPDATE, K_NCLASS
 };
+static_assert(K_NCLASS <= FMT_PROFILE_CLASSES, "profile classes exceed FMT_PROFILE_CLASSES");
 const char* const kClassNames[K_NCLASS] = {"check_maxabs", "morton", "radix_sort", "gather", "plan_root",
                                            "tile_qr", "combine", "back_solve", "residual", "child_stats",
                                            "refine", "evaluate", "make_hcoef", "mixed_box", "mixed_gram",
                                            "mixed_factor", "mixed_sresid", "mixed_proj", "mixed_update",
-                                           "graph_launch"};
+                                           "graph_launch", "fp64_gram", "fp64_factor", "fp64_proj",
+                                           "fp64_update"};
 struct ProfRec {
   int k;
   cudaEvent_t a, b;
@@ -528,6 +530,13 @@ fmt_status ensure_mixed(fmt_tree* t, int depth, cudaStream_t s) {
     TRY(talloc(t, &b.gacc, 256 * L.n_items, s));
     b.cap_items = L.n_items;
   }
+  if (b.cap_dproj < L.n_items * (int64_t)t->nmono) {
+    if (b.dproj) tfree_one(t, b.dproj, s);
+    b.dproj = nullptr;
+    b.cap_dproj = 0;
+    TRY(talloc(t, &b.dproj, L.n_items * (int64_t)t->nmono, s));
+    b.cap_dproj = L.n_items * (int64_t)t->nmono;
+  }
   // basis cache of the sweeps, unless it would exceed kCacheCap (then each sweep regenerates)
   const size_t cache = mixed_cache_bytes(t, depth);
   constexpr size_t kCacheCap = (size_t)16 << 30;
@@ -581,6 +590,30 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
     {
       ProfScope ps(K_MUPDATE, s, 1, nodes, 0.0);
       CUDA_TRY(t, launch_mixed_update(t, depth, b, k == sweeps - 1, s), "mixed update launch");
+    }
+  }
+  // FP64 normal-equations tier for the nodes the tensor-core tier left
+  // (its Gram and R live in the level's QR scratch, t->Rbuf)
+  {
+    ProfScope ps(K_DGRAM, s, 1, rows, 0.0);
+    CUDA_TRY(t, launch_tier2_gram(t, depth, b, s), "FP64 Gram launch");
+  }
+  {
+    ProfScope ps(K_DFACTOR, s, 1, nodes, 0.0);
+    CUDA_TRY(t, launch_tier2_factor(t, depth, b, s), "FP64 factor launch");
+  }
+  for (int k = 0; k < sweeps; ++k) {
+    {
+      ProfScope ps(K_MSRESID, s, 1, rows, 0.0);
+      CUDA_TRY(t, launch_tier2_sweep(t, depth, b, 0, false, s), "FP64 sweep residual launch");
+    }
+    {
+      ProfScope ps(K_DPROJ, s, 1, rows, 0.0);
+      CUDA_TRY(t, launch_tier2_sweep(t, depth, b, 1, false, s), "FP64 projection launch");
+    }
+    {
+      ProfScope ps(K_DUPDATE, s, 1, nodes, 0.0);
+      CUDA_TRY(t, launch_tier2_sweep(t, depth, b, 2, k == sweeps - 1, s), "FP64 update launch");
     }
   }
   return FMT_OK;

@@ -237,10 +237,11 @@ struct fmt_mixed_bufs {
   double* acc = nullptr;                // acc_stride per item
   int64_t acc_stride = 0;
   double* gacc = nullptr;               // 256 per item
+  double* dproj = nullptr;              // FP64 tier: nmono per item (B^T s)
   double* lcoef = nullptr;              // nmono per node
   uint8_t* cache = nullptr;             // digit tiles of the projection basis, or NULL
   size_t cap_cache = 0;
-  int64_t cap_nodes = 0, cap_items = 0, cap_acc = 0;
+  int64_t cap_nodes = 0, cap_items = 0, cap_acc = 0, cap_dproj = 0;
 };
 
 struct fmt_tree {
@@ -336,6 +337,12 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, 
 // mixed precision (fmt_mixed.cu)
 int mixed_m_cap(int max_m);            // largest m a mixed node of the level can have
 size_t mixed_acc_stride(int max_m);    // doubles of Gram accumulator per work item
+// the mixed path's FP64 normal-equations tier (fmt_mixed.cu): Gram, factor,
+// and the sweeps' parts 0 (residual), 1 (projection), 2 (update)
+cudaError_t launch_tier2_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
+cudaError_t launch_tier2_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
+cudaError_t launch_tier2_sweep(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, int part, bool last,
+                               cudaStream_t s);
 cudaError_t launch_mixed_box(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
 // cache_mode: 0 generate the basis digits, 1 generate and store them (Gram), 2 load them (projection);
 // without a cache buffer every launch generates

@@ -36,6 +36,7 @@
 // of fmt_fit.cu.
 
 #include <cuda_bf16.h>
+#include <float.h>
 
 #include "fmt_internal.cuh"
 
@@ -66,6 +67,10 @@ __host__ __device__ __forceinline__ int gram_cols(int m) {
 __host__ __device__ __forceinline__ bool mixed_ok_degree(int p) { return p >= 0 && p <= FMT_MIXED_MAX_DEGREE; }
 __device__ __forceinline__ bool mixed_eligible(const fmt_problem& pr, int depth) {
   return mixed_ok_degree(pr.degree) && !(depth == 0 && pr.q_root < pr.degree);
+}
+// the FP64 normal-equations tier takes any degree; a clamped root stays with Householder
+__device__ __forceinline__ bool tier2_eligible(const fmt_problem& pr, int depth) {
+  return pr.degree >= 1 && !(depth == 0 && pr.q_root < pr.degree);
 }
 
 // ------------------------------------------------------------------ PTX
@@ -279,6 +284,11 @@ struct MArgs {
   uint32_t cache_atom_bytes;
   int last_sweep;
   int* err;
+  int tier;                     // sweeps of tier 1 (tensor-core Gram) or tier 2 (FP64 Gram)
+  double* rbuf;                 // tier 2: per item the packed FP64 Gram, per node R (first item), in the QR scratch
+  const int64_t* item_roff;     // offset of each item's slot in rbuf
+  double* dproj;                // tier 2: per item B^T s (dstride doubles)
+  int dstride;
 };
 
 // ------------------------------------------------------------------ k_mbox
@@ -287,7 +297,7 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
   const int item = blockIdx.x;
   const int64_t node = a.item_node[item];
   const fmt_problem& pr = a.prob[a.node_prob[node]];
-  if (!mixed_eligible(pr, a.depth)) return;
+  if (!tier2_eligible(pr, a.depth)) return;  // the frame serves both tiers
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
   fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
@@ -969,7 +979,8 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
 __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
   const int item = blockIdx.x;
   const int64_t node = a.item_node[item];
-  if (!(a.flags[node] & FMT_FLAG_MIXED)) return;
+  const int32_t nf = a.flags[node];
+  if (!(nf & FMT_FLAG_MIXED) || (a.tier == 2 && !(nf & FMT_FLAG_MIXED_FP64))) return;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
@@ -1127,6 +1138,472 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ tier 2
+// Nodes the tensor-core tier could not fit (a small pivot, no convergence, or
+// a degree above FMT_MIXED_MAX_DEGREE) are fitted by corrected semi-normal
+// equations in FP64 before any falls back to Householder: the Gram of
+// [B | sig r] in FP64 on the FP64 pipe (n m^2 flops against Householder's
+// 2 n m^2), its Cholesky factor, F = R^{-1} R^{-T} B^T r, then sweeps
+// F += R^{-1} R^{-T} B^T (r - Lambda F) with the FP64 residual and an FP64
+// projection, under the convergence tests of the tensor-core tier.  The basis
+// is the same Legendre product basis in the same node frame.  The fixed point
+// of the sweeps solves B^T (r - B F) = 0 as evaluated in FP64, whose rounding
+// (about c eps |B| (|B| |F| + |r|) in the residual) moves F by up to
+// (B^T B)^{-1} of its projection: with a small residual and cancelling
+// coefficients (nearly square or clustered nodes) that is kappa times worse
+// than Householder.  So after the last sweep a perturbation of that size,
+// delta g_j = +-c eps sqrt(G_jj) (sum_k |F_k| sqrt(G_kk) + |r|) with
+// pseudo-random signs, is solved through R^T R, and the node is kept only if
+// the resulting change of the polynomial over its box stays within
+// kRoundRel max |f| (else Householder, which the mixed path is held to,
+// refits it).
+constexpr double kPivotFloor2 = 1e-12;  // FP64 Gram: a column must keep 1e-6 of its norm
+constexpr double kRoundRel = 1e-9;      // bound of the rounding-driven change over the box, relative to max |f|
+constexpr int kDT = 64;                 // Gram tile (columns)
+constexpr int kDRows = 32;              // rows per shared-memory chunk
+constexpr int kPanel = 32;              // rows per Cholesky panel
+constexpr int kRT = 4;                  // factored rows staged per update pass
+
+#define FMT_LA64(k) ((double)(2 * (k) + 1) / (double)((k) + 1))
+#define FMT_LB64(k) ((double)(k) / (double)((k) + 1))
+#define FMT_L64(k) {FMT_LA64(k), FMT_LB64(k)}
+// Bonnet's recurrence constants a_k, b_k in FP64, k = 0..13
+static __constant__ double c_leg64[FMT_MAX_DEGREE][2] = {
+    FMT_L64(0), FMT_L64(1), FMT_L64(2), FMT_L64(3),  FMT_L64(4),  FMT_L64(5),  FMT_L64(6),
+    FMT_L64(7), FMT_L64(8), FMT_L64(9), FMT_L64(10), FMT_L64(11), FMT_L64(12), FMT_L64(13)};
+#undef FMT_L64
+#undef FMT_LB64
+#undef FMT_LA64
+
+// A node whose tensor-core Cholesky met a pivot below kPivotFloor is too
+// ill-conditioned for the normal equations at the mixed path's bar as well
+// (the FP64 tier's rounding check rejects nearly all of them), so it goes to
+// Householder directly; the FP64 tier takes the nodes that did not converge
+// and those of degree above FMT_MIXED_MAX_DEGREE.
+__device__ __forceinline__ bool tier2_selected(const MArgs& a, int64_t node, const fmt_problem& pr) {
+  const int32_t f = a.flags[node];
+  return tier2_eligible(pr, a.depth) && !(f & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_PIVOT));
+}
+
+// (a, b, c) of basis column j in Alg. 2 order, packed a | b << 8 | c << 16
+__device__ __forceinline__ int col_abc(int j, int p) {
+  int r = j, la = 0;
+  while (r >= (p - la + 1) * (p - la + 2) / 2) {
+    r -= (p - la + 1) * (p - la + 2) / 2;
+    ++la;
+  }
+  int lb = 0;
+  while (r >= p - la - lb + 1) {
+    r -= p - la - lb + 1;
+    ++lb;
+  }
+  return la | (lb << 8) | (r << 16);
+}
+
+// P_0..P_p of one coordinate (FP64 recurrence): t = u 2^e
+__device__ __forceinline__ void legendre64(double t, int p, double* P) {
+  P[0] = 1.0;
+  if (p >= 1) P[1] = t;
+  for (int k = 1; k < p; ++k) P[k + 1] = fma(c_leg64[k][0] * t, P[k], -c_leg64[k][1] * P[k - 1]);
+}
+
+// The 1-D Legendre values of a chunk of rows: Pl[row][axis][0..p]
+__device__ __forceinline__ void chunk_legendre(const MArgs& a, const MFrame& F, int64_t r0, int nr, int p,
+                                               double* Pl) {
+  constexpr int P1 = FMT_MAX_DEGREE + 1;
+  const int tid = threadIdx.x;
+  if (tid < 3 * kDRows) {
+    const int row = tid / 3, ax = tid - 3 * row;
+    double* P = Pl + (row * 3 + ax) * P1;
+    if (row < nr) {
+      const double* X = ax == 0 ? a.x : ax == 1 ? a.y : a.z;
+      const double t = fmt_local(X[r0 + row], F.c[ax], F.s[ax]) * F.ex[ax];
+      legendre64(t, p, P);
+    } else {
+      for (int k = 0; k <= p; ++k) P[k] = 0.0;
+    }
+  }
+}
+
+// Packed upper triangle of one item's FP64 Gram, one 64 x 64 tile (bi, bj)
+// per CTA: 256 threads, 4 x 4 entries each (rows ty + 16 i, columns tx + 16 j
+// of the tile), rows streamed through shared memory 32 at a time.
+__global__ void __launch_bounds__(256) k_dgram(MArgs a, int npairs) {
+  constexpr int P1 = FMT_MAX_DEGREE + 1;
+  __shared__ double Pl[kDRows * 3 * P1];
+  __shared__ double As[kDRows][kDT], Bs[kDRows][kDT];
+  __shared__ int cabc[2][kDT];
+  const int item = blockIdx.x / npairs, pair = blockIdx.x - item * npairs;
+  const int64_t node = a.item_node[item];
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  if (!tier2_selected(a, node, pr)) return;
+  const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, nt = (m + kDT - 1) / kDT;
+  if (pair >= nt * (nt + 1) / 2) return;
+  int bi = 0, rem = pair;
+  while (rem >= nt - bi) {
+    rem -= nt - bi;
+    ++bi;
+  }
+  const int bj = bi + rem;
+  const bool diag = bi == bj;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
+  if (tid < 2 * kDT) {
+    const int w = tid / kDT, c = tid - w * kDT, j = (w ? bj : bi) * kDT + c;
+    cabc[w][c] = j < L ? col_abc(j, p) : -1 - (j == L);  // -2: the value column, -1: padding
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const int64_t rs = a.item_start[item], re = a.item_end[item];
+  for (int64_t r0 = rs; r0 < re; r0 += kDRows) {
+    const int nr = (int)(re - r0 < kDRows ? re - r0 : kDRows);
+    __syncthreads();  // the previous chunk's tiles are consumed
+    chunk_legendre(a, F, r0, nr, p, Pl);
+    __syncthreads();
+    for (int e = tid; e < (diag ? 1 : 2) * kDRows * kDT; e += 256) {
+      const int w = e / (kDRows * kDT), r2 = e - w * (kDRows * kDT), row = r2 / kDT, c = r2 - row * kDT;
+      const int code = cabc[w][c];
+      double v = 0.0;
+      if (row < nr) {
+        if (code >= 0) {
+          const double* P = Pl + row * 3 * P1;
+          v = P[code & 0xff] * P[P1 + ((code >> 8) & 0xff)] * P[2 * P1 + (code >> 16)];
+        } else if (code == -2) {
+          v = a.r[r0 + row] * F.sig;
+        }
+      }
+      (w ? Bs : As)[row][c] = v;
+    }
+    __syncthreads();
+    const double(*Bt)[kDT] = diag ? As : Bs;
+    for (int row = 0; row < nr; ++row) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        av[i] = As[row][ty + 16 * i];
+        bv[i] = Bt[row][tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+  }
+  double* G = a.rbuf + a.item_roff[item];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gi = bi * kDT + ty + 16 * i, gj = bj * kDT + tx + 16 * j;
+      if (gi <= gj && gj < m) G[ro_of(gi, m) + (gj - gi)] = acc[i][j];
+    }
+}
+
+// Per node: the item Grams summed (fixed order) and factorised by a blocked
+// left-looking Cholesky, 32-row panels in shared memory; R (packed, column L
+// = the scaled R^{-T} B^T r, then rho) overwrites the first item's slot, whose
+// rows below the current panel are still the Gram's.  Then F = R^{-1} y.
+__global__ void __launch_bounds__(256) k_dfactor(MArgs a) {
+  extern __shared__ double dsm[];
+  const int64_t node = blockIdx.x;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  if (!tier2_selected(a, node, pr)) return;
+  const int tid = threadIdx.x;
+  const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1;
+  const int64_t i0 = a.node_item0[node];
+  const int ni = a.node_nitems[node];
+  double* PS = dsm;                  // kPanel rows x m (absolute column index)
+  double* RT = PS + kPanel * m;      // kRT factored rows x m
+  double* d0 = RT + kRT * m;         // the Gram's diagonal
+  double* invd = d0 + m;
+  double* Fl = invd + m;
+  double* ws = Fl + m;
+  __shared__ int s_fail;
+  if (tid == 0) s_fail = 0;
+  double* R = a.rbuf + a.item_roff[i0];
+  for (int k0 = 0; k0 < m; k0 += kPanel) {
+    const int k1 = k0 + kPanel < m ? k0 + kPanel : m, np = k1 - k0, w = m - k0;
+    __syncthreads();
+    for (int e = tid; e < np * w; e += 256) {
+      const int r = e / w, j = k0 + (e - r * w), i = k0 + r;
+      double v = 0.0;
+      if (j >= i) {
+        const int64_t o = ro_of(i, m) + (j - i);
+        for (int t = 0; t < ni; ++t) v += a.rbuf[a.item_roff[i0 + t] + o];
+      }
+      PS[r * m + j] = v;
+      if (j == i) d0[i] = v;
+    }
+    // left-looking update by the factored rows t < k0
+    for (int t0 = 0; t0 < k0; t0 += kRT) {
+      const int nt = k0 - t0 < kRT ? k0 - t0 : kRT;
+      __syncthreads();
+      for (int e = tid; e < nt * w; e += 256) {
+        const int tt = e / w, j = k0 + (e - tt * w), t = t0 + tt;
+        RT[tt * m + j] = R[ro_of(t, m) + (j - t)];
+      }
+      __syncthreads();
+      for (int e = tid; e < np * w; e += 256) {
+        const int r = e / w, j = k0 + (e - r * w), i = k0 + r;
+        if (j < i) continue;
+        double v = PS[r * m + j];
+        for (int tt = 0; tt < nt; ++tt) v = fma(-RT[tt * m + i], RT[tt * m + j], v);
+        PS[r * m + j] = v;
+      }
+    }
+    // the panel itself, right-looking
+    for (int k = k0; k < k1 && k < L; ++k) {
+      __syncthreads();
+      const double d = PS[(k - k0) * m + k];
+      if (!(d0[k] > 0.0 && d > kPivotFloor2 * d0[k])) {  // the same decision in every thread
+        if (tid == 0) s_fail = 1;
+        break;
+      }
+      const double rkk = sqrt(d), irk = 1.0 / rkk;
+      double* rowk = PS + (k - k0) * m;
+      for (int j = k + 1 + tid; j < m; j += 256) rowk[j] *= irk;
+      __syncthreads();
+      if (tid == 0) {
+        rowk[k] = rkk;
+        invd[k] = irk;
+      }
+      const int wk = m - k - 1;
+      for (int e = tid; e < (k1 - k - 1) * wk; e += 256) {
+        const int r = e / wk, j = k + 1 + (e - r * wk), i = k + 1 + r;
+        if (j >= i) PS[(i - k0) * m + j] = fma(-rowk[i], rowk[j], PS[(i - k0) * m + j]);
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    for (int e = tid; e < np * w; e += 256) {
+      const int r = e / w, j = k0 + (e - r * w), i = k0 + r;
+      if (j >= i) R[ro_of(i, m) + (j - i)] = PS[r * m + j];
+    }
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) a.flags[node] |= FMT_FLAG_MIXED_PIVOT;
+    return;  // Householder refits this node
+  }
+  for (int k = tid; k < L; k += 256) Fl[k] = R[ro_of(k, m) + (L - k)];
+  for (int k = tid; k < m; k += 256) R[ro_of(m, m) + k] = d0[k];  // the Gram's diagonal, after R (slot of m^2)
+  __syncthreads();
+  if (tid < 32) warp_back_solve(R, m, L, invd, Fl);
+  __syncthreads();
+  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
+  for (int k = tid; k < L; k += 256) {
+    Fl[k] = Fl[k] / F.sig;
+    a.lcoef[node * a.stride + k] = Fl[k];
+  }
+  if (tid == 0) {  // convergence history of this tier's sweeps
+    a.mstat[kMStat * node + 4] = 0ull;
+    a.mstat[kMStat * node + 5] = 0ull;
+    a.mstat[kMStat * node + 6] = 0ull;
+  }
+  __syncthreads();
+  legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
+  if (tid == 0) {
+    a.flags[node] |= FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64;
+    a.deg_used[node] = p;
+  }
+}
+
+// Per item: B^T s in FP64, one column per thread (three for degree > 8)
+__global__ void __launch_bounds__(256) k_dproj(MArgs a) {
+  constexpr int P1 = FMT_MAX_DEGREE + 1;
+  __shared__ double Pl[kDRows * 3 * P1];
+  __shared__ double sv[kDRows];
+  const int item = blockIdx.x;
+  const int64_t node = a.item_node[item];
+  if ((a.flags[node] & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) != (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) return;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const int p = pr.degree, L = fmt_nmono_d(p);
+  const int tid = threadIdx.x;
+  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
+  int code[3];
+  double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) code[q] = tid + 256 * q < L ? col_abc(tid + 256 * q, p) : -1;
+  const int64_t rs = a.item_start[item], re = a.item_end[item];
+  for (int64_t r0 = rs; r0 < re; r0 += kDRows) {
+    const int nr = (int)(re - r0 < kDRows ? re - r0 : kDRows);
+    __syncthreads();
+    chunk_legendre(a, F, r0, nr, p, Pl);
+    if (tid < kDRows) sv[tid] = tid < nr ? a.s[r0 + tid] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (code[q] < 0) continue;
+      const int ca = code[q] & 0xff, cb = P1 + ((code[q] >> 8) & 0xff), cc = 2 * P1 + (code[q] >> 16);
+      double g = acc[q];
+      for (int row = 0; row < nr; ++row) {
+        const double* P = Pl + row * 3 * P1;
+        g = fma(P[ca] * P[cb] * P[cc], sv[row], g);
+      }
+      acc[q] = g;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    if (code[q] >= 0) a.dproj[(int64_t)item * a.dstride + tid + 256 * q] = acc[q];
+}
+
+// Per node: F += R^{-1} R^{-T} g with R in global memory (the node's first
+// item slot), then the convergence tests of k_mupdate.
+__global__ void __launch_bounds__(kFThreads) k_dupdate(MArgs a) {
+  extern __shared__ double usm2[];
+  __shared__ double red[kFThreads / 32], red2[kFThreads / 32];
+  __shared__ double s_pt[3][FMT_MAX_DEGREE + 1];
+  const int64_t node = blockIdx.x;
+  if ((a.flags[node] & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) != (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) return;
+  const int tid = threadIdx.x;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1;
+  const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
+  const int64_t i0 = a.node_item0[node];
+  const int ni = a.node_nitems[node];
+  const double* R = a.rbuf + a.item_roff[i0];
+  double* g = usm2;
+  double* Fl = g + m;
+  double* invd = Fl + m;
+  double* ws = invd + m;
+  for (int j = tid; j < L; j += kFThreads) {
+    double sum = 0.0;
+    for (int t = 0; t < ni; ++t) sum += a.dproj[(i0 + t) * a.dstride + j];
+    g[j] = sum;
+    Fl[j] = a.lcoef[node * a.stride + j];
+    invd[j] = 1.0 / R[ro_of(j, m)];
+  }
+  __syncthreads();
+  double wn = 0.0;
+  if (tid < 32) {
+    const int lane = tid;
+    for (int k = 0; k < L; ++k) {  // R^T w = g, then |w|^2 = |R d|^2
+      const double wk = g[k] * invd[k];
+      __syncwarp();
+      if (lane == 0) {
+        g[k] = wk;
+        wn += wk * wk;
+      }
+      const double* rowk = R + ro_of(k, m) - k;
+      for (int j = k + 1 + lane; j < L; j += 32) g[j] = fma(-rowk[j], wk, g[j]);
+      __syncwarp();
+    }
+    warp_back_solve(R, m, L, invd, g);
+  }
+  __syncthreads();
+  for (int j = tid; j < L; j += kFThreads) {
+    Fl[j] += g[j];
+    a.lcoef[node * a.stride + j] = Fl[j];
+  }
+  if (tid < 3) {
+    const double T = F.ex[tid];
+    double q0 = 1.0, q1 = T;
+    s_pt[tid][0] = 1.0;
+    if (p >= 1) s_pt[tid][1] = T;
+    for (int kk = 1; kk < p; ++kk) {
+      const double q2 = ((double)(2 * kk + 1) * T * q1 - (double)kk * q0) / (double)(kk + 1);
+      s_pt[tid][kk + 1] = q2;
+      q0 = q1;
+      q1 = q2;
+    }
+  }
+  __syncthreads();
+  const double* d0 = R + ro_of(m, m);  // the Gram's diagonal (k_dfactor)
+  double zn = 0.0, cw = 0.0, fa = 0.0;
+  for (int i = tid; i < L; i += kFThreads) {
+    const double* rowi = R + ro_of(i, m) - i;
+    double zi = 0.0;
+    for (int j = i; j < L; ++j) zi = fma(rowi[j], Fl[j], zi);
+    zn += zi * zi;
+    const int c = col_abc(i, p);
+    cw += fabs(g[i]) * s_pt[0][c & 0xff] * s_pt[1][(c >> 8) & 0xff] * s_pt[2][c >> 16];
+    fa += fabs(Fl[i]) * sqrt(d0[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    zn += __shfl_xor_sync(0xffffffffu, zn, o);
+    cw += __shfl_xor_sync(0xffffffffu, cw, o);
+    fa += __shfl_xor_sync(0xffffffffu, fa, o);
+  }
+  __shared__ double red3[kFThreads / 32];
+  if ((tid & 31) == 0) {
+    red[tid >> 5] = zn;
+    red2[tid >> 5] = cw;
+    red3[tid >> 5] = fa;
+  }
+  __syncthreads();
+  double ztot = 0.0, ctot = 0.0, atot = 0.0;
+  for (int i = 0; i < kFThreads / 32; ++i) {
+    ztot += red[i];
+    ctot += red2[i];
+    atot += red3[i];
+  }
+  // last sweep: the rounding perturbation of the fixed point, solved through R^T R
+  double etot = 0.0;
+  if (a.last_sweep) {
+    const double rn = sqrt(d0[L]) / F.sig;  // |r|: column L of the Gram is sig r
+    const double scale = (double)(3 * p + 4) * DBL_EPSILON * (atot + rn);
+    __syncthreads();  // every thread is done with g
+    for (int j = tid; j < L; j += kFThreads) {
+      const uint32_t hsh = (uint32_t)j * 2654435761u;
+      g[j] = ((hsh >> 16) & 1u ? scale : -scale) * sqrt(d0[j]);
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const int lane = tid;
+      for (int k = 0; k < L; ++k) {
+        const double wk = g[k] * invd[k];
+        __syncwarp();
+        if (lane == 0) g[k] = wk;
+        const double* rowk = R + ro_of(k, m) - k;
+        for (int j = k + 1 + lane; j < L; j += 32) g[j] = fma(-rowk[j], wk, g[j]);
+        __syncwarp();
+      }
+      warp_back_solve(R, m, L, invd, g);
+    }
+    __syncthreads();
+    double ew = 0.0;
+    for (int i = tid; i < L; i += kFThreads) {
+      const int c = col_abc(i, p);
+      ew += fabs(g[i]) * s_pt[0][c & 0xff] * s_pt[1][(c >> 8) & 0xff] * s_pt[2][c >> 16];
+    }
+    for (int o = 16; o > 0; o >>= 1) ew += __shfl_xor_sync(0xffffffffu, ew, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red3[tid >> 5] = ew;
+    __syncthreads();
+    for (int i = 0; i < kFThreads / 32; ++i) etot += red3[i];
+  }
+  legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
+  if (tid == 0) {
+    unsigned long long* slot = a.mstat + kMStat * node + 4;
+    unsigned long long* cslot = a.mstat + kMStat * node + 6;
+    const double upd = sqrt(wn), zr = sqrt(ztot), prev = __longlong_as_double((long long)*slot);
+    const double cprev = __longlong_as_double((long long)*cslot);
+    *slot = (unsigned long long)__double_as_longlong(upd);
+    *cslot = (unsigned long long)__double_as_longlong(ctot);
+    a.mstat[kMStat * node + 5] = 0ull;
+    if (a.last_sweep) {
+      bool conv = upd <= kConvergedRel * zr;
+      if (!conv && prev > 0.0 && upd < prev) {
+        const double rho = upd / prev;
+        conv = upd * rho / (1.0 - rho) <= kConvergedRel * zr;
+      }
+      const double cthr = kBoxChangeRel * pr.maxabs;
+      bool cconv = ctot <= cthr;
+      if (!cconv && cprev > 0.0 && ctot < cprev) {
+        const double rho = ctot / cprev;
+        cconv = ctot * rho / (1.0 - rho) <= cthr;
+      }
+      const bool stable = etot <= kRoundRel * pr.maxabs;  // insensitive to the FP64 rounding
+      if (!(conv && cconv && stable))
+        a.flags[node] = (a.flags[node] & ~(FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) | FMT_FLAG_MIXED_SLOW;
+    }
+  }
+}
+
 int nsm() {
   static const int n = [] {
     int dev = 0, v = 0;
@@ -1176,6 +1653,11 @@ MArgs make_margs(const fmt_tree* t, int depth, const fmt_mixed_bufs& b) {
   a.cache_atom_bytes = 0;
   a.last_sweep = 0;
   a.err = t->d_err;
+  a.tier = 1;
+  a.rbuf = t->Rbuf;
+  a.item_roff = L.item_roff;
+  a.dproj = b.dproj;
+  a.dstride = t->nmono;
   return a;
 }
 
@@ -1281,5 +1763,48 @@ cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bu
   cudaError_t e = cudaFuncSetAttribute(k_mupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_mupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- tier 2 launchers
+size_t tier2_factor_smem(int max_m) {
+  return sizeof(double) * ((size_t)(kPanel + kRT + 3) * max_m + conv_ws_doubles(FMT_MAX_DEGREE));
+}
+
+cudaError_t launch_tier2_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_items <= 0) return cudaSuccess;
+  const int nt = (L.max_m + kDT - 1) / kDT, npairs = nt * (nt + 1) / 2;
+  k_dgram<<<(unsigned)(L.n_items * npairs), 256, 0, s>>>(make_margs(t, depth, b), npairs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tier2_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_nodes <= 0) return cudaSuccess;
+  const size_t smem = tier2_factor_smem(L.max_m);
+  cudaError_t e = cudaFuncSetAttribute(k_dfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_dfactor<<<(unsigned)L.n_nodes, 256, smem, s>>>(make_margs(t, depth, b));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tier2_sweep(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, int part, bool last,
+                               cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_items <= 0) return cudaSuccess;
+  MArgs a = make_margs(t, depth, b);
+  a.tier = 2;
+  a.last_sweep = last ? 1 : 0;
+  if (part == 0) {
+    k_msresid<<<(unsigned)L.n_items, 256, 0, s>>>(a);
+  } else if (part == 1) {
+    k_dproj<<<(unsigned)L.n_items, 256, 0, s>>>(a);
+  } else {
+    const size_t smem = sizeof(double) * (3 * (size_t)L.max_m + conv_ws_doubles(FMT_MAX_DEGREE));
+    cudaError_t e = cudaFuncSetAttribute(k_dupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_dupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }

@@ -2,10 +2,12 @@
 
 The mixed path computes each node's least-squares fit (Alg. 2) from a Gram
 matrix formed on the tensor cores (3-term BF16 splits, FP32 accumulation,
-FP64 promotion), an FP64 Cholesky factor and FP64 refinement sweeps.  Its
-stated bar is an interpolant within 1e-6 * max|f| of the FP64 oracle; nodes
-it cannot fit that way (rank-deficient, ill-conditioned, degree above 9,
-clamped root) go to the FP64 path and then meet the FP64 bar of 1e-10.
+FP64 promotion), an FP64 Cholesky factor and FP64 refinement sweeps.  Nodes
+that tier cannot fit (ill-conditioned, not converged, degree above 9) go to
+its FP64 normal-equations tier (FP64 Gram, Cholesky, corrected semi-normal
+sweeps); what neither fits (rank-deficient, clamped root) goes to the FP64
+Householder path and then meets the FP64 bar of 1e-10.  The stated bar of
+the mixed path is an interpolant within 1e-6 * max|f| of the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -109,14 +111,42 @@ def test_coplanar_points_fall_back_to_fp64():
     assert np.max(np.abs(ex.resid - T.resid)) <= FP64_TOL * T.maxabs
 
 
-def test_degree_above_mixed_limit_uses_fp64():
+@pytest.mark.parametrize("degree", [10, 12])
+def test_degree_above_tensor_limit_uses_the_fp64_tier(degree):
     rng = np.random.default_rng(8)
-    x, y, z = rng.uniform(0, 1, (3, 1500))
+    x, y, z = rng.uniform(0, 1, (3, 3000))
     f = np.exp(-((x - 0.4) ** 2 + (y - 0.6) ** 2 + z ** 2))
-    T = O.fit(x, y, z, f, 10, 0, 1, 0.0)
-    tree, ex, st = mixed_fit(x, y, z, f, 10, 0, 1, 0.0)
-    assert not (ex.flags[0] & 8)
-    assert np.max(np.abs(ex.resid - T.resid)) <= FP64_TOL * T.maxabs
+    T = O.fit(x, y, z, f, degree, 0, 1, 0.0)
+    tree, ex, st = mixed_fit(x, y, z, f, degree, 0, 1, 0.0)
+    assert ex.flags[0] & 8 and ex.flags[0] & 64  # FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64
+    err = np.max(np.abs(ex.resid - T.resid)) / T.maxabs
+    assert err <= MIXED_TOL, err
+    xq, yq, zq = rng.uniform(0, 1, (3, 2000))
+    b, _ = T.evaluate(xq, yq, zq)
+    assert np.max(np.abs(gpu_eval(tree, xq, yq, zq) - b)) / T.maxabs <= MIXED_TOL
+
+
+def test_clustered_nodes_across_the_tiers():
+    # three Gaussian clusters in one root, narrower and narrower: the degree-9
+    # basis grows ill-conditioned on the data, past the tensor-core Gram, then
+    # past the FP64 normal equations (whose rounding-driven change over the
+    # box is checked), then to numerical rank deficiency.  Each fit meets the
+    # bar of the tier that took it (mixed 1e-6; Householder 1e-10).
+    rng = np.random.default_rng(9)
+    cs = np.array([[0.2, 0.3, 0.25], [0.7, 0.6, 0.8], [0.35, 0.8, 0.5]])
+    seen = []
+    for sigma in (0.25, 0.18, 0.12, 0.08, 0.05, 0.035, 0.025):
+        pts = np.concatenate([c + sigma * rng.normal(size=(1500, 3)) for c in cs])
+        x, y, z = np.clip(pts, 0.0, 0.999).T.copy()
+        f = np.sin(4 * x) * np.cos(3 * y) + z * z
+        T = O.fit(x, y, z, f, 9, 0, 1, 0.0)
+        tree, ex, st = mixed_fit(x, y, z, f, 9, 0, 1, 0.0)
+        fl = int(ex.flags[0])
+        err = np.max(np.abs(ex.resid - T.resid)) / T.maxabs
+        seen.append((sigma, fl, err))
+        assert err <= (MIXED_TOL if fl & 8 else FP64_TOL), seen[-1]
+    print("sigma, root flags, error:", seen)
+    assert seen[0][1] & 8 and seen[-1][1] & 2  # the widest on the tensor cores, the narrowest rank-deficient
 
 
 def test_sweeps_reduce_the_error():
@@ -132,7 +162,7 @@ def test_sweeps_reduce_the_error():
 
 
 def test_forest_of_mixed_degrees():
-    # Problems of degree 4..10 (degree 10 takes the FP64 path) fitted in one
+    # Problems of degree 4..10 (degree 10 takes the FP64 tier) fitted in one
     # forest; the interpolant meets the mixed bar at each problem's data
     # points and at fresh targets of its cloud (a node is accepted only if
     # its polynomial has settled over its whole box, not only at its data).
@@ -148,6 +178,7 @@ def test_forest_of_mixed_degrees():
     a = out.cpu().numpy()
     st = F.fmt_tree_stats(tree)
     assert mixed_points(st) > 0
+    assert np.any(ex.flags & 64)  # degree-10 problems (at least) took the FP64 tier
     report = []
     for i in range(b.n_problems):
         s, e = int(b.offsets[i]), int(b.offsets[i + 1])
