@@ -290,27 +290,37 @@ def run_experiments(args, rank, world):
         x, y, z = W.uniform_points(seed, stream, n)
         return [dev(a) for a in (x, y, z, W.franke_paper(x, y, z))]
 
+    prec = F.FMT_MIXED if args.precision == "mixed" else F.FMT_FP64
+
     def run(pts, tgt, p, D, tol, warm):
         n = pts[0].shape[0]
-        prm = F.make_params(p, D, 0, tol)
+        prm = F.make_params(p, D, 0, tol, precision=prec, sweeps=args.sweeps)
         if warm:
             F.fit(prm, *pts[:4]).close()
         torch.cuda.synchronize()
+        F.fmt_profile_enable(True)
         t0 = time.perf_counter()
         tree = F.fit(prm, *pts[:4])
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
+        prof = F.fmt_profile_read()
+        F.fmt_profile_enable(False)
+        kms = {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"] and k != "graph_launch"}
         out = torch.empty(tgt[0].shape[0], dtype=torch.float64, device="cuda")
         F.evaluate(tree, *tgt[:3], out)
         torch.cuda.synchronize()
         st = F.fmt_tree_stats(tree)
         nodes = int(sum(st.nodes[d] for d in range(st.n_levels)))
         depth = st.n_levels - 1
+        fl = F.parse_export(F.fmt_tree_export(tree)).flags
+        tiers = {"tensor": int(np.sum(((fl & F.FMT_FLAG_MIXED) != 0) & ((fl & F.FMT_FLAG_MIXED_FP64) == 0))),
+                 "fp64_normal_eq": int(np.sum((fl & F.FMT_FLAG_MIXED_FP64) != 0)),
+                 "householder": int(np.sum((fl & F.FMT_FLAG_MIXED) == 0))}
         tree.close()
         erms, einf = W.errors(out.cpu().numpy(), tgt[3].cpu().numpy())
         return {"N": n, "N_q": int(tgt[0].shape[0]), "p": p, "nmono": F.fmt_nmono(p), "max_depth": D,
                 "tol_rel": tol, "nodes": nodes, "depth": depth, "E_rms": erms, "E_inf": einf,
-                "fit_ms": t * 1e3, "fitted_pts_per_s": n / t}
+                "fit_ms": t * 1e3, "fitted_pts_per_s": n / t, "nodes_by_tier": tiers, "kernel_ms": kms}
 
     rows = []
     if args.workload == "fig1":
@@ -335,7 +345,8 @@ def run_experiments(args, rank, world):
             torch.cuda.empty_cache()
         metric = "tau x N x p sweep (Figs. 2-4): E_rms, E_inf, nodes"
         targets = "N_q = N_p"
-    line = {"metric": metric, "unit": "see rows", "n_gpus": world, "dtype": "f64", "data": "synthetic",
+    line = {"metric": metric, "unit": "see rows", "n_gpus": world,
+            "dtype": "f64" if prec == F.FMT_FP64 else "f64+bf16x3 (mixed path)", "data": "synthetic",
             "config": {"workload": args.workload, "points": "uniform [0,1)^3", "values": "Franke (Eq. eqF1)",
                        "targets": targets, "min_pts": 0}, "rows": rows}
     if rank == 0:

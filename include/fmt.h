@@ -51,7 +51,8 @@ typedef enum {
 
 #define FMT_FP64 0  /* FP64 path: Householder QR of every node in binary64 */
 #define FMT_MIXED 1 /* split-BF16 tensor-core Gram + FP64 factorisation and refinement */
-#define FMT_MIXED_MAX_DEGREE 9 /* nodes of higher degree take the FP64 path */
+#define FMT_MIXED_MAX_DEGREE 9 /* nodes of higher degree skip the tensor-core tier */
+#define FMT_MIXED_FP64_MAX_DEGREE 10 /* nodes of higher degree take Householder (see fit_level) */
 #define FMT_MIXED_MAX_SWEEPS 3
 
 #define FMT_MAX_DEPTH 21  /* 21 bits per axis in the Morton code */
@@ -167,8 +168,8 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  * by the ratio of the last two changes, above 1e-7 |Lambda F|), or whose
  * polynomial may still change by more than 1e-8 max|f| somewhere in the node
  * box (the same extrapolation of a bound of the last change over the box)
- * (FMT_FLAG_MIXED_SLOW), and every node of degree above FMT_MIXED_MAX_DEGREE,
- * goes to the mixed path's FP64 tier: the same basis, its Gram [B|r]^T[B|r]
+ * (FMT_FLAG_MIXED_SLOW), and every node of degree above FMT_MIXED_MAX_DEGREE
+ * up to FMT_MIXED_FP64_MAX_DEGREE, goes to the mixed path's FP64 tier: the same basis, its Gram [B|r]^T[B|r]
  * formed in FP64 on the CUDA cores (n m^2 flops, half of Householder's), an
  * FP64 Cholesky (pivot floor 1e-12 of the diagonal), and `sweeps` corrected
  * semi-normal steps with FP64 residuals and FP64 projections under the same
@@ -176,7 +177,10 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  * box caused by the FP64 rounding of the residual (a perturbation of that
  * size solved through R^T R) must stay within 1e-9 max|f|.  Nodes this tier
  * fits carry FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64; the rest are refitted by
- * Householder.  Nodes fitted the mixed way carry FMT_FLAG_MIXED.
+ * Householder.  Above degree 10 the moment basis of Alg. 2 is so badly scaled
+ * (u^14/14! is ~1e-11) that Householder's rank rule drops columns the
+ * Legendre basis keeps, so those nodes always take Householder.  Nodes
+ * fitted the mixed way carry FMT_FLAG_MIXED.
  * The mixed path targets an interpolant within 1e-6 max|f| of the FP64
  * path (not the 1e-10 of FP64), and its tree may differ where a refinement
  * decision is that close to tau.  FMT_ETIMEOUT if a tensor-core completion

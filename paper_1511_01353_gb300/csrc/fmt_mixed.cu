@@ -68,9 +68,12 @@ __host__ __device__ __forceinline__ bool mixed_ok_degree(int p) { return p >= 0 
 __device__ __forceinline__ bool mixed_eligible(const fmt_problem& pr, int depth) {
   return mixed_ok_degree(pr.degree) && !(depth == 0 && pr.q_root < pr.degree);
 }
-// the FP64 normal-equations tier takes any degree; a clamped root stays with Householder
+// the FP64 normal-equations tier takes degrees 1..FMT_MIXED_FP64_MAX_DEGREE:
+// above that Householder's rank rule on the badly scaled moment basis of
+// Alg. 2 drops columns this tier's Legendre basis would keep (a different
+// fit); a clamped root stays with Householder too
 __device__ __forceinline__ bool tier2_eligible(const fmt_problem& pr, int depth) {
-  return pr.degree >= 1 && !(depth == 0 && pr.q_root < pr.degree);
+  return pr.degree >= 1 && pr.degree <= FMT_MIXED_FP64_MAX_DEGREE && !(depth == 0 && pr.q_root < pr.degree);
 }
 
 // ------------------------------------------------------------------ PTX
@@ -1226,8 +1229,11 @@ __device__ __forceinline__ void chunk_legendre(const MArgs& a, const MFrame& F, 
 }
 
 // Packed upper triangle of one item's FP64 Gram, one 64 x 64 tile (bi, bj)
-// per CTA: 256 threads, 4 x 4 entries each (rows ty + 16 i, columns tx + 16 j
-// of the tile), rows streamed through shared memory 32 at a time.
+// per CTA, rows streamed through shared memory 32 at a time.  The tile is
+// four 32 x 32 sub-tiles of two warps each (64 threads, 4 x 4 entries per
+// thread at rows ty + 8 i, columns tx + 8 j); a sub-tile below the diagonal
+// or past column m is skipped by whole warps (at degree 10, 90% of the
+// multiply-adds are then entries of the triangle, against 67% for whole tiles).
 __global__ void __launch_bounds__(256) k_dgram(MArgs a, int npairs) {
   constexpr int P1 = FMT_MAX_DEGREE + 1;
   __shared__ double Pl[kDRows * 3 * P1];
@@ -1246,7 +1252,10 @@ __global__ void __launch_bounds__(256) k_dgram(MArgs a, int npairs) {
   }
   const int bj = bi + rem;
   const bool diag = bi == bj;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, sub = tid >> 6, sr = sub >> 1, sc = sub & 1;
+  const int tx = tid & 7, ty = (tid >> 3) & 7;
+  const int ro = bi * kDT + 32 * sr, co = bj * kDT + 32 * sc;     // the sub-tile's first row / column
+  const bool active = !(diag && sr > sc) && ro < m && co < m;      // warp-uniform
   const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
   if (tid < 2 * kDT) {
     const int w = tid / kDT, c = tid - w * kDT, j = (w ? bj : bi) * kDT + c;
@@ -1279,25 +1288,28 @@ __global__ void __launch_bounds__(256) k_dgram(MArgs a, int npairs) {
     }
     __syncthreads();
     const double(*Bt)[kDT] = diag ? As : Bs;
-    for (int row = 0; row < nr; ++row) {
-      double av[4], bv[4];
+    if (active) {
+      for (int row = 0; row < nr; ++row) {
+        double av[4], bv[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        av[i] = As[row][ty + 16 * i];
-        bv[i] = Bt[row][tx + 16 * i];
+        for (int i = 0; i < 4; ++i) {
+          av[i] = As[row][32 * sr + ty + 8 * i];
+          bv[i] = Bt[row][32 * sc + tx + 8 * i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
       }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
   }
+  if (!active) return;
   double* G = a.rbuf + a.item_roff[item];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int gi = bi * kDT + ty + 16 * i, gj = bj * kDT + tx + 16 * j;
+      const int gi = ro + ty + 8 * i, gj = co + tx + 8 * j;
       if (gi <= gj && gj < m) G[ro_of(gi, m) + (gj - gi)] = acc[i][j];
     }
 }

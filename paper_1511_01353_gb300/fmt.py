@@ -25,6 +25,7 @@ FMT_FP64, FMT_MIXED = 0, 1
 FMT_FLAG_NEAR_TAU, FMT_FLAG_RANK, FMT_FLAG_DEG_CLAMPED, FMT_FLAG_MIXED = 1, 2, 4, 8
 FMT_FLAG_MIXED_SLOW, FMT_FLAG_MIXED_PIVOT, FMT_FLAG_MIXED_FP64 = 16, 32, 64
 MIXED_MAX_DEGREE = 9
+MIXED_FP64_MAX_DEGREE = 10
 MIXED_MAX_SWEEPS = 3
 FMT_OPT_GRAPH = 1
 MAX_DEPTH = 21
