@@ -98,12 +98,15 @@ __device__ __forceinline__ NodeGeom node_geom(const QRArgs& a, int64_t node) {
 // Structured Householder absorb of a row block B (NB x m in shared memory,
 // leading dimension ldB) into the upper triangle R (m x m, row-major, global).
 // For each column j >= j_begin: alpha = R_jj, x = B[:, j],
-// beta = -sign(alpha) sqrt(alpha^2 + |x|^2) (sign(0) = +), and
-// H = I - tau [1; v][1; v]^T with v = x / (alpha - beta) and
-// tau = (beta - alpha) / beta = 1 + |alpha| / |beta| (LAPACK's normalisation:
-// tau lies in [1, 2] and |v| <= 1, so nothing over- or underflows however
-// small |x| is, e.g. the rounding residue left in a block's columns beyond
-// its rank).  A column with |x| = 0 is left alone (tau = 0).
+// beta = -sign(alpha) sqrt(alpha^2 + |x|^2) (sign(0) = +), u = [alpha - beta; x]
+// and H = I - gamma u u^T, gamma = 1 / (h (h + |alpha|)), h = |beta|: the
+// update of a column [rv; b] is d = gamma (amb rv + x.b), rv -= d amb,
+// b -= d x with amb = alpha - beta.  Where h h nears underflow (the rounding
+// residue left in a block's columns beyond its rank, whose squares go
+// subnormal at degree >= 12) gamma would overflow, so there the column is
+// scaled in place to v = x / amb and (gamma, amb) = (tau, 1) with LAPACK's
+// tau = 1 + |alpha| / h in [1, 2]: the same formula, nothing over- or
+// underflows.  A column with |x| = 0 is left alone (gamma = 0).
 //
 // Schedule per step j (one barrier per step):
 //  * row j of R sits in shared memory (Rs[j&1]); row j+1 was prefetched into
@@ -114,7 +117,25 @@ __device__ __forceinline__ NodeGeom node_geom(const QRArgs& a, int64_t node) {
 //  * warp 0, right after its first round (which updates column j+1), computes
 //    the reflector of step j+1 (look-ahead), so no step waits on a serial
 //    norm / sqrt / divide phase of its own.
-// One warp: tau of column j into sc[0], beta into R_jj, and v over x in B.
+// The scalars of a reflector from alpha and s = |x|^2 (every lane of the
+// warp computes them: lane-0-only FP64 code costs the same issue slots).
+// Returns the factor to scale x by (0: none).
+__device__ __forceinline__ double refl_scalars(double alpha, double s, double& gamma, double& amb, double& beta) {
+  const double h = sqrt(fma(alpha, alpha, s));
+  beta = alpha >= 0.0 ? -h : h;
+  const double hpa = h + fabs(alpha);  // |alpha - beta|
+  if (h > 0x1p-400) {
+    gamma = 1.0 / (h * hpa);
+    amb = alpha - beta;
+    return 0.0;
+  }
+  gamma = hpa / h;  // tau
+  amb = 1.0;
+  return alpha >= 0.0 ? 1.0 / hpa : -1.0 / hpa;
+}
+
+// One warp: gamma and amb of column j into sc, beta into R_jj (shared row and
+// global R).
 __device__ __forceinline__ void reflector(double* __restrict__ B, int ldB, int NB, int j, double* Rrow,
                                           double* __restrict__ Rg, int m, double* sc) {
   const int lane = threadIdx.x & 31;
@@ -123,24 +144,26 @@ __device__ __forceinline__ void reflector(double* __restrict__ B, int ldB, int N
     const double xv = B[i * ldB + j];
     s = fma(xv, xv, s);
   }
-  s = warp_sum(s);
-  double inv = 0.0;
-  if (lane == 0) {
-    const double alpha = Rrow[j];
-    if (s == 0.0) {
+  s = warp_sum(s);  // the same value in every lane (butterfly)
+  const double alpha = Rrow[j];
+  __syncwarp();  // every lane has read R_jj before it is overwritten
+  if (s == 0.0) {
+    if (lane == 0) {
       sc[0] = 0.0;
-    } else {
-      const double h = sqrt(fma(alpha, alpha, s));
-      const double beta = alpha >= 0.0 ? -h : h;
-      sc[0] = (h + fabs(alpha)) / h;
-      inv = 1.0 / (alpha - beta);
-      Rrow[j] = beta;
-      Rg[(size_t)j * m + j] = beta;
+      sc[1] = 0.0;
     }
+    return;
   }
-  inv = __shfl_sync(0xffffffffu, inv, 0);
-  if (inv != 0.0)
-    for (int i = lane; i < NB; i += 32) B[i * ldB + j] *= inv;
+  double gamma, amb, beta;
+  const double scale = refl_scalars(alpha, s, gamma, amb, beta);
+  if (scale != 0.0)
+    for (int i = lane; i < NB; i += 32) B[i * ldB + j] *= scale;
+  if (lane == 0) {
+    sc[0] = gamma;
+    sc[1] = amb;
+    Rrow[j] = beta;
+    Rg[(size_t)j * m + j] = beta;
+  }
 }
 
 // tri_row0 >= 0 marks a block whose row i is zero left of column tri_row0+i
@@ -195,9 +218,9 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
     }
     // groups of four rows that can hold nonzeros at this step (warp uniform)
     const int tmax = tri_row0 < 0 ? RPT : min(RPT, max(0, (j - tri_row0) / 4 + 1));
-    const double tau = sc[cur * 2];
-    const bool upd = tau != 0.0;
-    double xr[RPT];  // v of step j
+    const double gamma = sc[cur * 2], amb = sc[cur * 2 + 1];
+    const bool upd = gamma != 0.0;
+    double xr[RPT];
     if (upd) {
 #pragma unroll
       for (int t = 0; t < RPT; ++t) xr[t] = (t < tmax) ? B[(rg + 4 * t) * ldB + j] : 0.0;
@@ -235,7 +258,7 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (act) {
           const double rv = Rc[k];
-          const double d = tau * (rv + acc);
+          const double d = gamma * fma(amb, rv, acc);
 #pragma unroll
           for (int t = 0; t < RPT; ++t) {
             if (t < tmax) {
@@ -243,7 +266,7 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
               *bp = fma(-d, xr[t], *bp);
             }
           }
-          if (rg == 0) R[(size_t)j * m + k] = rv - d;
+          if (rg == 0) R[(size_t)j * m + k] = fma(-d, amb, rv);
         }
         k0 += 8 * NW;
       }
@@ -393,28 +416,30 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
   for (int k = tid; k < m; k += kMergeThreads) Rs[k] = Ra[k];  // row 0 of R_a
   __syncthreads();
 
-  auto reflect = [&](int j, double* Rrow, double* scj) {  // one warp; tau and v as in reflector()
+  auto reflect = [&](int j, double* Rrow, double* scj) {  // one warp; as reflector()
     double* col = Bp + j * (j + 1) / 2;
     double sq = 0.0;
     for (int i = lane; i <= j; i += 32) sq = fma(col[i], col[i], sq);
     sq = warp_sum(sq);
-    double inv = 0.0;
-    if (lane == 0) {
-      const double alpha = Rrow[j];
-      if (sq == 0.0) {
+    const double alpha = Rrow[j];
+    __syncwarp();
+    if (sq == 0.0) {
+      if (lane == 0) {
         scj[0] = 0.0;
-      } else {
-        const double h = sqrt(fma(alpha, alpha, sq));
-        const double beta = alpha >= 0.0 ? -h : h;
-        scj[0] = (h + fabs(alpha)) / h;
-        inv = 1.0 / (alpha - beta);
-        Rrow[j] = beta;
-        Ra[(size_t)j * m + j] = beta;
+        scj[1] = 0.0;
       }
+      return;
     }
-    inv = __shfl_sync(0xffffffffu, inv, 0);
-    if (inv != 0.0)
-      for (int i = lane; i <= j; i += 32) col[i] *= inv;
+    double gamma, amb, beta;
+    const double scale = refl_scalars(alpha, sq, gamma, amb, beta);
+    if (scale != 0.0)
+      for (int i = lane; i <= j; i += 32) col[i] *= scale;
+    if (lane == 0) {
+      scj[0] = gamma;
+      scj[1] = amb;
+      Rrow[j] = beta;
+      Ra[(size_t)j * m + j] = beta;
+    }
   };
   auto rot = [&](int jj) { return (tid - 32 * ((jj + (int)blockIdx.x) & (kMergeWarps - 1))) & (kMergeThreads - 1); };
   constexpr int kPF = (680 + kMergeThreads - 1) / kMergeThreads;
@@ -447,9 +472,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
         pf[e] = (k < m) ? Ra[(size_t)(j + 2) * m + k] : 0.0;
       }
     }
-    const double tau = sc[cur * 2];
-    const bool upd = tau != 0.0;
-    const double* xj = Bp + j * (j + 1) / 2;  // v of step j, rows 0..j
+    const double gamma = sc[cur * 2], amb = sc[cur * 2 + 1];
+    const bool upd = gamma != 0.0;
+    const double* xj = Bp + j * (j + 1) / 2;  // column j, rows 0..j
     const int slot = (warp - j - (int)blockIdx.x) & (kMergeWarps - 1);
     int k0 = j + 1 + 8 * slot;
     bool lookahead = (slot == 0) && (j + 1 < m);
@@ -472,7 +497,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (act) {
           const double rv = Rc[k];
-          const double d = tau * (rv + acc);
+          const double d = gamma * fma(amb, rv, acc);
           int i2 = rg;
           for (; i2 + 12 <= j; i2 += 16) {
             const double b0 = fma(-d, xj[i2], ck[i2]);
@@ -485,7 +510,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
             ck[i2 + 12] = b3;
           }
           for (; i2 <= j; i2 += 4) ck[i2] = fma(-d, xj[i2], ck[i2]);
-          if (rg == 0) Ra[(size_t)j * m + k] = rv - d;
+          if (rg == 0) Ra[(size_t)j * m + k] = fma(-d, amb, rv);
         }
         k0 += 8 * kMergeWarps;
       }
