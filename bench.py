@@ -37,7 +37,7 @@ UNIT = "fitted pts/s"
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
 # DRAM bytes (read + write) per row of k_tile_qr, from one ncu capture of the
 # current kernel on the 3e5-point recipe (profiles/tile_qr_3e5pts_p8.md):
-# 14.92 MB read + 50.52 MB written for 3e5 rows.  Scaled to a full launch by
+# 14.86 MB read + 51.45 MB written for 3e5 rows.  Scaled to a full launch by
 # its rows; set to None whenever the kernel changes until it is re-captured.
 TILE_QR_DRAM_BYTES_PER_ROW = (14.864640e6 + 51.453952e6) / 3.0e5
 
