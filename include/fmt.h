@@ -346,7 +346,8 @@ fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream);
  *   warps         warps per tile-QR CTA: 4 or 8;
  *   chunk_factor  smallest row chunk (one work item of the persistent queue)
  *                 = chunk_factor * (nmono + 1) rows rounded up to 64:
- *                 1, 2, 4, 8 or 16 (fmt_params.chunk_rows > 0 overrides it);
+ *                 1, 2, 4, 8 or 16 (fmt_params.chunk_rows > 0 overrides it;
+ *                 a forest of several degrees keeps the built-in 4);
  *   merge         pairwise reduction of a node's chunk triangles: 0 packs the
  *                 second triangle into shared memory where it fits (nmono+1
  *                 <= 166), 1 always streams it in row blocks.
@@ -354,8 +355,10 @@ fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream);
  * (source 0): the largest of 64/32/16 rows that fits two (64) or one CTA per
  * SM, 4 warps, chunk_factor 4, merge 0.  The configuration changes the order
  * of floating-point operations, not the method: every configuration meets
- * the same accuracy, and runs with one table are bitwise reproducible.  A
- * level of a forest uses the entry of its largest node's degree.  The table
+ * the same accuracy, and runs with one table are bitwise reproducible.  The
+ * tile QR of a level runs one launch per degree present (on side streams,
+ * largest degree first), each with its degree's entry; the merges use the
+ * entry of the level's largest degree.  The table
  * is per process (all devices of this pool are alike); change it only while
  * no fit is running.
  *

@@ -248,6 +248,11 @@ void destroy(fmt_tree* t) {
   cudaDeviceSynchronize();
   for (int i = 0; i < t->n_allocs; ++i) cudaFreeAsync(t->allocs[i], 0);
   cudaStreamSynchronize(0);
+  for (int q = 0; q <= FMT_MAX_DEGREE; ++q) {
+    if (t->side[q]) cudaStreamDestroy(t->side[q]);
+    if (t->join_ev[q]) cudaEventDestroy(t->join_ev[q]);
+  }
+  if (t->fork_ev) cudaEventDestroy(t->fork_ev);
   free(t->allocs);
   if (t->h_plan) cudaFreeHost(t->h_plan);
   if (t->h_err) cudaFreeHost(t->h_err);
@@ -299,12 +304,13 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
   const int64_t n = offsets[P];
   if (n > (int64_t)0xfffffffe) return set_err(nullptr, FMT_EINVAL, "n = %lld above 2^32-2 points", (long long)n);
   if (!x || !y || !z || !f) return set_err(nullptr, FMT_EINVAL, "NULL input pointer");
-  int32_t maxdeg = -1;
+  int32_t maxdeg = -1, mindeg = FMT_MAX_DEGREE + 1;
   for (int64_t i = 0; i < P; ++i) {
     const int32_t p = degrees ? degrees[i] : PP.degree;
     if (p < 0 || p > FMT_MAX_DEGREE)
       return set_err(nullptr, FMT_EINVAL, "degree %d outside [0, %d]", p, FMT_MAX_DEGREE);
     if (p > maxdeg) maxdeg = p;
+    if (p < mindeg) mindeg = p;
     const double* b = boxes ? boxes + 4 * i : nullptr;
     TRY(validate_box(b ? b[0] : PP.lo[0], b ? b[1] : PP.lo[1], b ? b[2] : PP.lo[2], b ? b[3] : PP.side));
   }
@@ -338,10 +344,13 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
   {
     // A chunk of C rows costs about 2 m^2 C flops and one merge about (2/3) m^3,
     // so C >= 4m keeps merges under ~10% of the chunk work (the built-in
-    // factor 4; the autotuner may pick another); above that floor the planner
+    // factor 4; the autotuner may pick another, which a tree of one degree
+    // uses: the floor is tree-wide, and a tuned factor measured on one degree
+    // does not carry over to a forest's mix); above that floor the planner
     // sizes chunks to the rows per resident QR CTA, so that the largest item
     // is no longer than the average share of a CTA.
-    int64_t fl = (int64_t)qr_config(t->nmono + 1).chunk_factor * (int64_t)(t->nmono + 1);
+    const int64_t factor = mindeg == maxdeg ? qr_config(t->nmono + 1).chunk_factor : 4;
+    int64_t fl = factor * (int64_t)(t->nmono + 1);
     t->chunk_floor = fl < 64 ? 64 : (fl + 63) / 64 * 64;
   }
   t->h_prob = (fmt_problem*)calloc((size_t)P, sizeof(fmt_problem));
@@ -389,7 +398,7 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
       (st = talloc(t, (char**)&temp, (int64_t)radix_sort_temp_bytes(n, key64), s)) ||
       (st = talloc(t, &t->d_err, 1, s)) || (st = talloc(t, &d_maxbits, P, s)) ||
       (st = talloc(t, &t->d_plan, 1, s)) || (st = talloc(t, &t->d_counter, 1, s)) ||
-      (st = talloc(t, &t->d_work, 1, s)) || (st = talloc(t, &t->d_prob, P, s)))
+      (st = talloc(t, &t->d_work, kWorkSlots, s)) || (st = talloc(t, &t->d_prob, P, s)))
     return fail(st);
   if (cudaMallocHost((void**)&t->h_plan, sizeof(fmt_plan_out)) != cudaSuccess ||
       cudaMallocHost((void**)&t->h_err, sizeof(int)) != cudaSuccess) {
@@ -492,6 +501,7 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
   L0.chunk_rows = pl.chunk_rows;
   L0.n_points = n;
   L0.max_m = (int32_t)pl.max_m;
+  L0.deg_mask = pl.deg_mask;
   L0.r_total = pl.r_total;
   L0.qr_flops = pl.qr_flops;
   L0.horner_flops = pl.horner_flops;
@@ -628,7 +638,9 @@ fmt_status fit_level_launches(fmt_tree* t, int depth, cudaStream_t s) {
   {
     // Householder on [Lambda | r]: 2 m^2 flops per row (m = nmono + 1 of the row's node);
     // on the mixed path only the nodes it left to FP64 are factorised here
-    ProfScope ps(K_TILE_QR, s, 1, rows, t->P.precision == FMT_MIXED ? 0.0 : L.qr_flops);
+    // one launch per degree present in the level (launch_tile_qr)
+    const int nlaunch = L.deg_mask ? __builtin_popcountll((unsigned long long)L.deg_mask) : 1;
+    ProfScope ps(K_TILE_QR, s, nlaunch, rows, t->P.precision == FMT_MIXED ? 0.0 : L.qr_flops);
     CUDA_TRY(t, launch_tile_qr(t, depth, t->Rbuf, s), "tile QR launch");
   }
   int levels = 0;
@@ -813,6 +825,7 @@ fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream
   N.chunk_rows = pl.chunk_rows;
   N.n_points = pl.n_points;
   N.max_m = (int32_t)pl.max_m;
+  N.deg_mask = pl.deg_mask;
   N.r_total = pl.r_total;
   N.qr_flops = pl.qr_flops;
   N.horner_flops = pl.horner_flops;

@@ -71,6 +71,7 @@ struct QRArgs {
   int* work;
   int n_items;
   const int32_t* flags;  // nodes with FMT_FLAG_MIXED are already fitted (mixed path)
+  int only_m;            // tile QR: > 0 takes only the items of nodes with this m
 };
 
 __device__ __forceinline__ bool node_done(const QRArgs& a, int64_t node) {
@@ -305,6 +306,7 @@ __global__ void __launch_bounds__(32 * NW) k_tile_qr(QRArgs a) {
     if (node_done(a, node)) continue;
     const int64_t rs = a.item_start[item], re = a.item_end[item];
     const NodeGeom g = node_geom(a, node);
+    if (a.only_m > 0 && g.m != a.only_m) continue;  // another degree's launch takes it
     const int m = g.m, q = g.q, ldB = g.ldB;
     double* R = a.R + a.item_roff[item];
     for (int e = threadIdx.x; e < m * m; e += NT) {
@@ -837,6 +839,7 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.work = t->d_work;
   a.n_items = (int)L.n_items;
   a.flags = L.flags;
+  a.only_m = 0;
   return a;
 }
 
@@ -967,18 +970,48 @@ int qr_resident_ctas(int m) {
   return nsm * qr_ops(c).resident(qr_smem_bytes(m, c.rows));
 }
 
-cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t s) {
-  QRArgs a = make_qr_args(t, depth, R);
-  const int64_t n_items = t->lv[depth].n_items;
+// One launch per degree present in the level, each with its degree's
+// configuration, shared-memory pitch and work-queue counter, so a forest
+// level mixing degrees 4..10 does not run every item with the largest
+// degree's blocks.  The launches go to side streams forked from s, largest
+// degree first: as one launch's persistent CTAs run out of items the next
+// one's take their SMs, so the launches share one tail instead of one each.
+// A level of one degree is one launch on s.
+cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  const int64_t n_items = L.n_items;
   if (n_items <= 0) return cudaSuccess;
-  const int mx = t->lv[depth].max_m;
-  const QRConfig c = qr_config(mx);
-  const size_t smem = qr_smem_bytes(mx, c.rows);
-  int64_t grid = qr_resident_ctas(mx);
-  if (grid > n_items) grid = n_items;
-  cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  return qr_ops(c).tile(a, (unsigned)grid, smem, s);
+  const uint64_t mask = (uint64_t)L.deg_mask;
+  const bool several = (mask & (mask - 1)) != 0;
+  auto launch_one = [&](int mq, cudaStream_t st, int* work) -> cudaError_t {
+    QRArgs a = make_qr_args(t, depth, R);
+    a.only_m = several ? mq : 0;
+    a.ld_max = ld_for(mq);
+    a.work = work;
+    const QRConfig c = qr_config(mq);
+    const size_t smem = qr_smem_bytes(mq, c.rows);
+    int64_t grid = qr_resident_ctas(mq);
+    if (grid > n_items) grid = n_items;
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    return qr_ops(c).tile(a, (unsigned)grid, smem, st);
+  };
+  if (!several) return launch_one(L.max_m, s, t->d_work + 1);
+  cudaError_t e;
+  if (!t->fork_ev && (e = cudaEventCreateWithFlags(&t->fork_ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(t->fork_ev, s)) != cudaSuccess) return e;
+  for (int q = FMT_MAX_DEGREE; q >= 0; --q) {
+    if (!(mask & (1ull << q))) continue;
+    if (!t->side[q] && (e = cudaStreamCreateWithFlags(&t->side[q], cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if (!t->join_ev[q] && (e = cudaEventCreateWithFlags(&t->join_ev[q], cudaEventDisableTiming)) != cudaSuccess)
+      return e;
+    if ((e = cudaStreamWaitEvent(t->side[q], t->fork_ev, 0)) != cudaSuccess) return e;
+    if ((e = launch_one(fmt_nmono(q) + 1, t->side[q], t->d_work + 1 + q)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(t->join_ev[q], t->side[q])) != cudaSuccess) return e;
+  }
+  for (int q = 0; q <= FMT_MAX_DEGREE; ++q)
+    if ((mask & (1ull << q)) && (e = cudaStreamWaitEvent(s, t->join_ev[q], 0)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s) {

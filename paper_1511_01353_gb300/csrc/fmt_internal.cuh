@@ -189,6 +189,7 @@ struct fmt_level {
   int64_t n_nodes = 0, cap_nodes = 0;
   int64_t n_items = 0, cap_items = 0, max_chunks = 0, chunk_rows = 0, n_points = 0;
   int32_t max_m = 0;  // largest nmono + 1 among this level's nodes
+  int64_t deg_mask = 0;  // degrees present among this level's nodes (bit q)
   double qr_flops = 0.0, horner_flops = 0.0;  // algorithmic flops of the level's fit
   bool fitted = false;
   // nodes
@@ -221,13 +222,17 @@ struct fmt_level {
 };
 
 // Small result block that refine reads back in one copy.
+// work-queue counters per tree: slot 0 for single launches, slot 1 + q for
+// the tile-QR launch of degree q
+constexpr int kWorkSlots = FMT_MAX_DEGREE + 2;
+
 struct fmt_plan_out {
   int64_t n_new, n_items, max_chunks, chunk_rows, n_points, n_near, err;
   int64_t max_m;       // largest nmono + 1 among the planned nodes
   double qr_flops;     // sum over nodes of rows x 2 m^2 (Householder on [Lambda | r])
   double horner_flops; // sum over nodes of rows x Horner flops of the node degree
   int64_t r_total;     // doubles of QR scratch: sum over items of m^2
-  int64_t pad_;
+  int64_t deg_mask;    // bit q set: some planned node has (effective) degree q
 };
 
 // Scratch of the mixed-precision fit (fmt_mixed.cu), grown per tree.
@@ -253,6 +258,10 @@ struct fmt_tree {
   bool imported = false;
   int device = 0;
   cudaStream_t stream = nullptr;  // last stream used (for the final free)
+  // the tile QR's per-degree launches run on side streams forked from the
+  // caller's (created on first use, destroyed with the tree)
+  cudaStream_t side[FMT_MAX_DEGREE + 1] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[FMT_MAX_DEGREE + 1] = {};
   double tau = 0.0, maxabs = 0.0; // problem 0 (single-problem trees)
   int sort_bits = 0;       // Morton bits in the sort key (3 per sorted level)
   int pid_bits = 0;        // problem-id bits above them
@@ -276,7 +285,7 @@ struct fmt_tree {
   fmt_plan_out* h_plan = nullptr;  // pinned
   int* h_err = nullptr;            // pinned
   unsigned long long* d_counter = nullptr;
-  int* d_work = nullptr;  // work-queue counter of the persistent QR kernel
+  int* d_work = nullptr;  // work-queue counters of the persistent kernels (kWorkSlots)
   int64_t chunk_floor = 64;
   fmt_mixed_bufs mx;
   fmt_status sticky = FMT_OK;
@@ -322,7 +331,7 @@ fmt_status tune_install(const fmt_tune_entry& e);  // FMT_EINVAL on a bad entry
 fmt_tune_entry tune_current(int degree);
 int qr_resident_ctas(int m);  // SMs x resident QR CTAs per SM
 size_t qr_smem_bytes(int m, int rows);
-cudaError_t launch_tile_qr(const fmt_tree* t, int depth, double* R, cudaStream_t s);
+cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s);  // may create side streams
 cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s);
 cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream_t s);
 cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s);

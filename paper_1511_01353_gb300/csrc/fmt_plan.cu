@@ -134,6 +134,8 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
   __syncthreads();
   int64_t maxc = 0, maxm = 0;
   double qrf = 0.0, hf = 0.0;
+  __shared__ unsigned long long s_degmask;
+  if (threadIdx.x == 0) s_degmask = 0ull;
   __shared__ int64_t rcarry;
   if (threadIdx.x == 0) rcarry = 0;
   __syncthreads();
@@ -149,6 +151,7 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
       const int q = a.depth == 0 ? pr.q_root : pr.degree;
       m = fmt_nmono_d(q) + 1;
       maxm = m > maxm ? m : maxm;
+      atomicOr(&s_degmask, 1ull << q);
       qrf += 2.0 * (double)m * (double)m * (double)cnt;
       hf += horner_flops_d(pr.degree) * (double)cnt;
     }
@@ -217,6 +220,7 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
     out->r_total = rcarry;
     out->max_chunks = maxc;
     out->max_m = maxm;
+    out->deg_mask = (int64_t)s_degmask;
     out->qr_flops = qrf;
     out->horner_flops = hf;
     out->chunk_rows = C;
@@ -344,6 +348,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_refine(RefineArgs r, PlanArgs 
       out->chunk_rows = 0;
       out->n_points = pts;
       out->max_m = 0;
+      out->deg_mask = 0;
       out->qr_flops = 0.0;
       out->horner_flops = 0.0;
       out->r_total = 0;
