@@ -113,3 +113,25 @@ def test_graph_form_is_bitwise_the_stream_form(clustered, precision):
     assert gl["launches"] == 2 * levels
     assert gl["units"] >= levels  # the second fit reused every level's executable graph
     assert prof["tile_qr"]["ms"] > 0.0  # event timing works inside graphs
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_form_of_a_forest_of_several_degrees(precision):
+    # a forest of degrees 4..10: the tile QR of a level forks one launch per
+    # degree onto side streams; captured in a graph, the fork and join are
+    # part of the graph, and the results are bitwise those of the stream form
+    from paper_1511_01353_gb300 import fmt as F
+    b = W.batch(n_problems=20, n_min=300, n_max=6000)
+
+    def run(graph):
+        p = F.make_params(4, b.max_depth, b.min_pts, b.tol_rel, precision=precision, graph=graph)
+        tree = F.oct_build_batch(p, b.offsets, dev(b.x), dev(b.y), dev(b.z), dev(b.f), degrees=b.degrees,
+                                 boxes=b.boxes)
+        F.fit_all(tree)
+        return F.parse_export(F.fmt_tree_export(tree))
+
+    ref, g = run(False), run(True)
+    assert len(set(int(d) for d in b.degrees)) > 2
+    assert np.array_equal(g.coef, ref.coef)
+    assert np.array_equal(g.resid, ref.resid)
+    assert np.array_equal(g.flags, ref.flags)
