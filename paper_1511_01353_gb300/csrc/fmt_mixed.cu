@@ -935,15 +935,29 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   }
   __syncthreads();
   for (int k = tid; k < L; k += kFThreads) d0[k] = G[ro_of(k, m)];
-  // 2. Cholesky, right-looking, on the packed rows; column L (r) is carried along
+  // 2. Cholesky, right-looking, on the packed rows; column L (r) is carried
+  // along.  Thread 0 forms each pivot's square root and reciprocal once (it
+  // updates the next pivot G[k+1][k+1] itself, first in its trailing tile):
+  // FP64 sqrt and divide in every warp cost as much pipe time as the updates.
+  __shared__ double s_rkk, s_irk;
+  __shared__ int s_bad;
+  auto pivot = [&](int k) {  // thread 0
+    const double d = G[ro_of(k, m)];
+    s_bad = !(d0[k] > 0.0 && d > kPivotFloor * d0[k]);
+    if (!s_bad) {
+      s_rkk = sqrt(d);
+      s_irk = 1.0 / s_rkk;
+    }
+  };
+  __syncthreads();
+  if (tid == 0 && L > 0) pivot(0);
   for (int k = 0; k < L; ++k) {
     __syncthreads();
-    const double d = G[ro_of(k, m)];
-    if (!(d0[k] > 0.0 && d > kPivotFloor * d0[k])) {  // the same decision in every thread
+    if (s_bad) {  // the same decision in every thread
       if (tid == 0) a.flags[node] |= FMT_FLAG_MIXED_PIVOT;
       return;  // the FP64 path refits this node
     }
-    const double rkk = sqrt(d), irk = 1.0 / rkk;
+    const double rkk = s_rkk, irk = s_irk;
     double* Gk = G + ro_of(k, m) - k;
     for (int j = k + 1 + tid; j < m; j += kFThreads) {
       const double v = Gk[j] * irk;
@@ -954,6 +968,7 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
     __syncthreads();
     if (tid == 0) Gk[k] = rkk;  // every thread has read the pivot by now
     trailing_update(G, rk, k, m);
+    if (tid == 0 && k + 1 < L) pivot(k + 1);  // thread 0 wrote G[k+1][k+1] in its first tile
   }
   __syncthreads();
   // 3. R F = y, y = the scaled Q^T r column
@@ -1334,6 +1349,7 @@ __global__ void __launch_bounds__(256) k_dfactor(MArgs a) {
   double* Fl = invd + m;
   double* ws = Fl + m;
   __shared__ int s_fail;
+  __shared__ double s_piv[2];
   if (tid == 0) s_fail = 0;
   double* R = a.rbuf + a.item_roff[i0];
   for (int k0 = 0; k0 < m; k0 += kPanel) {
@@ -1366,15 +1382,22 @@ __global__ void __launch_bounds__(256) k_dfactor(MArgs a) {
         PS[r * m + j] = v;
       }
     }
-    // the panel itself, right-looking
+    // the panel itself, right-looking (thread 0 forms each pivot's square
+    // root and reciprocal once: FP64 sqrt and divide in every warp are costly)
     for (int k = k0; k < k1 && k < L; ++k) {
       __syncthreads();
-      const double d = PS[(k - k0) * m + k];
-      if (!(d0[k] > 0.0 && d > kPivotFloor2 * d0[k])) {  // the same decision in every thread
-        if (tid == 0) s_fail = 1;
-        break;
+      if (tid == 0) {
+        const double d = PS[(k - k0) * m + k];
+        const bool bad = !(d0[k] > 0.0 && d > kPivotFloor2 * d0[k]);
+        s_fail = bad ? 1 : 0;
+        if (!bad) {
+          s_piv[0] = sqrt(d);
+          s_piv[1] = 1.0 / s_piv[0];
+        }
       }
-      const double rkk = sqrt(d), irk = 1.0 / rkk;
+      __syncthreads();
+      if (s_fail) break;  // the same decision in every thread
+      const double rkk = s_piv[0], irk = s_piv[1];
       double* rowk = PS + (k - k0) * m;
       for (int j = k + 1 + tid; j < m; j += 256) rowk[j] *= irk;
       __syncthreads();
