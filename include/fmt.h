@@ -396,6 +396,22 @@ fmt_status fmt_tune_get(int32_t degree, fmt_tune_entry* out);
 fmt_status fmt_tune_set(const fmt_tune_entry* entry);
 
 /*
+ * Failure-path diagnostics (no counterpart in the paper).
+ * fmt_debug_fail_alloc(k): the k-th device allocation the library makes from
+ * now on (k >= 1) fails as if the device were out of memory: the call that
+ * needed it returns FMT_ENOMEM and the tree stays safe to free; k = 0
+ * disarms.  Process-wide; host only (no GPU needed).  FMT_EINVAL for k < 0.
+ * fmt_wait_probe(limit_ns): one thread waits on an mbarrier that nothing
+ * arrives on, through the same bounded wait the mixed kernels use for their
+ * tensor-core completions (bound 2 s there), here with the bound limit_ns
+ * (1e3..1e10 ns).  It returns FMT_ETIMEOUT when the bound runs out -- the
+ * error path of a stuck completion -- and the context stays usable: no trap,
+ * no hang.  Synchronises.  FMT_EINVAL for a bound outside the range.
+ */
+fmt_status fmt_debug_fail_alloc(int64_t k);
+fmt_status fmt_wait_probe(int64_t limit_ns, void* stream);
+
+/*
  * fmt_fit_node_static -- allocation-free least-squares fit of ONE point set.
  * The paper has no counterpart: this exists for callers that cannot let a
  * library allocate device memory -- code whose device memory is owned by

@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -131,10 +132,19 @@ struct ProfScope {
   }
 };
 
+// fmt_debug_fail_alloc: > 0 counts down the device allocations; the one that
+// takes it from 1 to 0 fails as if the device were out of memory
+std::atomic<int64_t> g_fail_alloc{0};
+
 template <typename T>
 fmt_status talloc(fmt_tree* t, T** p, int64_t count, cudaStream_t s) {
   size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
   bytes = (bytes + 255) & ~(size_t)255;
+  for (int64_t k = g_fail_alloc.load(); k > 0; k = g_fail_alloc.load())
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+      if (k == 1) return set_err(t, FMT_ENOMEM, "device allocation of %zu bytes failed (injected)", bytes);
+      break;
+    }
   void* ptr = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync(&ptr, bytes, g_pool[t->device], s);
   if (e != cudaSuccess) {
@@ -1299,3 +1309,27 @@ fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream) {
 const char* fmt_profile_class_name(int32_t k) { return (k >= 0 && k < K_NCLASS) ? kClassNames[k] : nullptr; }
 
 }  // extern "C"
+
+extern "C" fmt_status fmt_debug_fail_alloc(int64_t k) {
+  if (k < 0) return set_err(nullptr, FMT_EINVAL, "fmt_debug_fail_alloc: k < 0");
+  g_fail_alloc.store(k);
+  return FMT_OK;
+}
+
+extern "C" fmt_status fmt_wait_probe(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 10000000000ll)
+    return set_err(nullptr, FMT_EINVAL, "fmt_wait_probe: limit_ns outside [1e3, 1e10]");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d_err = nullptr;
+  int h_err = 0;
+  cudaError_t e = cudaMalloc(&d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_wait_probe((unsigned long long)limit_ns, d_err, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (d_err) cudaFree(d_err);
+  if (e != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "fmt_wait_probe: %s", cudaGetErrorString(e));
+  if (h_err & FMT_ERR_TIMEOUT)
+    return set_err(nullptr, FMT_ETIMEOUT, "bounded mbarrier wait ran out after %lld ns", (long long)limit_ns);
+  return FMT_OK;
+}

@@ -346,6 +346,8 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, 
 // mixed precision (fmt_mixed.cu)
 int mixed_m_cap(int max_m);            // largest m a mixed node of the level can have
 size_t mixed_acc_stride(int max_m);    // doubles of Gram accumulator per work item
+// a bounded mbarrier wait that nothing satisfies (fmt_wait_probe)
+cudaError_t launch_wait_probe(unsigned long long limit_ns, int* d_err, cudaStream_t s);
 // the mixed path's FP64 normal-equations tier (fmt_mixed.cu): Gram, factor,
 // and the sweeps' parts 0 (residual), 1 (projection), 2 (update)
 cudaError_t launch_tier2_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);

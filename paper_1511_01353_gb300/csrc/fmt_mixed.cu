@@ -100,14 +100,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of `parity` to complete; false after kWaitNs.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for the phase of `parity` to complete; false after limit_ns (and,
+// should the global timer ever stand still, after limit_ns polls: each takes
+// more than a nanosecond).
+__device__ __noinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
-  while (!mbar_try(bar, parity))
-    if (gtimer() - t0 > kWaitNs) return false;
+  for (unsigned long long it = 0; !mbar_try(bar, parity); ++it)
+    if (gtimer() - t0 > limit_ns || it > limit_ns) return false;
   return true;
 }
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitNs); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -1841,5 +1844,24 @@ cudaError_t launch_tier2_sweep(const fmt_tree* t, int depth, const fmt_mixed_buf
     if (e != cudaSuccess) return e;
     k_dupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- bounded-wait probe
+namespace {
+// One thread waits on an mbarrier that nothing arrives on, through the same
+// bounded wait as the kernels above; when the bound runs out it records
+// FMT_ERR_TIMEOUT in the error word and returns (no trap, no hang).
+__global__ void k_wait_probe(unsigned long long limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait_for(&bar, 0, limit_ns)) atomicOr(err, FMT_ERR_TIMEOUT);
+}
+}  // namespace
+
+cudaError_t launch_wait_probe(unsigned long long limit_ns, int* d_err, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(limit_ns, d_err);
   return cudaGetLastError();
 }

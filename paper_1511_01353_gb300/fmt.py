@@ -84,7 +84,7 @@ EXPORTED = ["fmt_nmono", "oct_build", "oct_build_batch", "fit_level", "refine", 
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
             "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static", "fmt_server_create",
             "fmt_server_submit", "fmt_server_wait", "fmt_server_destroy", "fmt_server_clock", "fmt_autotune",
-            "fmt_tune_get", "fmt_tune_set"]
+            "fmt_tune_get", "fmt_tune_set", "fmt_debug_fail_alloc", "fmt_wait_probe"]
 STATIC_MAX_DEGREE = 8
 PROFILE_CLASSES = 24
 
@@ -171,6 +171,10 @@ def load(build: bool = True):
         L.fmt_tune_get.restype = ctypes.c_int
         L.fmt_tune_set.argtypes = [ctypes.POINTER(fmt_tune_entry)]
         L.fmt_tune_set.restype = ctypes.c_int
+        L.fmt_debug_fail_alloc.argtypes = [i64]
+        L.fmt_debug_fail_alloc.restype = ctypes.c_int
+        L.fmt_wait_probe.argtypes = [i64, P]
+        L.fmt_wait_probe.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -372,6 +376,16 @@ def fmt_tune_set(entry: dict):
     if "source" not in entry:
         e.source = 2
     _check(load().fmt_tune_set(ctypes.byref(e)))
+
+
+def fmt_debug_fail_alloc(k: int):
+    """Make the k-th device allocation of the library from now fail (FMT_ENOMEM); 0 disarms."""
+    _check(load().fmt_debug_fail_alloc(k))
+
+
+def fmt_wait_probe(limit_ns: int, stream=None):
+    """Bounded wait that nothing satisfies; raises FmtError(FMT_ETIMEOUT) when the bound runs out."""
+    _check(load().fmt_wait_probe(limit_ns, _stream_handle(stream)))
 
 
 def fmt_fit_node_static(degree: int, x, y, z, r_in, coef, r_out, flags=None, lo=(0.0, 0.0, 0.0), side=1.0,

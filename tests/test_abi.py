@@ -153,3 +153,11 @@ def test_import_rejects_garbage():
     junk = ctypes.create_string_buffer(b"\0" * 512, 512)
     assert lib.fmt_tree_import(junk, 512, None, ctypes.byref(h)) == F.FMT_EINVAL
     assert lib.fmt_tree_import(junk, 8, None, ctypes.byref(h)) == F.FMT_EINVAL
+
+
+def test_failure_diagnostics_check_arguments_on_the_host():
+    lib = F.load()
+    assert lib.fmt_debug_fail_alloc(-1) == F.FMT_EINVAL
+    assert lib.fmt_debug_fail_alloc(0) == F.FMT_OK
+    assert lib.fmt_wait_probe(10, None) == F.FMT_EINVAL  # bound below 1 us
+    assert lib.fmt_wait_probe(10 ** 11, None) == F.FMT_EINVAL
