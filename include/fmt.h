@@ -175,7 +175,7 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  * semi-normal steps with FP64 residuals and FP64 projections under the same
  * convergence tests, plus one more: the change of the polynomial over the
  * box caused by the FP64 rounding of the residual (a perturbation of that
- * size solved through R^T R) must stay within 1e-9 max|f|.  Nodes this tier
+ * size solved through R^T R) must stay within 1e-8 max|f|.  Nodes this tier
  * fits carry FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64; the rest are refitted by
  * Householder.  Above degree 10 the moment basis of Alg. 2 is so badly scaled
  * (u^14/14! is ~1e-11) that Householder's rank rule drops columns the

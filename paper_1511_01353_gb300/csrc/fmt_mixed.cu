@@ -1179,7 +1179,7 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
 // kRoundRel max |f| (else Householder, which the mixed path is held to,
 // refits it).
 constexpr double kPivotFloor2 = 1e-12;  // FP64 Gram: a column must keep 1e-6 of its norm
-constexpr double kRoundRel = 1e-9;      // bound of the rounding-driven change over the box, relative to max |f|
+constexpr double kRoundRel = 1e-8;      // bound of the rounding-driven change over the box, relative to max |f|
 constexpr int kDT = 64;                 // Gram tile (columns)
 constexpr int kDRows = 32;              // rows per shared-memory chunk
 constexpr int kPanel = 32;              // rows per Cholesky panel
