@@ -167,8 +167,11 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  * within 1e-7 of converged (the last change |Lambda d|, or its extrapolation
  * by the ratio of the last two changes, above 1e-7 |Lambda F|), or whose
  * polynomial may still change by more than 1e-8 max|f| somewhere in the node
- * box (the same extrapolation of a bound of the last change over the box)
- * (FMT_FLAG_MIXED_SLOW), and every node of degree above FMT_MIXED_MAX_DEGREE
+ * box (the same extrapolation of a bound of the last change over the box),
+ * or whose polynomial the bias of the quantised basis (|B~ - B| <= 2^-31)
+ * may move by more than 1e-8 max|f| over the box (a perturbation of that
+ * size solved through R^T R) (FMT_FLAG_MIXED_SLOW), and every node of degree
+ * above FMT_MIXED_MAX_DEGREE
  * up to FMT_MIXED_FP64_MAX_DEGREE, goes to the mixed path's FP64 tier: the same basis, its Gram [B|r]^T[B|r]
  * formed in FP64 on the CUDA cores (n m^2 flops, half of Householder's), an
  * FP64 Cholesky (pivot floor 1e-12 of the diagonal), and `sweeps` corrected

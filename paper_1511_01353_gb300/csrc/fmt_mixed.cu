@@ -1130,6 +1130,53 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
     ztot += red[i];
     ctot += red2[i];
   }
+  // Last sweep: the fixed point solves B~^T (r - Lambda F) = 0 with the basis
+  // quantised to 2^-31 (the digit tiles), which moves F by (R^T R)^{-1} E^T r_LS,
+  // |E_ij| <= 2^-31: about 2^-31 |r_LS| per column.  That perturbation (with
+  // pseudo-random signs, twice the size) is solved through R^T R; a node whose
+  // polynomial it moves by more than kBoxChangeRel max |f| over the box goes to
+  // the FP64 tier.  |r_LS| = sqrt(R_LL^2) / sig (column L carries sig r).
+  double etot = 0.0;
+  if (a.last_sweep) {
+    const double rls = sqrt(fmax(R[ro_of(L, m)], 0.0)) / F.sig;
+    const double scale = 2.0 * 0x1p-31 * rls;
+    __syncthreads();  // every thread is done with g
+    for (int j = tid; j < L; j += kFThreads)
+      g[j] = (((uint32_t)j * 2654435761u) >> 16) & 1u ? scale : -scale;
+    __syncthreads();
+    if (tid < 32) {
+      const int lane = tid;
+      for (int k = 0; k < L; ++k) {
+        const double wk = g[k] * invd[k];
+        __syncwarp();
+        if (lane == 0) g[k] = wk;
+        const double* rowk = R + ro_of(k, m) - k;
+        for (int j = k + 1 + lane; j < L; j += 32) g[j] = fma(-rowk[j], wk, g[j]);
+        __syncwarp();
+      }
+      warp_back_solve(R, m, L, invd, g);
+    }
+    __syncthreads();
+    double ew = 0.0;
+    for (int i = tid; i < L; i += kFThreads) {
+      int r = i, la = 0;
+      while (r >= (p - la + 1) * (p - la + 2) / 2) {
+        r -= (p - la + 1) * (p - la + 2) / 2;
+        ++la;
+      }
+      int lb = 0;
+      while (r >= p - la - lb + 1) {
+        r -= p - la - lb + 1;
+        ++lb;
+      }
+      ew += fabs(g[i]) * s_pt[0][la] * s_pt[1][lb] * s_pt[2][r];
+    }
+    for (int o = 16; o > 0; o >>= 1) ew += __shfl_xor_sync(0xffffffffu, ew, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = ew;
+    __syncthreads();
+    for (int i = 0; i < kFThreads / 32; ++i) etot += red[i];
+  }
   legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
   if (tid == 0) {
     // |R d| = |Lambda d| is the change of the fit at the data, ctot its bound
@@ -1154,7 +1201,8 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
         const double rho = ctot / cprev;
         cconv = ctot * rho / (1.0 - rho) <= cthr;
       }
-      if (!(conv && cconv)) a.flags[node] = (a.flags[node] & ~FMT_FLAG_MIXED) | FMT_FLAG_MIXED_SLOW;
+      const bool stable = etot <= cthr;  // the basis quantisation's bias, bounded over the box
+      if (!(conv && cconv && stable)) a.flags[node] = (a.flags[node] & ~FMT_FLAG_MIXED) | FMT_FLAG_MIXED_SLOW;
     }
   }
 }
