@@ -82,9 +82,11 @@ typedef enum {
  *              outside it are clamped into the boundary cells.
  *   chunk_rows rows per QR work item for large nodes (multiple of 64);
  *              0 picks a size from the number of active points.
- *   sweeps     FMT_MIXED only: FP64 refinement sweeps after the first solve:
- *              1..3 (FMT_MIXED_MAX_SWEEPS), 0 selects 3, -1 none (then no
- *              convergence test either).  Ignored for FP64.
+ *   sweeps     FMT_MIXED only: at most this many FP64 refinement sweeps after
+ *              the first solve: 1..3 (FMT_MIXED_MAX_SWEEPS), 0 selects 3, -1
+ *              none (then no convergence test either); a node that passes
+ *              the acceptance tests after an earlier sweep skips the rest.
+ *              Ignored for FP64.
  *   options    bit set: FMT_OPT_GRAPH captures the launches of each
  *              fit_level in a CUDA graph (one graph per level step) and
  *              launches that; other bits must be 0.

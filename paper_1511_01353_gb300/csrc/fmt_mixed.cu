@@ -50,6 +50,7 @@ constexpr double kConvergedRel = 1e-7;
 constexpr double kBoxChangeRel = 1e-8;  // remaining change over the node box, relative to max |f| of the problem
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
 constexpr int kMStat = 8;        // per-node words of mstat
+constexpr int kSettled = 7;      // mstat word: 1 once the node passed every acceptance test (later sweeps skip it)
 
 // ------------------------------------------------------------------ shapes
 __host__ __device__ __forceinline__ int mpad16(int m) { return (m + 15) & ~15; }
@@ -296,6 +297,9 @@ struct MArgs {
   double* dproj;                // tier 2: per item B^T s (dstride doubles)
   int dstride;
 };
+__device__ __forceinline__ bool settled(const MArgs& a, int64_t node) {
+  return a.mstat[kMStat * node + kSettled] != 0ull;
+}
 
 // ------------------------------------------------------------------ k_mbox
 __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       const int item = a.sched[it];
       const int64_t node = a.item_node[item];
       const fmt_problem& pr = a.prob[a.node_prob[node]];
-      if (kProj ? !(a.flags[node] & FMT_FLAG_MIXED) : !mixed_eligible(pr, a.depth)) continue;
+      if (kProj ? (!(a.flags[node] & FMT_FLAG_MIXED) || settled(a, node)) : !mixed_eligible(pr, a.depth)) continue;
       const int p = pr.degree;
       const int L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m);
       const int nw = kProj ? L : m;
@@ -1001,7 +1005,7 @@ __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
   const int item = blockIdx.x;
   const int64_t node = a.item_node[item];
   const int32_t nf = a.flags[node];
-  if (!(nf & FMT_FLAG_MIXED) || (a.tier == 2 && !(nf & FMT_FLAG_MIXED_FP64))) return;
+  if (!(nf & FMT_FLAG_MIXED) || (a.tier == 2 && !(nf & FMT_FLAG_MIXED_FP64)) || settled(a, node)) return;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
@@ -1029,7 +1033,7 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   extern __shared__ double usm[];
   __shared__ double red[kFThreads / 32];
   const int64_t node = blockIdx.x;
-  if (!(a.flags[node] & FMT_FLAG_MIXED)) return;
+  if (!(a.flags[node] & FMT_FLAG_MIXED) || settled(a, node)) return;
   const int tid = threadIdx.x;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
@@ -1130,17 +1134,47 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
     ztot += red[i];
     ctot += red2[i];
   }
-  // Last sweep: the fixed point solves B~^T (r - Lambda F) = 0 with the basis
-  // quantised to 2^-31 (the digit tiles), which moves F by (R^T R)^{-1} E^T r_LS,
-  // |E_ij| <= 2^-31: about 2^-31 |r_LS| per column.  That perturbation (with
-  // pseudo-random signs, twice the size) is solved through R^T R; a node whose
-  // polynomial it moves by more than kBoxChangeRel max |f| over the box goes to
-  // the FP64 tier.  |r_LS| = sqrt(R_LL^2) / sig (column L carries sig r).
+  // The acceptance tests, after every sweep: the change of the fit at the
+  // data |R d| = |Lambda d| against |R F|, and the bound ctot of the change
+  // over the node box against kBoxChangeRel max |f| (with the previous
+  // sweep's values: the contraction rho and the remaining error ~ change *
+  // rho / (1 - rho)).  A node that passes them and the bias test below is
+  // settled: the later sweeps skip it.  On the last sweep a node that has not
+  // settled goes to the FP64 tier.
+  __shared__ int s_conv;
+  const double cthr = kBoxChangeRel * pr.maxabs;
+  if (tid == 0) {
+    unsigned long long* slot = a.mstat + kMStat * node + 4;
+    unsigned long long* cslot = a.mstat + kMStat * node + 6;
+    const double upd = sqrt(wn), zr = sqrt(ztot), prev = __longlong_as_double((long long)*slot);
+    const double cprev = __longlong_as_double((long long)*cslot);
+    *slot = (unsigned long long)__double_as_longlong(upd);
+    *cslot = (unsigned long long)__double_as_longlong(ctot);
+    a.mstat[kMStat * node + 5] = 0ull;  // max |s| of the next sweep
+    bool conv = upd <= kConvergedRel * zr;
+    if (!conv && prev > 0.0 && upd < prev) {
+      const double rho = upd / prev;
+      conv = upd * rho / (1.0 - rho) <= kConvergedRel * zr;
+    }
+    bool cconv = ctot <= cthr;
+    if (!cconv && cprev > 0.0 && ctot < cprev) {
+      const double rho = ctot / cprev;
+      cconv = ctot * rho / (1.0 - rho) <= cthr;
+    }
+    s_conv = conv && cconv;
+  }
+  __syncthreads();
+  // Bias of the quantised basis: the fixed point solves B~^T (r - Lambda F) = 0
+  // with the basis quantised to 2^-31 (the digit tiles), which moves F by
+  // (R^T R)^{-1} E^T r_LS, |E_ij| <= 2^-31: about 2^-31 |r_LS| per column.
+  // That perturbation (with pseudo-random signs, twice the size) is solved
+  // through R^T R and bounded over the box.  |r_LS| = sqrt(R_LL^2) / sig
+  // (column L carries sig r).
+  const bool check = s_conv || a.last_sweep;
   double etot = 0.0;
-  if (a.last_sweep) {
+  if (check) {
     const double rls = sqrt(fmax(R[ro_of(L, m)], 0.0)) / F.sig;
     const double scale = 2.0 * 0x1p-31 * rls;
-    __syncthreads();  // every thread is done with g
     for (int j = tid; j < L; j += kFThreads)
       g[j] = (((uint32_t)j * 2654435761u) >> 16) & 1u ? scale : -scale;
     __syncthreads();
@@ -1179,31 +1213,10 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   }
   legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
   if (tid == 0) {
-    // |R d| = |Lambda d| is the change of the fit at the data, ctot its bound
-    // over the node box; with the previous sweep's values they give the
-    // contraction rho and the remaining error ~ change * rho / (1 - rho)
-    unsigned long long* slot = a.mstat + kMStat * node + 4;
-    unsigned long long* cslot = a.mstat + kMStat * node + 6;
-    const double upd = sqrt(wn), zn = sqrt(ztot), prev = __longlong_as_double((long long)*slot);
-    const double cprev = __longlong_as_double((long long)*cslot);
-    *slot = (unsigned long long)__double_as_longlong(upd);
-    *cslot = (unsigned long long)__double_as_longlong(ctot);
-    a.mstat[kMStat * node + 5] = 0ull;  // max |s| of the next sweep
-    if (a.last_sweep) {
-      bool conv = upd <= kConvergedRel * zn;
-      if (!conv && prev > 0.0 && upd < prev) {
-        const double rho = upd / prev;
-        conv = upd * rho / (1.0 - rho) <= kConvergedRel * zn;
-      }
-      const double cthr = kBoxChangeRel * pr.maxabs;
-      bool cconv = ctot <= cthr;
-      if (!cconv && cprev > 0.0 && ctot < cprev) {
-        const double rho = ctot / cprev;
-        cconv = ctot * rho / (1.0 - rho) <= cthr;
-      }
-      const bool stable = etot <= cthr;  // the basis quantisation's bias, bounded over the box
-      if (!(conv && cconv && stable)) a.flags[node] = (a.flags[node] & ~FMT_FLAG_MIXED) | FMT_FLAG_MIXED_SLOW;
-    }
+    if (s_conv && etot <= cthr)
+      a.mstat[kMStat * node + kSettled] = 1ull;
+    else if (a.last_sweep)
+      a.flags[node] = (a.flags[node] & ~FMT_FLAG_MIXED) | FMT_FLAG_MIXED_SLOW;
   }
 }
 
@@ -1488,6 +1501,7 @@ __global__ void __launch_bounds__(256) k_dfactor(MArgs a) {
     a.mstat[kMStat * node + 4] = 0ull;
     a.mstat[kMStat * node + 5] = 0ull;
     a.mstat[kMStat * node + 6] = 0ull;
+    a.mstat[kMStat * node + kSettled] = 0ull;
   }
   __syncthreads();
   legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
@@ -1504,7 +1518,9 @@ __global__ void __launch_bounds__(256) k_dproj(MArgs a) {
   __shared__ double sv[kDRows];
   const int item = blockIdx.x;
   const int64_t node = a.item_node[item];
-  if ((a.flags[node] & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) != (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) return;
+  if ((a.flags[node] & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) != (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64) ||
+      settled(a, node))
+    return;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const int p = pr.degree, L = fmt_nmono_d(p);
   const int tid = threadIdx.x;
@@ -1544,7 +1560,9 @@ __global__ void __launch_bounds__(kFThreads) k_dupdate(MArgs a) {
   __shared__ double red[kFThreads / 32], red2[kFThreads / 32];
   __shared__ double s_pt[3][FMT_MAX_DEGREE + 1];
   const int64_t node = blockIdx.x;
-  if ((a.flags[node] & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) != (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) return;
+  if ((a.flags[node] & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) != (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64) ||
+      settled(a, node))
+    return;
   const int tid = threadIdx.x;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1;
@@ -1627,12 +1645,36 @@ __global__ void __launch_bounds__(kFThreads) k_dupdate(MArgs a) {
     ctot += red2[i];
     atot += red3[i];
   }
-  // last sweep: the rounding perturbation of the fixed point, solved through R^T R
+  // the acceptance tests after every sweep (as in k_mupdate); a node that
+  // passes them and the rounding test is settled, later sweeps skip it
+  __shared__ int s_conv;
+  const double cthr = kBoxChangeRel * pr.maxabs;
+  if (tid == 0) {
+    unsigned long long* slot = a.mstat + kMStat * node + 4;
+    unsigned long long* cslot = a.mstat + kMStat * node + 6;
+    const double upd = sqrt(wn), zr = sqrt(ztot), prev = __longlong_as_double((long long)*slot);
+    const double cprev = __longlong_as_double((long long)*cslot);
+    *slot = (unsigned long long)__double_as_longlong(upd);
+    *cslot = (unsigned long long)__double_as_longlong(ctot);
+    a.mstat[kMStat * node + 5] = 0ull;
+    bool conv = upd <= kConvergedRel * zr;
+    if (!conv && prev > 0.0 && upd < prev) {
+      const double rho = upd / prev;
+      conv = upd * rho / (1.0 - rho) <= kConvergedRel * zr;
+    }
+    bool cconv = ctot <= cthr;
+    if (!cconv && cprev > 0.0 && ctot < cprev) {
+      const double rho = ctot / cprev;
+      cconv = ctot * rho / (1.0 - rho) <= cthr;
+    }
+    s_conv = conv && cconv;
+  }
+  __syncthreads();
+  // the rounding perturbation of the fixed point, solved through R^T R
   double etot = 0.0;
-  if (a.last_sweep) {
+  if (s_conv || a.last_sweep) {
     const double rn = sqrt(d0[L]) / F.sig;  // |r|: column L of the Gram is sig r
     const double scale = (double)(3 * p + 4) * DBL_EPSILON * (atot + rn);
-    __syncthreads();  // every thread is done with g
     for (int j = tid; j < L; j += kFThreads) {
       const uint32_t hsh = (uint32_t)j * 2654435761u;
       g[j] = ((hsh >> 16) & 1u ? scale : -scale) * sqrt(d0[j]);
@@ -1664,29 +1706,10 @@ __global__ void __launch_bounds__(kFThreads) k_dupdate(MArgs a) {
   }
   legendre_to_moments(Fl, p, F, a.coef + node * a.stride, a.hcoef + node * a.stride, a.stride, ws);
   if (tid == 0) {
-    unsigned long long* slot = a.mstat + kMStat * node + 4;
-    unsigned long long* cslot = a.mstat + kMStat * node + 6;
-    const double upd = sqrt(wn), zr = sqrt(ztot), prev = __longlong_as_double((long long)*slot);
-    const double cprev = __longlong_as_double((long long)*cslot);
-    *slot = (unsigned long long)__double_as_longlong(upd);
-    *cslot = (unsigned long long)__double_as_longlong(ctot);
-    a.mstat[kMStat * node + 5] = 0ull;
-    if (a.last_sweep) {
-      bool conv = upd <= kConvergedRel * zr;
-      if (!conv && prev > 0.0 && upd < prev) {
-        const double rho = upd / prev;
-        conv = upd * rho / (1.0 - rho) <= kConvergedRel * zr;
-      }
-      const double cthr = kBoxChangeRel * pr.maxabs;
-      bool cconv = ctot <= cthr;
-      if (!cconv && cprev > 0.0 && ctot < cprev) {
-        const double rho = ctot / cprev;
-        cconv = ctot * rho / (1.0 - rho) <= cthr;
-      }
-      const bool stable = etot <= kRoundRel * pr.maxabs;  // insensitive to the FP64 rounding
-      if (!(conv && cconv && stable))
-        a.flags[node] = (a.flags[node] & ~(FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) | FMT_FLAG_MIXED_SLOW;
-    }
+    if (s_conv && etot <= kRoundRel * pr.maxabs)  // insensitive to the FP64 rounding
+      a.mstat[kMStat * node + kSettled] = 1ull;
+    else if (a.last_sweep)
+      a.flags[node] = (a.flags[node] & ~(FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) | FMT_FLAG_MIXED_SLOW;
   }
 }
 
