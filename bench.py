@@ -346,7 +346,7 @@ def run_experiments(args, rank, world):
         metric = "tau x N x p sweep (Figs. 2-4): E_rms, E_inf, nodes"
         targets = "N_q = N_p"
     line = {"metric": metric, "unit": "see rows", "n_gpus": world,
-            "dtype": "f64" if prec == F.FMT_FP64 else "f64+bf16x3 (mixed path)", "data": "synthetic",
+            "dtype": "f64" if prec == F.FMT_FP64 else "f64+bf16 (mixed path)", "data": "synthetic",
             "config": {"workload": args.workload, "points": "uniform [0,1)^3", "values": "Franke (Eq. eqF1)",
                        "targets": targets, "min_pts": 0}, "rows": rows}
     if rank == 0:
@@ -412,7 +412,7 @@ def run_serve(args, rank, world):
     line = {"metric": "fitted pts/s and p50/p99 request latency (serving)", "value": float(pts.sum() / span),
             "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": max(args.warmup, 1),
             "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 and f64+bf16x3 per request", "data": "synthetic",
+            "dtype": "f64 and f64+bf16 per request", "data": "synthetic",
             "config": {"workload": "serve: %d requests, Poisson %.0f/s, points log-uniform [1e3, 2e6], targets "
                                    "log-uniform [1, 1e6], p 4..10, FP64 or mixed per request" % (len(reqs), args.rate),
                        "slots": args.slots, "budget_bytes": 150e9, "max_batch_points": 4_000_000,
@@ -720,7 +720,7 @@ def main():
         "metric": METRIC, "value": job_throughput(world, w.n, fit_s), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (fit_s + eval_s) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+bf16x3 (tensor-core Gram, FP64 factor/refine)",
+        "dtype": "f64" if args.precision == "fp64" else "f64+bf16 (tensor-core Gram and projection, FP64 factor/refine)",
         "data": "synthetic",
         "config": {"workload": w.name, "points": w.n, "targets": w.m,
                    "degree": ("%d..%d per problem" % (w.degrees.min(), w.degrees.max())) if is_batch else w.degree,

@@ -154,8 +154,10 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  *    node's points in |t| <= 1.  It spans the same polynomial space as the
  *    moments of Alg. 2, so the least-squares fit is the same function.
  *  - the Gram matrix [B | r]^T [B | r] of the node (r scaled by a power of
- *    two) is formed on the tensor cores from 3-term BF16 splits of FP32
- *    values, FP32 accumulation, promoted to FP64 every 256 rows;
+ *    two) is formed on the tensor cores from split-BF16 operands: each value
+ *    cut into four fixed-point digits (exact BF16 tiles, pre-scaled), the six
+ *    leading digit-tile products accumulated in FP32, promoted to FP64 every
+ *    256 rows;
  *  - its FP64 Cholesky factor is the R-hat = [[R, Q^T r], [0, rho]] of the
  *    FP64 path (same matrix, up to row signs); F = R^{-1} Q^T r;
  *  - `sweeps` refinement steps: s = r - Lambda F in FP64, g = B^T s on the

@@ -335,9 +335,12 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
 }
 
 // ------------------------------------------------------------------ k_mgram
-// Gram mode: the basis in FP32, every value split into three BF16 terms
-// (floating point; the six leading products are accumulated).
-// Projection mode: the basis in double-float (pairs of FP32, about 48 bits)
+// Both modes store the basis (double-float, pairs of FP32, about 48 bits) as
+// the four pre-scaled digit tiles below.  Gram mode: the six leading tile
+// products (digit indices q_a + q_b <= 2, a split-BF16 product of about 24
+// bits) are accumulated together in FP32 in tensor memory and drained into a
+// double-float copy every 256 rows (not exact: the products' weights differ).
+// Projection mode: the basis tiles
 // and s in FP64, both cut into four signed 8-bit digits of a fixed-point
 // number (|P_l(t)| <= 1 for |t| <= 1, and |s| is scaled below 1 per node):
 //   v = (d0 2^23 + d1 2^15 + d2 2^7 + d3) 2^-30,   |d| <= 128,

@@ -1,7 +1,7 @@
 """Mixed-precision fit (FMT_MIXED) against the FP64 oracle.
 
 The mixed path computes each node's least-squares fit (Alg. 2) from a Gram
-matrix formed on the tensor cores (3-term BF16 splits, FP32 accumulation,
+matrix formed on the tensor cores (split-BF16 digit tiles, FP32 accumulation,
 FP64 promotion), an FP64 Cholesky factor and FP64 refinement sweeps.  Nodes
 that tier cannot fit (ill-conditioned, not converged, degree above 9) go to
 its FP64 normal-equations tier (FP64 Gram, Cholesky, corrected semi-normal
