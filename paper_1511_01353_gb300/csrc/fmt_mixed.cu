@@ -340,9 +340,9 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
 // products (digit indices q_a + q_b <= 2, a split-BF16 product of about 24
 // bits) are accumulated together in FP32 in tensor memory and drained into a
 // double-float copy every 256 rows (not exact: the products' weights differ).
-// Projection mode: the basis tiles
-// and s in FP64, both cut into four signed 8-bit digits of a fixed-point
-// number (|P_l(t)| <= 1 for |t| <= 1, and |s| is scaled below 1 per node):
+// Projection mode: the basis tiles times the digits of s (FP64), both
+// values cut into four signed 8-bit digits of a fixed-point number
+// (|P_l(t)| <= 1 for |t| <= 1, and |s| is scaled below 1 per node):
 //   v = (d0 2^23 + d1 2^15 + d2 2^7 + d3) 2^-30,   |d| <= 128,
 // so every digit is an exact BF16 integer and each digit pair's sum over 256
 // rows stays below 2^22: the FP32 tensor-core accumulation is exact, each
