@@ -920,13 +920,19 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   const int tid = threadIdx.x;
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
   const int ncols = gram_cols(m);
+  // Shared: G | rk | invd | Fl (114.9 KB at degree 8, so two CTAs fit on an
+  // SM); the change of basis at the end reuses G, rk and invd, and the pivot
+  // test reads the Gram's diagonal from global memory (thread 0 only).
   double* G = fsm;
   double* rk = G + ro_of(m, m);
-  double* d0 = rk + m;
-  double* invd = d0 + m;
+  double* invd = rk + m;
   double* Fl = invd + m;
-  double* ws = Fl + m;
+  double* ws = G;
   const int64_t i0 = a.node_item0[node];
+  const double* Gg = a.acc + i0 * a.acc_stride;  // the summed Gram, band layout (column c, lane i)
+  auto diag0 = [&](int k) {  // G[k][k] before the factorisation
+    return Gg[k < 128 ? (int64_t)k * 129 : (int64_t)(Lp + k - 128) * 128 + (k - b1)];
+  };
   // 1. the node's FP64 Gram (column c, lane i), summed over items by k_mreduce
   for (int e = tid; e < ncols * 128; e += kFThreads) {
     const int c = e >> 7, lane = e & 127;
@@ -943,8 +949,6 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
     if (gi > gj || gj >= m) continue;
     G[ro_of(gi, m) + (gj - gi)] = a.acc[i0 * a.acc_stride + e];
   }
-  __syncthreads();
-  for (int k = tid; k < L; k += kFThreads) d0[k] = G[ro_of(k, m)];
   // 2. Cholesky, right-looking, on the packed rows; column L (r) is carried
   // along.  Thread 0 forms each pivot's square root and reciprocal once (it
   // updates the next pivot G[k+1][k+1] itself, first in its trailing tile):
@@ -952,8 +956,8 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   __shared__ double s_rkk, s_irk;
   __shared__ int s_bad;
   auto pivot = [&](int k) {  // thread 0
-    const double d = G[ro_of(k, m)];
-    s_bad = !(d0[k] > 0.0 && d > kPivotFloor * d0[k]);
+    const double d = G[ro_of(k, m)], d0 = diag0(k);
+    s_bad = !(d0 > 0.0 && d > kPivotFloor * d0);
     if (!s_bad) {
       s_rkk = sqrt(d);
       s_irk = 1.0 / s_rkk;
@@ -991,7 +995,9 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
     Fl[k] = Fl[k] / F.sig;
     a.lcoef[node * a.stride + k] = Fl[k];
   }
-  // keep R-hat for the sweeps in the node's first accumulator
+  // keep R-hat for the sweeps in the node's first accumulator (the Gram there
+  // has been read for the last time: every pivot test is done)
+  __syncthreads();
   double* Rg = a.acc + i0 * a.acc_stride;
   for (int64_t e = tid; e < ro_of(m, m); e += kFThreads) Rg[e] = G[e];
   __syncthreads();
@@ -1836,9 +1842,8 @@ size_t mixed_cache_bytes(const fmt_tree* t, int depth) {
   return (size_t)(L.n_items + t->n / kAtom + 2) * 4 * (size_t)mrows_for(mixed_m_cap(L.max_m)) * 128;
 }
 
-size_t mixed_factor_smem(int max_m) {
-  const int p_max = FMT_MIXED_MAX_DEGREE;
-  return sizeof(double) * ((size_t)ro_of(max_m, max_m) + 4 * (size_t)max_m + conv_ws_doubles(p_max));
+size_t mixed_factor_smem(int max_m) {  // G | rk | invd | Fl; the conversion scratch reuses G, rk, invd
+  return sizeof(double) * ((size_t)ro_of(max_m, max_m) + 3 * (size_t)max_m);
 }
 
 cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
