@@ -1049,11 +1049,13 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
   const int64_t i0 = a.node_item0[node];
   const int ni = a.node_nitems[node];
+  // Shared: R | g | invd | Fl (114.9 KB at degree 8: two CTAs per SM); the
+  // change of basis at the end reuses R, g and invd, which are dead by then.
   double* R = usm;  // R-hat rows 0..L-1, packed (row i at ro(i)), copied from the node's first accumulator
   double* g = R + ro_of(m, m);
-  double* Fl = g + m;
-  double* invd = Fl + m;
-  double* ws = invd + m;
+  double* invd = g + m;
+  double* Fl = invd + m;
+  double* ws = R;
   {
     const double* Rg = a.acc + i0 * a.acc_stride;
     for (int64_t e = tid; e < ro_of(m, m); e += kFThreads) R[e] = Rg[e];
@@ -1876,7 +1878,7 @@ cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bu
   MArgs a = make_margs(t, depth, b);
   a.last_sweep = last ? 1 : 0;
   const int mc = mixed_m_cap(L.max_m);
-  const size_t smem = sizeof(double) * ((size_t)ro_of(mc, mc) + 3 * (size_t)mc + conv_ws_doubles(FMT_MIXED_MAX_DEGREE));
+  const size_t smem = sizeof(double) * ((size_t)ro_of(mc, mc) + 3 * (size_t)mc);
   cudaError_t e = cudaFuncSetAttribute(k_mupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_mupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
