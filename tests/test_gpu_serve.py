@@ -25,6 +25,16 @@ def requests(k, seed_offset=0):
     return out
 
 
+def blocker(seed=0):
+    # a request large enough (4e5 points, degree 8) to keep a worker busy for
+    # far longer than the test takes to submit the others, so that they queue
+    # behind it and form batches whatever the timing of the submissions
+    rng = np.random.default_rng(1000 + seed)
+    x, y, z = rng.uniform(0, 1, (3, 400_000))
+    q = rng.uniform(0, 1, (3, 10))
+    return (F.make_params(8, 3, 1, 1e-3), x, y, z, np.sin(3 * x) * y + z, *q)
+
+
 def tol_of(req):
     rel = 1e-10 if req[0].precision == F.FMT_FP64 else 1e-6
     return rel * np.max(np.abs(req[4]))
@@ -41,6 +51,7 @@ def test_each_result_same_alone_and_in_the_mix():
         alone.append(out)
     sv.close()
     sv = F.Server(slots=2, max_batch_points=60000)
+    held = [sv.submit(*blocker(k)) for k in range(2)]  # both workers busy while the requests queue
     tickets = [sv.submit(*r) for r in reqs]
     mixed_batches = 0
     for r, t, a in zip(reqs, tickets, alone):
@@ -48,6 +59,8 @@ def test_each_result_same_alone_and_in_the_mix():
         assert info["status"] == F.FMT_OK
         mixed_batches = max(mixed_batches, info["batch_requests"])
         assert np.max(np.abs(out - a)) <= tol_of(r), (r[0].precision, np.max(np.abs(out - a)))
+    for t in held:
+        assert sv.wait(t)[1]["status"] == F.FMT_OK
     sv.close()
     assert mixed_batches > 1  # requests were batched together
 
@@ -85,8 +98,8 @@ def test_budget_rejects_a_request_that_can_never_fit():
 def test_requests_arriving_during_a_batch_join_the_next_one():
     reqs = requests(8, 2)
     sv = F.Server(slots=1)
-    first = sv.submit(*reqs[0])
-    later = [sv.submit(*r) for r in reqs[1:]]  # queued while the first batch runs
+    first = sv.submit(*blocker())
+    later = [sv.submit(*r) for r in reqs]  # queued while the first batch runs
     _, i0 = sv.wait(first)
     infos = [sv.wait(t)[1] for t in later]
     sv.close()
