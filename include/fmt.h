@@ -317,7 +317,12 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
  * recorded on the launching stream right before and after each launch, plus
  * the work units the launch processed (rows for tile_qr/residual, node pairs
  * for combine, nodes for back_solve/refine, targets x fitted levels for
- * evaluate, points for the build kernels).
+ * evaluate, points for the build kernels).  tile_qr counts one launch per
+ * degree present in the level.  The class "graph_launch" counts the graphs
+ * launched under FMT_OPT_GRAPH (units: those that reused an executable graph
+ * updated in place); the kernels inside are counted in their own classes, and
+ * their events are recorded inside the graph.  The mixed path's classes are
+ * mixed_* (tensor-core tier) and fp64_* (its FP64 normal-equations tier).
  * fmt_profile_enable(1) resets the counters and starts event timing;
  * fmt_profile_enable(0) stops it.  fmt_profile_read synchronises the device.
  */
