@@ -69,6 +69,8 @@ def parse_args():
                     help="time QR launch configurations (fmt_autotune) for the workload's degrees before the run")
     ap.add_argument("--sweep-max-exp", type=int, default=7,
                     help="sweep: largest N = 8^E (E <= 9; degree 12 runs up to 8^7)")
+    ap.add_argument("--sweep-min-exp", type=int, default=4, help="sweep: smallest N = 8^E (E >= 4)")
+    ap.add_argument("--sweep-tols", default="1e-6,1e-8,1e-10,1e-12", help="sweep: comma-separated tol_rel values")
     return ap.parse_args()
 
 
@@ -332,14 +334,14 @@ def run_experiments(args, rank, world):
         targets = 100_000
     else:
         emax = max(4, min(9, args.sweep_max_exp))
-        for e in range(4, emax + 1):
+        for e in range(max(4, args.sweep_min_exp), emax + 1):
             n = 8 ** e
             pts = cloud(n, 1 + n)
             tgt = cloud(n, 9)
             for p in (4, 8, 12):
                 if p == 12 and e > 7:
                     continue  # about 100 s per fit at 8^8 on the FP64 path
-                for k, tol in enumerate((1e-6, 1e-8, 1e-10, 1e-12)):
+                for k, tol in enumerate(float(v) for v in args.sweep_tols.split(",")):
                     rows.append(run(pts, tgt, p, 10, tol, k == 0))
             del pts, tgt
             torch.cuda.empty_cache()
