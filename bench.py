@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--points", type=int, default=0, help="override the number of points")
     ap.add_argument("--targets", type=int, default=0, help="override the number of targets")
     ap.add_argument("--cpu-points", type=int, default=200_000, help="oracle sample size for cpu_baseline")
+    ap.add_argument("--cpu-points-serial", type=int, default=50_000,
+                    help="oracle sample for cpu_baseline.single_core (0 = skip)")
     ap.add_argument("--ref-points", type=int, default=40_000, help="oracle sample per step for --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -263,10 +265,20 @@ def cpu_baseline(args):
     t1 = time.perf_counter()
     T.evaluate(w.xq, w.yq, w.zq)
     t2 = time.perf_counter()
-    return {"value": w.n / (t1 - t0), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": "%s: %d points (same recipe, p, depth, min_pts, tol), fit %.2f s; OpenMP over sibling "
-                      "subtrees, each node serial" % (w.name, w.n, t1 - t0),
-            "evals_per_s": w.m / (t2 - t1)}
+    out = {"value": w.n / (t1 - t0), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+           "sample": "%s: %d points (same recipe, p, depth, min_pts, tol), fit %.2f s; OpenMP over sibling "
+                     "subtrees, each node serial" % (w.name, w.n, t1 - t0),
+           "evals_per_s": w.m / (t2 - t1)}
+    ns = args.cpu_points_serial
+    if ns > 0:
+        # the same oracle on one core: Alg. 1's depth-first recursion as printed
+        ws = W.scale(n=ns, n_targets=1) if args.workload == "scale" else W.small()
+        t0 = time.perf_counter()
+        O.fit(ws.x, ws.y, ws.z, ws.f, ws.degree, ws.max_depth, ws.min_pts, ws.tol_rel, mode="dfs")
+        dt = time.perf_counter() - t0
+        out["single_core"] = {"value": ws.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": "%s: %d points, depth-first on one thread, fit %.2f s" % (ws.name, ws.n, dt)}
+    return out
 
 
 def run_experiments(args, rank, world):
