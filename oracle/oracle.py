@@ -30,23 +30,31 @@ FLAG_RANK = 2
 FLAG_DEG_CLAMPED = 4
 
 
+def compile_library(src: str, out: str) -> None:
+    """gcc build of an oracle source: IEEE FP64, no contraction, OpenMP."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (IEEE FP64, no contraction, OpenMP)."""
+    """Compile oracle/fmt_oracle.c into oracle/liboracle.so when it is stale."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        compile_library(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
 
 
 def lib():
+    """The loaded oracle library.  FMT_ORACLE_LIB names another build of an
+    oracle source to load instead (the mutation test loads deliberately broken
+    copies this way, in child processes)."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB)
+            path = os.environ.get("FMT_ORACLE_LIB") or build()
+            L = ctypes.CDLL(path)
             d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
             P = ctypes.c_void_p
             L.ora_nmono.argtypes = [i32]

@@ -149,6 +149,29 @@ def test_fit_node_sign_of_zero_alpha():
     assert np.allclose(F[[0, 2, 3]], Fr, atol=1e-13)
 
 
+def test_fit_node_no_cancellation_in_the_reflector():
+    # Column 1 of the degree-1 basis is w.  The data make the w column, after
+    # the first reflector, almost e_1 with tails of size delta: had the first
+    # reflector taken beta = +sign(alpha)*||x|| (x the column from the pivot
+    # down), alpha - beta would cancel
+    # in the second column.  The dgeqr2 sign (beta = -sign(alpha)*||x||,
+    # |alpha - beta| >= |alpha|) never cancels, so the fit stays exact to
+    # rounding against rational least squares.
+    rng = np.random.default_rng(3)
+    n, delta = 24, 1e-7
+    t = np.concatenate([[1.0], delta * rng.choice([-1.0, 1.0], n - 2)])
+    w = np.concatenate([[0.0], t - t.sum() / (math.sqrt(n) - 1.0)])
+    u, v = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    r = rng.normal(size=n)
+    rows = [[Fraction(float(a)) ** l * Fraction(float(b)) ** m * Fraction(float(c)) ** k for l, m, k in BF.exponents(1)]
+            for a, b, c in zip(u, v, w)]
+    Fx = np.array([float(q) for q in _exact_ls(rows, [Fraction(float(q)) for q in r])])
+    F, _, flags = O.fit_node(1, u, v, w, r)
+    assert flags == 0
+    cond = np.linalg.cond(BF.basis(1, u, v, w))
+    assert np.max(np.abs(F - Fx)) <= 50 * cond * 2.2e-16 * np.max(np.abs(Fx))
+
+
 # ---------------------------------------------------------------- whole tree
 def _small_case(n=1500, seed=5):
     rng = np.random.default_rng(seed)
@@ -176,6 +199,41 @@ def test_tree_matches_independent_svd_restatement():
         assert np.max(np.abs(T.coef[i] - bn["coef"])) <= 1e-9 * scale
         assert np.allclose(T.child_E[i], bn["childE"], rtol=1e-7, atol=1e-12)
     assert np.max(np.abs(T.resid - bf_r)) <= 1e-11 * T.maxabs
+
+
+def test_tree_reaches_max_depth_and_matches_restatement():
+    # tau = 0: every child with at least max(L, min_pts) points refines, so the
+    # tree is the full octree down to D_max = 2 and no deeper (Alg. 1 stops at
+    # the depth limit); the brute-force restatement makes the same decisions
+    rng = np.random.default_rng(17)
+    n = 4000
+    x, y, z = (rng.uniform(0, 1, n) for _ in range(3))
+    f = W.franke_bj(x, y, z)
+    p, D, mp = 1, 2, 4
+    T = O.fit(x, y, z, f, p, D, mp, 0.0)
+    counts = np.bincount(T.depth, minlength=D + 1)
+    assert counts.tolist() == [1, 8, 64]
+    bf_nodes, bf_r, _ = BF.fmt_tree(x, y, z, f, p, D, mp, 0.0)
+    keys = {(int(T.depth[i]),) + tuple(int(a) for a in T.ixyz[i]): i for i in range(T.n_nodes)}
+    assert set(keys) == set(bf_nodes)
+    for k, i in keys.items():
+        assert np.max(np.abs(T.coef[i] - bf_nodes[k]["coef"])) <= 1e-10 * max(1.0, np.max(np.abs(T.coef[i])))
+    assert np.max(np.abs(T.resid - bf_r)) <= 1e-12 * T.maxabs
+
+
+def test_sign_symmetry():
+    # tau = tol_rel * max|f| is even in f and every other step is odd in the
+    # residual, and round-to-nearest is symmetric under negation: fitting -f
+    # gives the same tree with every coefficient and residual negated, bitwise
+    x, y, z, f = _small_case(2500, 19)
+    a = O.fit(x, y, z, f, 3, 3, 20, 1e-4)
+    b = O.fit(x, y, z, -f, 3, 3, 20, 1e-4)
+    assert a.tau == b.tau == 1e-4 * float(np.max(np.abs(f)))
+    assert a.n_nodes == b.n_nodes > 9
+    assert np.array_equal(a.depth, b.depth) and np.array_equal(a.ixyz, b.ixyz)
+    assert np.array_equal(a.coef, -b.coef)
+    assert np.array_equal(a.resid, -b.resid)
+    assert np.array_equal(a.child_E, b.child_E)
 
 
 def test_polynomial_reproduction():
