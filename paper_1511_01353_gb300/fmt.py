@@ -192,13 +192,48 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dptr(t, name):
+def _ptrs(stream, *specs):
+    """Device pointers of caller-owned tensors, checked before the library
+    sees them (the library cannot check a device buffer's size).
+
+    Each spec is (tensor, name, dtype, count, exact): a contiguous torch
+    tensor of that dtype with exactly `count` elements (at least `count` when
+    `exact` is False, for outputs), on the CUDA device the call runs on (the
+    stream's, else the current device).  A wrong type, dtype, layout or
+    device raises TypeError; a wrong size FmtError(FMT_EINVAL).  Sizes are
+    checked first, then the device."""
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError("%s must be a CUDA tensor" % name)
-    if t.dtype != torch.float64 or not t.is_contiguous():
-        raise TypeError("%s must be a contiguous float64 tensor" % name)
-    return ctypes.c_void_p(t.data_ptr())
+    for t, name, dtype, count, exact in specs:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s must be a torch tensor" % name)
+        if t.dtype != dtype or not t.is_contiguous():
+            raise TypeError("%s must be a contiguous %s tensor" % (name, str(dtype).replace("torch.", "")))
+        k = t.numel()
+        if (k != count) if exact else (k < count):
+            raise FmtError(FMT_EINVAL, "%s has %d elements; %s %d" % (name, k, "expected" if exact else
+                                                                       "needs at least", count))
+    for t, name, *_ in specs:
+        if not t.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+    sdev = getattr(stream, "device", None) if stream is not None else None
+    dev = sdev.index if sdev is not None else torch.cuda.current_device()
+    for t, name, *_ in specs:
+        if t.device.index != dev:
+            raise TypeError("%s is on %s, the call runs on cuda:%d" % (name, t.device, dev))
+    return [ctypes.c_void_p(t.data_ptr()) for t, *_ in specs]
+
+
+def _f64(n, **named):
+    """_ptrs specs of float64 buffers of exactly n elements, in keyword order."""
+    import torch
+    return [(t, name, torch.float64, n, True) for name, t in named.items()]
+
+
+def _numel(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    return int(t.numel())
 
 
 class Tree:
@@ -240,11 +275,11 @@ def fmt_nmono(degree: int) -> int:
 
 
 def oct_build(params: fmt_params, x, y, z, f, stream=None) -> Tree:
+    n = _numel(x, "x")
+    px, py, pz, pf = _ptrs(stream, *_f64(n, x=x, y=y, z=z, f=f))
     L = load()
     h = ctypes.c_void_p()
-    n = int(x.numel())
-    st = L.oct_build(ctypes.byref(params), n, _dptr(x, "x"), _dptr(y, "y"), _dptr(z, "z"), _dptr(f, "f"),
-                     _stream_handle(stream), ctypes.byref(h))
+    st = L.oct_build(ctypes.byref(params), n, px, py, pz, pf, _stream_handle(stream), ctypes.byref(h))
     _check(st)
     return Tree(h)
 
@@ -252,16 +287,23 @@ def oct_build(params: fmt_params, x, y, z, f, stream=None) -> Tree:
 def oct_build_batch(params: fmt_params, offsets, x, y, z, f, degrees=None, boxes=None, stream=None) -> Tree:
     """Forest of independent problems: offsets (n_problems+1, host), per-problem
     degrees (host int32) and boxes (host, 4 per problem: lo x, lo y, lo z, side)."""
-    L = load()
-    off = np.ascontiguousarray(offsets, dtype=np.int64)
-    deg = None if degrees is None else np.ascontiguousarray(degrees, dtype=np.int32)
+    off = np.ascontiguousarray(offsets, dtype=np.int64).reshape(-1)
+    if off.shape[0] < 2:
+        raise FmtError(FMT_EINVAL, "offsets needs n_problems + 1 >= 2 entries")
+    n_prob = int(off.shape[0] - 1)
+    deg = None if degrees is None else np.ascontiguousarray(degrees, dtype=np.int32).reshape(-1)
     box = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1)
+    if deg is not None and deg.shape[0] != n_prob:
+        raise FmtError(FMT_EINVAL, "degrees has %d entries; expected %d" % (deg.shape[0], n_prob))
+    if box is not None and box.shape[0] != 4 * n_prob:
+        raise FmtError(FMT_EINVAL, "boxes has %d values; expected 4 per problem (%d)" % (box.shape[0], 4 * n_prob))
+    px, py, pz, pf = _ptrs(stream, *_f64(int(off[-1]), x=x, y=y, z=z, f=f))
+    L = load()
     h = ctypes.c_void_p()
-    st = L.oct_build_batch(ctypes.byref(params), int(off.shape[0] - 1), off.ctypes.data_as(ctypes.c_void_p),
+    st = L.oct_build_batch(ctypes.byref(params), n_prob, off.ctypes.data_as(ctypes.c_void_p),
                            None if deg is None else deg.ctypes.data_as(ctypes.c_void_p),
                            None if box is None else box.ctypes.data_as(ctypes.c_void_p),
-                           _dptr(x, "x"), _dptr(y, "y"), _dptr(z, "z"), _dptr(f, "f"), _stream_handle(stream),
-                           ctypes.byref(h))
+                           px, py, pz, pf, _stream_handle(stream), ctypes.byref(h))
     _check(st)
     return Tree(h)
 
@@ -277,10 +319,12 @@ def refine(tree: Tree, depth: int, stream=None) -> int:
 
 
 def evaluate(tree: Tree, xq, yq, zq, out, count_outside=False, stream=None):
-    m = int(xq.numel())
+    import torch
+    m = _numel(xq, "xq")
+    px, py, pz, po = _ptrs(stream, *_f64(m, xq=xq, yq=yq, zq=zq), (out, "out", torch.float64, m, False))
     nout = ctypes.c_int64(0)
-    st = load().evaluate(tree.handle, m, _dptr(xq, "xq"), _dptr(yq, "yq"), _dptr(zq, "zq"), _dptr(out, "out"),
-                         ctypes.byref(nout) if count_outside else None, _stream_handle(stream))
+    st = load().evaluate(tree.handle, m, px, py, pz, po, ctypes.byref(nout) if count_outside else None,
+                         _stream_handle(stream))
     _check(st, tree)
     return int(nout.value) if count_outside else None
 
@@ -288,14 +332,13 @@ def evaluate(tree: Tree, xq, yq, zq, out, count_outside=False, stream=None):
 def evaluate_batch(tree: Tree, target_problem, xq, yq, zq, out, count_outside=False, stream=None):
     """target_problem: int32 CUDA tensor with the problem index of every target."""
     import torch
-    if not (isinstance(target_problem, torch.Tensor) and target_problem.is_cuda and
-            target_problem.dtype == torch.int32 and target_problem.is_contiguous()):
-        raise TypeError("target_problem must be a contiguous int32 CUDA tensor")
-    m = int(xq.numel())
+    m = _numel(xq, "xq")
+    px, py, pz, pt, po = _ptrs(stream, *_f64(m, xq=xq, yq=yq, zq=zq),
+                               (target_problem, "target_problem", torch.int32, m, True),
+                               (out, "out", torch.float64, m, False))
     nout = ctypes.c_int64(0)
-    st = load().evaluate_batch(tree.handle, m, ctypes.c_void_p(target_problem.data_ptr()), _dptr(xq, "xq"),
-                               _dptr(yq, "yq"), _dptr(zq, "zq"), _dptr(out, "out"),
-                               ctypes.byref(nout) if count_outside else None, _stream_handle(stream))
+    st = load().evaluate_batch(tree.handle, m, pt, px, py, pz, po, ctypes.byref(nout) if count_outside else None,
+                               _stream_handle(stream))
     _check(st, tree)
     return int(nout.value) if count_outside else None
 
@@ -397,14 +440,19 @@ def fmt_fit_node_static(degree: int, x, y, z, r_in, coef, r_out, flags=None, lo=
     CUDA tensor.  The library allocates nothing for this call."""
     import torch
     lo_a = (ctypes.c_double * 3)(*lo)
-    fp = None
+    n = _numel(x, "x")
+    ncoef = fmt_nmono(degree) if degree >= 0 else 0
+    if _numel(coef, "coef") < ncoef:
+        raise FmtError(FMT_EINVAL, "coef has %d elements; degree %d needs %d" % (coef.numel(), degree, ncoef))
+    specs = _f64(n, x=x, y=y, z=z, r_in=r_in) + [(coef, "coef", torch.float64, ncoef, False),
+                                                  (r_out, "r_out", torch.float64, n, False)]
     if flags is not None:
-        if not (isinstance(flags, torch.Tensor) and flags.is_cuda and flags.dtype == torch.int32):
-            raise TypeError("flags must be an int32 CUDA tensor")
-        fp = ctypes.c_void_p(flags.data_ptr())
-    st = load().fmt_fit_node_static(degree, int(x.numel()), _dptr(x, "x"), _dptr(y, "y"), _dptr(z, "z"),
-                                    _dptr(r_in, "r_in"), ctypes.cast(lo_a, ctypes.c_void_p), side,
-                                    _dptr(coef, "coef"), _dptr(r_out, "r_out"), fp, _stream_handle(stream))
+        specs.append((flags, "flags", torch.int32, 1, False))
+    ptrs = _ptrs(stream, *specs)
+    px, py, pz, pr, pc, po = ptrs[:6]
+    fp = ptrs[6] if flags is not None else None
+    st = load().fmt_fit_node_static(degree, n, px, py, pz, pr, ctypes.cast(lo_a, ctypes.c_void_p), side, pc, po,
+                                    fp, _stream_handle(stream))
     _check(st)
 
 
@@ -566,9 +614,17 @@ class Server:
         return float(load().fmt_server_clock())
 
     def submit(self, params: fmt_params, x, y, z, f, xq=None, yq=None, zq=None) -> int:
-        arr = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, f)]
-        q = [np.ascontiguousarray(a, dtype=np.float64) for a in (xq, yq, zq)] if xq is not None else \
+        arr = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (x, y, z, f)]
+        if xq is None and (yq is not None or zq is not None):
+            raise FmtError(FMT_EINVAL, "targets need all of xq, yq, zq")
+        q = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (xq, yq, zq)] if xq is not None else \
             [np.zeros(0) for _ in range(3)]
+        for name, a in zip(("y", "z", "f"), arr[1:]):
+            if a.shape[0] != arr[0].shape[0]:
+                raise FmtError(FMT_EINVAL, "%s has %d points; x has %d" % (name, a.shape[0], arr[0].shape[0]))
+        for name, a in zip(("yq", "zq"), q[1:]):
+            if a.shape[0] != q[0].shape[0]:
+                raise FmtError(FMT_EINVAL, "%s has %d targets; xq has %d" % (name, a.shape[0], q[0].shape[0]))
         out = np.empty(q[0].shape[0], dtype=np.float64)
         r = fmt_request()
         r.params = params

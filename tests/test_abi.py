@@ -161,3 +161,70 @@ def test_failure_diagnostics_check_arguments_on_the_host():
     assert lib.fmt_debug_fail_alloc(0) == F.FMT_OK
     assert lib.fmt_wait_probe(10, None) == F.FMT_EINVAL  # bound below 1 us
     assert lib.fmt_wait_probe(10 ** 11, None) == F.FMT_EINVAL
+
+
+def test_binding_checks_buffer_sizes_before_any_call():
+    # The library cannot see the size of a device buffer, so the binding
+    # checks every tensor against the counts the call passes: a short buffer
+    # would otherwise be read or written out of bounds on the device.
+    torch = pytest.importorskip("torch")
+    v = lambda n, dt=torch.float64: torch.zeros(n, dtype=dt)  # noqa: E731
+    p = F.make_params(2, 3, 10, 1e-4)
+    with pytest.raises(F.FmtError) as e:
+        F.oct_build(p, v(6), v(5), v(6), v(6))
+    assert e.value.status == F.FMT_EINVAL and "y has 5 elements" in str(e.value)
+    with pytest.raises(F.FmtError):
+        F.oct_build(p, v(6), v(6), v(6), v(7))
+    with pytest.raises(TypeError, match="CUDA"):  # right sizes: then the device is checked
+        F.oct_build(p, v(6), v(6), v(6), v(6))
+    with pytest.raises(TypeError, match="float64"):
+        F.oct_build(p, v(6), v(6, torch.float32), v(6), v(6))
+    with pytest.raises(TypeError, match="contiguous"):
+        F.oct_build(p, v(6), v(12)[::2], v(6), v(6))
+    with pytest.raises(TypeError):
+        F.oct_build(p, [0.0] * 6, v(6), v(6), v(6))
+
+    x = v(100)
+    with pytest.raises(F.FmtError, match="expected 90"):  # offsets end short of the buffers
+        F.oct_build_batch(p, [0, 40, 90], x, x, x, x)
+    with pytest.raises(F.FmtError, match="degrees"):
+        F.oct_build_batch(p, [0, 40, 100], x, x, x, x, degrees=[3])
+    with pytest.raises(F.FmtError, match="boxes"):
+        F.oct_build_batch(p, [0, 40, 100], x, x, x, x, boxes=[0.0, 0.0, 0.0, 1.0])
+    with pytest.raises(F.FmtError, match="offsets"):
+        F.oct_build_batch(p, [0], x, x, x, x)
+
+    t = F.Tree(None)  # never reached: the checks come first
+    with pytest.raises(F.FmtError, match="out has 9 elements"):
+        F.evaluate(t, v(10), v(10), v(10), v(9))
+    with pytest.raises(F.FmtError, match="zq"):
+        F.evaluate(t, v(10), v(10), v(11), v(10))
+    with pytest.raises(TypeError, match="CUDA"):  # a larger output buffer is allowed
+        F.evaluate(t, v(10), v(10), v(10), v(12))
+    with pytest.raises(F.FmtError, match="target_problem"):
+        F.evaluate_batch(t, v(9, torch.int32), v(10), v(10), v(10), v(10))
+    with pytest.raises(TypeError, match="int32"):
+        F.evaluate_batch(t, v(10, torch.int64), v(10), v(10), v(10), v(10))
+
+    with pytest.raises(F.FmtError, match="degree 4 needs 35"):
+        F.fmt_fit_node_static(4, v(50), v(50), v(50), v(50), v(34), v(50))
+    with pytest.raises(F.FmtError, match="r_out"):
+        F.fmt_fit_node_static(4, v(50), v(50), v(50), v(50), v(35), v(49))
+    with pytest.raises(F.FmtError, match="r_in"):
+        F.fmt_fit_node_static(4, v(50), v(50), v(50), v(51), v(35), v(50))
+    with pytest.raises(F.FmtError, match="flags"):
+        F.fmt_fit_node_static(4, v(50), v(50), v(50), v(50), v(35), v(50), flags=v(0, torch.int32))
+
+
+def test_server_submit_checks_host_array_sizes():
+    import numpy as np
+    srv = object.__new__(F.Server)  # no engine: the checks come before the call
+    srv.handle, srv._live = None, {}
+    p = F.make_params(2, 3, 10, 1e-4)
+    a = np.zeros(8)
+    with pytest.raises(F.FmtError, match="f has 7 points"):
+        srv.submit(p, a, a, a, np.zeros(7))
+    with pytest.raises(F.FmtError, match="zq has 3 targets"):
+        srv.submit(p, a, a, a, a, np.zeros(4), np.zeros(4), np.zeros(3))
+    with pytest.raises(F.FmtError, match="all of xq"):
+        srv.submit(p, a, a, a, a, None, np.zeros(4), np.zeros(4))
