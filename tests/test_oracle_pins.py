@@ -236,6 +236,41 @@ def test_sign_symmetry():
     assert np.array_equal(a.child_E, b.child_E)
 
 
+def test_power_of_two_value_scaling():
+    # every step is linear in the residual, E_RMS and tau scale with |f|, and
+    # scaling by a power of two commutes with IEEE rounding: fitting 4 f
+    # gives the same tree with 4x every coefficient, residual, E and tau
+    x, y, z, f = _small_case(2500, 23)
+    a = O.fit(x, y, z, f, 3, 3, 20, 1e-4)
+    b = O.fit(x, y, z, 4.0 * f, 3, 3, 20, 1e-4)
+    assert b.tau == 4.0 * a.tau and a.n_nodes == b.n_nodes > 9
+    assert np.array_equal(a.ixyz, b.ixyz) and np.array_equal(a.npts, b.npts)
+    assert np.array_equal(4.0 * a.coef, b.coef)
+    assert np.array_equal(4.0 * a.resid, b.resid)
+    assert np.array_equal(4.0 * a.child_E, b.child_E)
+
+
+def test_dyadic_rescaling_of_the_domain():
+    # doubling the points, lo and side doubles every box centre and halves
+    # every frame scale exactly, so the node coordinates (x - c) * s and the
+    # quantised codes are bitwise unchanged (Sec. 4 maps each box onto
+    # [-1,1]^3): the same tree, coefficients and residual; evaluation at the
+    # doubled targets gives the same values
+    x, y, z, f = _small_case(2500, 29)
+    lo = (0.25, -0.5, 0.125)
+    x, y, z = x + lo[0], y + lo[1], z + lo[2]
+    a = O.fit(x, y, z, f, 3, 3, 20, 1e-4, lo=lo)
+    b = O.fit(2 * x, 2 * y, 2 * z, f, 3, 3, 20, 1e-4, lo=tuple(2 * t for t in lo), side=2.0)
+    assert a.n_nodes == b.n_nodes > 9
+    assert np.array_equal(a.ixyz, b.ixyz) and np.array_equal(a.npts, b.npts)
+    assert np.array_equal(a.coef, b.coef) and np.array_equal(a.resid, b.resid)
+    rng = np.random.default_rng(31)
+    q = rng.uniform(0, 1, (3, 400)) + np.array(lo)[:, None]
+    va, _ = a.evaluate(*q)
+    vb, _ = b.evaluate(*(2 * q))
+    assert np.array_equal(va, vb)
+
+
 def test_polynomial_reproduction():
     rng = np.random.default_rng(21)
     p = 3
