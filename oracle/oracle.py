@@ -30,10 +30,11 @@ FLAG_RANK = 2
 FLAG_DEG_CLAMPED = 4
 
 
-def compile_library(src: str, out: str) -> None:
-    """gcc build of an oracle source: IEEE FP64, no contraction, OpenMP."""
+def compile_library(src: str, out: str, extra=()) -> None:
+    """gcc build of an oracle source: IEEE FP64, no contraction, OpenMP;
+    extra flags are appended (the sanitizer test adds ASan/UBSan)."""
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-o", out, src, "-lm"]
+           "-fno-fast-math", *extra, "-o", out, src, "-lm"]
     subprocess.run(cmd, check=True)
 
 

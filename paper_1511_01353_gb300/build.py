@@ -37,13 +37,21 @@ def _stale() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    return compile_library(LIB, BUILD, verbose=verbose)
+
+
+def compile_library(lib: str, objdir: str, host_flags=(), verbose: bool = False) -> str:
+    """Compile every csrc/*.cu in parallel into objdir and link them into lib.
+    host_flags go to the host compiler of each object and of the link (the
+    sanitizer test builds an ASan/UBSan variant this way)."""
+    xhost = [a for f in host_flags for a in ("-Xcompiler", f)]
+    os.makedirs(objdir, exist_ok=True)
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *xhost, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -57,11 +65,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join("%s\n%s" % (" ".join(c), o) for c, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", *xhost]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

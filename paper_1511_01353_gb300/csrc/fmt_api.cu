@@ -1086,19 +1086,20 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
       H->n_levels > FMT_MAX_DEPTH + 1 || H->n_nodes < 1 || H->n_problems < 1)
     return set_err(nullptr, FMT_EINVAL, "inconsistent blob header");
   const int64_t K = H->n_nodes, nm = H->nmono, P = H->n_problems;
+  // bound the counts by the bytes present before any product or sum of them,
+  // so that a corrupt header cannot wrap the size check below
+  const size_t body = len - sizeof(fmt_export_header);
+  if ((uint64_t)K > body / blob_node_bytes(1, nm) || (uint64_t)P > body / blob_problem_bytes(1))
+    return set_err(nullptr, FMT_EINVAL, "blob truncated");
   int64_t sumk = 0;
   for (int d = 0; d < H->n_levels; ++d) {
     if (H->level_nodes[d] < 1) return set_err(nullptr, FMT_EINVAL, "empty level %d in blob", d);
+    if (H->level_nodes[d] > K) return set_err(nullptr, FMT_EINVAL, "level %d larger than the blob", d);
     sumk += H->level_nodes[d];
   }
   if (sumk != K) return set_err(nullptr, FMT_EINVAL, "level sizes do not add up");
   const size_t need = sizeof(fmt_export_header) + blob_node_bytes(K, nm) + blob_problem_bytes(P);
   if (len < need) return set_err(nullptr, FMT_EINVAL, "blob truncated");
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
-  TRY(device_init(dev));
-  cudaStream_t s = (cudaStream_t)stream;
   const char* p = (const char*)host_buf + sizeof(fmt_export_header);
   const uint64_t* prefix = (const uint64_t*)p;
   const int64_t* start = (const int64_t*)(prefix + K);
@@ -1127,6 +1128,21 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
   }
   for (int64_t i = 0; i < K; ++i)
     if (nprob[i] < 0 || nprob[i] >= P) return set_err(nullptr, FMT_EINVAL, "node problem out of range");
+  {
+    int64_t o = 0;  // first node of level d
+    for (int d = 0; d < H->n_levels; ++d) {
+      for (int64_t i = 0; i < H->level_nodes[d]; ++i)
+        if (depth[o + i] != d || (i > 0 && prefix[o + i] <= prefix[o + i - 1]))
+          return set_err(nullptr, FMT_EINVAL, "blob level %d is not sorted by node key", d);
+      o += H->level_nodes[d];
+    }
+  }
+  // the blob is consistent: only now touch the device
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
+  TRY(device_init(dev));
+  cudaStream_t s = (cudaStream_t)stream;
 
   fmt_tree* t = new (std::nothrow) fmt_tree();
   if (!t) return set_err(nullptr, FMT_ENOMEM, "host allocation failed");
@@ -1183,11 +1199,6 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
   int64_t off = 0;
   for (int d = 0; d < H->n_levels; ++d) {
     const int64_t k = H->level_nodes[d];
-    for (int64_t i = 1; i < k; ++i)
-      if (prefix[off + i] <= prefix[off + i - 1] || depth[off + i] != d) {
-        destroy(t);
-        return set_err(nullptr, FMT_EINVAL, "blob level %d is not sorted by node key", d);
-      }
     if ((st = alloc_level(t, d, k, 1, s))) {
       destroy(t);
       return st;

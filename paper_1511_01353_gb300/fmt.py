@@ -109,17 +109,22 @@ _lib = None
 
 
 def load(build: bool = True):
-    """Load libfmt.so (building it with nvcc first when it is stale)."""
+    """Load libfmt.so (building it with nvcc first when it is stale).
+
+    FMT_LIBRARY names another build of the same sources to load instead
+    (the sanitizer test loads an ASan/UBSan build this way, in a child
+    process); it is loaded as is, never built here."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        if build:
+        path = os.environ.get("FMT_LIBRARY") or LIB_PATH
+        if build and path == LIB_PATH:
             from . import build as _b
             _b.build()
-        if not os.path.exists(LIB_PATH):
-            raise ImportError("libfmt.so not found at %s; run paper_1511_01353_gb300/build.py" % LIB_PATH)
-        L = ctypes.CDLL(LIB_PATH)
+        if not os.path.exists(path):
+            raise ImportError("libfmt.so not found at %s; run paper_1511_01353_gb300/build.py" % path)
+        L = ctypes.CDLL(path)
         P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         L.fmt_nmono.argtypes = [i32]
         L.fmt_nmono.restype = i32

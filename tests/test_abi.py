@@ -7,6 +7,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 from paper_1511_01353_gb300 import fmt as F
@@ -228,3 +229,92 @@ def test_server_submit_checks_host_array_sizes():
         srv.submit(p, a, a, a, a, np.zeros(4), np.zeros(4), np.zeros(3))
     with pytest.raises(F.FmtError, match="all of xq"):
         srv.submit(p, a, a, a, a, None, np.zeros(4), np.zeros(4))
+
+
+def _oracle_blob():
+    # an FMT2 blob of a small three-level oracle tree, as a caller would
+    # serialise a tree built elsewhere (no device involved)
+    import numpy as np
+    from oracle import oracle as O
+    from tests import treecmp as TC
+    rng = np.random.default_rng(41)
+    x, y, z = rng.uniform(0, 1, (3, 1500))
+    T = O.fit(x, y, z, np.sin(3 * x) + y * z, 2, 2, 10, 1e-4)
+    pref = (TC.spread3(T.ixyz[:, 0]) | (TC.spread3(T.ixyz[:, 1]) << np.uint64(1)) |
+            (TC.spread3(T.ixyz[:, 2]) << np.uint64(2)))
+    order = np.lexsort((pref, T.depth))
+    hdr = dict(degree=T.degree, nmono=T.nmono, max_depth=T.max_depth, min_pts=T.min_pts, tol_rel=T.tol_rel,
+               tau=T.tau, maxabs_f=T.maxabs, lo=T.lo, side=T.side, n_points=x.shape[0])
+    blob = F.build_export(hdr, pref[order], T.depth[order], T.flags[order], T.deg_used[order], T.child_E[order],
+                          T.child_n[order], T.coef[order])
+    return T, blob
+
+
+def test_import_validates_the_blob_before_touching_the_device():
+    # fmt_tree_import parses a caller's host blob: every size, count and
+    # index in it is checked against the bytes present before the first CUDA
+    # call, so truncated or corrupt blobs (including counts chosen to wrap the
+    # size arithmetic) are rejected with FMT_EINVAL and never read past the
+    # buffer.  A valid blob passes every host check: on a machine without a
+    # GPU it then fails at the device (FMT_ECUDA).
+    import struct
+    torch = pytest.importorskip("torch")
+    T, blob = _oracle_blob()
+    K, nm = T.n_nodes, T.nmono
+    assert K > 9 and int(T.depth.max()) == 2
+    lib = F.load()
+
+    def imp(b):
+        h = ctypes.c_void_p()
+        buf = (ctypes.c_char * max(len(b), 1)).from_buffer_copy(b if b else b"\0")
+        st = lib.fmt_tree_import(buf, len(b), None, ctypes.byref(h))
+        if h.value:
+            lib.fmt_tree_free(h)
+        return st
+
+    assert imp(blob) == (F.FMT_OK if torch.cuda.is_available() else F.FMT_ECUDA)
+    for n in range(len(blob)):
+        assert imp(blob[:n]) == F.FMT_EINVAL, n
+
+    hs = ctypes.sizeof(F.fmt_export_header)
+
+    def header(**kw):
+        h = F.fmt_export_header.from_buffer_copy(blob)
+        for k, v in kw.items():
+            if k == "level_nodes":
+                for i in range(len(h.level_nodes)):
+                    h.level_nodes[i] = v[i] if i < len(v) else 0
+            else:
+                setattr(h, k, v)
+        return bytes(h) + blob[hs:]
+
+    lv = [int(c) for c in np.bincount(T.depth)]
+    bad_headers = [dict(magic=0), dict(version=1), dict(degree=15), dict(nmono=nm + 1), dict(n_levels=0),
+                   dict(n_levels=23), dict(n_nodes=0), dict(n_problems=0), dict(n_problems=2 ** 31 - 1),
+                   dict(n_levels=2, n_nodes=2 ** 62, level_nodes=[1, 2 ** 62 - 1]),  # wraps K * bytes per node
+                   dict(n_levels=2, n_nodes=2 ** 57, level_nodes=[1, 2 ** 57 - 1]),
+                   dict(n_nodes=K + 1, level_nodes=lv[:-1] + [lv[-1] + 1]),
+                   dict(level_nodes=[0] + lv[1:]),
+                   dict(level_nodes=[lv[0] + 5, lv[1] - 5] + lv[2:]),
+                   dict(n_levels=2, level_nodes=[lv[0], lv[1] + lv[2]])]
+    for kw in bad_headers:
+        assert imp(header(**kw)) == F.FMT_EINVAL, kw
+
+    def patch(off, fmt, value):
+        b = bytearray(blob)
+        struct.pack_into(fmt, b, hs + off, value)
+        return bytes(b)
+
+    prefix0 = struct.unpack_from("<Q", blob, hs + 8 * lv[0])[0]  # first node of level 1
+    depth_at, nprob_at = 24 * K, 24 * K + 16 * K
+    prob_at = K * (176 + 8 * nm)
+    bad_bodies = [patch(8 * (lv[0] + 1), "<Q", prefix0),        # level 1 not strictly increasing
+                  patch(depth_at + 4 * 1, "<i", 0),             # a level-1 node labelled depth 0
+                  patch(nprob_at, "<i", 1),                     # node of problem 1 in a 1-problem blob
+                  patch(nprob_at + 4 * (K - 1), "<i", -1),
+                  patch(prob_at, "<i", T.degree + 1),           # problem degree above the blob's
+                  patch(prob_at + 8 + 8 + 8 + 24, "<d", -1.0),  # problem side
+                  patch(prob_at + 8 + 8 + 8 + 24, "<d", float("nan")),
+                  patch(prob_at + 8 + 8 + 8, "<d", float("inf"))]   # problem lo
+    for i, b in enumerate(bad_bodies):
+        assert imp(b) == F.FMT_EINVAL, i
