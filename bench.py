@@ -251,8 +251,23 @@ def cpu_baseline_batch(args, w):
         pts += b - a
         k += 1
     dt = time.perf_counter() - t0
-    return {"value": pts / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": "first %d problems of the batch (%d points), fitted one after another, %.1f s" % (k, pts, dt)}
+    out = {"value": pts / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+           "sample": "first %d problems of the batch (%d points), fitted one after another, %.1f s" % (k, pts, dt)}
+    if args.cpu_points_serial > 0:
+        # the same problems on one thread (depth-first as printed), up to the serial sample size
+        t0 = time.perf_counter()
+        ps, j = 0, 0
+        while j < k and ps < args.cpu_points_serial:
+            a, b = int(w.offsets[j]), int(w.offsets[j + 1])
+            O.fit(w.x[a:b], w.y[a:b], w.z[a:b], w.f[a:b], int(w.degrees[j]), w.max_depth, w.min_pts, w.tol_rel,
+                  mode="dfs")
+            ps += b - a
+            j += 1
+        ds = time.perf_counter() - t0
+        out["single_core"] = {"value": ps / ds, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": "first %d problems (%d points), depth-first on one thread, %.1f s"
+                                        % (j, ps, ds)}
+    return out
 
 
 def cpu_baseline(args):
