@@ -218,7 +218,6 @@ def test_binding_checks_buffer_sizes_before_any_call():
 
 
 def test_server_submit_checks_host_array_sizes():
-    import numpy as np
     srv = object.__new__(F.Server)  # no engine: the checks come before the call
     srv.handle, srv._live = None, {}
     p = F.make_params(2, 3, 10, 1e-4)
@@ -234,7 +233,6 @@ def test_server_submit_checks_host_array_sizes():
 def _oracle_blob():
     # an FMT2 blob of a small three-level oracle tree, as a caller would
     # serialise a tree built elsewhere (no device involved)
-    import numpy as np
     from oracle import oracle as O
     from tests import treecmp as TC
     rng = np.random.default_rng(41)

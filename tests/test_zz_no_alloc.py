@@ -12,8 +12,6 @@ parity tests (1e-10 * max|f|).
 
 This file is named to be collected last.
 """
-import ctypes
-
 import numpy as np
 import pytest
 
