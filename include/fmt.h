@@ -307,7 +307,13 @@ fmt_status fmt_tree_export(fmt_tree* tree, void* host_buf, size_t* len);
 
 /* Rebuild an evaluation-only tree from a blob (has_points may be 0; every
  * level in the blob is taken as fitted).  fit_level/refine on it return
- * FMT_EINVAL.  Synchronises. */
+ * FMT_EINVAL.  Synchronises.  host_buf (len bytes) is the caller's and is
+ * only read.  Before any device work the whole blob is checked on the host:
+ * header fields, every count against the bytes present (so no count can
+ * overflow the size check), each problem's degree and box, each node's
+ * problem index, and each level's strictly increasing node keys.  A
+ * truncated or inconsistent blob returns FMT_EINVAL and allocates nothing;
+ * *out is NULL on every error. */
 fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_tree** out);
 
 /*
