@@ -2,7 +2,8 @@
  * fmt_oracle.c -- plain, slow FP64 CPU oracle for the free-mesh transform (FMT).
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
- * CPU-baseline leg of bench.py may build, load or call this file.  It shares
+ * CPU legs of bench.py (cpu_baseline, --impl reference) may build, load or
+ * call this file (__graft_entry__.build() compiles it).  It shares
  * no code, header, table or helper with the CUDA library; the product path
  * never routes through it.
  *

@@ -1,7 +1,8 @@
 """ctypes binding of the plain FP64 C oracle (oracle/fmt_oracle.c).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()``
-and the CPU-baseline legs of bench.py, never by the product path.
+and the CPU legs of bench.py (cpu_baseline, --impl reference), never by the
+product path.
 
 The oracle follows Alg. 1 (recursive octree decomposition of the residual)
 and Alg. 2 (geometric-moment Vandermonde, Householder QR, F = R^-1 Q^T f,
