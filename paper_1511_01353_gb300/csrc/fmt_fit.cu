@@ -9,15 +9,20 @@
 // rate, and a masked lane still costs a full slot), so the kernels keep every
 // FP64 instruction full-warp and avoid cross-lane reductions on the long
 // loops:
-//  * k_tile_qr: one CTA per work item (a chunk of <= C rows of one node).  The
-//    item's triangle R (m x m, m = nmono+1) lives in global memory (L2); row
-//    blocks of 4*RPT rows of [Lambda | r] are generated into shared memory and
-//    absorbed by a structured Householder step per column j (the reflector
-//    touches R's row j and the block's rows).  Threads form quads: a quad owns
-//    a column k > j, each lane a quarter of the block's rows, so a column's
-//    dot product needs only two shuffle-adds.
-//  * k_combine: pairwise reduction of the triangles of a node (TSQR), same
-//    absorb step with the second triangle as the row block.
+//  * k_tile_qr: persistent CTAs take work items (chunks of <= C rows of one
+//    node) from a queue ordered largest first; a level with several degrees
+//    runs one launch per degree, on side streams.  An item's triangle R
+//    (m x m, m = nmono+1) lives in global memory (L2); row blocks of 4*RPT
+//    rows of [Lambda | r] are generated into shared memory and absorbed by a
+//    structured Householder step per column j (the reflector touches R's row
+//    j and the block's rows).  Threads form quads: a quad owns a column
+//    k > j, each lane a quarter of the block's rows, so a column's dot
+//    product needs only two shuffle-adds.
+//  * k_merge / k_combine: pairwise reduction of the triangles of a node
+//    (TSQR).  k_merge holds the second triangle packed in shared memory
+//    (m <= 166); k_combine absorbs it in row blocks, for any m.  The launch
+//    configuration table (rows per block, warps, chunk floor, merge kernel)
+//    is per degree, built in or autotuned.
 //  * k_backsolve: one warp per node, column-oriented back substitution.
 //  * k_residual: r <- r - Lambda F in Horner form (nmono FMAs per point).
 //  * k_child_bounds / k_child_sums: octant ranges by binary search on the
