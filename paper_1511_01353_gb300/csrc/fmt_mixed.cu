@@ -28,12 +28,19 @@
 //     in the scaling, Legendre coefficients are dyadic rationals), so the
 //     residual update, the evaluation and the export are those of the FP64
 //     path.
-// Nodes whose Cholesky pivot is below kPivotFloor of its diagonal entry, or
-// whose last sweep (extrapolated by the contraction of the last two) still
-// moves the fit at the data by more than kConvergedRel of its norm, or the
-// polynomial anywhere in the node box by more than kBoxChangeRel of the
-// problem's max |f|, lose FMT_FLAG_MIXED and are refitted by the FP64 kernels
-// of fmt_fit.cu.
+// Acceptance, after every sweep: a node is settled (and skipped by the later
+// sweeps) once its change at the data is below kConvergedRel of the fit, its
+// change anywhere in the node box below kBoxChangeRel of the problem's
+// max |f|, and the bias of the quantised basis (a +-2^-31 perturbation solved
+// through R^T R) within the same box bound.  A node that fails, or whose
+// Cholesky pivot is below kPivotFloor of its diagonal entry, loses
+// FMT_FLAG_MIXED.  Nodes of degree 1..10 that did not fail on the pivot (and
+// are not a clamped root) then go to the FP64 normal-equations tier (k_dgram,
+// k_dfactor, k_dproj, k_dupdate: FP64 Gram, Cholesky and corrected
+// semi-normal sweeps, kept only if a rounding-size perturbation moves the
+// polynomial by less than the box bound; FMT_FLAG_MIXED_FP64).  Degrees above
+// 9 skip the tensor cores, degrees above 10 both tiers.  What neither tier
+// keeps is refitted by the Householder kernels of fmt_fit.cu.
 
 #include <cuda_bf16.h>
 #include <float.h>
