@@ -1,6 +1,13 @@
 // fmt_api.cu -- the C ABI of libfmt (declared in include/fmt.h): argument
-// checks, the tree's memory, the call-order state machine, and the sequence
-// of kernels behind oct_build / fit_level / refine / evaluate.
+// checks, the tree's memory (a stream-ordered pool per device), the
+// call-order state machine, and the sequence of kernels behind oct_build /
+// oct_build_batch / fit_level / refine / evaluate (FP64 path; the mixed
+// path's tensor-core tier, its FP64 normal-equations tier and the Householder
+// refits in one level step).  Also here: the CUDA-graph form of fit_level
+// (one executable graph per level step, updated in place), the versioned
+// export / import of a tree (the import checks the whole host blob before
+// any device work), kernel profiling by CUDA events, and the failure-path
+// diagnostics (allocation-failure injection, the bounded-wait probe).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
