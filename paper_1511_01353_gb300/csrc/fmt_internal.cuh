@@ -1,6 +1,8 @@
 // fmt_internal.cuh -- internal types and device helpers of libfmt (not part of
-// the C ABI).  Every kernel of the FP64 path is declared here through a host
-// launcher; fmt_api.cu sequences them.
+// the C ABI).  Every kernel is declared here through a host launcher (build,
+// FP64 fit, mixed path and its FP64 tier, refine and evaluation, the DFMA
+// and bounded-wait probes), with the per-degree QR launch-configuration
+// table; fmt_api.cu sequences them.
 #pragma once
 
 #include <cuda_runtime.h>
