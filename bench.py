@@ -73,6 +73,10 @@ def parse_args():
                     help="sweep: largest N = 8^E (E <= 9; degree 12 runs up to 8^7)")
     ap.add_argument("--sweep-min-exp", type=int, default=4, help="sweep: smallest N = 8^E (E >= 4)")
     ap.add_argument("--sweep-tols", default="1e-6,1e-8,1e-10,1e-12", help="sweep: comma-separated tol_rel values")
+    ap.add_argument("--blocks", default="c3,batch,serve",
+                    help="scale workload: extra blocks of the line (comma-separated: c3 = the precision form of "
+                         "the small workload against the oracle, batch = the 4096-problem form in FP64 and mixed, "
+                         "serve = the Poisson request stream); 'none' for none")
     return ap.parse_args()
 
 
@@ -383,10 +387,10 @@ def run_experiments(args, rank, world):
     return 0
 
 
-def run_serve(args, rank, world):
-    """Serving: a Poisson stream of fit+evaluate requests through the
-    library's serving engine (continuous batching over worker streams);
-    latency = completion minus submission on the engine's clock, with the
+def serve_measure(args, n_requests, rate, slots, seed_offset=0):
+    """One Poisson stream of fit+evaluate requests through the library's
+    serving engine (continuous batching over worker streams).  Latency =
+    completion minus submission on the engine's clock, with the
     host->device copy of the request's arrays and the device->host copy of
     its results inside it."""
     import threading
@@ -396,15 +400,13 @@ def run_serve(args, rank, world):
     from paper_1511_01353_gb300 import fmt as F
     from paper_1511_01353_gb300 import workloads as W
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    F.load()
-    reqs = W.serve_stream(n_requests=args.requests, rate=args.rate, seed=W.SEED_BASE + 4 + 1000 * rank)
+    reqs = W.serve_stream(n_requests=n_requests, rate=rate, seed=W.SEED_BASE + 4 + seed_offset)
     prec = {"fp64": F.FMT_FP64, "mixed": F.FMT_MIXED}
 
     def params(r):
         return F.make_params(r.degree, 8, 0, 1e-6, precision=prec[r.precision], sweeps=args.sweeps)
 
-    sv = F.Server(slots=args.slots, budget_bytes=150e9, max_batch_points=4_000_000)
+    sv = F.Server(slots=slots, budget_bytes=150e9, max_batch_points=4_000_000)
     for r in reqs[:max(args.warmup, 1)]:  # warm-up: contexts, pools, kernels
         sv.wait(sv.submit(params(r), r.x[:2000], r.y[:2000], r.z[:2000], r.f[:2000], r.xq[:100], r.yq[:100],
                           r.zq[:100]))
@@ -438,13 +440,10 @@ def run_serve(args, rank, world):
             by[name] = {"requests": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50) * 1e3),
                         "p99_ms": float(np.percentile(lat[sel], 99) * 1e3), "points": int(pts[sel].sum())}
     offered = pts.sum() / max(reqs[-1].arrival, 1e-9)
-    line = {"metric": "fitted pts/s and p50/p99 request latency (serving)", "value": float(pts.sum() / span),
-            "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": max(args.warmup, 1),
-            "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 and f64+bf16 per request", "data": "synthetic",
+    return {"value": float(pts.sum() / span), "unit": UNIT, "span_ms": span * 1e3,
             "config": {"workload": "serve: %d requests, Poisson %.0f/s, points log-uniform [1e3, 2e6], targets "
-                                   "log-uniform [1, 1e6], p 4..10, FP64 or mixed per request" % (len(reqs), args.rate),
-                       "slots": args.slots, "budget_bytes": 150e9, "max_batch_points": 4_000_000,
+                                   "log-uniform [1, 1e6], p 4..10, FP64 or mixed per request" % (len(reqs), rate),
+                       "slots": slots, "budget_bytes": 150e9, "max_batch_points": 4_000_000,
                        "max_depth": 8, "tol_rel": 1e-6},
             "evals_per_s": float(tg.sum() / span), "all_ok": ok,
             "latency": by, "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
@@ -453,11 +452,254 @@ def run_serve(args, rank, world):
             "batches": len(set(i["batch_id"] for i in infos)),
             "mean_batch_requests": float(np.mean([i["batch_requests"] for i in infos])),
             "clocks": clocks,
-            "e2e": {"value": float(pts.sum() / span), "unit": UNIT,
-                    "h2d_bytes_per_step": int(32 * pts.sum() + 24 * tg.sum()), "d2h_bytes_per_step": int(8 * tg.sum())}}
+            "h2d_bytes": int(32 * pts.sum() + 24 * tg.sum()), "d2h_bytes": int(8 * tg.sum())}
+
+
+def run_serve(args, rank, world):
+    """Serving: the Poisson request stream as the headline line."""
+    import torch
+    from paper_1511_01353_gb300 import fmt as F
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    F.load()
+    s = serve_measure(args, args.requests, args.rate, args.slots, 1000 * rank)
+    line = {"metric": "fitted pts/s and p50/p99 request latency (serving)", "value": s["value"],
+            "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": max(args.warmup, 1),
+            "ms_per_step": s["span_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 and f64+bf16 per request", "data": "synthetic"}
+    line.update({k: v for k, v in s.items() if k not in ("value", "unit", "span_ms", "h2d_bytes", "d2h_bytes")})
+    line["e2e"] = {"value": s["value"], "unit": UNIT, "h2d_bytes_per_step": s["h2d_bytes"],
+                   "d2h_bytes_per_step": s["d2h_bytes"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def block_c3(args, stream, flush):
+    """The precision form of the small workload: its 4096 points and 1e4
+    targets at p = 8, depth 7 (min 64 points, tol 1e-4), fitted and
+    evaluated on the mixed path and on the FP64 path, each compared with the
+    FP64 oracle at the targets and at the data points (error relative to
+    max|f|; target for the mixed path 1e-6)."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_1511_01353_gb300 import fmt as F
+    from paper_1511_01353_gb300 import workloads as W
+
+    w = W.small()
+    p, D, mp, tol = 8, 7, w.min_pts, w.tol_rel
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, y, z, f = dev(w.x), dev(w.y), dev(w.z), dev(w.f)
+    xq, yq, zq = dev(w.xq), dev(w.yq), dev(w.zq)
+    out = torch.empty(w.m, dtype=torch.float64, device="cuda")
+    T = O.fit(w.x, w.y, w.z, w.f, p, D, mp, tol)
+    ref_q, _ = T.evaluate(w.xq, w.yq, w.zq)
+    ref_d, _ = T.evaluate(w.x, w.y, w.z)
+    scale = max(T.maxabs, 1e-300)
+    res = {"workload": "small_n4096_p8_d7_min64_tol1e-4", "points": w.n, "targets": w.m, "degree": p,
+           "max_depth": D, "oracle_nodes": int(T.n_nodes)}
+    steps, warm = max(args.steps, 5), max(args.warmup, 3)
+    for name, prec in (("mixed", F.FMT_MIXED), ("fp64", F.FMT_FP64)):
+        prm = F.make_params(p, D, mp, tol, precision=prec, sweeps=args.sweeps)
+        fit_ms, ev_ms = [], []
+        for i in range(warm + steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record(stream)
+                tr = F.fit(prm, x, y, z, f, stream)
+                b.record(stream)
+                F.evaluate(tr, xq, yq, zq, out, stream=stream)
+                c.record(stream)
+            stream.synchronize()
+            if i >= warm:
+                fit_ms.append(a.elapsed_time(b))
+                ev_ms.append(b.elapsed_time(c))
+            if i < warm + steps - 1:
+                tr.close()
+        gq = out.cpu().numpy()
+        outd = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        F.evaluate(tr, x, y, z, outd, stream=stream)
+        stream.synchronize()
+        gd = outd.cpu().numpy()
+        st = F.fmt_tree_stats(tr)
+        nodes = int(sum(st.nodes[d] for d in range(st.n_levels)))
+        tr.close()
+        fm = float(np.mean(fit_ms))
+        res[name] = {"value": w.n / (fm * 1e-3), "unit": UNIT, "fit_ms": fm, "eval_ms": float(np.mean(ev_ms)),
+                     "evals_per_s": w.m / (float(np.mean(ev_ms)) * 1e-3),
+                     "max_err_vs_oracle_over_max_f_targets": float(np.max(np.abs(gq - ref_q))) / scale,
+                     "max_err_vs_oracle_over_max_f_data": float(np.max(np.abs(gd - ref_d))) / scale,
+                     "nodes": nodes, "steps": steps, "warmup": warm}
+    res["mixed"]["target_err"] = 1e-6
+    res["fp64"]["target_err"] = 1e-10
+    res["note"] = ("4096 points fit in a few ms: launch- and latency-bound at this size (no roofline claimed); "
+                   "errors against the FP64 oracle run in the same job")
+    return res
+
+
+def block_batch(args, stream, flush):
+    """The batched form: 4096 independent problems (degrees 4..10, log-uniform
+    sizes, 4.76e7 points) as one forest, one timed step each on the FP64 and
+    the mixed path after a warm-up on the first 256 problems; mixed against
+    FP64 at every target, and both against the FP64 oracle on a sample of
+    problems."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_1511_01353_gb300 import fmt as F
+    from paper_1511_01353_gb300 import workloads as W
+
+    t_gen = time.perf_counter()
+    w = W.batch(n_problems=args.problems, seed=W.SEED_BASE + 3)
+    t_gen = time.perf_counter() - t_gen
+    N, M, P = int(w.offsets[-1]), int(w.xq.shape[0]), w.n_problems
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, y, z, f = dev(w.x), dev(w.y), dev(w.z), dev(w.f)
+    xq, yq, zq, tp = dev(w.xq), dev(w.yq), dev(w.zq), dev(w.tprob)
+    out = torch.empty(M, dtype=torch.float64, device="cuda")
+    preds, res = {}, {}
+    for name, prec in (("fp64", F.FMT_FP64), ("mixed", F.FMT_MIXED)):
+        prm = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel, precision=prec, sweeps=args.sweeps)
+        # warm-up on the first 256 problems (kernels, pools, tables)
+        k = min(256, P)
+        nk, mk = int(w.offsets[k]), int(w.toff[k])
+        tw = F.fit_all(F.oct_build_batch(prm, w.offsets[:k + 1], x[:nk], y[:nk], z[:nk], f[:nk],
+                                         degrees=w.degrees[:k], boxes=w.boxes[:k], stream=stream), stream)
+        F.evaluate_batch(tw, tp[:mk], xq[:mk], yq[:mk], zq[:mk], out[:mk], stream=stream)
+        stream.synchronize()
+        tw.close()
+        F.fmt_profile_enable(True)
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            tr = F.fit_all(F.oct_build_batch(prm, w.offsets, x, y, z, f, degrees=w.degrees, boxes=w.boxes,
+                                             stream=stream), stream)
+            b.record(stream)
+            F.evaluate_batch(tr, tp, xq, yq, zq, out, stream=stream)
+            c.record(stream)
+        stream.synchronize()
+        prof = F.fmt_profile_read()
+        F.fmt_profile_enable(False)
+        preds[name] = out.cpu().numpy()
+        st = F.fmt_tree_stats(tr)
+        fl = F.parse_export(F.fmt_tree_export(tr)).flags if name == "mixed" else None
+        tr.close()
+        fit_s, ev_s = a.elapsed_time(b) * 1e-3, b.elapsed_time(c) * 1e-3
+        qr = prof.get("tile_qr", {})
+        res[name] = {"value": N / fit_s, "unit": UNIT, "fit_ms": fit_s * 1e3, "eval_ms": ev_s * 1e3,
+                     "evals_per_s": M / ev_s,
+                     "nodes": int(sum(st.nodes[d] for d in range(st.n_levels))),
+                     "kernels_ms": {kk: round(v["ms"], 2) for kk, v in prof.items()
+                                    if v["launches"] and kk != "graph_launch"},
+                     "gpu_launches": int(sum(v["launches"] for kk, v in prof.items() if kk != "graph_launch"))}
+        if qr.get("ms") and qr.get("flops"):
+            ach = qr["flops"] / (qr["ms"] * 1e-3) / 1e12
+            res[name]["tile_qr_roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+                                             "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS}
+        if fl is not None:
+            tc = (fl & F.FMT_FLAG_MIXED) != 0
+            t2 = (fl & F.FMT_FLAG_MIXED_FP64) != 0
+            res[name]["nodes_by_tier"] = {"tensor": int(np.sum(tc & ~t2)), "fp64_normal_eq": int(np.sum(t2)),
+                                          "householder": int(np.sum(~tc))}
+    # per-problem error of the mixed path against the FP64 path, relative to the problem's max|f|
+    rel = np.empty(P)
+    for i in range(P):
+        a_, b_ = int(w.toff[i]), int(w.toff[i + 1])
+        fi = float(np.max(np.abs(w.f[int(w.offsets[i]):int(w.offsets[i + 1])])))
+        rel[i] = float(np.max(np.abs(preds["mixed"][a_:b_] - preds["fp64"][a_:b_]))) / max(fi, 1e-300)
+    # both paths against the oracle on a sample of problems, one per degree, the smallest of each
+    sample, ora = [], {"fp64": 0.0, "mixed": 0.0}
+    t_or = time.perf_counter()
+    for d in sorted(set(int(v) for v in w.degrees)):
+        idx = [i for i in range(P) if int(w.degrees[i]) == d]
+        i = min(idx, key=lambda j: int(w.offsets[j + 1] - w.offsets[j]))
+        a_, b_ = int(w.offsets[i]), int(w.offsets[i + 1])
+        T = O.fit(w.x[a_:b_], w.y[a_:b_], w.z[a_:b_], w.f[a_:b_], d, w.max_depth, w.min_pts, w.tol_rel,
+                  mode="omp")
+        qa, qb = int(w.toff[i]), int(w.toff[i + 1])
+        ref, _ = T.evaluate(w.xq[qa:qb], w.yq[qa:qb], w.zq[qa:qb])
+        for name in ora:
+            ora[name] = max(ora[name], float(np.max(np.abs(preds[name][qa:qb] - ref))) / max(T.maxabs, 1e-300))
+        sample.append(i)
+    t_or = time.perf_counter() - t_or
+    return {"workload": w.name, "problems": P, "points": N, "targets": M,
+            "degree": "%d..%d per problem" % (w.degrees.min(), w.degrees.max()),
+            "max_depth": w.max_depth, "min_pts": w.min_pts, "tol_rel": w.tol_rel,
+            "fp64": res["fp64"], "mixed": res["mixed"],
+            "mixed_over_fp64_fitted_pts_per_s": res["mixed"]["value"] / res["fp64"]["value"],
+            "mixed_vs_fp64_max_err_over_max_f": float(np.max(rel)),
+            "mixed_vs_fp64_median_err_over_max_f": float(np.median(rel)),
+            "vs_oracle_max_err_over_max_f": ora,
+            "oracle_sample": "problems %s (the smallest of each degree), oracle fit %.1f s" % (sample, t_or),
+            "l2": "flushed before each timed step (256 MB write)",
+            "warmup": "first 256 problems, each path", "steps": 1, "generation_s": t_gen,
+            "target_err": {"mixed": 1e-6, "fp64": 1e-10}}
+
+
+def block_serve(args):
+    """The serving configuration as a block of the default line."""
+    s = serve_measure(args, args.requests, args.rate, args.slots)
+    s.pop("span_ms", None)
+    return s
+
+
+def mixed_rooflines(prof, degree, steps, probe_tflops, peaks):
+    """Per-kernel roofline of the mixed path's kernels from their launch
+    units (rows or nodes) and the algorithmic work per unit at `degree`."""
+    L = (degree + 1) * (degree + 2) * (degree + 3) // 6
+    m = L + 1
+    Lp = (m + 15) // 16 * 16
+    band1 = max(Lp - 128, 0)
+    out = {}
+
+    def entry(name, bound, work, unit, peak, peak_source, what):
+        v = prof.get(name, {})
+        if not v.get("ms"):
+            return
+        ach = work(v) / (v["ms"] * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        out[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                     "peak_source": peak_source, "ms_per_step": v["ms"] / steps, "work": what}
+
+    fp64_src = "GB300 nominal FP64 (non-tensor) 1.25 TFLOP/s; live DFMA probe %.3f" % probe_tflops
+    # tensor Gram: six digit-pair products of the 128-lane bands, M = 128, K = 64 per 64-row atom
+    gram_flops_row = 6 * 2 * 128 * (Lp + band1)
+    entry("mixed_gram", "tensor", lambda v: v["units"] * gram_flops_row, "TFLOP/s", peaks["bf16_tflops"],
+          peaks["source"] + " (bf16 dense, burst)",
+          "issued MMA flops: 6 digit-pair products x 2 x 128 x (%d + %d) per row" % (Lp, band1))
+    # projection: the cached digit tiles (4 x Lp rows x 128 B per 64-row atom) and s (8 B) per row
+    proj_bytes_row = 4 * Lp * 128 / 64 + 8
+    entry("mixed_proj", "hbm", lambda v: v["units"] * proj_bytes_row, "GB/s", peaks["hbm_gbs"],
+          peaks["source"] + " (copy)", "%.0f B per row (digit-tile cache + s)" % proj_bytes_row)
+    # sweep residual: FP64 Horner (flops recorded by the library)
+    entry("mixed_sresid", "alu", lambda v: v["flops"], "TFLOP/s", FP64_NOMINAL_TFLOPS, fp64_src,
+          "Horner flops of s = r - Lambda F per row")
+    # factor: Cholesky of the m x m Gram (m^3 / 3 FMAs) + back substitution, per node
+    entry("mixed_factor", "alu", lambda v: v["units"] * (2.0 * m ** 3 / 3.0 + 2.0 * L * L), "TFLOP/s",
+          FP64_NOMINAL_TFLOPS, fp64_src, "2 m^3/3 + 2 L^2 flops per node (latency-bound: one node per CTA)")
+    # update: two triangular solves, |R F| and the bias solves per node and sweep
+    entry("mixed_update", "alu", lambda v: v["units"] * 6.0 * L * L, "TFLOP/s", FP64_NOMINAL_TFLOPS, fp64_src,
+          "6 L^2 flops per node and sweep (latency-bound: one node per CTA)")
+    entry("mixed_box", "hbm", lambda v: v["units"] * 32.0, "GB/s", peaks["hbm_gbs"], peaks["source"] + " (copy)",
+          "32 B per row (x, y, z, r)")
+    return out
+
+
+def load_peaks():
+    """The machine's measured peaks (generated MEASURED_PEAKS.json when
+    present, else the figures it recorded for the GB300s)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        hbm = float(d.get("hbm_gbs"))
+        bf = float(d.get("bf16_tflops"))
+        return {"hbm_gbs": hbm, "bf16_tflops": bf, "source": "MEASURED_PEAKS.json"}
+    except Exception:
+        return {"hbm_gbs": 6669.5, "bf16_tflops": 1982.8,
+                "source": "measured peaks of this pool's GB300s (MEASURED_PEAKS.json not present in this run)"}
 
 
 def main():
@@ -698,6 +940,8 @@ def main():
                  "tiers": fallback,
                  "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps}
                              for k, v in oprof.items() if v["launches"]},
+                 "rooflines": mixed_rooflines(oprof if oprec == "mixed" else prof, params.degree, args.steps,
+                                              probe_tflops, load_peaks()),
                  "note": "error vs the FP64 GPU path, which matches the FP64 oracle to 1e-10 max|f|; "
                          "target for the mixed path: 1e-6 max|f|"}
 
@@ -742,6 +986,17 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_batch(args, w) if is_batch else cpu_baseline(args)
+    # the other configurations as blocks of the same line (one GPU only; not the headline)
+    blocks = {}
+    wanted = [b for b in args.blocks.split(",") if b and b != "none"]
+    if rank == 0 and world == 1 and args.workload == "scale" and wanted:
+        if "c3" in wanted:
+            blocks["c3"] = block_c3(args, stream, flush)
+        if "batch" in wanted:
+            blocks["batch"] = block_batch(args, stream, flush)
+            torch.cuda.empty_cache()
+        if "serve" in wanted:
+            blocks["serve"] = block_serve(args)
 
     nodes = [int(stats.nodes[d]) for d in range(stats.n_levels)]
     points = [int(stats.points[d]) for d in range(stats.n_levels)]
@@ -791,6 +1046,7 @@ def main():
         "e2e": e2e, "cpu_baseline": cpu,
         "precision": args.precision, ("mixed" if args.precision == "fp64" else "fp64"): other,
     }
+    line.update(blocks)
     last.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

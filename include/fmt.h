@@ -359,7 +359,7 @@ fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream);
  * configuration of the QR of fit_level (Alg. 2 per node, chunks reduced
  * pairwise):
  *   rows          rows of [Lambda | r] absorbed per shared-memory block:
- *                 16, 32 or 64, and (rows + 2) * ld * 8 + 32 bytes must fit
+ *                 16, 32, 64 or 128, and (rows + 2) * ld * 8 + 32 bytes must fit
  *                 in 227 KB, ld = the padded row pitch of nmono(p) + 1 columns;
  *   warps         warps per tile-QR CTA: 4 or 8;
  *   chunk_factor  smallest row chunk (one work item of the persistent queue)
@@ -448,7 +448,10 @@ fmt_status fmt_wait_probe(int64_t limit_ns, void* stream);
  *   x,y,z    device, n doubles each (global coordinates), caller owned.
  *   r_in     device, n doubles: the values to fit, caller owned.
  *   lo, side host: the box, read during the call.
- *   coef     device, nmono(degree) doubles, written: F in Alg. 2 order.
+ *   coef     device, nmono(degree) doubles, written: the coefficients of the
+ *            monomials u^l v^m w^n / (l! m! n!), l outermost, then m, then n
+ *            innermost (the coef layout of fmt_tree_export); with a lowered
+ *            degree the coefficients of the dropped monomials are zero.
  *   r_out    device, n doubles, written: r_in - Lambda F (may equal r_in).
  *   flags    device int32 or NULL, written: FMT_FLAG_RANK | FMT_FLAG_DEG_CLAMPED.
  * One CTA does the whole fit, so it suits small point sets (it is slow for
@@ -457,8 +460,10 @@ fmt_status fmt_wait_probe(int64_t limit_ns, void* stream);
  * use): calls that can overlap on the GPU (different streams, or threads
  * without ordering) race and corrupt each other -- order them on one stream.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  Asynchronous.
+ * (cudaGetSymbolAddress) and caches it with the id of the device's context;
+ * make that first call before any stream capture.  A call that finds a
+ * different context (after cudaDeviceReset the module is reloaded at a new
+ * address) looks the address up again.  Asynchronous.
  */
 #define FMT_STATIC_MAX_DEGREE 8
 fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const double* x, const double* y, const double* z,

@@ -15,9 +15,13 @@
 //    (m x m, m = nmono+1) lives in global memory (L2); row blocks of 4*RPT
 //    rows of [Lambda | r] are generated into shared memory and absorbed by a
 //    structured Householder step per column j (the reflector touches R's row
-//    j and the block's rows).  Threads form quads: a quad owns a column
-//    k > j, each lane a quarter of the block's rows, so a column's dot
-//    product needs only two shuffle-adds.
+//    j and the block's rows).  Threads form quads: a quad owns a column for
+//    the whole block, each lane a quarter of the block's rows, so a column's
+//    dot product needs only two shuffle-adds.  Groups of eight columns
+//    belong to one warp each, and there is no barrier per step: each warp
+//    schedules its own groups (the task that finalises the next pivot
+//    column first) and waits only for reflectors, which the owner of each
+//    pivot column publishes through a shared-memory counter (absorb_owned).
 //  * k_merge / k_combine: pairwise reduction of the triangles of a node
 //    (TSQR).  k_merge holds the second triangle packed in shared memory
 //    (m <= 166); k_combine absorbs it in row blocks, for any m.  The launch
@@ -77,6 +81,7 @@ struct QRArgs {
   int n_items;
   const int32_t* flags;  // nodes with FMT_FLAG_MIXED are already fitted (mixed path)
   int only_m;            // tile QR: > 0 takes only the items of nodes with this m
+  int* err;              // device error word (a bounded wait that ran out sets FMT_ERR_TIMEOUT)
 };
 
 __device__ __forceinline__ bool node_done(const QRArgs& a, int64_t node) {
@@ -288,18 +293,239 @@ __device__ __forceinline__ void absorb_block(double* __restrict__ B, int ldB, in
   }
 }
 
+// ---------------------------------------------------------------- owned absorb
+// The tile QR's absorb of a row block B (NB x m, shared) into R (m x m,
+// global), with no barrier per Householder step.  Column k belongs to quad
+// k & 7 of warp own(k >> 3) for the whole block (groups of eight columns
+// dealt round robin over the warps, rotated from block to block), so the
+// updates of a column by reflectors 0, 1, 2, ... are done in order by one
+// quad and a warp waits only for the reflector of the step it is at.  The
+// owner of column j+1 applies reflector j to its group first, then forms
+// reflector j+1 and publishes it (scalars in scv[2(j+1)], scv[2(j+1)+1];
+// R_{j+1,j+1} = beta; column j+1 of B is final) by raising *pub to j+2.
+// A warp at step j: waits for *pub > j (bounded: the wait sets
+// FMT_ERR_TIMEOUT and *abort on expiry, and every warp then leaves the
+// block), then updates every column k > j it owns:
+// d = gamma (amb R_jk + x . b_k), R_jk -= d amb, b_k -= d x.
+// Compared with one barrier per step, a warp with no column left at a step
+// goes on to the next step as soon as its reflector is out, so a step's last
+// partial round of 8 NW columns costs no idle lanes in the other warps.
+constexpr long long kOwnSpinMax = 1ll << 26;  // polls of one wait (about a second)
+
+__device__ __forceinline__ void own_reflector(double* __restrict__ B, int ldB, int NB, int j,
+                                              double* __restrict__ Rg, int m, double* scv) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < NB; i += 32) {
+    const double xv = B[i * ldB + j];
+    s = fma(xv, xv, s);
+  }
+  s = warp_sum(s);
+  const double alpha = Rg[(size_t)j * m + j];
+  __syncwarp();  // every lane has read R_jj before it is overwritten
+  if (s == 0.0) {
+    if (lane == 0) {
+      scv[2 * j] = 0.0;
+      scv[2 * j + 1] = 0.0;
+    }
+    return;
+  }
+  double gamma, amb, beta;
+  const double scale = refl_scalars(alpha, s, gamma, amb, beta);
+  if (scale != 0.0)
+    for (int i = lane; i < NB; i += 32) B[i * ldB + j] *= scale;
+  if (lane == 0) {
+    scv[2 * j] = gamma;
+    scv[2 * j + 1] = amb;
+    Rg[(size_t)j * m + j] = beta;
+  }
+}
+
+// Raises *pub to v once every lane's writes are visible to the block.
+__device__ __forceinline__ void own_publish(volatile int* pub, int v) {
+  __threadfence_block();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) *pub = v;
+}
+
+// Waits (lane 0, bounded) until *pub >= v and returns the value seen (in
+// every lane; the reflectors below it are visible to the warp), or -1 if
+// the block is aborting.
+__device__ __forceinline__ int own_wait(volatile int* pub, int v, volatile int* abort_flag, int* err) {
+  int seen = -1;
+  if ((threadIdx.x & 31) == 0) {
+    long long spins = 0;
+    for (;;) {
+      const int p = *pub;
+      if (p >= v) {
+        seen = p;
+        break;
+      }
+      if (*abort_flag) break;
+      if (++spins > kOwnSpinMax) {
+        atomicOr(err, FMT_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+    }
+    __threadfence_block();
+  }
+  seen = __shfl_sync(0xffffffffu, seen, 0);
+  __syncwarp();  // orders the other lanes' reads after lane 0's wait
+  return seen;
+}
+
+// Owner table of the column groups for m columns: longest first, each group
+// (work: the sum of its column indices, one update per earlier step) to the
+// warp with the least work so far (the busiest warp ends 1% above the mean
+// at m = 166 with 4 warps, 10% with 8; round robin 7% and 28%).  Also the
+// groups of every table warp in ascending order (list / start / count).
+// One thread.
+constexpr int kMaxGroups = (FMT_MAX_DEGREE + 1) * (FMT_MAX_DEGREE + 2) * (FMT_MAX_DEGREE + 3) / 6 / 8 + 1;
+struct OwnTab {
+  unsigned char own[kMaxGroups];   // table warp of each group
+  unsigned char list[kMaxGroups];  // groups by table warp, ascending
+  unsigned char start[8], count[8];
+};
+template <int NW>
+__device__ void own_table(int m, OwnTab& T) {
+  const int ng = (m + 7) >> 3;
+  int load[NW];
+  for (int w = 0; w < NW; ++w) load[w] = 0;
+  for (int g = ng - 1; g >= 0; --g) {  // the cost grows with g: descending g is longest first
+    const int k1 = 8 * g + 8 < m ? 8 * g + 8 : m;
+    const int cost = (8 * g + k1 - 1) * (k1 - 8 * g) / 2;
+    int best = 0;
+    for (int w = 1; w < NW; ++w)
+      if (load[w] < load[best]) best = w;
+    T.own[g] = (unsigned char)best;
+    load[best] += cost;
+  }
+  int o = 0;
+  for (int w = 0; w < NW; ++w) {
+    T.start[w] = (unsigned char)o;
+    for (int g = 0; g < ng; ++g)
+      if (T.own[g] == w) T.list[o++] = (unsigned char)g;
+    T.count[w] = (unsigned char)(o - T.start[w]);
+  }
+}
+
+// Lane 0 reads the published count; broadcast to the warp.  No fence: a
+// warp fences (own_acquire) before it first uses a reflector it has seen.
+__device__ __forceinline__ int own_peek(volatile int* pub) {
+  int v = 0;
+  if ((threadIdx.x & 31) == 0) v = *pub;
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+__device__ __forceinline__ void own_acquire() {
+  if ((threadIdx.x & 31) == 0) __threadfence_block();
+  __syncwarp();
+}
+
+// Every warp runs its own schedule over the groups it owns: the task
+// "apply reflector ver[g] to group g" is ready once that reflector is
+// published.  The task that makes the next reflector final (the group of
+// column P, P reflectors published, at version P-1) goes first, so the
+// owner of column j+1 publishes reflector j+1 as soon as reflector j is
+// out, whatever else it still has to do; otherwise the ready task of the
+// lowest version.  A warp with nothing ready waits for the next reflector.
+// Lane i of a warp keeps the version of the warp's i-th group in a
+// register; one warp-wide minimum picks the task.
+template <int RPT, int NW>
+__device__ __forceinline__ bool absorb_owned(double* __restrict__ B, int ldB, int m, double* __restrict__ R,
+                                             double* __restrict__ scv, volatile int* pub, volatile int* abort_flag,
+                                             int rotw, const OwnTab& T, int* err) {
+  constexpr int NB = 4 * RPT;
+  static_assert((NW & (NW - 1)) == 0, "warp count must be a power of two");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, rg = lane & 3, qi = lane >> 2;
+  const int tw = (warp - rotw) & (NW - 1);  // this warp's row of the table
+  const int gn = T.count[tw];               // at most 32 groups per warp (m <= 681, 4+ warps)
+  const int mg = lane < gn ? T.list[T.start[tw] + lane] : -1;  // the group this lane tracks
+  const int mk = mg >= 0 ? (8 * mg + 7 < m - 1 ? 8 * mg + 7 : m - 1) : 0;  // reflectors it needs
+  int mv = 0;                                                             // reflectors applied to it
+  int P = 0, Pacq = 0;  // reflectors seen published / acquired (visible) by this warp
+  if (((T.own[0] + rotw) & (NW - 1)) == warp) {
+    own_reflector(B, ldB, NB, 0, R, m, scv);
+    own_publish(pub, 1);
+    P = Pacq = 1;
+  }
+  for (;;) {
+    const bool live = mg >= 0 && mv < mk;
+    if (!__any_sync(0xffffffffu, live)) break;
+    // key: -1 for the critical task, else the version of a ready task
+    int key = 0x7fffffff;
+    if (live && mv < P) key = (mv == P - 1 && mg == (P >> 3)) ? -1 : mv;
+    const int kmin = __reduce_min_sync(0xffffffffu, key);
+    if (kmin == 0x7fffffff) {  // nothing ready: the next reflector
+      const int seen = own_wait(pub, P + 1, abort_flag, err);
+      if (seen < 0) return false;
+      P = Pacq = seen;
+      continue;
+    }
+    const int src = __ffs(__ballot_sync(0xffffffffu, key == kmin)) - 1;
+    const int sel = __shfl_sync(0xffffffffu, mg, src);
+    const int j = __shfl_sync(0xffffffffu, mv, src);
+    if (j >= Pacq) {
+      own_acquire();
+      Pacq = P;
+    }
+    const double gamma = scv[2 * j], amb = scv[2 * j + 1];
+    if (gamma != 0.0) {
+      double xr[RPT];
+#pragma unroll
+      for (int t = 0; t < RPT; ++t) xr[t] = B[(rg + 4 * t) * ldB + j];
+      const int k = 8 * sel + qi;
+      const bool act = k > j && k < m;
+      const int kk = act ? k : j;  // inactive quads read a valid column
+      const double rv = act ? R[(size_t)j * m + k] : 0.0;
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < RPT; ++t) acc = fma(xr[t], B[(rg + 4 * t) * ldB + kk], acc);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (act) {
+        const double d = gamma * fma(amb, rv, acc);
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+          double* bp = B + (rg + 4 * t) * ldB + k;
+          *bp = fma(-d, xr[t], *bp);
+        }
+        if (rg == 0) R[(size_t)j * m + k] = fma(-d, amb, rv);
+      }
+    }
+    if (lane == src) mv = j + 1;
+    if (((j + 1) >> 3) == sel) {  // column j+1 is final: reflector j+1
+      __syncwarp();
+      own_reflector(B, ldB, NB, j + 1, R, m, scv);
+      own_publish(pub, j + 2);
+      if (P < j + 2) P = Pacq = j + 2;
+    } else {
+      const int v = own_peek(pub);
+      if (v > P) P = v;
+    }
+  }
+  return true;
+}
+
 // Persistent CTAs take work items from a queue in the order of `sched`
 // (largest items first), so the longest chunks start early.  NW warps per
-// CTA (the autotuner picks 4 or 8).
+// CTA (the autotuner picks 4 or 8).  Shared memory: the row block (NB x
+// ld_max), then the reflector scalars of every step (2 ld_max >= 2 m).
 template <int RPT, int NW>
-__global__ void __launch_bounds__(32 * NW) k_tile_qr(QRArgs a) {
+__global__ void __launch_bounds__(32 * NW, NW >= 8 ? 2 : 1) k_tile_qr(QRArgs a) {
   extern __shared__ double smem[];
   constexpr int NB = 4 * RPT, NT = 32 * NW;
   static_assert(NB <= NT, "one thread generates each row of a block");
   double* Bs = smem;
-  double* Rs = smem + NB * a.ld_max;
-  double* sc = Rs + 2 * a.ld_max;
+  double* scv = smem + NB * a.ld_max;
   __shared__ int s_item;
+  __shared__ int s_pub, s_abort, s_own_m;
+  __shared__ OwnTab s_own;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_own_m = -1;
+  }
+  int nblk = 0;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
     __syncthreads();
@@ -314,6 +540,10 @@ __global__ void __launch_bounds__(32 * NW) k_tile_qr(QRArgs a) {
     if (a.only_m > 0 && g.m != a.only_m) continue;  // another degree's launch takes it
     const int m = g.m, q = g.q, ldB = g.ldB;
     double* R = a.R + a.item_roff[item];
+    if (threadIdx.x == 0 && s_own_m != m) {  // the items of a launch share m except a clamped root
+      own_table<NW>(m, s_own);
+      s_own_m = m;
+    }
     for (int e = threadIdx.x; e < m * m; e += NT) {
       const int j = e / m, k = e - j * m;
       if (k >= j) R[e] = 0.0;
@@ -349,8 +579,13 @@ __global__ void __launch_bounds__(32 * NW) k_tile_qr(QRArgs a) {
           for (int k = 0; k < m; ++k) row[k] = 0.0;
         }
       }
+      if (threadIdx.x == 0) s_pub = 0;
       __syncthreads();
-      absorb_block<RPT, NW>(Bs, ldB, 0, m, R, Rs, sc, -1);
+      absorb_owned<RPT, NW>(Bs, ldB, m, R, scv, &s_pub, &s_abort, (nblk + (int)blockIdx.x) & (NW - 1), s_own,
+                            a.err);
+      ++nblk;
+      __syncthreads();  // the block is absorbed (or abandoned): the next one may overwrite it
+      if (s_abort) return;
     }
   }
 }
@@ -812,11 +1047,18 @@ __global__ void __launch_bounds__(128) k_child_sums(ChildArgs a) {
   }
 }
 
+// The merges of a configuration with 128-row blocks absorb in 64-row blocks
+// (16 warps of k_combine would not hold 32 rows per lane in registers); its
+// shared memory is the tile QR's, which is larger.
+template <int RPT>
+constexpr int combine_rpt() { return RPT > 16 ? 16 : RPT; }
+
 template <int RPT, int NW>
 cudaError_t set_smem_attr(size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(k_tile_qr<RPT, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_combine<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_combine<combine_rpt<RPT>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
 }
 
 int ld_for(int m) { return fmt_ld_for(m); }
@@ -845,6 +1087,7 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.n_items = (int)L.n_items;
   a.flags = L.flags;
   a.only_m = 0;
+  a.err = t->d_err;
   return a;
 }
 
@@ -886,7 +1129,7 @@ fmt_tune_entry builtin_entry(int p) {
 bool entry_ok(const fmt_tune_entry& e) {
   if (e.degree < 0 || e.degree > FMT_MAX_DEGREE) return false;
   if (e.source == 0) return true;
-  if (e.rows != 16 && e.rows != 32 && e.rows != 64) return false;
+  if (e.rows != 16 && e.rows != 32 && e.rows != 64 && e.rows != 128) return false;
   if (e.warps != 4 && e.warps != 8) return false;
   if (e.chunk_factor != 1 && e.chunk_factor != 2 && e.chunk_factor != 4 && e.chunk_factor != 8 &&
       e.chunk_factor != 16)
@@ -946,7 +1189,7 @@ template <int RPT, int NW>
 cudaError_t combine_launch(const QRArgs& a, unsigned grid, size_t smem, cudaStream_t s, int level) {
   cudaError_t e = set_smem_attr<RPT, NW>(smem);
   if (e != cudaSuccess) return e;
-  k_combine<RPT><<<grid, 32 * kCombineWarps, smem, s>>>(a, level);
+  k_combine<combine_rpt<RPT>()><<<grid, 32 * kCombineWarps, smem, s>>>(a, level);
   return cudaGetLastError();
 }
 
@@ -961,8 +1204,11 @@ QROps ops_for() {
   return QROps{&resident_for<RPT, NW>, &tile_launch<RPT, NW>, &combine_launch<RPT, NW>};
 }
 QROps qr_ops(const QRConfig& c) {
-  if (c.warps == 8) return c.rows == 64 ? ops_for<16, 8>() : c.rows == 32 ? ops_for<8, 8>() : ops_for<4, 8>();
-  return c.rows == 64 ? ops_for<16, 4>() : c.rows == 32 ? ops_for<8, 4>() : ops_for<4, 4>();
+  if (c.warps == 8)
+    return c.rows == 128 ? ops_for<32, 8>() : c.rows == 64 ? ops_for<16, 8>() : c.rows == 32 ? ops_for<8, 8>()
+                                                                                               : ops_for<4, 8>();
+  return c.rows == 128 ? ops_for<32, 4>() : c.rows == 64 ? ops_for<16, 4>() : c.rows == 32 ? ops_for<8, 4>()
+                                                                                           : ops_for<4, 4>();
 }
 }  // namespace
 
@@ -1202,6 +1448,38 @@ __global__ void __launch_bounds__(kQRThreads) k_fit_node_static(StaticArgs a) {
 std::mutex g_static_mu;
 double* g_static_addr[64];
 bool g_static_ready[64];
+unsigned long long g_static_ctx[64];  // driver id of the context g_static_addr belongs to (0: unknown)
+
+// The driver's unique id of the device's current context, or 0.  A
+// cudaDeviceReset destroys the primary context and the module with it; the
+// next runtime call creates a new context with a new id (ids are never
+// reused), so a changed id marks the cached symbol address as stale.  The
+// driver entry points come through the runtime, so the library does not link
+// against libcuda.
+unsigned long long current_ctx_id() {
+  typedef int (*ctx_get_current_t)(void**);
+  typedef int (*ctx_get_id_t)(void*, unsigned long long*);
+  static ctx_get_current_t get_current = nullptr;
+  static ctx_get_id_t get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess && qb == cudaDriverEntryPointSuccess) {
+      get_current = (ctx_get_current_t)a;
+      get_id = (ctx_get_id_t)b;
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 }  // namespace
 
@@ -1226,7 +1504,13 @@ extern "C" fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const doubl
   double* R = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ready[dev]) {
+    // cudaSetDevice creates the device's primary context if a reset destroyed it
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) {
+      snprintf(msg, sizeof(msg), "fmt_fit_node_static: cudaSetDevice failed: %s", cudaGetErrorString(e));
+      return fmt_set_error(FMT_ECUDA, msg);
+    }
+    const unsigned long long ctx = current_ctx_id();
+    if (!g_static_ready[dev] || ctx == 0 || ctx != g_static_ctx[dev]) {
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_static_tri);
       if (e != cudaSuccess) {
@@ -1235,6 +1519,7 @@ extern "C" fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const doubl
       }
       g_static_addr[dev] = (double*)ptr;
       g_static_ready[dev] = true;
+      g_static_ctx[dev] = current_ctx_id();
     }
     R = g_static_addr[dev];
   }
@@ -1286,7 +1571,7 @@ extern "C" fmt_status fmt_tune_set(const fmt_tune_entry* entry) {
   if (!entry) return fmt_set_error(FMT_EINVAL, "fmt_tune_set: NULL entry");
   if (tune_install(*entry) != FMT_OK)
     return fmt_set_error(FMT_EINVAL,
-                         "fmt_tune_set: bad entry (degree 0..14, rows 16/32/64 within 227 KB of shared memory, "
+                         "fmt_tune_set: bad entry (degree 0..14, rows 16/32/64/128 within 227 KB of shared memory, "
                          "warps 4/8, chunk_factor 1/2/4/8/16, merge 0/1)");
   return FMT_OK;
 }

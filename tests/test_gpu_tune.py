@@ -49,7 +49,8 @@ def eval_tree(tree, w):
     return out.cpu().numpy()
 
 
-CONFIGS = [(rows, warps, cf, merge) for rows in (16, 32, 64) for warps in (4, 8) for cf, merge in ((1, 0), (16, 1))]
+CONFIGS = [(rows, warps, cf, merge) for rows in (16, 32, 64, 128) for warps in (4, 8)
+           for cf, merge in ((1, 0), (16, 1))]
 
 
 @pytest.mark.parametrize("rows,warps,chunk_factor,merge", CONFIGS)
