@@ -22,9 +22,13 @@
 //    schedules its own groups (the task that finalises the next pivot
 //    column first) and waits only for reflectors, which the owner of each
 //    pivot column publishes through a shared-memory counter (absorb_owned).
-//  * k_merge / k_combine: pairwise reduction of the triangles of a node
-//    (TSQR).  k_merge holds the second triangle packed in shared memory
-//    (m <= 166); k_combine absorbs it in row blocks, for any m.  The launch
+//  * k_merge / k_merge_cl / k_combine: pairwise reduction of the triangles
+//    of a node (TSQR).  k_merge holds the second triangle packed in shared
+//    memory (m <= 166); k_merge_cl spreads one merge over a cluster of 2-8
+//    CTAs at the upper tree levels (few pairs in flight), column groups
+//    owned by warps and reflectors published through shared-memory counters
+//    and read over distributed shared memory; k_combine absorbs the second
+//    triangle in row blocks, for any m.  The launch
 //    configuration table (rows per block, warps, chunk floor, merge kernel)
 //    is per degree, built in or autotuned.
 //  * k_backsolve: one warp per node, column-oriented back substitution.
@@ -37,6 +41,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <cooperative_groups.h>
 #include <mutex>
 
 #include "fmt_internal.cuh"
@@ -772,6 +777,344 @@ size_t merge_smem_bytes(int m) {
   return ((size_t)((m * (m + 1) / 2 + 1) & ~1) + 2 * (size_t)ld_for(m) + 4) * sizeof(double);
 }
 
+// ---------------------------------------------------------------- cluster merge
+// The merge of two triangles [R_a; R_b] (a TSQR tree level) by a cluster of
+// C CTAs: the top levels of a node's merge tree hold few pairs, and one merge
+// on one SM is a chain of m dependent Householder steps, so there the steps
+// are spread over C SMs.  Columns come in groups of W = 32 / LW (LW lanes per
+// column); each group belongs to one warp of one CTA, which keeps the
+// group's columns of R_b and of R_a (rows 0 .. W g + W - 1, both upper
+// triangular; step j touches rows 0..j of R_b and row j of R_a) in its
+// shared memory for the whole merge and writes R_a back at the end.  Step
+// j's reflector is formed from column j by the warp that owns it as soon as
+// reflector j-1 has reached that column: its scalars stay in the owner
+// CTA's shared memory and a counter in every CTA is raised by a release
+// reduction.  A warp applies reflector j to its groups once the counter of
+// its own CTA passes j (acquire load), reading the reflector's scalars and
+// vector from the owner CTA's shared memory (distributed shared memory).  Each warp schedules its
+// groups as absorb_owned does: the task that finalises the next pivot
+// column first, else the oldest ready one.  Waits are bounded (kOwnSpinMax
+// polls; FMT_ERR_TIMEOUT).  C = 1 is the same kernel on one SM.
+namespace cg = cooperative_groups;
+constexpr int kMCWarps = 8;
+constexpr int kMCMaxM = 287;  // degree <= 10
+constexpr int kMCMaxGroups = kMCMaxM;
+
+struct MCLayout {
+  unsigned char own_cta[kMCMaxGroups], own_warp[kMCMaxGroups];
+  int off[kMCMaxGroups];                 // offset (doubles) of the group's blocks in its CTA's block area
+  unsigned short list[kMCMaxGroups];     // groups by owner (cta-major), ascending
+  unsigned short start[8 * kMCWarps], count[8 * kMCWarps];
+  int cta_doubles[8];                    // block area of each CTA
+};
+
+// Longest-first over the C * kMCWarps owners (owner o: CTA o % C, warp o / C,
+// so consecutive owners sit on different SMs); work of group g ~ (W g + W)^2.
+// A group's blocks: R_b part then R_a part, (W g + W) rows of W doubles each.
+__host__ __device__ inline bool mc_layout(int m, int C, int W, MCLayout& L) {
+  const int ng = (m + W - 1) / W, no = C * kMCWarps;
+  if (ng > kMCMaxGroups) return false;
+  long long load[8 * kMCWarps];
+  for (int o = 0; o < no; ++o) load[o] = 0;
+  unsigned short own_o[kMCMaxGroups];
+  for (int g = ng - 1; g >= 0; --g) {
+    int best = 0;
+    for (int o = 1; o < no; ++o)
+      if (load[o] < load[best]) best = o;
+    own_o[g] = (unsigned short)best;
+    load[best] += (long long)(W * g + W) * (W * g + W);
+  }
+  for (int c = 0; c < 8; ++c) L.cta_doubles[c] = 0;
+  for (int g = 0; g < ng; ++g) {
+    const int o = own_o[g], c = o % C;
+    L.own_cta[g] = (unsigned char)c;
+    L.own_warp[g] = (unsigned char)(o / C);
+    L.off[g] = L.cta_doubles[c];
+    L.cta_doubles[c] += 2 * (W * g + W) * W;
+  }
+  int n = 0;
+  for (int c = 0; c < C; ++c)
+    for (int w = 0; w < kMCWarps; ++w) {
+      L.start[c * kMCWarps + w] = (unsigned short)n;
+      for (int g = 0; g < ng; ++g)
+        if (L.own_cta[g] == c && L.own_warp[g] == w) L.list[n++] = (unsigned short)g;
+      L.count[c * kMCWarps + w] = (unsigned short)(n - L.start[c * kMCWarps + w]);
+      if (L.count[c * kMCWarps + w] > 32) return false;  // one lane tracks each group of a warp
+    }
+  return true;
+}
+
+__host__ __device__ inline int mc_scv_doubles(int m) { return (2 * m + 1) & ~1; }
+
+__device__ __forceinline__ uint32_t mc_smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Raise the counter at shared address `laddr` of CTA `rank` to at least v,
+// after this thread's earlier writes (and those ordered before it) are
+// visible to the cluster (C > 1) or the CTA.
+template <int C>
+__device__ __forceinline__ void mc_raise(uint32_t laddr, int rank, int v) {
+  if (C > 1) {
+    uint32_t raddr;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
+    asm volatile("red.release.cluster.shared::cluster.max.s32 [%0], %1;" ::"r"(raddr), "r"(v) : "memory");
+  } else {
+    asm volatile("red.release.cta.shared::cta.max.s32 [%0], %1;" ::"r"(laddr), "r"(v) : "memory");
+  }
+}
+template <int C>
+__device__ __forceinline__ int mc_read(uint32_t laddr) {
+  int v;
+  if (C > 1)
+    asm volatile("ld.acquire.cluster.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(laddr) : "memory");
+  else
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(laddr) : "memory");
+  return v;
+}
+
+template <int C, int LW>
+__global__ void __launch_bounds__(32 * kMCWarps) k_merge_cl(QRArgs a, int level) {
+  constexpr int W = 32 / LW;  // columns per group (one per LW lanes)
+  extern __shared__ double smem[];
+  __shared__ MCLayout L;
+  __shared__ int s_pub, s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, rg = lane % LW, qi = lane / LW;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = C > 1 ? (int)cl.block_rank() : 0;
+  const int item = (int)(blockIdx.x / C);
+  const int sidx = a.item_local[item];
+  const int64_t node = a.item_node[item];
+  const int cnt = a.node_nitems[node];
+  const int step = 1 << level;
+  // every CTA of a cluster takes the same decision
+  if ((sidx & (2 * step - 1)) != 0 || sidx + step >= cnt || node_done(a, node)) return;
+  const NodeGeom geo = node_geom(a, node);
+  const int m = geo.m;
+  double* Ra = a.R + a.item_roff[item];
+  const double* Rb = a.R + a.item_roff[item + step];
+  double* scv = smem;                      // gamma_j, amb_j of every step
+  double* vbuf = smem + mc_scv_doubles(m); // per warp: a copy of another CTA's pivot column (m doubles)
+  double* blk = vbuf + kMCWarps * m;       // this CTA's group blocks
+  if (tid == 0) {
+    mc_layout(m, C, W, L);
+    s_pub = 0;
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int ng = (m + W - 1) / W;
+  for (int g = 0; g < ng; ++g) {
+    if (L.own_cta[g] != rank) continue;
+    const int rows = W * g + W;
+    double* b = blk + L.off[g];
+    for (int e = tid; e < rows * W; e += 32 * kMCWarps) {
+      const int i = e / W, k = W * g + (e % W);
+      const bool in = k < m && i <= k;
+      b[e] = in ? Rb[(size_t)i * m + k] : 0.0;
+      b[rows * W + e] = in ? Ra[(size_t)i * m + k] : 0.0;
+    }
+  }
+  __syncthreads();
+  if (C > 1) cl.sync();  // every CTA's blocks and counter are set before any remote access
+  const uint32_t pub_addr = mc_smem_u32(&s_pub);
+  volatile int* vab = &s_abort;
+
+  auto cta_ptr = [&](double* p, int c) -> double* { return C > 1 ? cl.map_shared_rank(p, c) : p; };
+  auto kmax = [&](int g) { return W * g + W - 1 < m - 1 ? W * g + W - 1 : m - 1; };
+  // Reflector j from column j of its group (this warp) and R_a[j][j]; the
+  // scalars to every CTA, then the counters.
+  // s = |rows 0..j of R_b's column j|^2, the same value in every lane.
+  auto reflect_publish = [&](int j, double s) {
+    const int gj = j / W, cj = j % W, rows = W * gj + W;
+    double* col = blk + L.off[gj] + cj;  // R_b row i at col[W i], R_a row i at col[W (rows + i)]
+    double* ajj = col + W * (rows + j);
+    const double alpha = *ajj;
+    __syncwarp();
+    double gamma = 0.0, amb = 0.0, beta;
+    if (s != 0.0) {
+      const double scale = refl_scalars(alpha, s, gamma, amb, beta);
+      if (scale != 0.0)
+        for (int i = lane; i <= j; i += 32) col[W * i] *= scale;
+      if (lane == 0) *ajj = beta;
+    }
+    if (lane == 0) {  // the scalars stay with the owner; other CTAs read them remotely
+      scv[2 * j] = gamma;
+      scv[2 * j + 1] = amb;
+    }
+    __syncwarp();
+    if (lane < C) mc_raise<C>(pub_addr, lane, j + 1);
+  };
+
+  const int ow = rank * kMCWarps + warp;
+  const int gn = L.count[ow];
+  const int mg = lane < gn ? L.list[L.start[ow] + lane] : -1;
+  const int mk = mg >= 0 ? kmax(mg) : 0;
+  int mv = 0;
+  int P = 0;
+  int vcopy = -1;  // the remote pivot column this warp's buffer holds
+  if (L.own_cta[0] == rank && L.own_warp[0] == warp) {
+    const double b00 = blk[L.off[0]];
+    reflect_publish(0, b00 * b00);
+    P = 1;
+  }
+  for (;;) {
+    const bool live = mg >= 0 && mv < mk;
+    if (!__any_sync(0xffffffffu, live)) break;
+    int key = 0x7fffffff;
+    // the critical task, else the oldest ready one (ties: the group needed soonest)
+    if (live && mv < P) key = (mv == P - 1 && mg == P / W) ? -1 : (mv << 10) | mg;
+    const int kmin = __reduce_min_sync(0xffffffffu, key);
+    if (kmin == 0x7fffffff) {  // nothing ready: wait for the next reflector
+      int seen = -1;
+      if (lane == 0) {
+        long long spins = 0;
+        for (;;) {
+          const int pv = mc_read<C>(pub_addr);
+          if (pv > P) {
+            seen = pv;
+            break;
+          }
+          if (*vab) break;
+          if (++spins > kOwnSpinMax) {
+            atomicOr(a.err, FMT_ERR_TIMEOUT);
+            *vab = 1;
+            break;
+          }
+        }
+      }
+      seen = __shfl_sync(0xffffffffu, seen, 0);
+      __syncwarp();
+      if (seen < 0) break;  // aborting: leave through the cluster barrier
+      P = seen;
+      continue;
+    }
+    const int srcl = __ffs(__ballot_sync(0xffffffffu, key == kmin)) - 1;
+    const int sel = __shfl_sync(0xffffffffu, mg, srcl);
+    const int j = __shfl_sync(0xffffffffu, mv, srcl);
+    const int gj = j / W, oj = L.own_cta[gj];
+    const double* sj = oj == rank ? scv : cta_ptr(scv, oj);
+    const double gamma = sj[2 * j], amb = sj[2 * j + 1];
+    const int rows = W * sel + W;
+    double nsq = 0.0;
+    if (gamma != 0.0) {
+      const double* vj = blk + L.off[gj] + (j % W);  // v_i at vj[vs i]
+      int vs = W;
+      if (oj != rank) {
+        // another CTA's column: one pipelined pass of remote loads into this
+        // warp's buffer (kept while the warp stays on the same reflector)
+        double* lv = vbuf + warp * m;
+        if (vcopy != j) {
+          const double* rv_ = cta_ptr(blk + L.off[gj], oj) + (j % W);
+          for (int i = lane; i <= j; i += 32) lv[i] = rv_[W * i];
+          __syncwarp();
+          vcopy = j;
+        }
+        vj = lv;
+        vs = 1;
+      }
+      double* ck = blk + L.off[sel] + qi;  // R_b column W sel + qi: row i at ck[W i]
+      double* ak = ck + W * (rows + j);    // R_a[j][W sel + qi]
+      const int k = W * sel + qi;
+      const bool act = k > j && k < m;
+      const double rv = *ak;
+      double a0 = 0.0, a1 = 0.0;
+      int i = rg;
+      for (; i + LW <= j; i += 2 * LW) {
+        a0 = fma(vj[vs * i], ck[W * i], a0);
+        a1 = fma(vj[vs * (i + LW)], ck[W * (i + LW)], a1);
+      }
+      if (i <= j) a0 = fma(vj[vs * i], ck[W * i], a0);
+      double acc = a0 + a1;
+#pragma unroll
+      for (int o = 1; o < LW; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (act) {
+        const double d = gamma * fma(amb, rv, acc);
+        double sq = 0.0;  // squares of the updated rows (the next pivot column's norm)
+        for (int i2 = rg; i2 <= j; i2 += LW) {
+          const double nv = fma(-d, vj[vs * i2], ck[W * i2]);
+          ck[W * i2] = nv;
+          sq = fma(nv, nv, sq);
+        }
+        if (rg == 0) *ak = fma(-d, amb, rv);
+        nsq = sq;
+      }
+    }
+    if (lane == srcl) mv = j + 1;
+    if ((j + 1) / W == sel) {  // column j+1 is final: reflector j+1
+      // its norm: the updated rows 0..j (summed over the column's LW lanes) and row j+1
+      const int cq = (j + 1) % W;
+      double s;
+      if (gamma != 0.0) {
+        double part = lane / LW == cq ? nsq : 0.0;
+#pragma unroll
+        for (int o = 1; o < LW; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        s = __shfl_sync(0xffffffffu, part, cq * LW);
+      } else {
+        // no reflection at step j: column j+1's rows 0..j are unchanged
+        double part = 0.0;
+        const double* cc = blk + L.off[sel] + cq;
+        for (int i = lane; i <= j; i += 32) part = fma(cc[W * i], cc[W * i], part);
+        s = warp_sum(part);
+      }
+      const double bjj = blk[L.off[sel] + cq + W * (j + 1)];  // row j+1 of column j+1 (no step has touched it)
+      __syncwarp();
+      reflect_publish(j + 1, fma(bjj, bjj, s));
+      if (P < j + 2) P = j + 2;
+    } else {
+      int v = 0;
+      if (lane == 0) v = mc_read<C>(pub_addr);
+      v = __shfl_sync(0xffffffffu, v, 0);
+      __syncwarp();
+      if (v > P) P = v;
+    }
+  }
+  __syncthreads();
+  // R_a back to global memory: the owned columns, rows 0..k
+  for (int g = 0; g < ng; ++g) {
+    if (L.own_cta[g] != rank) continue;
+    const int rows = W * g + W;
+    const double* b = blk + L.off[g] + rows * W;
+    for (int e = tid; e < rows * W; e += 32 * kMCWarps) {
+      const int i = e / W, k = W * g + (e % W);
+      if (k < m && i <= k) Ra[(size_t)i * m + k] = b[e];
+    }
+  }
+  if (C > 1) cl.sync();  // no CTA leaves while another may still read its blocks or raise its counter
+}
+
+// Dynamic shared memory of the cluster merge with C CTAs (the largest CTA's
+// share), or 0 if the layout does not exist or a share exceeds 200 KB.
+size_t merge_cl_smem_bytes(int m, int C, int W) {
+  if (m > kMCMaxM) return 0;
+  MCLayout L;
+  if (!mc_layout(m, C, W, L)) return 0;
+  int mx = 0;
+  for (int c = 0; c < C; ++c) mx = L.cta_doubles[c] > mx ? L.cta_doubles[c] : mx;
+  const size_t b = ((size_t)mc_scv_doubles(m) + (size_t)kMCWarps * m + (size_t)mx) * sizeof(double);
+  return b <= 200 * 1024 ? b : 0;
+}
+
+template <int C, int LW>
+cudaError_t merge_cl_launch(const QRArgs& a, int64_t n_items, size_t smem, int level, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_merge_cl<C, LW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_items * C));
+  cfg.blockDim = dim3(32 * kMCWarps);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_merge_cl<C, LW>, a, level);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- back solve
 struct BSArgs {
   int64_t n_nodes;
@@ -1273,6 +1616,23 @@ cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double*
   const int mx = t->lv[depth].max_m;
   const QRConfig cfg = qr_config(mx);
   const size_t msm = merge_smem_bytes(mx);
+  // Upper tree levels (few pairs in flight): each merge on a cluster of C SMs,
+  // C from the estimated pairs of this tree level, raised until a CTA's share
+  // of the two triangles fits in shared memory.
+  const int64_t est = n_items >> (tree_level + 1);
+  if (cfg.merge == 0 && est < 76) {
+    int C = est >= 38 ? 2 : est >= 19 ? 4 : 8;
+    constexpr int kLW = 8, kW = 32 / kLW;
+    while (C < 8 && merge_cl_smem_bytes(mx, C, kW) == 0) C *= 2;
+    const size_t csm = merge_cl_smem_bytes(mx, C, kW);
+    if (csm > 0) {
+      switch (C) {
+        case 2: return merge_cl_launch<2, kLW>(a, n_items, csm, tree_level, s);
+        case 4: return merge_cl_launch<4, kLW>(a, n_items, csm, tree_level, s);
+        default: return merge_cl_launch<8, kLW>(a, n_items, csm, tree_level, s);
+      }
+    }
+  }
   if (cfg.merge == 0 && msm <= 200 * 1024) {
     if ((e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm)) != cudaSuccess)
       return e;
