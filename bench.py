@@ -673,9 +673,12 @@ def mixed_rooflines(prof, degree, steps, probe_tflops, peaks):
     proj_bytes_row = 4 * Lp * 128 / 64 + 8
     entry("mixed_proj", "hbm", lambda v: v["units"] * proj_bytes_row, "GB/s", peaks["hbm_gbs"],
           peaks["source"] + " (copy)", "%.0f B per row (digit-tile cache + s)" % proj_bytes_row)
-    # sweep residual: FP64 Horner (flops recorded by the library)
-    entry("mixed_sresid", "alu", lambda v: v["flops"], "TFLOP/s", FP64_NOMINAL_TFLOPS, fp64_src,
-          "Horner flops of s = r - Lambda F per row")
+    # sweep residual: double-float Horner on the FP32 pipe, 18 FP32 instructions per multiply-add
+    # (the library records 2 flops per multiply-add); peak = 152 SMs x 128 lanes x 2.07 GHz
+    fp32_lane_instr_peak = 152 * 128 * 2.07e9 / 1e12
+    entry("mixed_sresid", "alu", lambda v: v["flops"] / 2.0 * 18.0, "TFLOP/s", fp32_lane_instr_peak,
+          "FP32 pipe issue rate (152 SMs x 128 lanes x 2.07 GHz, T lane-instructions/s)",
+          "double-float Horner of s = r - Lambda F: 18 FP32 instructions per multiply-add (T lane-instr/s)")
     # factor: Cholesky of the m x m Gram (m^3 / 3 FMAs) + back substitution, per node
     entry("mixed_factor", "alu", lambda v: v["units"] * (2.0 * m ** 3 / 3.0 + 2.0 * L * L), "TFLOP/s",
           FP64_NOMINAL_TFLOPS, fp64_src, "2 m^3/3 + 2 L^2 flops per node (latency-bound: one node per CTA)")

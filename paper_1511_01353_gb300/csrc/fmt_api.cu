@@ -270,6 +270,9 @@ void destroy(fmt_tree* t) {
     if (t->join_ev[q]) cudaEventDestroy(t->join_ev[q]);
   }
   if (t->fork_ev) cudaEventDestroy(t->fork_ev);
+  if (t->piv_stream) cudaStreamDestroy(t->piv_stream);
+  if (t->piv_fork) cudaEventDestroy(t->piv_fork);
+  if (t->piv_join) cudaEventDestroy(t->piv_join);
   free(t->allocs);
   if (t->h_plan) cudaFreeHost(t->h_plan);
   if (t->h_err) cudaFreeHost(t->h_err);
@@ -604,6 +607,25 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
     ProfScope ps(K_MFACTOR, s, 1, nodes, 0.0);
     CUDA_TRY(t, launch_mixed_factor(t, depth, b, s), "mixed factor launch");
   }
+  // Nodes whose Cholesky pivot was too small go to Householder: refit them on
+  // a side stream while the sweeps run (their QR scratch slots are not used
+  // by the FP64 tier, which skips them); fit_level_launches joins it before
+  // the other Householder refits.
+  {
+    cudaError_t e = cudaSuccess;
+    if (!t->piv_stream) e = cudaStreamCreateWithFlags(&t->piv_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !t->piv_fork) e = cudaEventCreateWithFlags(&t->piv_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !t->piv_join) e = cudaEventCreateWithFlags(&t->piv_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(t->piv_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(t->piv_stream, t->piv_fork, 0);
+    if (e == cudaSuccess) {
+      ProfScope ps(K_TILE_QR, t->piv_stream, 1, 0.0, 0.0);
+      e = launch_tile_qr(t, depth, t->Rbuf, t->piv_stream, 1);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(t->piv_join, t->piv_stream);
+    CUDA_TRY(t, e, "early Householder refit launch");
+    t->piv_pending = true;
+  }
   const int sweeps = t->P.sweeps == 0 ? FMT_MIXED_MAX_SWEEPS : (t->P.sweeps < 0 ? 0 : t->P.sweeps);
   for (int k = 0; k < sweeps; ++k) {
     {
@@ -657,8 +679,14 @@ fmt_status fit_level_launches(fmt_tree* t, int depth, cudaStream_t s) {
     // on the mixed path only the nodes it left to FP64 are factorised here
     // one launch per degree present in the level (launch_tile_qr)
     const int nlaunch = L.deg_mask ? __builtin_popcountll((unsigned long long)L.deg_mask) : 1;
+    int mode = 0;
+    if (t->piv_pending) {  // the early refits (fit_level_mixed) are done before the rest
+      CUDA_TRY(t, cudaStreamWaitEvent(s, t->piv_join, 0), "early refit join");
+      t->piv_pending = false;
+      mode = 2;
+    }
     ProfScope ps(K_TILE_QR, s, nlaunch, rows, t->P.precision == FMT_MIXED ? 0.0 : L.qr_flops);
-    CUDA_TRY(t, launch_tile_qr(t, depth, t->Rbuf, s), "tile QR launch");
+    CUDA_TRY(t, launch_tile_qr(t, depth, t->Rbuf, s, mode), "tile QR launch");
   }
   int levels = 0;
   while ((int64_t(1) << levels) < L.max_chunks) ++levels;

@@ -87,10 +87,26 @@ struct QRArgs {
   const int32_t* flags;  // nodes with FMT_FLAG_MIXED are already fitted (mixed path)
   int only_m;            // tile QR: > 0 takes only the items of nodes with this m
   int* err;              // device error word (a bounded wait that ran out sets FMT_ERR_TIMEOUT)
+  int node_mode;         // tile QR: which nodes it takes (launch_tile_qr's mode)
 };
 
+// A node the mixed path's tensor-core tier left for a small Cholesky pivot:
+// eligible for that tier (degree <= FMT_MIXED_MAX_DEGREE, not a clamped root),
+// FMT_FLAG_MIXED_PIVOT and no FMT_FLAG_MIXED_SLOW (the FP64 tier, which
+// runs later, sets the pivot flag only on nodes that were not eligible or
+// did not converge).  These are known right after the factor kernel.
+__device__ __forceinline__ bool early_refit(const QRArgs& a, int64_t node, int32_t f) {
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const bool eligible = pr.degree <= FMT_MIXED_MAX_DEGREE && !(a.depth == 0 && pr.q_root < pr.degree);
+  return eligible && (f & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_SLOW | FMT_FLAG_MIXED_PIVOT)) == FMT_FLAG_MIXED_PIVOT;
+}
+
 __device__ __forceinline__ bool node_done(const QRArgs& a, int64_t node) {
-  return (a.flags[node] & FMT_FLAG_MIXED) != 0;
+  const int32_t f = a.flags[node];
+  if (f & FMT_FLAG_MIXED) return true;
+  if (a.node_mode == 1) return !early_refit(a, node, f);
+  if (a.node_mode == 2) return early_refit(a, node, f);
+  return false;
 }
 
 // degree, column count and frame of a node of the level
@@ -1431,6 +1447,7 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.flags = L.flags;
   a.only_m = 0;
   a.err = t->d_err;
+  a.node_mode = 0;
   return a;
 }
 
@@ -1571,14 +1588,16 @@ int qr_resident_ctas(int m) {
 // degree first: as one launch's persistent CTAs run out of items the next
 // one's take their SMs, so the launches share one tail instead of one each.
 // A level of one degree is one launch on s.
-cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s) {
+cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s, int mode) {
   const fmt_level& L = t->lv[depth];
   const int64_t n_items = L.n_items;
   if (n_items <= 0) return cudaSuccess;
   const uint64_t mask = (uint64_t)L.deg_mask;
   const bool several = (mask & (mask - 1)) != 0;
+  int* work0 = t->d_work + 1 + (mode == 1 ? FMT_MAX_DEGREE + 1 : 0);
   auto launch_one = [&](int mq, cudaStream_t st, int* work) -> cudaError_t {
     QRArgs a = make_qr_args(t, depth, R);
+    a.node_mode = mode;
     a.only_m = several ? mq : 0;
     a.ld_max = ld_for(mq);
     a.work = work;
@@ -1590,7 +1609,7 @@ cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     return qr_ops(c).tile(a, (unsigned)grid, smem, st);
   };
-  if (!several) return launch_one(L.max_m, s, t->d_work + 1);
+  if (!several) return launch_one(L.max_m, s, work0);
   cudaError_t e;
   if (!t->fork_ev && (e = cudaEventCreateWithFlags(&t->fork_ev, cudaEventDisableTiming)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(t->fork_ev, s)) != cudaSuccess) return e;
@@ -1600,7 +1619,7 @@ cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s) {
     if (!t->join_ev[q] && (e = cudaEventCreateWithFlags(&t->join_ev[q], cudaEventDisableTiming)) != cudaSuccess)
       return e;
     if ((e = cudaStreamWaitEvent(t->side[q], t->fork_ev, 0)) != cudaSuccess) return e;
-    if ((e = launch_one(fmt_nmono(q) + 1, t->side[q], t->d_work + 1 + q)) != cudaSuccess) return e;
+    if ((e = launch_one(fmt_nmono(q) + 1, t->side[q], work0 + q)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t->join_ev[q], t->side[q])) != cudaSuccess) return e;
   }
   for (int q = 0; q <= FMT_MAX_DEGREE; ++q)

@@ -226,7 +226,7 @@ struct fmt_level {
 // Small result block that refine reads back in one copy.
 // work-queue counters per tree: slot 0 for single launches, slot 1 + q for
 // the tile-QR launch of degree q
-constexpr int kWorkSlots = FMT_MAX_DEGREE + 2;
+constexpr int kWorkSlots = 2 * (FMT_MAX_DEGREE + 1) + 2;  // 0: mixed Gram; 1 + q: tile QR; 16 + q: early refits
 
 struct fmt_plan_out {
   int64_t n_new, n_items, max_chunks, chunk_rows, n_points, n_near, err;
@@ -264,6 +264,11 @@ struct fmt_tree {
   // caller's (created on first use, destroyed with the tree)
   cudaStream_t side[FMT_MAX_DEGREE + 1] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[FMT_MAX_DEGREE + 1] = {};
+  // mixed path: the Householder refits of small-pivot nodes run on piv_stream
+  // while the sweeps run on the caller's stream
+  cudaStream_t piv_stream = nullptr;
+  cudaEvent_t piv_fork = nullptr, piv_join = nullptr;
+  bool piv_pending = false;
   double tau = 0.0, maxabs = 0.0; // problem 0 (single-problem trees)
   int sort_bits = 0;       // Morton bits in the sort key (3 per sorted level)
   int pid_bits = 0;        // problem-id bits above them
@@ -333,7 +338,9 @@ fmt_status tune_install(const fmt_tune_entry& e);  // FMT_EINVAL on a bad entry
 fmt_tune_entry tune_current(int degree);
 int qr_resident_ctas(int m);  // SMs x resident QR CTAs per SM
 size_t qr_smem_bytes(int m, int rows);
-cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s);  // may create side streams
+// mode 0: every node not fitted by the mixed path; 1: only the mixed path's
+// small-pivot nodes (refitted early); 2: mode 0 without those.
+cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s, int mode = 0);  // may create side streams
 cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s);
 cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream_t s);
 cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s);

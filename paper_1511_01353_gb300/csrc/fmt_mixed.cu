@@ -20,7 +20,7 @@
 //  3. k_mfactor: per node, the item Grams are summed in FP64 and factorised by
 //     Cholesky; the factor is R-hat = [[R, Q^T r], [0, rho]] of the FP64 path
 //     (the same matrix's R factor, up to row signs).  F = R^{-1} Q^T r.
-//  4. sweeps: s = r - Lambda F in FP64 (k_msresid), g = B^T s on the tensor
+//  4. sweeps: s = r - Lambda F (k_msresid, double-float), g = B^T s on the tensor
 //     cores from the stored digit tiles (TMA bulk loads) and the integer
 //     digits of s, exactly (k_mgram projection mode), F += R^{-1} R^{-T} g
 //     (k_mupdate).
@@ -1016,7 +1016,34 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
 }
 
 // ------------------------------------------------------------------ sweeps
-// s = r - Lambda F in FP64 (the residual of the current fit, r untouched)
+// The node polynomial of fmt_horner_t in double-float with the Horner
+// coefficients in shared memory (hi, lo pairs).
+__device__ __forceinline__ dfl horner_df_shared(const float2* G, int p, int nmono, dfl u, dfl v, dfl w) {
+  int idx = nmono - 1;
+  dfl P = {0.0f, 0.0f};
+  for (int l = p; l >= 0; --l) {
+    dfl t = {0.0f, 0.0f};
+    for (int m = p - l; m >= 0; --m) {
+      dfl s = {0.0f, 0.0f};
+      for (int n = p - l - m; n >= 0; --n) {
+        const float2 g = G[idx--];
+        s = df_fma(s, w, dfl{g.x, g.y});
+      }
+      t = df_fma(t, v, s);
+    }
+    P = df_fma(P, u, t);
+  }
+  return P;
+}
+
+// s = r - Lambda F (the residual of the current fit, r untouched).  The
+// tensor-core tier (kDF) evaluates the polynomial in double-float (FP32
+// pairs, about 48 bits) on the FP32 pipe, node frame and the final
+// subtraction in FP64: the sweeps' fixed point then carries a relative error
+// of about 2^-48 of |Lambda F| in s, far below the tier's acceptance bounds
+// (1e-7 of the fit, 1e-8 max|f|, and the 2^-31 quantisation of its basis).
+// The FP64 tier keeps the FP64 residual its rounding test assumes.
+template <bool kDF>
 __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
   const int item = blockIdx.x;
   const int64_t node = a.item_node[item];
@@ -1030,10 +1057,25 @@ __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
   fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
   const int p = pr.degree, nm = fmt_nmono_d(p);
   const double* Gc = a.hcoef + node * a.stride;
+  __shared__ float2 hdf[kDF ? (FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6 : 1];
+  if (kDF) {
+    for (int k = threadIdx.x; k < nm; k += blockDim.x) {
+      const double g = Gc[k];
+      const float h = __double2float_rn(g);
+      hdf[k] = make_float2(h, __double2float_rn(g - (double)h));
+    }
+    __syncthreads();
+  }
   double ms = 0.0;
   for (int64_t i = a.item_start[item] + threadIdx.x; i < a.item_end[item]; i += blockDim.x) {
     const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
-    const double si = a.r[i] - fmt_horner(Gc, p, nm, u, v, w);
+    double si;
+    if (kDF) {
+      const dfl P = horner_df_shared(hdf, p, nm, df_of(u), df_of(v), df_of(w));
+      si = a.r[i] - ((double)P.h + (double)P.l);
+    } else {
+      si = a.r[i] - fmt_horner(Gc, p, nm, u, v, w);
+    }
     a.s[i] = si;
     ms = fmax(ms, fabs(si));
   }
@@ -1874,7 +1916,7 @@ cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bu
 cudaError_t launch_mixed_sresid(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
   const fmt_level& L = t->lv[depth];
   if (L.n_items <= 0) return cudaSuccess;
-  k_msresid<<<(unsigned)L.n_items, 256, 0, s>>>(make_margs(t, depth, b));
+  k_msresid<true><<<(unsigned)L.n_items, 256, 0, s>>>(make_margs(t, depth, b));
   return cudaGetLastError();
 }
 
@@ -1923,7 +1965,7 @@ cudaError_t launch_tier2_sweep(const fmt_tree* t, int depth, const fmt_mixed_buf
   a.tier = 2;
   a.last_sweep = last ? 1 : 0;
   if (part == 0) {
-    k_msresid<<<(unsigned)L.n_items, 256, 0, s>>>(a);
+    k_msresid<false><<<(unsigned)L.n_items, 256, 0, s>>>(a);
   } else if (part == 1) {
     k_dproj<<<(unsigned)L.n_items, 256, 0, s>>>(a);
   } else {
