@@ -560,6 +560,17 @@ def block_batch(args, stream, flush):
     xq, yq, zq, tp = dev(w.xq), dev(w.yq), dev(w.zq), dev(w.tprob)
     out = torch.empty(M, dtype=torch.float64, device="cuda")
     preds, res = {}, {}
+    # the project's autotuner on the first 256 problems (all degrees, concurrent launches)
+    k = min(256, P)
+    nk = int(w.offsets[k])
+    t_tune = time.perf_counter()
+    tprm = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel)
+    tune = F.fmt_autotune_forest(tprm, w.offsets[:k + 1], x[:nk], y[:nk], z[:nk], f[:nk], degrees=w.degrees[:k],
+                                 boxes=w.boxes[:k], stream=stream)
+    tune["seconds"] = time.perf_counter() - t_tune
+    tune["sample"] = "first %d problems (%d points), FP64 level loop timed per candidate" % (k, nk)
+    tune["table"] = {str(d): {kk: F.fmt_tune_get(d)[kk] for kk in ("rows", "warps", "chunk_factor", "merge", "source")}
+                     for d in sorted(set(int(v) for v in w.degrees))}
     for name, prec in (("fp64", F.FMT_FP64), ("mixed", F.FMT_MIXED)):
         prm = F.make_params(4, w.max_depth, w.min_pts, w.tol_rel, precision=prec, sweeps=args.sweeps)
         # warm-up on the first 256 problems (kernels, pools, tables)
@@ -634,6 +645,7 @@ def block_batch(args, stream, flush):
             "mixed_vs_fp64_median_err_over_max_f": float(np.median(rel)),
             "vs_oracle_max_err_over_max_f": ora,
             "oracle_sample": "problems %s (the smallest of each degree), oracle fit %.1f s" % (sample, t_or),
+            "autotune": tune,
             "l2": "flushed before each timed step (256 MB write)",
             "warmup": "first 256 problems, each path", "steps": 1, "generation_s": t_gen,
             "target_err": {"mixed": 1e-6, "fp64": 1e-10}}
@@ -997,6 +1009,8 @@ def main():
             blocks["c3"] = block_c3(args, stream, flush)
         if "batch" in wanted:
             blocks["batch"] = block_batch(args, stream, flush)
+            for d in range(F.FMT_MAX_DEGREE + 1):  # back to the built-in rule for what follows
+                F.fmt_tune_set(dict(degree=d, source=0, rows=64, warps=4, chunk_factor=4, merge=0))
             torch.cuda.empty_cache()
         if "serve" in wanted:
             blocks["serve"] = block_serve(args)

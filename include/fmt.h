@@ -410,6 +410,33 @@ typedef struct {
   int32_t pad;
 } fmt_tune_entry;
 fmt_status fmt_autotune(int32_t degree, int64_t sample_points, void* stream, fmt_tune_entry* out);
+
+/*
+ * fmt_autotune_forest -- the autotuner on the forest a caller is about to
+ * fit (no counterpart in the paper).  A one-degree trial cannot see how the
+ * per-degree tile-QR launches of a level share the GPU, so this one times
+ * the whole level loop (fit_level / refine to the end, after
+ * oct_build_batch) of the given problems -- a sample of the real forest,
+ * e.g. its first few hundred problems -- with the table in force, then
+ * degree by degree (every degree present, largest first) the candidates
+ * warps 4 <-> 8 and rows 32 / 64 / 128 where they fit, each timed on the
+ * same forest, keeping a candidate when the whole loop is more than 2%
+ * faster than the incumbent.  The winners stay installed (source 1);
+ * chunk_factor and merge are left as they are.
+ *   params .. f   as for oct_build_batch (device point arrays).
+ *   report        host or NULL: time of the loop with the table at entry
+ *                 (ms_start) and with the result (ms_best), trials, and the
+ *                 number of entries changed.
+ * Synchronises; allocates through the trees it builds and frees them.  On
+ * an error the table at entry is restored.
+ */
+typedef struct {
+  double ms_start, ms_best;
+  int32_t trials, changed;
+} fmt_tune_report;
+fmt_status fmt_autotune_forest(const fmt_params* params, int64_t n_problems, const int64_t* offsets,
+                               const int32_t* degrees, const double* boxes, const double* x, const double* y,
+                               const double* z, const double* f, void* stream, fmt_tune_report* report);
 fmt_status fmt_tune_get(int32_t degree, fmt_tune_entry* out);
 fmt_status fmt_tune_set(const fmt_tune_entry* entry);
 

@@ -88,6 +88,7 @@ struct QRArgs {
   int only_m;            // tile QR: > 0 takes only the items of nodes with this m
   int* err;              // device error word (a bounded wait that ran out sets FMT_ERR_TIMEOUT)
   int node_mode;         // tile QR: which nodes it takes (launch_tile_qr's mode)
+  const int* work_base;  // the tree's d_work (kPivSlot: the level's small-pivot count)
 };
 
 // A node the mixed path's tensor-core tier left for a small Cholesky pivot:
@@ -95,10 +96,14 @@ struct QRArgs {
 // FMT_FLAG_MIXED_PIVOT and no FMT_FLAG_MIXED_SLOW (the FP64 tier, which
 // runs later, sets the pivot flag only on nodes that were not eligible or
 // did not converge).  These are known right after the factor kernel.
+// Both launches read the level's count of such nodes (kPivSlot, written by
+// the factor kernel) and take the early path only when it is at most
+// kEarlyRefitMax, so they agree on which nodes the early launch takes.
 __device__ __forceinline__ bool early_refit(const QRArgs& a, int64_t node, int32_t f) {
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const bool eligible = pr.degree <= FMT_MIXED_MAX_DEGREE && !(a.depth == 0 && pr.q_root < pr.degree);
-  return eligible && (f & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_SLOW | FMT_FLAG_MIXED_PIVOT)) == FMT_FLAG_MIXED_PIVOT;
+  return eligible && (f & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_SLOW | FMT_FLAG_MIXED_PIVOT)) == FMT_FLAG_MIXED_PIVOT &&
+         a.work_base[kPivSlot] <= kEarlyRefitMax;
 }
 
 __device__ __forceinline__ bool node_done(const QRArgs& a, int64_t node) {
@@ -1448,6 +1453,7 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.only_m = 0;
   a.err = t->d_err;
   a.node_mode = 0;
+  a.work_base = t->d_work;
   return a;
 }
 

@@ -226,7 +226,14 @@ struct fmt_level {
 // Small result block that refine reads back in one copy.
 // work-queue counters per tree: slot 0 for single launches, slot 1 + q for
 // the tile-QR launch of degree q
-constexpr int kWorkSlots = 2 * (FMT_MAX_DEGREE + 1) + 2;  // 0: mixed Gram; 1 + q: tile QR; 16 + q: early refits
+// d_work slots: 0 the mixed Gram's queue; 1 + q the tile QR's; 16 + q the
+// early refits'; kPivSlot the tensor-core tier's small-pivot count of a level
+constexpr int kPivSlot = 2 * (FMT_MAX_DEGREE + 1) + 1;
+constexpr int kWorkSlots = kPivSlot + 1;
+// a level refits its small-pivot nodes early (beside the sweeps) only when
+// there are at most this many: more Householder work than that competes with
+// the sweeps for the SMs
+constexpr int kEarlyRefitMax = 64;
 
 struct fmt_plan_out {
   int64_t n_new, n_items, max_chunks, chunk_rows, n_points, n_near, err;

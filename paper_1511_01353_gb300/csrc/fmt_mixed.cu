@@ -52,6 +52,7 @@ namespace {
 constexpr int kAtom = 64;        // rows per operand tile: one 128-byte swizzle row of BF16
 constexpr int kDrainAtoms = 4;   // FP32 -> FP64 promotion every 256 rows
 constexpr int kFThreads = 256;   // factor / update kernels
+constexpr int kFPanel = 16;      // rows per panel of the factor's Cholesky
 constexpr double kPivotFloor = 1e-6;
 constexpr double kConvergedRel = 1e-7;
 constexpr double kBoxChangeRel = 1e-8;  // remaining change over the node box, relative to max |f| of the problem
@@ -888,24 +889,6 @@ __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
 // One CTA per node.  Shared: the packed upper triangle of the m x m Gram
 // (row i at ro(i), m = nmono + 1 with r last), the initial diagonal, y, F and
 // the change-of-basis scratch.
-// G[i][j] -= rk[i] rk[j] for k < i <= j < m (packed rows): threads form a
-// 16 x 16 grid over the upper tiles of the trailing matrix.
-__device__ __forceinline__ void trailing_update(double* __restrict__ G, const double* __restrict__ rk, int k,
-                                                int m) {
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
-  const int n = m - k - 1;
-  for (int ib = 0; ib < n; ib += 16) {
-    const int i = k + 1 + ib + ti;
-    if (i >= m) break;
-    const double ri = rk[i];
-    double* Gi = G + ro_of(i, m) - i;  // Gi[j] = G[i][j]
-    for (int jb = ib; jb < n; jb += 16) {
-      const int j = k + 1 + jb + tj;
-      if (j >= i && j < m) Gi[j] = fma(-ri, rk[j], Gi[j]);
-    }
-  }
-}
-
 // One warp: R x = y (x overwrites y).
 __device__ void warp_back_solve(const double* __restrict__ R, int m, int L, const double* __restrict__ invd,
                                 double* __restrict__ y) {
@@ -956,42 +939,89 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
     if (gi > gj || gj >= m) continue;
     G[ro_of(gi, m) + (gj - gi)] = a.acc[i0 * a.acc_stride + e];
   }
-  // 2. Cholesky, right-looking, on the packed rows; column L (r) is carried
-  // along.  Thread 0 forms each pivot's square root and reciprocal once (it
-  // updates the next pivot G[k+1][k+1] itself, first in its trailing tile):
-  // FP64 sqrt and divide in every warp cost as much pipe time as the updates.
+  // 2. Cholesky on the packed rows, column L (r) carried along, in panels of
+  // kFPanel rows: within a panel, column by column, thread 0 forms the pivot
+  // (the floor test, one reciprocal square root), the row is scaled and the
+  // panel's later rows are updated; then the trailing triangle (rows and
+  // columns past the panel) takes the panel's rank-kFPanel update at once,
+  // each thread a 4 x 4 register tile (two barriers per panel instead of two
+  // per column, and full-warp FMAs).
   __shared__ double s_rkk, s_irk;
   __shared__ int s_bad;
   auto pivot = [&](int k) {  // thread 0
     const double d = G[ro_of(k, m)], d0 = diag0(k);
     s_bad = !(d0 > 0.0 && d > kPivotFloor * d0);
     if (!s_bad) {
-      s_rkk = sqrt(d);
-      s_irk = 1.0 / s_rkk;
+      const double ir = rsqrt(d);
+      s_irk = ir;
+      s_rkk = d * ir;
     }
   };
   __syncthreads();
-  if (tid == 0 && L > 0) pivot(0);
-  for (int k = 0; k < L; ++k) {
-    __syncthreads();
-    if (s_bad) {  // the same decision in every thread
-      if (tid == 0) a.flags[node] |= FMT_FLAG_MIXED_PIVOT;
-      return;  // the FP64 path refits this node
+  for (int k0 = 0; k0 < L; k0 += kFPanel) {
+    const int k1 = k0 + kFPanel < L ? k0 + kFPanel : L;
+    for (int k = k0; k < k1; ++k) {
+      if (tid == 0) pivot(k);
+      __syncthreads();
+      if (s_bad) {  // the same decision in every thread
+        if (tid == 0) {
+          a.flags[node] |= FMT_FLAG_MIXED_PIVOT;
+          atomicAdd(a.work + kPivSlot, 1);  // the level's count of small-pivot nodes
+        }
+        return;  // the FP64 path refits this node
+      }
+      const double rkk = s_rkk, irk = s_irk;
+      double* Gk = G + ro_of(k, m) - k;  // Gk[j] = G[k][j]
+      for (int j = k + 1 + tid; j < m; j += kFThreads) Gk[j] *= irk;
+      if (tid == 0) invd[k] = irk;
+      __syncthreads();
+      if (tid == 0) Gk[k] = rkk;  // every thread has read the pivot by now
+      // the panel's later rows i in (k, k1): G[i][j] -= R[k][i] R[k][j], j >= i
+      const int w = m - k - 1;
+      for (int e = tid; e < (k1 - k - 1) * w; e += kFThreads) {
+        const int i = k + 1 + e / w, j = k + 1 + e % w;
+        if (j >= i) G[ro_of(i, m) + (j - i)] = fma(-Gk[i], Gk[j], G[ro_of(i, m) + (j - i)]);
+      }
+      __syncthreads();
     }
-    const double rkk = s_rkk, irk = s_irk;
-    double* Gk = G + ro_of(k, m) - k;
-    for (int j = k + 1 + tid; j < m; j += kFThreads) {
-      const double v = Gk[j] * irk;
-      rk[j] = v;
-      Gk[j] = v;
+    // trailing triangle, rows and columns in [k1, m): G[i][j] -= sum_{k in panel} R[k][i] R[k][j]
+    const int n = m - k1, nt = (n + 3) >> 2, ntiles = nt * (nt + 1) / 2;
+    for (int t = tid; t < ntiles; t += kFThreads) {
+      int ta = 0, rem = t;  // tile (ta, tb), tb >= ta, row-major over the upper tiles
+      while (rem >= nt - ta) {
+        rem -= nt - ta;
+        ++ta;
+      }
+      const int tb = ta + rem;
+      const int i0 = k1 + 4 * ta, j0 = k1 + 4 * tb;
+      double acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+      for (int k = k0; k < k1; ++k) {
+        const double* Gk = G + ro_of(k, m) - k;
+        double ri[4], rj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ri[u] = i0 + u < m ? Gk[i0 + u] : 0.0;
+          rj[u] = j0 + u < m ? Gk[j0 + u] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fma(ri[u], rj[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int i = i0 + u, j = j0 + v;
+          if (i < m && j < m && j >= i) G[ro_of(i, m) + (j - i)] -= acc[u][v];
+        }
     }
-    if (tid == 0) invd[k] = irk;
     __syncthreads();
-    if (tid == 0) Gk[k] = rkk;  // every thread has read the pivot by now
-    trailing_update(G, rk, k, m);
-    if (tid == 0 && k + 1 < L) pivot(k + 1);  // thread 0 wrote G[k+1][k+1] in its first tile
   }
-  __syncthreads();
   // 3. R F = y, y = the scaled Q^T r column
   for (int k = tid; k < L; k += kFThreads) Fl[k] = G[ro_of(k, m) + (L - k)];
   __syncthreads();
@@ -1907,7 +1937,9 @@ cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bu
     if (e != cudaSuccess) return e;
   }
   const size_t smem = mixed_factor_smem(mixed_m_cap(L.max_m));
-  cudaError_t e = cudaFuncSetAttribute(k_mfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaMemsetAsync(t->d_work + kPivSlot, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_mfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_mfactor<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(make_margs(t, depth, b));
   return cudaGetLastError();

@@ -186,3 +186,109 @@ extern "C" fmt_status fmt_autotune(int32_t degree, int64_t sample_points, void* 
   if (out) *out = best;
   return FMT_OK;
 }
+
+// ---------------------------------------------------------------- forest tuner
+namespace {
+
+// The level loop of one fit of the forest (after oct_build_batch, which does
+// not depend on the table): fit_level / refine to the end, CUDA events.
+fmt_status time_forest(const fmt_params* P, int64_t np, const int64_t* off, const int32_t* deg, const double* box,
+                       const double* x, const double* y, const double* z, const double* f, cudaStream_t s,
+                       cudaEvent_t ea, cudaEvent_t eb, double* ms) {
+  fmt_tree* t = nullptr;
+  fmt_status st = oct_build_batch(P, np, off, deg, box, x, y, z, f, s, &t);
+  if (st != FMT_OK) return st;
+  cudaEventRecord(ea, s);
+  for (int d = 0; st == FMT_OK; ++d) {
+    if ((st = fit_level(t, d, s)) != FMT_OK) break;
+    int64_t nn = 0;
+    if ((st = refine(t, d, &nn, s)) != FMT_OK || nn == 0) break;
+  }
+  cudaEventRecord(eb, s);
+  const cudaError_t ce = cudaEventSynchronize(eb);
+  float el = 0.0f;
+  if (st == FMT_OK && ce == cudaSuccess) cudaEventElapsedTime(&el, ea, eb);
+  fmt_tree_free(t);
+  if (st != FMT_OK) return st;
+  if (ce != cudaSuccess) return fmt_set_error(FMT_ECUDA, "fmt_autotune_forest: timed fit failed");
+  *ms = el;
+  return FMT_OK;
+}
+
+}  // namespace
+
+extern "C" fmt_status fmt_autotune_forest(const fmt_params* params, int64_t n_problems, const int64_t* offsets,
+                                          const int32_t* degrees, const double* boxes, const double* x,
+                                          const double* y, const double* z, const double* f, void* stream,
+                                          fmt_tune_report* report) {
+  if (!params || n_problems < 1 || !offsets || !x || !y || !z || !f)
+    return fmt_set_error(FMT_EINVAL, "fmt_autotune_forest: NULL argument or n_problems < 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the degrees present, largest first
+  bool present[FMT_MAX_DEGREE + 1] = {};
+  for (int64_t i = 0; i < n_problems; ++i) {
+    const int d = degrees ? degrees[i] : params->degree;
+    if (d < 0 || d > FMT_MAX_DEGREE) return fmt_set_error(FMT_EINVAL, "fmt_autotune_forest: degree outside [0, 14]");
+    present[d] = true;
+  }
+  fmt_tune_entry saved[FMT_MAX_DEGREE + 1];
+  for (int d = 0; d <= FMT_MAX_DEGREE; ++d) saved[d] = tune_current(d);
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess) {
+    cudaGetLastError();
+    if (ea) cudaEventDestroy(ea);
+    return fmt_set_error(FMT_ECUDA, "fmt_autotune_forest: event creation failed");
+  }
+  int trials = 0;
+  double ms0 = 0.0, warm = 0.0;
+  fmt_status st = time_forest(params, n_problems, offsets, degrees, boxes, x, y, z, f, s, ea, eb, &warm);  // warm-up
+  if (st == FMT_OK) st = time_forest(params, n_problems, offsets, degrees, boxes, x, y, z, f, s, ea, eb, &ms0);
+  ++trials;
+  double ms_best = ms0;
+  int changed = 0;
+  for (int d = FMT_MAX_DEGREE; d >= 0 && st == FMT_OK; --d) {
+    if (!present[d]) continue;
+    const int m = fmt_nmono(d) + 1;
+    fmt_tune_entry best = tune_current(d);
+    std::vector<fmt_tune_entry> cand;
+    {
+      fmt_tune_entry e = best;
+      e.warps = best.warps == 4 ? 8 : 4;
+      cand.push_back(e);
+    }
+    for (int rows : {32, 64, 128}) {
+      fmt_tune_entry e = best;
+      e.rows = rows;
+      if (rows != best.rows) cand.push_back(e);
+    }
+    for (fmt_tune_entry e : cand) {
+      if (qr_smem_bytes(m, e.rows) > kQRSmemMax) continue;
+      e.degree = d;
+      e.source = 1;
+      if ((st = tune_install(e)) != FMT_OK) break;
+      double ms = 0.0;
+      st = time_forest(params, n_problems, offsets, degrees, boxes, x, y, z, f, s, ea, eb, &ms);
+      ++trials;
+      if (st != FMT_OK) break;
+      if (ms < 0.98 * ms_best) {  // more than 2% faster: the new incumbent
+        ms_best = ms;
+        best = e;
+        ++changed;
+      }
+      tune_install(best);  // back to the incumbent before the next candidate
+    }
+  }
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  if (st != FMT_OK) {
+    for (int d = 0; d <= FMT_MAX_DEGREE; ++d) tune_install(saved[d]);
+    return st;
+  }
+  if (report) {
+    report->ms_start = ms0;
+    report->ms_best = ms_best;
+    report->trials = trials;
+    report->changed = changed;
+  }
+  return FMT_OK;
+}

@@ -28,6 +28,7 @@ MIXED_MAX_DEGREE = 9
 MIXED_FP64_MAX_DEGREE = 10
 MIXED_MAX_SWEEPS = 3
 FMT_OPT_GRAPH = 1
+FMT_MAX_DEGREE = 14
 MAX_DEPTH = 21
 _STATUS = {0: "FMT_OK", 1: "FMT_EINVAL", 2: "FMT_ENOMEM", 3: "FMT_ECUDA", 4: "FMT_ETIMEOUT", 5: "FMT_EINTERNAL"}
 
@@ -84,7 +85,7 @@ EXPORTED = ["fmt_nmono", "oct_build", "oct_build_batch", "fit_level", "refine", 
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
             "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static", "fmt_server_create",
             "fmt_server_submit", "fmt_server_wait", "fmt_server_destroy", "fmt_server_clock", "fmt_autotune",
-            "fmt_tune_get", "fmt_tune_set", "fmt_debug_fail_alloc", "fmt_wait_probe"]
+            "fmt_tune_get", "fmt_tune_set", "fmt_debug_fail_alloc", "fmt_wait_probe", "fmt_autotune_forest"]
 STATIC_MAX_DEGREE = 8
 PROFILE_CLASSES = 24
 
@@ -98,6 +99,11 @@ class fmt_tune_entry(ctypes.Structure):
 
 TUNE_FIELDS = ("degree", "rows", "warps", "chunk_factor", "merge", "source", "sample_points", "ms", "ms_builtin",
                "trials")
+
+
+class fmt_tune_report(ctypes.Structure):
+    _fields_ = [("ms_start", ctypes.c_double), ("ms_best", ctypes.c_double), ("trials", ctypes.c_int32),
+                ("changed", ctypes.c_int32)]
 
 
 class fmt_profile(ctypes.Structure):
@@ -172,6 +178,8 @@ def load(build: bool = True):
         L.fmt_fit_node_static.restype = ctypes.c_int
         L.fmt_autotune.argtypes = [i32, i64, P, ctypes.POINTER(fmt_tune_entry)]
         L.fmt_autotune.restype = ctypes.c_int
+        L.fmt_autotune_forest.argtypes = [P, i64, P, P, P, P, P, P, P, P, ctypes.POINTER(fmt_tune_report)]
+        L.fmt_autotune_forest.restype = ctypes.c_int
         L.fmt_tune_get.argtypes = [i32, ctypes.POINTER(fmt_tune_entry)]
         L.fmt_tune_get.restype = ctypes.c_int
         L.fmt_tune_set.argtypes = [ctypes.POINTER(fmt_tune_entry)]
@@ -406,6 +414,28 @@ def fmt_autotune(degree: int, sample_points: int = 0, stream=None) -> dict:
     e = fmt_tune_entry()
     _check(load().fmt_autotune(degree, sample_points, _stream_handle(stream), ctypes.byref(e)))
     return _entry_dict(e)
+
+
+def fmt_autotune_forest(params: fmt_params, offsets, x, y, z, f, degrees=None, boxes=None, stream=None) -> dict:
+    """Tune the per-degree QR table on a forest (a sample of the one about to be
+    fitted) by timing its whole level loop (synchronises); returns the report."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64).reshape(-1)
+    if off.shape[0] < 2:
+        raise FmtError(FMT_EINVAL, "offsets needs n_problems + 1 >= 2 entries")
+    n_prob = int(off.shape[0] - 1)
+    deg = None if degrees is None else np.ascontiguousarray(degrees, dtype=np.int32).reshape(-1)
+    box = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1)
+    if deg is not None and deg.shape[0] != n_prob:
+        raise FmtError(FMT_EINVAL, "degrees has %d entries; expected %d" % (deg.shape[0], n_prob))
+    if box is not None and box.shape[0] != 4 * n_prob:
+        raise FmtError(FMT_EINVAL, "boxes has %d values; expected 4 per problem (%d)" % (box.shape[0], 4 * n_prob))
+    px, py, pz, pf = _ptrs(stream, *_f64(int(off[-1]), x=x, y=y, z=z, f=f))
+    rep = fmt_tune_report()
+    _check(load().fmt_autotune_forest(ctypes.byref(params), n_prob, off.ctypes.data_as(ctypes.c_void_p),
+                                      None if deg is None else deg.ctypes.data_as(ctypes.c_void_p),
+                                      None if box is None else box.ctypes.data_as(ctypes.c_void_p),
+                                      px, py, pz, pf, _stream_handle(stream), ctypes.byref(rep)))
+    return {"ms_start": rep.ms_start, "ms_best": rep.ms_best, "trials": int(rep.trials), "changed": int(rep.changed)}
 
 
 def fmt_tune_get(degree: int) -> dict:

@@ -136,3 +136,28 @@ def test_graph_form_of_a_forest_of_several_degrees(precision):
     assert np.array_equal(g.coef, ref.coef)
     assert np.array_equal(g.resid, ref.resid)
     assert np.array_equal(g.flags, ref.flags)
+
+
+def test_forest_tuner_keeps_the_fp64_bar():
+    # The forest autotuner times the whole level loop of a mixed-degree forest
+    # under candidate tables and installs the winners; whatever it picks, the
+    # fit of every problem meets the FP64 bar against the oracle.
+    from paper_1511_01353_gb300 import fmt as F
+    b = W.batch(n_problems=16, n_min=300, n_max=6000, deg_min=3, deg_max=7)
+    p = F.make_params(3, b.max_depth, b.min_pts, b.tol_rel)
+    saved = {d: F.fmt_tune_get(d) for d in range(F.FMT_MAX_DEGREE + 1)}
+    try:
+        rep = F.fmt_autotune_forest(p, b.offsets, dev(b.x), dev(b.y), dev(b.z), dev(b.f), degrees=b.degrees,
+                                    boxes=b.boxes)
+        assert rep["trials"] >= 2 and rep["ms_start"] > 0.0 and rep["ms_best"] <= rep["ms_start"]
+        tree = F.fit_all(F.oct_build_batch(p, b.offsets, dev(b.x), dev(b.y), dev(b.z), dev(b.f),
+                                           degrees=b.degrees, boxes=b.boxes))
+        ex = F.parse_export(F.fmt_tree_export(tree))
+        tree.close()
+        for i in range(b.n_problems):
+            s, e = int(b.offsets[i]), int(b.offsets[i + 1])
+            T = O.fit(b.x[s:e], b.y[s:e], b.z[s:e], b.f[s:e], int(b.degrees[i]), b.max_depth, b.min_pts, b.tol_rel)
+            assert np.max(np.abs(ex.resid[s:e] - T.resid)) <= REL_TOL * T.maxabs
+    finally:
+        for d, e in saved.items():
+            F.fmt_tune_set(dict(e, source=0) if e["source"] == 0 else e)
