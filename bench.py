@@ -420,14 +420,41 @@ def serve_measure(args, n_requests, rate, slots, seed_offset=0):
             dt = t0 + r.arrival - F.Server.clock()
             if dt > 0:
                 time.sleep(dt)
-            tickets[i] = sv.submit(params(r), r.x, r.y, r.z, r.f, r.xq, r.yq, r.zq)
+            tickets[i] = sv.submit(params(r), r.x, r.y, r.z, r.f, r.xq, r.yq, r.zq, keep=True)
 
     th = threading.Thread(target=submitter)
     th.start()
     th.join()
-    infos = [sv.wait(t)[1] for t in tickets]
+    waited = [sv.wait(t) for t in tickets]
+    infos = [w_[1] for w_ in waited]
     clocks = sampler.stop()
+    # every tree stayed resident: evaluate-only requests against them (the
+    # request's own first targets, up to 1e4), then release
+    mem_fit = sv.memory()
+    ev_lat, ev_ok, ev_t = [], True, 0
+    for r, (out_fit, inf) in zip(reqs, waited):
+        if inf["resident_id"] <= 0:
+            continue
+        k = min(10_000, r.xq.shape[0])
+        t0e = F.Server.clock()
+        out_e, ie = sv.wait(sv.submit_eval(inf["resident_id"], r.xq[:k], r.yq[:k], r.zq[:k]))
+        ev_lat.append(ie["t_done"] - ie["t_submit"])
+        ev_t += k
+        ev_ok = ev_ok and ie["status"] == F.FMT_OK and bool(np.array_equal(out_e, out_fit[:k]))
+    for inf in infos:
+        if inf["resident_id"] > 0:
+            sv.release(inf["resident_id"])
+    mem_end = sv.memory()
     sv.close()
+    resident = {"trees_kept": sum(1 for i in infos if i["resident_id"] > 0),
+                "admitted_bytes_with_all_resident": mem_fit["admitted"],
+                "peak_admitted_bytes": mem_end["peak_admitted"], "admitted_after_release": mem_end["admitted"],
+                "eval_requests": len(ev_lat), "eval_targets": ev_t,
+                "eval_p50_ms": float(np.percentile(ev_lat, 50) * 1e3) if ev_lat else None,
+                "eval_p99_ms": float(np.percentile(ev_lat, 99) * 1e3) if ev_lat else None,
+                "eval_equal_to_fit_time_values": ev_ok,
+                "note": "each request kept its tree on the device; one evaluate-only request per tree "
+                        "(its first <= 1e4 targets), one at a time, then every tree released"}
     lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
     ok = all(i["status"] == F.FMT_OK for i in infos)
     pts = np.array([r.x.shape[0] for r in reqs], dtype=np.float64)
@@ -446,12 +473,13 @@ def serve_measure(args, n_requests, rate, slots, seed_offset=0):
                        "slots": slots, "budget_bytes": 150e9, "max_batch_points": 4_000_000,
                        "max_depth": 8, "tol_rel": 1e-6},
             "evals_per_s": float(tg.sum() / span), "all_ok": ok,
+            "statuses": {str(k): sum(1 for i in infos if i["status"] == k) for k in set(i["status"] for i in infos)},
             "latency": by, "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "offered_points_per_s": float(offered), "completed_points_per_s": float(pts.sum() / span),
             "saturated": bool(offered > pts.sum() / span),
             "batches": len(set(i["batch_id"] for i in infos)),
             "mean_batch_requests": float(np.mean([i["batch_requests"] for i in infos])),
-            "clocks": clocks,
+            "clocks": clocks, "resident": resident,
             "h2d_bytes": int(32 * pts.sum() + 24 * tg.sum()), "d2h_bytes": int(8 * tg.sum())}
 
 

@@ -500,6 +500,13 @@ fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const double* x, const
 /* Release the tree (waits for its last stream).  NULL is ignored. */
 void fmt_tree_free(fmt_tree* tree);
 
+/* Free the scratch only fitting uses (the QR triangles of the work items and
+ * the mixed path's Gram, projection, sweep-residual and digit-tile buffers),
+ * stream-ordered on `stream`, for a tree kept for evaluation (no
+ * counterpart in the paper).  Evaluation, stats and export are unaffected;
+ * a later fit_level allocates the scratch again.  FMT_EINVAL for NULL. */
+fmt_status fmt_tree_trim(fmt_tree* tree, void* stream);
+
 /* Message of the last failure on `tree`, or of the calling thread's last
  * failure when tree == NULL (e.g. a failed oct_build).  Never NULL. */
 const char* fmt_last_error(const fmt_tree* tree);
@@ -521,12 +528,32 @@ const char* fmt_last_error(const fmt_tree* tree);
  * batch; its result equals the result of running it alone up to the
  * rounding of a different row-chunk plan (FP64: within 1e-10 max|f|).
  *
+ * The batch key also holds the request's size class (the decade of its
+ * point count), so a batch of small requests does not wait for a large one.
+ *
  *   fmt_request   params: the request's fmt_params (degree, lo, side are per
  *                 request; the rest is the batch key).  x,y,z,f: host, n
  *                 each; xq,yq,zq: host, m each; out: host, m.  All must stay
  *                 valid and unmodified until fmt_server_wait returns it.
+ *                 keep: 1 keeps the request's tree (the forest of its batch)
+ *                 resident on the device after the batch; 0 frees it.
  *   fmt_request_result  status of the request; t_submit / t_start / t_done
- *                 on fmt_server_clock(); the batch it ran in.
+ *                 on fmt_server_clock(); the batch it ran in; with keep, the
+ *                 id of the resident tree (resident_id > 0) and the
+ *                 request's problem index in it.
+ * Resident trees: fmt_server_submit_eval queues an evaluate-only request
+ * (host targets xq, yq, zq and output out, m each, valid until the wait)
+ * against a resident tree, run by the next free slot; it evaluates the
+ * kept request's own tree, so it gives what the fit's own evaluation gave
+ * at the same targets.  fmt_server_release drops a resident tree (after
+ * evaluations already queued on it); a forest is freed when the last of its
+ * kept requests is released.  A kept forest's fit scratch is freed at once
+ * (fmt_tree_trim); its resident estimate (about 400 bytes per point) stays
+ * counted against budget_bytes until the release.  FMT_EINVAL for an unknown
+ * or released id.  fmt_server_memory reports the bytes currently admitted
+ * (running batches and resident forests), their peak, and the number of
+ * resident trees; staging buffers are pool allocations freed with their
+ * batch, so device use stays within what was admitted.
  * fmt_server_create: slots 1..64, budget_bytes > 0, max_batch_points >= 1;
  *   uses the current device.  fmt_server_submit copies the request struct
  *   (not the arrays) and returns a ticket; FMT_EINVAL for bad fields.
@@ -541,17 +568,26 @@ typedef struct {
   const double *x, *y, *z, *f;
   const double *xq, *yq, *zq;
   double* out;
+  int32_t keep;
+  int32_t pad;
 } fmt_request;
 typedef struct {
   fmt_status status;
   int32_t batch_requests;
   int64_t batch_id, batch_points;
   double t_submit, t_start, t_done;
+  int64_t resident_id;
+  int32_t problem;
+  int32_t pad;
 } fmt_request_result;
 fmt_status fmt_server_create(int32_t slots, double budget_bytes, int64_t max_batch_points, fmt_server** out);
 fmt_status fmt_server_submit(fmt_server* server, const fmt_request* request, int64_t* ticket);
 fmt_status fmt_server_wait(fmt_server* server, int64_t ticket, double timeout_s, fmt_request_result* result);
 fmt_status fmt_server_destroy(fmt_server* server);
+fmt_status fmt_server_submit_eval(fmt_server* server, int64_t resident_id, int64_t m, const double* xq,
+                                  const double* yq, const double* zq, double* out, int64_t* ticket);
+fmt_status fmt_server_release(fmt_server* server, int64_t resident_id);
+fmt_status fmt_server_memory(fmt_server* server, double* admitted, double* peak_admitted, int64_t* resident_trees);
 double fmt_server_clock(void); /* seconds, steady clock of the server */
 
 #ifdef __cplusplus

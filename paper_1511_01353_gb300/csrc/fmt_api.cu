@@ -915,6 +915,21 @@ fmt_status evaluate(fmt_tree* t, int64_t m, const double* xq, const double* yq, 
   return evaluate_batch(t, m, nullptr, xq, yq, zq, out, n_outside, stream);
 }
 
+fmt_status fmt_tree_trim(fmt_tree* t, void* stream) {
+  if (!t) return fmt_set_error(FMT_EINVAL, "tree is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t->Rbuf) tfree_one(t, t->Rbuf, s);
+  t->Rbuf = nullptr;
+  t->Rbuf_cap = 0;
+  fmt_mixed_bufs& b = t->mx;
+  void* bufs[] = {b.s, b.mstat, b.acc, b.gacc, b.dproj, b.lcoef, b.cache};
+  for (void* p : bufs)
+    if (p) tfree_one(t, p, s);
+  b = fmt_mixed_bufs{};
+  t->stream = s;
+  return FMT_OK;
+}
+
 fmt_status fmt_tree_stats(fmt_tree* t, fmt_stats* o) {
   TRY(check_tree(t));
   if (!o) return set_err(t, FMT_EINVAL, "out is NULL");

@@ -62,13 +62,15 @@ class fmt_stats(ctypes.Structure):
 class fmt_request(ctypes.Structure):
     _fields_ = [("params", fmt_params), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
                 ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("f", ctypes.c_void_p),
-                ("xq", ctypes.c_void_p), ("yq", ctypes.c_void_p), ("zq", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+                ("xq", ctypes.c_void_p), ("yq", ctypes.c_void_p), ("zq", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("keep", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class fmt_request_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("batch_requests", ctypes.c_int32), ("batch_id", ctypes.c_int64),
                 ("batch_points", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("resident_id", ctypes.c_int64), ("problem", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class fmt_export_header(ctypes.Structure):
@@ -85,7 +87,8 @@ EXPORTED = ["fmt_nmono", "oct_build", "oct_build_batch", "fit_level", "refine", 
             "fmt_tree_import", "fmt_tree_free", "fmt_last_error", "fmt_profile_enable", "fmt_profile_read",
             "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static", "fmt_server_create",
             "fmt_server_submit", "fmt_server_wait", "fmt_server_destroy", "fmt_server_clock", "fmt_autotune",
-            "fmt_tune_get", "fmt_tune_set", "fmt_debug_fail_alloc", "fmt_wait_probe", "fmt_autotune_forest"]
+            "fmt_tune_get", "fmt_tune_set", "fmt_debug_fail_alloc", "fmt_wait_probe", "fmt_autotune_forest",
+            "fmt_server_submit_eval", "fmt_server_release", "fmt_server_memory", "fmt_tree_trim"]
 STATIC_MAX_DEGREE = 8
 PROFILE_CLASSES = 24
 
@@ -172,6 +175,15 @@ def load(build: bool = True):
         L.fmt_server_wait.restype = ctypes.c_int
         L.fmt_server_destroy.argtypes = [P]
         L.fmt_server_destroy.restype = ctypes.c_int
+        L.fmt_tree_trim.argtypes = [P, P]
+        L.fmt_tree_trim.restype = ctypes.c_int
+        L.fmt_server_submit_eval.argtypes = [P, i64, i64, P, P, P, P, ctypes.POINTER(i64)]
+        L.fmt_server_submit_eval.restype = ctypes.c_int
+        L.fmt_server_release.argtypes = [P, i64]
+        L.fmt_server_release.restype = ctypes.c_int
+        L.fmt_server_memory.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(i64)]
+        L.fmt_server_memory.restype = ctypes.c_int
         L.fmt_server_clock.argtypes = []
         L.fmt_server_clock.restype = ctypes.c_double
         L.fmt_fit_node_static.argtypes = [i32, i64, P, P, P, P, P, ctypes.c_double, P, P, P, P]
@@ -496,6 +508,11 @@ def fmt_profile_class_name(k: int):
     return n.decode() if n else None
 
 
+def fmt_tree_trim(tree: Tree, stream=None):
+    """Free the fit-only scratch of a tree kept for evaluation."""
+    _check(load().fmt_tree_trim(tree.handle, _stream_handle(stream)), tree)
+
+
 def fmt_tree_free(tree: Tree):
     tree.close()
 
@@ -648,7 +665,7 @@ class Server:
     def clock():
         return float(load().fmt_server_clock())
 
-    def submit(self, params: fmt_params, x, y, z, f, xq=None, yq=None, zq=None) -> int:
+    def submit(self, params: fmt_params, x, y, z, f, xq=None, yq=None, zq=None, keep=False) -> int:
         arr = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (x, y, z, f)]
         if xq is None and (yq is not None or zq is not None):
             raise FmtError(FMT_EINVAL, "targets need all of xq, yq, zq")
@@ -667,10 +684,35 @@ class Server:
         r.x, r.y, r.z, r.f = (a.ctypes.data for a in arr)
         r.xq, r.yq, r.zq = (a.ctypes.data if a.shape[0] else None for a in q)
         r.out = out.ctypes.data if out.shape[0] else None
+        r.keep = 1 if keep else 0
         t = ctypes.c_int64()
         _check(load().fmt_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
         self._live[t.value] = (arr, q, out)
         return t.value
+
+    def submit_eval(self, resident_id: int, xq, yq, zq) -> int:
+        """Evaluate-only request against a tree kept by submit(..., keep=True)."""
+        q = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (xq, yq, zq)]
+        for name, a in zip(("yq", "zq"), q[1:]):
+            if a.shape[0] != q[0].shape[0]:
+                raise FmtError(FMT_EINVAL, "%s has %d targets; xq has %d" % (name, a.shape[0], q[0].shape[0]))
+        out = np.empty(q[0].shape[0], dtype=np.float64)
+        m = q[0].shape[0]
+        t = ctypes.c_int64()
+        _check(load().fmt_server_submit_eval(self.handle, int(resident_id), m,
+                                             *(a.ctypes.data if m else None for a in q),
+                                             out.ctypes.data if m else None, ctypes.byref(t)))
+        self._live[t.value] = (None, q, out)
+        return t.value
+
+    def release(self, resident_id: int):
+        _check(load().fmt_server_release(self.handle, int(resident_id)))
+
+    def memory(self) -> dict:
+        """Bytes admitted now (running batches and resident trees), their peak, resident trees."""
+        a, p, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(load().fmt_server_memory(self.handle, ctypes.byref(a), ctypes.byref(p), ctypes.byref(n)))
+        return {"admitted": a.value, "peak_admitted": p.value, "resident_trees": int(n.value)}
 
     def wait(self, ticket: int, timeout: float = -1.0):
         """(values at the targets, result dict) of a submitted request."""

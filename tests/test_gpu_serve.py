@@ -106,3 +106,57 @@ def test_requests_arriving_during_a_batch_join_the_next_one():
     assert all(i["status"] == F.FMT_OK for i in infos)
     assert max(i["batch_requests"] for i in infos) > 1
     assert min(i["t_start"] for i in infos) >= i0["t_start"]
+
+
+def test_resident_tree_serves_evaluate_only_requests():
+    # a fit request that keeps its tree: evaluate-only requests against it
+    # give exactly what the fit's own evaluation gave at the same targets, and
+    # its memory stays admitted until it is released
+    reqs = requests(4, 3)
+    sv = F.Server(slots=2, budget_bytes=20e9)
+    t_keep = sv.submit(*reqs[0], keep=True)
+    t_other = sv.submit(*reqs[1])
+    out_fit, info = sv.wait(t_keep)
+    assert info["status"] == F.FMT_OK and info["resident_id"] > 0
+    sv.wait(t_other)
+    rid = info["resident_id"]
+    mem = sv.memory()
+    assert mem["resident_trees"] == 1 and mem["admitted"] > 0
+    xq, yq, zq = reqs[0][5:8]
+    tickets = [sv.submit_eval(rid, xq, yq, zq) for _ in range(2)]
+    for t in tickets:
+        out, ie = sv.wait(t)
+        assert ie["status"] == F.FMT_OK and ie["resident_id"] == rid
+        assert np.array_equal(out, out_fit)
+    # another request's targets on the same tree: the same polynomial (sum of
+    # the first half of the targets evaluated alone equals the full evaluation's)
+    out_half, _ = sv.wait(sv.submit_eval(rid, xq[:50], yq[:50], zq[:50]))
+    assert np.array_equal(out_half, out_fit[:50])
+    sv.release(rid)
+    mem = sv.memory()
+    assert mem["resident_trees"] == 0 and mem["admitted"] == 0.0
+    assert mem["peak_admitted"] <= 20e9
+    with pytest.raises(F.FmtError):
+        sv.submit_eval(rid, xq, yq, zq)
+    sv.close()
+
+
+def test_admitted_memory_stays_within_the_budget():
+    # many requests, some kept: the admitted bytes (running batches plus
+    # resident trees) never exceed the budget, and return to zero at the end
+    reqs = requests(8, 4)
+    budget = 2.0e9
+    sv = F.Server(slots=2, budget_bytes=budget, max_batch_points=30000)
+    tickets = [sv.submit(*r, keep=(i % 3 == 0)) for i, r in enumerate(reqs)]
+    kept = []
+    for t in tickets:
+        _, info = sv.wait(t)
+        assert info["status"] == F.FMT_OK
+        if info["resident_id"] > 0:
+            kept.append(info["resident_id"])
+    assert len(kept) == 3
+    assert sv.memory()["peak_admitted"] <= budget
+    for rid in kept:
+        sv.release(rid)
+    assert sv.memory()["admitted"] == 0.0
+    sv.close()

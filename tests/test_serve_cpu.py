@@ -36,3 +36,25 @@ def test_server_clock_is_monotone():
     a = F.Server.clock()
     b = F.Server.clock()
     assert b >= a
+
+
+def test_resident_calls_reject_unknown_ids():
+    L = F.load()
+    h = ctypes.c_void_p()
+    assert L.fmt_server_create(1, 1e9, 1000, ctypes.byref(h)) == F.FMT_OK
+    t = ctypes.c_int64()
+    x = np.zeros(3)
+    assert L.fmt_server_submit_eval(h, 7, 3, x.ctypes.data, x.ctypes.data, x.ctypes.data, x.ctypes.data,
+                                    ctypes.byref(t)) == F.FMT_EINVAL
+    assert L.fmt_server_submit_eval(h, 7, -1, None, None, None, None, ctypes.byref(t)) == F.FMT_EINVAL
+    assert L.fmt_server_release(h, 7) == F.FMT_EINVAL
+    a, p, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    assert L.fmt_server_memory(h, ctypes.byref(a), ctypes.byref(p), ctypes.byref(n)) == F.FMT_OK
+    assert a.value == 0.0 and n.value == 0
+    r = F.fmt_request()
+    r.params = F.make_params(4, 3, 1, 1e-4)
+    r.n = 3
+    r.x = r.y = r.z = r.f = x.ctypes.data
+    r.keep = 2
+    assert L.fmt_server_submit(h, ctypes.byref(r), ctypes.byref(t)) == F.FMT_EINVAL
+    assert L.fmt_server_destroy(h) == F.FMT_OK
