@@ -39,7 +39,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
 # current kernel on the 3e5-point recipe (profiles/tile_qr_3e5pts_p8.md):
 # 14.86 MB read + 51.45 MB written for 3e5 rows.  Scaled to a full launch by
 # its rows; set to None whenever the kernel changes until it is re-captured.
-TILE_QR_DRAM_BYTES_PER_ROW = None
+TILE_QR_DRAM_BYTES_PER_ROW = (15.191296e6 + 48.828416e6) / 3.0e5
 
 
 def parse_args():
