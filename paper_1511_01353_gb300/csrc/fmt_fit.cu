@@ -1607,7 +1607,10 @@ cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s, in
     a.only_m = several ? mq : 0;
     a.ld_max = ld_for(mq);
     a.work = work;
-    const QRConfig c = qr_config(mq);
+    QRConfig c = qr_config(mq);
+    // the early refits are a few small nodes beside other work: latency-bound
+    // single CTAs, where 8 warps hide more of the FP64 latency than 4
+    if (mode == 1) c.warps = 8;
     const size_t smem = qr_smem_bytes(mq, c.rows);
     int64_t grid = qr_resident_ctas(mq);
     if (grid > n_items) grid = n_items;
