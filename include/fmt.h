@@ -371,7 +371,7 @@ fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream);
  *                 <= 166), 1 always streams it in row blocks.
  * A degree without a tuned or installed entry uses the built-in rule
  * (source 0): the largest of 64/32/16 rows that fits two (64) or one CTA per
- * SM, 4 warps, chunk_factor 4, merge 0.  The configuration changes the order
+ * SM, 4 warps (8 from degree 8 on), chunk_factor 4, merge 0.  The configuration changes the order
  * of floating-point operations, not the method: every configuration meets
  * the same accuracy, and runs with one table are bitwise reproducible.  The
  * tile QR of a level runs one launch per degree present (on side streams,

@@ -1485,7 +1485,10 @@ fmt_tune_entry builtin_entry(int p) {
   fmt_tune_entry e{};
   e.degree = p;
   e.rows = qr_rows_per_block(fmt_nmono_d(p) + 1);
-  e.warps = 4;
+  // 8 warps from degree 8 on: two warps per sub-partition hide more of the
+  // FP64 latency of the owned-column schedule (p = 8: 300 against 305 ms of
+  // tile QR per scale step; the one-degree tuner picks 8 at p = 10 to 12)
+  e.warps = fmt_nmono_d(p) + 1 >= 160 ? 8 : 4;
   e.chunk_factor = 4;
   e.merge = 0;
   e.source = 0;

@@ -86,9 +86,11 @@ def test_struct_layouts_match_c():
 
 def test_tune_table_is_host_only_and_checks_entries():
     # built-in rule: 64-row blocks while two CTAs fit (ld(166) = 180), 32 rows
-    # for degree 14 (ld(681) = 692), 4 warps, chunks of 4 m rows, packed merge
+    # for degree 14 (ld(681) = 692), 4 warps below degree 8 and 8 from it on,
+    # chunks of 4 m rows, packed merge
     e = F.fmt_tune_get(8)
-    assert (e["source"], e["rows"], e["warps"], e["chunk_factor"], e["merge"]) == (0, 64, 4, 4, 0)
+    assert (e["source"], e["rows"], e["warps"], e["chunk_factor"], e["merge"]) == (0, 64, 8, 4, 0)
+    assert F.fmt_tune_get(7)["warps"] == 4
     assert F.fmt_tune_get(14)["rows"] == 32
     F.fmt_tune_set(dict(degree=8, rows=16, warps=8, chunk_factor=2, merge=1))
     try:
