@@ -1498,7 +1498,7 @@ fmt_tune_entry builtin_entry(int p) {
 bool entry_ok(const fmt_tune_entry& e) {
   if (e.degree < 0 || e.degree > FMT_MAX_DEGREE) return false;
   if (e.source == 0) return true;
-  if (e.rows != 16 && e.rows != 32 && e.rows != 64 && e.rows != 128) return false;
+  if (e.rows != 16 && e.rows != 32 && e.rows != 48 && e.rows != 64 && e.rows != 128) return false;
   if (e.warps != 4 && e.warps != 8) return false;
   if (e.chunk_factor != 1 && e.chunk_factor != 2 && e.chunk_factor != 4 && e.chunk_factor != 8 &&
       e.chunk_factor != 16)
@@ -1574,10 +1574,16 @@ QROps ops_for() {
 }
 QROps qr_ops(const QRConfig& c) {
   if (c.warps == 8)
-    return c.rows == 128 ? ops_for<32, 8>() : c.rows == 64 ? ops_for<16, 8>() : c.rows == 32 ? ops_for<8, 8>()
-                                                                                               : ops_for<4, 8>();
-  return c.rows == 128 ? ops_for<32, 4>() : c.rows == 64 ? ops_for<16, 4>() : c.rows == 32 ? ops_for<8, 4>()
-                                                                                           : ops_for<4, 4>();
+    return c.rows == 128  ? ops_for<32, 8>()
+           : c.rows == 64 ? ops_for<16, 8>()
+           : c.rows == 48 ? ops_for<12, 8>()
+           : c.rows == 32 ? ops_for<8, 8>()
+                          : ops_for<4, 8>();
+  return c.rows == 128  ? ops_for<32, 4>()
+         : c.rows == 64 ? ops_for<16, 4>()
+         : c.rows == 48 ? ops_for<12, 4>()
+         : c.rows == 32 ? ops_for<8, 4>()
+                        : ops_for<4, 4>();
 }
 }  // namespace
 

@@ -50,7 +50,8 @@
 namespace {
 
 constexpr int kAtom = 64;        // rows per operand tile: one 128-byte swizzle row of BF16
-constexpr int kDrainAtoms = 4;   // FP32 -> FP64 promotion every 256 rows
+constexpr int kDrainAtoms = 4;   // projection: exact FP32 sums, promoted every 256 rows
+constexpr int kGramDrainAtoms = 8;  // Gram: FP32 sums (not exact anyway) promoted every 512 rows
 constexpr int kFThreads = 256;   // factor / update kernels
 constexpr int kFPanel = 16;      // rows per panel of the factor's Cholesky
 constexpr double kPivotFloor = 1e-6;
@@ -177,6 +178,10 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
 }
 // the shared-memory sources of every committed store have been read
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... of every committed store but the most recent one
+__device__ __forceinline__ void bulk_wait_read_but1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
 // every committed store is complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // load `bytes` into shared memory; the mbarrier's phase completes when they have landed
@@ -491,6 +496,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
   __shared__ uint32_t tmem_slot;
   __shared__ int s_item, s_deg;
   __shared__ uint16_t s_lmn[(FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6];
+  __shared__ uint16_t s_jb[kGenThreads / 32 + 1];  // column range of each generator warp
   __shared__ double s_val[kAtom];
   constexpr int kTiles = 4;  // the four digit tiles of the basis (Gram: plus the r row)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -562,7 +568,24 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           s_lmn[j] = (uint16_t)(l | (mm << 4) | (r << 8));
         }
         gen_bar();
-        if (tid == 0) s_deg = p;
+        if (tid == 0) {
+          // Contiguous column ranges of about equal work per generator warp:
+          // a column costs 4 units (its product and digits), 2 more where
+          // its (l, m) differs from the column before (the x-y product is
+          // formed again), and the r row (the last warp's) 4.
+          constexpr int kW = kGenThreads / 32;
+          int total = 4;
+          for (int j = 0; j < L; ++j) total += 4 + ((j == 0 || (s_lmn[j] & 255) != (s_lmn[j - 1] & 255)) ? 2 : 0);
+          int w = 0, acc = 0;
+          s_jb[0] = 0;
+          for (int j = 0; j < L && w < kW - 1; ++j) {
+            acc += 4 + ((j == 0 || (s_lmn[j] & 255) != (s_lmn[j - 1] & 255)) ? 2 : 0);
+            if (acc * kW >= total * (w + 1)) s_jb[++w] = (uint16_t)(j + 1);
+          }
+          while (w < kW) s_jb[++w] = (uint16_t)L;
+          s_deg = p;
+        }
+        gen_bar();
       }
       const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
       // projection: |s| scaled below 1 by a power of two (max |s| of the node, this sweep)
@@ -585,7 +608,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           ok = mbar_wait(&mbar[st], (ncommit[st] - 1u) & 1u);
           pending[st] = false;
         }
-        if (cmode == 1 && tid == 0) bulk_wait_read();  // the stage's previous store has read it
+        // the stage's previous store (two atoms back with two stages) has read
+        // it; the store of the other stage, one atom back, may still be reading
+        if (cmode == 1 && tid == 0) {
+          if (nst > 1)
+            bulk_wait_read_but1();
+          else
+            bulk_wait_read();
+        }
         if (gen_bar_or(!ok)) {
           ok = false;
           break;
@@ -639,9 +669,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           const float4* qx = reinterpret_cast<const float4*>(legd + kp);
           const float4* qy = reinterpret_cast<const float4*>(legd + P1 * kAtom + kp);
           const float4* qz = reinterpret_cast<const float4*>(legd + 2 * P1 * kAtom + kp);
-          constexpr int kWarps = kGenThreads / 32;
-          const int per = (L + kWarps - 1) / kWarps;
-          const int jb = warp * per, je = jb + per < L ? jb + per : L;
+          const int jb = s_jb[warp], je = s_jb[warp + 1];
           int plm_key = -1;
           dfl pa = {0.0f, 0.0f}, pb = {0.0f, 0.0f};
           for (int j = jb; j < je; ++j) {
@@ -704,7 +732,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
         pending[st] = true;
         stage = (stage + 1) % nst;
         ++since;
-        if (since == kDrainAtoms || at == natoms - 1) {
+        if (since == (kProj ? kDrainAtoms : kGramDrainAtoms) || at == natoms - 1) {
           for (int s2 = 0; s2 < 2; ++s2)
             if (pending[s2]) {
               ok = mbar_wait(&mbar[s2], (ncommit[s2] - 1u) & 1u) && ok;
@@ -717,12 +745,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           tc_fence_after();
           const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16);
           if (!kProj) {
-            // warps 0..11: three per lane group, every third 16-column chunk
-            if (warp < 12) {
+            // the first 4 kDrainGroups generator warps: kDrainGroups per lane
+            // group, every kDrainGroups-th 16-column chunk
+            constexpr int kDrainGroups = (kGenThreads / 32) / 4;
+            if (warp < 4 * kDrainGroups) {
               // double-float running sums on the FP32 pipe (k_mreduce turns them into FP64)
               const int ncols = band1 ? N0 + (Lp - 128) : N0;
               float2* acc2 = reinterpret_cast<float2*>(acc);
-              for (int c0 = 16 * (warp >> 2); c0 < ncols; c0 += 48) {
+              for (int c0 = 16 * (warp >> 2); c0 < ncols; c0 += 16 * kDrainGroups) {
                 float vv[16];
                 tc_ld16(trow + (uint32_t)c0, vv);
                 float2* dst = acc2 + (int64_t)c0 * 128 + trow_lane;
