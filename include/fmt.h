@@ -359,7 +359,7 @@ fmt_status fmt_probe_dfma(int64_t iters, double* dfma_per_s, void* stream);
  * configuration of the QR of fit_level (Alg. 2 per node, chunks reduced
  * pairwise):
  *   rows          rows of [Lambda | r] absorbed per shared-memory block:
- *                 16, 32, 64 or 128, and (rows + 2) * ld * 8 + 32 bytes must fit
+ *                 16, 32, 48, 64 or 128, and (rows + 2) * ld * 8 + 32 bytes must fit
  *                 in 227 KB, ld = the padded row pitch of nmono(p) + 1 columns;
  *   warps         warps per tile-QR CTA: 4 or 8;
  *   chunk_factor  smallest row chunk (one work item of the persistent queue)

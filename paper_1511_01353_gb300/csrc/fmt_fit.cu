@@ -1968,7 +1968,7 @@ extern "C" fmt_status fmt_tune_set(const fmt_tune_entry* entry) {
   if (!entry) return fmt_set_error(FMT_EINVAL, "fmt_tune_set: NULL entry");
   if (tune_install(*entry) != FMT_OK)
     return fmt_set_error(FMT_EINVAL,
-                         "fmt_tune_set: bad entry (degree 0..14, rows 16/32/64/128 within 227 KB of shared memory, "
+                         "fmt_tune_set: bad entry (degree 0..14, rows 16/32/48/64/128 within 227 KB of shared memory, "
                          "warps 4/8, chunk_factor 1/2/4/8/16, merge 0/1)");
   return FMT_OK;
 }

@@ -150,7 +150,7 @@ extern "C" fmt_status fmt_autotune(int32_t degree, int64_t sample_points, void* 
     }
   };
   // rows x warps, then the chunk factor, then the merge kernel
-  for (int rows : {16, 32, 64, 128})
+  for (int rows : {16, 32, 48, 64, 128})
     for (int warps : {4, 8}) {
       fmt_tune_entry e = best;
       e.rows = rows;

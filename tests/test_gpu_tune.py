@@ -49,7 +49,7 @@ def eval_tree(tree, w):
     return out.cpu().numpy()
 
 
-CONFIGS = [(rows, warps, cf, merge) for rows in (16, 32, 64, 128) for warps in (4, 8)
+CONFIGS = [(rows, warps, cf, merge) for rows in (16, 32, 48, 64, 128) for warps in (4, 8)
            for cf, merge in ((1, 0), (16, 1))]
 
 
