@@ -98,7 +98,7 @@ def test_tune_table_is_host_only_and_checks_entries():
         assert (g["source"], g["rows"], g["warps"], g["chunk_factor"], g["merge"]) == (2, 16, 8, 2, 1)
         assert F.fmt_tune_get(7)["source"] == 0  # other degrees untouched
         good = dict(degree=8, rows=32, warps=4, chunk_factor=4, merge=0)
-        for k, v in (("rows", 48), ("warps", 6), ("chunk_factor", 3), ("merge", 2), ("degree", 15),
+        for k, v in (("rows", 40), ("warps", 6), ("chunk_factor", 3), ("merge", 2), ("degree", 15),
                      ("degree", -1)):
             with pytest.raises(F.FmtError):
                 F.fmt_tune_set(dict(good, **{k: v}))
