@@ -457,6 +457,35 @@ fmt_status fmt_debug_fail_alloc(int64_t k);
 fmt_status fmt_wait_probe(int64_t limit_ns, void* stream);
 
 /*
+ * Bounds-checked build.  Compiled with -DFMT_CHECKED, every kernel tests the
+ * indices it reads from device memory (a work item's node, rows and scratch
+ * slot; a node's problem, points, items and coefficient slot; a parent found
+ * by search; a sort position) against the sizes of the buffers it addresses,
+ * before any access through them.  A failed test skips the guarded work and
+ * records where it failed; oct_build, oct_build_batch, fit_level, refine,
+ * evaluate(_batch), fmt_tree_import and fmt_fit_node_static then synchronise
+ * the device and return FMT_EINTERNAL, fmt_last_error naming the first failed
+ * site.  (While the stream is being captured into a graph nothing has run
+ * yet, and nothing is read.)  The default build compiles the tests out.
+ * fmt_checked_build(): 1 for the checked build, else 0.
+ * fmt_check_probe(i, n): the mechanism's self-test.  One thread writes
+ * element i (0 <= i < 64) of a 64-element device array when the checked
+ * build's test i < n (0 <= n <= 32) passes; the default build writes it
+ * unconditionally (always inside the array).  The checked build returns
+ * FMT_EINTERNAL for i >= n, else FMT_OK; the default build FMT_OK.
+ * Synchronises.  FMT_EINVAL for i or n outside those ranges.
+ * fmt_debug_item_rows(tree, depth, item, start, end): test hook that sets
+ * the row range of one work item of a planned, not yet fitted level, with
+ * 0 <= start <= end <= n (FMT_EINVAL otherwise), so that every access stays
+ * inside the point arrays; a range outside the item's node is what the
+ * checked build's tests report at the next fit_level.
+ */
+int32_t fmt_checked_build(void);
+fmt_status fmt_check_probe(int32_t i, int32_t n, void* stream);
+fmt_status fmt_debug_item_rows(fmt_tree* tree, int32_t depth, int64_t item, int64_t start, int64_t end,
+                               void* stream);
+
+/*
  * fmt_fit_node_static -- allocation-free least-squares fit of ONE point set.
  * The paper has no counterpart: this exists for callers that cannot let a
  * library allocate device memory -- code whose device memory is owned by

@@ -2,7 +2,9 @@
 
 Each .cu under csrc/ is compiled in parallel, then linked into a shared
 library next to this file.  Rebuilds only when a source or header is newer
-than the library.
+than the library.  build_checked() makes libfmt_checked.so, the same sources
+with -DFMT_CHECKED: every kernel tests the indices it reads from device
+memory against the sizes of the buffers they address (include/fmt.h).
 """
 from __future__ import annotations
 
@@ -17,6 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfmt.so")
+LIB_CHECKED = os.path.join(HERE, "libfmt_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -26,10 +29,10 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -40,11 +43,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return compile_library(LIB, BUILD, verbose=verbose)
 
 
-def compile_library(lib: str, objdir: str, host_flags=(), verbose: bool = False) -> str:
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    if not force and not _stale(LIB_CHECKED):
+        return LIB_CHECKED
+    return compile_library(LIB_CHECKED, os.path.join(BUILD, "checked"), defines=("FMT_CHECKED",), verbose=verbose)
+
+
+def compile_library(lib: str, objdir: str, host_flags=(), defines=(), verbose: bool = False) -> str:
     """Compile every csrc/*.cu in parallel into objdir and link them into lib.
     host_flags go to the host compiler of each object and of the link (the
-    sanitizer test builds an ASan/UBSan variant this way)."""
-    xhost = [a for f in host_flags for a in ("-Xcompiler", f)]
+    sanitizer test builds an ASan/UBSan variant this way); defines are
+    preprocessor macros of every object (FMT_CHECKED)."""
+    xhost = [a for f in host_flags for a in ("-Xcompiler", f)] + ["-D" + d for d in defines]
     os.makedirs(objdir, exist_ok=True)
     procs = []
     objs = []
@@ -73,5 +83,7 @@ def compile_library(lib: str, objdir: str, host_flags=(), verbose: bool = False)
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
-    print(LIB)
+    if "--checked" in sys.argv:
+        print(build_checked(force="--force" in sys.argv, verbose=True))
+    else:
+        print(build(force="--force" in sys.argv, verbose=True))

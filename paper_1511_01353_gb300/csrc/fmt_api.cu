@@ -534,6 +534,10 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
   tfree_one(t, temp, s);
   tfree_one(t, vout == vals ? (void*)vals_alt : (void*)vals, s);
   tfree_one(t, d_maxbits, s);
+  if (check_end(t, s) != FMT_OK) {
+    set_err(nullptr, FMT_EINTERNAL, "%s", t->msg);
+    return fail(FMT_EINTERNAL);
+  }
   *out = t;
   return FMT_OK;
 }
@@ -776,6 +780,57 @@ fmt_status fit_level_graph(fmt_tree* t, int depth, cudaStream_t s) {
 
 }  // namespace
 
+const char* check_site_name(int site) {
+  static const char* const kNames[CK_SITES] = {
+      "none",
+      "build (k_morton, k_radix_scatter, k_gather): point index",
+      "plan (k_plan_root, k_refine): node problem or rows",
+      "tile QR (k_tile_qr): work item",
+      "merge (k_merge, k_merge_cl, k_combine): item pair",
+      "back substitution (k_backsolve): node",
+      "residual (k_residual): work item",
+      "child statistics (k_child_bounds, k_child_sums): rows",
+      "mixed path per item (k_mbox, k_mgram, k_msresid, k_dgram, k_dproj)",
+      "mixed path per node (k_mreduce, k_mfactor, k_mupdate, k_dfactor, k_dupdate)",
+      "evaluation (k_evaluate): node degree",
+      "cumulative polynomials (k_make_cum, k_make_hcoef): node",
+      "allocation-free fit (k_fit_node_static): degree or size",
+      "fmt_check_probe: index outside [0, n)"};
+  return site > 0 && site < CK_SITES ? kNames[site] : "unknown site";
+}
+
+// Checked build: wait for the call's work (every stream of the tree), read
+// every translation unit's check word and report the first failed site.
+// While s is being captured nothing has run yet, and nothing is read.
+fmt_status check_end(fmt_tree* t, cudaStream_t s) {
+#ifdef FMT_CHECKED
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return FMT_OK;
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_err(t, FMT_ECUDA, "synchronise: %s", cudaGetErrorString(e));
+  // each translation unit keeps its first failed site; all of them are named
+  int (*const readers[])() = {check_site_build, check_site_plan, check_site_fit, check_site_mixed};
+  int sites[4], n_failed = 0;
+  for (auto rd : readers) {
+    const int v = rd();
+    if (v < 0) return set_err(t, FMT_ECUDA, "reading a bounds-check word failed");
+    if (v > 0) sites[n_failed++] = v;
+  }
+  if (n_failed == 1) return set_err(t, FMT_EINTERNAL, "bounds check failed: %s", check_site_name(sites[0]));
+  if (n_failed > 1) {
+    char buf[256];
+    int o = snprintf(buf, sizeof(buf), "bounds checks failed:");
+    for (int i = 0; i < n_failed && o < (int)sizeof(buf); ++i)
+      o += snprintf(buf + o, sizeof(buf) - o, "%s %s", i ? ";" : "", check_site_name(sites[i]));
+    return set_err(t, FMT_EINTERNAL, "%s", buf);
+  }
+#else
+  (void)t;
+  (void)s;
+#endif
+  return FMT_OK;
+}
+
 // error reporting for entry points defined in other translation units
 fmt_status fmt_set_error(fmt_status st, const char* msg) { return set_err(nullptr, st, "%s", msg); }
 
@@ -828,7 +883,7 @@ fmt_status fit_level(fmt_tree* t, int32_t depth, void* stream) {
   L.fitted = true;
   t->next_fit = -1;
   t->next_refine = depth;
-  return FMT_OK;
+  return check_end(t, s);
 }
 
 fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream) {
@@ -861,7 +916,7 @@ fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream
   t->next_refine = -1;
   if (!deep_ok || pl.n_new <= 0) {
     t->done = 1;
-    return FMT_OK;
+    return check_end(t, s);
   }
   fmt_level& N = t->lv[depth + 1];
   N.n_nodes = pl.n_new;
@@ -878,7 +933,7 @@ fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream
   t->n_levels = depth + 2;
   t->next_fit = depth + 1;
   *n_new_nodes = pl.n_new;
-  return FMT_OK;
+  return check_end(t, s);
 }
 
 fmt_status evaluate_batch(fmt_tree* t, int64_t m, const int32_t* target_problem, const double* xq,
@@ -907,7 +962,7 @@ fmt_status evaluate_batch(fmt_tree* t, int64_t m, const int32_t* target_problem,
     if (*t->h_err & FMT_ERR_INDEX) return set_err(t, FMT_EINVAL, "target problem index out of range");
     *n_outside = (int64_t)h;
   }
-  return FMT_OK;
+  return check_end(t, s);
 }
 
 fmt_status evaluate(fmt_tree* t, int64_t m, const double* xq, const double* yq, const double* zq, double* out,
@@ -1289,6 +1344,11 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
     destroy(t);
     return set_err(nullptr, FMT_ECUDA, "synchronise: %s", cudaGetErrorString(e));
   }
+  if (check_end(t, s) != FMT_OK) {
+    set_err(nullptr, FMT_EINTERNAL, "%s", t->msg);
+    destroy(t);
+    return FMT_EINTERNAL;
+  }
   *out = t;
   return FMT_OK;
 }
@@ -1392,5 +1452,41 @@ extern "C" fmt_status fmt_wait_probe(int64_t limit_ns, void* stream) {
   if (e != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "fmt_wait_probe: %s", cudaGetErrorString(e));
   if (h_err & FMT_ERR_TIMEOUT)
     return set_err(nullptr, FMT_ETIMEOUT, "bounded mbarrier wait ran out after %lld ns", (long long)limit_ns);
+  return FMT_OK;
+}
+
+extern "C" int32_t fmt_checked_build(void) {
+#ifdef FMT_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+extern "C" fmt_status fmt_check_probe(int32_t i, int32_t n, void* stream) {
+  if (i < 0 || i >= 64 || n < 0 || n > 32)
+    return set_err(nullptr, FMT_EINVAL, "fmt_check_probe: i outside [0, 64) or n outside [0, 32]");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_check_probe(i, n, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_err(nullptr, FMT_ECUDA, "fmt_check_probe: %s", cudaGetErrorString(e));
+  return check_end(nullptr, s);
+}
+
+extern "C" fmt_status fmt_debug_item_rows(fmt_tree* t, int32_t depth, int64_t item, int64_t start, int64_t end,
+                                          void* stream) {
+  TRY(check_tree(t));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t->imported || t->done || depth != t->next_fit)
+    return set_err(t, FMT_EINVAL, "fmt_debug_item_rows: depth %d is not the planned level awaiting its fit", depth);
+  const fmt_level& L = t->lv[depth];
+  if (item < 0 || item >= L.n_items) return set_err(t, FMT_EINVAL, "fmt_debug_item_rows: item out of range");
+  if (start < 0 || start > end || end > t->n)
+    return set_err(t, FMT_EINVAL, "fmt_debug_item_rows: rows outside [0, n]");
+  const int64_t v[2] = {start, end};
+  cudaError_t e = cudaMemcpyAsync(L.item_start + item, &v[0], sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(L.item_end + item, &v[1], sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // v lives on this stack
+  if (e != cudaSuccess) return set_err(t, FMT_ECUDA, "fmt_debug_item_rows: %s", cudaGetErrorString(e));
   return FMT_OK;
 }

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256) k_morton(int64_t n, const double* __restr
                                                 int sort_bits, K* __restrict__ keys, uint32_t* __restrict__ vals) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int p = P > 1 ? problem_of_point(prob, P, i) : 0;
+    if (!FMT_CHECK(fmt_in(p, P), CK_BUILD_INDEX)) continue;
     const fmt_problem& pr = prob[p];
     const uint64_t code = fmt_spread3(fmt_quant(x[i], pr.lo[0], pr.S)) |
                           (fmt_spread3(fmt_quant(y[i], pr.lo[1], pr.S)) << 1) |
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
       run[tid] = acc;
     }
     __syncthreads();
-    if (valid) {
+    if (valid && FMT_CHECK((int64_t)gofs[d] + cnt[warp][d] + rank < n, CK_BUILD_INDEX)) {
       uint32_t pos = gofs[d] + cnt[warp][d] + rank;
       okeys[pos] = key;
       ovals[pos] = vals[i];
@@ -209,8 +210,10 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* __res
                                                 uint64_t* __restrict__ code) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t j = perm[i];
+    const int p = P > 1 ? problem_of_point(prob, P, i) : 0;
+    if (!FMT_CHECK((int64_t)j < n && fmt_in(p, P), CK_BUILD_INDEX)) continue;
     const double a = x[j], b = y[j], c = z[j];
-    const fmt_problem& pr = prob[P > 1 ? problem_of_point(prob, P, i) : 0];
+    const fmt_problem& pr = prob[p];
     xs[i] = a;
     ys[i] = b;
     zs[i] = c;
@@ -308,3 +311,7 @@ cudaError_t launch_gather(int64_t n, const uint32_t* perm, const double* x, cons
   k_gather<<<grid_for(n, 256), 256, 0, s>>>(n, perm, x, y, z, f, prob, P, xs, ys, zs, rs, code);
   return cudaGetLastError();
 }
+
+#ifdef FMT_CHECKED
+FMT_CHECK_READER(check_site_build)
+#endif

@@ -89,7 +89,39 @@ struct QRArgs {
   int* err;              // device error word (a bounded wait that ran out sets FMT_ERR_TIMEOUT)
   int node_mode;         // tile QR: which nodes it takes (launch_tile_qr's mode)
   const int* work_base;  // the tree's d_work (kPivSlot: the level's small-pivot count)
+  const int64_t* node_start;  // the level's node point ranges (checked build)
+  const int64_t* node_count;
+  fmt_bounds bd;
 };
+
+#ifdef FMT_CHECKED
+__device__ __forceinline__ bool qr_item_ok(const QRArgs& a, int64_t item);
+// Checked build: the second item of a merge pair is a valid item of the same node.
+__device__ __forceinline__ bool merge_pair_ok(const QRArgs& a, int64_t item, int step) {
+  return qr_item_ok(a, item + step) && a.item_node[item + step] == a.item_node[item];
+}
+// the node's m (its problem and degree already checked)
+__device__ __forceinline__ int geo_m_of(const QRArgs& a, int64_t node) {
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  return fmt_nmono_d(a.depth == 0 ? pr.q_root : pr.degree) + 1;
+}
+
+// Checked build: the item's node, problem, degree, rows (inside its node's,
+// inside the points) and m x m triangle (inside the level's QR scratch).
+__device__ __forceinline__ bool qr_item_ok(const QRArgs& a, int64_t item) {
+  if (!fmt_in(item, a.bd.n_items)) return false;
+  const int64_t node = a.item_node[item];
+  if (!fmt_in(node, a.bd.n_nodes) || !fmt_in(a.node_prob[node], a.bd.n_problems)) return false;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const int q = a.depth == 0 ? pr.q_root : pr.degree;
+  if (pr.degree > FMT_MAX_DEGREE || q < 0 || q > pr.degree) return false;
+  const int64_t m = fmt_nmono_d(q) + 1, ro = a.item_roff[item];
+  if (m > a.bd.max_m || ro < 0 || ro + m * m > a.bd.r_cap) return false;
+  const int64_t s = a.node_start[node], e = s + a.node_count[node];
+  const int64_t rs = a.item_start[item], re = a.item_end[item];
+  return 0 <= s && s <= rs && rs <= re && re <= e && e <= a.bd.n_points;
+}
+#endif
 
 // A node the mixed path's tensor-core tier left for a small Cholesky pivot:
 // eligible for that tier (degree <= FMT_MIXED_MAX_DEGREE, not a clamped root),
@@ -559,11 +591,13 @@ __global__ void __launch_bounds__(32 * NW, NW >= 8 ? 2 : 1) k_tile_qr(QRArgs a) 
     __syncthreads();
     if (it >= a.n_items) break;
     const int item = a.sched[it];
+    if (!FMT_CHECK(qr_item_ok(a, item), CK_QR_ITEM)) continue;
     const int64_t node = a.item_node[item];
     if (node_done(a, node)) continue;
     const int64_t rs = a.item_start[item], re = a.item_end[item];
     const NodeGeom g = node_geom(a, node);
     if (a.only_m > 0 && g.m != a.only_m) continue;  // another degree's launch takes it
+    if (!FMT_CHECK(g.ldB <= a.ld_max, CK_QR_ITEM)) continue;
     const int m = g.m, q = g.q, ldB = g.ldB;
     double* R = a.R + a.item_roff[item];
     if (threadIdx.x == 0 && s_own_m != m) {  // the items of a launch share m except a clamped root
@@ -628,11 +662,13 @@ __global__ void __launch_bounds__(32 * kCombineWarps) k_combine(QRArgs a, int le
   double* Rs = smem + NB * a.ld_max;
   double* sc = Rs + 2 * a.ld_max;
   const int item = blockIdx.x;
+  if (!FMT_CHECK(qr_item_ok(a, item), CK_MERGE_ITEM)) return;
   const int s = a.item_local[item];
   const int64_t node = a.item_node[item];
   const int cnt = a.node_nitems[node];
   const int step = 1 << level;
   if ((s & (2 * step - 1)) != 0 || s + step >= cnt || node_done(a, node)) return;
+  if (!FMT_CHECK(merge_pair_ok(a, item, step), CK_MERGE_ITEM)) return;
   const NodeGeom g = node_geom(a, node);
   const int m = g.m;
   double* Ra = a.R + a.item_roff[item];
@@ -665,10 +701,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
   extern __shared__ double smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, rg = tid & 3;
   const int item = blockIdx.x;
+  if (!FMT_CHECK(qr_item_ok(a, item), CK_MERGE_ITEM)) return;
   const int sidx = a.item_local[item];
   const int cnt = a.node_nitems[a.item_node[item]];
   const int step = 1 << level;
   if ((sidx & (2 * step - 1)) != 0 || sidx + step >= cnt || node_done(a, a.item_node[item])) return;
+  if (!FMT_CHECK(merge_pair_ok(a, item, step), CK_MERGE_ITEM)) return;
   const NodeGeom g = node_geom(a, a.item_node[item]);
   const int m = g.m;
   double* Ra = a.R + a.item_roff[item];
@@ -904,12 +942,14 @@ __global__ void __launch_bounds__(32 * kMCWarps) k_merge_cl(QRArgs a, int level)
   cg::cluster_group cl = cg::this_cluster();
   const int rank = C > 1 ? (int)cl.block_rank() : 0;
   const int item = (int)(blockIdx.x / C);
+  // every CTA of a cluster takes the same decisions
+  if (!FMT_CHECK(qr_item_ok(a, item), CK_MERGE_ITEM)) return;
   const int sidx = a.item_local[item];
   const int64_t node = a.item_node[item];
   const int cnt = a.node_nitems[node];
   const int step = 1 << level;
-  // every CTA of a cluster takes the same decision
   if ((sidx & (2 * step - 1)) != 0 || sidx + step >= cnt || node_done(a, node)) return;
+  if (!FMT_CHECK(merge_pair_ok(a, item, step) && geo_m_of(a, node) <= kMCMaxM, CK_MERGE_ITEM)) return;
   const NodeGeom geo = node_geom(a, node);
   const int m = geo.m;
   double* Ra = a.R + a.item_roff[item];
@@ -1151,6 +1191,8 @@ struct BSArgs {
   double* hcoef;
   int32_t* flags;
   int32_t* deg_used;
+  int64_t n_items;
+  fmt_bounds bd;
 };
 
 __device__ __forceinline__ int tri2(int k) { return (k + 1) * (k + 2) / 2; }
@@ -1282,12 +1324,29 @@ __device__ int backsolve_warp(double* __restrict__ R, int m, int q, int p, int n
 
 __host__ __device__ inline int backsolve_ws_doubles(int L) { return 3 * L + (L + 1) / 2 + 1; }
 
+#ifdef FMT_CHECKED
+// Checked build: the node's problem and degree, its first item's triangle
+// inside the QR scratch, its coefficients inside the node's slot and its m
+// within the workspace the launch sized.
+__device__ __forceinline__ bool backsolve_node_ok(const BSArgs& a, int64_t node) {
+  if (!fmt_in(a.node_prob[node], a.bd.n_problems)) return false;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const int q = a.depth == 0 ? pr.q_root : pr.degree;
+  if (pr.degree > FMT_MAX_DEGREE || q < 0 || q > pr.degree || fmt_nmono_d(pr.degree) > a.stride) return false;
+  const int64_t m = fmt_nmono_d(q) + 1, i0 = a.node_item0[node];
+  if (m > a.bd.max_m || !fmt_in(i0, a.bd.n_items)) return false;
+  const int64_t ro = a.item_roff[i0];
+  return ro >= 0 && ro + m * m <= a.bd.r_cap;
+}
+#endif
+
 __global__ void __launch_bounds__(128) k_backsolve(BSArgs a) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t node = (int64_t)blockIdx.x * 4 + wib;
   if (node >= a.n_nodes) return;
   if (a.flags[node] & FMT_FLAG_MIXED) return;  // fitted by the mixed path
+  if (!FMT_CHECK(backsolve_node_ok(a, node), CK_BACKSOLVE_NODE)) return;  // one warp per node
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const int p = pr.degree;
   const int q = a.depth == 0 ? pr.q_root : p;
@@ -1322,10 +1381,28 @@ struct ResArgs {
   double* r;
   const double* hcoef;
   int depth, stride;
+  const int64_t* node_start;  // checked build
+  const int64_t* node_count;
+  fmt_bounds bd;
 };
+
+#ifdef FMT_CHECKED
+// Checked build: the item's node, problem and degree, and its rows inside
+// its node's inside the points.
+__device__ __forceinline__ bool residual_item_ok(const ResArgs& a, int64_t item) {
+  const int64_t node = a.item_node[item];
+  if (!fmt_in(node, a.bd.n_nodes) || !fmt_in(a.node_prob[node], a.bd.n_problems)) return false;
+  const int p = a.prob[a.node_prob[node]].degree;
+  if (p < 0 || p > FMT_MAX_DEGREE || fmt_nmono_d(p) > a.stride) return false;
+  const int64_t s = a.node_start[node], e = s + a.node_count[node];
+  const int64_t rs = a.item_start[item], re = a.item_end[item];
+  return 0 <= s && s <= rs && rs <= re && re <= e && e <= a.bd.n_points;
+}
+#endif
 
 __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   const int item = blockIdx.x;
+  if (!FMT_CHECK(residual_item_ok(a, item), CK_RESIDUAL_ITEM)) return;
   const int64_t node = a.item_node[item];
   const int64_t rs = a.item_start[item], re = a.item_end[item];
   const fmt_problem& pr = a.prob[a.node_prob[node]];
@@ -1355,6 +1432,7 @@ struct ChildArgs {
   int64_t* child_n;
   int shift;  // 3*(21-depth-1); < 0 when the node has no child level
   int depth;
+  fmt_bounds bd;
 };
 
 __global__ void __launch_bounds__(256) k_child_bounds(ChildArgs a) {
@@ -1363,6 +1441,7 @@ __global__ void __launch_bounds__(256) k_child_bounds(ChildArgs a) {
   const int64_t node = gid / 9;
   const int o = (int)(gid - node * 9);
   const int64_t s = a.start[node], e = s + a.count[node];
+  if (!FMT_CHECK(0 <= s && s <= e && e <= a.bd.n_points, CK_CHILD_NODE)) return;
   int64_t b;
   if (a.shift < 0) {
     b = s;  // no octants below the deepest code level
@@ -1388,6 +1467,7 @@ __global__ void __launch_bounds__(128) k_child_sums(ChildArgs a) {
   const int64_t node = blockIdx.x >> 3;
   const int o = blockIdx.x & 7;
   const int64_t b0 = a.bounds[node * 9 + o], b1 = a.bounds[node * 9 + o + 1];
+  if (!FMT_CHECK(0 <= b0 && b0 <= b1 && b1 <= a.bd.n_points, CK_CHILD_NODE)) return;  // uniform over the CTA
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int64_t i = b0 + threadIdx.x;
   for (; i + 3 * 128 < b1; i += 4 * 128) {
@@ -1454,6 +1534,9 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.err = t->d_err;
   a.node_mode = 0;
   a.work_base = t->d_work;
+  a.node_start = L.start;
+  a.node_count = L.count;
+  a.bd = level_bounds(t, depth);
   return a;
 }
 
@@ -1698,6 +1781,8 @@ cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream
   a.hcoef = L.hcoef;
   a.flags = L.flags;
   a.deg_used = L.deg_used;
+  a.n_items = L.n_items;
+  a.bd = level_bounds(t, depth);
   const size_t smem = 4 * (size_t)a.ws * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1724,6 +1809,9 @@ cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s) {
   a.hcoef = L.hcoef;
   a.depth = depth;
   a.stride = t->nmono;
+  a.node_start = L.start;
+  a.node_count = L.count;
+  a.bd = level_bounds(t, depth);
   k_residual<<<(unsigned)L.n_items, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -1742,6 +1830,7 @@ cudaError_t launch_child_stats(const fmt_tree* t, int depth, cudaStream_t s) {
   a.child_S = L.child_S;
   a.child_n = L.child_n;
   a.depth = depth;
+  a.bd = level_bounds(t, depth);
   const int child_depth = depth + 1;
   a.shift = (child_depth <= FMT_QBITS && child_depth <= t->sort_bits / 3) ? 3 * (FMT_QBITS - child_depth) : -1;
   const int64_t nb = L.n_nodes * 9;
@@ -1787,6 +1876,10 @@ __global__ void __launch_bounds__(kQRThreads) k_fit_node_static(StaticArgs a) {
   double* Rs = smem + NB * a.ldB;
   double* sc = Rs + 2 * a.ldB;
   double* G = sc + 4;  // F / (l! m! n!), degree-p layout
+  if (!FMT_CHECK(a.q >= -1 && a.q <= a.p && a.p <= FMT_STATIC_MAX_DEGREE && a.m == fmt_nmono_d(a.q) + 1 &&
+                     a.m <= FMT_STATIC_MAX_M && a.n >= 0,
+                 CK_STATIC_ROWS))
+    return;
   const int m = a.m, q = a.q;
   double* R = a.R;
   for (int e = threadIdx.x; e < m * m; e += kQRThreads) {
@@ -1954,7 +2047,7 @@ extern "C" fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const doubl
     snprintf(msg, sizeof(msg), "fmt_fit_node_static: launch failed: %s", cudaGetErrorString(e));
     return fmt_set_error(FMT_ECUDA, msg);
   }
-  return FMT_OK;
+  return check_end(nullptr, (cudaStream_t)stream);
 }
 
 extern "C" fmt_status fmt_tune_get(int32_t degree, fmt_tune_entry* out) {
@@ -1972,3 +2065,7 @@ extern "C" fmt_status fmt_tune_set(const fmt_tune_entry* entry) {
                          "warps 4/8, chunk_factor 1/2/4/8/16, merge 0/1)");
   return FMT_OK;
 }
+
+#ifdef FMT_CHECKED
+FMT_CHECK_READER(check_site_fit)
+#endif

@@ -20,6 +20,77 @@
 #define FMT_ERR_CAPACITY 4
 #define FMT_ERR_TIMEOUT 8
 
+// ---------------------------------------------------------------------------
+// Bounds-checked build (nvcc -DFMT_CHECKED).  Before a kernel addresses
+// memory through an index it read from device memory (a work item's node,
+// rows and scratch slot, a node's problem, points, items and coefficient
+// slot, a parent found by search), it tests that index against the size of
+// the buffer it addresses.  A failed test records its site in the check word
+// of its translation unit and skips the work it guards, so no access leaves
+// its buffer; the results are then incomplete, and the ABI call that
+// launched the kernel synchronises, reads every check word and returns
+// FMT_EINTERNAL naming the first failed site.  In the default build
+// FMT_CHECK(cond, site) is the constant true and cond is not evaluated.
+// The tests are uniform over a CTA (a cluster, for the cluster merge), so
+// skipping never splits a barrier.
+enum fmt_check_site {
+  CK_NONE = 0,
+  CK_BUILD_INDEX,    // build: a point's problem, a sort position or a permutation entry
+  CK_PLAN_NODE,      // plan: a node's problem, degree or point range
+  CK_QR_ITEM,        // tile QR: the item, its node, rows, problem or R triangle
+  CK_MERGE_ITEM,     // merges: the pair of items and their R triangles
+  CK_BACKSOLVE_NODE, // back substitution: the node's R triangle or coefficient slot
+  CK_RESIDUAL_ITEM,  // residual update: the item, its node and rows
+  CK_CHILD_NODE,     // child statistics: a node's points or octant bounds
+  CK_MIXED_ITEM,     // mixed path, per item: node, rows, accumulator slot
+  CK_MIXED_NODE,     // mixed path, per node: its items, problem and scratch
+  CK_EVAL_NODE,      // evaluation: a node's problem or coefficient slot
+  CK_CUM_NODE,       // cumulative polynomials: a node, its problem or parent
+  CK_STATIC_ROWS,    // allocation-free fit: the rows or the degree
+  CK_PROBE,          // fmt_check_probe: the self-test of the mechanism
+  CK_SITES
+};
+
+// Sizes a level's indices are tested against (every build passes them; only
+// the checked build reads them).
+struct fmt_bounds {
+  int64_t n_points;   // sorted points of the tree
+  int64_t n_nodes;    // nodes of the level
+  int64_t n_items;    // work items of the level
+  int64_t r_cap;      // doubles of QR scratch the level's triangles may use
+  int32_t n_problems; // entries of the problem table
+  int32_t max_m;      // largest m (nmono + 1) a node of the level may have
+};
+
+__host__ __device__ __forceinline__ bool fmt_in(int64_t i, int64_t n) { return i >= 0 && i < n; }
+
+#ifdef FMT_CHECKED
+static __device__ int g_fmt_check_site;  // this translation unit's first failed site
+__device__ __forceinline__ bool fmt_check_fail(int site) {
+  atomicCAS(&g_fmt_check_site, 0, site);
+  return false;
+}
+#define FMT_CHECK(cond, site) ((cond) || fmt_check_fail(site))
+// defines fn(): this translation unit's failed site (0: none), then clears it
+#define FMT_CHECK_READER(fn)                                              \
+  int fn() {                                                              \
+    int v = 0;                                                            \
+    if (cudaMemcpyFromSymbol(&v, g_fmt_check_site, sizeof v) != cudaSuccess) return -1; \
+    if (v != 0) {                                                         \
+      const int zero = 0;                                                 \
+      cudaMemcpyToSymbol(g_fmt_check_site, &zero, sizeof zero);           \
+    }                                                                     \
+    return v;                                                             \
+  }
+int check_site_build();
+int check_site_fit();
+int check_site_mixed();
+int check_site_plan();
+#else
+#define FMT_CHECK(cond, site) true
+#endif
+const char* check_site_name(int site);
+
 // 1/l! for l = 0..14, each a correctly rounded binary64 quotient (l! is exact)
 static __constant__ double c_invfact[FMT_MAX_DEGREE + 1] = {
     1.0,          1.0,          1.0 / 2.0,          1.0 / 6.0,           1.0 / 24.0,
@@ -309,6 +380,19 @@ struct fmt_tree {
   int n_allocs = 0, cap_allocs = 0;
 };
 
+// The sizes a level's kernels test their indices against.
+inline fmt_bounds level_bounds(const fmt_tree* t, int depth) {
+  const fmt_level& L = t->lv[depth];
+  fmt_bounds b;
+  b.n_points = t->n;
+  b.n_nodes = L.n_nodes;
+  b.n_items = L.n_items;
+  b.r_cap = L.r_total;
+  b.n_problems = (int32_t)t->n_problems;
+  b.max_m = L.max_m;
+  return b;
+}
+
 // Records msg as the calling thread's last error (fmt_last_error(NULL)).
 fmt_status fmt_set_error(fmt_status st, const char* msg);
 
@@ -381,6 +465,10 @@ cudaError_t launch_mixed_sresid(const fmt_tree* t, int depth, const fmt_mixed_bu
 cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool last,
                                 cudaStream_t s);
 cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream_t s);
+cudaError_t launch_check_probe(int i, int n, cudaStream_t s);  // fmt_check_probe's kernel
+// Checked build: synchronise and report a failed bounds check (FMT_EINTERNAL,
+// message on t, or the thread's when t is NULL); FMT_OK in the default build.
+fmt_status check_end(fmt_tree* t, cudaStream_t s);
 cudaError_t launch_make_hcoef(const fmt_tree* t, int depth, cudaStream_t s);
 // ccoef (and ccoef_df) of a level from its hcoef and the parent level's ccoef
 cudaError_t launch_make_cum(const fmt_tree* t, int depth, cudaStream_t s);

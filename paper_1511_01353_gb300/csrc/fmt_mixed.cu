@@ -309,7 +309,45 @@ struct MArgs {
   const int64_t* item_roff;     // offset of each item's slot in rbuf
   double* dproj;                // tier 2: per item B^T s (dstride doubles)
   int dstride;
+  const int64_t* node_start;    // the level's node point ranges (checked build)
+  const int64_t* node_count;
+  fmt_bounds bd;
 };
+
+#ifdef FMT_CHECKED
+// Checked build: a node's problem and degree (its coefficients fit the
+// stride, its m the level's largest) and its items inside the level's.
+__device__ __forceinline__ bool mixed_node_ok(const MArgs& a, int64_t node) {
+  if (!fmt_in(node, a.bd.n_nodes) || !fmt_in(a.node_prob[node], a.bd.n_problems)) return false;
+  const int p = a.prob[a.node_prob[node]].degree;
+  if (p < 0 || p > FMT_MAX_DEGREE || fmt_nmono_d(p) > a.stride || fmt_nmono_d(p) > a.dstride) return false;
+  const int64_t i0 = a.node_item0[node], ni = a.node_nitems[node];
+  return ni >= 1 && i0 >= 0 && i0 + ni <= a.bd.n_items;
+}
+// ... and an item of it: the rows inside its node's inside the points.
+__device__ __forceinline__ bool mixed_item_ok(const MArgs& a, int64_t item) {
+  if (!fmt_in(item, a.bd.n_items)) return false;
+  const int64_t node = a.item_node[item];
+  if (!mixed_node_ok(a, node)) return false;
+  const int64_t s = a.node_start[node], e = s + a.node_count[node];
+  const int64_t rs = a.item_start[item], re = a.item_end[item];
+  return 0 <= s && s <= rs && rs <= re && re <= e && e <= a.bd.n_points;
+}
+// The node's m (nmono + 1) within the level's largest, which sized the
+// launch's shared memory and accumulators; the FP64 tier also needs each
+// item's m x m slot of the QR scratch.
+__device__ __forceinline__ bool mixed_m_ok(const MArgs& a, int64_t node, bool slots) {
+  const int64_t m = fmt_nmono_d(a.prob[a.node_prob[node]].degree) + 1;
+  if (m > a.bd.max_m) return false;
+  if (!slots) return true;
+  const int64_t i0 = a.node_item0[node], ni = a.node_nitems[node];
+  for (int64_t i = i0; i < i0 + ni; ++i) {
+    const int64_t ro = a.item_roff[i];
+    if (ro < 0 || ro + m * m > a.bd.r_cap) return false;
+  }
+  return true;
+}
+#endif
 __device__ __forceinline__ bool settled(const MArgs& a, int64_t node) {
   return a.mstat[kMStat * node + kSettled] != 0ull;
 }
@@ -318,6 +356,7 @@ __device__ __forceinline__ bool settled(const MArgs& a, int64_t node) {
 __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
   __shared__ double red[8];
   const int item = blockIdx.x;
+  if (!FMT_CHECK(mixed_item_ok(a, item), CK_MIXED_ITEM)) return;
   const int64_t node = a.item_node[item];
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   if (!tier2_eligible(pr, a.depth)) return;  // the frame serves both tiers
@@ -544,9 +583,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       gen_bar();
       if (it >= a.n_items) break;
       const int item = a.sched[it];
+      // (the generator warps take the same decision)
+      if (!FMT_CHECK(mixed_item_ok(a, item), CK_MIXED_ITEM)) continue;
       const int64_t node = a.item_node[item];
       const fmt_problem& pr = a.prob[a.node_prob[node]];
       if (kProj ? (!(a.flags[node] & FMT_FLAG_MIXED) || settled(a, node)) : !mixed_eligible(pr, a.depth)) continue;
+      if (!FMT_CHECK(mixed_m_ok(a, node, false), CK_MIXED_ITEM)) continue;
       const int p = pr.degree;
       const int L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m);
       const int nw = kProj ? L : m;
@@ -898,9 +940,11 @@ constexpr int kRedChunk = 256;
 __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
   const int64_t node = blockIdx.x / chunks;
   const int ch = blockIdx.x - (int)(node * chunks);
+  if (!FMT_CHECK(mixed_node_ok(a, node), CK_MIXED_NODE)) return;
   const int ni = a.node_nitems[node];
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   if (!mixed_eligible(pr, a.depth)) return;
+  if (!FMT_CHECK(mixed_m_ok(a, node, false), CK_MIXED_NODE)) return;
   const int64_t words = (int64_t)gram_cols(fmt_nmono_d(pr.degree) + 1) * 128;
   const int64_t i0 = a.node_item0[node];
   // the Gram kernel leaves (hi, lo) FP32 pairs; the node's sum goes to its first item as FP64
@@ -935,8 +979,10 @@ __device__ void warp_back_solve(const double* __restrict__ R, int m, int L, cons
 __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   extern __shared__ double fsm[];
   const int64_t node = blockIdx.x;
+  if (!FMT_CHECK(mixed_node_ok(a, node), CK_MIXED_NODE)) return;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   if (!mixed_eligible(pr, a.depth)) return;
+  if (!FMT_CHECK(mixed_m_ok(a, node, false), CK_MIXED_NODE)) return;
   const int tid = threadIdx.x;
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
   const int ncols = gram_cols(m);
@@ -1106,6 +1152,7 @@ __device__ __forceinline__ dfl horner_df_shared(const float2* G, int p, int nmon
 template <bool kDF>
 __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
   const int item = blockIdx.x;
+  if (!FMT_CHECK(mixed_item_ok(a, item), CK_MIXED_ITEM)) return;
   const int64_t node = a.item_node[item];
   const int32_t nf = a.flags[node];
   if (!(nf & FMT_FLAG_MIXED) || (a.tier == 2 && !(nf & FMT_FLAG_MIXED_FP64)) || settled(a, node)) return;
@@ -1151,7 +1198,9 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   extern __shared__ double usm[];
   __shared__ double red[kFThreads / 32];
   const int64_t node = blockIdx.x;
+  if (!FMT_CHECK(mixed_node_ok(a, node), CK_MIXED_NODE)) return;
   if (!(a.flags[node] & FMT_FLAG_MIXED) || settled(a, node)) return;
+  if (!FMT_CHECK(mixed_m_ok(a, node, false), CK_MIXED_NODE)) return;
   const int tid = threadIdx.x;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
@@ -1439,9 +1488,11 @@ __global__ void __launch_bounds__(256) k_dgram(MArgs a, int npairs) {
   __shared__ double As[kDRows][kDT], Bs[kDRows][kDT];
   __shared__ int cabc[2][kDT];
   const int item = blockIdx.x / npairs, pair = blockIdx.x - item * npairs;
+  if (!FMT_CHECK(mixed_item_ok(a, item), CK_MIXED_ITEM)) return;
   const int64_t node = a.item_node[item];
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   if (!tier2_selected(a, node, pr)) return;
+  if (!FMT_CHECK(mixed_m_ok(a, node, true), CK_MIXED_ITEM)) return;
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, nt = (m + kDT - 1) / kDT;
   if (pair >= nt * (nt + 1) / 2) return;
   int bi = 0, rem = pair;
@@ -1520,8 +1571,10 @@ __global__ void __launch_bounds__(256) k_dgram(MArgs a, int npairs) {
 __global__ void __launch_bounds__(256) k_dfactor(MArgs a) {
   extern __shared__ double dsm[];
   const int64_t node = blockIdx.x;
+  if (!FMT_CHECK(mixed_node_ok(a, node), CK_MIXED_NODE)) return;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   if (!tier2_selected(a, node, pr)) return;
+  if (!FMT_CHECK(mixed_m_ok(a, node, true), CK_MIXED_NODE)) return;
   const int tid = threadIdx.x;
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1;
   const int64_t i0 = a.node_item0[node];
@@ -1637,6 +1690,7 @@ __global__ void __launch_bounds__(256) k_dproj(MArgs a) {
   __shared__ double Pl[kDRows * 3 * P1];
   __shared__ double sv[kDRows];
   const int item = blockIdx.x;
+  if (!FMT_CHECK(mixed_item_ok(a, item), CK_MIXED_ITEM)) return;
   const int64_t node = a.item_node[item];
   if ((a.flags[node] & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) != (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64) ||
       settled(a, node))
@@ -1680,9 +1734,11 @@ __global__ void __launch_bounds__(kFThreads) k_dupdate(MArgs a) {
   __shared__ double red[kFThreads / 32], red2[kFThreads / 32];
   __shared__ double s_pt[3][FMT_MAX_DEGREE + 1];
   const int64_t node = blockIdx.x;
+  if (!FMT_CHECK(mixed_node_ok(a, node), CK_MIXED_NODE)) return;
   if ((a.flags[node] & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64)) != (FMT_FLAG_MIXED | FMT_FLAG_MIXED_FP64) ||
       settled(a, node))
     return;
+  if (!FMT_CHECK(mixed_m_ok(a, node, true), CK_MIXED_NODE)) return;
   const int tid = threadIdx.x;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1;
@@ -1887,6 +1943,9 @@ MArgs make_margs(const fmt_tree* t, int depth, const fmt_mixed_bufs& b) {
   a.item_roff = L.item_roff;
   a.dproj = b.dproj;
   a.dstride = t->nmono;
+  a.node_start = L.start;
+  a.node_count = L.count;
+  a.bd = level_bounds(t, depth);
   return a;
 }
 
@@ -2057,3 +2116,7 @@ cudaError_t launch_wait_probe(unsigned long long limit_ns, int* d_err, cudaStrea
   k_wait_probe<<<1, 32, 0, s>>>(limit_ns, d_err);
   return cudaGetLastError();
 }
+
+#ifdef FMT_CHECKED
+FMT_CHECK_READER(check_site_mixed)
+#endif

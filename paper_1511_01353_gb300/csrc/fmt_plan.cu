@@ -66,7 +66,20 @@ struct PlanArgs {
   const int32_t* node_prob;
   const fmt_problem* prob;
   int depth;
+  int64_t n_points;    // sorted points of the tree (checked build)
+  int32_t n_problems;
 };
+
+#ifdef FMT_CHECKED
+// Checked build: the planned node's problem, degree and point range.
+__device__ __forceinline__ bool plan_node_ok(const PlanArgs& a, int64_t node) {
+  if (!fmt_in(a.node_prob[node], a.n_problems)) return false;
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const int q = a.depth == 0 ? pr.q_root : pr.degree;
+  const int64_t st = a.start[node], cnt = a.count[node];
+  return pr.degree <= FMT_MAX_DEGREE && q >= 0 && q <= pr.degree && st >= 0 && cnt >= 0 && st + cnt <= a.n_points;
+}
+#endif
 
 __device__ __forceinline__ double horner_flops_d(int p) {
   return 2.0 * ((double)fmt_nmono_d(p) + (p + 1) * (p + 2) / 2.0 + (p + 1));
@@ -142,7 +155,10 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
   for (int64_t b = 0; b < a.n_nodes; b += blockDim.x) {
     const int64_t node = b + threadIdx.x;
     int64_t nch = 0, cnt = 0, st = 0, m = 0;
-    if (node < a.n_nodes) {
+    if (node < a.n_nodes && !FMT_CHECK(plan_node_ok(a, node), CK_PLAN_NODE)) {
+      nch = 1;  // one empty item at row 0 of degree 0 (the ABI call reports the failed check)
+      m = 1;
+    } else if (node < a.n_nodes) {
       cnt = a.count[node];
       st = a.start[node];
       nch = (cnt + C - 1) / C;
@@ -286,6 +302,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_refine(RefineArgs r, PlanArgs 
     int pid = 0;
     if (node < r.n_nodes) {
       pid = r.node_prob[node];
+      if (!FMT_CHECK(fmt_in(pid, a.n_problems), CK_PLAN_NODE)) pid = 0;
       const fmt_problem& pr = r.prob[pid];
       const double tau = pr.tau;
       int64_t nmin = fmt_nmono_d(pr.degree);
@@ -405,7 +422,8 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
       const uint64_t code = fmt_spread3(fmt_quant(x, pr.lo[0], pr.S)) |
                             (fmt_spread3(fmt_quant(y, pr.lo[1], pr.S)) << 1) |
                             (fmt_spread3(fmt_quant(z, pr.lo[2], pr.S)) << 2);
-      const int p = pr.degree, nm = fmt_nmono_d(p);
+      int p = pr.degree, nm = fmt_nmono_d(p);
+      if (!FMT_CHECK(p <= FMT_MAX_DEGREE && nm <= a.stride, CK_EVAL_NODE)) p = -1, nm = 0;  // no coefficient read
       double acc = 0.0;
       int deep = -1;
       int64_t deep_idx = 0;
@@ -475,6 +493,7 @@ struct CumArgs {
   int64_t pn;
   const double* pccoef;
   int* err;
+  int32_t n_problems;
 };
 
 __global__ void __launch_bounds__(128) k_make_cum(CumArgs a) {
@@ -483,6 +502,12 @@ __global__ void __launch_bounds__(128) k_make_cum(CumArgs a) {
   __shared__ int64_t s_parent;
   const int64_t node = blockIdx.x;
   const int tid = threadIdx.x;
+  // the node's problem, and a degree whose coefficients fit the stride and
+  // whose (p+1)^3 cube fits the launch's shared memory
+  if (!FMT_CHECK(fmt_in(a.node_prob[node], a.n_problems) && a.prob[a.node_prob[node]].degree >= 0 &&
+                     fmt_nmono_d(a.prob[a.node_prob[node]].degree) <= a.stride && (a.depth == 0 || a.pn >= 1),
+                 CK_CUM_NODE))
+    return;
   const int p = a.prob[a.node_prob[node]].degree, P1 = p + 1, nm = fmt_nmono_d(p);
   const double* own = a.hcoef + node * a.stride;
   double* out = a.ccoef + node * a.stride;
@@ -571,10 +596,12 @@ __global__ void __launch_bounds__(128) k_make_cum(CumArgs a) {
 // past the problem's nmono are zero)
 __global__ void k_make_hcoef(int64_t n, int stride, const int32_t* __restrict__ node_prob,
                              const fmt_problem* __restrict__ prob, const double* __restrict__ coef,
-                             double* __restrict__ hcoef) {
+                             double* __restrict__ hcoef, int n_problems) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * stride) return;
   const int64_t node = i / stride;
+  if (!FMT_CHECK(fmt_in(node_prob[node], n_problems) && prob[node_prob[node]].degree <= FMT_MAX_DEGREE, CK_CUM_NODE))
+    return;
   const int p = prob[node_prob[node]].degree;
   int k = (int)(i - node * stride);
   if (k >= fmt_nmono_d(p)) {
@@ -633,6 +660,8 @@ PlanArgs plan_args_for(const fmt_tree* t, const fmt_level& L, int64_t chunk_fixe
   a.node_prob = L.prob;
   a.prob = t->d_prob;
   a.depth = 0;
+  a.n_points = t->n;
+  a.n_problems = (int32_t)t->n_problems;
   return a;
 }
 
@@ -723,6 +752,7 @@ cudaError_t launch_make_cum(const fmt_tree* t, int depth, cudaStream_t s) {
   a.pn = depth > 0 ? t->lv[depth - 1].n_nodes : 0;
   a.pccoef = depth > 0 ? t->lv[depth - 1].ccoef : nullptr;
   a.err = t->d_err;
+  a.n_problems = (int32_t)t->n_problems;
   const int P1 = t->max_degree + 1;
   k_make_cum<<<(unsigned)L.n_nodes, 128, sizeof(double) * (size_t)(P1 * P1 * P1), s>>>(a);
   return cudaGetLastError();
@@ -733,7 +763,21 @@ cudaError_t launch_make_hcoef(const fmt_tree* t, int depth, cudaStream_t s) {
   const int64_t tot = L.n_nodes * t->nmono;
   if (tot <= 0) return cudaSuccess;
   k_make_hcoef<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.n_nodes, t->nmono, L.prob, t->d_prob, L.coef,
-                                                             L.hcoef);
+                                                             L.hcoef, (int)t->n_problems);
+  return cudaGetLastError();
+}
+
+namespace {
+// fmt_check_probe: element i of a 64-element array, written when the checked
+// build's test i < n passes (every i the host accepts lies inside the array)
+__device__ int g_probe_cells[64];
+__global__ void k_check_probe(int i, int n) {
+  if (FMT_CHECK(i < n, CK_PROBE)) g_probe_cells[i] = 1;
+}
+}  // namespace
+
+cudaError_t launch_check_probe(int i, int n, cudaStream_t s) {
+  k_check_probe<<<1, 1, 0, s>>>(i, n);
   return cudaGetLastError();
 }
 
@@ -741,3 +785,7 @@ cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream
   k_probe_dfma<<<blocks, 256, 0, s>>>(iters, out);
   return cudaGetLastError();
 }
+
+#ifdef FMT_CHECKED
+FMT_CHECK_READER(check_site_plan)
+#endif

@@ -88,7 +88,8 @@ EXPORTED = ["fmt_nmono", "oct_build", "oct_build_batch", "fit_level", "refine", 
             "fmt_profile_class_name", "fmt_probe_dfma", "fmt_fit_node_static", "fmt_server_create",
             "fmt_server_submit", "fmt_server_wait", "fmt_server_destroy", "fmt_server_clock", "fmt_autotune",
             "fmt_tune_get", "fmt_tune_set", "fmt_debug_fail_alloc", "fmt_wait_probe", "fmt_autotune_forest",
-            "fmt_server_submit_eval", "fmt_server_release", "fmt_server_memory", "fmt_tree_trim"]
+            "fmt_server_submit_eval", "fmt_server_release", "fmt_server_memory", "fmt_tree_trim",
+            "fmt_checked_build", "fmt_check_probe", "fmt_debug_item_rows"]
 STATIC_MAX_DEGREE = 8
 PROFILE_CLASSES = 24
 
@@ -200,6 +201,12 @@ def load(build: bool = True):
         L.fmt_debug_fail_alloc.restype = ctypes.c_int
         L.fmt_wait_probe.argtypes = [i64, P]
         L.fmt_wait_probe.restype = ctypes.c_int
+        L.fmt_checked_build.argtypes = []
+        L.fmt_checked_build.restype = i32
+        L.fmt_check_probe.argtypes = [i32, i32, P]
+        L.fmt_check_probe.restype = ctypes.c_int
+        L.fmt_debug_item_rows.argtypes = [P, i32, i64, i64, i64, P]
+        L.fmt_debug_item_rows.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -476,6 +483,24 @@ def fmt_debug_fail_alloc(k: int):
 def fmt_wait_probe(limit_ns: int, stream=None):
     """Bounded wait that nothing satisfies; raises FmtError(FMT_ETIMEOUT) when the bound runs out."""
     _check(load().fmt_wait_probe(limit_ns, _stream_handle(stream)))
+
+
+def fmt_checked_build() -> bool:
+    """True when the loaded library was built with device bounds checks (-DFMT_CHECKED)."""
+    return bool(load().fmt_checked_build())
+
+
+def fmt_check_probe(i: int, n: int, stream=None):
+    """Self-test of the device bounds checks: element i of a 64-element device
+    array, written when i < n passes the checked build's test.  Raises
+    FmtError(FMT_EINTERNAL) for i >= n in the checked build."""
+    _check(load().fmt_check_probe(i, n, _stream_handle(stream)))
+
+
+def fmt_debug_item_rows(tree: "Tree", depth: int, item: int, start: int, end: int, stream=None):
+    """Test hook: set one work item's row range (0 <= start <= end <= n) of
+    the planned level awaiting its fit."""
+    _check(load().fmt_debug_item_rows(tree.handle, depth, item, start, end, _stream_handle(stream)), tree)
 
 
 def fmt_fit_node_static(degree: int, x, y, z, r_in, coef, r_out, flags=None, lo=(0.0, 0.0, 0.0), side=1.0,

@@ -36,6 +36,18 @@ def test_library_exports_every_declared_symbol():
     assert sorted(F.EXPORTED) == declared_functions()
 
 
+def test_checked_build_compiles_and_exports_the_same_symbols():
+    # the bounds-checked build (-DFMT_CHECKED) of the same sources; host-only
+    # calls, no GPU needed
+    from paper_1511_01353_gb300 import build as B
+    lib = ctypes.CDLL(B.build_checked())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    lib.fmt_checked_build.restype = ctypes.c_int32
+    assert lib.fmt_checked_build() == 1
+    assert not F.fmt_checked_build()
+
+
 def _c_layout():
     code = r'''
 #include <stdio.h>
@@ -147,7 +159,14 @@ def test_calls_on_null_tree_fail_cleanly():
     assert lib.fit_level(None, 0, None) == F.FMT_EINVAL
     assert lib.refine(None, 0, ctypes.byref(n), None) == F.FMT_EINVAL
     assert lib.evaluate(None, 0, None, None, None, None, None, None) == F.FMT_EINVAL
+    assert lib.fmt_debug_item_rows(None, 0, 0, 0, 1, None) == F.FMT_EINVAL
     lib.fmt_tree_free(None)
+
+
+def test_check_probe_rejects_indices_outside_its_array():
+    lib = F.load()
+    for i, n in ((64, 8), (-1, 8), (3, 33), (3, -1)):
+        assert lib.fmt_check_probe(i, n, None) == F.FMT_EINVAL
 
 
 def test_import_rejects_garbage():
