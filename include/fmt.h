@@ -165,9 +165,14 @@ fmt_status oct_build(const fmt_params* params, int64_t n, const double* x, const
  *  - F is converted exactly to Alg. 2's moment basis in the node frame (the
  *    stored coefficients have the FP64 path's layout), and r <- r - Lambda F
  *    runs in FP64 as on the FP64 path.
- * A node whose Cholesky pivot falls below 1e-6 of its diagonal entry
- * (FMT_FLAG_MIXED_PIVOT), or whose root degree was clamped, is refitted by
- * the FP64 Householder path.  A node whose fit after the last sweep is not
+ * A node whose root degree was clamped is fitted by the FP64 Householder
+ * path, and so are the nodes with fewer than 1.5 m points (m = nmono + 1:
+ * nearly square systems, whose Gram is often too ill-conditioned for either
+ * normal-equations tier) of a level that has at most 304 items of them:
+ * those start at the beginning of the level on a side stream, beside the
+ * tensor-core tier (with more, they take the tiers like any other node).  A node whose Cholesky pivot
+ * falls below 1e-6 of its diagonal entry (FMT_FLAG_MIXED_PIVOT) is refitted
+ * by Householder too.  A node whose fit after the last sweep is not
  * within 1e-7 of converged (the last change |Lambda d|, or its extrapolation
  * by the ratio of the last two changes, above 1e-7 |Lambda F|), or whose
  * polynomial may still change by more than 1e-8 max|f| somewhere in the node

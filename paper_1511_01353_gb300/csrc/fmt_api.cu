@@ -523,6 +523,7 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
   L0.max_m = (int32_t)pl.max_m;
   L0.deg_mask = pl.deg_mask;
   L0.r_total = pl.r_total;
+  L0.n_hard_items = pl.n_hard_items;
   L0.qr_flops = pl.qr_flops;
   L0.horner_flops = pl.horner_flops;
   t->n_levels = 1;
@@ -599,6 +600,24 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
   fmt_mixed_bufs b = t->mx;
   if (b.cap_cache < mixed_cache_bytes(t, depth)) b.cache = nullptr;  // too large: regenerate per sweep
   const double rows = (double)L.n_points, nodes = (double)L.n_nodes;
+  // Householder refits beside the tensor-core tier run on a side stream; the
+  // nearly square nodes (fewer than 1.5 m points), which the normal-equations
+  // tiers often cannot fit, start there right away when the level has few
+  // (route_hard).  Their QR scratch
+  // slots are not used by the FP64 tier, which skips them.
+  {
+    cudaError_t e = cudaSuccess;
+    if (!t->piv_stream) e = cudaStreamCreateWithFlags(&t->piv_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !t->piv_fork) e = cudaEventCreateWithFlags(&t->piv_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !t->piv_join) e = cudaEventCreateWithFlags(&t->piv_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(t->piv_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(t->piv_stream, t->piv_fork, 0);
+    if (e == cudaSuccess && route_hard(t, depth)) {
+      ProfScope ps(K_TILE_QR, t->piv_stream, 1, 0.0, 0.0);
+      e = launch_tile_qr(t, depth, t->Rbuf, t->piv_stream, 3);
+    }
+    CUDA_TRY(t, e, "nearly square nodes: Householder launch");
+  }
   {
     ProfScope ps(K_MBOX, s, 2, rows, 0.0);
     CUDA_TRY(t, launch_mixed_box(t, depth, b, s), "mixed box launch");
@@ -612,15 +631,10 @@ fmt_status fit_level_mixed(fmt_tree* t, int depth, cudaStream_t s) {
     CUDA_TRY(t, launch_mixed_factor(t, depth, b, s), "mixed factor launch");
   }
   // Nodes whose Cholesky pivot was too small go to Householder: refit them on
-  // a side stream while the sweeps run (their QR scratch slots are not used
-  // by the FP64 tier, which skips them); fit_level_launches joins it before
-  // the other Householder refits.
+  // the side stream (after the nearly square ones) while the sweeps run;
+  // fit_level_launches joins it before the other Householder refits.
   {
-    cudaError_t e = cudaSuccess;
-    if (!t->piv_stream) e = cudaStreamCreateWithFlags(&t->piv_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !t->piv_fork) e = cudaEventCreateWithFlags(&t->piv_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess && !t->piv_join) e = cudaEventCreateWithFlags(&t->piv_join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(t->piv_fork, s);
+    cudaError_t e = cudaEventRecord(t->piv_fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(t->piv_stream, t->piv_fork, 0);
     if (e == cudaSuccess) {
       ProfScope ps(K_TILE_QR, t->piv_stream, 1, 0.0, 0.0);
@@ -927,6 +941,7 @@ fmt_status refine(fmt_tree* t, int32_t depth, int64_t* n_new_nodes, void* stream
   N.max_m = (int32_t)pl.max_m;
   N.deg_mask = pl.deg_mask;
   N.r_total = pl.r_total;
+  N.n_hard_items = pl.n_hard_items;
   N.qr_flops = pl.qr_flops;
   N.horner_flops = pl.horner_flops;
   N.fitted = false;

@@ -89,9 +89,10 @@ struct QRArgs {
   int* err;              // device error word (a bounded wait that ran out sets FMT_ERR_TIMEOUT)
   int node_mode;         // tile QR: which nodes it takes (launch_tile_qr's mode)
   const int* work_base;  // the tree's d_work (kPivSlot: the level's small-pivot count)
-  const int64_t* node_start;  // the level's node point ranges (checked build)
-  const int64_t* node_count;
+  const int64_t* node_start;  // the level's node point ranges (the checked build's tests;
+  const int64_t* node_count;  // the count also picks the mixed path's nearly square nodes)
   fmt_bounds bd;
+  int route_hard;             // route_hard(): the level sends its nearly square nodes straight to Householder
 };
 
 #ifdef FMT_CHECKED
@@ -138,11 +139,21 @@ __device__ __forceinline__ bool early_refit(const QRArgs& a, int64_t node, int32
          a.work_base[kPivSlot] <= kEarlyRefitMax;
 }
 
+// A node the mixed path sends straight to Householder (on a level that
+// routes them): of a degree its tiers cover, not a clamped root, nearly
+// square (fmt_mixed_hard).
+__device__ __forceinline__ bool hard_node(const QRArgs& a, int64_t node) {
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  return a.route_hard && pr.degree <= FMT_MIXED_FP64_MAX_DEGREE && !(a.depth == 0 && pr.q_root < pr.degree) &&
+         fmt_mixed_hard(pr.degree, a.node_count[node]);
+}
+
 __device__ __forceinline__ bool node_done(const QRArgs& a, int64_t node) {
   const int32_t f = a.flags[node];
   if (f & FMT_FLAG_MIXED) return true;
+  if (a.node_mode == 3) return !hard_node(a, node);
   if (a.node_mode == 1) return !early_refit(a, node, f);
-  if (a.node_mode == 2) return early_refit(a, node, f);
+  if (a.node_mode == 2) return early_refit(a, node, f) || hard_node(a, node);
   return false;
 }
 
@@ -1537,6 +1548,7 @@ QRArgs make_qr_args(const fmt_tree* t, int depth, double* R) {
   a.node_start = L.start;
   a.node_count = L.count;
   a.bd = level_bounds(t, depth);
+  a.route_hard = route_hard(t, depth) ? 1 : 0;
   return a;
 }
 
@@ -1692,7 +1704,8 @@ cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s, in
   if (n_items <= 0) return cudaSuccess;
   const uint64_t mask = (uint64_t)L.deg_mask;
   const bool several = (mask & (mask - 1)) != 0;
-  int* work0 = t->d_work + 1 + (mode == 1 ? FMT_MAX_DEGREE + 1 : 0);
+  // the side-stream launches (modes 1 and 3, one after the other) have their own counters
+  int* work0 = t->d_work + 1 + (mode == 1 || mode == 3 ? FMT_MAX_DEGREE + 1 : 0);
   auto launch_one = [&](int mq, cudaStream_t st, int* work) -> cudaError_t {
     QRArgs a = make_qr_args(t, depth, R);
     a.node_mode = mode;
@@ -1702,10 +1715,11 @@ cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s, in
     QRConfig c = qr_config(mq);
     // the early refits are a few small nodes beside other work: latency-bound
     // single CTAs, where 8 warps hide more of the FP64 latency than 4
-    if (mode == 1) c.warps = 8;
+    if (mode == 1 || mode == 3) c.warps = 8;
     const size_t smem = qr_smem_bytes(mq, c.rows);
     int64_t grid = qr_resident_ctas(mq);
     if (grid > n_items) grid = n_items;
+    if (mode == 3 && grid > L.n_hard_items) grid = L.n_hard_items;  // only those items have work
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     return qr_ops(c).tile(a, (unsigned)grid, smem, st);

@@ -224,6 +224,14 @@ __device__ __forceinline__ dfl fmt_horner_df(const float2* __restrict__ G, int p
 // nmono(p) on the device
 __host__ __device__ __forceinline__ int fmt_nmono_d(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
 
+// Mixed path: a node with fewer than 1.5 m points (m = nmono + 1) is nearly
+// square, its Gram often too ill-conditioned for both normal-equations tiers;
+// on a level with few such nodes (route_hard) they go straight to
+// Householder, refitted at the start of the level beside the tensor-core tier.
+__host__ __device__ __forceinline__ bool fmt_mixed_hard(int degree, int64_t count) {
+  return 2 * count < 3 * (int64_t)(fmt_nmono_d(degree) + 1);
+}
+
 // Shared-memory row pitch of the QR kernels for m columns: the smallest
 // ld >= m with ld = 4 (mod 16) doubles (64-bit accesses are served per
 // half-warp: 4 columns x 4 row groups; this puts the row groups of a quad
@@ -292,6 +300,7 @@ struct fmt_level {
   int32_t* sched = nullptr;       // item order for the QR queue (largest first)
   int64_t* item_roff = nullptr;   // offset of the item's m x m triangle in the QR scratch
   int64_t r_total = 0;            // doubles of QR scratch the level needs
+  int64_t n_hard_items = 0;       // items of the mixed path's nearly square nodes (fmt_mixed_hard)
 };
 
 // Small result block that refine reads back in one copy.
@@ -313,6 +322,7 @@ struct fmt_plan_out {
   double horner_flops; // sum over nodes of rows x Horner flops of the node degree
   int64_t r_total;     // doubles of QR scratch: sum over items of m^2
   int64_t deg_mask;    // bit q set: some planned node has (effective) degree q
+  int64_t n_hard_items; // items of nodes the mixed path sends straight to Householder
 };
 
 // Scratch of the mixed-precision fit (fmt_mixed.cu), grown per tree.
@@ -381,6 +391,18 @@ struct fmt_tree {
 };
 
 // The sizes a level's kernels test their indices against.
+// Whether a mixed level refits its nearly square nodes (fmt_mixed_hard) with
+// Householder from the start: only when they are few enough to run in one
+// wave beside the tensor-core tier (two CTAs on each of the 152 SMs), where
+// that costs the level nothing and spares it the later fallbacks, which run
+// one after another at its end.  Many such nodes (a forest of small problems)
+// are left to the tiers, which fit most of them at far fewer FP64 flops.
+constexpr int64_t kHardRouteMax = 2 * 152;
+inline bool route_hard(const fmt_tree* t, int depth) {
+  const int64_t h = t->lv[depth].n_hard_items;
+  return t->P.precision == FMT_MIXED && h > 0 && h <= kHardRouteMax;
+}
+
 inline fmt_bounds level_bounds(const fmt_tree* t, int depth) {
   const fmt_level& L = t->lv[depth];
   fmt_bounds b;
@@ -430,7 +452,9 @@ fmt_tune_entry tune_current(int degree);
 int qr_resident_ctas(int m);  // SMs x resident QR CTAs per SM
 size_t qr_smem_bytes(int m, int rows);
 // mode 0: every node not fitted by the mixed path; 1: only the mixed path's
-// small-pivot nodes (refitted early); 2: mode 0 without those.
+// small-pivot nodes (refitted early); 2: mode 0 without those and without the
+// nearly square nodes (fmt_mixed_hard); 3: only the nearly square nodes (at
+// the start of a mixed level).
 cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s, int mode = 0);  // may create side streams
 cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s);
 cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream_t s);

@@ -75,15 +75,17 @@ __host__ __device__ __forceinline__ int gram_cols(int m) {
   return l <= 128 ? l : l + (l - 128);
 }
 __host__ __device__ __forceinline__ bool mixed_ok_degree(int p) { return p >= 0 && p <= FMT_MIXED_MAX_DEGREE; }
-__device__ __forceinline__ bool mixed_eligible(const fmt_problem& pr, int depth) {
-  return mixed_ok_degree(pr.degree) && !(depth == 0 && pr.q_root < pr.degree);
+// (hard: a nearly square node sent straight to Householder, routed_hard)
+__device__ __forceinline__ bool mixed_eligible(const fmt_problem& pr, int depth, bool hard) {
+  return mixed_ok_degree(pr.degree) && !(depth == 0 && pr.q_root < pr.degree) && !hard;
 }
 // the FP64 normal-equations tier takes degrees 1..FMT_MIXED_FP64_MAX_DEGREE:
 // above that Householder's rank rule on the badly scaled moment basis of
 // Alg. 2 drops columns this tier's Legendre basis would keep (a different
 // fit); a clamped root stays with Householder too
-__device__ __forceinline__ bool tier2_eligible(const fmt_problem& pr, int depth) {
-  return pr.degree >= 1 && pr.degree <= FMT_MIXED_FP64_MAX_DEGREE && !(depth == 0 && pr.q_root < pr.degree);
+__device__ __forceinline__ bool tier2_eligible(const fmt_problem& pr, int depth, bool hard) {
+  return pr.degree >= 1 && pr.degree <= FMT_MIXED_FP64_MAX_DEGREE && !(depth == 0 && pr.q_root < pr.degree) &&
+         !hard;
 }
 
 // ------------------------------------------------------------------ PTX
@@ -309,10 +311,15 @@ struct MArgs {
   const int64_t* item_roff;     // offset of each item's slot in rbuf
   double* dproj;                // tier 2: per item B^T s (dstride doubles)
   int dstride;
-  const int64_t* node_start;    // the level's node point ranges (checked build)
-  const int64_t* node_count;
+  const int64_t* node_start;    // the level's node point ranges (the checked build's tests;
+  const int64_t* node_count;    // the count also keeps nearly square nodes off both tiers)
   fmt_bounds bd;
+  int route_hard;               // route_hard(): nearly square nodes go straight to Householder
 };
+// a nearly square node this level sends straight to Householder
+__device__ __forceinline__ bool routed_hard(const MArgs& a, int64_t node, const fmt_problem& pr) {
+  return a.route_hard && fmt_mixed_hard(pr.degree, a.node_count[node]);
+}
 
 #ifdef FMT_CHECKED
 // Checked build: a node's problem and degree (its coefficients fit the
@@ -359,7 +366,7 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
   if (!FMT_CHECK(mixed_item_ok(a, item), CK_MIXED_ITEM)) return;
   const int64_t node = a.item_node[item];
   const fmt_problem& pr = a.prob[a.node_prob[node]];
-  if (!tier2_eligible(pr, a.depth)) return;  // the frame serves both tiers
+  if (!tier2_eligible(pr, a.depth, routed_hard(a, node, pr))) return;  // the frame serves both tiers
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
   fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
@@ -587,7 +594,9 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       if (!FMT_CHECK(mixed_item_ok(a, item), CK_MIXED_ITEM)) continue;
       const int64_t node = a.item_node[item];
       const fmt_problem& pr = a.prob[a.node_prob[node]];
-      if (kProj ? (!(a.flags[node] & FMT_FLAG_MIXED) || settled(a, node)) : !mixed_eligible(pr, a.depth)) continue;
+      if (kProj ? (!(a.flags[node] & FMT_FLAG_MIXED) || settled(a, node))
+                : !mixed_eligible(pr, a.depth, routed_hard(a, node, pr)))
+        continue;
       if (!FMT_CHECK(mixed_m_ok(a, node, false), CK_MIXED_ITEM)) continue;
       const int p = pr.degree;
       const int L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m);
@@ -943,7 +952,7 @@ __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
   if (!FMT_CHECK(mixed_node_ok(a, node), CK_MIXED_NODE)) return;
   const int ni = a.node_nitems[node];
   const fmt_problem& pr = a.prob[a.node_prob[node]];
-  if (!mixed_eligible(pr, a.depth)) return;
+  if (!mixed_eligible(pr, a.depth, routed_hard(a, node, pr))) return;
   if (!FMT_CHECK(mixed_m_ok(a, node, false), CK_MIXED_NODE)) return;
   const int64_t words = (int64_t)gram_cols(fmt_nmono_d(pr.degree) + 1) * 128;
   const int64_t i0 = a.node_item0[node];
@@ -981,7 +990,7 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   const int64_t node = blockIdx.x;
   if (!FMT_CHECK(mixed_node_ok(a, node), CK_MIXED_NODE)) return;
   const fmt_problem& pr = a.prob[a.node_prob[node]];
-  if (!mixed_eligible(pr, a.depth)) return;
+  if (!mixed_eligible(pr, a.depth, routed_hard(a, node, pr))) return;
   if (!FMT_CHECK(mixed_m_ok(a, node, false), CK_MIXED_NODE)) return;
   const int tid = threadIdx.x;
   const int p = pr.degree, L = fmt_nmono_d(p), m = L + 1, Lp = mpad16(m), b1 = Lp - 128;
@@ -1433,7 +1442,7 @@ static __constant__ double c_leg64[FMT_MAX_DEGREE][2] = {
 // and those of degree above FMT_MIXED_MAX_DEGREE.
 __device__ __forceinline__ bool tier2_selected(const MArgs& a, int64_t node, const fmt_problem& pr) {
   const int32_t f = a.flags[node];
-  return tier2_eligible(pr, a.depth) && !(f & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_PIVOT));
+  return tier2_eligible(pr, a.depth, routed_hard(a, node, pr)) && !(f & (FMT_FLAG_MIXED | FMT_FLAG_MIXED_PIVOT));
 }
 
 // (a, b, c) of basis column j in Alg. 2 order, packed a | b << 8 | c << 16
@@ -1946,6 +1955,7 @@ MArgs make_margs(const fmt_tree* t, int depth, const fmt_mixed_bufs& b) {
   a.node_start = L.start;
   a.node_count = L.count;
   a.bd = level_bounds(t, depth);
+  a.route_hard = route_hard(t, depth) ? 1 : 0;
   return a;
 }
 

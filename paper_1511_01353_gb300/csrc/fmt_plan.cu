@@ -145,7 +145,7 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  int64_t maxc = 0, maxm = 0;
+  int64_t maxc = 0, maxm = 0, nhard = 0;
   double qrf = 0.0, hf = 0.0;
   __shared__ unsigned long long s_degmask;
   if (threadIdx.x == 0) s_degmask = 0ull;
@@ -170,6 +170,8 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
       atomicOr(&s_degmask, 1ull << q);
       qrf += 2.0 * (double)m * (double)m * (double)cnt;
       hf += horner_flops_d(pr.degree) * (double)cnt;
+      // the mixed path's nearly square nodes (fmt_fit.cu, hard_node)
+      if (pr.degree <= FMT_MIXED_FP64_MAX_DEGREE && q == pr.degree && fmt_mixed_hard(pr.degree, cnt)) nhard += nch;
     }
     int64_t tot, rtot;
     const int64_t ex = block_exscan<int64_t>(nch, &tot);
@@ -200,6 +202,7 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
   }
   maxc = block_max<int64_t>(maxc);
   maxm = block_max<int64_t>(maxm);
+  nhard = block_sum<int64_t>(nhard);
   qrf = block_sum<double>(qrf);
   hf = block_sum<double>(hf);
   // Queue order for the QR kernel: items bucketed by floor(log2(rows)),
@@ -237,6 +240,7 @@ __device__ void plan_items(const PlanArgs& a, fmt_plan_out* out, int* err) {
     out->max_chunks = maxc;
     out->max_m = maxm;
     out->deg_mask = (int64_t)s_degmask;
+    out->n_hard_items = nhard;
     out->qr_flops = qrf;
     out->horner_flops = hf;
     out->chunk_rows = C;
@@ -369,6 +373,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_refine(RefineArgs r, PlanArgs 
       out->qr_flops = 0.0;
       out->horner_flops = 0.0;
       out->r_total = 0;
+      out->n_hard_items = 0;
     }
     return;
   }
