@@ -718,7 +718,13 @@ fmt_status fit_level_launches(fmt_tree* t, int depth, cudaStream_t s) {
     ProfScope ps(K_BACKSOLVE, s, 1, (double)L.n_nodes, (double)L.n_nodes * (dm - 1) * (dm - 1));
     CUDA_TRY(t, launch_backsolve(t, depth, t->Rbuf, s), "back-solve launch");
   }
-  {
+  if (t->P.precision == FMT_MIXED) {
+    // double-float Horner for the degrees of the tensor-core tier, FP64 above
+    ProfScope ps(K_RESIDUAL, s, 2, rows, L.horner_flops);
+    CUDA_TRY(t, launch_mixed_final_residual(t, depth, t->mx, s), "residual launch");
+    if (t->max_degree > FMT_MIXED_MAX_DEGREE)
+      CUDA_TRY(t, launch_residual(t, depth, s, FMT_MIXED_MAX_DEGREE + 1), "residual launch");
+  } else {
     ProfScope ps(K_RESIDUAL, s, 1, rows, L.horner_flops);
     CUDA_TRY(t, launch_residual(t, depth, s), "residual launch");
   }

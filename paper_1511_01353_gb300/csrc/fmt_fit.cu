@@ -1395,6 +1395,7 @@ struct ResArgs {
   const int64_t* node_start;  // checked build
   const int64_t* node_count;
   fmt_bounds bd;
+  int min_degree;  // nodes of lower degree are skipped (their residual is computed elsewhere)
 };
 
 #ifdef FMT_CHECKED
@@ -1423,6 +1424,7 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
   fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
   const int p = pr.degree, nm = fmt_nmono_d(p);
+  if (p < a.min_degree) return;
   const double* G = a.hcoef + (size_t)node * a.stride;
   for (int64_t i = rs + threadIdx.x; i < re; i += blockDim.x) {
     const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
@@ -1806,7 +1808,7 @@ cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s) {
+cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s, int min_degree) {
   const fmt_level& L = t->lv[depth];
   if (L.n_items <= 0) return cudaSuccess;
   ResArgs a;
@@ -1826,6 +1828,7 @@ cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s) {
   a.node_start = L.start;
   a.node_count = L.count;
   a.bd = level_bounds(t, depth);
+  a.min_degree = min_degree;
   k_residual<<<(unsigned)L.n_items, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

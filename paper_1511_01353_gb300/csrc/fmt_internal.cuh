@@ -458,7 +458,8 @@ size_t qr_smem_bytes(int m, int rows);
 cudaError_t launch_tile_qr(fmt_tree* t, int depth, double* R, cudaStream_t s, int mode = 0);  // may create side streams
 cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double* R, cudaStream_t s);
 cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream_t s);
-cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s);
+// r <- r - Lambda F in FP64 for the nodes of degree >= min_degree
+cudaError_t launch_residual(const fmt_tree* t, int depth, cudaStream_t s, int min_degree = 0);
 cudaError_t launch_child_stats(const fmt_tree* t, int depth, cudaStream_t s);
 
 // refine / evaluate
@@ -486,6 +487,8 @@ cudaError_t launch_mixed_gram(const fmt_tree* t, int depth, const fmt_mixed_bufs
 size_t mixed_cache_bytes(const fmt_tree* t, int depth);  // device bytes of the basis cache of a level
 cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
 cudaError_t launch_mixed_sresid(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
+// r <- r - Lambda F of a mixed level's nodes of degree <= FMT_MIXED_MAX_DEGREE (double-float Horner)
+cudaError_t launch_mixed_final_residual(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s);
 cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, bool last,
                                 cudaStream_t s);
 cudaError_t launch_probe_dfma(int64_t iters, int blocks, double* out, cudaStream_t s);

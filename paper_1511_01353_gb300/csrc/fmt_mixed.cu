@@ -315,6 +315,7 @@ struct MArgs {
   const int64_t* node_count;    // the count also keeps nearly square nodes off both tiers)
   fmt_bounds bd;
   int route_hard;               // route_hard(): nearly square nodes go straight to Householder
+  double* r_out;                // k_mresid_final: the residual, updated in place
 };
 // a nearly square node this level sends straight to Householder
 __device__ __forceinline__ bool routed_hard(const MArgs& a, int64_t node, const fmt_problem& pr) {
@@ -1201,6 +1202,39 @@ __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
     atomicMax(a.mstat + kMStat * node + 5, (unsigned long long)__double_as_longlong(ms));
 }
 
+// The residual update r <- r - Lambda F that ends a level of a mixed tree,
+// for the nodes of degree <= FMT_MIXED_MAX_DEGREE, whatever fitted them: the
+// polynomial in double-float as in the sweeps (an error of about 2^-48
+// |Lambda F|, far below the mixed bar and below the FP64 bar of the nodes
+// Householder fitted), frame and subtraction in FP64.  Nodes of higher
+// degree keep the FP64 residual (k_residual).
+__global__ void __launch_bounds__(256) k_mresid_final(MArgs a) {
+  const int item = blockIdx.x;
+  if (!FMT_CHECK(mixed_item_ok(a, item), CK_MIXED_ITEM)) return;
+  const int64_t node = a.item_node[item];
+  const fmt_problem& pr = a.prob[a.node_prob[node]];
+  const int p = pr.degree, nm = fmt_nmono_d(p);
+  if (p > FMT_MIXED_MAX_DEGREE) return;
+  const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
+  double c0, s0, c1, s1, c2, s2;
+  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  const double* Gc = a.hcoef + node * a.stride;
+  __shared__ float2 hdf[(FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6];
+  for (int k = threadIdx.x; k < nm; k += blockDim.x) {
+    const double g = Gc[k];
+    const float h = __double2float_rn(g);
+    hdf[k] = make_float2(h, __double2float_rn(g - (double)h));
+  }
+  __syncthreads();
+  for (int64_t i = a.item_start[item] + threadIdx.x; i < a.item_end[item]; i += blockDim.x) {
+    const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+    const dfl P = horner_df_shared(hdf, p, nm, df_of(u), df_of(v), df_of(w));
+    a.r_out[i] -= (double)P.h + (double)P.l;
+  }
+}
+
 // F += R^{-1} R^{-T} g per node; on the last sweep a node whose update is
 // still above kConvergedRel of its fit loses FMT_FLAG_MIXED.
 __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
@@ -1956,6 +1990,7 @@ MArgs make_margs(const fmt_tree* t, int depth, const fmt_mixed_bufs& b) {
   a.node_count = L.count;
   a.bd = level_bounds(t, depth);
   a.route_hard = route_hard(t, depth) ? 1 : 0;
+  a.r_out = t->r;
   return a;
 }
 
@@ -2048,6 +2083,14 @@ cudaError_t launch_mixed_sresid(const fmt_tree* t, int depth, const fmt_mixed_bu
   const fmt_level& L = t->lv[depth];
   if (L.n_items <= 0) return cudaSuccess;
   k_msresid<true><<<(unsigned)L.n_items, 256, 0, s>>>(make_margs(t, depth, b));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_final_residual(const fmt_tree* t, int depth, const fmt_mixed_bufs& b, cudaStream_t s) {
+  const fmt_level& L = t->lv[depth];
+  if (L.n_items <= 0) return cudaSuccess;
+  MArgs a = make_margs(t, depth, b);
+  k_mresid_final<<<(unsigned)L.n_items, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
