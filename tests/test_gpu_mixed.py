@@ -5,8 +5,9 @@ matrix formed on the tensor cores (split-BF16 digit tiles, FP32 accumulation,
 FP64 promotion), an FP64 Cholesky factor and FP64 refinement sweeps.  Nodes
 that tier cannot fit (ill-conditioned, not converged, degree above 9) go to
 its FP64 normal-equations tier (FP64 Gram, Cholesky, corrected semi-normal
-sweeps); what neither fits (rank-deficient, clamped root) goes to the FP64
-Householder path and then meets the FP64 bar of 1e-10.  The stated bar of
+sweeps); what neither fits (rank-deficient, clamped root), and the nearly
+square nodes of a level with few of them, go to the FP64 Householder path
+and then meet the FP64 bar of 1e-10.  The stated bar of
 the mixed path is an interpolant within 1e-6 * max|f| of the FP64 oracle.
 """
 import numpy as np
@@ -129,6 +130,25 @@ def test_degree_above_tensor_limit(degree):
     xq, yq, zq = rng.uniform(0, 1, (3, 2000))
     b, _ = T.evaluate(xq, yq, zq)
     assert np.max(np.abs(gpu_eval(tree, xq, yq, zq) - b)) / T.maxabs <= MIXED_TOL
+
+
+@pytest.mark.parametrize("degree,n", [(4, 40), (6, 110), (8, 200)])
+def test_nearly_square_nodes_take_householder(degree, n):
+    # fewer than 1.5 m points (m = nmono + 1), more than nmono: the node skips
+    # both normal-equations tiers, is refitted by Householder from the start
+    # of its level and meets the FP64 bar
+    rng = np.random.default_rng(10 + degree)
+    x, y, z = rng.uniform(0, 1, (3, n))
+    f = np.sin(2 * x) + y * z - z
+    from paper_1511_01353_gb300 import fmt as F
+    m = F.fmt_nmono(degree) + 1
+    assert m - 1 <= n < 1.5 * m
+    T = O.fit(x, y, z, f, degree, 0, 1, 0.0)
+    tree, ex, st = mixed_fit(x, y, z, f, degree, 0, 1, 0.0)
+    assert not (ex.flags[0] & 8) and int(st.mixed[0]) == 0
+    assert np.max(np.abs(ex.resid - T.resid)) <= FP64_TOL * T.maxabs
+    # the interpolant at the data points is f - r
+    assert np.max(np.abs(gpu_eval(tree, x, y, z) - (f - T.resid))) <= FP64_TOL * T.maxabs
 
 
 def test_clustered_nodes_across_the_tiers():
