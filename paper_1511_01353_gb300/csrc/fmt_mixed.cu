@@ -973,17 +973,70 @@ __global__ void __launch_bounds__(256) k_mreduce(MArgs a, int chunks) {
 // One CTA per node.  Shared: the packed upper triangle of the m x m Gram
 // (row i at ro(i), m = nmono + 1 with r last), the initial diagonal, y, F and
 // the change-of-basis scratch.
-// One warp: R x = y (x overwrites y).
-__device__ void warp_back_solve(const double* __restrict__ R, int m, int L, const double* __restrict__ invd,
-                                double* __restrict__ y) {
-  const int lane = threadIdx.x & 31;
-  for (int j = L - 1; j >= 0; --j) {
-    const double xj = y[j] * invd[j];
-    __syncwarp();
-    if (lane == 0) y[j] = xj;
-    for (int i = lane; i < j; i += 32) y[i] = fma(-R[ro_of(i, m) + (j - i)], xj, y[i]);
-    __syncwarp();
+// Triangular solves with R packed upper (row i at ro_of(i, m), entry j >= i
+// at offset j - i) and invd = 1 / R_ii, by the first kSolveThreads threads of
+// the CTA (four warps, one per SM sub-partition): at each step every thread
+// updates at most two entries, so a step costs about one FP64 instruction
+// per sub-partition instead of one warp's several.  The steps are ordered by
+// named barrier 1 (those threads only).
+constexpr int kSolveThreads = 128;
+__device__ __forceinline__ void solve_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kSolveThreads) : "memory"); }
+
+// Two unknowns per barrier: every thread forms both from shared memory (the
+// second one after the first one's term), then updates its entries with both.
+// R^T w = g (w overwrites g); returns |w|^2 in thread 0.
+__device__ double cta_fwd_solve(const double* __restrict__ R, int m, int L, const double* __restrict__ invd,
+                                double* __restrict__ g) {
+  const int t = threadIdx.x;
+  double wn = 0.0;
+  int k = 0;
+  for (; k + 1 < L; k += 2) {
+    const double* r0 = R + ro_of(k, m) - k;          // r0[j] = R[k][j]
+    const double* r1 = R + ro_of(k + 1, m) - (k + 1);  // r1[j] = R[k+1][j]
+    const double w0 = g[k] * invd[k];
+    const double w1 = fma(-r0[k + 1], w0, g[k + 1]) * invd[k + 1];
+    for (int j = k + 2 + t; j < L; j += kSolveThreads) g[j] = fma(-r1[j], w1, fma(-r0[j], w0, g[j]));
+    if (t == 0) wn = fma(w1, w1, fma(w0, w0, wn));
+    solve_bar();  // g[k + 2] is final; every thread has read g[k], g[k + 1]
+    if (t == 0) {
+      g[k] = w0;
+      g[k + 1] = w1;
+    }
   }
+  if (k < L) {
+    const double w0 = g[k] * invd[k];
+    if (t == 0) wn = fma(w0, w0, wn);
+    solve_bar();
+    if (t == 0) g[k] = w0;
+  }
+  solve_bar();
+  return wn;
+}
+
+// R x = y (x overwrites y).
+__device__ void cta_back_solve(const double* __restrict__ R, int m, int L, const double* __restrict__ invd,
+                               double* __restrict__ y) {
+  const int t = threadIdx.x;
+  int j = L - 1;
+  for (; j >= 1; j -= 2) {
+    const double x0 = y[j] * invd[j];
+    const double x1 = fma(-R[ro_of(j - 1, m) + 1], x0, y[j - 1]) * invd[j - 1];  // R[j-1][j]
+    for (int i = t; i < j - 1; i += kSolveThreads) {
+      const double* ri = R + ro_of(i, m) - i;  // ri[c] = R[i][c]
+      y[i] = fma(-ri[j - 1], x1, fma(-ri[j], x0, y[i]));
+    }
+    solve_bar();  // y[j - 2] is final; every thread has read y[j], y[j - 1]
+    if (t == 0) {
+      y[j] = x0;
+      y[j - 1] = x1;
+    }
+  }
+  if (j == 0) {
+    const double x0 = y[0] * invd[0];
+    solve_bar();
+    if (t == 0) y[0] = x0;
+  }
+  solve_bar();
 }
 
 __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
@@ -1111,7 +1164,7 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   // 3. R F = y, y = the scaled Q^T r column
   for (int k = tid; k < L; k += kFThreads) Fl[k] = G[ro_of(k, m) + (L - k)];
   __syncthreads();
-  if (tid < 32) warp_back_solve(G, m, L, invd, Fl);
+  if (tid < kSolveThreads) cta_back_solve(G, m, L, invd, Fl);
   __syncthreads();
   const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
   for (int k = tid; k < L; k += kFThreads) {
@@ -1272,21 +1325,10 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
   for (int k = tid; k < L; k += kFThreads) invd[k] = 1.0 / R[ro_of(k, m)];
   __syncthreads();
   double wn = 0.0;
-  if (tid < 32) {
+  if (tid < kSolveThreads) {
     // |R d|^2 = |R^{-T} g|^2 is taken between the two triangular solves
-    const int lane = tid;
-    for (int k = 0; k < L; ++k) {
-      const double wk = g[k] * invd[k];
-      __syncwarp();
-      if (lane == 0) {
-        g[k] = wk;
-        wn += wk * wk;
-      }
-      const double* rowk = R + ro_of(k, m) - k;
-      for (int j = k + 1 + lane; j < L; j += 32) g[j] = fma(-rowk[j], wk, g[j]);
-      __syncwarp();
-    }
-    warp_back_solve(R, m, L, invd, g);
+    wn = cta_fwd_solve(R, m, L, invd, g);
+    cta_back_solve(R, m, L, invd, g);
   }
   __syncthreads();
   for (int j = tid; j < L; j += kFThreads) {
@@ -1390,17 +1432,9 @@ __global__ void __launch_bounds__(kFThreads) k_mupdate(MArgs a) {
     for (int j = tid; j < L; j += kFThreads)
       g[j] = (((uint32_t)j * 2654435761u) >> 16) & 1u ? scale : -scale;
     __syncthreads();
-    if (tid < 32) {
-      const int lane = tid;
-      for (int k = 0; k < L; ++k) {
-        const double wk = g[k] * invd[k];
-        __syncwarp();
-        if (lane == 0) g[k] = wk;
-        const double* rowk = R + ro_of(k, m) - k;
-        for (int j = k + 1 + lane; j < L; j += 32) g[j] = fma(-rowk[j], wk, g[j]);
-        __syncwarp();
-      }
-      warp_back_solve(R, m, L, invd, g);
+    if (tid < kSolveThreads) {
+      cta_fwd_solve(R, m, L, invd, g);
+      cta_back_solve(R, m, L, invd, g);
     }
     __syncthreads();
     double ew = 0.0;
@@ -1706,7 +1740,7 @@ __global__ void __launch_bounds__(256) k_dfactor(MArgs a) {
   for (int k = tid; k < L; k += 256) Fl[k] = R[ro_of(k, m) + (L - k)];
   for (int k = tid; k < m; k += 256) R[ro_of(m, m) + k] = d0[k];  // the Gram's diagonal, after R (slot of m^2)
   __syncthreads();
-  if (tid < 32) warp_back_solve(R, m, L, invd, Fl);
+  if (tid < kSolveThreads) cta_back_solve(R, m, L, invd, Fl);
   __syncthreads();
   const MFrame F = mframe(pr, a.prefix[node], a.depth, a.mstat + kMStat * node);
   for (int k = tid; k < L; k += 256) {
@@ -1802,20 +1836,9 @@ __global__ void __launch_bounds__(kFThreads) k_dupdate(MArgs a) {
   }
   __syncthreads();
   double wn = 0.0;
-  if (tid < 32) {
-    const int lane = tid;
-    for (int k = 0; k < L; ++k) {  // R^T w = g, then |w|^2 = |R d|^2
-      const double wk = g[k] * invd[k];
-      __syncwarp();
-      if (lane == 0) {
-        g[k] = wk;
-        wn += wk * wk;
-      }
-      const double* rowk = R + ro_of(k, m) - k;
-      for (int j = k + 1 + lane; j < L; j += 32) g[j] = fma(-rowk[j], wk, g[j]);
-      __syncwarp();
-    }
-    warp_back_solve(R, m, L, invd, g);
+  if (tid < kSolveThreads) {
+    wn = cta_fwd_solve(R, m, L, invd, g);  // R^T w = g, then |w|^2 = |R d|^2
+    cta_back_solve(R, m, L, invd, g);
   }
   __syncthreads();
   for (int j = tid; j < L; j += kFThreads) {
@@ -1899,17 +1922,9 @@ __global__ void __launch_bounds__(kFThreads) k_dupdate(MArgs a) {
       g[j] = ((hsh >> 16) & 1u ? scale : -scale) * sqrt(d0[j]);
     }
     __syncthreads();
-    if (tid < 32) {
-      const int lane = tid;
-      for (int k = 0; k < L; ++k) {
-        const double wk = g[k] * invd[k];
-        __syncwarp();
-        if (lane == 0) g[k] = wk;
-        const double* rowk = R + ro_of(k, m) - k;
-        for (int j = k + 1 + lane; j < L; j += 32) g[j] = fma(-rowk[j], wk, g[j]);
-        __syncwarp();
-      }
-      warp_back_solve(R, m, L, invd, g);
+    if (tid < kSolveThreads) {
+      cta_fwd_solve(R, m, L, invd, g);
+      cta_back_solve(R, m, L, invd, g);
     }
     __syncthreads();
     double ew = 0.0;
