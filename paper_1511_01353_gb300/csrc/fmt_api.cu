@@ -386,6 +386,7 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
     pr.lo[2] = b ? b[2] : PP.lo[2];
     pr.side = b ? b[3] : PP.side;
     pr.S = 2097152.0 / pr.side;
+    pr.inv_side = 1.0 / pr.side;
     pr.degree = degrees ? degrees[i] : PP.degree;
     pr.start = offsets[i];
     pr.count = offsets[i + 1] - offsets[i];
@@ -1302,6 +1303,7 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
     for (int a = 0; a < 3; ++a) pr.lo[a] = plo[3 * i + a];
     pr.side = pside[i];
     pr.S = 2097152.0 / pr.side;
+    pr.inv_side = 1.0 / pr.side;
     pr.start = pstart[i];
     pr.count = pcount[i];
   }

@@ -169,9 +169,9 @@ __device__ __forceinline__ NodeGeom node_geom(const QRArgs& a, int64_t node) {
   g.m = fmt_nmono_d(g.q) + 1;
   g.ldB = fmt_ld_for(g.m);
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
-  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), g.c0, g.s0);
-  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), g.c1, g.s1);
-  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), g.c2, g.s2);
+  fmt_frame(pr.lo[0], pr.side, pr.inv_side, a.depth, fmt_compact3(pf), g.c0, g.s0);
+  fmt_frame(pr.lo[1], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 1), g.c1, g.s1);
+  fmt_frame(pr.lo[2], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 2), g.c2, g.s2);
   return g;
 }
 
@@ -1420,9 +1420,9 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
-  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
-  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
-  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  fmt_frame(pr.lo[0], pr.side, pr.inv_side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(pr.lo[1], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(pr.lo[2], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 2), c2, s2);
   const int p = pr.degree, nm = fmt_nmono_d(p);
   if (p < a.min_degree) return;
   const double* G = a.hcoef + (size_t)node * a.stride;
@@ -1879,7 +1879,7 @@ struct StaticArgs {
   double* r_out;
   double* coef;
   int32_t* flags;
-  double lo0, lo1, lo2, side;
+  double lo0, lo1, lo2, side, inv_side;
   int p, q, m, ldB, nmono_p;
   double* R;
 };
@@ -1904,9 +1904,9 @@ __global__ void __launch_bounds__(kQRThreads) k_fit_node_static(StaticArgs a) {
     if (k >= j) R[e] = 0.0;
   }
   double c0, s0, c1, s1, c2, s2;
-  fmt_frame(a.lo0, a.side, 0, 0u, c0, s0);
-  fmt_frame(a.lo1, a.side, 0, 0u, c1, s1);
-  fmt_frame(a.lo2, a.side, 0, 0u, c2, s2);
+  fmt_frame(a.lo0, a.side, a.inv_side, 0, 0u, c0, s0);
+  fmt_frame(a.lo1, a.side, a.inv_side, 0, 0u, c1, s1);
+  fmt_frame(a.lo2, a.side, a.inv_side, 0, 0u, c2, s2);
   __syncthreads();
   for (int64_t b0 = 0; b0 < a.n; b0 += NB) {
     const int nb = (int)((a.n - b0) < NB ? (a.n - b0) : NB);
@@ -2048,6 +2048,7 @@ extern "C" fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const doubl
   a.lo1 = lo[1];
   a.lo2 = lo[2];
   a.side = side;
+  a.inv_side = 1.0 / side;
   a.p = degree;
   a.q = q;
   a.m = fmt_nmono(q) + 1;

@@ -128,11 +128,14 @@ __device__ __forceinline__ uint32_t fmt_quant(double x, double lo, double S) {
 }
 
 // Node frame of Alg. 1: h = side 2^-(d+1), c = lo + (2i+1) h, s = 1/h.
-__device__ __forceinline__ void fmt_frame(double lo, double side, int depth, uint32_t i, double& c,
-                                          double& s) {
+// inv_side = 1/side rounded once on the host: h is side times a power of two,
+// so 1/h rounded is exactly inv_side 2^(d+1) (scaling by a power of two
+// commutes with rounding), which spares every frame a division.
+__device__ __forceinline__ void fmt_frame(double lo, double side, double inv_side, int depth, uint32_t i,
+                                          double& c, double& s) {
   double h = ldexp(side, -(depth + 1));
   c = __dadd_rn(lo, __dmul_rn((double)(2u * i + 1u), h));
-  s = __ddiv_rn(1.0, h);
+  s = ldexp(inv_side, depth + 1);
 }
 
 // u = (x - c) * s without contraction
@@ -251,7 +254,7 @@ struct fmt_problem {
   int32_t degree; // p
   int32_t q_root; // root degree after the N < nmono clamp
   int64_t start, count;
-  int64_t pad_;
+  double inv_side;  // 1 / side (fmt_frame)
 };
 
 // Node keys of a forest: the problem id sits above the 3d Morton bits of a

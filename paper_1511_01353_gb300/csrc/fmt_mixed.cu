@@ -240,9 +240,9 @@ __device__ __forceinline__ MFrame mframe(const fmt_problem& pr, uint64_t key, in
                                          const unsigned long long* ms) {
   MFrame F;
   const uint64_t pf = fmt_morton_part(key, depth);
-  fmt_frame(pr.lo[0], pr.side, depth, fmt_compact3(pf), F.c[0], F.s[0]);
-  fmt_frame(pr.lo[1], pr.side, depth, fmt_compact3(pf >> 1), F.c[1], F.s[1]);
-  fmt_frame(pr.lo[2], pr.side, depth, fmt_compact3(pf >> 2), F.c[2], F.s[2]);
+  fmt_frame(pr.lo[0], pr.side, pr.inv_side, depth, fmt_compact3(pf), F.c[0], F.s[0]);
+  fmt_frame(pr.lo[1], pr.side, pr.inv_side, depth, fmt_compact3(pf >> 1), F.c[1], F.s[1]);
+  fmt_frame(pr.lo[2], pr.side, pr.inv_side, depth, fmt_compact3(pf >> 2), F.c[2], F.s[2]);
   for (int a = 0; a < 3; ++a) {
     const double mu = __longlong_as_double((long long)ms[a]);
     int e = 0;
@@ -370,9 +370,9 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
   if (!tier2_eligible(pr, a.depth, routed_hard(a, node, pr))) return;  // the frame serves both tiers
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
-  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
-  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
-  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  fmt_frame(pr.lo[0], pr.side, pr.inv_side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(pr.lo[1], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(pr.lo[2], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 2), c2, s2);
   double mu = 0.0, mv = 0.0, mw = 0.0, mr = 0.0;
   for (int64_t i = a.item_start[item] + threadIdx.x; i < a.item_end[item]; i += blockDim.x) {
     mu = fmax(mu, fabs(fmt_local(a.x[i], c0, s0)));
@@ -1222,9 +1222,9 @@ __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
   const fmt_problem& pr = a.prob[a.node_prob[node]];
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
-  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
-  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
-  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  fmt_frame(pr.lo[0], pr.side, pr.inv_side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(pr.lo[1], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(pr.lo[2], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 2), c2, s2);
   const int p = pr.degree, nm = fmt_nmono_d(p);
   const double* Gc = a.hcoef + node * a.stride;
   __shared__ float2 hdf[kDF ? (FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6 : 1];
@@ -1270,9 +1270,9 @@ __global__ void __launch_bounds__(256) k_mresid_final(MArgs a) {
   if (p > FMT_MIXED_MAX_DEGREE) return;
   const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
   double c0, s0, c1, s1, c2, s2;
-  fmt_frame(pr.lo[0], pr.side, a.depth, fmt_compact3(pf), c0, s0);
-  fmt_frame(pr.lo[1], pr.side, a.depth, fmt_compact3(pf >> 1), c1, s1);
-  fmt_frame(pr.lo[2], pr.side, a.depth, fmt_compact3(pf >> 2), c2, s2);
+  fmt_frame(pr.lo[0], pr.side, pr.inv_side, a.depth, fmt_compact3(pf), c0, s0);
+  fmt_frame(pr.lo[1], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 1), c1, s1);
+  fmt_frame(pr.lo[2], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> 2), c2, s2);
   const double* Gc = a.hcoef + node * a.stride;
   __shared__ float2 hdf[(FMT_MIXED_MAX_DEGREE + 1) * (FMT_MIXED_MAX_DEGREE + 2) * (FMT_MIXED_MAX_DEGREE + 3) / 6];
   for (int k = threadIdx.x; k < nm; k += blockDim.x) {

@@ -451,17 +451,17 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
           continue;
         }
         double c0, s0, c1, s1, c2, s2;
-        fmt_frame(pr.lo[0], pr.side, d, fmt_compact3(mp), c0, s0);
-        fmt_frame(pr.lo[1], pr.side, d, fmt_compact3(mp >> 1), c1, s1);
-        fmt_frame(pr.lo[2], pr.side, d, fmt_compact3(mp >> 2), c2, s2);
+        fmt_frame(pr.lo[0], pr.side, pr.inv_side, d, fmt_compact3(mp), c0, s0);
+        fmt_frame(pr.lo[1], pr.side, pr.inv_side, d, fmt_compact3(mp >> 1), c1, s1);
+        fmt_frame(pr.lo[2], pr.side, pr.inv_side, d, fmt_compact3(mp >> 2), c2, s2);
         acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.stride, p, nm, fmt_local(x, c0, s0), fmt_local(y, c1, s1),
                           fmt_local(z, c2, s2));
       }
       if (deep >= 0) {
         double c0, s0, c1, s1, c2, s2;
-        fmt_frame(pr.lo[0], pr.side, deep, fmt_compact3(deep_mp), c0, s0);
-        fmt_frame(pr.lo[1], pr.side, deep, fmt_compact3(deep_mp >> 1), c1, s1);
-        fmt_frame(pr.lo[2], pr.side, deep, fmt_compact3(deep_mp >> 2), c2, s2);
+        fmt_frame(pr.lo[0], pr.side, pr.inv_side, deep, fmt_compact3(deep_mp), c0, s0);
+        fmt_frame(pr.lo[1], pr.side, pr.inv_side, deep, fmt_compact3(deep_mp >> 1), c1, s1);
+        fmt_frame(pr.lo[2], pr.side, pr.inv_side, deep, fmt_compact3(deep_mp >> 2), c2, s2);
         if (kDF) {
           const dfl v = fmt_horner_df(a.ccoef_df[deep] + (size_t)deep_idx * a.stride, p, nm,
                                       df_of(fmt_local(x, c0, s0)), df_of(fmt_local(y, c1, s1)),
