@@ -227,6 +227,7 @@ fmt_status alloc_level(fmt_tree* t, int d, int64_t cap_nodes, int64_t cap_items,
   TRY(talloc(t, &L.coef, nm * cap_nodes, s));
   TRY(talloc(t, &L.hcoef, nm * cap_nodes, s));
   TRY(talloc(t, &L.ccoef, nm * cap_nodes, s));
+  TRY(talloc(t, &L.frame, 6 * cap_nodes, s));
   if (t->P.precision == FMT_MIXED) TRY(talloc(t, &L.ccoef_df, nm * cap_nodes, s));
   TRY(talloc(t, &L.node_item0, cap_nodes, s));
   TRY(talloc(t, &L.node_nitems, cap_nodes, s));
@@ -387,6 +388,7 @@ fmt_status build_forest(const fmt_params* params, int64_t P, const int64_t* offs
     pr.side = b ? b[3] : PP.side;
     pr.S = 2097152.0 / pr.side;
     pr.inv_side = 1.0 / pr.side;
+    for (int a = 0; a < 3; ++a) pr.hi[a] = pr.lo[a] + pr.side;
     pr.degree = degrees ? degrees[i] : PP.degree;
     pr.start = offsets[i];
     pr.count = offsets[i + 1] - offsets[i];
@@ -1304,6 +1306,7 @@ fmt_status fmt_tree_import(const void* host_buf, size_t len, void* stream, fmt_t
     pr.side = pside[i];
     pr.S = 2097152.0 / pr.side;
     pr.inv_side = 1.0 / pr.side;
+    for (int a = 0; a < 3; ++a) pr.hi[a] = pr.lo[a] + pr.side;
     pr.start = pstart[i];
     pr.count = pcount[i];
   }

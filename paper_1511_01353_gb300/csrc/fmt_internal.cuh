@@ -119,12 +119,17 @@ __host__ __device__ inline uint32_t fmt_compact3(uint64_t v) {
 }
 
 // Exact quantisation: floor((x - lo) * S), S = 2^21/side, clamped; the
-// subtraction and the product are separately rounded (no contraction).
+// subtraction and the product are separately rounded (no contraction).  The
+// floor is one conversion to a 64-bit integer, which saturates (and sends a
+// NaN below zero), clamped with integer compares.
+__device__ __forceinline__ int64_t fmt_floor_scaled(double x, double lo, double S) {
+  return __double2ll_rd(__dmul_rn(__dsub_rn(x, lo), S));
+}
+__device__ __forceinline__ uint32_t fmt_clamp_q(int64_t f) {
+  return f < 0 ? 0u : (f > (int64_t)FMT_QMAX ? FMT_QMAX : (uint32_t)f);
+}
 __device__ __forceinline__ uint32_t fmt_quant(double x, double lo, double S) {
-  double t = __dmul_rn(__dsub_rn(x, lo), S);
-  if (!(t >= 0.0)) return 0u;
-  if (t >= 2097152.0) return FMT_QMAX;
-  return (uint32_t)floor(t);
+  return fmt_clamp_q(fmt_floor_scaled(x, lo, S));
 }
 
 // Node frame of Alg. 1: h = side 2^-(d+1), c = lo + (2i+1) h, s = 1/h.
@@ -255,6 +260,7 @@ struct fmt_problem {
   int32_t q_root; // root degree after the N < nmono clamp
   int64_t start, count;
   double inv_side;  // 1 / side (fmt_frame)
+  double hi[3];     // lo + side, rounded once (the cube's upper faces)
 };
 
 // Node keys of a forest: the problem id sits above the 3d Morton bits of a
@@ -290,6 +296,7 @@ struct fmt_level {
   double* child_E = nullptr;   // 8 per node: RMS
   double* coef = nullptr;      // nmono per node: F (Alg. 2 order)
   double* hcoef = nullptr;     // nmono per node: F / (l! m! n!) for Horner
+  double* frame = nullptr;     // 6 per node: c, s of x, y, z (fmt_frame), for evaluation
   double* ccoef = nullptr;     // nmono per node: the node's and all its ancestors' polynomials summed,
                                // as one polynomial in the node's frame (Horner form, like hcoef)
   float2* ccoef_df = nullptr;  // mixed trees: ccoef as double-float (hi, lo) for evaluation

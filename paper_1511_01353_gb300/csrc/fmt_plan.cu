@@ -392,6 +392,7 @@ struct EvalArgs {
   const double* hcoef[FMT_MAX_DEPTH + 1];
   const double* ccoef[FMT_MAX_DEPTH + 1];
   const float2* ccoef_df[FMT_MAX_DEPTH + 1];
+  const double* frame[FMT_MAX_DEPTH + 1];  // 6 per node: c, s per axis
   int64_t n_nodes[FMT_MAX_DEPTH + 1];
 };
 
@@ -422,17 +423,21 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
       }
       const fmt_problem& pr = a.prob[pid];
       const double x = xq[t], y = yq[t], z = zq[t];
-      const double hi0 = pr.lo[0] + pr.side, hi1 = pr.lo[1] + pr.side, hi2 = pr.lo[2] + pr.side;
-      outs = !(x >= pr.lo[0] && x <= hi0 && y >= pr.lo[1] && y <= hi1 && z >= pr.lo[2] && z <= hi2);
-      const uint64_t code = fmt_spread3(fmt_quant(x, pr.lo[0], pr.S)) |
-                            (fmt_spread3(fmt_quant(y, pr.lo[1], pr.S)) << 1) |
-                            (fmt_spread3(fmt_quant(z, pr.lo[2], pr.S)) << 2);
+      // fmt_quant's steps; inside the cube: x - lo >= 0 (its rounding keeps
+      // the sign; a NaN floors below zero) and x <= lo + side, per axis
+      const double dx = __dsub_rn(x, pr.lo[0]), dy = __dsub_rn(y, pr.lo[1]), dz = __dsub_rn(z, pr.lo[2]);
+      const int64_t fx = __double2ll_rd(__dmul_rn(dx, pr.S)), fy = __double2ll_rd(__dmul_rn(dy, pr.S)),
+                    fz = __double2ll_rd(__dmul_rn(dz, pr.S));
+      outs = !((fx | fy | fz) >= 0 &&
+               (__double_as_longlong(dx) | __double_as_longlong(dy) | __double_as_longlong(dz)) >= 0 &&
+               x <= pr.hi[0] && y <= pr.hi[1] && z <= pr.hi[2]);
+      const uint64_t code = fmt_spread3(fmt_clamp_q(fx)) | (fmt_spread3(fmt_clamp_q(fy)) << 1) |
+                            (fmt_spread3(fmt_clamp_q(fz)) << 2);
       int p = pr.degree, nm = fmt_nmono_d(p);
       if (!FMT_CHECK(p <= FMT_MAX_DEGREE && nm <= a.stride, CK_EVAL_NODE)) p = -1, nm = 0;  // no coefficient read
       double acc = 0.0;
       int deep = -1;
       int64_t deep_idx = 0;
-      uint64_t deep_mp = 0;
       for (int d = 0; d < a.n_levels; ++d) {
         const uint64_t mp = d == 0 ? 0ull : (code >> (3 * (FMT_QBITS - d)));
         const uint64_t P = ((uint64_t)pid << (3 * d)) | mp;
@@ -447,21 +452,15 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
         if (!outs) {
           deep = d;
           deep_idx = lo;
-          deep_mp = mp;
           continue;
         }
-        double c0, s0, c1, s1, c2, s2;
-        fmt_frame(pr.lo[0], pr.side, pr.inv_side, d, fmt_compact3(mp), c0, s0);
-        fmt_frame(pr.lo[1], pr.side, pr.inv_side, d, fmt_compact3(mp >> 1), c1, s1);
-        fmt_frame(pr.lo[2], pr.side, pr.inv_side, d, fmt_compact3(mp >> 2), c2, s2);
-        acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.stride, p, nm, fmt_local(x, c0, s0), fmt_local(y, c1, s1),
-                          fmt_local(z, c2, s2));
+        const double* fr = a.frame[d] + 6 * lo;  // the node's frame (k_make_cum)
+        acc += fmt_horner(a.hcoef[d] + (size_t)lo * a.stride, p, nm, fmt_local(x, fr[0], fr[1]),
+                          fmt_local(y, fr[2], fr[3]), fmt_local(z, fr[4], fr[5]));
       }
       if (deep >= 0) {
-        double c0, s0, c1, s1, c2, s2;
-        fmt_frame(pr.lo[0], pr.side, pr.inv_side, deep, fmt_compact3(deep_mp), c0, s0);
-        fmt_frame(pr.lo[1], pr.side, pr.inv_side, deep, fmt_compact3(deep_mp >> 1), c1, s1);
-        fmt_frame(pr.lo[2], pr.side, pr.inv_side, deep, fmt_compact3(deep_mp >> 2), c2, s2);
+        const double* fr = a.frame[deep] + 6 * deep_idx;
+        const double c0 = fr[0], s0 = fr[1], c1 = fr[2], s1 = fr[3], c2 = fr[4], s2 = fr[5];
         if (kDF) {
           const dfl v = fmt_horner_df(a.ccoef_df[deep] + (size_t)deep_idx * a.stride, p, nm,
                                       df_of(fmt_local(x, c0, s0)), df_of(fmt_local(y, c1, s1)),
@@ -499,6 +498,7 @@ struct CumArgs {
   const double* pccoef;
   int* err;
   int32_t n_problems;
+  double* frame;  // out: the node's frame, 6 per node
 };
 
 __global__ void __launch_bounds__(128) k_make_cum(CumArgs a) {
@@ -514,6 +514,14 @@ __global__ void __launch_bounds__(128) k_make_cum(CumArgs a) {
                  CK_CUM_NODE))
     return;
   const int p = a.prob[a.node_prob[node]].degree, P1 = p + 1, nm = fmt_nmono_d(p);
+  if (tid < 3) {  // the node frame evaluation reads (fmt_frame, axis tid)
+    const fmt_problem& pr = a.prob[a.node_prob[node]];
+    const uint64_t pf = fmt_morton_part(a.prefix[node], a.depth);
+    double c, s;
+    fmt_frame(pr.lo[tid], pr.side, pr.inv_side, a.depth, fmt_compact3(pf >> tid), c, s);
+    a.frame[6 * node + 2 * tid] = c;
+    a.frame[6 * node + 2 * tid + 1] = s;
+  }
   const double* own = a.hcoef + node * a.stride;
   double* out = a.ccoef + node * a.stride;
   if (a.depth > 0) {
@@ -727,6 +735,7 @@ cudaError_t launch_evaluate(const fmt_tree* t, int64_t m, const int32_t* tprob, 
     a.hcoef[d] = d < nf ? t->lv[d].hcoef : nullptr;
     a.ccoef[d] = d < nf ? t->lv[d].ccoef : nullptr;
     a.ccoef_df[d] = d < nf ? t->lv[d].ccoef_df : nullptr;
+    a.frame[d] = d < nf ? t->lv[d].frame : nullptr;
     a.n_nodes[d] = d < nf ? t->lv[d].n_nodes : 0;
   }
   bool df = t->P.precision == FMT_MIXED && nf > 0;
@@ -758,6 +767,7 @@ cudaError_t launch_make_cum(const fmt_tree* t, int depth, cudaStream_t s) {
   a.pccoef = depth > 0 ? t->lv[depth - 1].ccoef : nullptr;
   a.err = t->d_err;
   a.n_problems = (int32_t)t->n_problems;
+  a.frame = L.frame;
   const int P1 = t->max_degree + 1;
   k_make_cum<<<(unsigned)L.n_nodes, 128, sizeof(double) * (size_t)(P1 * P1 * P1), s>>>(a);
   return cudaGetLastError();
