@@ -228,7 +228,7 @@ fmt_status alloc_level(fmt_tree* t, int d, int64_t cap_nodes, int64_t cap_items,
   TRY(talloc(t, &L.hcoef, nm * cap_nodes, s));
   TRY(talloc(t, &L.ccoef, nm * cap_nodes, s));
   TRY(talloc(t, &L.frame, 6 * cap_nodes, s));
-  if (t->P.precision == FMT_MIXED) TRY(talloc(t, &L.ccoef_df, nm * cap_nodes, s));
+  if (t->P.precision == FMT_MIXED) TRY(talloc(t, &L.ccoef_df, ((nm + 1) & ~1) * cap_nodes, s));  // fmt_horner_df
   TRY(talloc(t, &L.node_item0, cap_nodes, s));
   TRY(talloc(t, &L.node_nitems, cap_nodes, s));
   TRY(talloc(t, &L.item_node, cap_items, s));

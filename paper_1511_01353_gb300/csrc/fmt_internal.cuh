@@ -210,17 +210,25 @@ __device__ __forceinline__ dfl df_add(dfl x, dfl y) {
 __device__ __forceinline__ dfl df_fma(dfl x, dfl w, dfl c) { return df_add(df_mul(x, w), c); }
 
 // The node polynomial of fmt_horner_t in double-float: the same nested Horner
-// order, coefficients G as (hi, lo) pairs.
-__device__ __forceinline__ dfl fmt_horner_df(const float2* __restrict__ G, int p, int nmono, dfl u, dfl v, dfl w) {
-  int idx = nmono - 1;
+// order, with the coefficients as (hi, lo) pairs stored in the order Horner
+// reads them (Gr[k] = G[nmono - 1 - k]) from a 16-byte boundary, so that one
+// 16-byte load brings two of them (the evaluation is bound by the number of
+// L1 sectors it reads: one coefficient per load, a target per thread, the
+// threads of a warp on different nodes).
+__device__ __forceinline__ int fmt_df_stride(int stride) { return (stride + 1) & ~1; }
+__device__ __forceinline__ dfl fmt_horner_df(const float2* __restrict__ Gr, int p, dfl u, dfl v, dfl w) {
+  const float4* G4 = reinterpret_cast<const float4*>(Gr);
+  int k = 0;
+  float4 pair = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   dfl P = {0.0f, 0.0f};
   for (int l = p; l >= 0; --l) {
     dfl t = {0.0f, 0.0f};
     for (int m = p - l; m >= 0; --m) {
       dfl s = {0.0f, 0.0f};
-      for (int n = p - l - m; n >= 0; --n) {
-        const float2 g = __ldg(G + idx--);
-        s = df_fma(s, w, dfl{g.x, g.y});
+      for (int n = p - l - m; n >= 0; --n, ++k) {
+        if (!(k & 1)) pair = __ldg(G4 + (k >> 1));
+        const dfl g = (k & 1) ? dfl{pair.z, pair.w} : dfl{pair.x, pair.y};
+        s = df_fma(s, w, g);
       }
       t = df_fma(t, v, s);
     }

@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a, int64_t m, const d
         const double* fr = a.frame[deep] + 6 * deep_idx;
         const double c0 = fr[0], s0 = fr[1], c1 = fr[2], s1 = fr[3], c2 = fr[4], s2 = fr[5];
         if (kDF) {
-          const dfl v = fmt_horner_df(a.ccoef_df[deep] + (size_t)deep_idx * a.stride, p, nm,
+          const dfl v = fmt_horner_df(a.ccoef_df[deep] + (size_t)deep_idx * fmt_df_stride(a.stride), p,
                                       df_of(fmt_local(x, c0, s0)), df_of(fmt_local(y, c1, s1)),
                                       df_of(fmt_local(z, c2, s2)));
           acc = (double)v.h + (double)v.l;
@@ -594,15 +594,16 @@ __global__ void __launch_bounds__(128) k_make_cum(CumArgs a) {
         if ((J & (blockDim.x - 1)) == tid) {
           const double v = own[J] + (a.depth > 0 ? cube[(l * P1 + m) * P1 + n] : 0.0);
           out[J] = v;
-          if (a.ccoef_df) {
+          if (a.ccoef_df) {  // reversed, for fmt_horner_df
             const float h = __double2float_rn(v);
-            a.ccoef_df[node * a.stride + J] = make_float2(h, __double2float_rn(v - (double)h));
+            a.ccoef_df[node * fmt_df_stride(a.stride) + (nm - 1 - J)] =
+                make_float2(h, __double2float_rn(v - (double)h));
           }
         }
-  for (int J = nm + tid; J < a.stride; J += blockDim.x) {
-    out[J] = 0.0;
-    if (a.ccoef_df) a.ccoef_df[node * a.stride + J] = make_float2(0.0f, 0.0f);
-  }
+  for (int J = nm + tid; J < a.stride; J += blockDim.x) out[J] = 0.0;
+  if (a.ccoef_df)
+    for (int k = nm + tid; k < fmt_df_stride(a.stride); k += blockDim.x)
+      a.ccoef_df[node * fmt_df_stride(a.stride) + k] = make_float2(0.0f, 0.0f);
 }
 
 // F / (l! m! n!) for imported trees (node degree from its problem; entries
