@@ -51,7 +51,7 @@ namespace {
 
 constexpr int kAtom = 64;        // rows per operand tile: one 128-byte swizzle row of BF16
 constexpr int kDrainAtoms = 4;   // projection: exact FP32 sums, promoted every 256 rows
-constexpr int kGramDrainAtoms = 8;  // Gram: FP32 sums (not exact anyway) promoted every 512 rows
+constexpr int kGramDrainAtoms = 16;  // Gram: FP32 sums (not exact anyway) promoted every 1024 rows
 constexpr int kFThreads = 256;   // factor / update kernels
 constexpr int kFPanel = 16;      // rows per panel of the factor's Cholesky
 constexpr double kPivotFloor = 1e-6;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256) k_mbox(MArgs a) {
 // the four pre-scaled digit tiles below.  Gram mode: the six leading tile
 // products (digit indices q_a + q_b <= 2, a split-BF16 product of about 24
 // bits) are accumulated together in FP32 in tensor memory and drained into a
-// double-float copy every 256 rows (not exact: the products' weights differ).
+// double-float copy every 1024 rows (not exact: the products' weights differ).
 // Projection mode: the basis tiles times the digits of s (FP64), both
 // values cut into four signed 8-bit digits of a fixed-point number
 // (|P_l(t)| <= 1 for |t| <= 1, and |s| is scaled below 1 per node):
