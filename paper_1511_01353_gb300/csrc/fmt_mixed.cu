@@ -14,7 +14,7 @@
 //     cores (tcgen05.mma kind::f16): the basis (in double-float) and r are
 //     cut into four fixed-point digits stored as BF16 tiles; the six leading
 //     digit-tile products are accumulated in FP32 in tensor memory, and every
-//     256 rows the accumulator is added into a double-float (FP32 pair) copy
+//     1024 rows the accumulator is added into a double-float (FP32 pair) copy
 //     in global memory; k_mreduce sums a node's items in FP64.
 //     The digit tiles are also stored in HBM (TMA bulk stores) for the sweeps.
 //  3. k_mfactor: per node, the item Grams are summed in FP64 and factorised by
@@ -23,11 +23,14 @@
 //  4. sweeps: s = r - Lambda F (k_msresid, double-float), g = B^T s on the tensor
 //     cores from the stored digit tiles (TMA bulk loads) and the integer
 //     digits of s, exactly (k_mgram projection mode), F += R^{-1} R^{-T} g
-//     (k_mupdate).
+//     (k_mupdate; the triangular solves on four warps).
 //  5. F is converted to the moment basis of Alg. 2 in the node frame (exact
 //     in the scaling, Legendre coefficients are dyadic rationals), so the
-//     residual update, the evaluation and the export are those of the FP64
-//     path.
+//     evaluation and the export are those of the FP64 path; the residual
+//     update r <- r - Lambda F evaluates it in double-float (k_mresid_final).
+// Nodes with fewer than 1.5 m points (nearly square) on a level with few of
+// them skip both tiers: their Householder refit starts with the level on a
+// side stream (launch_tile_qr mode 3, fmt_api.cu).
 // Acceptance, after every sweep: a node is settled (and skipped by the later
 // sweeps) once its change at the data is below kConvergedRel of the fit, its
 // change anywhere in the node box below kBoxChangeRel of the problem's
