@@ -149,6 +149,25 @@ def test_root_box_and_outside_targets():
     check_case(x, y, z, f, 3, 3, 20, 1e-5, xq, yq, zq, lo=lo, side=side)
 
 
+def test_targets_that_are_not_numbers_or_infinite():
+    # NaN and infinite targets lie outside every cube: counted in n_outside,
+    # and the targets beside them evaluate as they do alone
+    rng = np.random.default_rng(4)
+    x, y, z = rng.uniform(0, 1, (3, 2000))
+    f = np.cos(2 * x) * y + z
+    tree, ex = gpu_fit(x, y, z, f, 3, 3, 20, 1e-5)
+    xq, yq, zq = rng.uniform(0, 1, (3, 300))
+    base, n0 = gpu_eval(tree, xq, yq, zq)
+    assert n0 == 0
+    bad = [3, 50, 51, 199, 250]
+    xb, yb, zb = xq.copy(), yq.copy(), zq.copy()
+    xb[3], yb[50], zb[51], xb[199], yb[250] = np.nan, np.inf, -np.inf, -np.nan, np.nan
+    a, na = gpu_eval(tree, xb, yb, zb)
+    assert na == len(bad)
+    keep = np.setdiff1d(np.arange(300), bad)
+    assert np.array_equal(a[keep], base[keep])
+
+
 def test_evaluate_imported_oracle_tree():
     """Evaluation alone: upload the oracle's tree through fmt_tree_import."""
     from paper_1511_01353_gb300 import fmt as F
