@@ -654,6 +654,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
       const int natoms = (int)((re - rs + kAtom - 1) / kAtom);
       double* acc = kProj ? a.gacc + (int64_t)item * 256 : a.acc + (int64_t)item * a.acc_stride;
       const double* val = kProj ? a.s : a.r;
+      // phase A's operand of the next atom, loaded one atom ahead (a point
+      // coordinate for threads 0..191, the value for 192..255)
+      const double* pre_src = tid < 3 * kAtom ? (tid < kAtom ? a.x : tid < 2 * kAtom ? a.y : a.z) : val;
+      const bool pre_on = (tid < 3 * kAtom && cmode != 2) || (tid >= 3 * kAtom && tid < 4 * kAtom);
+      double pre = pre_on && rs + k < re ? pre_src[rs + k] : 0.0;
       bool first_drain = true;
       dfl g0 = {0.0f, 0.0f}, g1 = {0.0f, 0.0f};  // projection, threads < 128: sums of band 0 / 1 at lane tid
       int since = 0;
@@ -693,11 +698,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
         hi[st] = nw;
         // phase A: 1-D Legendre values (threads 0..191) and the value column (192..255)
         const int64_t i0 = rs + (int64_t)at * kAtom;
+        const double cur = pre;
+        if (pre_on) pre = i0 + kAtom + k < re ? pre_src[i0 + kAtom + k] : 0.0;
         if (tid < 3 * kAtom && cmode != 2) {
           const int ax = tid / kAtom;
           const int64_t i = i0 + k;
-          const double* X = ax == 0 ? a.x : ax == 1 ? a.y : a.z;
-          const double t = i < re ? fmt_local(X[i], F.c[ax], F.s[ax]) * F.ex[ax] : 0.0;
+          const double t = i < re ? fmt_local(cur, F.c[ax], F.s[ax]) * F.ex[ax] : 0.0;
           dfl* q = legd + ax * (p + 1) * kAtom + k;
           const dfl td = df_of(t);
           dfl qm = {1.0f, 0.0f}, q0 = td;
@@ -712,7 +718,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mgram(MArgs a) {
           }
         } else if (tid >= 3 * kAtom && tid < 4 * kAtom) {
           const int64_t i = i0 + k;
-          s_val[k] = i < re ? val[i] * vscale : 0.0;
+          s_val[k] = i < re ? cur * vscale : 0.0;
         }
         gen_bar();
         // phase B: products as pre-scaled digits; generator warp w takes a
