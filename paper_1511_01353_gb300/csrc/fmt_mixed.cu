@@ -1246,14 +1246,31 @@ __global__ void __launch_bounds__(256) k_msresid(MArgs a) {
     __syncthreads();
   }
   double ms = 0.0;
-  for (int64_t i = a.item_start[item] + threadIdx.x; i < a.item_end[item]; i += blockDim.x) {
-    const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
+  // each thread's next point is loaded while it evaluates the current one
+  const int64_t ie = a.item_end[item];
+  int64_t i = a.item_start[item] + threadIdx.x;
+  double nx = 0.0, ny = 0.0, nz = 0.0, nr = 0.0;
+  if (i < ie) {
+    nx = a.x[i];
+    ny = a.y[i];
+    nz = a.z[i];
+    nr = a.r[i];
+  }
+  for (; i < ie; i += blockDim.x) {
+    const double xv = nx, yv = ny, zv = nz, rv = nr;
+    if (i + blockDim.x < ie) {
+      nx = a.x[i + blockDim.x];
+      ny = a.y[i + blockDim.x];
+      nz = a.z[i + blockDim.x];
+      nr = a.r[i + blockDim.x];
+    }
+    const double u = fmt_local(xv, c0, s0), v = fmt_local(yv, c1, s1), w = fmt_local(zv, c2, s2);
     double si;
     if (kDF) {
       const dfl P = horner_df_shared(hdf, p, nm, df_of(u), df_of(v), df_of(w));
-      si = a.r[i] - ((double)P.h + (double)P.l);
+      si = rv - ((double)P.h + (double)P.l);
     } else {
-      si = a.r[i] - fmt_horner(Gc, p, nm, u, v, w);
+      si = rv - fmt_horner(Gc, p, nm, u, v, w);
     }
     a.s[i] = si;
     ms = fmax(ms, fabs(si));
@@ -1290,10 +1307,26 @@ __global__ void __launch_bounds__(256) k_mresid_final(MArgs a) {
     hdf[k] = make_float2(h, __double2float_rn(g - (double)h));
   }
   __syncthreads();
-  for (int64_t i = a.item_start[item] + threadIdx.x; i < a.item_end[item]; i += blockDim.x) {
-    const double u = fmt_local(a.x[i], c0, s0), v = fmt_local(a.y[i], c1, s1), w = fmt_local(a.z[i], c2, s2);
-    const dfl P = horner_df_shared(hdf, p, nm, df_of(u), df_of(v), df_of(w));
-    a.r_out[i] -= (double)P.h + (double)P.l;
+  const int64_t ie = a.item_end[item];
+  int64_t i = a.item_start[item] + threadIdx.x;
+  double nx = 0.0, ny = 0.0, nz = 0.0, nr = 0.0;  // the next point, loaded ahead
+  if (i < ie) {
+    nx = a.x[i];
+    ny = a.y[i];
+    nz = a.z[i];
+    nr = a.r_out[i];
+  }
+  for (; i < ie; i += blockDim.x) {
+    const double xv = nx, yv = ny, zv = nz, rv = nr;
+    if (i + blockDim.x < ie) {
+      nx = a.x[i + blockDim.x];
+      ny = a.y[i + blockDim.x];
+      nz = a.z[i + blockDim.x];
+      nr = a.r_out[i + blockDim.x];
+    }
+    const dfl P = horner_df_shared(hdf, p, nm, df_of(fmt_local(xv, c0, s0)), df_of(fmt_local(yv, c1, s1)),
+                                   df_of(fmt_local(zv, c2, s2)));
+    a.r_out[i] = rv - ((double)P.h + (double)P.l);
   }
 }
 
