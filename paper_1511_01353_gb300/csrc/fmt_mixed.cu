@@ -1096,8 +1096,10 @@ __global__ void __launch_bounds__(kFThreads) k_mfactor(MArgs a) {
   // per column, and full-warp FMAs).
   __shared__ double s_rkk, s_irk;
   __shared__ int s_bad;
+  double d0_next = tid == 0 ? diag0(0) : 0.0;  // thread 0: the next pivot's original diagonal, loaded ahead
   auto pivot = [&](int k) {  // thread 0
-    const double d = G[ro_of(k, m)], d0 = diag0(k);
+    const double d = G[ro_of(k, m)], d0 = d0_next;
+    if (k + 1 < L) d0_next = diag0(k + 1);
     s_bad = !(d0 > 0.0 && d > kPivotFloor * d0);
     if (!s_bad) {
       const double ir = rsqrt(d);
