@@ -42,7 +42,9 @@
 #include <stdio.h>
 
 #include <cooperative_groups.h>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "fmt_internal.cuh"
 
@@ -701,10 +703,12 @@ __global__ void __launch_bounds__(32 * kCombineWarps) k_combine(QRArgs a, int le
 // Householder steps.  Step j reflects row j of R_a with rows 0..j of R_b
 // (rows below j are still zero in column j); columns k > j are updated by
 // quads whose four lanes split the rows 0..j.  R_a's rows are streamed
-// through shared memory with a one-step prefetch, and the warp holding column
-// j+1 computes the next reflector (look-ahead), as in absorb_block.  Used
-// when the packed triangle fits in shared memory (m <= 166 with two CTAs per
-// SM); the merge is latency-bound, so it runs 16 warps.
+// through shared memory with a one-step prefetch.  The m steps form a chain
+// (reflector j+1 needs column j+1 after step j), so one warp per step
+// finalises column j+1 with all its lanes and forms reflector j+1 while the
+// other warps update the columns past it.  Used when the packed triangle
+// fits in shared memory (m <= 166 with two CTAs per SM); the merge is
+// latency-bound, so it runs 16 warps.
 constexpr int kMergeWarps = 16;
 constexpr int kMergeThreads = 32 * kMergeWarps;
 
@@ -733,11 +737,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
   for (int k = tid; k < m; k += kMergeThreads) Rs[k] = Ra[k];  // row 0 of R_a
   __syncthreads();
 
-  auto reflect = [&](int j, double* Rrow, double* scj) {  // one warp; as reflector()
+  // Reflector j from column j of R_b (rows 0..j), sq = its squared norm
+  // (the same value in every lane) and R_a[j][j]; one warp, as reflector().
+  auto reflect = [&](int j, double* Rrow, double* scj, double sq) {
     double* col = Bp + j * (j + 1) / 2;
-    double sq = 0.0;
-    for (int i = lane; i <= j; i += 32) sq = fma(col[i], col[i], sq);
-    sq = warp_sum(sq);
     const double alpha = Rrow[j];
     __syncwarp();
     if (sq == 0.0) {
@@ -760,7 +763,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
   };
   auto rot = [&](int jj) { return (tid - 32 * ((jj + (int)blockIdx.x) & (kMergeWarps - 1))) & (kMergeThreads - 1); };
   constexpr int kPF = (680 + kMergeThreads - 1) / kMergeThreads;
-  if (warp == 0) reflect(0, Rs, sc);
+  if (warp == 0) reflect(0, Rs, sc, Bp[0] * Bp[0]);
   double pf[kPF];
   {
     const int rt = rot(0);
@@ -771,6 +774,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
     }
   }
   __syncthreads();
+  // Step j: the warp of slot 0 finalises column j+1 alone (all 32 lanes on its
+  // rows 0..j, then its norm) and forms reflector j+1: the chain of dependent
+  // steps runs through that warp only, a few full-warp instructions per
+  // step.  The other warps update columns j+2 .. m-1 in quads, eight columns
+  // per warp and round.
   for (int j = 0; j < m; ++j) {
     const int cur = j & 1, nxt = cur ^ 1;
     double* Rc = Rs + cur * ldR;
@@ -780,7 +788,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
 #pragma unroll
       for (int e = 0; e < kPF; ++e) {
         const int k = j + 1 + rs + kMergeThreads * e;
-        if (k < m) Rn[k] = pf[e];
+        if (k < m) Rn[k] = pf[e];  // the slot-0 warp's lane 0 writes Rn[j + 1]
       }
       const int rp = rot(j + 1);
 #pragma unroll
@@ -793,10 +801,32 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
     const bool upd = gamma != 0.0;
     const double* xj = Bp + j * (j + 1) / 2;  // column j, rows 0..j
     const int slot = (warp - j - (int)blockIdx.x) & (kMergeWarps - 1);
-    int k0 = j + 1 + 8 * slot;
-    bool lookahead = (slot == 0) && (j + 1 < m);
-    for (;;) {
-      if (upd && k0 < m) {
+    if (slot == 0) {
+      if (j + 1 < m) {
+        double* cn = Bp + (j + 1) * (j + 2) / 2;  // column j+1
+        double sq = 0.0;
+        if (upd) {
+          double acc = 0.0;
+          for (int i = lane; i <= j; i += 32) acc = fma(xj[i], cn[i], acc);
+          acc = warp_sum(acc);
+          const double rv = Rc[j + 1];
+          const double d = gamma * fma(amb, rv, acc);
+          for (int i = lane; i <= j; i += 32) {
+            const double nv = fma(-d, xj[i], cn[i]);
+            cn[i] = nv;
+            sq = fma(nv, nv, sq);
+          }
+          if (lane == 0) Ra[(size_t)j * m + j + 1] = fma(-d, amb, rv);
+        } else {
+          for (int i = lane; i <= j; i += 32) sq = fma(cn[i], cn[i], sq);
+        }
+        if (lane == 0) sq = fma(cn[j + 1], cn[j + 1], sq);  // row j+1: no step has touched it
+        sq = warp_sum(sq);
+        __syncwarp();  // lane 0's Rn[j + 1] is visible to the warp
+        reflect(j + 1, Rn, sc + nxt * 2, sq);
+      }
+    } else if (upd) {
+      for (int k0 = j + 2 + 8 * (slot - 1); k0 < m; k0 += 8 * (kMergeWarps - 1)) {
         const int k = k0 + (lane >> 2);
         const bool act = k < m;
         double* ck = Bp + (act ? k * (k + 1) / 2 : j * (j + 1) / 2);  // column k (column j when idle)
@@ -829,15 +859,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(QRArgs a, int level) {
           for (; i2 <= j; i2 += 4) ck[i2] = fma(-d, xj[i2], ck[i2]);
           if (rg == 0) Ra[(size_t)j * m + k] = fma(-d, amb, rv);
         }
-        k0 += 8 * kMergeWarps;
       }
-      if (lookahead) {
-        __syncwarp();
-        reflect(j + 1, Rn, sc + nxt * 2);
-        lookahead = false;
-        continue;
-      }
-      if (!upd || k0 >= m) break;
     }
     __syncthreads();
   }
@@ -863,7 +885,10 @@ size_t merge_smem_bytes(int m) {
 // its own CTA passes j (acquire load), reading the reflector's scalars and
 // vector from the owner CTA's shared memory (distributed shared memory).  Each warp schedules its
 // groups as absorb_owned does: the task that finalises the next pivot
-// column first, else the oldest ready one.  Waits are bounded (kOwnSpinMax
+// column first, else the oldest ready one.  In that task all 32 lanes
+// update the pivot column and form its reflector, which is published before
+// the group's other columns are updated, so the chain of m dependent steps
+// costs a few full-warp instructions per step.  Waits are bounded (kOwnSpinMax
 // polls; FMT_ERR_TIMEOUT).  C = 1 is the same kernel on one SM.
 namespace cg = cooperative_groups;
 constexpr int kMCWarps = 8;
@@ -1067,27 +1092,58 @@ __global__ void __launch_bounds__(32 * kMCWarps) k_merge_cl(QRArgs a, int level)
     const double* sj = oj == rank ? scv : cta_ptr(scv, oj);
     const double gamma = sj[2 * j], amb = sj[2 * j + 1];
     const int rows = W * sel + W;
-    double nsq = 0.0;
-    if (gamma != 0.0) {
-      const double* vj = blk + L.off[gj] + (j % W);  // v_i at vj[vs i]
-      int vs = W;
-      if (oj != rank) {
-        // another CTA's column: one pipelined pass of remote loads into this
-        // warp's buffer (kept while the warp stays on the same reflector)
-        double* lv = vbuf + warp * m;
-        if (vcopy != j) {
-          const double* rv_ = cta_ptr(blk + L.off[gj], oj) + (j % W);
-          for (int i = lane; i <= j; i += 32) lv[i] = rv_[W * i];
-          __syncwarp();
-          vcopy = j;
-        }
-        vj = lv;
-        vs = 1;
+    const bool crit = (j + 1) / W == sel;  // column j+1 is in this group: the task finalises it
+    const int cq = (j + 1) % W;
+    const double* vj = blk + L.off[gj] + (j % W);  // v_i at vj[vs i]
+    int vs = W;
+    if (gamma != 0.0 && oj != rank) {
+      // another CTA's column: one pipelined pass of remote loads into this
+      // warp's buffer (kept while the warp stays on the same reflector)
+      double* lv = vbuf + warp * m;
+      if (vcopy != j) {
+        const double* rv_ = cta_ptr(blk + L.off[gj], oj) + (j % W);
+        for (int i = lane; i <= j; i += 32) lv[i] = rv_[W * i];
+        __syncwarp();
+        vcopy = j;
       }
+      vj = lv;
+      vs = 1;
+    }
+    if (crit) {
+      // column j+1 by all 32 lanes (its rows 0..j and its norm), then
+      // reflector j+1: the chain of dependent steps passes through here
+      double* cc = blk + L.off[sel] + cq;  // R_b row i at cc[W i]
+      double sq = 0.0;
+      if (gamma != 0.0) {
+        double* ac = cc + W * (rows + j);  // R_a[j][j+1]
+        const double rvc = *ac;
+        double acc = 0.0;
+        for (int i = lane; i <= j; i += 32) acc = fma(vj[vs * i], cc[W * i], acc);
+        acc = warp_sum(acc);
+        const double d = gamma * fma(amb, rvc, acc);
+        for (int i = lane; i <= j; i += 32) {
+          const double nv = fma(-d, vj[vs * i], cc[W * i]);
+          cc[W * i] = nv;
+          sq = fma(nv, nv, sq);
+        }
+        __syncwarp();  // every lane has read R_a[j][j+1]
+        if (lane == 0) *ac = fma(-d, amb, rvc);
+      } else {
+        // no reflection at step j: column j+1's rows 0..j are unchanged
+        for (int i = lane; i <= j; i += 32) sq = fma(cc[W * i], cc[W * i], sq);
+      }
+      const double s = warp_sum(sq);
+      const double bjj = cc[W * (j + 1)];  // row j+1 of column j+1 (no step has touched it)
+      __syncwarp();
+      reflect_publish(j + 1, fma(bjj, bjj, s));
+      if (P < j + 2) P = j + 2;
+    }
+    // the group's columns past j (past j+1 when column j+1 was done above), LW lanes each
+    if (gamma != 0.0 && !(crit && cq == W - 1)) {
       double* ck = blk + L.off[sel] + qi;  // R_b column W sel + qi: row i at ck[W i]
       double* ak = ck + W * (rows + j);    // R_a[j][W sel + qi]
       const int k = W * sel + qi;
-      const bool act = k > j && k < m;
+      const bool act = k > (crit ? j + 1 : j) && k < m;
       const double rv = *ak;
       double a0 = 0.0, a1 = 0.0;
       int i = rg;
@@ -1101,38 +1157,12 @@ __global__ void __launch_bounds__(32 * kMCWarps) k_merge_cl(QRArgs a, int level)
       for (int o = 1; o < LW; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (act) {
         const double d = gamma * fma(amb, rv, acc);
-        double sq = 0.0;  // squares of the updated rows (the next pivot column's norm)
-        for (int i2 = rg; i2 <= j; i2 += LW) {
-          const double nv = fma(-d, vj[vs * i2], ck[W * i2]);
-          ck[W * i2] = nv;
-          sq = fma(nv, nv, sq);
-        }
+        for (int i2 = rg; i2 <= j; i2 += LW) ck[W * i2] = fma(-d, vj[vs * i2], ck[W * i2]);
         if (rg == 0) *ak = fma(-d, amb, rv);
-        nsq = sq;
       }
     }
     if (lane == srcl) mv = j + 1;
-    if ((j + 1) / W == sel) {  // column j+1 is final: reflector j+1
-      // its norm: the updated rows 0..j (summed over the column's LW lanes) and row j+1
-      const int cq = (j + 1) % W;
-      double s;
-      if (gamma != 0.0) {
-        double part = lane / LW == cq ? nsq : 0.0;
-#pragma unroll
-        for (int o = 1; o < LW; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        s = __shfl_sync(0xffffffffu, part, cq * LW);
-      } else {
-        // no reflection at step j: column j+1's rows 0..j are unchanged
-        double part = 0.0;
-        const double* cc = blk + L.off[sel] + cq;
-        for (int i = lane; i <= j; i += 32) part = fma(cc[W * i], cc[W * i], part);
-        s = warp_sum(part);
-      }
-      const double bjj = blk[L.off[sel] + cq + W * (j + 1)];  // row j+1 of column j+1 (no step has touched it)
-      __syncwarp();
-      reflect_publish(j + 1, fma(bjj, bjj, s));
-      if (P < j + 2) P = j + 2;
-    } else {
+    if (!crit) {
       int v = 0;
       if (lane == 0) v = mc_read<C>(pub_addr);
       v = __shfl_sync(0xffffffffu, v, 0);
@@ -1168,7 +1198,7 @@ size_t merge_cl_smem_bytes(int m, int C, int W) {
 
 template <int C, int LW>
 cudaError_t merge_cl_launch(const QRArgs& a, int64_t n_items, size_t smem, int level, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_merge_cl<C, LW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = fmt_smem_at_least((const void*)k_merge_cl<C, LW>, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_items * C));
@@ -1512,10 +1542,9 @@ constexpr int combine_rpt() { return RPT > 16 ? 16 : RPT; }
 
 template <int RPT, int NW>
 cudaError_t set_smem_attr(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_tile_qr<RPT, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = fmt_smem_at_least((const void*)k_tile_qr<RPT, NW>, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_combine<combine_rpt<RPT>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  return fmt_smem_at_least((const void*)k_combine<combine_rpt<RPT>()>, smem);
 }
 
 int ld_for(int m) { return fmt_ld_for(m); }
@@ -1770,7 +1799,7 @@ cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double*
     }
   }
   if (cfg.merge == 0 && msm <= 200 * 1024) {
-    if ((e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm)) != cudaSuccess)
+    if ((e = fmt_smem_at_least((const void*)k_merge, msm)) != cudaSuccess)
       return e;
     k_merge<<<(unsigned)n_items, kMergeThreads, msm, s>>>(a, tree_level);
     return cudaGetLastError();
@@ -1800,7 +1829,7 @@ cudaError_t launch_backsolve(const fmt_tree* t, int depth, double* R, cudaStream
   a.n_items = L.n_items;
   a.bd = level_bounds(t, depth);
   const size_t smem = 4 * (size_t)a.ws * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = fmt_smem_at_least((const void*)k_backsolve, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((L.n_nodes + 3) / 4);
   if (grid == 0) return cudaSuccess;
@@ -1968,8 +1997,8 @@ unsigned long long current_ctx_id() {
   typedef int (*ctx_get_id_t)(void*, unsigned long long*);
   static ctx_get_current_t get_current = nullptr;
   static ctx_get_id_t get_id = nullptr;
-  static bool looked_up = false;
-  if (!looked_up) {
+  static std::once_flag looked_up;
+  std::call_once(looked_up, [] {
     void* a = nullptr;
     void* b = nullptr;
     cudaDriverEntryPointQueryResult qa, qb;
@@ -1980,8 +2009,7 @@ unsigned long long current_ctx_id() {
       get_id = (ctx_get_id_t)b;
     }
     cudaGetLastError();
-    looked_up = true;
-  }
+  });
   void* ctx = nullptr;
   unsigned long long id = 0;
   if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
@@ -1989,6 +2017,22 @@ unsigned long long current_ctx_id() {
 }
 
 }  // namespace
+
+// The largest limit set so far per (context, kernel).  A context id of 0
+// (the driver query unavailable) still never lowers a limit: the largest
+// value seen for the kernel is set again.
+cudaError_t fmt_smem_at_least(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<unsigned long long, const void*>, size_t> lim;
+  const unsigned long long ctx = current_ctx_id();
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = lim[std::make_pair(ctx, func)];
+  if (ctx != 0 && bytes <= cur) return cudaSuccess;
+  const size_t want = bytes > cur ? bytes : cur;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+  if (e == cudaSuccess) cur = want;
+  return e;
+}
 
 extern "C" fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const double* x, const double* y,
                                           const double* z, const double* r_in, const double* lo, double side,
@@ -2056,7 +2100,7 @@ extern "C" fmt_status fmt_fit_node_static(int32_t degree, int64_t n, const doubl
   a.nmono_p = fmt_nmono(degree);
   a.R = R;
   const size_t smem = ((size_t)66 * a.ldB + 4 + a.nmono_p) * sizeof(double);
-  e = cudaFuncSetAttribute(k_fit_node_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = fmt_smem_at_least((const void*)k_fit_node_static, smem);
   if (e == cudaSuccess) {
     k_fit_node_static<<<1, kQRThreads, smem, (cudaStream_t)stream>>>(a);
     e = cudaGetLastError();

@@ -436,6 +436,14 @@ inline fmt_bounds level_bounds(const fmt_tree* t, int depth) {
 // Records msg as the calling thread's last error (fmt_last_error(NULL)).
 fmt_status fmt_set_error(fmt_status st, const char* msg);
 
+// Raises the dynamic shared-memory limit of kernel `func` on the current
+// device to at least `bytes` (cudaFuncAttributeMaxDynamicSharedMemorySize),
+// never lowering it.  The limit belongs to the function in each context, not
+// to a launch: threads that launch the same kernel with different needs (the
+// serving engine's worker slots, or any caller fitting trees from several
+// threads) must not lower it between another thread's setting and launch.
+cudaError_t fmt_smem_at_least(const void* func, size_t bytes);
+
 // ---------------------------------------------------------------------------
 // Launchers (return cudaGetLastError() of the launch).
 

@@ -2072,7 +2072,7 @@ cudaError_t launch_gram_t(const fmt_tree* t, int depth, const fmt_mixed_bufs& b,
   const size_t fixed = 1024 + kLegBytes + 12 * 1024;  // alignment, Legendre table, static shared
   a.nstages = fixed + 2 * stage <= 227 * 1024 ? 2 : 1;
   const size_t smem = 1024 + kLegBytes + a.nstages * stage;
-  cudaError_t e = cudaFuncSetAttribute(k_mgram<kProj>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = fmt_smem_at_least((const void*)k_mgram<kProj>, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgram<kProj>, kGThreads, smem)) != cudaSuccess)
@@ -2132,7 +2132,7 @@ cudaError_t launch_mixed_factor(const fmt_tree* t, int depth, const fmt_mixed_bu
   const size_t smem = mixed_factor_smem(mixed_m_cap(L.max_m));
   cudaError_t e = cudaMemsetAsync(t->d_work + kPivSlot, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_mfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = fmt_smem_at_least((const void*)k_mfactor, smem);
   if (e != cudaSuccess) return e;
   k_mfactor<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(make_margs(t, depth, b));
   return cudaGetLastError();
@@ -2161,7 +2161,7 @@ cudaError_t launch_mixed_update(const fmt_tree* t, int depth, const fmt_mixed_bu
   a.last_sweep = last ? 1 : 0;
   const int mc = mixed_m_cap(L.max_m);
   const size_t smem = sizeof(double) * ((size_t)ro_of(mc, mc) + 3 * (size_t)mc);
-  cudaError_t e = cudaFuncSetAttribute(k_mupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = fmt_smem_at_least((const void*)k_mupdate, smem);
   if (e != cudaSuccess) return e;
   k_mupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
   return cudaGetLastError();
@@ -2184,7 +2184,7 @@ cudaError_t launch_tier2_factor(const fmt_tree* t, int depth, const fmt_mixed_bu
   const fmt_level& L = t->lv[depth];
   if (L.n_nodes <= 0) return cudaSuccess;
   const size_t smem = tier2_factor_smem(L.max_m);
-  cudaError_t e = cudaFuncSetAttribute(k_dfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = fmt_smem_at_least((const void*)k_dfactor, smem);
   if (e != cudaSuccess) return e;
   k_dfactor<<<(unsigned)L.n_nodes, 256, smem, s>>>(make_margs(t, depth, b));
   return cudaGetLastError();
@@ -2203,7 +2203,7 @@ cudaError_t launch_tier2_sweep(const fmt_tree* t, int depth, const fmt_mixed_buf
     k_dproj<<<(unsigned)L.n_items, 256, 0, s>>>(a);
   } else {
     const size_t smem = sizeof(double) * (3 * (size_t)L.max_m + conv_ws_doubles(FMT_MAX_DEGREE));
-    cudaError_t e = cudaFuncSetAttribute(k_dupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = fmt_smem_at_least((const void*)k_dupdate, smem);
     if (e != cudaSuccess) return e;
     k_dupdate<<<(unsigned)L.n_nodes, kFThreads, smem, s>>>(a);
   }
