@@ -337,3 +337,21 @@ def test_import_validates_the_blob_before_touching_the_device():
                   patch(prob_at + 8 + 8 + 8, "<d", float("inf"))]   # problem lo
     for i, b in enumerate(bad_bodies):
         assert imp(b) == F.FMT_EINVAL, i
+
+
+def test_shared_memory_limits_go_through_the_never_lowering_helper():
+    # The dynamic shared-memory limit belongs to a kernel, not to one launch:
+    # a launcher that set it directly to its own need could lower it under
+    # another thread's launch of the same kernel.  Only fmt_smem_at_least,
+    # which raises the limit and never lowers it, calls the runtime for it.
+    csrc = os.path.join(ROOT, "paper_1511_01353_gb300", "csrc")
+    calls = []
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            src = open(os.path.join(csrc, fn)).read()
+            for m in re.finditer(r"cudaFuncSetAttribute\s*\(", src):
+                calls.append((fn, src.count("\n", 0, m.start())))
+    assert len(calls) == 1, calls
+    fn, line = calls[0]
+    before = open(os.path.join(csrc, fn)).read().splitlines()[max(0, line - 12):line]
+    assert any("fmt_smem_at_least(" in s for s in before), (fn, line)
