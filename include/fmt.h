@@ -24,6 +24,12 @@
  *    coefficients; fmt_tree_free releases them.
  *  - Errors are sticky per tree: after a device-side error every later call
  *    on that tree returns the same status.
+ *  - Threads: calls on different trees may run at the same time from
+ *    different host threads, each on its own stream (the library's shared
+ *    state -- launch limits, the tuning table, the profile counters, the
+ *    memory pool -- is guarded).  One tree is used by one thread at a time.
+ *    fmt_tune_set and fmt_autotune change the table that later fits read, so
+ *    they belong between fits, not beside them.
  *  - Precision: everything on the FP64 path is IEEE binary64.  The
  *    quantisation and node-frame arithmetic use no fused multiply-add so the
  *    tree structure is bit-reproducible.  The mixed path (FMT_MIXED) forms
