@@ -1799,9 +1799,22 @@ cudaError_t launch_combine(const fmt_tree* t, int depth, int tree_level, double*
     }
   }
   if (cfg.merge == 0 && msm <= 200 * 1024) {
-    if ((e = fmt_smem_at_least((const void*)k_merge, msm)) != cudaSuccess)
+    // Fewer pairs than SMs: the launch asks for more than half of an SM's
+    // shared memory, so one CTA fits per SM and no SM runs two merges while
+    // others idle (a merge is one CTA's work; the CTAs of the pairs' second
+    // items exit at once).
+    size_t lsm = msm;
+    int dev = 0, nsm = 0, smsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess) {
+      const size_t one = (size_t)smsm / 2 + 1024;
+      if (est < nsm && one > lsm && one <= 200 * 1024) lsm = one;
+    }
+    cudaGetLastError();
+    if ((e = fmt_smem_at_least((const void*)k_merge, lsm)) != cudaSuccess)
       return e;
-    k_merge<<<(unsigned)n_items, kMergeThreads, msm, s>>>(a, tree_level);
+    k_merge<<<(unsigned)n_items, kMergeThreads, lsm, s>>>(a, tree_level);
     return cudaGetLastError();
   }
   // the packed triangle does not fit (large degrees) or the configuration
