@@ -28,6 +28,8 @@
  *    different host threads, each on its own stream (the library's shared
  *    state -- launch limits, the tuning table, the profile counters, the
  *    memory pool -- is guarded).  One tree is used by one thread at a time.
+ *    fmt_fit_node_static is the exception: its calls share one scratch
+ *    array per device and must be ordered (see there).
  *    fmt_tune_set and fmt_autotune change the table that later fits read, so
  *    they belong between fits, not beside them.
  *  - Precision: everything on the FP64 path is IEEE binary64.  The
